@@ -1,0 +1,84 @@
+"""Pins for oracle.rng and oracle.sphynx (Algorithm 2 and Eq. 4)."""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle.rng import mix64, GAMMA
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_splitmix64_reference_outputs():
+    ref = [int(line, 16) for line in open(os.path.join(GOLDEN, "splitmix64_seed0.txt"))
+           if line.strip() and not line.startswith("#")]
+    assert [mix64(GAMMA * (i + 1)) for i in range(3)] == ref
+
+
+def test_random_block_layout_and_range():
+    x = O.splitmix64_block(5, 3, 42)
+    state = mix64(42 + GAMMA)
+    z = mix64(state + 4 * GAMMA)          # counter i*b + j + 1 for (1, 0)
+    assert x[1, 0] == 2.0 * ((z >> 11) * 2.0 ** -53) - 1.0
+    assert np.all(x >= -1.0) and np.all(x < 1.0)
+
+
+def test_eq4_number_of_eigenvectors():
+    assert O.num_eigenvectors(4) == 3       # worked example of Sec. 4
+    assert O.num_eigenvectors(24) == 5      # Sec. 6.4: 4 coordinate vectors for K = 24
+    assert O.num_eigenvectors(1) == 1
+    assert [O.num_eigenvectors(k) for k in (64, 256, 8, 1024)] == [7, 9, 4, 11]
+
+
+def test_piecewise_initial_block():
+    g = W.grid2d(5, 4)
+    x = O.initial_block(g, O.COMBINATORIAL, 3, "piecewise", 0)
+    assert np.all(x[:, 0] == 1.0)
+    assert list(x[:, 1]) == [1.0] * 6 + [0.0] * 14
+    assert list(x[:, 2]) == [0.0] * 6 + [1.0] * 7 + [0.0] * 7
+    xn = O.initial_block(g, O.NORMALIZED, 3, "piecewise", 0)
+    assert np.allclose(xn[:, 0], np.sqrt(O.weighted_degree(g)))
+
+
+def test_two_cliques_bisect_on_the_bridge():
+    a, b = np.triu_indices(8, 1)
+    src = np.concatenate([a, a + 8, [7]])
+    dst = np.concatenate([b, b + 8, [8]])
+    g = W.symmetrize_edges(16, src, dst)
+    for prob in (O.COMBINATORIAL, O.GENERALIZED, O.NORMALIZED):
+        r = O.partition(g, 2, problem=prob, tol=1e-6, seed=3)
+        assert r.cut == 1 and r.imbalance == 1.0
+        assert len(set(r.parts[:8])) == 1 and len(set(r.parts[8:])) == 1
+
+
+def test_rectangular_grid_fiedler_bisection():
+    g = W.grid2d(64, 48)
+    r = O.partition(g, 2, tol=1e-6, seed=1)
+    assert r.status == "ok"
+    assert r.cut == 48 and r.imbalance == 1.0
+
+
+def test_c1_small_grid_partition_quality():
+    g = W.grid2d(64, 64)
+    r = O.partition(g, 4, problem=O.COMBINATORIAL, precond="jacobi", tol=1e-2, seed=1)
+    exact = 2 - 2 * np.cos(np.pi / 64)
+    assert r.status == "ok"
+    assert np.allclose(r.eigenvalues[1:], exact, rtol=1e-3)
+    assert r.imbalance == 1.0
+    # lambda_2 = lambda_3: any rotation of the pair is a valid embedding, so
+    # only a loose bound holds (two straight cuts give 128)
+    assert 128 <= r.cut <= 4 * 64
+
+
+@pytest.mark.parametrize("prob,pc", [(O.GENERALIZED, "poly"), (O.NORMALIZED, "poly"),
+                                     (O.GENERALIZED, "jacobi"), (O.NORMALIZED, "none")])
+def test_problem_and_preconditioner_variants_agree_on_spectrum(prob, pc):
+    g = W.grid2d(30, 22)
+    r = O.partition(g, 8, problem=prob, precond=pc, tol=1e-6, seed=2, poly_degree=8)
+    assert r.status == "ok"
+    ref = np.linalg.eigvalsh(O.laplacian_normalized(g).toarray())[:4]
+    assert np.allclose(r.eigenvalues, ref, rtol=1e-5, atol=1e-12)
+    assert r.imbalance == 83 * 8 / 660      # 660 unit vertices into 8 parts: best is 83

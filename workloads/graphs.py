@@ -1,0 +1,336 @@
+"""Seeded synthetic graphs in CSR form.
+
+Every generator returns a :class:`CSRGraph` describing a simple undirected
+graph: symmetric adjacency, sorted column indices per row, no duplicate
+entries and no self-loops.  The paper's inputs are symmetrised as A + A^T + I
+and reduced to their largest connected component (Sec. 6.1); the diagonal
+``I`` is the Laplacian's business, so the adjacency stored here carries only
+off-diagonal entries and the structure count with the diagonal is
+``nnz + n``.
+
+Random draws come from a counter-based SplitMix64 stream (Steele, Lea and
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014) so that a
+graph is the same bit for bit on every machine and numpy version.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function applied element-wise (uint64, wrapping)."""
+    z = z.astype(np.uint64, copy=True)
+    with np.errstate(over="ignore"):
+        z ^= z >> np.uint64(30)
+        z *= _M1
+        z ^= z >> np.uint64(27)
+        z *= _M2
+        z ^= z >> np.uint64(31)
+    return z
+
+
+def _stream_key(seed: int, stream: int) -> np.uint64:
+    with np.errstate(over="ignore"):
+        base = np.array([(seed * 0x632BE59BD9B4E019 + stream * 0x9E3779B97F4A7C15 + 0x5851F42D4C957F2D)
+                         & 0xFFFFFFFFFFFFFFFF], dtype=np.uint64)
+    return _mix64(base)[0]
+
+
+def uniform01(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    """``count`` doubles in [0, 1) from counter ``offset .. offset+count-1``."""
+    key = _stream_key(seed, stream)
+    ctr = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = _mix64(key + ctr * _GOLDEN)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+@dataclasses.dataclass
+class CSRGraph:
+    """Undirected simple graph: ``row_ptr`` int64 (n+1), ``col`` int32 (nnz)."""
+
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    w: Optional[np.ndarray] = None  # float32 per stored entry, symmetric
+    name: str = ""
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.row_ptr)
+
+    def rows(self) -> np.ndarray:
+        """Row index of every stored entry (int64)."""
+        return np.repeat(np.arange(self.n, dtype=np.int64), np.diff(self.row_ptr))
+
+
+def _from_sorted_pairs(n: int, rows: np.ndarray, cols: np.ndarray, w=None, name="") -> CSRGraph:
+    counts = np.bincount(rows, minlength=n).astype(np.int64)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return CSRGraph(n=n, row_ptr=row_ptr, col=cols.astype(np.int32), w=w, name=name)
+
+
+def symmetrize_edges(n: int, src: np.ndarray, dst: np.ndarray, name: str = "") -> CSRGraph:
+    """Simple undirected graph from a directed edge list: A + A^T with
+    self-loops dropped and duplicate entries merged."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    keep = src != dst
+    a = np.minimum(src[keep], dst[keep])
+    b = np.maximum(src[keep], dst[keep])
+    key = np.unique(a * n + b)
+    a = key // n
+    b = key % n
+    del key
+    rows = np.concatenate([a, b])
+    cols = np.concatenate([b, a])
+    del a, b
+    order = np.argsort(rows * n + cols, kind="stable")
+    rows = rows[order]
+    cols = cols[order]
+    return _from_sorted_pairs(n, rows, cols, name=name)
+
+
+def _offsets_csr(shape, offsets, periodic: bool, name: str) -> CSRGraph:
+    """CSR of a structured grid whose vertex (x, y, z, ...) is numbered
+    x + nx*(y + ny*z ...), connected to every listed offset."""
+    dims = list(shape)
+    n = int(np.prod(dims))
+    coords = np.indices(dims[::-1]).reshape(len(dims), -1)[::-1]  # coords[d] of vertex i
+    strides = np.cumprod([1] + dims[:-1])
+    rows_l, cols_l = [], []
+    for off in offsets:
+        valid = np.ones(n, dtype=bool)
+        nbr = np.zeros(n, dtype=np.int64)
+        for d, o in enumerate(off):
+            c = coords[d] + o
+            if periodic:
+                c = np.mod(c, dims[d])
+            else:
+                valid &= (c >= 0) & (c < dims[d])
+            nbr += np.clip(c, 0, dims[d] - 1) * strides[d]
+        idx = np.nonzero(valid)[0]
+        rows_l.append(idx)
+        cols_l.append(nbr[idx])
+    rows = np.concatenate(rows_l)
+    cols = np.concatenate(cols_l)
+    keep = rows != cols
+    rows, cols = rows[keep], cols[keep]
+    key = np.unique(rows * n + cols)
+    rows = key // n
+    cols = key % n
+    g = _from_sorted_pairs(n, rows, cols, name=name)
+    g.meta["shape"] = tuple(dims)
+    g.meta["periodic"] = periodic
+    return g
+
+
+def _grid3d_fast(nx: int, ny: int, nz: int, offsets, name: str) -> CSRGraph:
+    """Non-periodic grid built row by row without a global sort (large meshes)."""
+    n = nx * ny * nz
+    offs = sorted(offsets, key=lambda o: o[0] + nx * (o[1] + ny * o[2]))
+    x = np.tile(np.arange(nx, dtype=np.int32), ny * nz)
+    y = np.tile(np.repeat(np.arange(ny, dtype=np.int32), nx), nz)
+    z = np.repeat(np.arange(nz, dtype=np.int32), nx * ny)
+    masks = []
+    for dx, dy, dz in offs:
+        m = np.ones(n, dtype=bool)
+        if dx:
+            m &= (x + dx >= 0) & (x + dx < nx)
+        if dy:
+            m &= (y + dy >= 0) & (y + dy < ny)
+        if dz:
+            m &= (z + dz >= 0) & (z + dz < nz)
+        masks.append(m)
+    del x, y, z
+    counts = np.zeros(n, dtype=np.int64)
+    for m in masks:
+        counts += m
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    col = np.empty(int(row_ptr[-1]), dtype=np.int32)
+    run = row_ptr[:-1].copy()
+    ids = np.arange(n, dtype=np.int64)
+    for (dx, dy, dz), m in zip(offs, masks):
+        idx = ids[m]
+        col[run[m]] = (idx + dx + nx * (dy + ny * dz)).astype(np.int32)
+        run[m] += 1
+    g = CSRGraph(n=n, row_ptr=row_ptr, col=col, name=name)
+    g.meta["shape"] = (nx, ny, nz)
+    g.meta["periodic"] = False
+    return g
+
+
+def path_graph(n: int) -> CSRGraph:
+    return _offsets_csr((n,), [(-1,), (1,)], False, f"path{n}")
+
+
+def cycle_graph(n: int) -> CSRGraph:
+    if n < 3:
+        raise ValueError("cycle needs n >= 3")
+    return _offsets_csr((n,), [(-1,), (1,)], True, f"cycle{n}")
+
+
+def grid2d(nx: int, ny: int, periodic: bool = False) -> CSRGraph:
+    """5-point grid graph (4-neighbour mesh) on nx x ny vertices."""
+    if periodic and min(nx, ny) < 3:
+        raise ValueError("periodic grid needs every side >= 3")
+    return _offsets_csr((nx, ny), [(-1, 0), (1, 0), (0, -1), (0, 1)], periodic,
+                        f"grid2d_{nx}x{ny}{'_torus' if periodic else ''}")
+
+
+def _stencil3d(points: int):
+    if points == 7:
+        return [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    if points == 27:
+        return [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                if (dx, dy, dz) != (0, 0, 0)]
+    raise ValueError("stencil must be 7 or 27")
+
+
+def grid3d(nx: int, ny: int, nz: int, points: int = 27, periodic: bool = False) -> CSRGraph:
+    """3D structured mesh graph with a 7- or 27-point stencil (the 27-point
+    box is the structure of the Brick3D meshes of Sec. 6.1)."""
+    offs = _stencil3d(points)
+    name = f"grid3d{points}_{nx}x{ny}x{nz}{'_torus' if periodic else ''}"
+    if periodic:
+        if min(nx, ny, nz) < 3:
+            raise ValueError("periodic grid needs every side >= 3")
+        return _offsets_csr((nx, ny, nz), offs, True, name)
+    return _grid3d_fast(nx, ny, nz, offs, name)
+
+
+def star_graph(n: int) -> CSRGraph:
+    """Vertex 0 joined to vertices 1..n-1 (a maximally irregular degree profile)."""
+    src = np.zeros(n - 1, dtype=np.int64)
+    dst = np.arange(1, n, dtype=np.int64)
+    return symmetrize_edges(n, src, dst, name=f"star{n}")
+
+
+def erdos_renyi(n: int, p: float, seed: int) -> CSRGraph:
+    """G(n, p) on small n (all n(n-1)/2 pairs are drawn)."""
+    iu, ju = np.triu_indices(n, k=1)
+    u = uniform01(seed, 11, iu.size)
+    keep = u < p
+    return symmetrize_edges(n, iu[keep], ju[keep], name=f"er{n}_{p}_{seed}")
+
+
+def largest_component(g: CSRGraph) -> CSRGraph:
+    """Induced subgraph on the largest connected component, vertices kept in
+    their original relative order (Sec. 6.1 keeps the largest component)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    data = np.ones(g.nnz, dtype=np.int8)
+    a = sp.csr_matrix((data, g.col, g.row_ptr), shape=(g.n, g.n))
+    ncomp, labels = connected_components(a, directed=False)
+    if ncomp == 1:
+        g.meta["n_before_lcc"] = g.n
+        return g
+    big = np.argmax(np.bincount(labels))
+    keep = np.nonzero(labels == big)[0]
+    newid = -np.ones(g.n, dtype=np.int64)
+    newid[keep] = np.arange(keep.size)
+    rows = g.rows()
+    m = labels[rows] == big
+    r2 = newid[rows[m]]
+    c2 = newid[g.col[m].astype(np.int64)]
+    w2 = None if g.w is None else g.w[m]
+    out = _from_sorted_pairs(int(keep.size), r2, c2, w=w2, name=g.name + "_lcc")
+    out.meta = dict(g.meta)
+    out.meta["n_before_lcc"] = g.n
+    out.meta["components"] = int(ncomp)
+    return out
+
+
+def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
+         c: float = 0.19, seed: int = 3, lcc: bool = True, chunk: int = 1 << 24) -> CSRGraph:
+    """R-MAT graph (Chakrabarti, Zhan, Faloutsos 2004): ``edge_factor * 2^scale``
+    edge draws, each descending ``scale`` quadrant choices with probabilities
+    (a, b, c, d).  Symmetrised, deduplicated, self-loops dropped and reduced to
+    the largest component.  Vertex ids are not permuted."""
+    n = 1 << scale
+    m = edge_factor * n
+    ab, abc = a + b, a + b + c
+    src = np.zeros(m, dtype=np.int64)
+    dst = np.zeros(m, dtype=np.int64)
+    for lo in range(0, m, chunk):
+        hi = min(m, lo + chunk)
+        s = np.zeros(hi - lo, dtype=np.int64)
+        d = np.zeros(hi - lo, dtype=np.int64)
+        for lvl in range(scale):
+            u = uniform01(seed, 100 + lvl, hi - lo, offset=lo)
+            sb = u >= ab
+            db = ((u >= a) & (u < ab)) | (u >= abc)
+            bit = np.int64(1) << np.int64(scale - 1 - lvl)
+            s |= sb.astype(np.int64) * bit
+            d |= db.astype(np.int64) * bit
+        src[lo:hi] = s
+        dst[lo:hi] = d
+    g = symmetrize_edges(n, src, dst, name=f"rmat{scale}_ef{edge_factor}_s{seed}")
+    del src, dst
+    g.meta["edge_draws"] = m
+    return largest_component(g) if lcc else g
+
+
+def rgg(n: int, radius: Optional[float] = None, seed: int = 4, lcc: bool = True) -> CSRGraph:
+    """Random geometric graph: n points uniform in the unit square, joined
+    when closer than ``radius`` (default sqrt(8 / (pi n)), mean degree ~8)."""
+    from scipy.spatial import cKDTree
+
+    if radius is None:
+        radius = float(np.sqrt(8.0 / (np.pi * n)))
+    x = uniform01(seed, 21, n)
+    y = uniform01(seed, 22, n)
+    pts = np.stack([x, y], axis=1)
+    pairs = cKDTree(pts).query_pairs(radius, output_type="ndarray")
+    g = symmetrize_edges(n, pairs[:, 0], pairs[:, 1], name=f"rgg{n}_s{seed}")
+    g.meta["radius"] = radius
+    return largest_component(g) if lcc else g
+
+
+def random_edge_weights(g: CSRGraph, lo: float = 0.5, hi: float = 1.5, seed: int = 5) -> CSRGraph:
+    """Attach FP32 weights uniform in [lo, hi), one draw per undirected edge
+    (keyed by the unordered pair, so the weight matrix is symmetric)."""
+    rows = g.rows()
+    cols = g.col.astype(np.int64)
+    a = np.minimum(rows, cols)
+    b = np.maximum(rows, cols)
+    key = _stream_key(seed, 31)
+    with np.errstate(over="ignore"):
+        z = _mix64(key + (a.astype(np.uint64) * np.uint64(g.n) + b.astype(np.uint64) + np.uint64(1)) * _GOLDEN)
+    u = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    w = (lo + (hi - lo) * u).astype(np.float32)
+    return dataclasses.replace(g, w=w, name=g.name + "_w", meta=dict(g.meta))
+
+
+def random_vertex_weights(n: int, lo: int = 1, hi: int = 10, seed: int = 6) -> np.ndarray:
+    """int64 vertex weights uniform in [lo, hi]."""
+    u = uniform01(seed, 41, n)
+    return (lo + np.floor(u * (hi - lo + 1))).astype(np.int64)
+
+
+def random_coords(n: int, dim: int, seed: int, dtype=np.float64, ties: bool = False) -> np.ndarray:
+    """Row-major n x dim coordinates uniform in [-1, 1); with ``ties`` the
+    values are snapped to a coarse lattice so that many coordinates repeat and
+    signed zeros appear."""
+    u = uniform01(seed, 51, n * dim).reshape(n, dim)
+    x = 2.0 * u - 1.0
+    if ties:
+        x = np.round(x * 4.0) / 4.0
+        neg = uniform01(seed, 52, n * dim).reshape(n, dim) < 0.5
+        x = np.where((x == 0.0) & neg, -0.0, x)
+    return np.ascontiguousarray(x.astype(dtype))
