@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the Sphynx hot path on one GB300 (or N independent replicas).
+
+A step is one whole partition (Algorithm 2: Laplacian setup, polynomial
+preconditioner setup, LOBPCG, embedding, multi-jagged, cut and imbalance) of
+the default workload: the 128^3 27-point mesh (2,097,152 vertices,
+53,645,816 off-diagonal entries, synthetic stand-in for the paper's Brick3D
+meshes), generalized Laplacian, polynomial preconditioner of degree 25,
+K = 64 (d = 7), tol 1e-3.  The headline path stores blocks in FP32 and runs
+the polynomial chain in BF16 (FP64 Gram / Rayleigh-Ritz / norms); the plain
+FP64 path is timed beside it at the same tolerance.
+
+Multi-GPU: the path does not shard in this build (one graph per GPU), so
+N > 1 runs N independent replicas ("scaling": "weak").
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "partitions/sec + Laplacian SpMM HBM GB/s, mixed vs FP64 at equal residual"
+UNIT = "partitions/s"
+
+WORKLOADS = {
+    "c2": dict(desc="3D 27-point mesh 128^3 (2,097,152 vertices, 53,645,816 off-diagonal nnz, unit weights), "
+                    "generalized Laplacian, polynomial preconditioner degree 25, K=64 (d=7), LOBPCG tol 1e-3",
+               K=64, laplacian="generalized", precond="poly", poly_degree=25, tol=1e-3, seed=2,
+               precision="mixed_bf16", golden="c2_oracle.json"),
+    "c1": dict(desc="2D 5-point mesh 64x64 (4096 vertices), combinatorial Laplacian, Jacobi, K=4 (d=3), tol 1e-2",
+               K=4, laplacian="combinatorial", precond="jacobi", poly_degree=25, tol=1e-2, seed=1,
+               precision="fp64", golden="c1_oracle.json"),
+    "c3": dict(desc="R-MAT scale 22 (edge factor 16, a=.57 b=.19 c=.19), symmetrised, deduplicated, self-loops "
+                    "dropped, largest component; normalized Laplacian, Jacobi, K=256 (d=9), tol 1e-2",
+               K=256, laplacian="normalized", precond="jacobi", poly_degree=25, tol=1e-2, seed=3,
+               precision="fp32", golden=None),
+}
+
+
+def make_graph(name: str):
+    import workloads
+    if name == "c2":
+        return workloads.grid3d(128, 128, 128, 27)
+    if name == "c1":
+        return workloads.grid2d(64, 64)
+    if name == "c3":
+        return workloads.rmat(22, 16, 0.57, 0.19, 0.19, seed=3)
+    raise ValueError(name)
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs"), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1].strip())
+            except ValueError:
+                return None
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i - 5] for r in rows for i in range(5, 9) if "Active" in r[i] and "Not" not in r[i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(name: str, steps: int = 1):
+    """The FP64 oracle on the same workload, bounded: one run with the
+    iteration cap at 0 (setup, initial Rayleigh-Ritz, embedding, MJ, cut) and
+    one with the cap at 1; partitions/s are extrapolated with the oracle's
+    own full-run iteration count from tests/golden (written by oracle code)."""
+    import oracle
+    w = WORKLOADS[name]
+    g = make_graph(name)
+    kw = dict(problem=w["laplacian"], precond=w["precond"], tol=w["tol"], seed=w["seed"],
+              poly_degree=w["poly_degree"])
+    t0s, t1s = [], []
+    for _ in range(steps):
+        t = time.perf_counter()
+        oracle.partition(g, w["K"], maxit=0, **kw)
+        t0s.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        oracle.partition(g, w["K"], maxit=1, **kw)
+        t1s.append(time.perf_counter() - t)
+    t0, t1 = float(np.median(t0s)), float(np.median(t1s))
+    iters = None
+    if w["golden"]:
+        p = os.path.join(ROOT, "tests", "golden", w["golden"])
+        if os.path.exists(p):
+            with open(p) as f:
+                iters = json.load(f)["iterations"]
+    if iters is None:
+        iters = 1
+    per_iter = max(t1 - t0, 0.0)
+    est = t0 + iters * per_iter
+    sample = (f"oracle.partition with the LOBPCG cap at 0 ({t0:.1f} s) and 1 ({t1:.1f} s) iterations, "
+              f"extrapolated to the oracle's {iters} iterations (tests/golden/{w['golden']}); "
+              f"scipy sparse products single-threaded, numpy BLAS on all cores")
+    return 1.0 / est, sample, t0 + t1
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; its samples are timed below
+    vals = []
+    total_s = 0.0
+    sample = ""
+    for _ in range(args.steps):
+        v, sample, s = oracle_sample(args.workload)
+        vals.append(v)
+        total_s += s
+    value = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["desc"], "K": w["K"]},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2105_00578_gb300 as spx
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WORKLOADS[args.workload]
+    precision = args.precision or w["precision"]
+    g = make_graph(args.workload)
+    stream = torch.cuda.current_stream()
+    graph = spx.Graph(g, stream=stream)
+    n = g.n
+    part = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def opts(prec):
+        return spx.options(laplacian=w["laplacian"], precond=w["precond"], poly_degree=w["poly_degree"],
+                           precision=prec, tol=w["tol"], seed=w["seed"], out_device=True)
+
+    o_main = opts(precision)
+
+    def step(o):
+        return spx.sphynx_partition(graph.h, w["K"], o, part)
+
+    for _ in range(args.warmup):
+        step(o_main)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    stats = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            code, cut, imb, st = step(o_main)
+            stats.append((code, cut, imb, st))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world / (ms / 1000.0)
+
+    spmm_ms = sum(s[3]["ms_spmm"] for s in stats)
+    spmm_bytes = sum(s[3]["spmm_bytes"] for s in stats)
+    spmm_launches = sum(s[3]["spmm_launches"] for s in stats)
+    launches = sum(s[3]["kernel_launches"] for s in stats)
+    last = stats[-1]
+    pk = peaks()
+    achieved = spmm_bytes / (spmm_ms / 1000.0) / 1e9 if spmm_ms > 0 else None
+
+    # plain FP64 path at the same tolerance
+    fp64 = None
+    if args.fp64_steps > 0 and precision != "fp64":
+        o64 = opts("fp64")
+        step(o64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        fst = []
+        for _ in range(args.fp64_steps):
+            fst.append(step(o64))
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1) / args.fp64_steps
+        s64 = fst[-1][3]
+        fp64 = {"ms_per_partition": fms, "partitions_per_s": 1000.0 / fms, "iterations": s64["iterations"],
+                "max_resnorm_over_tol_theta": _res_ratio(s64, w["tol"]), "cut": fst[-1][1],
+                "status": fst[-1][0], "speedup_of_mixed": fms / ms}
+
+    # end to end through the C ABI with host buffers: create (H2D of the CSR
+    # from pinned memory) + partition + read of the part ids (D2H) per step
+    rp = torch.from_numpy(g.row_ptr).pin_memory()
+    cl = torch.from_numpy(g.col).pin_memory()
+    hp = torch.empty(n, dtype=torch.int32).pin_memory()
+    o_host = spx.options(laplacian=w["laplacian"], precond=w["precond"], poly_degree=w["poly_degree"],
+                         precision=precision, tol=w["tol"], seed=w["seed"])
+    e2e_steps = max(1, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        h = spx.sphynx_create(rp.data_ptr(), cl.data_ptr(), None, None, n, g.nnz, spx.HOST_PTRS, stream)
+        spx.sphynx_partition(h, w["K"], o_host, hp.data_ptr())
+        spx.sphynx_destroy(h)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample, _ = oracle_sample(args.workload)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if precision != "fp64" else "f64",
+            "data": "synthetic",
+            "config": {"workload": w["desc"], "K": w["K"], "precision": precision,
+                       "l2": "inputs larger than L2 (CSR column array 215 MB > 129 MB)"
+                       if args.workload == "c2" else "no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "iterations": last[3]["iterations"], "status": last[0], "cut": last[1], "imbalance": last[2],
+            "eigenvalues": last[3]["eigenvalues"],
+            "max_resnorm_over_tol_theta": _res_ratio(last[3], w["tol"]),
+            "spmm": {"gbs": achieved, "launches_per_step": spmm_launches / args.steps,
+                     "ms_per_step": spmm_ms / args.steps},
+            "fp64": fp64,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
+                         "peak_source": pk["src"],
+                         "kernel": "k_spmm_short (Laplacian SpMM incl. polynomial-chain steps)",
+                         "traffic": profiled_traffic("spmm", args.workload)},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes),
+                    "d2h_bytes_per_step": int(n * 4)},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    graph.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _res_ratio(st, tol):
+    """max over the non-null columns of ||r|| / (tol |theta|)"""
+    vals = [r / (tol * abs(t)) for r, t in zip(st["resnorm"][1:], st["eigenvalues"][1:]) if t != 0]
+    return max(vals) if vals else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "mixed_bf16"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

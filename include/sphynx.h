@@ -1,0 +1,248 @@
+/*
+ * sphynx.h -- C ABI of the GB300 spectral graph partitioner.
+ *
+ * The library computes a K-way partition of an undirected graph the way the
+ * Sphynx partitioner does (Acer, Boman, Glusa, Rajamanickam, "Sphynx: a
+ * parallel multi-GPU graph partitioner for distributed-memory systems",
+ * Algorithm 2): it forms a graph Laplacian, finds its d = floor(log2 K) + 1
+ * smallest eigenvectors with preconditioned LOBPCG (Algorithm 1), drops the
+ * first, and cuts the remaining d - 1 coordinates into K parts with
+ * multi-jagged multisection (Sec. 4).  Every step runs in the library's own
+ * CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Status: every call returns int, 0 (SPHYNX_OK) on success or one of the
+ *   SPHYNX_ERR_* codes below; nothing throws across the ABI.  After a
+ *   failure, sphynx_last_error() gives a message (thread-local, valid until
+ *   the next call on the same thread).
+ * - Graph: CSR of a simple undirected graph with n vertices and nnz stored
+ *   entries: row_ptr int64[n+1] (row_ptr[0] = 0, non-decreasing,
+ *   row_ptr[n] = nnz), col int32[nnz] (column indices strictly increasing in
+ *   each row, in [0, n), no self-loops), both (i,j) and (j,i) present.
+ *   Optional edge weights float32[nnz] (positive, symmetric) and vertex
+ *   weights int64[n] (>= 1).  NULL weights mean unit weights.
+ * - Blocks of vectors are row-major n x ld arrays (ld >= ncols, element
+ *   (i, j) at i*ld + j); "device" means a pointer to memory of the handle's
+ *   GPU (e.g. from torch.empty(..., device="cuda")).
+ * - Ownership: the caller owns every buffer it passes.  The handle owns its
+ *   device copy of the graph and its workspaces; sphynx_destroy frees them.
+ * - Streams: all work of a handle is ordered on the stream given to
+ *   sphynx_create (a cudaStream_t, NULL = legacy default stream).  Calls that
+ *   return results in host memory synchronise that stream before returning.
+ *   A handle is not thread-safe; distinct handles may be used concurrently.
+ */
+#ifndef SPHYNX_H
+#define SPHYNX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SPHYNX_OK 0
+#define SPHYNX_ERR_INVALID_ARG 1   /* bad pointer, size, option or CSR structure */
+#define SPHYNX_ERR_NOT_SYMMETRIC 2 /* some (i,j) has no matching (j,i) of equal weight */
+#define SPHYNX_ERR_ISOLATED 3      /* a vertex has no edge (generalized/normalized need deg > 0) */
+#define SPHYNX_ERR_OOM 4           /* device allocation failed */
+#define SPHYNX_ERR_CUDA 5          /* a CUDA runtime call or kernel launch failed */
+#define SPHYNX_ERR_NOCONV 6        /* LOBPCG hit max_iter; outputs hold the last iterate */
+#define SPHYNX_ERR_BREAKDOWN 7     /* Rayleigh-Ritz basis lost rank beyond recovery */
+#define SPHYNX_ERR_UNSUPPORTED 8   /* a size outside the documented limits */
+
+/* ---- sphynx_create flags ------------------------------------------------ */
+#define SPHYNX_HOST_PTRS 0u     /* row_ptr/col/weights are host pointers (copied) */
+#define SPHYNX_DEVICE_PTRS 1u   /* they are device pointers (adopted: keep alive until destroy) */
+#define SPHYNX_VALIDATE 2u      /* check CSR structure and symmetry on the GPU */
+
+/* ---- option enums ------------------------------------------------------- */
+/* Laplacian / eigenproblem (Sec. 3.2): L_C x = lambda x (Eq. 2),
+ * L_C x = lambda D x, or L_N x = lambda x (Eq. 3). */
+#define SPHYNX_COMBINATORIAL 0
+#define SPHYNX_GENERALIZED 1
+#define SPHYNX_NORMALIZED 2
+/* Preconditioner (Sec. 5): none, Jacobi M = diag(L)^-1 (Sec. 5.1), or the
+ * GMRES polynomial p_k(L) (Sec. 5.2). */
+#define SPHYNX_PRECOND_NONE 0
+#define SPHYNX_PRECOND_JACOBI 1
+#define SPHYNX_PRECOND_POLY 2
+/* Arithmetic.  FP64: every block and product in double.  FP32: blocks in
+ * float with float products; Gram matrices accumulated to double, the
+ * Cholesky / Rayleigh-Ritz small problems and the residual norms in double.
+ * MIXED_BF16: as FP32, but the polynomial preconditioner's chain vectors
+ * are stored in bfloat16 (products still accumulate in float). */
+#define SPHYNX_FP64 0
+#define SPHYNX_FP32 1
+#define SPHYNX_MIXED_BF16 2
+/* Initial block (Sec. 6.2.1): seeded random, or piecewise constant. */
+#define SPHYNX_INIT_RANDOM 0
+#define SPHYNX_INIT_PIECEWISE 1
+/* Element types of user blocks passed to the step-level calls. */
+#define SPHYNX_DT_F64 0
+#define SPHYNX_DT_F32 1
+#define SPHYNX_DT_BF16 2
+/* sphynx_options.flags */
+#define SPHYNX_OUT_DEVICE 1u    /* part_out of sphynx_partition is a device pointer */
+
+/* Largest block size the kernels are built for: d = floor(log2 K) + 1 <= 16,
+ * i.e. K < 65536. */
+#define SPHYNX_MAX_NEV 16
+/* Largest polynomial degree (Sec. 5.2 uses 25). */
+#define SPHYNX_MAX_POLY_DEGREE 64
+
+typedef struct sphynx_graph *sphynx_handle;
+
+typedef struct {
+  int32_t laplacian;   /* SPHYNX_COMBINATORIAL | _GENERALIZED | _NORMALIZED   */
+  int32_t precond;     /* SPHYNX_PRECOND_*                                     */
+  int32_t poly_degree; /* k of p_k, 1..SPHYNX_MAX_POLY_DEGREE (default 25)     */
+  int32_t precision;   /* SPHYNX_FP64 | SPHYNX_FP32 | SPHYNX_MIXED_BF16        */
+  int32_t init;        /* SPHYNX_INIT_RANDOM | SPHYNX_INIT_PIECEWISE           */
+  int32_t max_iter;    /* LOBPCG iteration cap (default 1000)                  */
+  double tol;          /* LOBPCG tolerance (default 1e-3)                      */
+  uint64_t seed;       /* seeds the random block and the polynomial start      */
+  uint32_t flags;      /* SPHYNX_OUT_DEVICE                                    */
+  int32_t sync_every;  /* iterations between host convergence checks (0=auto)  */
+  int32_t reserved[6];
+} sphynx_options;
+
+typedef struct {
+  int32_t status;        /* status of the LOBPCG solve (OK / NOCONV / BREAKDOWN)  */
+  int32_t iterations;    /* LOBPCG iterations (Algorithm 1 loop trips)            */
+  int32_t nev;           /* d                                                     */
+  int32_t svqb_steps;    /* Rayleigh-Ritz steps that fell back from Cholesky       */
+  double eigenvalues[SPHYNX_MAX_NEV]; /* Ritz values, ascending                    */
+  double resnorm[SPHYNX_MAX_NEV];     /* ||L x - theta B x||_{B^-1} per column     */
+  double ms_total;       /* wall time of the call (host clock)                     */
+  double ms_setup;       /* preconditioner setup (device events)                   */
+  double ms_lobpcg;      /* eigensolve incl. setup (device events)                 */
+  double ms_mj;          /* embedding + multi-jagged (device events)               */
+  double ms_eval;        /* cut and imbalance (device events)                      */
+  double ms_spmm;        /* summed duration of the Laplacian SpMM launches         */
+  int64_t spmm_launches; /* Laplacian SpMM launches (short-row kernel)             */
+  double spmm_bytes;     /* algorithmic bytes of those launches                    */
+  int64_t kernel_launches; /* all kernels this call launched                      */
+  double cut;            /* Eq. 1                                                  */
+  double cut_twice;      /* Eq. 1 counted from both endpoints (the paper's tables) */
+  double imbalance;      /* max_k W_k / W_avg                                      */
+  double reserved[8];
+} sphynx_stats;
+
+typedef struct {
+  int64_t n, nnz;
+  int64_t max_degree;        /* largest number of neighbours                       */
+  double max_wdegree;        /* largest weighted degree                            */
+  int64_t total_vweight;     /* sum of vertex weights                              */
+  int64_t long_rows;         /* rows the SpMM routes to the long-row kernel        */
+  int32_t weighted;          /* edge weights present                               */
+  int32_t spmm_variant;      /* autotuned short-row schedule (rows per warp)       */
+} sphynx_graph_info;
+
+/* Fill *opt with the defaults listed in sphynx_options. */
+void sphynx_default_options(sphynx_options *opt);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *sphynx_last_error(void);
+
+/* Create a graph handle (Sec. 3.1: G with vertex weights and edge costs).
+ * Copies (HOST_PTRS) or adopts (DEVICE_PTRS) the CSR, computes weighted
+ * degrees, D^{-1/2} and the SpMM plan, and with SPHYNX_VALIDATE checks the
+ * structure and symmetry on the GPU.  `stream` is a cudaStream_t.
+ * Errors: INVALID_ARG, NOT_SYMMETRIC, OOM, CUDA, UNSUPPORTED (n >= 2^31,
+ * nnz >= 2^40, or total vertex weight times 2^22 overflowing int64). */
+int sphynx_create(const int64_t *row_ptr, const int32_t *col, const float *edge_w,
+                  const int64_t *vtx_w, int64_t n, int64_t nnz, uint32_t flags,
+                  void *stream, sphynx_handle *out);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void sphynx_destroy(sphynx_handle g);
+
+/* Sizes and degree statistics of the graph (host struct). */
+int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info);
+
+/* Weighted degrees deg(v_i) (Sec. 3.2: the diagonal of L_C) into a device
+ * double[n]. */
+int sphynx_degrees(sphynx_handle g, double *deg_out);
+
+/* Y = L X for the chosen Laplacian without forming L (Eqs. 2-3 and the
+ * weighted rule of Sec. 3.2; the generalized problem's operator is L_C).
+ * X: device n x ldx block of dtype SPHYNX_DT_*; Y: device n x ldy block of
+ * double (F64 input) or float (F32/BF16 input).  ncols <= 16.  Padding
+ * columns of Y (ncols..ldy) are not written. */
+int sphynx_laplacian_apply(sphynx_handle g, int32_t laplacian, int32_t dtype, const void *x,
+                           int32_t ldx, void *y, int32_t ldy, int32_t ncols);
+
+/* Set up the preconditioner of `opt` (Sec. 5) and, for the polynomial,
+ * return its roots theta_1..theta_k in application order (harmonic Ritz
+ * values of k Lanczos steps, Leja ordered) in host double[poly_degree]
+ * (may be NULL).  Jacobi and none need no setup. */
+int sphynx_precond_setup(sphynx_handle g, const sphynx_options *opt, double *roots_out);
+
+/* H = M R for the preconditioner set up by the last sphynx_precond_setup
+ * (or Jacobi/none from `opt`).  R, H: device n x ld blocks of float (FP32 /
+ * MIXED_BF16 precision) or double (FP64); ncols <= 16. */
+int sphynx_precond_apply(sphynx_handle g, const sphynx_options *opt, const void *r, void *h,
+                         int32_t ld, int32_t ncols);
+
+/* Gram matrices of Rayleigh-Ritz (Sec. 3.3, Algorithm 1 line 7):
+ * G_A = S^T (L S) and G_B = S^T B S, where S = [S_0 | S_1 | S_2] and
+ * LS = [LS_0 | LS_1 | LS_2] are given as nblk (1..3) device n x ld blocks of
+ * dtype F32 or F64 (each ld columns wide, 4 | ld, ld <= 16), and B is
+ * diag(bdiag) (device double[n]) or the identity (bdiag = NULL).  Outputs
+ * are host double[(nblk*ld)^2], row-major, G_B symmetric.  Accumulation:
+ * products in the input type, partial sums per CTA in double.
+ * Scratch: allocated per call with cudaMallocAsync on `stream`. */
+int sphynx_gram(int32_t dtype, const void *const *s_blocks, const void *const *ls_blocks,
+                int32_t nblk, int32_t ld, int64_t n, const double *bdiag, double *ga_out,
+                double *gb_out, void *stream);
+
+/* Rayleigh-Ritz on the GPU in FP64 (Sec. 3.3): given host G_A, G_B (m x m,
+ * m <= 48) and an active mask (host int32[m], nonzero = column in S),
+ * returns the nev smallest Ritz values (host double[nev]) and coefficients
+ * Y (host double[m * nev], row-major m x nev, zero rows for inactive
+ * columns).  u_work sets the rank threshold 10 m u_work.  *used_svqb tells
+ * whether the Cholesky factor was replaced by an eigendecomposition. */
+int sphynx_rayleigh_ritz(const double *ga, const double *gb, const int32_t *active, int32_t m,
+                         int32_t nev, double u_work, double *theta_out, double *y_out,
+                         int32_t *used_svqb, void *stream);
+
+/* LOBPCG (Algorithm 1) for the nev smallest eigenpairs of the problem of
+ * `opt`.  x0: optional host double[n * nev] initial block (NULL = the
+ * seeded block of opt->init).  x_out: device n x ldx block of double (FP64)
+ * or float (FP32/MIXED_BF16) with the B-orthonormal Ritz vectors;
+ * theta_out / resnorm_out: host double[nev] (may be NULL).
+ * Returns OK, NOCONV or BREAKDOWN (outputs valid for the last two). */
+int sphynx_eigensolve(sphynx_handle g, const sphynx_options *opt, int32_t nev, const double *x0,
+                      void *x_out, int32_t ldx, double *theta_out, double *resnorm_out,
+                      sphynx_stats *stats);
+
+/* Multi-jagged multisection (Sec. 4) of n points with `dims` coordinates
+ * (device n x ldc block of SPHYNX_DT_F64 or _F32), vertex weights (device
+ * int64[n] or NULL = unit) into K parts: each section owning k parts splits
+ * ceil(k/2) | floor(k/2) along dimension (level mod dims) at the prefix of
+ * the (coordinate, vertex id) order minimising |k W_left - ceil(k/2) W|,
+ * ties to the shorter prefix (-0 == +0; NaN is INVALID_ARG).
+ * part_out: device int32[n].  Scratch is allocated per call.  Bit-exact. */
+int sphynx_mj(int32_t dtype, const void *coords, int32_t ldc, int32_t dims, int64_t n,
+              const int64_t *vtx_w, int32_t K, int32_t *part_out, void *stream);
+
+/* Cutsize (Eq. 1, exact: integer for unit weights, exact fixed point for
+ * float weights, rounded once) and imbalance max_k W_k / W_avg (Sec. 3.1)
+ * of a partition given as device int32[n] with values in [0, K). */
+int sphynx_eval(sphynx_handle g, const int32_t *part, int32_t K, double *cut,
+                double *cut_twice, double *imbalance);
+
+/* Algorithm 2: K-way partition.  part_out: int32[n], host memory unless
+ * opt->flags has SPHYNX_OUT_DEVICE.  cut_out / imbalance_out / stats may be
+ * NULL.  Returns OK, or NOCONV / BREAKDOWN with a valid partition of the
+ * last iterate. */
+int sphynx_partition(sphynx_handle g, int32_t K, const sphynx_options *opt, int32_t *part_out,
+                     double *cut_out, double *imbalance_out, sphynx_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPHYNX_H */

@@ -1,0 +1,866 @@
+// dense.cu -- the tall-skinny dense kernels of LOBPCG (Algorithm 1) and of the
+// polynomial preconditioner's Lanczos setup (Sec. 5.2).
+//
+// Blocks are row-major n x ld (ld = 4, 8, 12 or 16).  Every kernel here reads
+// and writes its blocks once with coalesced 16-byte accesses; reductions over
+// n go through per-CTA partials in double that a second, fixed-order pass adds,
+// so results do not depend on scheduling.
+#include "internal.cuh"
+
+#include <cmath>
+
+namespace sphynx {
+
+namespace {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// u in [0,1) from the top 53 bits, then 2u - 1 (exact in double)
+__device__ inline double splitmix_pm1(uint64_t state, uint64_t ctr) {
+  const uint64_t z = mix64(state + ctr * kGamma);
+  return 2.0 * (static_cast<double>(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
+template <typename T> __device__ inline T from_d(double v) { return static_cast<T>(v); }
+
+unsigned blocks_for(int64_t work, int threads) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > (1LL << 30)) b = (1LL << 30);
+  return static_cast<unsigned>(b);
+}
+
+// ---------------------------------------------------------------------------
+// initial blocks (Sec. 6.2.1)
+template <typename T>
+__global__ void k_random_block(T *x, int64_t n, int b, int ld, uint64_t state) {
+  const int64_t total = n * ld;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / ld;
+    const int j = static_cast<int>(idx - i * ld);
+    double v = 0.0;
+    if (j < b) v = splitmix_pm1(state, static_cast<uint64_t>(i * b + j + 1));
+    x[idx] = from_d<T>(v);
+  }
+}
+
+template <typename T>
+__global__ void k_piecewise_block(T *x, int64_t n, int b, int ld, int lap, const double *deg) {
+  const int64_t total = n * ld;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / ld;
+    const int j = static_cast<int>(idx - i * ld);
+    double v = 0.0;
+    if (j == 0) {
+      v = lap == SPHYNX_NORMALIZED ? sqrt(deg[i]) : 1.0;
+    } else if (j < b) {
+      const int64_t lo = (static_cast<int64_t>(j - 1) * n) / b, hi = (static_cast<int64_t>(j) * n) / b;
+      v = (i >= lo && i < hi) ? 1.0 : 0.0;
+    }
+    x[idx] = from_d<T>(v);
+  }
+}
+
+template <typename T>
+__global__ void k_from_f64(T *x, const double *src, int64_t n, int b, int ld) {
+  const int64_t total = n * ld;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / ld;
+    const int j = static_cast<int>(idx - i * ld);
+    x[idx] = from_d<T>(j < b ? src[i * b + j] : 0.0);
+  }
+}
+
+template <typename T>
+__global__ void k_to_f64(const T *x, double *dst, int64_t n, int b, int ld) {
+  const int64_t total = n * b;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / b;
+    const int j = static_cast<int>(idx - i * b);
+    dst[idx] = static_cast<double>(x[i * ld + j]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gram matrices G_A = S^T (L S), G_B = S^T B S (Algorithm 1 line 7).
+//
+// Output is tiled in 4x4 blocks: all (M/4)^2 blocks of G_A and the upper
+// triangle of G_B.  A CTA owns a slab of rows; its threads form `ngroups`
+// row groups of `tpg` threads, thread t of a group owning output block t.
+// float: products and short sums in float, folded every kFlushRows rows into
+// a float (hi, lo) pair with Knuth's TwoSum (about 48 significant bits),
+// converted to double at the end.  double: plain double FMAs.
+struct GramDev {
+  int nblk, ld, M, nbA, nbB, tpg, ngroups;
+  int64_t n;
+  const void *s[3];
+  const void *ls[3];
+  const void *bdiag;
+  double *partials;
+  const int *done;
+};
+
+constexpr int kGramThreads = 256;
+
+template <typename T> struct GramTile { static constexpr int rows = 64; };
+template <> struct GramTile<double> { static constexpr int rows = 32; };
+
+__device__ inline void two_sum_fold(float &hi, float &lo, float &acc) {
+  const float s = hi + acc;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (acc - bp);
+  hi = s;
+  lo += e;
+  acc = 0.f;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGramThreads) k_gram(const GramDev a) {
+  constexpr int TR = GramTile<T>::rows;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.done && *a.done) return;
+  const int M = a.M;
+  T *sS = reinterpret_cast<T *>(smem_raw);
+  T *sL = sS + TR * M;
+  T *sB = a.bdiag ? sL + TR * M : sS;
+  const int tid = threadIdx.x;
+  const int grp = tid / a.tpg, t = tid % a.tpg;
+  const int NB = a.nbA + a.nbB;
+  const int mb = M / 4;
+  const bool active = t < NB && grp < a.ngroups;
+  int bi = 0, bj = 0;
+  bool isA = true;
+  if (active) {
+    if (t < a.nbA) {
+      bi = t / mb;
+      bj = t % mb;
+    } else {
+      isA = false;
+      int k = t - a.nbA;
+      bi = 0;
+      while (k >= mb - bi) {
+        k -= mb - bi;
+        ++bi;
+      }
+      bj = bi + k;
+    }
+  }
+  T acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = T(0);
+  float hi[16], lo[16];
+  if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
+  }
+  const int64_t ntile = (a.n + TR - 1) / TR;
+  const T *C = isA ? sL : sB;
+  int since_flush = 0;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t r0 = tile * TR;
+    __syncthreads();
+    for (int idx = tid; idx < TR * M; idx += kGramThreads) {
+      const int r = idx / M, c = idx - (idx / M) * M;
+      const int blk = c / a.ld, cc = c - blk * a.ld;
+      const int64_t row = r0 + r;
+      T v = T(0), lv = T(0);
+      if (row < a.n) {
+        v = static_cast<const T *>(a.s[blk])[row * a.ld + cc];
+        lv = static_cast<const T *>(a.ls[blk])[row * a.ld + cc];
+      }
+      sS[idx] = v;
+      sL[idx] = lv;
+      if (a.bdiag) sB[idx] = row < a.n ? v * static_cast<const T *>(a.bdiag)[row] : T(0);
+    }
+    __syncthreads();
+    if (active) {
+      for (int r = grp; r < TR; r += a.ngroups) {
+        const T *ar = sS + r * M + 4 * bi;
+        const T *cr = C + r * M + 4 * bj;
+        T av[4], cv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { av[q] = ar[q]; cv[q] = cr[q]; }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i * 4 + j] += av[i] * cv[j];
+      }
+      if constexpr (std::is_same<T, float>::value) {
+        since_flush += TR / a.ngroups;
+        if (since_flush >= 64) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) two_sum_fold(hi[q], lo[q], acc[q]);
+          since_flush = 0;
+        }
+      }
+    }
+  }
+  // combine row groups in a fixed order through shared memory (double)
+  __syncthreads();
+  double *red = reinterpret_cast<double *>(smem_raw);  // [ngroups][NB*16]
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      double v;
+      if constexpr (std::is_same<T, float>::value) {
+        float h = hi[q], l = lo[q];
+        two_sum_fold(h, l, acc[q]);
+        v = static_cast<double>(h) + static_cast<double>(l);
+      } else {
+        v = acc[q];
+      }
+      red[grp * NB * 16 + t * 16 + q] = v;
+    }
+  }
+  __syncthreads();
+  for (int o = tid; o < NB * 16; o += kGramThreads) {
+    double s = 0.0;
+    for (int g = 0; g < a.ngroups; ++g) s += red[g * NB * 16 + o];
+    a.partials[static_cast<int64_t>(blockIdx.x) * NB * 16 + o] = s;
+  }
+}
+
+void gram_shape(int nblk, int ld, GramDev &d) {
+  d.nblk = nblk;
+  d.ld = ld;
+  d.M = nblk * ld;
+  const int mb = d.M / 4;
+  d.nbA = mb * mb;
+  d.nbB = mb * (mb + 1) / 2;
+  const int NB = d.nbA + d.nbB;
+  int tpg = 32;
+  while (tpg < NB) tpg *= 2;
+  d.tpg = tpg;
+  d.ngroups = kGramThreads / tpg;
+}
+
+// ---------------------------------------------------------------------------
+// X' = S Y, P' = [0 H P] Y, LP' = [0 LH LP] Y  (Algorithm 1 lines 8 and 12)
+template <typename T, int LD, int NBLK>
+__global__ void __launch_bounds__(256)
+k_update(int64_t n, const T *s0, const T *s1, const T *s2, const T *l1, const T *l2, const T *y,
+         T *xo, T *po, T *lpo, const int *done) {
+  constexpr int M = NBLK * LD;
+  __shared__ T sy[M * LD];
+  if (done && *done) return;
+  for (int i = threadIdx.x; i < M * LD; i += blockDim.x) sy[i] = y[i];
+  __syncthreads();
+  for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < n;
+       row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    T x[LD], p[LD], lp[LD];
+#pragma unroll
+    for (int c = 0; c < LD; ++c) { x[c] = T(0); p[c] = T(0); lp[c] = T(0); }
+    const T *rows[3] = {s0 + row * LD, NBLK > 1 ? s1 + row * LD : nullptr,
+                        NBLK > 2 ? s2 + row * LD : nullptr};
+#pragma unroll
+    for (int blk = 0; blk < NBLK; ++blk) {
+      T v[LD];
+#pragma unroll
+      for (int k = 0; k < LD; ++k) v[k] = rows[blk][k];
+#pragma unroll
+      for (int k = 0; k < LD; ++k) {
+#pragma unroll
+        for (int c = 0; c < LD; ++c) {
+          const T yk = sy[(blk * LD + k) * LD + c];
+          x[c] += v[k] * yk;
+          if (blk > 0) p[c] += v[k] * yk;
+        }
+      }
+    }
+    T *xr = xo + row * LD;
+#pragma unroll
+    for (int c = 0; c < LD; ++c) xr[c] = x[c];
+    if constexpr (NBLK == 3) {
+      const T *lrows[2] = {l1 + row * LD, l2 + row * LD};
+#pragma unroll
+      for (int blk = 1; blk < 3; ++blk) {
+        T v[LD];
+#pragma unroll
+        for (int k = 0; k < LD; ++k) v[k] = lrows[blk - 1][k];
+#pragma unroll
+        for (int k = 0; k < LD; ++k)
+#pragma unroll
+          for (int c = 0; c < LD; ++c) lp[c] += v[k] * sy[(blk * LD + k) * LD + c];
+      }
+      T *pr = po + row * LD, *lr = lpo + row * LD;
+#pragma unroll
+      for (int c = 0; c < LD; ++c) { pr[c] = p[c]; lr[c] = lp[c]; }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// R = L X - B X Theta (Algorithm 1 line 9), ||r_c||^2_{B^-1} partials, and
+// the Jacobi scaling H = diag(L)^{-1} R (Sec. 5.1) when jinv is given.
+template <typename T, int LD>
+__global__ void __launch_bounds__(256)
+k_residual(int64_t n, const T *x, const T *lx, const double *theta, const T *bdiag, const T *jinv,
+           T *out, double *partials, const int *done) {
+  __shared__ double red[256 / 32][LD];
+  if (done && *done) return;
+  T th[LD];
+#pragma unroll
+  for (int c = 0; c < LD; ++c) th[c] = static_cast<T>(theta[c]);
+  T acc[LD];
+#pragma unroll
+  for (int c = 0; c < LD; ++c) acc[c] = T(0);
+  for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < n;
+       row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const T bi = bdiag ? bdiag[row] : T(1);
+    const T ib = bdiag ? T(1) / bi : T(1);
+    const T sc = jinv ? jinv[row] : T(1);
+    T r[LD];
+#pragma unroll
+    for (int c = 0; c < LD; ++c) {
+      r[c] = lx[row * LD + c] - th[c] * (bi * x[row * LD + c]);
+      acc[c] += r[c] * r[c] * ib;
+    }
+#pragma unroll
+    for (int c = 0; c < LD; ++c) out[row * LD + c] = sc * r[c];
+  }
+  // block reduction in double, fixed order
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < LD; ++c) {
+    double v = static_cast<double>(acc[c]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[wid][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < LD) {
+    double s = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+    partials[static_cast<int64_t>(blockIdx.x) * LD + threadIdx.x] = s;
+  }
+}
+
+// Convergence test (lines 10-11): ||r||_{B^-1} <= tol |theta| or below the floor.
+__global__ void k_converge(SolverState *st, const double *partials, int grid, int b, int ld,
+                           double tol, double floor_abs, int count_iteration, int maxit) {
+  __shared__ double part[16][17];
+  if (st->done) return;
+  const int t = threadIdx.x;     // 256 threads: column t % 16, stripe t / 16
+  const int c = t & 15, stripe = t >> 4;
+  double s = 0.0;
+  if (c < ld)
+    for (int g = stripe; g < grid; g += 16) s += partials[static_cast<int64_t>(g) * ld + c];
+  part[stripe][c] = s;
+  __syncthreads();
+  if (t == 0) {
+    int nconv = 0;
+    for (int j = 0; j < b; ++j) {
+      double tot = 0.0;
+      for (int q = 0; q < 16; ++q) tot += part[q][j];
+      const double res = sqrt(tot);
+      st->resnorm[j] = res;
+      const bool ok = (res <= tol * fabs(st->theta[j])) || (res <= floor_abs);
+      st->conv[j] = ok ? 1 : 0;
+      nconv += ok ? 1 : 0;
+    }
+    st->nconv = nconv;
+    if (count_iteration) {
+      st->iters += 1;
+      st->pvalid = 1;
+    }
+    if (nconv == b) {
+      st->done = 1;
+      st->status = SPHYNX_OK;
+    } else if (st->iters >= maxit) {
+      st->done = 1;
+      st->status = SPHYNX_ERR_NOCONV;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// embedding signs: entry of largest magnitude of each column made positive
+// (lowest row on ties), then coords[i][j] = sign_{j+1} X[i][j+1] (Algorithm 2
+// lines 6-10).
+template <typename T>
+__global__ void k_argmax_partial(const T *x, int64_t n, int ld, int b, double *pval, int64_t *pidx) {
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  for (int c = 0; c < b; ++c) {
+    double best = -1.0, bestv = 0.0;
+    int64_t bidx = INT64_MAX;
+    for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < n;
+         row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      const double v = static_cast<double>(x[row * ld + c]);
+      const double m = fabs(v);
+      if (m > best) { best = m; bestv = v; bidx = row; }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bidx;
+    __shared__ double svv[256];
+    svv[threadIdx.x] = bestv;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        const double a = sv[threadIdx.x], o = sv[threadIdx.x + s];
+        const int64_t ia = si[threadIdx.x], io = si[threadIdx.x + s];
+        if (o > a || (o == a && io < ia)) {
+          sv[threadIdx.x] = o; si[threadIdx.x] = io; svv[threadIdx.x] = svv[threadIdx.x + s];
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      pval[(static_cast<int64_t>(blockIdx.x) * b + c) * 2] = sv[0];
+      pval[(static_cast<int64_t>(blockIdx.x) * b + c) * 2 + 1] = svv[0];
+      pidx[static_cast<int64_t>(blockIdx.x) * b + c] = si[0];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_argmax_final(const double *pval, const int64_t *pidx, int grid, int b, double *sign) {
+  const int c = threadIdx.x;
+  if (c >= b) return;
+  double best = -1.0, bestv = 0.0;
+  int64_t bidx = INT64_MAX;
+  for (int g = 0; g < grid; ++g) {
+    const double m = pval[(static_cast<int64_t>(g) * b + c) * 2];
+    const int64_t i = pidx[static_cast<int64_t>(g) * b + c];
+    if (m > best || (m == best && i < bidx)) {
+      best = m; bidx = i; bestv = pval[(static_cast<int64_t>(g) * b + c) * 2 + 1];
+    }
+  }
+  sign[c] = bestv < 0.0 ? -1.0 : 1.0;
+}
+
+template <typename T>
+__global__ void k_coords(const T *x, int64_t n, int ld, int b, const double *sign, T *coords) {
+  const int dims = b - 1;
+  const int64_t total = n * dims;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / dims;
+    const int j = static_cast<int>(idx - i * dims);
+    coords[idx] = sign[j + 1] < 0.0 ? -x[i * ld + j + 1] : x[i * ld + j + 1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos helpers (Sec. 5.2 setup): basis V is row-major n x ldv.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_lanczos_dots(const T *basis, int ldv, int j1, const T *w, int64_t n, double *partials) {
+  // blockDim (32, 8): x = column lane, y = row stripe
+  __shared__ double red[8][64];
+  using TA = T;
+  TA acc0 = 0, acc1 = 0;
+  const int c0 = threadIdx.x, c1 = threadIdx.x + 32;
+  for (int64_t row = blockIdx.x * 8LL + threadIdx.y; row < n; row += static_cast<int64_t>(gridDim.x) * 8) {
+    const TA wv = w[row];
+    if (c0 < j1) acc0 += basis[row * ldv + c0] * wv;
+    if (c1 < j1) acc1 += basis[row * ldv + c1] * wv;
+  }
+  red[threadIdx.y][c0] = static_cast<double>(acc0);
+  red[threadIdx.y][c1] = static_cast<double>(acc1);
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    for (int c = c0; c < 64; c += 32) {
+      if (c < j1) {
+        double s = 0.0;
+        for (int y = 0; y < 8; ++y) s += red[y][c];
+        partials[static_cast<int64_t>(blockIdx.x) * j1 + c] = s;
+      }
+    }
+  }
+}
+
+__global__ void k_reduce_cols(const double *partials, int grid, int cols, double *out) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < grid; g += blockDim.x) s += partials[static_cast<int64_t>(g) * cols + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = red[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_lanczos_sub(const T *basis, int ldv, int j1, T *w, int64_t n, const double *h, double *npart) {
+  __shared__ T sh[SPHYNX_MAX_POLY_DEGREE + 1];
+  __shared__ double red[8];
+  for (int c = threadIdx.x; c < j1; c += blockDim.x) sh[c] = static_cast<T>(h[c]);
+  __syncthreads();
+  T acc = 0;
+  for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < n;
+       row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    T v = w[row];
+    for (int c = 0; c < j1; ++c) v -= basis[row * ldv + c] * sh[c];
+    w[row] = v;
+    acc += v * v;
+  }
+  double d = static_cast<double>(acc);
+  for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += red[k];
+    npart[blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_lanczos_next(const T *w, T *v, T *basis, int ldv, int j, int64_t n, const double *beta2) {
+  const T inv = static_cast<T>(1.0 / sqrt(*beta2));
+  for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < n;
+       row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const T val = w[row] * inv;
+    v[row] = val;
+    basis[row * ldv + j] = val;
+  }
+}
+
+template <typename T>
+__global__ void k_poly_start(T *v, int64_t n, uint64_t state) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    v[i] = static_cast<T>(splitmix_pm1(state, static_cast<uint64_t>(i + 1)));
+}
+
+// partials of z.v and z.z with z the null vector (1, or sqrt(deg) for L_N)
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_null_dots(const T *v, int64_t n, int lap, const double *deg, double *partials) {
+  __shared__ double r0[8], r1[8];
+  double a0 = 0.0, a1 = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double z = lap == SPHYNX_NORMALIZED ? sqrt(deg[i]) : 1.0;
+    a0 += z * static_cast<double>(v[i]);
+    a1 += z * z;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    a0 += __shfl_down_sync(0xffffffffu, a0, off);
+    a1 += __shfl_down_sync(0xffffffffu, a1, off);
+  }
+  if ((threadIdx.x & 31) == 0) { r0[threadIdx.x >> 5] = a0; r1[threadIdx.x >> 5] = a1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = 0; k < 8; ++k) { s0 += r0[k]; s1 += r1[k]; }
+    partials[blockIdx.x * 2] = s0;
+    partials[blockIdx.x * 2 + 1] = s1;
+  }
+}
+
+template <typename T>
+__global__ void k_null_axpy(T *v, int64_t n, int lap, const double *deg, const double *scal) {
+  const double f = scal[0] / scal[1];
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double z = lap == SPHYNX_NORMALIZED ? sqrt(deg[i]) : 1.0;
+    v[i] = static_cast<T>(static_cast<double>(v[i]) - f * z);
+  }
+}
+
+// H = R / theta_1 (a polynomial of degree one)
+template <typename T>
+__global__ void k_poly_single(const T *r, T *h, int64_t total, const double *inv, const int *done) {
+  if (done && *done) return;
+  const T f = static_cast<T>(inv[0]);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    h[i] = r[i] * f;
+}
+
+}  // namespace
+
+// ===========================================================================
+// host launchers
+
+int vec_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 4 * kSmCount) g = 4 * kSmCount;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+void launch_zero(cudaStream_t s, void *p, size_t bytes) {
+  if (bytes) SPX_CUDA(cudaMemsetAsync(p, 0, bytes, s));
+}
+
+void launch_random_block(cudaStream_t s, DT dt, void *x, int64_t n, int b, int ld, uint64_t seed) {
+  const uint64_t state = mix64(seed + kGamma);
+  const unsigned g = blocks_for(n * ld, 256) > 8192 ? 8192 : blocks_for(n * ld, 256);
+  if (dt == DT::F64) k_random_block<double><<<g, 256, 0, s>>>(static_cast<double *>(x), n, b, ld, state);
+  else k_random_block<float><<<g, 256, 0, s>>>(static_cast<float *>(x), n, b, ld, state);
+  SPX_LAUNCHED();
+}
+
+void launch_piecewise_block(cudaStream_t s, DT dt, void *x, int64_t n, int b, int ld, int lap,
+                            const double *deg) {
+  const unsigned g = blocks_for(n * ld, 256) > 8192 ? 8192 : blocks_for(n * ld, 256);
+  if (dt == DT::F64) k_piecewise_block<double><<<g, 256, 0, s>>>(static_cast<double *>(x), n, b, ld, lap, deg);
+  else k_piecewise_block<float><<<g, 256, 0, s>>>(static_cast<float *>(x), n, b, ld, lap, deg);
+  SPX_LAUNCHED();
+}
+
+void launch_from_f64(cudaStream_t s, DT dt, void *x, const double *src, int64_t n, int b, int ld) {
+  const unsigned g = blocks_for(n * ld, 256) > 8192 ? 8192 : blocks_for(n * ld, 256);
+  if (dt == DT::F64) k_from_f64<double><<<g, 256, 0, s>>>(static_cast<double *>(x), src, n, b, ld);
+  else k_from_f64<float><<<g, 256, 0, s>>>(static_cast<float *>(x), src, n, b, ld);
+  SPX_LAUNCHED();
+}
+
+void launch_to_f64(cudaStream_t s, DT dt, const void *x, double *dst, int64_t n, int b, int ld) {
+  const unsigned g = blocks_for(n * b, 256) > 8192 ? 8192 : blocks_for(n * b, 256);
+  if (dt == DT::F64) k_to_f64<double><<<g, 256, 0, s>>>(static_cast<const double *>(x), dst, n, b, ld);
+  else k_to_f64<float><<<g, 256, 0, s>>>(static_cast<const float *>(x), dst, n, b, ld);
+  SPX_LAUNCHED();
+}
+
+int gram_grid(int64_t n) {
+  int64_t g = (n + 63) / 64;
+  if (g > 2 * kSmCount) g = 2 * kSmCount;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+size_t gram_partials_size(int nblk, int ld, int grid) {
+  GramDev d{};
+  gram_shape(nblk, ld, d);
+  return static_cast<size_t>(grid) * (d.nbA + d.nbB) * 16;
+}
+
+void launch_gram(cudaStream_t st, const GramArgs &a, int grid) {
+  GramDev d{};
+  gram_shape(a.nblk, a.ld, d);
+  d.n = a.n;
+  for (int k = 0; k < 3; ++k) {
+    d.s[k] = k < a.nblk ? a.s[k] : nullptr;
+    d.ls[k] = k < a.nblk ? a.ls[k] : nullptr;
+  }
+  d.partials = a.partials;
+  d.done = a.done;
+  const int NB = d.nbA + d.nbB;
+  if (a.dt == DT::F64) {
+    d.bdiag = a.bdiag;
+    const size_t tile = static_cast<size_t>(GramTile<double>::rows) * d.M * sizeof(double) * (a.bdiag ? 3 : 2);
+    const size_t red = static_cast<size_t>(d.ngroups) * NB * 16 * sizeof(double);
+    const size_t sm = tile > red ? tile : red;
+    SPX_CUDA(cudaFuncSetAttribute(k_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    k_gram<double><<<grid, kGramThreads, sm, st>>>(d);
+  } else {
+    d.bdiag = a.bdiagf;
+    const size_t tile = static_cast<size_t>(GramTile<float>::rows) * d.M * sizeof(float) * (a.bdiagf ? 3 : 2);
+    const size_t red = static_cast<size_t>(d.ngroups) * NB * 16 * sizeof(double);
+    const size_t sm = tile > red ? tile : red;
+    SPX_CUDA(cudaFuncSetAttribute(k_gram<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    k_gram<float><<<grid, kGramThreads, sm, st>>>(d);
+  }
+  SPX_LAUNCHED();
+}
+
+template <typename T, int LD>
+static void update_ld(cudaStream_t st, const UpdateArgs &a, unsigned g) {
+  const T *s0 = static_cast<const T *>(a.s[0]);
+  const T *y = static_cast<const T *>(a.y);
+  if (a.nblk == 1) {
+    k_update<T, LD, 1><<<g, 256, 0, st>>>(a.n, s0, nullptr, nullptr, nullptr, nullptr, y,
+                                          static_cast<T *>(a.xo), nullptr, nullptr, a.done);
+  } else {
+    k_update<T, LD, 3><<<g, 256, 0, st>>>(
+        a.n, s0, static_cast<const T *>(a.s[1]), static_cast<const T *>(a.s[2]),
+        static_cast<const T *>(a.ls[1]), static_cast<const T *>(a.ls[2]), y, static_cast<T *>(a.xo),
+        static_cast<T *>(a.po), static_cast<T *>(a.lpo), a.done);
+  }
+  SPX_LAUNCHED();
+}
+
+void launch_update(cudaStream_t st, const UpdateArgs &a) {
+  if (a.nblk != 1 && a.nblk != 3) fail(SPHYNX_ERR_INVALID_ARG, "update: nblk %d", a.nblk);
+  const unsigned g = static_cast<unsigned>(vec_grid(a.n) * 2);
+  if (a.dt == DT::F64) {
+    switch (a.ld) {
+      case 4: update_ld<double, 4>(st, a, g); break;
+      case 8: update_ld<double, 8>(st, a, g); break;
+      case 12: update_ld<double, 12>(st, a, g); break;
+      case 16: update_ld<double, 16>(st, a, g); break;
+      default: fail(SPHYNX_ERR_INVALID_ARG, "update: ld %d", a.ld);
+    }
+  } else {
+    switch (a.ld) {
+      case 4: update_ld<float, 4>(st, a, g); break;
+      case 8: update_ld<float, 8>(st, a, g); break;
+      case 12: update_ld<float, 12>(st, a, g); break;
+      case 16: update_ld<float, 16>(st, a, g); break;
+      default: fail(SPHYNX_ERR_INVALID_ARG, "update: ld %d", a.ld);
+    }
+  }
+}
+
+int residual_grid(int64_t n) { return vec_grid(n); }
+
+template <typename T, int LD>
+static void residual_ld(cudaStream_t st, const ResidualArgs &a, int grid) {
+  const T *bd = nullptr, *jv = nullptr;
+  if constexpr (std::is_same<T, double>::value) {
+    bd = a.bdiag;
+    jv = a.jinv;
+  } else {
+    bd = a.bdiagf;
+    jv = a.jinvf;
+  }
+  k_residual<T, LD><<<grid, 256, 0, st>>>(a.n, static_cast<const T *>(a.x), static_cast<const T *>(a.lx),
+                                          a.theta, bd, jv, static_cast<T *>(a.out), a.norm_partials, a.done);
+  SPX_LAUNCHED();
+}
+
+void launch_residual(cudaStream_t st, const ResidualArgs &a, int grid) {
+  if (a.dt == DT::F64) {
+    switch (a.ld) {
+      case 4: residual_ld<double, 4>(st, a, grid); break;
+      case 8: residual_ld<double, 8>(st, a, grid); break;
+      case 12: residual_ld<double, 12>(st, a, grid); break;
+      case 16: residual_ld<double, 16>(st, a, grid); break;
+      default: fail(SPHYNX_ERR_INVALID_ARG, "residual: ld %d", a.ld);
+    }
+  } else {
+    switch (a.ld) {
+      case 4: residual_ld<float, 4>(st, a, grid); break;
+      case 8: residual_ld<float, 8>(st, a, grid); break;
+      case 12: residual_ld<float, 12>(st, a, grid); break;
+      case 16: residual_ld<float, 16>(st, a, grid); break;
+      default: fail(SPHYNX_ERR_INVALID_ARG, "residual: ld %d", a.ld);
+    }
+  }
+}
+
+void launch_converge(cudaStream_t st, SolverState *state, const double *partials, int grid, int b,
+                     int ld, double tol, double floor_abs, int count_iteration, int maxit) {
+  k_converge<<<1, 256, 0, st>>>(state, partials, grid, b, ld, tol, floor_abs, count_iteration, maxit);
+  SPX_LAUNCHED();
+}
+
+void launch_signs_coords(cudaStream_t st, DT dt, const void *x, int64_t n, int ld, int b,
+                         void *coords, double *scratch) {
+  const int grid = vec_grid(n);
+  double *pval = scratch;                                            // grid * b * 2
+  int64_t *pidx = reinterpret_cast<int64_t *>(scratch + static_cast<size_t>(grid) * b * 2);
+  double *sign = scratch + static_cast<size_t>(grid) * b * 3;         // b
+  if (dt == DT::F64) {
+    k_argmax_partial<double><<<grid, 256, 0, st>>>(static_cast<const double *>(x), n, ld, b, pval, pidx);
+  } else {
+    k_argmax_partial<float><<<grid, 256, 0, st>>>(static_cast<const float *>(x), n, ld, b, pval, pidx);
+  }
+  SPX_LAUNCHED();
+  k_argmax_final<<<1, 32, 0, st>>>(pval, pidx, grid, b, sign);
+  SPX_LAUNCHED();
+  if (b > 1) {
+    const unsigned g = blocks_for(n * (b - 1), 256) > 8192 ? 8192 : blocks_for(n * (b - 1), 256);
+    if (dt == DT::F64)
+      k_coords<double><<<g, 256, 0, st>>>(static_cast<const double *>(x), n, ld, b, sign, static_cast<double *>(coords));
+    else
+      k_coords<float><<<g, 256, 0, st>>>(static_cast<const float *>(x), n, ld, b, sign, static_cast<float *>(coords));
+    SPX_LAUNCHED();
+  }
+}
+
+void launch_lanczos_dots(cudaStream_t st, DT dt, const void *basis, int ldv, int j1, const void *w,
+                         int64_t n, double *partials, int grid) {
+  dim3 blk(32, 8);
+  if (dt == DT::F64)
+    k_lanczos_dots<double><<<grid, blk, 0, st>>>(static_cast<const double *>(basis), ldv, j1,
+                                                 static_cast<const double *>(w), n, partials);
+  else
+    k_lanczos_dots<float><<<grid, blk, 0, st>>>(static_cast<const float *>(basis), ldv, j1,
+                                                static_cast<const float *>(w), n, partials);
+  SPX_LAUNCHED();
+}
+
+void launch_reduce_cols(cudaStream_t st, const double *partials, int grid, int cols, double *out) {
+  k_reduce_cols<<<cols, 256, 0, st>>>(partials, grid, cols, out);
+  SPX_LAUNCHED();
+}
+
+void launch_lanczos_sub(cudaStream_t st, DT dt, const void *basis, int ldv, int j1, void *w, int64_t n,
+                        const double *h, double *norm_partials, int grid) {
+  if (dt == DT::F64)
+    k_lanczos_sub<double><<<grid, 256, 0, st>>>(static_cast<const double *>(basis), ldv, j1,
+                                                static_cast<double *>(w), n, h, norm_partials);
+  else
+    k_lanczos_sub<float><<<grid, 256, 0, st>>>(static_cast<const float *>(basis), ldv, j1,
+                                               static_cast<float *>(w), n, h, norm_partials);
+  SPX_LAUNCHED();
+}
+
+void launch_lanczos_next(cudaStream_t st, DT dt, const void *w, void *v, void *basis, int ldv, int j,
+                         int64_t n, const double *beta2) {
+  const int g = vec_grid(n);
+  if (dt == DT::F64)
+    k_lanczos_next<double><<<g, 256, 0, st>>>(static_cast<const double *>(w), static_cast<double *>(v),
+                                              static_cast<double *>(basis), ldv, j, n, beta2);
+  else
+    k_lanczos_next<float><<<g, 256, 0, st>>>(static_cast<const float *>(w), static_cast<float *>(v),
+                                             static_cast<float *>(basis), ldv, j, n, beta2);
+  SPX_LAUNCHED();
+}
+
+void launch_poly_start(cudaStream_t st, DT dt, void *v, int64_t n, uint64_t seed) {
+  const uint64_t state = mix64(seed + 3 * kGamma);
+  const int g = vec_grid(n);
+  if (dt == DT::F64) k_poly_start<double><<<g, 256, 0, st>>>(static_cast<double *>(v), n, state);
+  else k_poly_start<float><<<g, 256, 0, st>>>(static_cast<float *>(v), n, state);
+  SPX_LAUNCHED();
+}
+
+void launch_project_null(cudaStream_t st, DT dt, void *v, int64_t n, int lap, const double *deg,
+                         double *partials, int grid, double *scal) {
+  if (dt == DT::F64)
+    k_null_dots<double><<<grid, 256, 0, st>>>(static_cast<const double *>(v), n, lap, deg, partials);
+  else
+    k_null_dots<float><<<grid, 256, 0, st>>>(static_cast<const float *>(v), n, lap, deg, partials);
+  SPX_LAUNCHED();
+  k_reduce_cols<<<2, 256, 0, st>>>(partials, grid, 2, scal);
+  SPX_LAUNCHED();
+  if (dt == DT::F64) k_null_axpy<double><<<grid, 256, 0, st>>>(static_cast<double *>(v), n, lap, deg, scal);
+  else k_null_axpy<float><<<grid, 256, 0, st>>>(static_cast<float *>(v), n, lap, deg, scal);
+  SPX_LAUNCHED();
+}
+
+void launch_poly_single(cudaStream_t st, DT dt, const void *r, void *h, int64_t n, int ld,
+                        const double *inv, const int *done) {
+  const int g = vec_grid(n * ld);
+  if (dt == DT::F64)
+    k_poly_single<double><<<g, 256, 0, st>>>(static_cast<const double *>(r), static_cast<double *>(h), n * ld, inv, done);
+  else
+    k_poly_single<float><<<g, 256, 0, st>>>(static_cast<const float *>(r), static_cast<float *>(h), n * ld, inv, done);
+  SPX_LAUNCHED();
+}
+
+}  // namespace sphynx
+
+namespace sphynx {
+namespace {
+__global__ void k_d2f(const double *src, float *dst, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[i] = static_cast<float>(src[i]);
+}
+}  // namespace
+void launch_d2f(cudaStream_t st, const double *src, float *dst, int64_t n) {
+  k_d2f<<<vec_grid(n), 256, 0, st>>>(src, dst, n);
+  SPX_LAUNCHED();
+}
+}  // namespace sphynx

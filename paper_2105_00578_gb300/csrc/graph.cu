@@ -1,0 +1,477 @@
+// graph.cu -- graph handles: CSR intake and checks, weighted degrees and
+// D^{-1/2} (Sec. 3.2), the SpMM row plan, and the exact partition metrics
+// (Eq. 1 cutsize and the imbalance of Sec. 3.1).
+#include "internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <memory>
+
+namespace sphynx {
+
+namespace {
+thread_local std::string g_error;
+}
+
+void set_error_message(const char *msg) { g_error = msg; }
+void clear_error() { g_error.clear(); }
+const char *last_error_message() { return g_error.c_str(); }
+
+void fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  throw Error{code};
+}
+
+void fail_cuda(cudaError_t e, const char *what, const char *file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error %d (%s) in %s at %s:%d", static_cast<int>(e), cudaGetErrorString(e),
+           what, file, line);
+  g_error = buf;
+  throw Error{e == cudaErrorMemoryAllocation ? SPHYNX_ERR_OOM : SPHYNX_ERR_CUDA};
+}
+
+void DevBuf::alloc(size_t nbytes) {
+  release();
+  if (nbytes == 0) return;
+  cudaError_t e = cudaMalloc(&p, nbytes);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    fail(SPHYNX_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", nbytes, cudaGetErrorString(e));
+  }
+  bytes = nbytes;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+namespace {
+
+enum : unsigned {
+  kBadRowPtr = 1u,
+  kBadCol = 2u,
+  kSelfLoop = 4u,
+  kUnsorted = 8u,
+  kAsym = 16u,
+  kBadWeight = 32u,
+  kBadVWeight = 64u,
+};
+
+struct GraphStatsDev {
+  unsigned long long max_deg;
+  unsigned long long max_wdeg_bits;   // non-negative double as ordered bits
+  unsigned long long isolated;
+  unsigned long long total_vw;
+  int min_exp, max_exp;
+  unsigned flags;
+  int pad;
+};
+
+// row_ptr monotone and in [0, nnz]; every column index in [0, n)
+__global__ void k_check_rowptr(const int64_t *rp, int64_t n, int64_t nnz, GraphStatsDev *gs) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t a = rp[i], b = rp[i + 1];
+    if (a < 0 || b < a || b > nnz) atomicOr(&gs->flags, kBadRowPtr);
+  }
+}
+
+__global__ void k_check_cols(const int32_t *col, int64_t nnz, int64_t n, GraphStatsDev *gs) {
+  unsigned bad = 0;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t j = col[e];
+    if (j < 0 || static_cast<int64_t>(j) >= n) bad = kBadCol;
+  }
+  if (bad) atomicOr(&gs->flags, bad);
+}
+
+// sortedness, self-loops and symmetry (binary search for (j, i)); weights
+// positive, finite and symmetric.  Only runs after the bounds checks passed.
+__global__ void k_validate(const int64_t *rp, const int32_t *col, const float *w, int64_t n,
+                           GraphStatsDev *gs) {
+  unsigned bad = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t a = rp[i], b = rp[i + 1];
+    for (int64_t e = a; e < b; ++e) {
+      const int32_t j = col[e];
+      if (j == i) bad |= kSelfLoop;
+      if (e > a && col[e - 1] >= j) bad |= kUnsorted;
+      if (w && !(w[e] > 0.f && isfinite(w[e]))) bad |= kBadWeight;
+      int64_t lo = rp[j], hi = rp[j + 1] - 1;
+      int64_t found = -1;
+      while (lo <= hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        const int32_t c = col[mid];
+        if (c == i) { found = mid; break; }
+        if (c < i) lo = mid + 1; else hi = mid - 1;
+      }
+      if (found < 0) bad |= kAsym;
+      else if (w && w[found] != w[e]) bad |= kAsym;
+    }
+  }
+  if (bad) atomicOr(&gs->flags, bad);
+}
+
+__device__ inline unsigned long long dbits(double v) { return static_cast<unsigned long long>(__double_as_longlong(v)); }
+
+__global__ void k_degrees(const int64_t *rp, const float *w, const int64_t *vw, int64_t n, double *deg,
+                          float *degf, double *dinv, float *dinvf, double *jinv, float *jinvf,
+                          GraphStatsDev *gs) {
+  unsigned long long mdeg = 0, mw = 0, iso = 0, tvw = 0;
+  int mine = 1 << 20, maxe = -(1 << 20);
+  unsigned bad = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t a = rp[i], b = rp[i + 1];
+    double d;
+    if (w) {
+      d = 0.0;
+      for (int64_t e = a; e < b; ++e) {
+        d += static_cast<double>(w[e]);
+        int ex;
+        frexpf(w[e], &ex);
+        if (w[e] != 0.f) { mine = min(mine, ex); maxe = max(maxe, ex); }
+      }
+    } else {
+      d = static_cast<double>(b - a);
+    }
+    deg[i] = d;
+    degf[i] = static_cast<float>(d);
+    const double s = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    dinv[i] = s;
+    dinvf[i] = static_cast<float>(s);
+    const double jv = d > 0.0 ? 1.0 / d : 1.0;
+    jinv[i] = jv;
+    jinvf[i] = static_cast<float>(jv);
+    mdeg = max(mdeg, static_cast<unsigned long long>(b - a));
+    mw = max(mw, dbits(d));
+    iso += (b == a) ? 1 : 0;
+    if (vw) {
+      if (vw[i] < 1) bad |= kBadVWeight;
+      tvw += static_cast<unsigned long long>(vw[i]);
+    } else {
+      tvw += 1;
+    }
+  }
+  atomicMax(&gs->max_deg, mdeg);
+  atomicMax(&gs->max_wdeg_bits, mw);
+  if (iso) atomicAdd(&gs->isolated, iso);
+  atomicAdd(&gs->total_vw, tvw);
+  if (w) {
+    atomicMin(&gs->min_exp, mine);
+    atomicMax(&gs->max_exp, maxe);
+  }
+  if (bad) atomicOr(&gs->flags, bad);
+}
+
+// ---- Eq. 1 cutsize and part weights ----------------------------------------
+__global__ void __launch_bounds__(256)
+k_eval(const int64_t *rp, const int32_t *col, const float *w, const int64_t *vw, int64_t n,
+       const int32_t *part, int K, int wscale, unsigned long long *cut2, long long *pw, unsigned *badpart,
+       int use_smem) {
+  extern __shared__ long long spw[];
+  if (use_smem) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) spw[k] = 0;
+    __syncthreads();
+  }
+  unsigned long long acc = 0;
+  unsigned bad = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t pi = part[i];
+    if (pi < 0 || pi >= K) { bad = 1; continue; }
+    const long long wv = vw ? vw[i] : 1;
+    if (use_smem) atomicAdd(reinterpret_cast<unsigned long long *>(&spw[pi]), static_cast<unsigned long long>(wv));
+    else atomicAdd(reinterpret_cast<unsigned long long *>(&pw[pi]), static_cast<unsigned long long>(wv));
+    const int64_t a = rp[i], b = rp[i + 1];
+    for (int64_t e = a; e < b; ++e) {
+      const int32_t pj = part[col[e]];
+      if (pj != pi) {
+        if (w) acc += static_cast<unsigned long long>(llrint(ldexp(static_cast<double>(w[e]), wscale)));
+        else acc += 1;
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(cut2, acc);
+  if (bad) atomicOr(badpart, 1u);
+  if (use_smem) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+      if (spw[k]) atomicAdd(reinterpret_cast<unsigned long long *>(&pw[k]), static_cast<unsigned long long>(spw[k]));
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 8 * kSmCount) g = 8 * kSmCount;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+void build_plan(sphynx_graph *g, const int64_t *host_rowptr) {
+  SpmmPlan &p = g->plan;
+  p.n_long = 0;
+  p.n_items = 0;
+  if (g->max_degree <= kShortDeg) return;
+  std::vector<int64_t> rp_copy;
+  const int64_t *rp = host_rowptr;
+  if (!rp) {
+    rp_copy.resize(static_cast<size_t>(g->n) + 1);
+    SPX_CUDA(cudaMemcpyAsync(rp_copy.data(), g->rowptr, (g->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             g->stream));
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
+    rp = rp_copy.data();
+  }
+  std::vector<int64_t> items, split;
+  for (int64_t i = 0; i < g->n; ++i) {
+    const int64_t a = rp[i], b = rp[i + 1];
+    if (b - a <= kShortDeg) continue;
+    const int64_t first = static_cast<int64_t>(items.size() / 4);
+    int64_t cnt = 0;
+    for (int64_t s = a; s < b; s += kLongChunk) {
+      items.push_back(i);
+      items.push_back(s);
+      items.push_back(s + kLongChunk < b ? s + kLongChunk : b);
+      items.push_back(first + cnt);
+      ++cnt;
+    }
+    split.push_back(i);
+    split.push_back(first);
+    split.push_back(cnt);
+  }
+  p.n_items = static_cast<int64_t>(items.size() / 4);
+  p.n_long = static_cast<int64_t>(split.size() / 3);
+  p.items.alloc(items.size() * sizeof(int64_t));
+  p.split.alloc(split.size() * sizeof(int64_t));
+  SPX_CUDA(cudaMemcpyAsync(p.items.p, items.data(), items.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
+  SPX_CUDA(cudaMemcpyAsync(p.split.p, split.data(), split.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
+  p.partials.alloc(static_cast<size_t>(p.n_items) * 16 * sizeof(double));
+  SPX_CUDA(cudaStreamSynchronize(g->stream));
+}
+
+}  // namespace
+
+void eval_partition(sphynx_graph *g, const int32_t *part, int K, double *cut, double *cut2, double *imb) {
+  if (K < 1) fail(SPHYNX_ERR_INVALID_ARG, "K must be >= 1");
+  if (g->weighted && !g->wexact)
+    fail(SPHYNX_ERR_UNSUPPORTED, "edge weights span too many binary orders for an exact cut");
+  const size_t need = 64 + static_cast<size_t>(K) * sizeof(long long);
+  char *ws = static_cast<char *>(g->workspace("eval", need, false));
+  SPX_CUDA(cudaMemsetAsync(ws, 0, need, g->stream));
+  unsigned long long *d_cut = reinterpret_cast<unsigned long long *>(ws);
+  unsigned *d_bad = reinterpret_cast<unsigned *>(ws + 8);
+  long long *d_pw = reinterpret_cast<long long *>(ws + 64);
+  const int use_smem = K <= 4096 ? 1 : 0;
+  const size_t sm = use_smem ? K * sizeof(long long) : 0;
+  k_eval<<<grid_for(g->n), 256, sm, g->stream>>>(g->rowptr, g->col, g->w, g->vw, g->n, part, K, g->wscale, d_cut,
+                                                 d_pw, d_bad, use_smem);
+  SPX_LAUNCHED();
+  g->ctr.launches++;
+  std::vector<char> host(need);
+  SPX_CUDA(cudaMemcpyAsync(host.data(), ws, need, cudaMemcpyDeviceToHost, g->stream));
+  SPX_CUDA(cudaStreamSynchronize(g->stream));
+  unsigned bad;
+  memcpy(&bad, host.data() + 8, sizeof(bad));
+  if (bad) fail(SPHYNX_ERR_INVALID_ARG, "part ids outside [0, K)");
+  unsigned long long c2;
+  memcpy(&c2, host.data(), sizeof(c2));
+  const long long *pw = reinterpret_cast<const long long *>(host.data() + 64);
+  long long mx = 0, tot = 0;
+  for (int k = 0; k < K; ++k) {
+    mx = pw[k] > mx ? pw[k] : mx;
+    tot += pw[k];
+  }
+  const double twice = ldexp(static_cast<double>(c2), g->weighted ? -g->wscale : 0);
+  if (cut2) *cut2 = twice;
+  if (cut) *cut = ldexp(static_cast<double>(c2), g->weighted ? -(g->wscale + 1) : -1);
+  if (imb) *imb = (static_cast<double>(mx) * static_cast<double>(K)) / static_cast<double>(tot);
+}
+
+}  // namespace sphynx
+
+using namespace sphynx;
+
+void *sphynx_graph::workspace(const std::string &name, size_t bytes, bool zero) {
+  DevBuf &b = ws[name];
+  if (b.bytes < bytes) {
+    b.alloc(bytes);
+    zero = true;
+  }
+  if (zero && bytes) SPX_CUDA(cudaMemsetAsync(b.p, 0, bytes, stream));
+  return b.p;
+}
+
+extern "C" {
+
+const char *sphynx_last_error(void) { return sphynx::last_error_message(); }
+
+void sphynx_default_options(sphynx_options *opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->laplacian = SPHYNX_COMBINATORIAL;
+  opt->precond = SPHYNX_PRECOND_JACOBI;
+  opt->poly_degree = 25;
+  opt->precision = SPHYNX_FP64;
+  opt->init = SPHYNX_INIT_RANDOM;
+  opt->max_iter = 1000;
+  opt->tol = 1e-3;
+  opt->seed = 1;
+  opt->flags = 0;
+  opt->sync_every = 0;
+}
+
+int sphynx_create(const int64_t *row_ptr, const int32_t *col, const float *edge_w, const int64_t *vtx_w,
+                  int64_t n, int64_t nnz, uint32_t flags, void *stream, sphynx_handle *out) {
+  return guarded([&]() -> int {
+    if (!out) fail(SPHYNX_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || nnz < 0) fail(SPHYNX_ERR_INVALID_ARG, "n must be >= 1 and nnz >= 0");
+    if (n >= (1LL << 31) - 1) fail(SPHYNX_ERR_UNSUPPORTED, "n >= 2^31 - 1");
+    if (nnz >= (1LL << 40)) fail(SPHYNX_ERR_UNSUPPORTED, "nnz >= 2^40");
+    if (!row_ptr || (nnz > 0 && !col)) fail(SPHYNX_ERR_INVALID_ARG, "row_ptr/col is NULL");
+    const bool dev = (flags & SPHYNX_DEVICE_PTRS) != 0;
+    if (!dev && (row_ptr[0] != 0 || row_ptr[n] != nnz))
+      fail(SPHYNX_ERR_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[n] = nnz");
+    std::unique_ptr<sphynx_graph> g(new sphynx_graph());
+    SPX_CUDA(cudaGetDevice(&g->device));
+    g->stream = static_cast<cudaStream_t>(stream);
+    g->n = n;
+    g->nnz = nnz;
+    g->weighted = edge_w != nullptr;
+    g->has_vw = vtx_w != nullptr;
+    if (dev) {
+      g->rowptr = row_ptr;
+      g->col = col;
+      g->w = edge_w;
+      g->vw = vtx_w;
+    } else {
+      g->own_rowptr.alloc((n + 1) * sizeof(int64_t));
+      SPX_CUDA(cudaMemcpyAsync(g->own_rowptr.p, row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
+      g->rowptr = g->own_rowptr.as<int64_t>();
+      g->own_col.alloc((nnz > 0 ? nnz : 1) * sizeof(int32_t));
+      if (nnz) SPX_CUDA(cudaMemcpyAsync(g->own_col.p, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+      g->col = g->own_col.as<int32_t>();
+      if (edge_w) {
+        g->own_w.alloc((nnz > 0 ? nnz : 1) * sizeof(float));
+        if (nnz) SPX_CUDA(cudaMemcpyAsync(g->own_w.p, edge_w, nnz * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+        g->w = g->own_w.as<float>();
+      }
+      if (vtx_w) {
+        g->own_vw.alloc(n * sizeof(int64_t));
+        SPX_CUDA(cudaMemcpyAsync(g->own_vw.p, vtx_w, n * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
+        g->vw = g->own_vw.as<int64_t>();
+      }
+    }
+    g->deg.alloc(n * sizeof(double));
+    g->degf.alloc(n * sizeof(float));
+    g->dinv.alloc(n * sizeof(double));
+    g->dinvf.alloc(n * sizeof(float));
+    g->jinv.alloc(n * sizeof(double));
+    g->jinvf.alloc(n * sizeof(float));
+    SPX_CUDA(cudaMallocHost(&g->host_flag, 256));
+
+    DevBuf gsb;
+    gsb.alloc(sizeof(GraphStatsDev));
+    GraphStatsDev init{};
+    init.min_exp = 1 << 20;
+    init.max_exp = -(1 << 20);
+    SPX_CUDA(cudaMemcpyAsync(gsb.p, &init, sizeof(init), cudaMemcpyHostToDevice, g->stream));
+    GraphStatsDev *gs = gsb.as<GraphStatsDev>();
+    GraphStatsDev h{};
+    // bounds first: nothing indexes col[] through row_ptr before these pass
+    k_check_rowptr<<<grid_for(n), 256, 0, g->stream>>>(g->rowptr, n, nnz, gs);
+    SPX_LAUNCHED();
+    if (nnz) {
+      k_check_cols<<<grid_for(nnz), 256, 0, g->stream>>>(g->col, nnz, n, gs);
+      SPX_LAUNCHED();
+    }
+    SPX_CUDA(cudaMemcpyAsync(&h, gs, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
+    if (h.flags & kBadRowPtr) fail(SPHYNX_ERR_INVALID_ARG, "row_ptr is not non-decreasing within [0, nnz]");
+    if (h.flags & kBadCol) fail(SPHYNX_ERR_INVALID_ARG, "column index outside [0, n)");
+    if (flags & SPHYNX_VALIDATE) {
+      k_validate<<<grid_for(n), 256, 0, g->stream>>>(g->rowptr, g->col, g->w, n, gs);
+      SPX_LAUNCHED();
+    }
+    k_degrees<<<grid_for(n), 256, 0, g->stream>>>(g->rowptr, g->w, g->vw, n, g->deg.as<double>(), g->degf.as<float>(),
+                                                  g->dinv.as<double>(), g->dinvf.as<float>(), g->jinv.as<double>(),
+                                                  g->jinvf.as<float>(), gs);
+    SPX_LAUNCHED();
+    SPX_CUDA(cudaMemcpyAsync(&h, gs, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
+    if (h.flags & kSelfLoop) fail(SPHYNX_ERR_INVALID_ARG, "self-loop in the adjacency");
+    if (h.flags & kUnsorted) fail(SPHYNX_ERR_INVALID_ARG, "column indices not strictly increasing in a row");
+    if (h.flags & kBadWeight) fail(SPHYNX_ERR_INVALID_ARG, "edge weight not positive and finite");
+    if (h.flags & kAsym) fail(SPHYNX_ERR_NOT_SYMMETRIC, "adjacency is not symmetric");
+    if (h.flags & kBadVWeight) fail(SPHYNX_ERR_INVALID_ARG, "vertex weight below 1");
+    g->max_degree = static_cast<int64_t>(h.max_deg);
+    memcpy(&g->max_wdeg, &h.max_wdeg_bits, sizeof(double));
+    g->isolated = static_cast<int64_t>(h.isolated);
+    g->total_vw = static_cast<int64_t>(h.total_vw);
+    if (g->total_vw >= (1LL << 40)) fail(SPHYNX_ERR_UNSUPPORTED, "total vertex weight >= 2^40");
+    if (g->weighted && nnz) {
+      // weight * 2^wscale is an integer for every float weight (24-bit mantissa)
+      g->wscale = 24 - h.min_exp;
+      const double top = ldexp(1.0, h.max_exp + g->wscale) * static_cast<double>(nnz);
+      g->wexact = top < 9.0e18;
+    }
+    build_plan(g.get(), dev ? nullptr : row_ptr);
+    *out = g.release();
+    return SPHYNX_OK;
+  });
+}
+
+void sphynx_destroy(sphynx_handle g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  for (auto e : g->ctr.ev_pool) cudaEventDestroy(e);
+  if (g->host_flag) cudaFreeHost(g->host_flag);
+  delete g;
+}
+
+int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info) {
+  return guarded([&]() -> int {
+    if (!g || !info) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->n = g->n;
+    info->nnz = g->nnz;
+    info->max_degree = g->max_degree;
+    info->max_wdegree = g->max_wdeg;
+    info->total_vweight = g->total_vw;
+    info->long_rows = g->plan.n_long;
+    info->weighted = g->weighted ? 1 : 0;
+    info->spmm_variant = g->plan.rows_per_warp;
+    return SPHYNX_OK;
+  });
+}
+
+int sphynx_degrees(sphynx_handle g, double *deg_out) {
+  return guarded([&]() -> int {
+    if (!g || !deg_out) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
+    SPX_CUDA(cudaMemcpyAsync(deg_out, g->deg.p, g->n * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    return SPHYNX_OK;
+  });
+}
+
+int sphynx_eval(sphynx_handle g, const int32_t *part, int32_t K, double *cut, double *cut_twice,
+                double *imbalance) {
+  return guarded([&]() -> int {
+    if (!g || !part) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
+    eval_partition(g, part, K, cut, cut_twice, imbalance);
+    return SPHYNX_OK;
+  });
+}
+
+}  // extern "C"

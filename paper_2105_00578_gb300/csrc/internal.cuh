@@ -1,0 +1,282 @@
+// internal.cuh -- declarations shared by the library's translation units.
+//
+// Nothing here is part of the public ABI (include/sphynx.h).  Errors inside
+// the library are C++ exceptions of type sphynx::Error; every extern "C"
+// entry point catches them and returns the status code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sphynx.h"
+
+namespace sphynx {
+
+struct Error {
+  int code;
+};
+
+[[noreturn]] void fail(int code, const char *fmt, ...);
+[[noreturn]] void fail_cuda(cudaError_t e, const char *what, const char *file, int line);
+void set_error_message(const char *msg);
+void clear_error();
+
+#define SPX_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) ::sphynx::fail_cuda(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define SPX_LAUNCHED() SPX_CUDA(cudaGetLastError())
+
+// Runs `body` and converts exceptions into status codes at the ABI boundary.
+template <class F>
+int guarded(F &&body) {
+  try {
+    clear_error();
+    return body();
+  } catch (const Error &e) {
+    return e.code;
+  } catch (...) {
+    set_error_message("unexpected C++ exception");
+    return SPHYNX_ERR_CUDA;
+  }
+}
+
+// Owning device allocation.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    release();
+    p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0;
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t nbytes);   // throws OOM; contents undefined
+  void release();
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Block element types used by the kernels.
+enum class DT { F64 = SPHYNX_DT_F64, F32 = SPHYNX_DT_F32, BF16 = SPHYNX_DT_BF16 };
+inline size_t dt_size(DT d) { return d == DT::F64 ? 8 : (d == DT::F32 ? 4 : 2); }
+
+constexpr int kShortDeg = 32;        // rows with more neighbours use the long-row kernels
+constexpr int kLongChunk = 4096;     // entries per long-row work item
+constexpr int kSmCount = 152;
+
+struct SpmmPlan {
+  int rows_per_warp = 32;            // short-row schedule
+  int64_t n_long = 0;                // rows with degree > kShortDeg
+  int64_t n_items = 0;               // long-row work items
+  int64_t n_split = 0;               // rows cut into more than one item
+  DevBuf items;                      // int64 [n_items][4]: row, begin, end, slot(-1 = direct)
+  DevBuf split;                      // int64 [n_split][3]: row, first slot, slot count
+  DevBuf partials;                   // scratch for split rows, sized per call
+};
+
+// Everything the iteration kernels need to apply L without forming it.
+struct LapView {
+  int64_t n;
+  const int64_t *rowptr;
+  const int32_t *col;
+  const float *w;          // NULL = unit weights
+  const double *deg;       // weighted degree (double)
+  const float *degf;       // weighted degree (float)
+  const double *dinv;      // deg^{-1/2}
+  const float *dinvf;
+};
+
+struct Counters {
+  int64_t launches = 0;
+  int64_t spmm_launches = 0;
+  double spmm_bytes = 0;
+  double spmm_ms = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;  // pairs recorded around SpMMs
+  size_t ev_used = 0;
+};
+
+}  // namespace sphynx
+
+struct sphynx_graph {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0, nnz = 0;
+  bool weighted = false, has_vw = false;
+  const int64_t *rowptr = nullptr;
+  const int32_t *col = nullptr;
+  const float *w = nullptr;
+  const int64_t *vw = nullptr;
+  sphynx::DevBuf own_rowptr, own_col, own_w, own_vw;
+  sphynx::DevBuf deg, degf, dinv, dinvf;
+  sphynx::DevBuf jinv, jinvf;  // Jacobi: 1 / deg (1 where deg = 0)
+  int64_t max_degree = 0;
+  double max_wdeg = 0;
+  int64_t total_vw = 0;
+  int64_t isolated = 0;
+  int wscale = 0;            // exact-cut fixed point: weight * 2^wscale is an integer
+  bool wexact = true;        // the fixed-point sum cannot overflow int64
+  sphynx::SpmmPlan plan;
+  // polynomial preconditioner state (Sec. 5.2)
+  int poly_k = 0;
+  int poly_laplacian = -1;
+  sphynx::DevBuf poly_inv;   // double[k]: 1 / theta_i
+  sphynx::DevBuf poly_invf;  // float[k]
+  std::vector<double> poly_roots;
+  std::map<std::string, sphynx::DevBuf> ws;  // named workspaces, grown on demand
+  sphynx::Counters ctr;
+  sphynx::DevBuf pinned_dummy;
+  void *host_flag = nullptr;                 // pinned int32[8] for convergence polls
+  sphynx::LapView view() const {
+    return sphynx::LapView{n, rowptr, col, w, deg.as<double>(), degf.as<float>(),
+                           dinv.as<double>(), dinvf.as<float>()};
+  }
+  void *workspace(const std::string &name, size_t bytes, bool zero = false);
+};
+
+namespace sphynx {
+
+// ---- spmm.cu ----------------------------------------------------------------
+// Y = L X (mode 0) or one step of the polynomial chain (mode 1):
+//   t_out = t - (L t) * inv_cur;  yacc = (first ? t * inv_first : yacc) + t_out * inv_next
+struct SpmmArgs {
+  int lap;                 // SPHYNX_COMBINATORIAL (also generalized) or SPHYNX_NORMALIZED
+  DT tin;                  // element type of x
+  int ld_x, ld_y;          // leading dimensions (elements)
+  int bp;                  // padded width: 1, 4, 8, 12 or 16
+  int b_true;              // columns counted as algorithmic bytes
+  const void *x;
+  void *y;                 // mode 0: double (F64 input) or float
+  int mode;                // 0 plain, 1 polynomial step
+  void *t_out;             // mode 1: next chain vector, element type tout
+  DT tout;                 // mode 1: F64 (with F64 input), F32 or BF16
+  void *yacc;              // mode 1: double or float accumulator (ld_y)
+  int first;               // mode 1: initialise yacc from t
+  const double *inv;       // mode 1: device array of 1/theta
+  int i_cur;               // mode 1: index of theta_i in inv
+  const int *done;         // device flag: skip the launch when nonzero (may be NULL)
+};
+void spmm(sphynx_graph *g, const SpmmArgs &a);
+
+// ---- dense.cu ---------------------------------------------------------------
+void launch_random_block(cudaStream_t s, DT dt, void *x, int64_t n, int b, int ld, uint64_t seed);
+void launch_piecewise_block(cudaStream_t s, DT dt, void *x, int64_t n, int b, int ld, int lap,
+                            const double *deg);
+void launch_from_f64(cudaStream_t s, DT dt, void *x, const double *src, int64_t n, int b, int ld);
+void launch_to_f64(cudaStream_t s, DT dt, const void *x, double *dst, int64_t n, int b, int ld);
+void launch_zero(cudaStream_t s, void *p, size_t bytes);
+
+struct GramArgs {
+  DT dt;                      // F64 or F32
+  int nblk, ld;               // S = [blk0 | blk1 | blk2], each ld wide
+  int64_t n;
+  const void *s[3];
+  const void *ls[3];
+  const double *bdiag;        // double (F64) -- NULL for B = I
+  const float *bdiagf;        // float copy (F32)
+  double *partials;           // scratch: gram_partials_size() doubles
+  double *ga, *gb;            // M x M outputs (device)
+  const int *done;
+};
+int gram_grid(int64_t n);
+size_t gram_partials_size(int nblk, int ld, int grid);
+void launch_gram(cudaStream_t st, const GramArgs &a, int grid);
+
+struct UpdateArgs {
+  DT dt;
+  int nblk, ld;
+  int64_t n;
+  const void *s[3];          // X, H, P
+  const void *ls[3];         // (unused), LH, LP
+  const void *y;             // M x ld coefficients in dt
+  void *xo, *po, *lpo;       // X' = S Y; P' = [0 H P] Y; LP' = [0 LH LP] Y
+  const int *done;
+};
+void launch_update(cudaStream_t st, const UpdateArgs &a);
+
+struct ResidualArgs {
+  DT dt;
+  int ld;
+  int64_t n;
+  const void *x, *lx;
+  const double *theta;       // device [ld]
+  const double *bdiag;       // B diagonal (double) or NULL
+  const float *bdiagf;
+  const double *jinv;        // Jacobi inverse diagonal (double) or NULL = no scaling
+  const float *jinvf;
+  void *out;                 // R or H = Jacobi(R)
+  double *norm_partials;     // [grid][ld]
+  const int *done;
+};
+int residual_grid(int64_t n);
+void launch_residual(cudaStream_t st, const ResidualArgs &a, int grid);
+
+struct SolverState {         // device-resident LOBPCG bookkeeping
+  double theta[SPHYNX_MAX_NEV];
+  double resnorm[SPHYNX_MAX_NEV];
+  int conv[SPHYNX_MAX_NEV];
+  int pvalid;
+  int done;
+  int iters;
+  int status;
+  int svqb_steps;
+  int nconv;
+  int pad[2];
+};
+void launch_converge(cudaStream_t st, SolverState *state, const double *partials, int grid, int b,
+                     int ld, double tol, double floor_abs, int count_iteration, int maxit);
+
+void launch_signs_coords(cudaStream_t st, DT dt, const void *x, int64_t n, int ld, int b,
+                         void *coords, double *scratch);
+
+// dots and vector ops for the Lanczos process of the polynomial setup
+void launch_lanczos_dots(cudaStream_t st, DT dt, const void *basis, int ldv, int j1,
+                         const void *w, int64_t n, double *partials, int grid);
+void launch_reduce_cols(cudaStream_t st, const double *partials, int grid, int cols, double *out);
+void launch_lanczos_sub(cudaStream_t st, DT dt, const void *basis, int ldv, int j1, void *w,
+                        int64_t n, const double *h, double *norm_partials, int grid);
+void launch_lanczos_next(cudaStream_t st, DT dt, const void *w, void *v, void *basis, int ldv,
+                         int j, int64_t n, const double *beta2);
+void launch_poly_start(cudaStream_t st, DT dt, void *v, int64_t n, uint64_t seed);
+void launch_project_null(cudaStream_t st, DT dt, void *v, int64_t n, int lap, const double *deg,
+                         double *partials, int grid, double *scal);
+void launch_poly_single(cudaStream_t st, DT dt, const void *r, void *h, int64_t n, int ld,
+                        const double *inv, const int *done);
+int vec_grid(int64_t n);
+
+// ---- small.cu ---------------------------------------------------------------
+// M x M Gram matrices; coefficients written as M x ld (ld >= b); without an
+// active mask, column k of S is block k / ld, column k % ld.
+void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, int M, int ld,
+                          int b, double u_work, SolverState *state, double *y64, void *yt, DT dt,
+                          const int *active_override, double *theta_out, int *svqb_out);
+void launch_d2f(cudaStream_t st, const double *src, float *dst, int64_t n);
+void launch_gram_reduce(cudaStream_t st, const double *partials, int nblk, int ld, int grid,
+                        double *ga, double *gb, const int *done);
+void launch_harmonic_ritz(cudaStream_t st, const double *alpha, const double *beta2, int k,
+                          double *roots, double *inv, float *invf, int *err);
+
+// ---- mj.cu ------------------------------------------------------------------
+void run_mj(cudaStream_t st, DT dt, const void *coords, int ldc, int dims, int64_t n,
+            const int64_t *vw, int K, int32_t *part, Counters *ctr);
+size_t mj_scratch_bytes(int64_t n, int K);
+void run_mj_scratch(cudaStream_t st, DT dt, const void *coords, int ldc, int dims, int64_t n,
+                    const int64_t *vw, int K, int32_t *part, Counters *ctr, void *scratch);
+
+// ---- graph.cu ---------------------------------------------------------------
+void eval_partition(sphynx_graph *g, const int32_t *part, int K, double *cut, double *cut2,
+                    double *imb);
+
+}  // namespace sphynx

@@ -1,0 +1,501 @@
+// small.cu -- FP64 small dense algebra on the GPU, one CTA per problem.
+//
+// * Rayleigh-Ritz (Sec. 3.3; Algorithm 1 lines 2 and 7): with G_A = S^T L S
+//   and G_B = S^T B S restricted to the active columns of S and symmetrised,
+//   scale to unit diagonal (D), factor D G_B D = R^T R (Cholesky, the small
+//   half of Cholesky-QR) and take C = R^{-1}; if a pivot falls below
+//   tau = 10 m u_work, use the eigendecomposition D G_B D = U Lambda U^T
+//   instead and keep the directions with lambda > tau lambda_max (SVQB).
+//   Then solve C^T (D G_A D) C w = theta w and return the nev smallest
+//   theta with Y = D C W (each w signed so its largest entry is positive).
+// * Gram partial reduction: the per-CTA partials of the Gram kernel are added
+//   in a fixed order, 8 threads per entry.
+// * Harmonic Ritz values (Sec. 5.2 setup): eigenvalues of
+//   (T^2 + beta_k^2 e_k e_k^T) y = theta T y through T = R^T R, Leja ordered.
+//
+// The symmetric eigensolver is the cyclic Jacobi method with round-robin
+// pairing (Golub and Van Loan, Matrix Computations, Sec. 8.5): m/2 disjoint
+// rotations per round are applied by all threads, rotations are skipped when
+// |a_pq| <= 1e-18 (|a_pp| + |a_qq|), and sweeps stop when none was applied.
+#include "internal.cuh"
+
+#include <cmath>
+
+namespace sphynx {
+
+namespace {
+
+constexpr int kMaxM = 3 * SPHYNX_MAX_NEV;   // 48
+constexpr int kSmallThreads = 256;
+
+// ---- cooperative building blocks (all threads of the CTA call them) --------
+
+// In-place Cholesky of the leading m x m of B (ld): on success the upper
+// triangle holds R with B = R^T R.  Returns the smallest pivot (R_kk^2) or
+// a negative value if a pivot was not positive.
+__device__ double chol_upper(double *B, int ld, int m, double *scratch) {
+  const int tid = threadIdx.x;
+  if (tid == 0) scratch[0] = INFINITY;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (tid == 0) {
+      const double d = B[k * ld + k];
+      if (!(d > 0.0)) {
+        scratch[0] = -1.0;
+      } else {
+        if (d < scratch[0]) scratch[0] = d;
+        B[k * ld + k] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (scratch[0] < 0.0) return -1.0;
+    const double rkk = B[k * ld + k];
+    for (int j = k + 1 + tid; j < m; j += blockDim.x) B[k * ld + j] /= rkk;
+    __syncthreads();
+    const int rem = m - k - 1;
+    for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
+      const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+      if (j >= i) B[i * ld + j] -= B[k * ld + i] * B[k * ld + j];
+    }
+    __syncthreads();
+  }
+  const double mn = scratch[0];
+  __syncthreads();
+  return mn;
+}
+
+// C = R^{-1} for upper-triangular R (leading m x m, ld); C is upper triangular.
+__device__ void tri_inv_upper(const double *R, int ld, int m, double *C, int ldc) {
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) C[(idx / m) * ldc + idx % m] = 0.0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    C[j * ldc + j] = 1.0 / R[j * ld + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= j; ++k) s += R[i * ld + k] * C[k * ldc + j];
+      C[i * ldc + j] = -s / R[i * ld + i];
+    }
+  }
+  __syncthreads();
+}
+
+// Out (ra x cb) = op(A) (ra x ka) * Bm (ka x cb); transA reads A as its transpose.
+__device__ void matmul(const double *A, int lda, bool transA, const double *Bm, int ldb, double *Out,
+                       int ldo, int ra, int ka, int cb) {
+  for (int idx = threadIdx.x; idx < ra * cb; idx += blockDim.x) {
+    const int i = idx / cb, j = idx % cb;
+    double s = 0.0;
+    for (int k = 0; k < ka; ++k) s += (transA ? A[k * lda + i] : A[i * lda + k]) * Bm[k * ldb + j];
+    Out[i * ldo + j] = s;
+  }
+  __syncthreads();
+}
+
+__device__ void symmetrize(double *A, int ld, int m) {
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int i = idx / m, j = idx % m;
+    if (i < j) {
+      const double v = 0.5 * (A[i * ld + j] + A[j * ld + i]);
+      A[i * ld + j] = v;
+      A[j * ld + i] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// Cyclic Jacobi: A (m x m, ld) -> diagonal of eigenvalues, V (ld) eigenvectors
+// in columns.  `pairs` needs 4 * kMaxM doubles, `cnt` one int.
+__device__ void jacobi_eig(double *A, int ld, double *V, int ldv, int m, double *pairs, int *cnt) {
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int i = idx / m, j = idx % m;
+    V[i * ldv + j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (m < 2) return;
+  const int mp = m + (m & 1);
+  const int np = mp / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) *cnt = 0;
+    __syncthreads();
+    for (int r = 0; r < mp - 1; ++r) {
+      if (tid < np) {
+        const int k = tid;
+        const int a0 = k == 0 ? 0 : ((k - 1 + r) % (mp - 1)) + 1;
+        const int k2 = mp - 1 - k;
+        const int a1 = k2 == 0 ? 0 : ((k2 - 1 + r) % (mp - 1)) + 1;
+        const int p = a0 < a1 ? a0 : a1, q = a0 < a1 ? a1 : a0;
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+          if (apq != 0.0 && fabs(apq) > 1e-18 * (fabs(app) + fabs(aqq))) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = tau == 0.0 ? 1.0 : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+            atomicAdd(cnt, 1);
+          }
+        }
+        pairs[4 * k] = c;
+        pairs[4 * k + 1] = s;
+        pairs[4 * k + 2] = p;
+        pairs[4 * k + 3] = q;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int idx = tid; idx < np * m; idx += blockDim.x) {
+        const int k = idx / m, j = idx % m;
+        const double c = pairs[4 * k], s = pairs[4 * k + 1];
+        const int p = static_cast<int>(pairs[4 * k + 2]), q = static_cast<int>(pairs[4 * k + 3]);
+        if (q < m && s != 0.0) {
+          const double ap = A[p * ld + j], aq = A[q * ld + j];
+          A[p * ld + j] = c * ap - s * aq;
+          A[q * ld + j] = s * ap + c * aq;
+        }
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int idx = tid; idx < np * m; idx += blockDim.x) {
+        const int k = idx / m, i = idx % m;
+        const double c = pairs[4 * k], s = pairs[4 * k + 1];
+        const int p = static_cast<int>(pairs[4 * k + 2]), q = static_cast<int>(pairs[4 * k + 3]);
+        if (q < m && s != 0.0) {
+          const double ap = A[i * ld + p], aq = A[i * ld + q];
+          A[i * ld + p] = c * ap - s * aq;
+          A[i * ld + q] = s * ap + c * aq;
+          const double vp = V[i * ldv + p], vq = V[i * ldv + q];
+          V[i * ldv + p] = c * vp - s * vq;
+          V[i * ldv + q] = s * vp + c * vq;
+        }
+      }
+      __syncthreads();
+      if (tid < np) {
+        const int p = static_cast<int>(pairs[4 * tid + 2]), q = static_cast<int>(pairs[4 * tid + 3]);
+        if (q < m && pairs[4 * tid + 1] != 0.0) {
+          A[p * ld + q] = 0.0;
+          A[q * ld + p] = 0.0;
+        }
+      }
+      __syncthreads();
+    }
+    if (*cnt == 0) break;
+    __syncthreads();
+  }
+  __syncthreads();
+}
+
+// order[0..m) = indices of diag(A) sorted ascending (stable on equal values)
+__device__ void sort_diag(const double *A, int ld, int m, int *order) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double di = A[i * ld + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double dj = A[j * ld + j];
+      if (dj < di || (dj == di && j < i)) ++rank;
+    }
+    order[rank] = i;
+  }
+  __syncthreads();
+}
+
+struct RRSmem {
+  double A[kMaxM * kMaxM];   // scaled G_A (active)
+  double B[kMaxM * kMaxM];   // scaled G_B -> R or U
+  double C[kMaxM * kMaxM];   // basis coefficients C (m x m2)
+  double T[kMaxM * kMaxM];   // temp
+  double W[kMaxM * kMaxM];   // projected matrix -> eigenvalues on diagonal
+  double V[kMaxM * kMaxM];   // eigenvectors of W
+  double d[kMaxM];
+  double pairs[4 * kMaxM];
+  double scratch[4];
+  int idx[kMaxM];            // active column -> full index
+  int order[kMaxM];
+  int keep[kMaxM];
+  int m, m2, cnt, fail, svqb;
+};
+
+// One Rayleigh-Ritz step.  ga/gb: full M x M (device).  The active mask is
+// taken from `active` (if not NULL) or derived from the solver state.
+__global__ void __launch_bounds__(kSmallThreads)
+k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, double u_work,
+                SolverState *st, const int *active, double *y64, void *yt, int yt_f32,
+                double *theta_out, int *svqb_out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  RRSmem &S = *reinterpret_cast<RRSmem *>(smraw);
+  const int tid = threadIdx.x;
+  if (st && st->done) return;
+  const int L = kMaxM;  // leading dimension of the shared matrices
+  if (tid == 0) {
+    int m = 0;
+    for (int k = 0; k < M; ++k) {
+      bool a;
+      if (active) {
+        a = active[k] != 0;
+      } else {
+        const int blk = k / ld, c = k % ld;
+        a = c < nev && (blk == 0 || (!st->conv[c] && (blk == 1 || st->pvalid)));
+      }
+      const double dg = gb[k * M + k];
+      if (a && isfinite(dg) && dg > 0.0) S.idx[m++] = k;
+    }
+    S.m = m;
+    S.fail = 0;
+    S.svqb = 0;
+  }
+  __syncthreads();
+  const int m = S.m;
+  for (int i = tid; i < m; i += blockDim.x) S.d[i] = 1.0 / sqrt(gb[S.idx[i] * M + S.idx[i]]);
+  __syncthreads();
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    const int fi = S.idx[i], fj = S.idx[j];
+    const double di = S.d[i], dj = S.d[j];
+    S.A[i * L + j] = 0.5 * (ga[fi * M + fj] + ga[fj * M + fi]) * di * dj;
+    S.B[i * L + j] = 0.5 * (gb[fi * M + fj] + gb[fj * M + fi]) * di * dj;
+  }
+  __syncthreads();
+  const double tau = 10.0 * m * u_work;
+  // keep a copy of the scaled G_B for the SVQB fallback in T
+  for (int e = tid; e < m * m; e += blockDim.x) S.T[(e / m) * L + e % m] = S.B[(e / m) * L + e % m];
+  __syncthreads();
+  const double minpiv = chol_upper(S.B, L, m, S.scratch);
+  int m2 = m;
+  if (minpiv >= tau) {
+    tri_inv_upper(S.B, L, m, S.C, L);
+  } else {
+    // SVQB: eigendecomposition of the scaled G_B (copy in T)
+    if (tid == 0) S.svqb = 1;
+    jacobi_eig(S.T, L, S.V, L, m, S.pairs, &S.cnt);
+    if (tid == 0) {
+      double lmax = 0.0;
+      for (int i = 0; i < m; ++i) lmax = fmax(lmax, S.T[i * L + i]);
+      int c = 0;
+      for (int i = 0; i < m; ++i)
+        if (S.T[i * L + i] > tau * lmax) S.keep[c++] = i;
+      S.m2 = c;
+    }
+    __syncthreads();
+    m2 = S.m2;
+    for (int e = tid; e < m * m2; e += blockDim.x) {
+      const int i = e / m2, j = e % m2;
+      const int kj = S.keep[j];
+      S.C[i * L + j] = S.V[i * L + kj] / sqrt(S.T[kj * L + kj]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) S.m2 = m2;
+  // W = C^T A C
+  matmul(S.A, L, false, S.C, L, S.T, L, m, m, m2);
+  matmul(S.C, L, true, S.T, L, S.W, L, m2, m, m2);
+  symmetrize(S.W, L, m2);
+  jacobi_eig(S.W, L, S.V, L, m2, S.pairs, &S.cnt);
+  sort_diag(S.W, L, m2, S.order);
+  if (tid == 0 && m2 < nev) S.fail = 1;
+  __syncthreads();
+  if (S.fail) {
+    if (tid == 0 && st) {
+      st->done = 1;
+      st->status = SPHYNX_ERR_BREAKDOWN;
+    }
+    if (tid == 0 && svqb_out) *svqb_out = -1;
+    return;
+  }
+  // sign of each selected eigenvector: largest |entry| positive, first on ties
+  if (tid < nev) {
+    const int col = S.order[tid];
+    double best = -1.0;
+    int bi = 0;
+    for (int k = 0; k < m2; ++k) {
+      const double a = fabs(S.V[k * L + col]);
+      if (a > best) { best = a; bi = k; }
+    }
+    S.keep[tid] = S.V[bi * L + col] < 0.0 ? -1 : 1;
+  }
+  __syncthreads();
+  // Y_active = D C W_sel  (m x nev)
+  for (int e = tid; e < m * nev; e += blockDim.x) {
+    const int i = e / nev, c = e % nev;
+    const int col = S.order[c];
+    double s = 0.0;
+    for (int k = 0; k < m2; ++k) s += S.C[i * L + k] * S.V[k * L + col];
+    S.T[i * L + c] = S.d[i] * s * S.keep[c];
+  }
+  __syncthreads();
+  for (int e = tid; e < M * ld; e += blockDim.x) {
+    if (y64) y64[e] = 0.0;
+    if (yt) {
+      if (yt_f32) static_cast<float *>(yt)[e] = 0.f;
+      else static_cast<double *>(yt)[e] = 0.0;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < m * nev; e += blockDim.x) {
+    const int i = e / nev, c = e % nev;
+    const double v = S.T[i * L + c];
+    const int o = S.idx[i] * ld + c;
+    if (y64) y64[o] = v;
+    if (yt) {
+      if (yt_f32) static_cast<float *>(yt)[o] = static_cast<float>(v);
+      else static_cast<double *>(yt)[o] = v;
+    }
+  }
+  if (tid < nev) {
+    const double th = S.W[S.order[tid] * L + S.order[tid]];
+    if (st) st->theta[tid] = th;
+    if (theta_out) theta_out[tid] = th;
+  }
+  if (tid == 0) {
+    if (st) st->svqb_steps += S.svqb;
+    if (svqb_out) *svqb_out = S.svqb;
+  }
+}
+
+// partials [grid][NB*16] -> G_A (M x M) and symmetric G_B
+__global__ void k_gram_reduce(const double *partials, int M, int nbA, int NB, int grid, double *ga,
+                              double *gb, const int *done) {
+  __shared__ double red[32][9];
+  if (done && *done) return;
+  const int lo = threadIdx.x & 7, oi = threadIdx.x >> 3;   // 8 threads per output, 32 outputs
+  const int o = blockIdx.x * 32 + oi;
+  double s = 0.0;
+  if (o < NB * 16)
+    for (int g = lo; g < grid; g += 8) s += partials[static_cast<int64_t>(g) * NB * 16 + o];
+  red[oi][lo] = s;
+  __syncthreads();
+  if (lo == 0 && o < NB * 16) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[oi][k];
+    const int blk = o / 16, q = o % 16, i = q / 4, j = q % 4;
+    const int mb = M / 4;
+    if (blk < nbA) {
+      const int bi = blk / mb, bj = blk % mb;
+      ga[(4 * bi + i) * M + 4 * bj + j] = t;
+    } else {
+      int k = blk - nbA, bi = 0;
+      while (k >= mb - bi) { k -= mb - bi; ++bi; }
+      const int bj = bi + k;
+      const int r = 4 * bi + i, c = 4 * bj + j;
+      if (bi < bj) {
+        gb[r * M + c] = t;
+        gb[c * M + r] = t;
+      } else if (i <= j) {
+        gb[r * M + c] = t;
+        gb[c * M + r] = t;
+      }
+    }
+  }
+}
+
+struct HRSmem {
+  double T[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
+  double Mx[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
+  double C[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
+  double Z[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
+  double V[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
+  double pairs[4 * SPHYNX_MAX_POLY_DEGREE];
+  double scratch[4];
+  double theta[SPHYNX_MAX_POLY_DEGREE];
+  double score[SPHYNX_MAX_POLY_DEGREE];
+  int order[SPHYNX_MAX_POLY_DEGREE];
+  int cnt;
+};
+
+__global__ void __launch_bounds__(kSmallThreads)
+k_harmonic_ritz(const double *alpha, const double *beta2, int k, double *roots, double *inv, float *invf,
+                int *err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  HRSmem &S = *reinterpret_cast<HRSmem *>(smraw);
+  const int L = SPHYNX_MAX_POLY_DEGREE;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int i = e / k, j = e % k;
+    double v = 0.0;
+    if (i == j) v = alpha[i];
+    else if (j == i + 1) v = sqrt(beta2[i]);
+    else if (i == j + 1) v = sqrt(beta2[j]);
+    S.T[i * L + j] = v;
+  }
+  __syncthreads();
+  matmul(S.T, L, false, S.T, L, S.Mx, L, k, k, k);
+  if (tid == 0) S.Mx[(k - 1) * L + (k - 1)] += beta2[k - 1];
+  __syncthreads();
+  const double mp = chol_upper(S.T, L, k, S.scratch);  // T = R^T R
+  if (!(mp > 0.0)) {
+    if (tid == 0) *err = 1;
+    return;
+  }
+  tri_inv_upper(S.T, L, k, S.C, L);
+  matmul(S.Mx, L, false, S.C, L, S.V, L, k, k, k);
+  matmul(S.C, L, true, S.V, L, S.Z, L, k, k, k);
+  symmetrize(S.Z, L, k);
+  jacobi_eig(S.Z, L, S.V, L, k, S.pairs, &S.cnt);
+  sort_diag(S.Z, L, k, S.order);
+  if (tid == 0) {
+    for (int i = 0; i < k; ++i) S.theta[i] = S.Z[S.order[i] * L + S.order[i]];
+    // modified Leja order: largest |theta| first, then maximise the product of
+    // distances to the roots already taken (sum of logs); ties -> lowest index
+    int used[SPHYNX_MAX_POLY_DEGREE];
+    for (int i = 0; i < k; ++i) { used[i] = 0; S.score[i] = 0.0; }
+    int first = 0;
+    for (int i = 1; i < k; ++i)
+      if (fabs(S.theta[i]) > fabs(S.theta[first])) first = i;
+    used[first] = 1;
+    roots[0] = S.theta[first];
+    int last = first;
+    for (int step = 1; step < k; ++step) {
+      int best = -1;
+      for (int i = 0; i < k; ++i) {
+        if (used[i]) continue;
+        const double dd = fabs(S.theta[i] - S.theta[last]);
+        S.score[i] += dd > 0.0 ? log(dd) : -INFINITY;
+        if (best < 0 || S.score[i] > S.score[best]) best = i;
+      }
+      used[best] = 1;
+      roots[step] = S.theta[best];
+      last = best;
+    }
+    int bad = 0;
+    for (int i = 0; i < k; ++i) {
+      if (!(roots[i] > 0.0) || !isfinite(roots[i])) bad = 1;
+      inv[i] = 1.0 / roots[i];
+      invf[i] = static_cast<float>(inv[i]);
+    }
+    inv[k] = 0.0;   // the chain reads inv[i + 1] on its last step
+    invf[k] = 0.f;
+    *err = bad ? 2 : 0;
+  }
+}
+
+}  // namespace
+
+void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, int M, int ld, int b,
+                          double u_work, SolverState *state, double *y64, void *yt, DT dt,
+                          const int *active_override, double *theta_out, int *svqb_out) {
+  if (M > kMaxM || M < 1) fail(SPHYNX_ERR_INVALID_ARG, "Rayleigh-Ritz size %d outside [1, %d]", M, kMaxM);
+  if (b < 1 || b > ld) fail(SPHYNX_ERR_INVALID_ARG, "Rayleigh-Ritz nev %d", b);
+  const size_t sm = sizeof(RRSmem);
+  SPX_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  k_rayleigh_ritz<<<1, kSmallThreads, sm, st>>>(ga, gb, M, ld, b, u_work, state, active_override, y64, yt,
+                                                dt == DT::F32 ? 1 : 0, theta_out, svqb_out);
+  SPX_LAUNCHED();
+}
+
+void launch_gram_reduce(cudaStream_t st, const double *partials, int nblk, int ld, int grid, double *ga,
+                        double *gb, const int *done) {
+  const int M = nblk * ld, mb = M / 4;
+  const int nbA = mb * mb, NB = nbA + mb * (mb + 1) / 2;
+  const int blocks = (NB * 16 + 31) / 32;
+  k_gram_reduce<<<blocks, 256, 0, st>>>(partials, M, nbA, NB, grid, ga, gb, done);
+  SPX_LAUNCHED();
+}
+
+void launch_harmonic_ritz(cudaStream_t st, const double *alpha, const double *beta2, int k, double *roots,
+                          double *inv, float *invf, int *err) {
+  if (k < 1 || k > SPHYNX_MAX_POLY_DEGREE) fail(SPHYNX_ERR_INVALID_ARG, "polynomial degree %d", k);
+  const size_t sm = sizeof(HRSmem);
+  SPX_CUDA(cudaFuncSetAttribute(k_harmonic_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  k_harmonic_ritz<<<1, kSmallThreads, sm, st>>>(alpha, beta2, k, roots, inv, invf, err);
+  SPX_LAUNCHED();
+}
+
+}  // namespace sphynx

@@ -1,0 +1,57 @@
+"""Write tests/golden/*_oracle.json: FP64 oracle results on the full-size
+synthetic workloads, for the GPU tests and the benchmark's CPU baseline.
+
+Calls only oracle/ (and the seeded generators in workloads/).  Usage:
+    python tests/golden/make_oracle_golden.py c2     # 128^3 27-point mesh
+    python tests/golden/make_oracle_golden.py c1     # 64 x 64 5-point mesh
+"""
+
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+import workloads  # noqa: E402
+
+CASES = {
+    "c1": dict(graph=lambda: workloads.grid2d(64, 64), K=4, problem="combinatorial", precond="jacobi",
+               tol=1e-2, seed=1, poly_degree=25, desc="2D 5-point 64x64, combinatorial, Jacobi, K=4, tol 1e-2"),
+    "c2": dict(graph=lambda: workloads.grid3d(128, 128, 128, 27), K=64, problem="generalized", precond="poly",
+               tol=1e-3, seed=2, poly_degree=25,
+               desc="3D 27-point 128^3, generalized, polynomial degree 25, K=64, tol 1e-3"),
+}
+
+
+def run(name: str) -> dict:
+    c = CASES[name]
+    g = c["graph"]()
+    t0 = time.time()
+    r = oracle.partition(g, c["K"], problem=c["problem"], precond=c["precond"], tol=c["tol"], seed=c["seed"],
+                         poly_degree=c["poly_degree"])
+    dt = time.time() - t0
+    out = {
+        "workload": c["desc"], "n": g.n, "nnz": g.nnz, "K": c["K"], "seed": c["seed"],
+        "eigenvalues": [float(v) for v in r.eigenvalues], "resnorm": [float(v) for v in r.resnorm],
+        "iterations": int(r.iterations), "status": r.status, "cut": float(r.cut), "cut_twice": float(r.cut_twice),
+        "imbalance": float(r.imbalance), "poly_roots": [float(v) for v in r.roots],
+        "oracle_seconds": round(dt, 2),
+        "part_weights": [int(v) for v in np.bincount(r.parts, minlength=c["K"])],
+    }
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_oracle.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    return out
+
+
+if __name__ == "__main__":
+    for name in sys.argv[1:] or ["c1", "c2"]:
+        res = run(name)
+        print(name, res["iterations"], res["eigenvalues"], res["cut"], res["oracle_seconds"])

@@ -1,0 +1,177 @@
+"""GPU parity of the dense LOBPCG pieces (Gram products, FP64 Rayleigh-Ritz,
+preconditioners, the eigensolver) against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import dev_block, rel_err, torch_mod
+from oracle.lobpcg import rayleigh_ritz, residual_norms, lobpcg as oracle_lobpcg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("nblk,ld", [(1, 4), (3, 4), (3, 8), (2, 12), (3, 16)])
+@pytest.mark.parametrize("withb", [False, True])
+def test_gram_matches_numpy(dtype, nblk, ld, withb):
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    n = 10007
+    rng = np.random.default_rng(nblk * 100 + ld)
+    s = [rng.standard_normal((n, ld)) for _ in range(nblk)]
+    ls = [rng.standard_normal((n, ld)) for _ in range(nblk)]
+    if dtype == "f32":
+        s = [x.astype(np.float32).astype(np.float64) for x in s]
+        ls = [x.astype(np.float32).astype(np.float64) for x in ls]
+    bd = rng.integers(1, 30, n).astype(np.float64) if withb else None
+    sd = [dev_block(x, ld, dtype) for x in s]
+    lsd = [dev_block(x, ld, dtype) for x in ls]
+    bdd = None if bd is None else torch.from_numpy(bd).cuda()
+    ga, gb = spx.sphynx_gram(spx.DT_F64 if dtype == "f64" else spx.DT_F32, sd, lsd, ld, n, bdd)
+    S = np.concatenate(s, axis=1)
+    LS = np.concatenate(ls, axis=1)
+    ref_a = S.T @ LS
+    ref_b = S.T @ (S if bd is None else bd[:, None] * S)
+    scale_a = np.abs(S).T @ np.abs(LS)
+    scale_b = np.abs(S).T @ np.abs(S if bd is None else bd[:, None] * S)
+    tol = 1e-14 if dtype == "f64" else 2e-6
+    assert np.all(np.abs(ga - ref_a) <= tol * scale_a + 1e-300)
+    assert np.all(np.abs(gb - ref_b) <= tol * scale_b + 1e-300)
+    assert np.array_equal(gb, gb.T)
+
+
+def _rr_case(seed, m, dep=False):
+    rng = np.random.default_rng(seed)
+    n = 300
+    a = np.diag(np.linspace(0.0, 10.0, n))
+    s = rng.standard_normal((n, m))
+    if dep:
+        s[:, -1] = s[:, 0] * 2.0 + 1e-9 * rng.standard_normal(n)
+    return s.T @ a @ s, s.T @ s
+
+
+@pytest.mark.parametrize("m,nev", [(3, 3), (9, 3), (21, 7), (33, 11), (48, 16)])
+def test_rayleigh_ritz_matches_oracle(m, nev):
+    import paper_2105_00578_gb300 as spx
+    ga, gb = _rr_case(m, m)
+    th, y, svqb = spx.sphynx_rayleigh_ritz(ga, gb, np.ones(m), nev, 2.0 ** -53)
+    th_o, y_o, svqb_o = rayleigh_ritz(ga, gb, nev)
+    assert svqb == svqb_o
+    assert np.allclose(th, th_o, rtol=1e-10, atol=1e-12)
+    assert rel_err(y, y_o) < 1e-8
+
+
+def test_rayleigh_ritz_rank_deficient_and_masked():
+    import paper_2105_00578_gb300 as spx
+    ga, gb = _rr_case(7, 12, dep=True)
+    th, y, svqb = spx.sphynx_rayleigh_ritz(ga, gb, np.ones(12), 4, 2.0 ** -53)
+    th_o, y_o, svqb_o = rayleigh_ritz(ga, gb, 4)
+    assert svqb and svqb_o
+    assert np.allclose(th, th_o, rtol=1e-7)
+    act = np.ones(12, dtype=np.int32)
+    act[[2, 5]] = 0
+    th, y, _ = spx.sphynx_rayleigh_ritz(ga, gb, act, 3, 2.0 ** -53)
+    keep = np.nonzero(act)[0]
+    th_o, y_o, _ = rayleigh_ritz(ga[np.ix_(keep, keep)], gb[np.ix_(keep, keep)], 3)
+    assert np.allclose(th, th_o, rtol=1e-7)
+    assert np.all(y[[2, 5]] == 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed_bf16"])
+@pytest.mark.parametrize("lap", ["combinatorial", "normalized", "generalized"])
+def test_poly_setup_and_apply(precision, lap):
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    g = W.largest_component(W.rmat(11, seed=3)) if lap != "combinatorial" else W.grid2d(50, 37)
+    k = 10
+    opt = spx.options(laplacian=lap, precond="poly", poly_degree=k, precision=precision, seed=4)
+    h = spx.sphynx_create(g.row_ptr, g.col, None, None)
+    try:
+        roots = spx.sphynx_precond_setup(h, opt)
+        lmat = O.operator_for(g, lap)
+        ref = O.gmres_poly_roots(g, lap, lambda v: lmat @ v, k, 4)
+        rtol = 1e-8 if precision == "fp64" else 2e-3
+        assert np.allclose(roots, ref, rtol=rtol)
+        rng = np.random.default_rng(1)
+        r = rng.standard_normal((g.n, 5))
+        dtype = "f64" if precision == "fp64" else "f32"
+        rd = dev_block(r, 8, dtype)
+        hd = torch.zeros_like(rd)
+        spx.sphynx_precond_apply(h, opt, rd, hd, 8, 5)
+        torch.cuda.synchronize()
+        rin = rd.double().cpu().numpy()[:, :5]
+        ref_h = O.poly_apply(lambda v: lmat @ v, roots, rin)   # same roots: isolate the apply
+        tol = {"fp64": 1e-10, "fp32": 1e-3, "mixed_bf16": 5e-2}[precision]
+        assert rel_err(hd.double().cpu().numpy()[:, :5], ref_h) < tol
+    finally:
+        spx.sphynx_destroy(h)
+
+
+@pytest.mark.parametrize("lap", ["combinatorial", "generalized", "normalized"])
+def test_jacobi_apply(lap):
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    g = W.random_edge_weights(W.largest_component(W.rmat(10, seed=2)))
+    h = spx.sphynx_create(g.row_ptr, g.col, g.w, None)
+    r = np.random.default_rng(0).standard_normal((g.n, 3))
+    rd = dev_block(r, 4, "f64")
+    hd = torch.zeros_like(rd)
+    spx.sphynx_precond_apply(h, spx.options(laplacian=lap, precond="jacobi"), rd, hd, 4, 3)
+    torch.cuda.synchronize()
+    ref = O.jacobi_diag(g, lap)[:, None] * r
+    assert rel_err(hd.cpu().numpy()[:, :3], ref) < 1e-15
+    spx.sphynx_destroy(h)
+
+
+def _oracle_eig(g, lap, precond, nev, tol, seed, u_work):
+    lmat = O.operator_for(g, lap)
+    bd = O.b_diag_for(g, lap)
+    jd = O.jacobi_diag(g, lap)
+    m = (lambda r: jd[:, None] * r) if precond == "jacobi" else None
+    x0 = O.splitmix64_block(g.n, nev, seed)
+    rho = 2.0 * O.weighted_degree(g).max() if lap == "combinatorial" else 2.0
+    return oracle_lobpcg(lambda v: lmat @ v, bd, m, x0, tol, 3000, rho, u_work), lmat, bd
+
+
+@pytest.mark.parametrize("gname,lap,precond,nev,tol", [
+    ("grid_17x11", "combinatorial", "jacobi", 5, 1e-6),
+    ("grid_64x48", "combinatorial", "jacobi", 3, 1e-2),
+    ("rmat9", "generalized", "jacobi", 4, 1e-4),
+    ("rmat10w", "normalized", "none", 6, 1e-3),
+    ("grid27", "generalized", "jacobi", 7, 1e-3),
+])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_eigensolve_matches_oracle(gname, lap, precond, nev, tol, precision):
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    g = {"grid_17x11": lambda: W.grid2d(17, 11), "grid_64x48": lambda: W.grid2d(64, 48),
+         "rmat9": lambda: W.largest_component(W.rmat(9, seed=11)),
+         "rmat10w": lambda: W.random_edge_weights(W.largest_component(W.rmat(10, seed=12))),
+         "grid27": lambda: W.grid3d(14, 11, 9, 27)}[gname]()
+    u = 2.0 ** -53 if precision == "fp64" else 2.0 ** -24
+    ref, lmat, bd = _oracle_eig(g, lap, precond, nev, tol, 3, 2.0 ** -53)
+    h = spx.sphynx_create(g.row_ptr, g.col, g.w, None)
+    try:
+        ld = (nev + 3) // 4 * 4
+        x = torch.zeros((g.n, ld), dtype=torch.float64 if precision == "fp64" else torch.float32, device="cuda")
+        opt = spx.options(laplacian=lap, precond=precond, precision=precision, tol=tol, seed=3, max_iter=3000)
+        code, theta, res, st = spx.sphynx_eigensolve(h, opt, nev, x, ld)
+        assert code == spx.OK
+        ev_rtol = 1e-6 if precision == "fp64" else 1e-3
+        assert np.allclose(theta[1:], ref.theta[1:], rtol=ev_rtol)
+        assert abs(theta[0]) < 1e-6
+        # the GPU's own residual claim, recomputed by the oracle in FP64 from its vectors
+        xv = x.double().cpu().numpy()[:, :nev]
+        r = lmat @ xv - (xv if bd is None else bd[:, None] * xv) * theta[None, :]
+        res_o = residual_norms(r, bd)
+        floor = 10 * u * (2 * O.weighted_degree(g).max() if lap == "combinatorial" else 2.0)
+        slack = 1.0 if precision == "fp64" else 3.0
+        assert np.all((res_o <= slack * tol * np.abs(theta)) | (res_o <= slack * floor))
+        gbm = xv.T @ (xv if bd is None else bd[:, None] * xv)
+        assert np.allclose(gbm, np.eye(nev), atol=1e-10 if precision == "fp64" else 1e-4)
+        if precision == "fp64":
+            assert abs(st["iterations"] - ref.iterations) <= max(2, ref.iterations // 20)
+    finally:
+        spx.sphynx_destroy(h)

@@ -1,0 +1,129 @@
+"""GPU parity of the fused Laplacian SpMM (Y = L X without forming L) against
+the oracle's explicit FP64 Laplacians (Eqs. 2-3, weighted rule)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import bf16_round, dev_block, rel_err, torch_mod
+
+pytestmark = pytest.mark.gpu
+
+
+def graphs():
+    return {
+        "grid2d": W.grid2d(67, 45),                                   # ragged row tail
+        "grid27": W.grid3d(19, 13, 11, 27),
+        "rmat": W.rmat(12, seed=7),                                   # power law: long rows
+        "rmat_w": W.random_edge_weights(W.rmat(11, seed=9), 0.5, 1.5, 5),
+        "star": W.star_graph(9001),                                   # one row split in 3 chunks
+    }
+
+
+GRAPHS = graphs()
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("lap", ["combinatorial", "normalized"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("ncols", [1, 3, 7, 9, 16])
+def test_spmm_matches_oracle(gname, lap, dtype, ncols):
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    if ncols == 1 and dtype == "bf16":
+        pytest.skip("single-column products are float/double only")
+    g = GRAPHS[gname]
+    h = spx.sphynx_create(g.row_ptr, g.col, g.w, None, g.n, g.nnz, spx.VALIDATE)
+    try:
+        rng = np.random.default_rng(ncols)
+        x = rng.standard_normal((g.n, ncols))
+        ld = 1 if ncols == 1 else (ncols + 3) // 4 * 4
+        xd = dev_block(x, ld, dtype)
+        ydt = torch.float64 if dtype == "f64" else torch.float32
+        y = torch.zeros((g.n, ld), dtype=ydt, device="cuda")
+        dt = {"f64": spx.DT_F64, "f32": spx.DT_F32, "bf16": spx.DT_BF16}[dtype]
+        spx.sphynx_laplacian_apply(h, lap, dt, xd, ld, y, ld, ncols)
+        torch.cuda.synchronize()
+        xin = x if dtype == "f64" else (x.astype(np.float32).astype(np.float64) if dtype == "f32" else bf16_round(x))
+        ref = O.operator_for(g, lap) @ xin
+        got = y.cpu().numpy().astype(np.float64)[:, :ncols]
+        tol = 1e-13 if dtype == "f64" else 2e-6
+        assert rel_err(got, ref) < tol
+        # padding columns stay zero when the input padding is zero
+        if ld > ncols and ncols > 1:
+            assert np.all(y.cpu().numpy()[:, ncols:] == 0)
+    finally:
+        spx.sphynx_destroy(h)
+
+
+def test_degrees_exact():
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    for g in GRAPHS.values():
+        h = spx.sphynx_create(g.row_ptr, g.col, g.w, None)
+        d = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        spx.sphynx_degrees(h, d)
+        torch.cuda.synchronize()
+        ref = O.weighted_degree(g)
+        if g.w is None:
+            assert np.array_equal(d.cpu().numpy(), ref)
+        else:
+            assert np.allclose(d.cpu().numpy(), ref, rtol=1e-15)
+        info = spx.sphynx_get_info(h)
+        assert info["max_degree"] == int(g.degrees().max())
+        assert info["long_rows"] == int(np.sum(g.degrees() > 32))
+        spx.sphynx_destroy(h)
+
+
+def test_full_size_27_point_mesh_sampled_rows():
+    """128^3 27-point mesh (the 2.1M-vertex workload): sampled rows of L_C X
+    recomputed by the oracle row by row."""
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    g = W.grid3d(128, 128, 128, 27)
+    h = spx.sphynx_create(g.row_ptr, g.col, None, None)
+    try:
+        rng = np.random.default_rng(5)
+        for dtype, ld in (("f32", 8), ("f64", 8), ("bf16", 8)):
+            x = rng.standard_normal((g.n, 7))
+            xd = dev_block(x, ld, dtype)
+            y = torch.zeros((g.n, ld), dtype=torch.float64 if dtype == "f64" else torch.float32, device="cuda")
+            spx.sphynx_laplacian_apply(h, "combinatorial", {"f64": 0, "f32": 1, "bf16": 2}[dtype], xd, ld, y, ld, 7)
+            torch.cuda.synchronize()
+            xin = xd.double().cpu().numpy()[:, :7]
+            rows = np.concatenate([np.arange(5), rng.integers(0, g.n, 2000), [g.n - 1]])
+            got = y.cpu().numpy().astype(np.float64)[rows, :7]
+            ref = np.zeros_like(got)
+            for k, i in enumerate(rows):
+                nb = g.col[g.row_ptr[i]:g.row_ptr[i + 1]]
+                ref[k] = len(nb) * xin[i] - xin[nb].sum(axis=0)
+            tol = 1e-13 if dtype == "f64" else 2e-6
+            assert rel_err(got, ref) < tol
+    finally:
+        spx.sphynx_destroy(h)
+
+
+def test_invalid_inputs_are_rejected():
+    import paper_2105_00578_gb300 as spx
+    g = W.grid2d(5, 4)
+    col = g.col.copy()
+    col[3] = g.n + 5                                   # out of range
+    with pytest.raises(spx.SphynxError) as e:
+        spx.sphynx_create(g.row_ptr, col, None, None)
+    assert e.value.code == spx.ERR_INVALID_ARG
+    # drop one direction of an edge: not symmetric
+    rows = g.rows()
+    keep = ~((rows == 0) & (g.col == 1))
+    rp = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=g.n))])
+    with pytest.raises(spx.SphynxError) as e:
+        spx.sphynx_create(rp, g.col[keep], None, None, flags=spx.VALIDATE)
+    assert e.value.code == spx.ERR_NOT_SYMMETRIC
+    # isolated vertex: normalized problem refused
+    g2 = W.symmetrize_edges(4, np.array([0, 1]), np.array([1, 2]))
+    h = spx.sphynx_create(g2.row_ptr, g2.col, None, None)
+    parts = np.zeros(4, dtype=np.int32)
+    with pytest.raises(spx.SphynxError) as e:
+        spx.sphynx_partition(h, 2, spx.options(laplacian="normalized"), parts)
+    assert e.value.code == spx.ERR_ISOLATED
+    spx.sphynx_destroy(h)
