@@ -54,7 +54,8 @@ extern "C" {
 
 /* ---- sphynx_create flags ------------------------------------------------ */
 #define SPHYNX_HOST_PTRS 0u     /* row_ptr/col/weights are host pointers (copied) */
-#define SPHYNX_DEVICE_PTRS 1u   /* they are device pointers (adopted: keep alive until destroy) */
+#define SPHYNX_DEVICE_PTRS 1u   /* they are device pointers (adopted: keep alive until destroy;
+                                   col and edge_w 16-byte aligned, row_ptr and vtx_w 8-byte) */
 #define SPHYNX_VALIDATE 2u      /* check CSR structure and symmetry on the GPU */
 
 /* ---- option enums ------------------------------------------------------- */
@@ -137,7 +138,12 @@ typedef struct {
   int64_t total_vweight;     /* sum of vertex weights                              */
   int64_t long_rows;         /* rows the SpMM routes to the long-row kernel        */
   int32_t weighted;          /* edge weights present                               */
-  int32_t spmm_variant;      /* autotuned short-row schedule (rows per warp)       */
+  int32_t spmm_variant;      /* short-row schedule the autotuner prefers for the
+                                float 8-column product: 0 = CSR staged in shared
+                                memory, 1 = SELL-32 (every product shape is tuned
+                                on its first launch)                               */
+  float tuned_us_csr;        /* the two schedules' times for that product (us)    */
+  float tuned_us_sell;
 } sphynx_graph_info;
 
 /* Fill *opt with the defaults listed in sphynx_options. */
@@ -161,6 +167,12 @@ void sphynx_destroy(sphynx_handle g);
 
 /* Sizes and degree statistics of the graph (host struct). */
 int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info);
+
+/* Pin the short-row SpMM schedule of the handle: 0 = CSR staged in shared
+ * memory, 1 = SELL-32, -1 = time both again and keep the faster (what
+ * sphynx_create does).  Both give the same products up to rounding order.
+ * Errors: INVALID_ARG. */
+int sphynx_set_spmm_variant(sphynx_handle g, int32_t variant);
 
 /* Weighted degrees deg(v_i) (Sec. 3.2: the diagonal of L_C) into a device
  * double[n]. */
@@ -191,8 +203,11 @@ int sphynx_precond_apply(sphynx_handle g, const sphynx_options *opt, const void 
  * LS = [LS_0 | LS_1 | LS_2] are given as nblk (1..3) device n x ld blocks of
  * dtype F32 or F64 (each ld columns wide, 4 | ld, ld <= 16), and B is
  * diag(bdiag) (device double[n]) or the identity (bdiag = NULL).  Outputs
- * are host double[(nblk*ld)^2], row-major, G_B symmetric.  Accumulation:
- * products in the input type, partial sums per CTA in double.
+ * are host double[(nblk*ld)^2], row-major and symmetric: both matrices are
+ * formed from their upper triangles (S^T L S is symmetric when LS = L S).
+ * Accumulation: products in the input type, short sums in the input type,
+ * then a (hi, lo) float pair (float input) or double, per-CTA partials in
+ * double added in a fixed order.
  * Scratch: allocated per call with cudaMallocAsync on `stream`. */
 int sphynx_gram(int32_t dtype, const void *const *s_blocks, const void *const *ls_blocks,
                 int32_t nblk, int32_t ld, int64_t n, const double *bdiag, double *ga_out,

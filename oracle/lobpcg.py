@@ -27,10 +27,11 @@ eigenvector of the projected problem is given the sign that makes its entry
 of largest magnitude positive (first such entry on ties).
 
 Convergence (the paper names the tolerance but not the test): column i has
-converged when ||r_i||_{B^-1} <= tol |theta_i|, or when ||r_i||_{B^-1} is below
-the noise floor 10 u_work rho, rho = 2 for L_N and the generalized problem and
-2 max deg for L_C (a Gershgorin bound); x_i is B-normalised by RR.  The floor
-only ever admits the eigenvalue-zero vector.
+converged when ||r_i||_{B^-1} <= tol |theta_i|, or when both |theta_i| and
+||r_i||_{B^-1} are below the noise floor 10 u_work rho, rho = 2 for L_N and the
+generalized problem and 2 max deg for L_C (a Gershgorin bound); x_i is
+B-normalised by RR.  The floor thus only admits the eigenvalue-zero vector,
+whose relative test can never be met.
 
 Pins (tests/test_oracle_lobpcg.py): closed-form path, cycle and grid spectra,
 dense ``eigh`` on small graphs (eigenvalues and subspace angles), the
@@ -127,7 +128,7 @@ def lobpcg(apply_l, bdiag, apply_m, x0: np.ndarray, tol: float, maxit: int,
 
     def test(r, th):
         res = residual_norms(r, bdiag)
-        return res, (res <= tol * np.abs(th)) | (res <= floor)
+        return res, (res <= tol * np.abs(th)) | ((np.abs(th) <= floor) & (res <= floor))
 
     # lines 1-3
     lx0 = apply_l(x0)

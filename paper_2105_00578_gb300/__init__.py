@@ -62,7 +62,7 @@ class Stats(C.Structure):
 class GraphInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("max_degree", C.c_int64), ("max_wdegree", C.c_double),
                 ("total_vweight", C.c_int64), ("long_rows", C.c_int64), ("weighted", C.c_int32),
-                ("spmm_variant", C.c_int32)]
+                ("spmm_variant", C.c_int32), ("tuned_us_csr", C.c_float), ("tuned_us_sell", C.c_float)]
 
 
 def _load():
@@ -77,6 +77,7 @@ def _load():
         "sphynx_create": (C.c_int, [vp, vp, vp, vp, i64, i64, u32, vp, C.POINTER(vp)]),
         "sphynx_destroy": (None, [vp]),
         "sphynx_get_info": (C.c_int, [vp, C.POINTER(GraphInfo)]),
+        "sphynx_set_spmm_variant": (C.c_int, [vp, i32]),
         "sphynx_degrees": (C.c_int, [vp, vp]),
         "sphynx_laplacian_apply": (C.c_int, [vp, i32, i32, vp, i32, vp, i32, i32]),
         "sphynx_precond_setup": (C.c_int, [vp, C.POINTER(Options), pd]),
@@ -171,10 +172,12 @@ def sphynx_create(row_ptr, col, edge_w=None, vtx_w=None, n=None, nnz=None, flags
     if nnz is None:
         nnz = len(col)
     if not (flags & DEVICE_PTRS):
-        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
-        col = np.ascontiguousarray(col, dtype=np.int32)
-        edge_w = None if edge_w is None else np.ascontiguousarray(edge_w, dtype=np.float32)
-        vtx_w = None if vtx_w is None else np.ascontiguousarray(vtx_w, dtype=np.int64)
+        def host(a, dt):
+            return a if a is None or isinstance(a, int) or hasattr(a, "data_ptr") else np.ascontiguousarray(a, dt)
+        row_ptr = host(row_ptr, np.int64)
+        col = host(col, np.int32)
+        edge_w = host(edge_w, np.float32)
+        vtx_w = host(vtx_w, np.int64)
     h = C.c_void_p()
     check(LIB.sphynx_create(ptr(row_ptr), ptr(col), ptr(edge_w), ptr(vtx_w), int(n), int(nnz), int(flags),
                             _stream(stream), C.byref(h)))
@@ -189,6 +192,10 @@ def sphynx_get_info(h) -> dict:
     info = GraphInfo()
     check(LIB.sphynx_get_info(h, C.byref(info)))
     return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def sphynx_set_spmm_variant(h, variant: int) -> None:
+    check(LIB.sphynx_set_spmm_variant(h, variant))
 
 
 def sphynx_degrees(h, deg_out) -> None:

@@ -30,7 +30,9 @@ int sphynx_gram(int32_t dtype, const void *const *s_blocks, const void *const *l
     double *part = reinterpret_cast<double *>(p);
     double *ga = part + npart;
     double *gb = ga + M * M;
-    float *bf = bdiag ? reinterpret_cast<float *>(gb + M * M) : nullptr;
+    // the float copy of diag(B) starts on a 16-byte boundary (staged copies)
+    float *bf = bdiag ? reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(gb + M * M) + 15) & ~uintptr_t(15))
+                      : nullptr;
     try {
       SPX_CUDA(cudaMemsetAsync(ga, 0, 2 * static_cast<size_t>(M) * M * 8, st));
       if (bdiag && dtype == SPHYNX_DT_F32) launch_d2f(st, bdiag, bf, n);
@@ -78,7 +80,7 @@ int sphynx_rayleigh_ritz(const double *ga, const double *gb, const int32_t *acti
       SPX_CUDA(cudaMemcpyAsync(dgb, gb, mm * 8, cudaMemcpyHostToDevice, st));
       SPX_CUDA(cudaMemcpyAsync(dact, active, static_cast<size_t>(m) * 4, cudaMemcpyHostToDevice, st));
       SPX_CUDA(cudaMemsetAsync(dsv, 0, 16, st));
-      launch_rayleigh_ritz(st, dga, dgb, m, nev, nev, u_work, nullptr, dy, nullptr, DT::F64, dact, dth, dsv);
+      launch_rayleigh_ritz(st, dga, dgb, m, nev, nev, u_work, nullptr, dy, nullptr, DT::F64, dact, dth, dsv, 0);
       SPX_CUDA(cudaMemcpyAsync(y_out, dy, static_cast<size_t>(m) * nev * 8, cudaMemcpyDeviceToHost, st));
       SPX_CUDA(cudaMemcpyAsync(theta_out, dth, static_cast<size_t>(nev) * 8, cudaMemcpyDeviceToHost, st));
       SPX_CUDA(cudaMemcpyAsync(&sv, dsv, 4, cudaMemcpyDeviceToHost, st));

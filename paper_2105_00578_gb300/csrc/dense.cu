@@ -92,159 +92,6 @@ __global__ void k_to_f64(const T *x, double *dst, int64_t n, int b, int ld) {
 }
 
 // ---------------------------------------------------------------------------
-// Gram matrices G_A = S^T (L S), G_B = S^T B S (Algorithm 1 line 7).
-//
-// Output is tiled in 4x4 blocks: all (M/4)^2 blocks of G_A and the upper
-// triangle of G_B.  A CTA owns a slab of rows; its threads form `ngroups`
-// row groups of `tpg` threads, thread t of a group owning output block t.
-// float: products and short sums in float, folded every kFlushRows rows into
-// a float (hi, lo) pair with Knuth's TwoSum (about 48 significant bits),
-// converted to double at the end.  double: plain double FMAs.
-struct GramDev {
-  int nblk, ld, M, nbA, nbB, tpg, ngroups;
-  int64_t n;
-  const void *s[3];
-  const void *ls[3];
-  const void *bdiag;
-  double *partials;
-  const int *done;
-};
-
-constexpr int kGramThreads = 256;
-
-template <typename T> struct GramTile { static constexpr int rows = 64; };
-template <> struct GramTile<double> { static constexpr int rows = 32; };
-
-__device__ inline void two_sum_fold(float &hi, float &lo, float &acc) {
-  const float s = hi + acc;
-  const float bp = s - hi;
-  const float e = (hi - (s - bp)) + (acc - bp);
-  hi = s;
-  lo += e;
-  acc = 0.f;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kGramThreads) k_gram(const GramDev a) {
-  constexpr int TR = GramTile<T>::rows;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (a.done && *a.done) return;
-  const int M = a.M;
-  T *sS = reinterpret_cast<T *>(smem_raw);
-  T *sL = sS + TR * M;
-  T *sB = a.bdiag ? sL + TR * M : sS;
-  const int tid = threadIdx.x;
-  const int grp = tid / a.tpg, t = tid % a.tpg;
-  const int NB = a.nbA + a.nbB;
-  const int mb = M / 4;
-  const bool active = t < NB && grp < a.ngroups;
-  int bi = 0, bj = 0;
-  bool isA = true;
-  if (active) {
-    if (t < a.nbA) {
-      bi = t / mb;
-      bj = t % mb;
-    } else {
-      isA = false;
-      int k = t - a.nbA;
-      bi = 0;
-      while (k >= mb - bi) {
-        k -= mb - bi;
-        ++bi;
-      }
-      bj = bi + k;
-    }
-  }
-  T acc[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = T(0);
-  float hi[16], lo[16];
-  if constexpr (std::is_same<T, float>::value) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
-  }
-  const int64_t ntile = (a.n + TR - 1) / TR;
-  const T *C = isA ? sL : sB;
-  int since_flush = 0;
-  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    const int64_t r0 = tile * TR;
-    __syncthreads();
-    for (int idx = tid; idx < TR * M; idx += kGramThreads) {
-      const int r = idx / M, c = idx - (idx / M) * M;
-      const int blk = c / a.ld, cc = c - blk * a.ld;
-      const int64_t row = r0 + r;
-      T v = T(0), lv = T(0);
-      if (row < a.n) {
-        v = static_cast<const T *>(a.s[blk])[row * a.ld + cc];
-        lv = static_cast<const T *>(a.ls[blk])[row * a.ld + cc];
-      }
-      sS[idx] = v;
-      sL[idx] = lv;
-      if (a.bdiag) sB[idx] = row < a.n ? v * static_cast<const T *>(a.bdiag)[row] : T(0);
-    }
-    __syncthreads();
-    if (active) {
-      for (int r = grp; r < TR; r += a.ngroups) {
-        const T *ar = sS + r * M + 4 * bi;
-        const T *cr = C + r * M + 4 * bj;
-        T av[4], cv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) { av[q] = ar[q]; cv[q] = cr[q]; }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i * 4 + j] += av[i] * cv[j];
-      }
-      if constexpr (std::is_same<T, float>::value) {
-        since_flush += TR / a.ngroups;
-        if (since_flush >= 64) {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) two_sum_fold(hi[q], lo[q], acc[q]);
-          since_flush = 0;
-        }
-      }
-    }
-  }
-  // combine row groups in a fixed order through shared memory (double)
-  __syncthreads();
-  double *red = reinterpret_cast<double *>(smem_raw);  // [ngroups][NB*16]
-  if (active) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      double v;
-      if constexpr (std::is_same<T, float>::value) {
-        float h = hi[q], l = lo[q];
-        two_sum_fold(h, l, acc[q]);
-        v = static_cast<double>(h) + static_cast<double>(l);
-      } else {
-        v = acc[q];
-      }
-      red[grp * NB * 16 + t * 16 + q] = v;
-    }
-  }
-  __syncthreads();
-  for (int o = tid; o < NB * 16; o += kGramThreads) {
-    double s = 0.0;
-    for (int g = 0; g < a.ngroups; ++g) s += red[g * NB * 16 + o];
-    a.partials[static_cast<int64_t>(blockIdx.x) * NB * 16 + o] = s;
-  }
-}
-
-void gram_shape(int nblk, int ld, GramDev &d) {
-  d.nblk = nblk;
-  d.ld = ld;
-  d.M = nblk * ld;
-  const int mb = d.M / 4;
-  d.nbA = mb * mb;
-  d.nbB = mb * (mb + 1) / 2;
-  const int NB = d.nbA + d.nbB;
-  int tpg = 32;
-  while (tpg < NB) tpg *= 2;
-  d.tpg = tpg;
-  d.ngroups = kGramThreads / tpg;
-}
-
-// ---------------------------------------------------------------------------
 // X' = S Y, P' = [0 H P] Y, LP' = [0 LH LP] Y  (Algorithm 1 lines 8 and 12)
 template <typename T, int LD, int NBLK>
 __global__ void __launch_bounds__(256)
@@ -364,7 +211,9 @@ __global__ void k_converge(SolverState *st, const double *partials, int grid, in
       for (int q = 0; q < 16; ++q) tot += part[q][j];
       const double res = sqrt(tot);
       st->resnorm[j] = res;
-      const bool ok = (res <= tol * fabs(st->theta[j])) || (res <= floor_abs);
+      // the floor only admits the eigenvalue-zero vector (|theta| itself below it)
+      const double th = fabs(st->theta[j]);
+      const bool ok = (res <= tol * th) || (th <= floor_abs && res <= floor_abs);
       st->conv[j] = ok ? 1 : 0;
       nconv += ok ? 1 : 0;
     }
@@ -627,48 +476,6 @@ void launch_to_f64(cudaStream_t s, DT dt, const void *x, double *dst, int64_t n,
   const unsigned g = blocks_for(n * b, 256) > 8192 ? 8192 : blocks_for(n * b, 256);
   if (dt == DT::F64) k_to_f64<double><<<g, 256, 0, s>>>(static_cast<const double *>(x), dst, n, b, ld);
   else k_to_f64<float><<<g, 256, 0, s>>>(static_cast<const float *>(x), dst, n, b, ld);
-  SPX_LAUNCHED();
-}
-
-int gram_grid(int64_t n) {
-  int64_t g = (n + 63) / 64;
-  if (g > 2 * kSmCount) g = 2 * kSmCount;
-  if (g < 1) g = 1;
-  return static_cast<int>(g);
-}
-
-size_t gram_partials_size(int nblk, int ld, int grid) {
-  GramDev d{};
-  gram_shape(nblk, ld, d);
-  return static_cast<size_t>(grid) * (d.nbA + d.nbB) * 16;
-}
-
-void launch_gram(cudaStream_t st, const GramArgs &a, int grid) {
-  GramDev d{};
-  gram_shape(a.nblk, a.ld, d);
-  d.n = a.n;
-  for (int k = 0; k < 3; ++k) {
-    d.s[k] = k < a.nblk ? a.s[k] : nullptr;
-    d.ls[k] = k < a.nblk ? a.ls[k] : nullptr;
-  }
-  d.partials = a.partials;
-  d.done = a.done;
-  const int NB = d.nbA + d.nbB;
-  if (a.dt == DT::F64) {
-    d.bdiag = a.bdiag;
-    const size_t tile = static_cast<size_t>(GramTile<double>::rows) * d.M * sizeof(double) * (a.bdiag ? 3 : 2);
-    const size_t red = static_cast<size_t>(d.ngroups) * NB * 16 * sizeof(double);
-    const size_t sm = tile > red ? tile : red;
-    SPX_CUDA(cudaFuncSetAttribute(k_gram<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-    k_gram<double><<<grid, kGramThreads, sm, st>>>(d);
-  } else {
-    d.bdiag = a.bdiagf;
-    const size_t tile = static_cast<size_t>(GramTile<float>::rows) * d.M * sizeof(float) * (a.bdiagf ? 3 : 2);
-    const size_t red = static_cast<size_t>(d.ngroups) * NB * 16 * sizeof(double);
-    const size_t sm = tile > red ? tile : red;
-    SPX_CUDA(cudaFuncSetAttribute(k_gram<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-    k_gram<float><<<grid, kGramThreads, sm, st>>>(d);
-  }
   SPX_LAUNCHED();
 }
 

@@ -164,6 +164,17 @@ __global__ void k_degrees(const int64_t *rp, const float *w, const int64_t *vw, 
       tvw += 1;
     }
   }
+  // one global atomic per warp and statistic
+  for (int off = 16; off > 0; off >>= 1) {
+    mdeg = max(mdeg, __shfl_down_sync(0xffffffffu, mdeg, off));
+    mw = max(mw, __shfl_down_sync(0xffffffffu, mw, off));
+    iso += __shfl_down_sync(0xffffffffu, iso, off);
+    tvw += __shfl_down_sync(0xffffffffu, tvw, off);
+    mine = min(mine, __shfl_down_sync(0xffffffffu, mine, off));
+    maxe = max(maxe, __shfl_down_sync(0xffffffffu, maxe, off));
+    bad |= __shfl_down_sync(0xffffffffu, bad, off);
+  }
+  if ((threadIdx.x & 31) != 0) return;
   atomicMax(&gs->max_deg, mdeg);
   atomicMax(&gs->max_wdeg_bits, mw);
   if (iso) atomicAdd(&gs->isolated, iso);
@@ -213,6 +224,35 @@ k_eval(const int64_t *rp, const int32_t *col, const float *w, const int64_t *vw,
   }
 }
 
+// SELL-32 layout of the short rows: per-row degree (0xFF marks a long row)
+// and, per 32-row slice, the largest short degree
+__global__ void k_sell_deg(const int64_t *rp, int64_t n, uint8_t *sdeg, int *smax) {
+  const int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  int d = 0, sd = 0xFF;
+  if (row < n) {
+    const int64_t dd = rp[row + 1] - rp[row];
+    d = dd > (1 << 30) ? (1 << 30) : static_cast<int>(dd);
+    sd = d > kShortDeg ? 0xFF : d;
+    sdeg[row] = static_cast<uint8_t>(sd);
+  }
+  int m = sd == 0xFF ? 0 : d;
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0 && row < n) smax[row >> 5] = m;
+}
+
+__global__ void k_sell_fill(const int64_t *rp, const int32_t *col, const float *w, int64_t n, const uint8_t *sdeg,
+                            const int64_t *sptr, int32_t *scol, float *sw) {
+  const int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (row >= n) return;
+  const int d = sdeg[row];
+  if (d == 0xFF) return;
+  const int64_t b = sptr[row >> 5] + (row & 31), src = rp[row];
+  for (int t = 0; t < d; ++t) {
+    scol[b + 32 * t] = col[src + t];
+    if (w) sw[b + 32 * t] = w[src + t];
+  }
+}
+
 int grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g > 8 * kSmCount) g = 8 * kSmCount;
@@ -259,6 +299,59 @@ void build_plan(sphynx_graph *g, const int64_t *host_rowptr) {
   SPX_CUDA(cudaMemcpyAsync(p.split.p, split.data(), split.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
   p.partials.alloc(static_cast<size_t>(p.n_items) * 16 * sizeof(double));
   SPX_CUDA(cudaStreamSynchronize(g->stream));
+}
+
+void build_sell(sphynx_graph *g) {
+  SpmmPlan &p = g->plan;
+  const int64_t n = g->n, slices = (n + 31) / 32;
+  p.sell_deg.alloc(static_cast<size_t>(n));
+  DevBuf smax;
+  smax.alloc(static_cast<size_t>(slices) * sizeof(int));
+  const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
+  k_sell_deg<<<blocks, 256, 0, g->stream>>>(g->rowptr, n, p.sell_deg.as<uint8_t>(), smax.as<int>());
+  SPX_LAUNCHED();
+  std::vector<int> hmax(static_cast<size_t>(slices));
+  SPX_CUDA(cudaMemcpyAsync(hmax.data(), smax.p, slices * sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  SPX_CUDA(cudaStreamSynchronize(g->stream));
+  std::vector<int64_t> hptr(static_cast<size_t>(slices) + 1, 0);
+  for (int64_t s = 0; s < slices; ++s) hptr[s + 1] = hptr[s] + 32 * static_cast<int64_t>(hmax[s]);
+  p.sell_entries = hptr[slices];
+  p.sell_ptr.alloc(hptr.size() * sizeof(int64_t));
+  SPX_CUDA(cudaMemcpyAsync(p.sell_ptr.p, hptr.data(), hptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           g->stream));
+  p.sell_col.alloc(static_cast<size_t>(p.sell_entries > 0 ? p.sell_entries : 1) * sizeof(int32_t));
+  if (g->weighted) p.sell_w.alloc(static_cast<size_t>(p.sell_entries > 0 ? p.sell_entries : 1) * sizeof(float));
+  k_sell_fill<<<blocks, 256, 0, g->stream>>>(g->rowptr, g->col, g->w, n, p.sell_deg.as<uint8_t>(),
+                                             p.sell_ptr.as<int64_t>(), p.sell_col.as<int32_t>(), p.sell_w.as<float>());
+  SPX_LAUNCHED();
+  SPX_CUDA(cudaStreamSynchronize(g->stream));
+}
+
+// The SpMM tunes every product shape (input type, width, mode, Laplacian)
+// the first time it is launched; at create the float 8-column product is
+// tuned so that sphynx_get_info can report the graph's preference.
+void autotune_spmm(sphynx_graph *g) {
+  const int64_t n = g->n;
+  const int ld = 8;
+  DevBuf x, y;
+  x.alloc(static_cast<size_t>(n) * ld * sizeof(float));
+  y.alloc(static_cast<size_t>(n) * ld * sizeof(float));
+  SPX_CUDA(cudaMemsetAsync(x.p, 0, static_cast<size_t>(n) * ld * sizeof(float), g->stream));
+  SpmmArgs a{};
+  a.lap = SPHYNX_COMBINATORIAL;
+  a.tin = DT::F32;
+  a.ld_x = ld;
+  a.ld_y = ld;
+  a.bp = ld;
+  a.b_true = ld;
+  a.x = x.p;
+  a.y = y.p;
+  spmm(g, a);
+  SPX_CUDA(cudaStreamSynchronize(g->stream));
+  std::vector<cudaEvent_t> pool;
+  pool.swap(g->ctr.ev_pool);
+  g->ctr = Counters{};
+  g->ctr.ev_pool.swap(pool);
 }
 
 }  // namespace
@@ -352,6 +445,10 @@ int sphynx_create(const int64_t *row_ptr, const int32_t *col, const float *edge_
     g->weighted = edge_w != nullptr;
     g->has_vw = vtx_w != nullptr;
     if (dev) {
+      // the SpMM stages column indices and weights with 16-byte loads
+      if (reinterpret_cast<uintptr_t>(col) % 16 || reinterpret_cast<uintptr_t>(edge_w) % 16 ||
+          reinterpret_cast<uintptr_t>(row_ptr) % 8 || reinterpret_cast<uintptr_t>(vtx_w) % 8)
+        fail(SPHYNX_ERR_INVALID_ARG, "adopted device arrays must be 16-byte (col, weights) / 8-byte aligned");
       g->rowptr = row_ptr;
       g->col = col;
       g->w = edge_w;
@@ -428,6 +525,8 @@ int sphynx_create(const int64_t *row_ptr, const int32_t *col, const float *edge_
       g->wexact = top < 9.0e18;
     }
     build_plan(g.get(), dev ? nullptr : row_ptr);
+    build_sell(g.get());
+    autotune_spmm(g.get());
     *out = g.release();
     return SPHYNX_OK;
   });
@@ -452,7 +551,25 @@ int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info) {
     info->total_vweight = g->total_vw;
     info->long_rows = g->plan.n_long;
     info->weighted = g->weighted ? 1 : 0;
-    info->spmm_variant = g->plan.rows_per_warp;
+    info->spmm_variant = g->plan.tuned_us[kSell32] < g->plan.tuned_us[kCsrStaged] ? kSell32 : kCsrStaged;
+    info->tuned_us_csr = g->plan.tuned_us[kCsrStaged];
+    info->tuned_us_sell = g->plan.tuned_us[kSell32];
+    return SPHYNX_OK;
+  });
+}
+
+int sphynx_set_spmm_variant(sphynx_handle g, int32_t variant) {
+  return guarded([&]() -> int {
+    if (!g) fail(SPHYNX_ERR_INVALID_ARG, "NULL handle");
+    if (variant == -1) {
+      g->plan.forced = -1;
+      g->plan.tuned.clear();
+      autotune_spmm(g);
+    } else if (variant == kCsrStaged || variant == kSell32) {
+      g->plan.forced = variant;
+    } else {
+      fail(SPHYNX_ERR_INVALID_ARG, "variant %d", variant);
+    }
     return SPHYNX_OK;
   });
 }

@@ -76,14 +76,37 @@ constexpr int kShortDeg = 32;        // rows with more neighbours use the long-r
 constexpr int kLongChunk = 4096;     // entries per long-row work item
 constexpr int kSmCount = 152;
 
+// Short-row schedules the autotuner chooses between.
+enum SpmmVariant : int {
+  kCsrStaged = 0,   // CSR: a warp stages its 32 rows' columns in shared memory
+  kSell32 = 1,      // SELL-32: columns stored slice-major, read straight from global memory
+};
+
+struct SpmmTuning {
+  int variant;
+  float us[2];                       // measured time of each schedule
+};
+
 struct SpmmPlan {
-  int rows_per_warp = 32;            // short-row schedule
+  int variant = kCsrStaged;          // schedule of the launch being issued
+  int forced = -1;                   // >= 0: every product uses this schedule
+  float tuned_us[2] = {0.f, 0.f};    // timings of the last tuned product shape
+  // autotuner record per product shape (input type, width, mode, Laplacian,
+  // output type): filled the first time a shape is launched
+  std::map<int, SpmmTuning> tuned;
+  DevBuf tune_scratch;
   int64_t n_long = 0;                // rows with degree > kShortDeg
   int64_t n_items = 0;               // long-row work items
-  int64_t n_split = 0;               // rows cut into more than one item
-  DevBuf items;                      // int64 [n_items][4]: row, begin, end, slot(-1 = direct)
-  DevBuf split;                      // int64 [n_split][3]: row, first slot, slot count
-  DevBuf partials;                   // scratch for split rows, sized per call
+  DevBuf items;                      // int64 [n_items][4]: row, begin, end, slot
+  DevBuf split;                      // int64 [n_long][3]: row, first slot, slot count
+  DevBuf partials;                   // per-item partial rows (n_items x 16 doubles)
+  // SELL-32 copy of the short rows: slice s (rows 32s..32s+31) holds entry t
+  // of its lane-th row at sell_col[sell_ptr[s] + 32 t + lane]
+  int64_t sell_entries = 0;
+  DevBuf sell_ptr;                   // int64 [n_slices + 1]
+  DevBuf sell_col;                   // int32 [sell_entries]
+  DevBuf sell_w;                     // float [sell_entries] (weighted graphs)
+  DevBuf sell_deg;                   // uint8 [n]: degree, or 0xFF for a long row
 };
 
 // Everything the iteration kernels need to apply L without forming it.
@@ -165,6 +188,7 @@ struct SpmmArgs {
   void *yacc;              // mode 1: double or float accumulator (ld_y)
   int first;               // mode 1: initialise yacc from t
   const double *inv;       // mode 1: device array of 1/theta
+  const float *invf;       // mode 1: its float copy
   int i_cur;               // mode 1: index of theta_i in inv
   const int *done;         // device flag: skip the launch when nonzero (may be NULL)
 };
@@ -258,10 +282,12 @@ int vec_grid(int64_t n);
 
 // ---- small.cu ---------------------------------------------------------------
 // M x M Gram matrices; coefficients written as M x ld (ld >= b); without an
-// active mask, column k of S is block k / ld, column k % ld.
+// active mask, column k of S is block k / ld, column k % ld.  mixed: the
+// Jacobi rotations run in float and every Ritz value is the double Rayleigh
+// quotient of its vector (for blocks stored in float).
 void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, int M, int ld,
                           int b, double u_work, SolverState *state, double *y64, void *yt, DT dt,
-                          const int *active_override, double *theta_out, int *svqb_out);
+                          const int *active_override, double *theta_out, int *svqb_out, int mixed);
 void launch_d2f(cudaStream_t st, const double *src, float *dst, int64_t n);
 void launch_gram_reduce(cudaStream_t st, const double *partials, int nblk, int ld, int grid,
                         double *ga, double *gb, const int *done);

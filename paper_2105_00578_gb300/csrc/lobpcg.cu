@@ -146,6 +146,7 @@ void poly_apply(sphynx_graph *g, int precision, const void *r, void *h, int ld, 
     a.yacc = h;
     a.first = i == 0 ? 1 : 0;
     a.inv = g->poly_inv.as<double>();
+    a.invf = g->poly_invf.as<float>();
     a.i_cur = i;
     a.done = done;
     spmm(g, a);
@@ -226,7 +227,8 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   GramArgs ga1{dt, 1, ld, n, {X[0], nullptr, nullptr}, {LX[0], nullptr, nullptr}, bd, bdf, gpart, ga, gb, done};
   launch_gram(st, ga1, ggrid);
   launch_gram_reduce(st, gpart, 1, ld, ggrid, ga, gb, done);
-  launch_rayleigh_ritz(st, ga, gb, ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr);
+  launch_rayleigh_ritz(st, ga, gb, ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr,
+                       o->precision != SPHYNX_FP64);
   UpdateArgs up1{dt, 1, ld, n, {X[0], nullptr, nullptr}, {nullptr, nullptr, nullptr}, yt, X[1], nullptr, nullptr, done};
   launch_update(st, up1);
   plain_spmm(g, lap, dt, X[1], LX[1], ld, b, done);
@@ -247,7 +249,8 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
     GramArgs g3{dt, 3, ld, n, {X[cur], H, P[cur]}, {LX[cur], LH, LP[cur]}, bd, bdf, gpart, ga, gb, done};
     launch_gram(st, g3, ggrid);                                                        // line 7
     launch_gram_reduce(st, gpart, 3, ld, ggrid, ga, gb, done);
-    launch_rayleigh_ritz(st, ga, gb, 3 * ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr);
+    launch_rayleigh_ritz(st, ga, gb, 3 * ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr,
+                       o->precision != SPHYNX_FP64);
     UpdateArgs u3{dt, 3, ld, n, {X[cur], H, P[cur]}, {nullptr, LH, LP[cur]}, yt, X[nx], P[nx], LP[nx], done};
     launch_update(st, u3);                                                             // lines 8, 12
     plain_spmm(g, lap, dt, X[nx], LX[nx], ld, b, done);                                 // line 9

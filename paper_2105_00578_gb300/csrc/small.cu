@@ -15,8 +15,9 @@
 //
 // The symmetric eigensolver is the cyclic Jacobi method with round-robin
 // pairing (Golub and Van Loan, Matrix Computations, Sec. 8.5): m/2 disjoint
-// rotations per round are applied by all threads, rotations are skipped when
-// |a_pq| <= 1e-18 (|a_pp| + |a_qq|), and sweeps stop when none was applied.
+// rotations per round are applied by all threads at once (one 2 x 2 block of
+// J^T A J per thread), rotations are skipped when
+// |a_pq| <= 1e-15 (|a_pp| + |a_qq|), and sweeps stop when none was applied.
 #include "internal.cuh"
 
 #include <cmath>
@@ -103,94 +104,116 @@ __device__ void symmetrize(double *A, int ld, int m) {
   __syncthreads();
 }
 
+__device__ __forceinline__ double inv_sqrt(double v) { return rsqrt(v); }
+__device__ __forceinline__ float inv_sqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double sqrt_t(double v) { return sqrt(v); }
+__device__ __forceinline__ float sqrt_t(float v) { return sqrtf(v); }
+__device__ __forceinline__ double abs_t(double v) { return fabs(v); }
+__device__ __forceinline__ float abs_t(float v) { return fabsf(v); }
+
 // Cyclic Jacobi: A (m x m, ld) -> diagonal of eigenvalues, V (ld) eigenvectors
-// in columns.  `pairs` needs 4 * kMaxM doubles, `cnt` one int.
-__device__ void jacobi_eig(double *A, int ld, double *V, int ldv, int m, double *pairs, int *cnt) {
+// in columns, in double or float.  `pairs` needs 4 * kMaxM entries, `cnt`
+// three ints.  A rotation is skipped below rel * (|a_pp| + |a_qq|), rel a few
+// units of the type's rounding.
+template <typename T>
+__device__ void jacobi_eig(T *A, int ld, T *V, int ldv, int m, T *pairs, int *cnt) {
+  const T rel = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
   const int tid = threadIdx.x;
   for (int idx = tid; idx < m * m; idx += blockDim.x) {
     const int i = idx / m, j = idx % m;
-    V[i * ldv + j] = i == j ? 1.0 : 0.0;
+    V[i * ldv + j] = i == j ? T(1) : T(0);
   }
   __syncthreads();
   if (m < 2) return;
   const int mp = m + (m & 1);
   const int np = mp / 2;
+  // cnt[0]: rotations this sweep; cnt[1 + (r & 1)]: rotations of round r.
+  // Each counter is reset only after a barrier that follows its last read.
   for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) *cnt = 0;
+    __syncthreads();
+    if (tid == 0) {
+      cnt[0] = 0;
+      cnt[1] = 0;
+      cnt[2] = 0;
+    }
     __syncthreads();
     for (int r = 0; r < mp - 1; ++r) {
+      int *rc = &cnt[1 + (r & 1)];
       if (tid < np) {
         const int k = tid;
         const int a0 = k == 0 ? 0 : ((k - 1 + r) % (mp - 1)) + 1;
         const int k2 = mp - 1 - k;
         const int a1 = k2 == 0 ? 0 : ((k2 - 1 + r) % (mp - 1)) + 1;
         const int p = a0 < a1 ? a0 : a1, q = a0 < a1 ? a1 : a0;
-        double c = 1.0, s = 0.0;
+        T c = T(1), s = T(0);
         if (q < m) {
-          const double app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
-          if (apq != 0.0 && fabs(apq) > 1e-18 * (fabs(app) + fabs(aqq))) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = tau == 0.0 ? 1.0 : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+          const T app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+          if (apq != T(0) && abs_t(apq) > rel * (abs_t(app) + abs_t(aqq))) {
+            const T tau = (aqq - app) / (T(2) * apq);
+            const T t = tau == T(0) ? T(1) : (tau > T(0) ? T(1) : T(-1)) / (abs_t(tau) + sqrt_t(T(1) + tau * tau));
+            c = inv_sqrt(T(1) + t * t);
             s = t * c;
-            atomicAdd(cnt, 1);
+            atomicAdd(rc, 1);
           }
         }
         pairs[4 * k] = c;
         pairs[4 * k + 1] = s;
-        pairs[4 * k + 2] = p;
-        pairs[4 * k + 3] = q;
+        pairs[4 * k + 2] = static_cast<T>(p);
+        pairs[4 * k + 3] = static_cast<T>(q);
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int idx = tid; idx < np * m; idx += blockDim.x) {
-        const int k = idx / m, j = idx % m;
-        const double c = pairs[4 * k], s = pairs[4 * k + 1];
-        const int p = static_cast<int>(pairs[4 * k + 2]), q = static_cast<int>(pairs[4 * k + 3]);
-        if (q < m && s != 0.0) {
-          const double ap = A[p * ld + j], aq = A[q * ld + j];
-          A[p * ld + j] = c * ap - s * aq;
-          A[q * ld + j] = s * ap + c * aq;
+      const int rot = *rc;                              // same value in every thread
+      if (tid == 0) cnt[1 + ((r + 1) & 1)] = 0;         // next round's counter, last read a round ago
+      // A <- J^T A J one 2 x 2 block per pair of rotation pairs (the pairs are
+      // disjoint, so the blocks are too), and V <- V J
+      for (int idx = rot ? tid : np * np + m * np; idx < np * np + m * np; idx += blockDim.x) {
+        if (idx < np * np) {
+          const int k = idx / np, l = idx - (idx / np) * np;
+          const T ck = pairs[4 * k], sk = pairs[4 * k + 1];
+          const T cl = pairs[4 * l], sl = pairs[4 * l + 1];
+          if (sk == T(0) && sl == T(0)) continue;
+          const int pk = static_cast<int>(pairs[4 * k + 2]), qk = static_cast<int>(pairs[4 * k + 3]);
+          const int pl = static_cast<int>(pairs[4 * l + 2]), ql = static_cast<int>(pairs[4 * l + 3]);
+          const bool hk = qk < m, hl = ql < m;
+          const T a = A[pk * ld + pl];
+          const T b = hl ? A[pk * ld + ql] : T(0);
+          const T c = hk ? A[qk * ld + pl] : T(0);
+          const T d = (hk && hl) ? A[qk * ld + ql] : T(0);
+          // rows (J_k^T), then columns (J_l)
+          const T r0a = ck * a - sk * c, r0b = ck * b - sk * d;
+          const T r1a = sk * a + ck * c, r1b = sk * b + ck * d;
+          A[pk * ld + pl] = cl * r0a - sl * r0b;
+          if (hl) A[pk * ld + ql] = (k == l) ? T(0) : sl * r0a + cl * r0b;
+          if (hk) A[qk * ld + pl] = (k == l) ? T(0) : cl * r1a - sl * r1b;
+          if (hk && hl) A[qk * ld + ql] = sl * r1a + cl * r1b;
+        } else {
+          const int it = idx - np * np;
+          const int i = it / np, l = it - (it / np) * np;
+          const T cl = pairs[4 * l], sl = pairs[4 * l + 1];
+          const int pl = static_cast<int>(pairs[4 * l + 2]), ql = static_cast<int>(pairs[4 * l + 3]);
+          if (sl == T(0) || ql >= m) continue;
+          const T vp = V[i * ldv + pl], vq = V[i * ldv + ql];
+          V[i * ldv + pl] = cl * vp - sl * vq;
+          V[i * ldv + ql] = sl * vp + cl * vq;
         }
       }
-      __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int idx = tid; idx < np * m; idx += blockDim.x) {
-        const int k = idx / m, i = idx % m;
-        const double c = pairs[4 * k], s = pairs[4 * k + 1];
-        const int p = static_cast<int>(pairs[4 * k + 2]), q = static_cast<int>(pairs[4 * k + 3]);
-        if (q < m && s != 0.0) {
-          const double ap = A[i * ld + p], aq = A[i * ld + q];
-          A[i * ld + p] = c * ap - s * aq;
-          A[i * ld + q] = s * ap + c * aq;
-          const double vp = V[i * ldv + p], vq = V[i * ldv + q];
-          V[i * ldv + p] = c * vp - s * vq;
-          V[i * ldv + q] = s * vp + c * vq;
-        }
-      }
-      __syncthreads();
-      if (tid < np) {
-        const int p = static_cast<int>(pairs[4 * tid + 2]), q = static_cast<int>(pairs[4 * tid + 3]);
-        if (q < m && pairs[4 * tid + 1] != 0.0) {
-          A[p * ld + q] = 0.0;
-          A[q * ld + p] = 0.0;
-        }
-      }
+      if (tid == 0) cnt[0] += rot;
       __syncthreads();
     }
-    if (*cnt == 0) break;
     __syncthreads();
+    if (cnt[0] == 0) break;   // read by all threads between two barriers: uniform
   }
   __syncthreads();
 }
 
 // order[0..m) = indices of diag(A) sorted ascending (stable on equal values)
-__device__ void sort_diag(const double *A, int ld, int m, int *order) {
+template <typename T>
+__device__ void sort_diag(const T *A, int ld, int m, int *order) {
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double di = A[i * ld + i];
+    const T di = A[i * ld + i];
     int rank = 0;
     for (int j = 0; j < m; ++j) {
-      const double dj = A[j * ld + j];
+      const T dj = A[j * ld + j];
       if (dj < di || (dj == di && j < i)) ++rank;
     }
     order[rank] = i;
@@ -205,21 +228,47 @@ struct RRSmem {
   double T[kMaxM * kMaxM];   // temp
   double W[kMaxM * kMaxM];   // projected matrix -> eigenvalues on diagonal
   double V[kMaxM * kMaxM];   // eigenvectors of W
+  double Bh[kMaxM * kMaxM];  // scaled G_B, kept for the Rayleigh quotients
+  float A32[kMaxM * kMaxM];  // float copies for the mixed-precision solve
+  float V32[kMaxM * kMaxM];
+  float pairs32[4 * kMaxM];
   double d[kMaxM];
   double pairs[4 * kMaxM];
+  double qa[SPHYNX_MAX_NEV], qb[SPHYNX_MAX_NEV];
   double scratch[4];
   int idx[kMaxM];            // active column -> full index
   int order[kMaxM];
   int keep[kMaxM];
-  int m, m2, cnt, fail, svqb;
+  int sel[SPHYNX_MAX_NEV];
+  int m, m2, cnt[3], fail, svqb;
 };
+
+// Symmetric eigendecomposition of the leading m x m of A (ld kMaxM) into
+// its diagonal and V: in double, or (mixed) with the rotations in float.
+__device__ void eig_sym(RRSmem &S, double *A, double *V, int m, bool mixed) {
+  const int L = kMaxM;
+  if (!mixed) {
+    jacobi_eig<double>(A, L, V, L, m, S.pairs, S.cnt);
+    return;
+  }
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x)
+    S.A32[(e / m) * L + e % m] = static_cast<float>(A[(e / m) * L + e % m]);
+  __syncthreads();
+  jacobi_eig<float>(S.A32, L, S.V32, L, m, S.pairs32, S.cnt);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    V[i * L + j] = static_cast<double>(S.V32[i * L + j]);
+    A[i * L + j] = i == j ? static_cast<double>(S.A32[i * L + j]) : 0.0;
+  }
+  __syncthreads();
+}
 
 // One Rayleigh-Ritz step.  ga/gb: full M x M (device).  The active mask is
 // taken from `active` (if not NULL) or derived from the solver state.
 __global__ void __launch_bounds__(kSmallThreads)
 k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, double u_work,
                 SolverState *st, const int *active, double *y64, void *yt, int yt_f32,
-                double *theta_out, int *svqb_out) {
+                double *theta_out, int *svqb_out, int mixed) {
   extern __shared__ __align__(16) unsigned char smraw[];
   RRSmem &S = *reinterpret_cast<RRSmem *>(smraw);
   const int tid = threadIdx.x;
@@ -255,8 +304,12 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
   }
   __syncthreads();
   const double tau = 10.0 * m * u_work;
-  // keep a copy of the scaled G_B for the SVQB fallback in T
-  for (int e = tid; e < m * m; e += blockDim.x) S.T[(e / m) * L + e % m] = S.B[(e / m) * L + e % m];
+  // keep copies of the scaled G_B: for the SVQB fallback (T) and the final
+  // Rayleigh quotients (Bh)
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    S.T[(e / m) * L + e % m] = S.B[(e / m) * L + e % m];
+    S.Bh[(e / m) * L + e % m] = S.B[(e / m) * L + e % m];
+  }
   __syncthreads();
   const double minpiv = chol_upper(S.B, L, m, S.scratch);
   int m2 = m;
@@ -265,7 +318,7 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
   } else {
     // SVQB: eigendecomposition of the scaled G_B (copy in T)
     if (tid == 0) S.svqb = 1;
-    jacobi_eig(S.T, L, S.V, L, m, S.pairs, &S.cnt);
+    eig_sym(S, S.T, S.V, m, mixed != 0);
     if (tid == 0) {
       double lmax = 0.0;
       for (int i = 0; i < m; ++i) lmax = fmax(lmax, S.T[i * L + i]);
@@ -288,7 +341,7 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
   matmul(S.A, L, false, S.C, L, S.T, L, m, m, m2);
   matmul(S.C, L, true, S.T, L, S.W, L, m2, m, m2);
   symmetrize(S.W, L, m2);
-  jacobi_eig(S.W, L, S.V, L, m2, S.pairs, &S.cnt);
+  eig_sym(S, S.W, S.V, m2, mixed != 0);
   sort_diag(S.W, L, m2, S.order);
   if (tid == 0 && m2 < nev) S.fail = 1;
   __syncthreads();
@@ -312,15 +365,53 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
     S.keep[tid] = S.V[bi * L + col] < 0.0 ? -1 : 1;
   }
   __syncthreads();
-  // Y_active = D C W_sel  (m x nev)
+  // y_c = C w_c in the scaled coordinates (m x nev)
   for (int e = tid; e < m * nev; e += blockDim.x) {
     const int i = e / nev, c = e % nev;
     const int col = S.order[c];
     double s = 0.0;
     for (int k = 0; k < m2; ++k) s += S.C[i * L + k] * S.V[k * L + col];
-    S.T[i * L + c] = S.d[i] * s * S.keep[c];
+    S.T[i * L + c] = s * S.keep[c];
+  }
+  if (tid < nev) {
+    S.sel[tid] = tid;
+    S.qa[tid] = S.W[S.order[tid] * L + S.order[tid]];
+    S.qb[tid] = 1.0;
   }
   __syncthreads();
+  if (mixed) {
+    // the rotations were float: take each Ritz value as the double Rayleigh
+    // quotient y^T A y / y^T B y of its vector, B-normalise the vector, and
+    // order the nev pairs by those values
+    for (int e = tid; e < m * nev; e += blockDim.x) {
+      const int i = e / nev, c = e % nev;
+      double sa = 0.0, sb = 0.0;
+      for (int k = 0; k < m; ++k) {
+        sa += S.A[i * L + k] * S.T[k * L + c];
+        sb += S.Bh[i * L + k] * S.T[k * L + c];
+      }
+      S.W[i * L + c] = sa;
+      S.V[i * L + c] = sb;
+    }
+    __syncthreads();
+    if (tid < nev) {
+      double qa = 0.0, qb = 0.0;
+      for (int i = 0; i < m; ++i) {
+        qa += S.T[i * L + tid] * S.W[i * L + tid];
+        qb += S.T[i * L + tid] * S.V[i * L + tid];
+      }
+      S.qa[tid] = qa / qb;
+      S.qb[tid] = qb;
+    }
+    __syncthreads();
+    if (tid < nev) {
+      int rank = 0;
+      for (int c = 0; c < nev; ++c)
+        if (S.qa[c] < S.qa[tid] || (S.qa[c] == S.qa[tid] && c < tid)) ++rank;
+      S.sel[rank] = tid;
+    }
+    __syncthreads();
+  }
   for (int e = tid; e < M * ld; e += blockDim.x) {
     if (y64) y64[e] = 0.0;
     if (yt) {
@@ -329,9 +420,11 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
     }
   }
   __syncthreads();
+  // Y = D y (rows of inactive columns stay zero)
   for (int e = tid; e < m * nev; e += blockDim.x) {
     const int i = e / nev, c = e % nev;
-    const double v = S.T[i * L + c];
+    const int src = S.sel[c];
+    const double v = S.d[i] * S.T[i * L + src] * (mixed ? rsqrt(S.qb[src]) : 1.0);
     const int o = S.idx[i] * ld + c;
     if (y64) y64[o] = v;
     if (yt) {
@@ -340,49 +433,13 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
     }
   }
   if (tid < nev) {
-    const double th = S.W[S.order[tid] * L + S.order[tid]];
+    const double th = S.qa[S.sel[tid]];
     if (st) st->theta[tid] = th;
     if (theta_out) theta_out[tid] = th;
   }
   if (tid == 0) {
     if (st) st->svqb_steps += S.svqb;
     if (svqb_out) *svqb_out = S.svqb;
-  }
-}
-
-// partials [grid][NB*16] -> G_A (M x M) and symmetric G_B
-__global__ void k_gram_reduce(const double *partials, int M, int nbA, int NB, int grid, double *ga,
-                              double *gb, const int *done) {
-  __shared__ double red[32][9];
-  if (done && *done) return;
-  const int lo = threadIdx.x & 7, oi = threadIdx.x >> 3;   // 8 threads per output, 32 outputs
-  const int o = blockIdx.x * 32 + oi;
-  double s = 0.0;
-  if (o < NB * 16)
-    for (int g = lo; g < grid; g += 8) s += partials[static_cast<int64_t>(g) * NB * 16 + o];
-  red[oi][lo] = s;
-  __syncthreads();
-  if (lo == 0 && o < NB * 16) {
-    double t = 0.0;
-    for (int k = 0; k < 8; ++k) t += red[oi][k];
-    const int blk = o / 16, q = o % 16, i = q / 4, j = q % 4;
-    const int mb = M / 4;
-    if (blk < nbA) {
-      const int bi = blk / mb, bj = blk % mb;
-      ga[(4 * bi + i) * M + 4 * bj + j] = t;
-    } else {
-      int k = blk - nbA, bi = 0;
-      while (k >= mb - bi) { k -= mb - bi; ++bi; }
-      const int bj = bi + k;
-      const int r = 4 * bi + i, c = 4 * bj + j;
-      if (bi < bj) {
-        gb[r * M + c] = t;
-        gb[c * M + r] = t;
-      } else if (i <= j) {
-        gb[r * M + c] = t;
-        gb[c * M + r] = t;
-      }
-    }
   }
 }
 
@@ -397,7 +454,7 @@ struct HRSmem {
   double theta[SPHYNX_MAX_POLY_DEGREE];
   double score[SPHYNX_MAX_POLY_DEGREE];
   int order[SPHYNX_MAX_POLY_DEGREE];
-  int cnt;
+  int cnt[3];
 };
 
 __global__ void __launch_bounds__(kSmallThreads)
@@ -428,7 +485,7 @@ k_harmonic_ritz(const double *alpha, const double *beta2, int k, double *roots, 
   matmul(S.Mx, L, false, S.C, L, S.V, L, k, k, k);
   matmul(S.C, L, true, S.V, L, S.Z, L, k, k, k);
   symmetrize(S.Z, L, k);
-  jacobi_eig(S.Z, L, S.V, L, k, S.pairs, &S.cnt);
+  jacobi_eig<double>(S.Z, L, S.V, L, k, S.pairs, S.cnt);
   sort_diag(S.Z, L, k, S.order);
   if (tid == 0) {
     for (int i = 0; i < k; ++i) S.theta[i] = S.Z[S.order[i] * L + S.order[i]];
@@ -470,22 +527,13 @@ k_harmonic_ritz(const double *alpha, const double *beta2, int k, double *roots, 
 
 void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, int M, int ld, int b,
                           double u_work, SolverState *state, double *y64, void *yt, DT dt,
-                          const int *active_override, double *theta_out, int *svqb_out) {
+                          const int *active_override, double *theta_out, int *svqb_out, int mixed) {
   if (M > kMaxM || M < 1) fail(SPHYNX_ERR_INVALID_ARG, "Rayleigh-Ritz size %d outside [1, %d]", M, kMaxM);
   if (b < 1 || b > ld) fail(SPHYNX_ERR_INVALID_ARG, "Rayleigh-Ritz nev %d", b);
   const size_t sm = sizeof(RRSmem);
   SPX_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
   k_rayleigh_ritz<<<1, kSmallThreads, sm, st>>>(ga, gb, M, ld, b, u_work, state, active_override, y64, yt,
-                                                dt == DT::F32 ? 1 : 0, theta_out, svqb_out);
-  SPX_LAUNCHED();
-}
-
-void launch_gram_reduce(cudaStream_t st, const double *partials, int nblk, int ld, int grid, double *ga,
-                        double *gb, const int *done) {
-  const int M = nblk * ld, mb = M / 4;
-  const int nbA = mb * mb, NB = nbA + mb * (mb + 1) / 2;
-  const int blocks = (NB * 16 + 31) / 32;
-  k_gram_reduce<<<blocks, 256, 0, st>>>(partials, M, nbA, NB, grid, ga, gb, done);
+                                                dt == DT::F32 ? 1 : 0, theta_out, svqb_out, mixed);
   SPX_LAUNCHED();
 }
 

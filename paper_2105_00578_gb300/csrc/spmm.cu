@@ -1,8 +1,74 @@
-// spmm.cu -- host entry of the Laplacian SpMM: argument checks, byte and
-// time accounting, dispatch to the per-type instantiations.
+// spmm.cu -- host entry of the Laplacian SpMM: argument checks, the
+// per-shape autotuner, byte and time accounting, dispatch to the per-type
+// instantiations.
 #include "spmm_kernels.cuh"
 
 namespace sphynx {
+
+namespace {
+
+void dispatch(sphynx_graph *g, const SpmmArgs &a, const SpmmDev &d) {
+  switch (a.tin) {
+    case DT::F64: spmm_dispatch_f64(g, a, d); break;
+    case DT::F32: spmm_dispatch_f32(g, a, d); break;
+    case DT::BF16: spmm_dispatch_bf16(g, a, d); break;
+  }
+}
+
+int shape_key(const SpmmArgs &a) {
+  return ((((static_cast<int>(a.tin) * 32 + a.bp) * 2 + a.mode) * 4 + a.lap) * 4) +
+         (a.mode == 1 ? static_cast<int>(a.tout) : 0);
+}
+
+// Time both short-row schedules for this product shape with the caller's
+// input and scratch outputs (a polynomial step's accumulator is read and
+// written, so the real one must not be touched), keep the faster.
+SpmmTuning tune(sphynx_graph *g, const SpmmArgs &a) {
+  const size_t out_bytes = static_cast<size_t>(g->n) * a.ld_y * 8 + 256;
+  const size_t t_bytes = static_cast<size_t>(g->n) * a.ld_x * 8 + 256;
+  if (g->plan.tune_scratch.bytes < out_bytes + t_bytes) g->plan.tune_scratch.alloc(out_bytes + t_bytes);
+  char *base = g->plan.tune_scratch.as<char>();
+  SPX_CUDA(cudaMemsetAsync(base, 0, out_bytes + t_bytes, g->stream));
+  SpmmArgs s = a;
+  s.done = nullptr;
+  if (a.mode == 0) {
+    s.y = base;
+  } else {
+    s.yacc = base;
+    s.t_out = base + out_bytes;
+  }
+  SpmmDev d{s.x, s.ld_x, s.ld_y, s.y, s.t_out, s.yacc, s.first, s.inv, s.invf, s.i_cur, nullptr};
+  cudaEvent_t e0, e1;
+  SPX_CUDA(cudaEventCreate(&e0));
+  SPX_CUDA(cudaEventCreate(&e1));
+  SpmmTuning t{kCsrStaged, {1e30f, 1e30f}};
+  const int64_t launches = g->ctr.launches;
+  for (int v = 0; v < 2; ++v) {   // warm-up of both
+    g->plan.variant = v;
+    dispatch(g, s, d);
+  }
+  // alternate the schedules so that neither always runs on a warmer L2
+  for (int round = 0; round < 3; ++round) {
+    for (int k = 0; k < 2; ++k) {
+      const int v = (round + k) & 1;
+      g->plan.variant = v;
+      SPX_CUDA(cudaEventRecord(e0, g->stream));
+      dispatch(g, s, d);
+      SPX_CUDA(cudaEventRecord(e1, g->stream));
+      SPX_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      SPX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      t.us[v] = ms * 1000.f < t.us[v] ? ms * 1000.f : t.us[v];
+    }
+  }
+  g->ctr.launches = launches;   // tuning launches are not part of the caller's work
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  t.variant = t.us[kSell32] < t.us[kCsrStaged] ? kSell32 : kCsrStaged;
+  return t;
+}
+
+}  // namespace
 
 void spmm(sphynx_graph *g, const SpmmArgs &a) {
   if (!(a.bp == 1 || a.bp == 4 || a.bp == 8 || a.bp == 12 || a.bp == 16))
@@ -11,7 +77,31 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: leading dimension smaller than block width");
   if (a.mode == 1 && a.tin == DT::F64 && a.tout != DT::F64)
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: double chain must stay double");
-  SpmmDev d{a.x, a.ld_x, a.ld_y, a.y, a.t_out, a.yacc, a.first, a.inv, a.i_cur, a.done};
+  // gathers are 16-byte vector loads (8-byte for bfloat16 rows of 4 or 12)
+  if (a.bp > 1) {
+    const size_t row_bytes = static_cast<size_t>(a.ld_x) * dt_size(a.tin);
+    const size_t need = (a.tin == DT::BF16 && a.bp % 8 != 0) ? 8 : 16;
+    if (row_bytes % need || reinterpret_cast<uintptr_t>(a.x) % need)
+      fail(SPHYNX_ERR_INVALID_ARG, "spmm: input rows must be %zu-byte aligned", need);
+  }
+  SpmmDev d{a.x, a.ld_x, a.ld_y, a.y, a.t_out, a.yacc, a.first, a.inv, a.invf, a.i_cur, a.done};
+
+  // schedule: forced, or the autotuner's choice for this product shape
+  if (g->plan.forced >= 0) {
+    g->plan.variant = g->plan.forced;
+  } else {
+    const int key = shape_key(a);
+    auto it = g->plan.tuned.find(key);
+    if (it == g->plan.tuned.end()) {
+      const bool timing = g->ctr.timing;
+      g->ctr.timing = false;
+      it = g->plan.tuned.emplace(key, tune(g, a)).first;
+      g->ctr.timing = timing;
+      g->plan.tuned_us[0] = it->second.us[0];
+      g->plan.tuned_us[1] = it->second.us[1];
+    }
+    g->plan.variant = it->second.variant;
+  }
 
   // algorithmic bytes: row pointers, column indices (+ weights), X once,
   // the diagonal / D^{-1/2} vector, and the outputs
@@ -41,11 +131,7 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
     e1 = g->ctr.ev_pool[g->ctr.ev_used++];
     SPX_CUDA(cudaEventRecord(e0, g->stream));
   }
-  switch (a.tin) {
-    case DT::F64: spmm_dispatch_f64(g, a, d); break;
-    case DT::F32: spmm_dispatch_f32(g, a, d); break;
-    case DT::BF16: spmm_dispatch_bf16(g, a, d); break;
-  }
+  dispatch(g, a, d);
   if (g->ctr.timing) SPX_CUDA(cudaEventRecord(e1, g->stream));
 }
 

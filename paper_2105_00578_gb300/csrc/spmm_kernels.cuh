@@ -149,6 +149,7 @@ struct SpmmDev {              // kernel-side view of SpmmArgs
   void *yacc;
   int first;
   const double *inv;
+  const float *invf;   // float copy of inv (the float path never touches FP64)
   int icur;
   const int *done;
 };
@@ -174,8 +175,14 @@ __device__ __forceinline__ void spmm_epilogue(const LapView &L, const SpmmDev &a
   if constexpr (MODE == 0) {
     store_row<BP>(static_cast<TA *>(a.y) + row * a.ldy, out);
   } else {
-    const TA ic = static_cast<TA>(a.inv[a.icur]);
-    const TA inx = static_cast<TA>(a.inv[a.icur + 1]);
+    TA ic, inx;
+    if constexpr (std::is_same<TA, double>::value) {
+      ic = a.inv[a.icur];
+      inx = a.inv[a.icur + 1];
+    } else {
+      ic = a.invf[a.icur];
+      inx = a.invf[a.icur + 1];
+    }
     TA tn[BP];
 #pragma unroll
     for (int c = 0; c < BP; ++c) tn[c] = xi[c] - out[c] * ic;
@@ -194,20 +201,272 @@ __device__ __forceinline__ void spmm_epilogue(const LapView &L, const SpmmDev &a
   }
 }
 
+// ---- packed float pairs: add.rn.f32x2 / fma.rn.f32x2 (sm_100 and later) ----
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// two bfloat16 in one 32-bit word -> the float pair (low, high), exactly
+__device__ __forceinline__ unsigned long long bf2_to_f2(unsigned w) {
+  return pk2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+// The raw bits of one gathered row of X (loaded first, converted later, so
+// that a batch of gathers is in flight at once).
+template <typename TI, int BP> struct RawRow;
+template <int BP> struct RawRow<float, BP> {
+  static constexpr int N = BP == 1 ? 1 : BP / 4;
+  float4 q[N];
+  __device__ __forceinline__ void load(const float *__restrict__ p) {
+    if constexpr (BP == 1) {
+      q[0].x = __ldg(p);
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k) q[k] = __ldg(reinterpret_cast<const float4 *>(p + 4 * k));
+    }
+  }
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < N; ++k) q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+};
+template <int BP> struct RawRow<__nv_bfloat16, BP> {
+  // rows of a multiple of 8 values are 16-byte aligned, rows of 4 or 12 only 8-byte
+  static constexpr bool kWide = BP % 8 == 0;
+  static constexpr int N = kWide ? BP / 8 : BP / 4;
+  uint4 q[kWide ? N : 1];
+  uint2 h[kWide ? 1 : N];
+  __device__ __forceinline__ void load(const __nv_bfloat16 *__restrict__ p) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      if constexpr (kWide) q[k] = __ldg(reinterpret_cast<const uint4 *>(p + 8 * k));
+      else h[k] = __ldg(reinterpret_cast<const uint2 *>(p + 4 * k));
+    }
+  }
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      if constexpr (kWide) q[k] = make_uint4(0u, 0u, 0u, 0u);
+      else h[k] = make_uint2(0u, 0u);
+    }
+  }
+};
+template <int BP> struct RawRow<double, BP> {
+  double v[BP];
+  __device__ __forceinline__ void load(const double *__restrict__ p) { load_row<BP>(p, v); }
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int c = 0; c < BP; ++c) v[c] = 0.0;
+  }
+};
+
+// gathers kept in flight per lane: about 128 bytes of X rows
+template <typename TI, int BP> struct GatherBatch {
+  static constexpr int bytes = BP * static_cast<int>(sizeof(TI));
+  static constexpr int U = bytes <= 16 ? 8 : (bytes <= 32 ? 4 : 2);
+};
+
+// Running sum of coef * X_j over a row's neighbours j.
+template <typename TI, int BP> struct RowAcc {
+  // float and bfloat16 inputs: packed float pairs (a scalar for BP == 1)
+  static constexpr int NP = BP >= 2 ? BP / 2 : 1;
+  unsigned long long v[NP];
+  float s;
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) v[q] = 0ull;
+    s = 0.f;
+  }
+  template <bool COEF>
+  __device__ __forceinline__ void add(const TI *__restrict__ p, float coef) {
+    const unsigned long long cc = COEF ? pk2(coef, coef) : 0ull;
+    if constexpr (BP == 1) {
+      const float xv = to_acc(p[0]);
+      s = COEF ? fmaf(coef, xv, s) : s + xv;
+    } else if constexpr (std::is_same<TI, float>::value) {
+#pragma unroll
+      for (int c = 0; c < BP; c += 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p + c));
+        const unsigned long long a0 = pk2(q.x, q.y), a1 = pk2(q.z, q.w);
+        v[c / 2] = COEF ? fma2(cc, a0, v[c / 2]) : add2(v[c / 2], a0);
+        v[c / 2 + 1] = COEF ? fma2(cc, a1, v[c / 2 + 1]) : add2(v[c / 2 + 1], a1);
+      }
+    } else if constexpr (BP % 8 == 0) {
+      // bfloat16 rows of a multiple of 8 values (leading dimension a multiple
+      // of 8, so rows are 16-byte aligned): 16-byte gathers
+#pragma unroll
+      for (int c = 0; c < BP; c += 8) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p + c));
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const unsigned long long f = bf2_to_f2(w[i]);
+          v[c / 2 + i] = COEF ? fma2(cc, f, v[c / 2 + i]) : add2(v[c / 2 + i], f);
+        }
+      }
+    } else {
+      // bfloat16 rows of 4 or 12 values: rows are only 8-byte aligned
+#pragma unroll
+      for (int c = 0; c < BP; c += 4) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p + c));
+        const unsigned long long f0 = bf2_to_f2(q.x), f1 = bf2_to_f2(q.y);
+        v[c / 2] = COEF ? fma2(cc, f0, v[c / 2]) : add2(v[c / 2], f0);
+        v[c / 2 + 1] = COEF ? fma2(cc, f1, v[c / 2 + 1]) : add2(v[c / 2 + 1], f1);
+      }
+    }
+  }
+  template <bool COEF>
+  __device__ __forceinline__ void accum(const RawRow<TI, BP> &r, float coef) {
+    const unsigned long long cc = COEF ? pk2(coef, coef) : 0ull;
+    if constexpr (BP == 1) {
+      const float xv = r.q[0].x;
+      s = COEF ? fmaf(coef, xv, s) : s + xv;
+    } else if constexpr (std::is_same<TI, float>::value) {
+#pragma unroll
+      for (int k = 0; k < BP / 4; ++k) {
+        const float4 q = r.q[k];
+        const unsigned long long a0 = pk2(q.x, q.y), a1 = pk2(q.z, q.w);
+        v[2 * k] = COEF ? fma2(cc, a0, v[2 * k]) : add2(v[2 * k], a0);
+        v[2 * k + 1] = COEF ? fma2(cc, a1, v[2 * k + 1]) : add2(v[2 * k + 1], a1);
+      }
+    } else if constexpr (RawRow<TI, BP>::kWide) {
+#pragma unroll
+      for (int k = 0; k < BP / 8; ++k) {
+        const unsigned w[4] = {r.q[k].x, r.q[k].y, r.q[k].z, r.q[k].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const unsigned long long f = bf2_to_f2(w[i]);
+          v[4 * k + i] = COEF ? fma2(cc, f, v[4 * k + i]) : add2(v[4 * k + i], f);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < BP / 4; ++k) {
+        const unsigned long long f0 = bf2_to_f2(r.h[k].x), f1 = bf2_to_f2(r.h[k].y);
+        v[2 * k] = COEF ? fma2(cc, f0, v[2 * k]) : add2(v[2 * k], f0);
+        v[2 * k + 1] = COEF ? fma2(cc, f1, v[2 * k + 1]) : add2(v[2 * k + 1], f1);
+      }
+    }
+  }
+  __device__ __forceinline__ void get(float (&o)[BP]) const {
+    if constexpr (BP == 1) {
+      o[0] = s;
+    } else {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const float2 f = upk2(v[q]);
+        o[2 * q] = f.x;
+        o[2 * q + 1] = f.y;
+      }
+    }
+  }
+};
+template <int BP> struct RowAcc<double, BP> {
+  double v[BP];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int c = 0; c < BP; ++c) v[c] = 0.0;
+  }
+  template <bool COEF>
+  __device__ __forceinline__ void add(const double *__restrict__ p, double coef) {
+    double xj[BP];
+    load_row<BP>(p, xj);
+#pragma unroll
+    for (int c = 0; c < BP; ++c) v[c] = COEF ? fma(coef, xj[c], v[c]) : v[c] + xj[c];
+  }
+  template <bool COEF>
+  __device__ __forceinline__ void accum(const RawRow<double, BP> &r, double coef) {
+#pragma unroll
+    for (int c = 0; c < BP; ++c) v[c] = COEF ? fma(coef, r.v[c], v[c]) : v[c] + r.v[c];
+  }
+  __device__ __forceinline__ void get(double (&o)[BP]) const {
+#pragma unroll
+    for (int c = 0; c < BP; ++c) o[c] = v[c];
+  }
+};
+
 template <int LAP, typename TI, int BP, bool W>
 __device__ __forceinline__ void spmm_accumulate(const LapView &L, const TI *__restrict__ x, int ldx,
-                                                int j, float wv, typename AccOf<TI>::T (&acc)[BP]) {
+                                                int j, float wv, RowAcc<TI, BP> &acc) {
   using TA = typename AccOf<TI>::T;
-  TA xj[BP];
-  load_row<BP>(x + static_cast<int64_t>(j) * ldx, xj);
+  const TI *p = x + static_cast<int64_t>(j) * ldx;
   if constexpr (LAP == SPHYNX_NORMALIZED || W) {
     TA coef = W ? static_cast<TA>(wv) : TA(1);
     if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, j);
-#pragma unroll
-    for (int c = 0; c < BP; ++c) acc[c] += coef * xj[c];
+    acc.template add<true>(p, coef);
   } else {
+    acc.template add<false>(p, TA(1));
+  }
+}
+
+// One row's d entries in batches: U column indices, then U gathers in flight
+// together, then U accumulations.  col_at(t) / w_at(t) read entry t < d.
+template <int LAP, typename TI, int BP, bool W, class ColAt, class WAt>
+__device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict__ x, int ldx, int d,
+                                         ColAt col_at, WAt w_at, RowAcc<TI, BP> &acc) {
+  using TA = typename AccOf<TI>::T;
+  constexpr int U = GatherBatch<TI, BP>::U;
+  // full batches without predicates
+  int t0 = 0;
+  for (; t0 + U <= d; t0 += U) {
+    int jj[U];
 #pragma unroll
-    for (int c = 0; c < BP; ++c) acc[c] += xj[c];
+    for (int u = 0; u < U; ++u) jj[u] = col_at(t0 + u);
+    RawRow<TI, BP> rr[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) rr[u].load(x + static_cast<int64_t>(jj[u]) * ldx);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if constexpr (LAP == SPHYNX_NORMALIZED || W) {
+        TA coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
+        if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
+        acc.template accum<true>(rr[u], coef);
+      } else {
+        acc.template accum<false>(rr[u], TA(1));
+      }
+    }
+  }
+  // the remainder, predicated
+  if (t0 < d) {
+    int jj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) jj[u] = t0 + u < d ? col_at(t0 + u) : -1;
+    RawRow<TI, BP> rr[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (jj[u] >= 0) rr[u].load(x + static_cast<int64_t>(jj[u]) * ldx);
+      else rr[u].zero();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if constexpr (LAP == SPHYNX_NORMALIZED || W) {
+        TA coef = TA(0);
+        if (jj[u] >= 0) {
+          coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
+          if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
+        }
+        acc.template accum<true>(rr[u], coef);
+      } else {
+        acc.template accum<false>(rr[u], TA(1));
+      }
+    }
   }
 }
 
@@ -215,8 +474,10 @@ template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_spmm_short(const LapView L, const SpmmDev a) {
   using TA = typename AccOf<TI>::T;
-  __shared__ int s_col[kWarpsPerCta][kStageCap];
-  __shared__ float s_w[kWarpsPerCta][W ? kStageCap : 1];
+  // column indices (and weights) of the warp's 32 rows, staged from the
+  // 16-byte-aligned position at or below the window start
+  __shared__ __align__(16) int s_col[kWarpsPerCta][kStageCap + 8];
+  __shared__ __align__(16) float s_w[kWarpsPerCta][W ? kStageCap + 8 : 4];
   if (a.done && *a.done) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row0 = (static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + wid) * 32;
@@ -225,36 +486,78 @@ k_spmm_short(const LapView L, const SpmmDev a) {
   const bool valid = row < L.n;
   int64_t rb = 0, re = 0;
   if (valid) {
-    rb = L.rowptr[row];
-    re = L.rowptr[row + 1];
+    rb = __ldcs(L.rowptr + row);
+    re = __ldcs(L.rowptr + row + 1);
   }
   const int nvalid = L.n - row0 < 32 ? static_cast<int>(L.n - row0) : 32;
   const int64_t wb = __shfl_sync(kFull, rb, 0);
   const int64_t we = __shfl_sync(kFull, re, nvalid - 1);
-  const int64_t cnt = we - wb;
-  const bool staged = cnt <= kStageCap;
+  const int64_t base = wb & ~static_cast<int64_t>(3);
+  const bool staged = we - base <= kStageCap + 4;
   if (staged) {
-    for (int e = lane; e < cnt; e += 32) {
-      s_col[wid][e] = __ldg(L.col + wb + e);
-      if constexpr (W) s_w[wid][e] = __ldg(L.w + wb + e);
+    // whole 16-byte chunks inside [base, we), then the tail one by one; the
+    // column stream is read once, so it is loaded evict-first
+    const int64_t vend = we & ~static_cast<int64_t>(3);
+    const int nvec = static_cast<int>((vend - base) >> 2);
+    const int4 *gc = reinterpret_cast<const int4 *>(L.col + base);
+    for (int v = lane; v < nvec; v += 32) *reinterpret_cast<int4 *>(&s_col[wid][4 * v]) = __ldcs(gc + v);
+    for (int64_t gidx = vend + lane; gidx < we; gidx += 32) s_col[wid][gidx - base] = __ldcs(L.col + gidx);
+    if constexpr (W) {
+      const float4 *gw = reinterpret_cast<const float4 *>(L.w + base);
+      for (int v = lane; v < nvec; v += 32) *reinterpret_cast<float4 *>(&s_w[wid][4 * v]) = __ldcs(gw + v);
+      for (int64_t gidx = vend + lane; gidx < we; gidx += 32) s_w[wid][gidx - base] = __ldcs(L.w + gidx);
     }
   }
   __syncwarp();
   if (!valid || re - rb > kShortDeg) return;
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
-  TA acc[BP];
-#pragma unroll
-  for (int c = 0; c < BP; ++c) acc[c] = TA(0);
+  RowAcc<TI, BP> acc;
+  acc.zero();
+  const int len = static_cast<int>(re - rb);
   if (staged) {
-    const int e0 = static_cast<int>(rb - wb), e1 = static_cast<int>(re - wb);
-#pragma unroll 4
-    for (int e = e0; e < e1; ++e)
-      spmm_accumulate<LAP, TI, BP, W>(L, x, a.ldx, s_col[wid][e], W ? s_w[wid][e] : 0.f, acc);
+    const int *sc = &s_col[wid][rb - base];
+    const float *sw = W ? &s_w[wid][rb - base] : nullptr;
+    spmm_row<LAP, TI, BP, W>(
+        L, x, a.ldx, len, [&](int t) { return sc[t]; }, [&](int t) { return sw[t]; }, acc);
   } else {
-    for (int64_t e = rb; e < re; ++e)
-      spmm_accumulate<LAP, TI, BP, W>(L, x, a.ldx, __ldg(L.col + e), W ? __ldg(L.w + e) : 0.f, acc);
+    const int32_t *gc = L.col + rb;
+    const float *gw = W ? L.w + rb : nullptr;
+    spmm_row<LAP, TI, BP, W>(
+        L, x, a.ldx, len, [&](int t) { return __ldg(gc + t); }, [&](int t) { return __ldg(gw + t); }, acc);
   }
-  spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, acc);
+  TA sum[BP];
+  acc.get(sum);
+  spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
+}
+
+// SELL-32 schedule: a warp per slice of 32 rows, lane = row.  Entry t of all
+// 32 rows is one contiguous 128-byte segment, so column reads are coalesced
+// without shared memory and all of L1 is left to the X gathers.
+template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
+__global__ void __launch_bounds__(128)
+k_spmm_sell(const LapView L, const SpmmDev a, const int32_t *__restrict__ scol, const float *__restrict__ sw,
+            const int64_t *__restrict__ sptr, const uint8_t *__restrict__ sdeg) {
+  using TA = typename AccOf<TI>::T;
+  if (a.done && *a.done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t slice = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (slice * 32 >= L.n) return;  // uniform per warp
+  const int64_t row = slice * 32 + lane;
+  const bool valid = row < L.n;
+  const int sd = valid ? sdeg[row] : 0xFF;
+  const int d = sd == 0xFF ? 0 : sd;
+  const int64_t base = __ldg(sptr + slice);
+  const int32_t *cp = scol + base + lane;
+  const float *wp = W ? sw + base + lane : nullptr;
+  const TI *__restrict__ x = static_cast<const TI *>(a.x);
+  RowAcc<TI, BP> acc;
+  acc.zero();
+  spmm_row<LAP, TI, BP, W>(
+      L, x, a.ldx, d, [&](int t) { return __ldcs(cp + 32 * t); }, [&](int t) { return __ldcs(wp + 32 * t); }, acc);
+  if (sd == 0xFF) return;   // padding lane or a long row
+  TA sum[BP];
+  acc.get(sum);
+  spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
 }
 
 // One warp per long-row work item: partial[item] = sum over the item's entries.
@@ -269,11 +572,12 @@ k_spmm_long(const LapView L, const SpmmDev a, const int64_t *__restrict__ items,
   if (item >= n_items) return;
   const int64_t b = items[item * 4 + 1], e = items[item * 4 + 2];
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
-  TA acc[BP];
-#pragma unroll
-  for (int c = 0; c < BP; ++c) acc[c] = TA(0);
+  RowAcc<TI, BP> racc;
+  racc.zero();
   for (int64_t k = b + lane; k < e; k += 32)
-    spmm_accumulate<LAP, TI, BP, W>(L, x, a.ldx, __ldg(L.col + k), W ? __ldg(L.w + k) : 0.f, acc);
+    spmm_accumulate<LAP, TI, BP, W>(L, x, a.ldx, __ldcs(L.col + k), W ? __ldcs(L.w + k) : 0.f, racc);
+  TA acc[BP];
+  racc.get(acc);
 #pragma unroll
   for (int c = 0; c < BP; ++c) {
 #pragma unroll
@@ -313,7 +617,13 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
   const int64_t warps = (g->n + 31) / 32;
   const int64_t grid = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
   if (grid > 0) {
-    k_spmm_short<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 32 * kWarpsPerCta, 0, st>>>(L, a);
+    if (g->plan.variant == kSell32) {
+      k_spmm_sell<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 128, 0, st>>>(
+          L, a, g->plan.sell_col.as<int32_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
+          g->plan.sell_deg.as<uint8_t>());
+    } else {
+      k_spmm_short<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 32 * kWarpsPerCta, 0, st>>>(L, a);
+    }
     SPX_LAUNCHED();
     g->ctr.launches++;
   }

@@ -43,16 +43,19 @@ def test_spmm_matches_oracle(gname, lap, dtype, ncols):
         ydt = torch.float64 if dtype == "f64" else torch.float32
         y = torch.zeros((g.n, ld), dtype=ydt, device="cuda")
         dt = {"f64": spx.DT_F64, "f32": spx.DT_F32, "bf16": spx.DT_BF16}[dtype]
-        spx.sphynx_laplacian_apply(h, lap, dt, xd, ld, y, ld, ncols)
-        torch.cuda.synchronize()
         xin = x if dtype == "f64" else (x.astype(np.float32).astype(np.float64) if dtype == "f32" else bf16_round(x))
         ref = O.operator_for(g, lap) @ xin
-        got = y.cpu().numpy().astype(np.float64)[:, :ncols]
         tol = 1e-13 if dtype == "f64" else 2e-6
-        assert rel_err(got, ref) < tol
-        # padding columns stay zero when the input padding is zero
-        if ld > ncols and ncols > 1:
-            assert np.all(y.cpu().numpy()[:, ncols:] == 0)
+        for variant in (0, 1):                 # CSR staged, SELL-32
+            spx.sphynx_set_spmm_variant(h, variant)
+            y.zero_()
+            spx.sphynx_laplacian_apply(h, lap, dt, xd, ld, y, ld, ncols)
+            torch.cuda.synchronize()
+            got = y.cpu().numpy().astype(np.float64)[:, :ncols]
+            assert rel_err(got, ref) < tol, variant
+            # padding columns stay zero when the input padding is zero
+            if ld > ncols and ncols > 1:
+                assert np.all(y.cpu().numpy()[:, ncols:] == 0)
     finally:
         spx.sphynx_destroy(h)
 
@@ -73,6 +76,9 @@ def test_degrees_exact():
         info = spx.sphynx_get_info(h)
         assert info["max_degree"] == int(g.degrees().max())
         assert info["long_rows"] == int(np.sum(g.degrees() > 32))
+        assert info["spmm_variant"] in (0, 1) and info["tuned_us_csr"] > 0 and info["tuned_us_sell"] > 0
+        # the tuner kept the faster schedule
+        assert (info["tuned_us_sell"] < info["tuned_us_csr"]) == (info["spmm_variant"] == 1)
         spx.sphynx_destroy(h)
 
 
