@@ -138,10 +138,10 @@ typedef struct {
   int64_t total_vweight;     /* sum of vertex weights                              */
   int64_t long_rows;         /* rows the SpMM routes to the long-row kernel        */
   int32_t weighted;          /* edge weights present                               */
-  int32_t spmm_variant;      /* short-row schedule the autotuner prefers for the
-                                float 8-column product: 0 = CSR staged in shared
-                                memory, 1 = SELL-32 (every product shape is tuned
-                                on its first launch)                               */
+  int32_t spmm_variant;      /* short-row schedule the autotuner chose at create
+                                from a float 8-column product and uses for every
+                                product: 0 = CSR staged in shared memory,
+                                1 = SELL-32                                         */
   float tuned_us_csr;        /* the two schedules' times for that product (us)    */
   float tuned_us_sell;
 } sphynx_graph_info;

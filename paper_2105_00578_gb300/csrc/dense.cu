@@ -29,6 +29,34 @@ __device__ inline double splitmix_pm1(uint64_t state, uint64_t ctr) {
 
 template <typename T> __device__ inline T from_d(double v) { return static_cast<T>(v); }
 
+// LD consecutive values (16-byte aligned) in 16-byte pieces
+template <typename T, int LD>
+__device__ __forceinline__ void row_load(const T *p, T (&o)[LD]) {
+  if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+    for (int c = 0; c < LD; c += 4) {
+      const float4 v = *reinterpret_cast<const float4 *>(p + c);
+      o[c] = v.x; o[c + 1] = v.y; o[c + 2] = v.z; o[c + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < LD; c += 2) {
+      const double2 v = *reinterpret_cast<const double2 *>(p + c);
+      o[c] = v.x; o[c + 1] = v.y;
+    }
+  }
+}
+template <typename T, int LD>
+__device__ __forceinline__ void row_store(T *p, const T (&v)[LD]) {
+  if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+    for (int c = 0; c < LD; c += 4) *reinterpret_cast<float4 *>(p + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < LD; c += 2) *reinterpret_cast<double2 *>(p + c) = make_double2(v[c], v[c + 1]);
+  }
+}
+
 unsigned blocks_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -98,50 +126,44 @@ __global__ void __launch_bounds__(256)
 k_update(int64_t n, const T *s0, const T *s1, const T *s2, const T *l1, const T *l2, const T *y,
          T *xo, T *po, T *lpo, const int *done) {
   constexpr int M = NBLK * LD;
-  __shared__ T sy[M * LD];
+  __shared__ __align__(16) T sy[M * LD];
   if (done && *done) return;
   for (int i = threadIdx.x; i < M * LD; i += blockDim.x) sy[i] = y[i];
   __syncthreads();
+  const T *srows[3] = {s0, s1, s2};
+  const T *lrows[3] = {nullptr, l1, l2};
   for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < n;
        row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     T x[LD], p[LD], lp[LD];
 #pragma unroll
     for (int c = 0; c < LD; ++c) { x[c] = T(0); p[c] = T(0); lp[c] = T(0); }
-    const T *rows[3] = {s0 + row * LD, NBLK > 1 ? s1 + row * LD : nullptr,
-                        NBLK > 2 ? s2 + row * LD : nullptr};
 #pragma unroll
     for (int blk = 0; blk < NBLK; ++blk) {
-      T v[LD];
+      // 4 columns of the input rows at a time; one coefficient row live at a time
+#pragma unroll 1
+      for (int k0 = 0; k0 < LD; k0 += 4) {
+        T v[4], lv[4];
+        row_load<T, 4>(srows[blk] + row * LD + k0, v);
+        if (blk > 0) row_load<T, 4>(lrows[blk] + row * LD + k0, lv);
 #pragma unroll
-      for (int k = 0; k < LD; ++k) v[k] = rows[blk][k];
+        for (int kk = 0; kk < 4; ++kk) {
+          T yr[LD];   // read once (a broadcast) for all three outputs
+          row_load<T, LD>(sy + (blk * LD + k0 + kk) * LD, yr);
 #pragma unroll
-      for (int k = 0; k < LD; ++k) {
-#pragma unroll
-        for (int c = 0; c < LD; ++c) {
-          const T yk = sy[(blk * LD + k) * LD + c];
-          x[c] += v[k] * yk;
-          if (blk > 0) p[c] += v[k] * yk;
+          for (int c = 0; c < LD; ++c) {
+            x[c] += v[kk] * yr[c];
+            if (blk > 0) {
+              p[c] += v[kk] * yr[c];
+              lp[c] += lv[kk] * yr[c];
+            }
+          }
         }
       }
     }
-    T *xr = xo + row * LD;
-#pragma unroll
-    for (int c = 0; c < LD; ++c) xr[c] = x[c];
+    row_store<T, LD>(xo + row * LD, x);
     if constexpr (NBLK == 3) {
-      const T *lrows[2] = {l1 + row * LD, l2 + row * LD};
-#pragma unroll
-      for (int blk = 1; blk < 3; ++blk) {
-        T v[LD];
-#pragma unroll
-        for (int k = 0; k < LD; ++k) v[k] = lrows[blk - 1][k];
-#pragma unroll
-        for (int k = 0; k < LD; ++k)
-#pragma unroll
-          for (int c = 0; c < LD; ++c) lp[c] += v[k] * sy[(blk * LD + k) * LD + c];
-      }
-      T *pr = po + row * LD, *lr = lpo + row * LD;
-#pragma unroll
-      for (int c = 0; c < LD; ++c) { pr[c] = p[c]; lr[c] = lp[c]; }
+      row_store<T, LD>(po + row * LD, p);
+      row_store<T, LD>(lpo + row * LD, lp);
     }
   }
 }
@@ -166,14 +188,16 @@ k_residual(int64_t n, const T *x, const T *lx, const double *theta, const T *bdi
     const T bi = bdiag ? bdiag[row] : T(1);
     const T ib = bdiag ? T(1) / bi : T(1);
     const T sc = jinv ? jinv[row] : T(1);
-    T r[LD];
+    T r[LD], xv[LD], lxv[LD];
+    row_load<T, LD>(x + row * LD, xv);
+    row_load<T, LD>(lx + row * LD, lxv);
 #pragma unroll
     for (int c = 0; c < LD; ++c) {
-      r[c] = lx[row * LD + c] - th[c] * (bi * x[row * LD + c]);
+      r[c] = lxv[c] - th[c] * (bi * xv[c]);
       acc[c] += r[c] * r[c] * ib;
+      r[c] *= sc;
     }
-#pragma unroll
-    for (int c = 0; c < LD; ++c) out[row * LD + c] = sc * r[c];
+    row_store<T, LD>(out + row * LD, r);
   }
   // block reduction in double, fixed order
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

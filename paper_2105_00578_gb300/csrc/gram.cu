@@ -23,8 +23,14 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <typename T> struct Tile { static constexpr int rows = 64; };
-template <> struct Tile<double> { static constexpr int rows = 32; };
+template <typename T> struct Tile {
+  static constexpr int rows = 64;
+  static constexpr int stages = 4;   // slabs in flight: enough bytes to cover DRAM latency
+};
+template <> struct Tile<double> {
+  static constexpr int rows = 32;
+  static constexpr int stages = 3;
+};
 
 // four consecutive elements, moved with 16-byte accesses
 template <typename T> struct Q4 { T x, y, z, w; };
@@ -46,6 +52,68 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// packed float pairs (fma.rn.f32x2, sm_100 and later)
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// 4 x 4 tile accumulator: a_i c_j for i, j < 4
+template <typename T> struct Acc44 {
+  T v[16];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = T(0);
+  }
+  __device__ __forceinline__ void add(const Q4<T> &a, const Q4<T> &c) {
+    const T av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[i * 4 + j] += av[i] * cv[j];
+  }
+  __device__ __forceinline__ T get(int q) const { return v[q]; }
+  __device__ __forceinline__ void set(int q, T x) { v[q] = x; }
+};
+template <> struct Acc44<float> {
+  unsigned long long v[8];   // pairs (i, j), (i, j + 1)
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = 0ull;
+  }
+  __device__ __forceinline__ void add(const Q4<float> &a, const Q4<float> &c) {
+    const unsigned long long c01 = pk2(c.x, c.y), c23 = pk2(c.z, c.w);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const unsigned long long ai = pk2(av[i], av[i]);
+      v[2 * i] = fma2(ai, c01, v[2 * i]);
+      v[2 * i + 1] = fma2(ai, c23, v[2 * i + 1]);
+    }
+  }
+  __device__ __forceinline__ float get(int q) const {
+    const float2 f = upk2(v[q >> 1]);
+    return (q & 1) ? f.y : f.x;
+  }
+  __device__ __forceinline__ void set(int q, float x) {
+    float2 f = upk2(v[q >> 1]);
+    if (q & 1) f.y = x; else f.x = x;
+    v[q >> 1] = pk2(f.x, f.y);
+  }
+};
+
 __device__ __forceinline__ void two_sum_fold(float &hi, float &lo, float &acc) {
   const float s = hi + acc;
   const float bp = s - hi;
@@ -55,17 +123,16 @@ __device__ __forceinline__ void two_sum_fold(float &hi, float &lo, float &acc) {
   acc = 0.f;
 }
 
+// nbu = upper tiles of one matrix; nb = 2 nbu tiles per row group; a group
+// is a whole number of warps (tpg threads) so that every warp reads one row
+// at a time and its shared loads of that row are broadcasts
 struct Shape {
-  int mb, nbu, nb, ngroups;   // nbu = upper tiles of one matrix; nb = 2 nbu
+  int mb, nbu, nb, tpg, ngroups;
 };
 
-__host__ __device__ inline Shape shape_of(int M) {
-  Shape s;
-  s.mb = M / 4;
-  s.nbu = s.mb * (s.mb + 1) / 2;
-  s.nb = 2 * s.nbu;
-  s.ngroups = kThreads / s.nb;
-  return s;
+__host__ __device__ constexpr Shape shape_of(int M) {
+  return Shape{M / 4, (M / 4) * (M / 4 + 1) / 2, (M / 4) * (M / 4 + 1), ((M / 4) * (M / 4 + 1) + 31) / 32 * 32,
+               kThreads / (((M / 4) * (M / 4 + 1) + 31) / 32 * 32)};
 }
 
 // tile index u in [0, nbu) -> (bi, bj) with bi <= bj (row-major upper triangle)
@@ -83,7 +150,9 @@ __device__ __forceinline__ void upper_tile(int u, int mb, int &bi, int &bj) {
 template <typename T, int LD, int NBLK>
 struct Slab {
   static constexpr int TR = Tile<T>::rows;
-  static constexpr int blk = TR * LD;                 // elements of one block
+  // elements of one block, padded by 16 bytes so that the same column of
+  // different blocks falls in different shared-memory banks
+  static constexpr int blk = TR * LD + 16 / static_cast<int>(sizeof(T));
   static constexpr int elems = 2 * NBLK * blk + TR;   // S, LS, diag(B)
 };
 
@@ -121,40 +190,47 @@ k_gram(int64_t n, const T *s0, const T *s1, const T *s2, const T *l0, const T *l
   using SL = Slab<T, LD, NBLK>;
   constexpr int M = LD * NBLK;
   constexpr int TR = SL::TR;
-  constexpr Shape sh = {M / 4, (M / 4) * (M / 4 + 1) / 2, (M / 4) * (M / 4 + 1), kThreads / ((M / 4) * (M / 4 + 1))};
+  constexpr Shape sh = shape_of(M);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (done && *done) return;
-  T *bufs[2] = {reinterpret_cast<T *>(smem_raw), reinterpret_cast<T *>(smem_raw) + SL::elems};
+  constexpr int NS = Tile<T>::stages;
+  T *const base = reinterpret_cast<T *>(smem_raw);
   const int tid = threadIdx.x;
-  const int grp = tid / sh.nb, t = tid - (tid / sh.nb) * sh.nb;
-  const bool active = grp < sh.ngroups;
+  const int grp = tid / sh.tpg, t = tid - (tid / sh.tpg) * sh.tpg;
+  const bool active = grp < sh.ngroups && t < sh.nb;
   int bi = 0, bj = 0;
-  const bool isA = t < sh.nbu;
-  upper_tile(isA ? t : t - sh.nbu, sh.mb, bi, bj);
+  const int tt = t < sh.nb ? t : 0;   // padding threads of a group take tile 0 and stay idle
+  const bool isA = tt < sh.nbu;
+  upper_tile(isA ? tt : tt - sh.nbu, sh.mb, bi, bj);
   // offsets of the thread's two column groups inside a slab
   const int offA = (bi * 4 / LD) * SL::blk + (bi * 4) % LD;                        // S, rows x LD
   const int offC = ((isA ? NBLK : 0) + bj * 4 / LD) * SL::blk + (bj * 4) % LD;    // LS or S
   const T *const srcS[3] = {s0, s1, s2};
   const T *const srcL[3] = {l0, l1, l2};
-  T acc[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = T(0);
+  Acc44<T> acc;
+  acc.zero();
   float hi[16], lo[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) { hi[q] = 0.f; lo[q] = 0.f; }
   const int64_t ntile = (n + TR - 1) / TR;
   const bool useB = !isA && bdiag != nullptr;
   int since_flush = 0;
+  // ring of NS slabs: slab it % NS holds this CTA's it-th row slab; NS - 1
+  // slabs are in flight while one is multiplied
   int64_t tile = blockIdx.x;
-  if (tile < ntile) stage<T, LD, NBLK>(bufs[0], tile * TR, n, srcS, srcL, bdiag);
-  cp_commit();
-  for (int it = 0; tile < ntile; tile += gridDim.x, ++it) {
-    const int64_t next = tile + gridDim.x;
-    if (next < ntile) stage<T, LD, NBLK>(bufs[(it + 1) & 1], next * TR, n, srcS, srcL, bdiag);
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) {
+    const int64_t tl = tile + static_cast<int64_t>(s) * gridDim.x;
+    if (tl < ntile) stage<T, LD, NBLK>(base + s * SL::elems, tl * TR, n, srcS, srcL, bdiag);
     cp_commit();
-    cp_wait<1>();          // this slab's copies have landed (the next one may be in flight)
+  }
+  for (int it = 0; tile < ntile; tile += gridDim.x, ++it) {
+    const int64_t ahead = tile + static_cast<int64_t>(NS - 1) * gridDim.x;
+    if (ahead < ntile) stage<T, LD, NBLK>(base + ((it + NS - 1) % NS) * SL::elems, ahead * TR, n, srcS, srcL, bdiag);
+    cp_commit();
+    cp_wait<NS - 1>();     // this slab's group has landed; the NS - 1 later ones may be in flight
     __syncthreads();
-    const T *buf = bufs[it & 1];
+    const T *buf = base + (it % NS) * SL::elems;
     if (active) {
       const T *bd = buf + 2 * NBLK * SL::blk;
 #pragma unroll 4
@@ -165,18 +241,17 @@ k_gram(int64_t n, const T *s0, const T *s1, const T *s2, const T *l0, const T *l
           const T b = bd[r];
           cv = {cv.x * b, cv.y * b, cv.z * b, cv.w * b};
         }
-        const T a[4] = {av.x, av.y, av.z, av.w};
-        const T c[4] = {cv.x, cv.y, cv.z, cv.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i * 4 + j] += a[i] * c[j];
+        acc.add(av, cv);
       }
       if constexpr (std::is_same<T, float>::value) {
         since_flush += (TR + sh.ngroups - 1) / sh.ngroups;
         if (since_flush >= 64) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) two_sum_fold(hi[q], lo[q], acc[q]);
+          for (int q = 0; q < 16; ++q) {
+            float a = acc.get(q);
+            two_sum_fold(hi[q], lo[q], a);
+          }
+          acc.zero();
           since_flush = 0;
         }
       }
@@ -191,10 +266,11 @@ k_gram(int64_t n, const T *s0, const T *s1, const T *s2, const T *l0, const T *l
     for (int q = 0; q < 16; ++q) {
       double v;
       if constexpr (std::is_same<T, float>::value) {
-        two_sum_fold(hi[q], lo[q], acc[q]);
+        float a = acc.get(q);
+        two_sum_fold(hi[q], lo[q], a);
         v = static_cast<double>(hi[q]) + static_cast<double>(lo[q]);
       } else {
-        v = acc[q];
+        v = acc.get(q);
       }
       red[(grp * sh.nb + t) * 16 + q] = v;
     }
@@ -239,7 +315,7 @@ template <typename T, int LD, int NBLK>
 void launch_t(cudaStream_t st, const GramArgs &a, const T *bd, int grid) {
   constexpr int M = LD * NBLK;
   const Shape sh = shape_of(M);
-  const size_t slabs = 2 * static_cast<size_t>(Slab<T, LD, NBLK>::elems) * sizeof(T);
+  const size_t slabs = static_cast<size_t>(Tile<T>::stages) * Slab<T, LD, NBLK>::elems * sizeof(T);
   const size_t red = static_cast<size_t>(sh.ngroups) * sh.nb * 16 * sizeof(double);
   const size_t sm = slabs > red ? slabs : red;
   if (sm > 48 * 1024)

@@ -327,9 +327,9 @@ void build_sell(sphynx_graph *g) {
   SPX_CUDA(cudaStreamSynchronize(g->stream));
 }
 
-// The SpMM tunes every product shape (input type, width, mode, Laplacian)
-// the first time it is launched; at create the float 8-column product is
-// tuned so that sphynx_get_info can report the graph's preference.
+// The short-row schedule is a property of the graph's structure: both are
+// timed at create on a float 8-column product and the faster serves every
+// later product of the handle.
 void autotune_spmm(sphynx_graph *g) {
   const int64_t n = g->n;
   const int ld = 8;
@@ -346,12 +346,11 @@ void autotune_spmm(sphynx_graph *g) {
   a.b_true = ld;
   a.x = x.p;
   a.y = y.p;
-  spmm(g, a);
+  const SpmmTuning t = spmm_tune(g, a);
+  g->plan.tuned_variant = t.variant;
+  g->plan.tuned_us[kCsrStaged] = t.us[kCsrStaged];
+  g->plan.tuned_us[kSell32] = t.us[kSell32];
   SPX_CUDA(cudaStreamSynchronize(g->stream));
-  std::vector<cudaEvent_t> pool;
-  pool.swap(g->ctr.ev_pool);
-  g->ctr = Counters{};
-  g->ctr.ev_pool.swap(pool);
 }
 
 }  // namespace
@@ -551,7 +550,7 @@ int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info) {
     info->total_vweight = g->total_vw;
     info->long_rows = g->plan.n_long;
     info->weighted = g->weighted ? 1 : 0;
-    info->spmm_variant = g->plan.tuned_us[kSell32] < g->plan.tuned_us[kCsrStaged] ? kSell32 : kCsrStaged;
+    info->spmm_variant = g->plan.tuned_variant;
     info->tuned_us_csr = g->plan.tuned_us[kCsrStaged];
     info->tuned_us_sell = g->plan.tuned_us[kSell32];
     return SPHYNX_OK;
@@ -563,7 +562,6 @@ int sphynx_set_spmm_variant(sphynx_handle g, int32_t variant) {
     if (!g) fail(SPHYNX_ERR_INVALID_ARG, "NULL handle");
     if (variant == -1) {
       g->plan.forced = -1;
-      g->plan.tuned.clear();
       autotune_spmm(g);
     } else if (variant == kCsrStaged || variant == kSell32) {
       g->plan.forced = variant;

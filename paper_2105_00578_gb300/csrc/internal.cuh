@@ -90,10 +90,8 @@ struct SpmmTuning {
 struct SpmmPlan {
   int variant = kCsrStaged;          // schedule of the launch being issued
   int forced = -1;                   // >= 0: every product uses this schedule
-  float tuned_us[2] = {0.f, 0.f};    // timings of the last tuned product shape
-  // autotuner record per product shape (input type, width, mode, Laplacian,
-  // output type): filled the first time a shape is launched
-  std::map<int, SpmmTuning> tuned;
+  int tuned_variant = kCsrStaged;    // the autotuner's choice for this graph
+  float tuned_us[2] = {0.f, 0.f};    // its timings of both schedules
   DevBuf tune_scratch;
   int64_t n_long = 0;                // rows with degree > kShortDeg
   int64_t n_items = 0;               // long-row work items
@@ -193,6 +191,8 @@ struct SpmmArgs {
   const int *done;         // device flag: skip the launch when nonzero (may be NULL)
 };
 void spmm(sphynx_graph *g, const SpmmArgs &a);
+// both short-row schedules timed on this product (scratch outputs)
+SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a);
 
 // ---- dense.cu ---------------------------------------------------------------
 void launch_random_block(cudaStream_t s, DT dt, void *x, int64_t n, int b, int ld, uint64_t seed);

@@ -15,15 +15,13 @@ void dispatch(sphynx_graph *g, const SpmmArgs &a, const SpmmDev &d) {
   }
 }
 
-int shape_key(const SpmmArgs &a) {
-  return ((((static_cast<int>(a.tin) * 32 + a.bp) * 2 + a.mode) * 4 + a.lap) * 4) +
-         (a.mode == 1 ? static_cast<int>(a.tout) : 0);
-}
+}  // namespace
 
-// Time both short-row schedules for this product shape with the caller's
-// input and scratch outputs (a polynomial step's accumulator is read and
-// written, so the real one must not be touched), keep the faster.
-SpmmTuning tune(sphynx_graph *g, const SpmmArgs &a) {
+// Time both short-row schedules for this product with the caller's input
+// and scratch outputs (a polynomial step's accumulator is read and written,
+// so the real one must not be touched), alternating them over five rounds,
+// and return the faster.
+SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a) {
   const size_t out_bytes = static_cast<size_t>(g->n) * a.ld_y * 8 + 256;
   const size_t t_bytes = static_cast<size_t>(g->n) * a.ld_x * 8 + 256;
   if (g->plan.tune_scratch.bytes < out_bytes + t_bytes) g->plan.tune_scratch.alloc(out_bytes + t_bytes);
@@ -48,7 +46,7 @@ SpmmTuning tune(sphynx_graph *g, const SpmmArgs &a) {
     dispatch(g, s, d);
   }
   // alternate the schedules so that neither always runs on a warmer L2
-  for (int round = 0; round < 3; ++round) {
+  for (int round = 0; round < 5; ++round) {
     for (int k = 0; k < 2; ++k) {
       const int v = (round + k) & 1;
       g->plan.variant = v;
@@ -68,8 +66,6 @@ SpmmTuning tune(sphynx_graph *g, const SpmmArgs &a) {
   return t;
 }
 
-}  // namespace
-
 void spmm(sphynx_graph *g, const SpmmArgs &a) {
   if (!(a.bp == 1 || a.bp == 4 || a.bp == 8 || a.bp == 12 || a.bp == 16))
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: block width %d", a.bp);
@@ -86,22 +82,8 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
   }
   SpmmDev d{a.x, a.ld_x, a.ld_y, a.y, a.t_out, a.yacc, a.first, a.inv, a.invf, a.i_cur, a.done};
 
-  // schedule: forced, or the autotuner's choice for this product shape
-  if (g->plan.forced >= 0) {
-    g->plan.variant = g->plan.forced;
-  } else {
-    const int key = shape_key(a);
-    auto it = g->plan.tuned.find(key);
-    if (it == g->plan.tuned.end()) {
-      const bool timing = g->ctr.timing;
-      g->ctr.timing = false;
-      it = g->plan.tuned.emplace(key, tune(g, a)).first;
-      g->ctr.timing = timing;
-      g->plan.tuned_us[0] = it->second.us[0];
-      g->plan.tuned_us[1] = it->second.us[1];
-    }
-    g->plan.variant = it->second.variant;
-  }
+  // schedule: forced, or the one the autotuner chose for this graph at create
+  g->plan.variant = g->plan.forced >= 0 ? g->plan.forced : g->plan.tuned_variant;
 
   // algorithmic bytes: row pointers, column indices (+ weights), X once,
   // the diagonal / D^{-1/2} vector, and the outputs

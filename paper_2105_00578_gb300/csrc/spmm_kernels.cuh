@@ -423,31 +423,77 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
                                          ColAt col_at, WAt w_at, RowAcc<TI, BP> &acc) {
   using TA = typename AccOf<TI>::T;
   constexpr int U = GatherBatch<TI, BP>::U;
-  // full batches without predicates
-  int t0 = 0;
-  for (; t0 + U <= d; t0 += U) {
-    int jj[U];
+  if constexpr (U > 4) {
+    // narrow rows (16 bytes or less): plain batches keep the register count,
+    // hence the number of resident warps, high
+    int t0 = 0;
+    for (; t0 + U <= d; t0 += U) {
+      int jj[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) jj[u] = col_at(t0 + u);
-    RawRow<TI, BP> rr[U];
+      for (int u = 0; u < U; ++u) jj[u] = col_at(t0 + u);
+      RawRow<TI, BP> rr[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) rr[u].load(x + static_cast<int64_t>(jj[u]) * ldx);
+      for (int u = 0; u < U; ++u) rr[u].load(x + static_cast<int64_t>(jj[u]) * ldx);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if constexpr (LAP == SPHYNX_NORMALIZED || W) {
-        TA coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
-        if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
-        acc.template accum<true>(rr[u], coef);
-      } else {
-        acc.template accum<false>(rr[u], TA(1));
+      for (int u = 0; u < U; ++u) {
+        if constexpr (LAP == SPHYNX_NORMALIZED || W) {
+          TA coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
+          if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
+          acc.template accum<true>(rr[u], coef);
+        } else {
+          acc.template accum<false>(rr[u], TA(1));
+        }
       }
     }
-  }
-  // the remainder, predicated
-  if (t0 < d) {
-    int jj[U];
+    if (t0 < d) {
+      int jj[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) jj[u] = t0 + u < d ? col_at(t0 + u) : -1;
+      for (int u = 0; u < U; ++u) jj[u] = t0 + u < d ? col_at(t0 + u) : -1;
+      RawRow<TI, BP> rr[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (jj[u] >= 0) rr[u].load(x + static_cast<int64_t>(jj[u]) * ldx);
+        else rr[u].zero();
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if constexpr (LAP == SPHYNX_NORMALIZED || W) {
+          TA coef = TA(0);
+          if (jj[u] >= 0) {
+            coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
+            if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
+          }
+          acc.template accum<true>(rr[u], coef);
+        } else {
+          acc.template accum<false>(rr[u], TA(1));
+        }
+      }
+    }
+    return;
+  }
+  // wide rows: software pipeline -- the next batch's column indices (and
+  // weights) are requested before this batch's gathers, so their latencies overlap
+  int jn[U];
+  float wn[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    jn[u] = u < d ? col_at(u) : -1;
+    if constexpr (W) wn[u] = u < d ? w_at(u) : 0.f;
+  }
+  for (int t0 = 0; t0 < d; t0 += U) {
+    int jj[U];
+    float wv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      jj[u] = jn[u];
+      if constexpr (W) wv[u] = wn[u];
+    }
+    const int t1 = t0 + U;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      jn[u] = t1 + u < d ? col_at(t1 + u) : -1;
+      if constexpr (W) wn[u] = t1 + u < d ? w_at(t1 + u) : 0.f;
+    }
     RawRow<TI, BP> rr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -459,7 +505,7 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
       if constexpr (LAP == SPHYNX_NORMALIZED || W) {
         TA coef = TA(0);
         if (jj[u] >= 0) {
-          coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
+          coef = W ? static_cast<TA>(wv[u]) : TA(1);
           if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
         }
         acc.template accum<true>(rr[u], coef);
