@@ -243,6 +243,23 @@ int sphynx_eigensolve(sphynx_handle g, const sphynx_options *opt, int32_t nev, c
 int sphynx_mj(int32_t dtype, const void *coords, int32_t ldc, int32_t dims, int64_t n,
               const int64_t *vtx_w, int32_t K, int32_t *part_out, void *stream);
 
+/* sphynx_mj without any device allocation (the paper has no counterpart;
+ * this serves callers that cannot let a library call cudaMalloc, such as
+ * frameworks that own the whole device memory pool through their own
+ * allocator, or latency-bound loops that must not pay cudaMalloc's cost and
+ * its implicit synchronisation).  Same arguments, same bit-exact result as
+ * sphynx_mj; part_out and every input stay caller-owned.  Scratch lives in a
+ * fixed 16 MiB array in device memory that every GPU loading the library
+ * holds until the process exits; calls needing more (roughly
+ * 8 n + 5200 K bytes; n <= 2^20 with K <= 1024 fits) fail with
+ * SPHYNX_ERR_UNSUPPORTED.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and should therefore come before any
+ * stream capture.  All calls share the one array and each call clears what
+ * it needs cleared: calls whose GPU work overlaps (different streams, or
+ * concurrent host threads) race and must be serialised by the caller. */
+int sphynx_mj_noalloc(int32_t dtype, const void *coords, int32_t ldc, int32_t dims, int64_t n,
+                      const int64_t *vtx_w, int32_t K, int32_t *part_out, void *stream);
+
 /* Cutsize (Eq. 1, exact: integer for unit weights, exact fixed point for
  * float weights, rounded once) and imbalance max_k W_k / W_avg (Sec. 3.1)
  * of a partition given as device int32[n] with values in [0, K). */

@@ -86,6 +86,7 @@ def _load():
         "sphynx_rayleigh_ritz": (C.c_int, [pd, pd, pi32, i32, i32, dbl, pd, pd, pi32, vp]),
         "sphynx_eigensolve": (C.c_int, [vp, C.POINTER(Options), i32, pd, vp, i32, pd, pd, C.POINTER(Stats)]),
         "sphynx_mj": (C.c_int, [i32, vp, i32, i32, i64, vp, i32, vp, vp]),
+        "sphynx_mj_noalloc": (C.c_int, [i32, vp, i32, i32, i64, vp, i32, vp, vp]),
         "sphynx_eval": (C.c_int, [vp, vp, i32, pd, pd, pd]),
         "sphynx_partition": (C.c_int, [vp, i32, C.POINTER(Options), vp, pd, pd, C.POINTER(Stats)]),
     }
@@ -256,6 +257,13 @@ def sphynx_eigensolve(h, opt: Options, nev, x_out, ldx, x0=None):
 
 def sphynx_mj(dtype, coords, ldc, dims, n, vtx_w, K, part_out, stream=None) -> None:
     check(LIB.sphynx_mj(dtype, ptr(coords), ldc, dims, int(n), ptr(vtx_w), K, ptr(part_out), _stream(stream)))
+
+
+def sphynx_mj_noalloc(dtype, coords, ldc, dims, n, vtx_w, K, part_out, stream=None) -> None:
+    """sphynx_mj with its scratch in the library's fixed device array: for
+    callers that cannot let the library allocate device memory."""
+    check(LIB.sphynx_mj_noalloc(dtype, ptr(coords), ldc, dims, int(n), ptr(vtx_w), K, ptr(part_out),
+                                _stream(stream)))
 
 
 def sphynx_eval(h, part, K):

@@ -21,6 +21,7 @@
 #include "internal.cuh"
 
 #include <cstring>
+#include <mutex>
 
 namespace sphynx {
 
@@ -511,6 +512,70 @@ extern "C" int sphynx_mj(int32_t dtype, const void *coords, int32_t ldc, int32_t
     if (n >= (1LL << 31)) fail(SPHYNX_ERR_UNSUPPORTED, "n >= 2^31");
     run_mj(static_cast<cudaStream_t>(stream), static_cast<DT>(dtype), coords, ldc, dims, n, vtx_w, K, part_out,
            nullptr);
+    return SPHYNX_OK;
+  });
+}
+
+// ---- multi-jagged without any device allocation ------------------------------
+//
+// Some callers cannot let a library call cudaMalloc: frameworks that own the
+// whole device memory pool through their own allocator, and latency-bound
+// loops that must not pay cudaMalloc's cost or its implicit device-wide
+// synchronisation.  For them sphynx_mj_noalloc does the same work as
+// sphynx_mj with its scratch (permutations, histograms, section tables) in
+// this file-scope device array.  Every GPU that loads the library holds the
+// array until the process exits.
+
+constexpr size_t kMjStaticBytes = size_t(16) << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_mj_static_scratch[kMjStaticBytes];
+
+namespace {
+
+// Device address of the array, per device.  In host code the array's name is
+// only a host-side stand-in, so the address comes from cudaGetSymbolAddress,
+// called once per device with that device current.
+std::mutex g_mj_static_mutex;
+void *g_mj_static_ptr[64] = {nullptr};
+
+void *mj_static_scratch() {
+  int dev = 0;
+  SPX_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) sphynx::fail(SPHYNX_ERR_UNSUPPORTED, "device ordinal %d", dev);
+  std::lock_guard<std::mutex> lock(g_mj_static_mutex);
+  if (!g_mj_static_ptr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_mj_static_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      sphynx::fail(SPHYNX_ERR_CUDA, "cudaGetSymbolAddress of the multi-jagged scratch failed: %s", cudaGetErrorString(e));
+    }
+    g_mj_static_ptr[dev] = p;
+  }
+  return g_mj_static_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" int sphynx_mj_noalloc(int32_t dtype, const void *coords, int32_t ldc, int32_t dims, int64_t n,
+                                 const int64_t *vtx_w, int32_t K, int32_t *part_out, void *stream) {
+  using namespace sphynx;
+  return guarded([&]() -> int {
+    if (n > 0 && (!coords || !part_out)) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
+    if (ldc < dims) fail(SPHYNX_ERR_INVALID_ARG, "ldc < dims");
+    if (dtype != SPHYNX_DT_F32 && dtype != SPHYNX_DT_F64) fail(SPHYNX_ERR_INVALID_ARG, "dtype");
+    if (n < 0) fail(SPHYNX_ERR_INVALID_ARG, "n < 0");
+    if (K < 1 || K > (1 << 20)) fail(SPHYNX_ERR_INVALID_ARG, "K must be in [1, 2^20]");
+    const size_t need = mj_scratch_bytes(n, K);
+    if (need > kMjStaticBytes)
+      fail(SPHYNX_ERR_UNSUPPORTED,
+           "sphynx_mj_noalloc: n = %lld, K = %d need %zu bytes of scratch, more than its fixed %zu "
+           "(e.g. n <= 2^20 with K <= 1024 fits); use sphynx_mj",
+           static_cast<long long>(n), K, need, kMjStaticBytes);
+    void *scratch = mj_static_scratch();
+    // run_mj_scratch clears the histograms and counters it relies on and
+    // rewrites everything else it reads
+    run_mj_scratch(static_cast<cudaStream_t>(stream), static_cast<DT>(dtype), coords, ldc, dims, n, vtx_w, K,
+                   part_out, nullptr, scratch);
     return SPHYNX_OK;
   });
 }
