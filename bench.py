@@ -43,7 +43,12 @@ WORKLOADS = {
     "c3": dict(desc="R-MAT scale 22 (edge factor 16, a=.57 b=.19 c=.19), symmetrised, deduplicated, self-loops "
                     "dropped, largest component; normalized Laplacian, Jacobi, K=256 (d=9), tol 1e-2",
                K=256, laplacian="normalized", precond="jacobi", poly_degree=25, tol=1e-2, seed=3,
-               precision="fp32", golden=None),
+               precision="fp32", golden="c3_oracle.json"),
+    "c5": dict(desc="R-MAT scale 24 (edge factor 16, a=.57 b=.19 c=.19), largest component, FP32 edge weights "
+                    "uniform in [0.5, 1.5); normalized Laplacian, polynomial preconditioner degree 10, K=1024 "
+                    "(d=11), BF16 polynomial chain, tol 1e-2",
+               K=1024, laplacian="normalized", precond="poly", poly_degree=10, tol=1e-2, seed=5,
+               precision="mixed_bf16", golden=None),
 }
 
 
@@ -55,6 +60,8 @@ def make_graph(name: str):
         return workloads.grid2d(64, 64)
     if name == "c3":
         return workloads.rmat(22, 16, 0.57, 0.19, 0.19, seed=3)
+    if name == "c5":
+        return workloads.random_edge_weights(workloads.rmat(24, 16, 0.57, 0.19, 0.19, seed=5), 0.5, 1.5, seed=5)
     raise ValueError(name)
 
 
@@ -203,6 +210,8 @@ def run_ours(args, world, rank, local):
     g = make_graph(args.workload)
     stream = torch.cuda.current_stream()
     graph = spx.Graph(g, stream=stream)
+    if args.spmm_variant is not None:
+        spx.sphynx_set_spmm_variant(graph.h, {"csr": 0, "sell": 1}[args.spmm_variant])
     n = g.n
     part = torch.empty(n, dtype=torch.int32, device="cuda")
 
@@ -249,7 +258,24 @@ def run_ours(args, world, rank, local):
     launches = sum(s[3]["kernel_launches"] for s in stats)
     last = stats[-1]
     pk = peaks()
-    achieved = spmm_bytes / (spmm_ms / 1000.0) / 1e9 if spmm_ms > 0 else None
+    achieved_all = spmm_bytes / (spmm_ms / 1000.0) / 1e9 if spmm_ms > 0 else None
+    # the SpMM launches split by input precision (F64, F32, BF16)
+    by_dt = {}
+    for i, name in enumerate(("f64", "f32", "bf16")):
+        ms_i = sum(s[3]["ms_spmm_by_dt"][i] for s in stats)
+        by_i = sum(s[3]["spmm_bytes_by_dt"][i] for s in stats)
+        la_i = sum(s[3]["spmm_launches_by_dt"][i] for s in stats)
+        if la_i:
+            by_dt[name] = {"launches_per_step": la_i / args.steps, "us_per_launch": 1000.0 * ms_i / la_i,
+                           "bytes_per_launch": by_i / la_i, "gbs": by_i / (ms_i / 1000.0) / 1e9 if ms_i > 0 else None}
+    # the dominant kernel: the SpMM flavour with the most device time
+    dom = max(by_dt, key=lambda k: by_dt[k]["us_per_launch"] * by_dt[k]["launches_per_step"]) if by_dt else None
+    info = spx.sphynx_get_info(graph.h)
+    schedule = "k_spmm_sell" if (args.spmm_variant or "").startswith("sell") or \
+        (args.spmm_variant is None and info["spmm_variant"] == 1) else "k_spmm_short"
+    achieved = by_dt[dom]["gbs"] if dom else None
+    kernel_name = f"{schedule}<{dom} in>"
+    traffic = profiled_traffic(f"spmm_{dom}", args.workload) if dom else None
 
     # plain FP64 path at the same tolerance
     fp64 = None
@@ -275,6 +301,7 @@ def run_ours(args, world, rank, local):
     # from pinned memory) + partition + read of the part ids (D2H) per step
     rp = torch.from_numpy(g.row_ptr).pin_memory()
     cl = torch.from_numpy(g.col).pin_memory()
+    wp = torch.from_numpy(g.w).pin_memory() if g.w is not None else None
     hp = torch.empty(n, dtype=torch.int32).pin_memory()
     o_host = spx.options(laplacian=w["laplacian"], precond=w["precond"], poly_degree=w["poly_degree"],
                          precision=precision, tol=w["tol"], seed=w["seed"])
@@ -283,7 +310,8 @@ def run_ours(args, world, rank, local):
     barrier()
     t = time.perf_counter()
     for _ in range(e2e_steps):
-        h = spx.sphynx_create(rp.data_ptr(), cl.data_ptr(), None, None, n, g.nnz, spx.HOST_PTRS, stream)
+        h = spx.sphynx_create(rp.data_ptr(), cl.data_ptr(), None if wp is None else wp.data_ptr(), None, n, g.nnz,
+                              spx.HOST_PTRS, stream)
         spx.sphynx_partition(h, w["K"], o_host, hp.data_ptr())
         spx.sphynx_destroy(h)
     torch.cuda.synchronize()
@@ -305,23 +333,24 @@ def run_ours(args, world, rank, local):
             "vs_baseline": None, "dtype": "f32" if precision != "fp64" else "f64",
             "data": "synthetic",
             "config": {"workload": w["desc"], "K": w["K"], "precision": precision,
-                       "l2": "inputs larger than L2 (CSR column array 215 MB > 129 MB)"
-                       if args.workload == "c2" else "no flush",
+                       "l2": (f"inputs larger than L2 (CSR column array {g.col.nbytes / 1e6:.0f} MB > 129 MB)"
+                              if g.col.nbytes > 129e6 else "inputs within L2, no flush"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "iterations": last[3]["iterations"], "status": last[0], "cut": last[1], "imbalance": last[2],
             "eigenvalues": last[3]["eigenvalues"],
             "max_resnorm_over_tol_theta": _res_ratio(last[3], w["tol"]),
-            "spmm": {"gbs": achieved, "launches_per_step": spmm_launches / args.steps,
-                     "ms_per_step": spmm_ms / args.steps},
+            "spmm": {"gbs": achieved_all, "launches_per_step": spmm_launches / args.steps,
+                     "ms_per_step": spmm_ms / args.steps, "by_input_precision": by_dt,
+                     "schedule": schedule},
             "fp64": fp64,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
-                         "peak_source": pk["src"],
-                         "kernel": "k_spmm_short (Laplacian SpMM incl. polynomial-chain steps)",
-                         "traffic": profiled_traffic("spmm", args.workload)},
+                         "peak_source": pk["src"], "kernel": kernel_name,
+                         "algorithmic_bytes_per_launch": by_dt[dom]["bytes_per_launch"] if dom else None,
+                         "traffic": traffic},
             "cpu_baseline": cpu,
             "e2e": {"value": world / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes),
+                    "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + (0 if g.w is None else g.w.nbytes)),
                     "d2h_bytes_per_step": int(n * 4)},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
@@ -349,6 +378,9 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "mixed_bf16"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spmm-variant", default=None, choices=[None, "csr", "sell"],
+                    help="pin the short-row SpMM schedule instead of the one tuned at create "
+                         "(used for profiler captures, where tuning times are distorted)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":

@@ -122,13 +122,19 @@ typedef struct {
   double ms_mj;          /* embedding + multi-jagged (device events)               */
   double ms_eval;        /* cut and imbalance (device events)                      */
   double ms_spmm;        /* summed duration of the Laplacian SpMM launches         */
-  int64_t spmm_launches; /* Laplacian SpMM launches (short-row kernel)             */
+  int64_t spmm_launches; /* Laplacian SpMM launches                                 */
   double spmm_bytes;     /* algorithmic bytes of those launches                    */
   int64_t kernel_launches; /* all kernels this call launched                      */
   double cut;            /* Eq. 1                                                  */
   double cut_twice;      /* Eq. 1 counted from both endpoints (the paper's tables) */
   double imbalance;      /* max_k W_k / W_avg                                      */
-  double reserved[8];
+  /* the three SpMM figures above split by the precision of the input block,
+     indexed by SPHYNX_DT_F64, _F32, _BF16 (the BF16 entries are the
+     polynomial-chain steps of SPHYNX_MIXED_BF16)                               */
+  double ms_spmm_by_dt[3];
+  double spmm_bytes_by_dt[3];
+  int64_t spmm_launches_by_dt[3];
+  double reserved[4];
 } sphynx_stats;
 
 typedef struct {
@@ -144,6 +150,12 @@ typedef struct {
                                 1 = SELL-32                                         */
   float tuned_us_csr;        /* the two schedules' times for that product (us)    */
   float tuned_us_sell;
+  int64_t sell_slices;       /* SELL-32 slices (32 rows each)                      */
+  int64_t sell_narrow_slices;/* slices whose entries all lie within 32767 of their
+                                row, stored as 16-bit offsets instead of 32-bit
+                                column indices                                      */
+  double spmm_graph_bytes;   /* bytes of graph structure one product reads with the
+                                chosen schedule (indices, weights, row metadata)   */
 } sphynx_graph_info;
 
 /* Fill *opt with the defaults listed in sphynx_options. */

@@ -30,9 +30,10 @@ from .laplacian import (  # noqa: F401
     adjacency, weighted_degree, laplacian_combinatorial, laplacian_normalized,
     operator_for, b_diag_for, null_vector,
 )
-from .rng import splitmix64_block, poly_start_vector  # noqa: F401
+from .rng import splitmix64_block, poly_start_vector, reference_block  # noqa: F401
 from .precond import jacobi_diag, gmres_poly_roots, poly_apply, leja_order  # noqa: F401
 from .lobpcg import lobpcg, rayleigh_ritz, LobpcgResult  # noqa: F401
 from .mj import multijagged, coord_sort_key  # noqa: F401
 from .metrics import cutsize, imbalance, part_weights  # noqa: F401
-from .sphynx import partition, num_eigenvectors, initial_block  # noqa: F401
+from .sphynx import (partition, num_eigenvectors, initial_block, canonical_rotation, eigen_clusters,  # noqa: F401
+                     sign_normalise)

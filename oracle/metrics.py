@@ -38,7 +38,12 @@ def cutsize(g, parts: np.ndarray):
         return twice / 2, twice
     s = _exact_scale(g.w)
     ints = (g.w[diff].astype(np.float64) * 2.0 ** s).astype(np.int64)
-    total = int(np.sum(ints.astype(object)))
+    if ints.size == 0:
+        total = 0
+    elif int(ints.max()) * ints.size < 2 ** 62:
+        total = int(np.sum(ints, dtype=np.int64))      # exact: no partial sum can overflow
+    else:
+        total = int(np.sum(ints.astype(object)))
     return total / 2 ** (s + 1), total / 2 ** s
 
 

@@ -6,7 +6,9 @@ n x b initial block is 2u - 1 with u the (i*b + j + 1)-th output of a SplitMix64
 generator (Steele, Lea, Flood, OOPSLA 2014) whose state starts at
 mix(seed + gamma), mapped to [0, 1) by its top 53 bits.  The start vector of the
 polynomial preconditioner's Lanczos process (Sec. 5.2) uses the same rule with
-state mix(seed + 3 gamma) and counter i + 1.
+state mix(seed + 3 gamma) and counter i + 1, and the reference block that fixes
+the rotation of eigenvectors inside a cluster of equal Ritz values (see
+sphynx.canonical_rotation) uses state mix(seed + 5 gamma) and counter i*d + j + 1.
 
 This is written from the published generator definition, independently of the
 GPU library's copy; the tests check the two agree bit for bit.
@@ -50,6 +52,12 @@ def splitmix64_block(n: int, b: int, seed: int) -> np.ndarray:
     """The n x b random initial block of LOBPCG (row-major)."""
     state = mix64((seed + GAMMA) & MASK)
     return _stream(state, n * b).reshape(n, b)
+
+
+def reference_block(n: int, d: int, seed: int) -> np.ndarray:
+    """The n x d reference block of the embedding's cluster rotation."""
+    state = mix64((seed + 5 * GAMMA) & MASK)
+    return _stream(state, n * d).reshape(n, d)
 
 
 def poly_start_vector(n: int, seed: int) -> np.ndarray:

@@ -8,9 +8,11 @@
    eigenvector is dropped (Sec. 4);
 5. parts <- MJ(coords, weights, K) (Sec. 4).
 
-Readings where the paper is silent: the eigenvectors are sign-normalised
-before the embedding (entry of largest magnitude positive, first one on ties)
-so that the embedding is deterministic; K = 1 returns part 0 for every vertex
+Readings where the paper is silent: within each cluster of Ritz values
+closer than tol the eigenvectors are rotated to their orthogonal Procrustes
+alignment with a seeded reference block (canonical_rotation), and then every
+eigenvector is sign-normalised (entry of largest magnitude positive, first one
+on ties), so that the embedding is a function of the eigen-subspaces only; K = 1 returns part 0 for every vertex
 without an eigensolve; the piecewise-constant block puts the null vector
 (1, or D^{1/2} 1 for L_N) in column 0 and the indicators of index blocks
 [floor(j n / d), floor((j + 1) n / d)), j = 0..d-2, in columns 1..d-1.
@@ -28,7 +30,7 @@ from .lobpcg import lobpcg, U_FP64
 from .mj import multijagged
 from .metrics import cutsize, imbalance
 from .precond import jacobi_diag, gmres_poly_roots, poly_apply
-from .rng import splitmix64_block
+from .rng import reference_block, splitmix64_block
 
 
 def num_eigenvectors(num_parts: int) -> int:
@@ -48,6 +50,44 @@ def initial_block(g, problem: str, d: int, init: str, seed: int) -> np.ndarray:
             x[(j * g.n) // d:((j + 1) * g.n) // d, j + 1] = 1.0
         return x
     raise ValueError(init)
+
+
+def eigen_clusters(theta: np.ndarray, tol: float) -> list:
+    """Runs (a, b) of consecutive columns a..b (a >= 1: the eigenvalue-zero
+    column is never part of one) whose neighbouring Ritz values differ by at
+    most tol relative to the larger; runs of one column are not listed."""
+    out = []
+    j = 1
+    while j < len(theta):
+        k = j
+        while k + 1 < len(theta) and abs(theta[k + 1] - theta[k]) <= tol * max(abs(theta[k]), abs(theta[k + 1])):
+            k += 1
+        if k > j:
+            out.append((j, k))
+        j = k + 1
+    return out
+
+
+def canonical_rotation(e: np.ndarray, theta: np.ndarray, tol: float, seed: int) -> np.ndarray:
+    """Fix the basis of every cluster of Ritz values closer than tol.
+
+    Eigenvectors of (nearly) equal eigenvalues are determined only up to a
+    rotation within their span, and LOBPCG returns whichever rotation its
+    rounding led to; the multi-jagged cuts depend on it (a few percent of the
+    cut on the 27-point meshes, whose eigenvalues come in triples).  Within each
+    cluster the columns E_c are replaced by E_c Q, Q the orthogonal polar factor
+    of E_c^T Z_c: the rotation of the span closest to the seeded reference
+    block Z (orthogonal Procrustes).  The result depends on the span only."""
+    clusters = eigen_clusters(theta, tol)
+    if not clusters:
+        return e
+    e = e.copy()
+    z = reference_block(e.shape[0], e.shape[1], seed)
+    for a, b in clusters:
+        m = e[:, a:b + 1].T @ z[:, a:b + 1]
+        u, _, vt = np.linalg.svd(m)
+        e[:, a:b + 1] = e[:, a:b + 1] @ (u @ vt)
+    return e
 
 
 def sign_normalise(x: np.ndarray) -> np.ndarray:
@@ -110,7 +150,7 @@ def partition(g, num_parts: int, problem: str = COMBINATORIAL, precond: str = "j
         raise ValueError(precond)
     x0 = initial_block(g, problem, d, init, seed)
     res = lobpcg(apply_l, bdiag, apply_m, x0, tol, maxit, gershgorin_rho(g, problem), u_work)
-    e = sign_normalise(res.x)
+    e = sign_normalise(canonical_rotation(res.x, res.theta, tol, seed))
     coords = np.ascontiguousarray(e[:, 1:d])
     parts = multijagged(coords, vwts, num_parts)
     cut, cut2 = cutsize(g, parts)

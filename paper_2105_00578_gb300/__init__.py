@@ -50,7 +50,9 @@ class Stats(C.Structure):
                 ("ms_lobpcg", C.c_double), ("ms_mj", C.c_double), ("ms_eval", C.c_double),
                 ("ms_spmm", C.c_double), ("spmm_launches", C.c_int64), ("spmm_bytes", C.c_double),
                 ("kernel_launches", C.c_int64), ("cut", C.c_double), ("cut_twice", C.c_double),
-                ("imbalance", C.c_double), ("reserved", C.c_double * 8)]
+                ("imbalance", C.c_double),
+                ("ms_spmm_by_dt", C.c_double * 3), ("spmm_bytes_by_dt", C.c_double * 3),
+                ("spmm_launches_by_dt", C.c_int64 * 3), ("reserved", C.c_double * 4)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "eigenvalues", "resnorm")}
@@ -62,7 +64,8 @@ class Stats(C.Structure):
 class GraphInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("max_degree", C.c_int64), ("max_wdegree", C.c_double),
                 ("total_vweight", C.c_int64), ("long_rows", C.c_int64), ("weighted", C.c_int32),
-                ("spmm_variant", C.c_int32), ("tuned_us_csr", C.c_float), ("tuned_us_sell", C.c_float)]
+                ("spmm_variant", C.c_int32), ("tuned_us_csr", C.c_float), ("tuned_us_sell", C.c_float),
+                ("sell_slices", C.c_int64), ("sell_narrow_slices", C.c_int64), ("spmm_graph_bytes", C.c_double)]
 
 
 def _load():

@@ -1,0 +1,836 @@
+// batch.cu -- many graphs partitioned in one call.
+//
+// The graphs arrive as one block-diagonal CSR: graph q owns rows
+// [gptr[q], gptr[q + 1]) and its rows reference only columns inside that
+// range.  Each graph gets its own LOBPCG (Algorithm 1) with its own Ritz
+// values, convergence test and soft locking, its own embedding and its own
+// multi-jagged partition into K parts (Algorithm 2), exactly as if it were
+// partitioned alone.
+//
+// What acts row by row -- the Laplacian SpMM, the Jacobi scaling, the residual
+// -- runs over the whole batch with the single-graph kernels' arithmetic.
+// What reduces over rows -- the Gram matrices, the residual norms, the
+// embedding signs -- runs over chunks of at most kBatchChunk rows that never
+// straddle two graphs, followed by a per-graph reduction in a fixed order.
+// Rayleigh-Ritz and the convergence test run one CTA per graph.  A converged
+// graph drops out of every per-chunk kernel.
+//
+// The iteration body is captured once into a CUDA graph under a conditional
+// WHILE node whose condition a device kernel sets (some graph not done and
+// the cap not reached), so the whole batched eigensolve is one graph launch
+// with no host round trip between iterations.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace sphynx {
+
+namespace {
+
+constexpr int kBatchChunk = 1024;   // rows per chunk
+constexpr int kGramRows = 64;       // rows staged per step of the batched Gram kernel
+constexpr int kGramThreads = 256;
+
+int round4(int b) { return (b + 3) & ~3; }
+
+struct ChunkView {
+  const int32_t *graph;   // [n_chunks] graph of each chunk
+  const int64_t *begin;   // [n_chunks + 1] first row of each chunk (last entry: n)
+};
+
+__device__ __forceinline__ bool chunk_done(const SolverState *st, int q) { return st[q].done != 0; }
+
+// ---- initial block: the single-graph random block of every graph (local rows) ----
+template <typename T>
+__global__ void k_brandom(T *x, ChunkView cv, const int64_t *gptr, int b, int ld, uint64_t state) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  const int64_t r0 = cv.begin[c], r1 = cv.begin[c + 1], base = gptr[q];
+  for (int64_t e = r0 * ld + threadIdx.x; e < r1 * ld; e += blockDim.x) {
+    const int64_t i = e / ld;
+    const int j = static_cast<int>(e - i * ld);
+    double v = 0.0;
+    if (j < b) v = splitmix_pm1(state, static_cast<uint64_t>((i - base) * b + j + 1));
+    x[e] = static_cast<T>(v);
+  }
+}
+
+// ---- Gram matrices per chunk -------------------------------------------------
+// S = [X | H | P] (nb blocks of ld columns, M = nb * ld), LS likewise.  The
+// chunk's partial upper triangles of S^T L S and S^T B S go to
+// partials[chunk][2 * npairs] (A pairs first).  Rows are staged kGramRows at a
+// time; a thread owns pairs tid, tid + 256, ... and sums a staged block in the
+// block type, then adds it into FP64 accumulators.
+template <typename T, int PPT>
+__global__ void __launch_bounds__(kGramThreads)
+k_bgram(ChunkView cv, const SolverState *states, int nb, int ld, const T *s0, const T *s1, const T *s2,
+        const T *l0, const T *l1, const T *l2, const T *bdiag, double *partials) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int c = blockIdx.x, q = cv.graph[c];
+  if (chunk_done(states, q)) return;
+  const int M = nb * ld, npairs = M * (M + 1) / 2, ntot = 2 * npairs;
+  T *ss = reinterpret_cast<T *>(smraw);                     // [kGramRows][M]
+  T *sl = ss + kGramRows * M;                               // [kGramRows][M]
+  T *sd = sl + kGramRows * M;                               // [kGramRows] B diagonal
+  unsigned char *pi = reinterpret_cast<unsigned char *>(sd + kGramRows);   // pair -> (i, j)
+  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+    int i = 0, rem = p;
+    while (rem >= M - i) {
+      rem -= M - i;
+      ++i;
+    }
+    pi[2 * p] = static_cast<unsigned char>(i);
+    pi[2 * p + 1] = static_cast<unsigned char>(i + rem);
+  }
+  double acc[PPT];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) acc[k] = 0.0;
+  const T *sb[3] = {s0, s1, s2}, *lb[3] = {l0, l1, l2};
+  const int64_t r0 = cv.begin[c], r1 = cv.begin[c + 1];
+  for (int64_t rs = r0; rs < r1; rs += kGramRows) {
+    const int rows = static_cast<int>(r1 - rs < kGramRows ? r1 - rs : kGramRows);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * M; e += blockDim.x) {
+      const int r = e / M, col = e % M, blk = col / ld, k = col % ld;
+      const int64_t row = rs + r;
+      ss[e] = sb[blk][row * ld + k];
+      sl[e] = lb[blk][row * ld + k];
+    }
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) sd[r] = bdiag ? bdiag[rs + r] : T(1);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int p = threadIdx.x + k * kGramThreads;
+      if (p >= ntot) break;
+      const bool isb = p >= npairs;
+      const int pp = isb ? p - npairs : p;
+      const int i = pi[2 * pp], j = pi[2 * pp + 1];
+      T s = T(0);
+      if (isb) {
+        for (int r = 0; r < rows; ++r) s += ss[r * M + i] * (sd[r] * ss[r * M + j]);
+      } else {
+        for (int r = 0; r < rows; ++r) s += ss[r * M + i] * sl[r * M + j];
+      }
+      acc[k] += static_cast<double>(s);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int p = threadIdx.x + k * kGramThreads;
+    if (p < ntot) partials[static_cast<int64_t>(c) * ntot + p] = acc[k];
+  }
+}
+
+// per graph: G = sum over its chunks (in chunk order) of the partials, both
+// triangles written from the upper one
+__global__ void k_bgram_reduce(const int32_t *gchunk0, const SolverState *states, int M, const double *partials,
+                               double *ga, double *gb) {
+  const int q = blockIdx.x;
+  if (states[q].done) return;
+  const int npairs = M * (M + 1) / 2, ntot = 2 * npairs;
+  const int c0 = gchunk0[q], c1 = gchunk0[q + 1];
+  double *A = ga + static_cast<size_t>(q) * M * M, *B = gb + static_cast<size_t>(q) * M * M;
+  for (int p = threadIdx.x; p < ntot; p += blockDim.x) {
+    double s = 0.0;
+    for (int c = c0; c < c1; ++c) s += partials[static_cast<int64_t>(c) * ntot + p];
+    const bool isb = p >= npairs;
+    int rem = isb ? p - npairs : p, i = 0;
+    while (rem >= M - i) {
+      rem -= M - i;
+      ++i;
+    }
+    const int j = i + rem;
+    double *G = isb ? B : A;
+    G[i * M + j] = s;
+    G[j * M + i] = s;
+  }
+}
+
+// ---- update: X' = S Y, P' = [0 H P] Y, LP' = [0 LH LP] Y with each graph's Y ----
+template <typename T, int LD, int NBLK>
+__global__ void __launch_bounds__(256)
+k_bupdate(ChunkView cv, const SolverState *states, const T *s0, const T *s1, const T *s2, const T *l1,
+          const T *l2, const T *yall, T *xo, T *po, T *lpo) {
+  constexpr int M = NBLK * LD;
+  __shared__ T sy[M * LD];
+  const int c = blockIdx.x, q = cv.graph[c];
+  if (chunk_done(states, q)) return;
+  const T *y = yall + static_cast<size_t>(q) * M * LD;   // Rayleigh-Ritz wrote M x LD per graph
+  for (int i = threadIdx.x; i < M * LD; i += blockDim.x) sy[i] = y[i];
+  __syncthreads();
+  const T *srows[3] = {s0, s1, s2};
+  const T *lrows[3] = {nullptr, l1, l2};
+  for (int64_t row = cv.begin[c] + threadIdx.x; row < cv.begin[c + 1]; row += blockDim.x) {
+    T x[LD], p[LD], lp[LD];
+#pragma unroll
+    for (int k = 0; k < LD; ++k) {
+      x[k] = T(0);
+      p[k] = T(0);
+      lp[k] = T(0);
+    }
+#pragma unroll
+    for (int blk = 0; blk < NBLK; ++blk) {
+#pragma unroll 1
+      for (int k = 0; k < LD; ++k) {
+        const T v = srows[blk][row * LD + k];
+        const T lv = blk > 0 ? lrows[blk][row * LD + k] : T(0);
+        const T *yr = sy + (blk * LD + k) * LD;
+#pragma unroll
+        for (int cc = 0; cc < LD; ++cc) {
+          x[cc] += v * yr[cc];
+          if (blk > 0) {
+            p[cc] += v * yr[cc];
+            lp[cc] += lv * yr[cc];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < LD; ++k) xo[row * LD + k] = x[k];
+    if constexpr (NBLK == 3) {
+#pragma unroll
+      for (int k = 0; k < LD; ++k) {
+        po[row * LD + k] = p[k];
+        lpo[row * LD + k] = lp[k];
+      }
+    }
+  }
+}
+
+// ---- residual R = LX - B X Theta (times the Jacobi diagonal), per-chunk norms ----
+template <typename T, int LD>
+__global__ void __launch_bounds__(256)
+k_bresidual(ChunkView cv, const SolverState *states, const T *x, const T *lx, const T *bdiag, const T *jinv,
+            T *out, double *partials) {
+  __shared__ double red[8][LD];
+  const int c = blockIdx.x, q = cv.graph[c];
+  if (chunk_done(states, q)) return;
+  T th[LD];
+#pragma unroll
+  for (int k = 0; k < LD; ++k) th[k] = static_cast<T>(states[q].theta[k]);
+  T acc[LD];
+#pragma unroll
+  for (int k = 0; k < LD; ++k) acc[k] = T(0);
+  for (int64_t row = cv.begin[c] + threadIdx.x; row < cv.begin[c + 1]; row += blockDim.x) {
+    const T bi = bdiag ? bdiag[row] : T(1);
+    const T ib = bdiag ? T(1) / bi : T(1);
+    const T sc = jinv ? jinv[row] : T(1);
+#pragma unroll
+    for (int k = 0; k < LD; ++k) {
+      T r = lx[row * LD + k] - th[k] * (bi * x[row * LD + k]);
+      acc[k] += r * r * ib;
+      out[row * LD + k] = r * sc;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < LD; ++k) {
+    double v = static_cast<double>(acc[k]);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < LD) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+    partials[static_cast<int64_t>(c) * LD + threadIdx.x] = s;
+  }
+}
+
+// ---- convergence per graph (the single-graph test), and the loop condition ----
+// ctl[0]: graphs not done; ctl[1]: iterations of the batch loop
+__global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int count, const double *partials, int b,
+                            int ld, double tol, double floor_abs, int count_iteration, int maxit, int *ctl) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  SolverState *st = states + q;
+  if (st->done) return;
+  const int c0 = gchunk0[q], c1 = gchunk0[q + 1];
+  int nconv = 0;
+  for (int j = 0; j < b; ++j) {
+    double tot = 0.0;
+    for (int c = c0; c < c1; ++c) tot += partials[static_cast<int64_t>(c) * ld + j];
+    const double res = sqrt(tot);
+    st->resnorm[j] = res;
+    const double th = fabs(st->theta[j]);
+    const bool ok = (res <= tol * th) || (th <= floor_abs && res <= floor_abs);
+    st->conv[j] = ok ? 1 : 0;
+    nconv += ok ? 1 : 0;
+  }
+  st->nconv = nconv;
+  if (count_iteration) {
+    st->iters += 1;
+    st->pvalid = 1;
+  }
+  if (nconv == b) {
+    st->done = 1;
+    st->status = SPHYNX_OK;
+  } else if (st->iters >= maxit) {
+    st->done = 1;
+    st->status = SPHYNX_ERR_NOCONV;
+  }
+  if (st->done) atomicSub(&ctl[0], 1);
+}
+
+__global__ void k_bloop_condition(int *ctl, int maxit, cudaGraphConditionalHandle h) {
+  ctl[1] += 1;
+  cudaGraphSetConditional(h, (ctl[0] > 0 && ctl[1] < maxit) ? 1u : 0u);
+}
+
+// ---- embedding signs per graph and column: largest |x| positive (lowest row on ties) ----
+template <typename T>
+__global__ void k_bargmax(ChunkView cv, const T *x, int ld, int b, double *pval, int64_t *pidx) {
+  __shared__ double sv[256], svv[256];
+  __shared__ int64_t si[256];
+  const int c = blockIdx.x;
+  for (int col = 0; col < b; ++col) {
+    double best = -1.0, bestv = 0.0;
+    int64_t bidx = INT64_MAX;
+    for (int64_t row = cv.begin[c] + threadIdx.x; row < cv.begin[c + 1]; row += blockDim.x) {
+      const double v = static_cast<double>(x[row * ld + col]);
+      const double m = fabs(v);
+      if (m > best) {
+        best = m;
+        bestv = v;
+        bidx = row;
+      }
+    }
+    sv[threadIdx.x] = best;
+    svv[threadIdx.x] = bestv;
+    si[threadIdx.x] = bidx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        const double a = sv[threadIdx.x], o = sv[threadIdx.x + s];
+        const int64_t ia = si[threadIdx.x], io = si[threadIdx.x + s];
+        if (o > a || (o == a && io < ia)) {
+          sv[threadIdx.x] = o;
+          si[threadIdx.x] = io;
+          svv[threadIdx.x] = svv[threadIdx.x + s];
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      pval[(static_cast<int64_t>(c) * b + col) * 2] = sv[0];
+      pval[(static_cast<int64_t>(c) * b + col) * 2 + 1] = svv[0];
+      pidx[static_cast<int64_t>(c) * b + col] = si[0];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_bsigns(const int32_t *gchunk0, int count, int b, const double *pval, const int64_t *pidx,
+                         double *sign) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count * b) return;
+  const int q = t / b, col = t % b;
+  double best = -1.0, bestv = 0.0;
+  int64_t bidx = INT64_MAX;
+  for (int c = gchunk0[q]; c < gchunk0[q + 1]; ++c) {
+    const double m = pval[(static_cast<int64_t>(c) * b + col) * 2];
+    const int64_t i = pidx[static_cast<int64_t>(c) * b + col];
+    if (m > best || (m == best && i < bidx)) {
+      best = m;
+      bidx = i;
+      bestv = pval[(static_cast<int64_t>(c) * b + col) * 2 + 1];
+    }
+  }
+  sign[t] = bestv < 0.0 ? -1.0 : 1.0;
+}
+
+template <typename T>
+__global__ void k_bcoords(ChunkView cv, const T *x, int ld, int b, const double *sign, T *coords) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  const double *sg = sign + static_cast<size_t>(q) * b;
+  const int dims = b - 1;
+  for (int64_t e = cv.begin[c] * dims + threadIdx.x; e < cv.begin[c + 1] * dims; e += blockDim.x) {
+    const int64_t i = e / dims;
+    const int j = static_cast<int>(e - i * dims);
+    const T v = x[i * ld + j + 1];
+    coords[e] = sg[j + 1] < 0.0 ? -v : v;
+  }
+}
+
+// ---- parts back to local ids, cut and part weights per graph ------------------
+__global__ void __launch_bounds__(256)
+k_beval(ChunkView cv, const int64_t *rp, const int32_t *col, const float *w, const int64_t *vw, int32_t *part,
+        int K, int wscale, unsigned long long *cut2, long long *pw, unsigned *bad) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  unsigned long long acc = 0;
+  unsigned b = 0;
+  const int32_t off = q * K;
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x) {
+    const int32_t pi = part[i];
+    if (pi < off || pi >= off + K) {
+      b = 1;
+      continue;
+    }
+    const long long wv = vw ? vw[i] : 1;
+    atomicAdd(reinterpret_cast<unsigned long long *>(&pw[pi]), static_cast<unsigned long long>(wv));
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      if (part[col[e]] != pi) {
+        if (w) acc += static_cast<unsigned long long>(llrint(ldexp(static_cast<double>(w[e]), wscale)));
+        else acc += 1;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&cut2[q], acc);
+  if (b) atomicOr(bad, 1u);
+}
+
+// local part ids: part -= q K (after the cut, which compares global ids)
+__global__ void k_blocal(ChunkView cv, int32_t *part, int K) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x) part[i] -= q * K;
+}
+
+// every column of a graph's rows lies inside the graph's own row range
+__global__ void k_check_blocks(ChunkView cv, const int64_t *gptr, const int64_t *rp, const int32_t *col,
+                               unsigned *bad) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  const int64_t lo = gptr[q], hi = gptr[q + 1];
+  unsigned b = 0;
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x)
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+      if (col[e] < lo || col[e] >= hi) b = 1;
+  if (b) atomicOr(bad, 1u);
+}
+
+ChunkView view_of(const sphynx_graph *g) {
+  return ChunkView{g->batch.chunk_graph.as<int32_t>(), g->batch.chunk_begin.as<int64_t>()};
+}
+
+template <typename T>
+void launch_bgram_t(cudaStream_t st, const sphynx_graph *g, const SolverState *states, int nb, int ld,
+                    const void *const *s, const void *const *ls, const void *bdiag, double *partials) {
+  const int M = nb * ld, ntot = M * (M + 1);
+  const size_t sm = static_cast<size_t>(kGramRows) * (2 * M + 1) * sizeof(T) + static_cast<size_t>(ntot) + 16;
+  const unsigned grid = static_cast<unsigned>(g->batch.n_chunks);
+  const T *S[3] = {static_cast<const T *>(s[0]), static_cast<const T *>(s[1]), static_cast<const T *>(s[2])};
+  const T *LS[3] = {static_cast<const T *>(ls[0]), static_cast<const T *>(ls[1]), static_cast<const T *>(ls[2])};
+  const int ppt = (ntot + kGramThreads - 1) / kGramThreads;
+#define SPX_BGRAM(P)                                                                                       \
+  {                                                                                                        \
+    SPX_CUDA(cudaFuncSetAttribute(k_bgram<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                                  static_cast<int>(sm)));                                                  \
+    k_bgram<T, P><<<grid, kGramThreads, sm, st>>>(view_of(g), states, nb, ld, S[0], S[1], S[2], LS[0],    \
+                                                  LS[1], LS[2], static_cast<const T *>(bdiag), partials); \
+  }
+  if (ppt <= 1) SPX_BGRAM(1)
+  else if (ppt <= 2) SPX_BGRAM(2)
+  else if (ppt <= 4) SPX_BGRAM(4)
+  else if (ppt <= 10) SPX_BGRAM(10)
+  else fail(SPHYNX_ERR_UNSUPPORTED, "batched Gram: block width %d too large", M);
+#undef SPX_BGRAM
+  SPX_LAUNCHED();
+}
+
+template <typename T, int LD>
+void launch_bupdate_t(cudaStream_t st, const sphynx_graph *g, const SolverState *states, int nblk,
+                      const void *const *s, const void *const *ls, const void *y, void *xo, void *po, void *lpo) {
+  const unsigned grid = static_cast<unsigned>(g->batch.n_chunks);
+  const T *S[3] = {static_cast<const T *>(s[0]), static_cast<const T *>(s[1]), static_cast<const T *>(s[2])};
+  if (nblk == 1)
+    k_bupdate<T, LD, 1><<<grid, 256, 0, st>>>(view_of(g), states, S[0], nullptr, nullptr, nullptr, nullptr,
+                                              static_cast<const T *>(y), static_cast<T *>(xo), nullptr, nullptr);
+  else
+    k_bupdate<T, LD, 3><<<grid, 256, 0, st>>>(view_of(g), states, S[0], S[1], S[2],
+                                              static_cast<const T *>(ls[1]), static_cast<const T *>(ls[2]),
+                                              static_cast<const T *>(y), static_cast<T *>(xo), static_cast<T *>(po),
+                                              static_cast<T *>(lpo));
+  SPX_LAUNCHED();
+}
+
+template <typename T>
+void launch_bupdate_ld(cudaStream_t st, const sphynx_graph *g, const SolverState *states, int ld, int nblk,
+                       const void *const *s, const void *const *ls, const void *y, void *xo, void *po, void *lpo) {
+  switch (ld) {
+    case 4: launch_bupdate_t<T, 4>(st, g, states, nblk, s, ls, y, xo, po, lpo); break;
+    case 8: launch_bupdate_t<T, 8>(st, g, states, nblk, s, ls, y, xo, po, lpo); break;
+    case 12: launch_bupdate_t<T, 12>(st, g, states, nblk, s, ls, y, xo, po, lpo); break;
+    case 16: launch_bupdate_t<T, 16>(st, g, states, nblk, s, ls, y, xo, po, lpo); break;
+    default: fail(SPHYNX_ERR_UNSUPPORTED, "batched update: ld %d", ld);
+  }
+}
+
+template <typename T>
+void launch_bresidual_ld(cudaStream_t st, const sphynx_graph *g, const SolverState *states, int ld, const void *x,
+                         const void *lx, const void *bdiag, const void *jinv, void *out, double *partials) {
+  const unsigned grid = static_cast<unsigned>(g->batch.n_chunks);
+  const T *X = static_cast<const T *>(x), *LX = static_cast<const T *>(lx);
+  const T *B = static_cast<const T *>(bdiag), *J = static_cast<const T *>(jinv);
+  T *O = static_cast<T *>(out);
+  switch (ld) {
+    case 4: k_bresidual<T, 4><<<grid, 256, 0, st>>>(view_of(g), states, X, LX, B, J, O, partials); break;
+    case 8: k_bresidual<T, 8><<<grid, 256, 0, st>>>(view_of(g), states, X, LX, B, J, O, partials); break;
+    case 12: k_bresidual<T, 12><<<grid, 256, 0, st>>>(view_of(g), states, X, LX, B, J, O, partials); break;
+    case 16: k_bresidual<T, 16><<<grid, 256, 0, st>>>(view_of(g), states, X, LX, B, J, O, partials); break;
+    default: fail(SPHYNX_ERR_UNSUPPORTED, "batched residual: ld %d", ld);
+  }
+  SPX_LAUNCHED();
+}
+
+}  // namespace
+
+void batch_setup(sphynx_graph *g, const int64_t *h_gptr, int count) {
+  BatchInfo &B = g->batch;
+  B.count = count;
+  B.h_gptr.assign(h_gptr, h_gptr + count + 1);
+  std::vector<int32_t> cg;
+  std::vector<int64_t> cb;
+  std::vector<int32_t> c0(static_cast<size_t>(count) + 1);
+  for (int q = 0; q < count; ++q) {
+    c0[q] = static_cast<int32_t>(cg.size());
+    for (int64_t r = h_gptr[q]; r < h_gptr[q + 1]; r += kBatchChunk) {
+      cg.push_back(q);
+      cb.push_back(r);
+    }
+  }
+  c0[count] = static_cast<int32_t>(cg.size());
+  cb.push_back(g->n);
+  B.n_chunks = static_cast<int64_t>(cg.size());
+  B.gptr.alloc((count + 1) * sizeof(int64_t));
+  B.chunk_graph.alloc(cg.size() * sizeof(int32_t) + 4);
+  B.chunk_begin.alloc(cb.size() * sizeof(int64_t));
+  B.graph_chunk0.alloc(c0.size() * sizeof(int32_t));
+  SPX_CUDA(cudaMemcpyAsync(B.gptr.p, h_gptr, (count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
+  SPX_CUDA(cudaMemcpyAsync(B.chunk_graph.p, cg.data(), cg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+  SPX_CUDA(cudaMemcpyAsync(B.chunk_begin.p, cb.data(), cb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
+  SPX_CUDA(cudaMemcpyAsync(B.graph_chunk0.p, c0.data(), c0.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           g->stream));
+  DevBuf bad;
+  bad.alloc(sizeof(unsigned));
+  SPX_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), g->stream));
+  k_check_blocks<<<static_cast<unsigned>(B.n_chunks), 256, 0, g->stream>>>(view_of(g), B.gptr.as<int64_t>(),
+                                                                          g->rowptr, g->col, bad.as<unsigned>());
+  SPX_LAUNCHED();
+  unsigned hb = 0;
+  SPX_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(hb), cudaMemcpyDeviceToHost, g->stream));
+  SPX_CUDA(cudaStreamSynchronize(g->stream));
+  if (hb) fail(SPHYNX_ERR_INVALID_ARG, "a graph of the batch has an edge leaving its own vertex range");
+}
+
+// The batched partition: every graph's LOBPCG in one captured graph launch,
+// then the per-graph embedding, multi-jagged and metrics.
+void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *dpart, double *cuts, double *imbs,
+                     int32_t *iters, int32_t *status, sphynx_stats *stats) {
+  BatchInfo &B = g->batch;
+  const int count = B.count;
+  if (o->precond == SPHYNX_PRECOND_POLY)
+    fail(SPHYNX_ERR_UNSUPPORTED, "batched partitions take the Jacobi preconditioner or none");
+  if (o->init != SPHYNX_INIT_RANDOM) fail(SPHYNX_ERR_UNSUPPORTED, "batched partitions start from the random block");
+  for (int q = 0; q < count; ++q)
+    if (B.h_gptr[q + 1] - B.h_gptr[q] < 2) fail(SPHYNX_ERR_INVALID_ARG, "graph %d of the batch has < 2 vertices", q);
+  int d = 0;
+  while ((1LL << (d + 1)) <= K) ++d;
+  d += 1;                                       // Eq. 4
+  if (K == 1) {
+    SPX_CUDA(cudaMemsetAsync(dpart, 0, static_cast<size_t>(g->n) * 4, g->stream));
+    for (int q = 0; q < count; ++q) {
+      if (cuts) cuts[q] = 0.0;
+      if (imbs) imbs[q] = 1.0;
+      if (iters) iters[q] = 0;
+      if (status) status[q] = SPHYNX_OK;
+    }
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
+    return;
+  }
+  const int b = d;
+  if (b > SPHYNX_MAX_NEV) fail(SPHYNX_ERR_UNSUPPORTED, "K too large for %d eigenvectors", SPHYNX_MAX_NEV);
+  cudaStream_t st = g->stream;
+  const int64_t n = g->n;
+  const DT dt = o->precision == SPHYNX_FP64 ? DT::F64 : DT::F32;
+  const size_t es = dt_size(dt);
+  const int ld = round4(b), M3 = 3 * ld;
+  const int lap = o->laplacian == SPHYNX_NORMALIZED ? SPHYNX_NORMALIZED : SPHYNX_COMBINATORIAL;
+  const bool gen = o->laplacian == SPHYNX_GENERALIZED;
+  const double u_work = o->precision == SPHYNX_FP64 ? 0x1.0p-53 : 0x1.0p-24;
+  const double rho = lap == SPHYNX_COMBINATORIAL && !gen ? 2.0 * g->max_wdeg : 2.0;
+  const double floor_abs = 10.0 * u_work * rho;
+  const bool jac = o->precond == SPHYNX_PRECOND_JACOBI && lap == SPHYNX_COMBINATORIAL;
+  const size_t blk = static_cast<size_t>(n) * ld * es;
+  const int64_t nch = B.n_chunks;
+
+  void *X[2] = {g->workspace("X0", blk, false), g->workspace("X1", blk, false)};
+  void *LX[2] = {g->workspace("LX0", blk, false), g->workspace("LX1", blk, false)};
+  void *P[2] = {g->workspace("P0", blk, true), g->workspace("P1", blk, true)};
+  void *LP[2] = {g->workspace("LP0", blk, true), g->workspace("LP1", blk, true)};
+  void *H = g->workspace("H", blk, true);
+  void *LH = g->workspace("LH", blk, true);
+  const size_t ntot3 = static_cast<size_t>(M3) * (M3 + 1);
+  double *gpart = static_cast<double *>(g->workspace("bgram_part", static_cast<size_t>(nch) * ntot3 * 8, false));
+  double *ga = static_cast<double *>(g->workspace("bga", static_cast<size_t>(count) * M3 * M3 * 8, true));
+  double *gb = static_cast<double *>(g->workspace("bgb", static_cast<size_t>(count) * M3 * M3 * 8, true));
+  void *yt = g->workspace("byt", static_cast<size_t>(count) * M3 * ld * es, true);
+  double *npart = static_cast<double *>(g->workspace("bnpart", static_cast<size_t>(nch) * ld * 8, false));
+  SolverState *states =
+      static_cast<SolverState *>(g->workspace("bstates", static_cast<size_t>(count) * sizeof(SolverState), true));
+  int *ctl = static_cast<int *>(g->workspace("bctl", 4 * sizeof(int), false));
+  const void *bd = gen ? (dt == DT::F64 ? static_cast<const void *>(g->deg.p) : g->degf.p) : nullptr;
+  const void *jv = jac ? (dt == DT::F64 ? static_cast<const void *>(g->jinv.p) : g->jinvf.p) : nullptr;
+  const int mixed = o->precision != SPHYNX_FP64;
+  const int32_t *gc0 = B.graph_chunk0.as<int32_t>();
+  const unsigned cgrid = static_cast<unsigned>(nch);
+  const int hctl[4] = {count, 0, 0, 0};
+  SPX_CUDA(cudaMemcpyAsync(ctl, hctl, sizeof(hctl), cudaMemcpyHostToDevice, st));
+  const bool timing = g->ctr.timing;
+  g->ctr.timing = false;   // per-launch events cannot live inside a captured loop
+
+  auto gram = [&](int nb, const void *const *s, const void *const *ls) {
+    if (dt == DT::F64) launch_bgram_t<double>(st, g, states, nb, ld, s, ls, bd, gpart);
+    else launch_bgram_t<float>(st, g, states, nb, ld, s, ls, bd, gpart);
+    k_bgram_reduce<<<count, 256, 0, st>>>(gc0, states, nb * ld, gpart, ga, gb);
+    SPX_LAUNCHED();
+  };
+  auto update = [&](int nb, const void *const *s, const void *const *ls, void *xo, void *po, void *lpo) {
+    if (dt == DT::F64) launch_bupdate_ld<double>(st, g, states, ld, nb, s, ls, yt, xo, po, lpo);
+    else launch_bupdate_ld<float>(st, g, states, ld, nb, s, ls, yt, xo, po, lpo);
+  };
+  auto residual = [&](const void *x, const void *lx, void *out) {
+    if (dt == DT::F64) launch_bresidual_ld<double>(st, g, states, ld, x, lx, bd, jv, out, npart);
+    else launch_bresidual_ld<float>(st, g, states, ld, x, lx, bd, jv, out, npart);
+  };
+  auto converge = [&](int count_iteration) {
+    k_bconverge<<<(count + 127) / 128, 128, 0, st>>>(gc0, states, count, npart, b, ld, o->tol, floor_abs,
+                                                      count_iteration, o->max_iter, ctl);
+    SPX_LAUNCHED();
+  };
+  auto spmm_block = [&](const void *x, void *y) {
+    SpmmArgs a{};
+    a.lap = lap;
+    a.tin = dt;
+    a.ld_x = ld;
+    a.ld_y = ld;
+    a.bp = ld;
+    a.b_true = b;
+    a.x = x;
+    a.y = y;
+    a.mode = 0;
+    spmm(g, a);
+  };
+
+  // line 1: every graph's random block on its local rows; lines 2-3
+  if (dt == DT::F64)
+    k_brandom<double><<<cgrid, 256, 0, st>>>(static_cast<double *>(X[0]), view_of(g), B.gptr.as<int64_t>(), b, ld,
+                                             mix64(o->seed + kGamma));
+  else
+    k_brandom<float><<<cgrid, 256, 0, st>>>(static_cast<float *>(X[0]), view_of(g), B.gptr.as<int64_t>(), b, ld,
+                                            mix64(o->seed + kGamma));
+  SPX_LAUNCHED();
+  spmm_block(X[0], LX[0]);
+  {
+    // the first Rayleigh-Ritz: ld x ld problems per graph, back to back
+    const void *s1[3] = {X[0], X[0], X[0]}, *l1[3] = {LX[0], LX[0], LX[0]};
+    gram(1, s1, l1);
+  }
+  launch_rayleigh_ritz(st, ga, gb, ld, ld, b, u_work, states, nullptr, yt, dt, nullptr, nullptr, nullptr, mixed,
+                       count);
+  {
+    const void *s1[3] = {X[0], nullptr, nullptr}, *l1[3] = {nullptr, nullptr, nullptr};
+    update(1, s1, l1, X[1], nullptr, nullptr);
+  }
+  spmm_block(X[1], LX[1]);
+  residual(X[1], LX[1], H);
+  converge(0);
+  SPX_CUDA(cudaStreamSynchronize(st));
+
+  // the iteration body, captured once and repeated by a conditional WHILE node
+  // (two bodies, one per ping-pong parity, so that a body is a fixed sequence)
+  cudaGraph_t graph;
+  SPX_CUDA(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  SPX_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  SPX_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs;
+  SPX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = g->stream;
+  g->stream = cs;
+  st = cs;
+  try {
+    SPX_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    for (int half = 0; half < 2; ++half) {   // X[1] -> X[0] -> X[1]: two iterations per body
+      const int cur = half == 0 ? 1 : 0, nx = cur ^ 1;
+      spmm_block(H, LH);
+      const void *s3[3] = {X[cur], H, P[cur]}, *l3[3] = {LX[cur], LH, LP[cur]};
+      gram(3, s3, l3);
+      launch_rayleigh_ritz(st, ga, gb, M3, ld, b, u_work, states, nullptr, yt, dt, nullptr, nullptr, nullptr, mixed,
+                           count);
+      update(3, s3, l3, X[nx], P[nx], LP[nx]);
+      spmm_block(X[nx], LX[nx]);
+      residual(X[nx], LX[nx], H);
+      converge(1);
+    }
+    k_bloop_condition<<<1, 1, 0, cs>>>(ctl, (o->max_iter + 1) / 2, cond);
+    SPX_LAUNCHED();
+    cudaGraph_t captured = nullptr;
+    SPX_CUDA(cudaStreamEndCapture(cs, &captured));
+  } catch (...) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(cs, &junk);
+    g->stream = saved;
+    cudaStreamDestroy(cs);
+    cudaGraphDestroy(graph);
+    throw;
+  }
+  g->stream = saved;
+  st = saved;
+  cudaGraphExec_t exec;
+  SPX_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  // the whole batched eigensolve: one launch
+  SPX_CUDA(cudaGraphLaunch(exec, st));
+  SPX_CUDA(cudaStreamSynchronize(st));
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  g->ctr.timing = timing;
+
+  // per-graph results; a graph's Ritz vectors are in X[(1 + iters) & 1]
+  std::vector<SolverState> hs(count);
+  SPX_CUDA(cudaMemcpyAsync(hs.data(), states, count * sizeof(SolverState), cudaMemcpyDeviceToHost, st));
+  SPX_CUDA(cudaStreamSynchronize(st));
+  // bring every graph's vectors into X[0] (rows of graphs that ended on X[1] copied over)
+  for (int q = 0; q < count; ++q) {
+    if (((1 + hs[q].iters) & 1) == 1) {
+      const size_t off = static_cast<size_t>(B.h_gptr[q]) * ld * es;
+      const size_t bytes = static_cast<size_t>(B.h_gptr[q + 1] - B.h_gptr[q]) * ld * es;
+      SPX_CUDA(cudaMemcpyAsync(static_cast<char *>(X[0]) + off, static_cast<const char *>(X[1]) + off, bytes,
+                               cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  for (int q = 0; q < count; ++q) {
+    const int64_t r0 = B.h_gptr[q], rows = B.h_gptr[q + 1] - r0;
+    canonical_rotation_block(g, static_cast<char *>(X[0]) + static_cast<size_t>(r0) * ld * es, rows, ld, dt,
+                             hs[q].theta, d, o->tol, o->seed);
+  }
+  // embedding (Algorithm 2 lines 6-10), signs per graph
+  double *pval = static_cast<double *>(g->workspace("bsg_val", static_cast<size_t>(nch) * b * 2 * 8, false));
+  int64_t *pidx = static_cast<int64_t *>(g->workspace("bsg_idx", static_cast<size_t>(nch) * b * 8, false));
+  double *sign = static_cast<double *>(g->workspace("bsg", static_cast<size_t>(count) * b * 8, false));
+  void *coords = g->workspace("coords", static_cast<size_t>(n) * (d - 1) * es + 16, false);
+  if (dt == DT::F64) k_bargmax<double><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const double *>(X[0]), ld, b, pval, pidx);
+  else k_bargmax<float><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const float *>(X[0]), ld, b, pval, pidx);
+  SPX_LAUNCHED();
+  k_bsigns<<<(count * b + 255) / 256, 256, 0, st>>>(gc0, count, b, pval, pidx, sign);
+  SPX_LAUNCHED();
+  if (dt == DT::F64)
+    k_bcoords<double><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const double *>(X[0]), ld, b, sign,
+                                             static_cast<double *>(coords));
+  else
+    k_bcoords<float><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const float *>(X[0]), ld, b, sign,
+                                            static_cast<float *>(coords));
+  SPX_LAUNCHED();
+  // multi-jagged over all graphs at once: graph q owns parts [q K, (q + 1) K)
+  const int ktot = count * K;
+  void *mjs = g->workspace("mj", mj_scratch_bytes(n, ktot, count), false);
+  run_mj_scratch(st, dt, coords, d - 1, d - 1, n, g->vw, ktot, dpart, &g->ctr, mjs, B.h_gptr.data(), count);
+  // metrics per graph
+  if (g->weighted && !g->wexact)
+    fail(SPHYNX_ERR_UNSUPPORTED, "edge weights span too many binary orders for an exact cut");
+  const size_t need = 64 + static_cast<size_t>(count) * 8 + static_cast<size_t>(ktot) * 8;
+  char *ws = static_cast<char *>(g->workspace("beval", need, false));
+  SPX_CUDA(cudaMemsetAsync(ws, 0, need, st));
+  unsigned *dbad = reinterpret_cast<unsigned *>(ws);
+  unsigned long long *dcut = reinterpret_cast<unsigned long long *>(ws + 64);
+  long long *dpw = reinterpret_cast<long long *>(ws + 64 + static_cast<size_t>(count) * 8);
+  k_beval<<<cgrid, 256, 0, st>>>(view_of(g), g->rowptr, g->col, g->w, g->vw, dpart, K, g->wscale, dcut, dpw, dbad);
+  SPX_LAUNCHED();
+  k_blocal<<<cgrid, 256, 0, st>>>(view_of(g), dpart, K);
+  SPX_LAUNCHED();
+  std::vector<char> host(need);
+  SPX_CUDA(cudaMemcpyAsync(host.data(), ws, need, cudaMemcpyDeviceToHost, st));
+  SPX_CUDA(cudaStreamSynchronize(st));
+  unsigned hbad;
+  memcpy(&hbad, host.data(), sizeof(hbad));
+  if (hbad) fail(SPHYNX_ERR_INVALID_ARG, "batched multi-jagged produced a part outside its graph");
+  const unsigned long long *hcut = reinterpret_cast<const unsigned long long *>(host.data() + 64);
+  const long long *hpw = reinterpret_cast<const long long *>(host.data() + 64 + static_cast<size_t>(count) * 8);
+  int nconv_graphs = 0;
+  for (int q = 0; q < count; ++q) {
+    long long mx = 0, tot = 0;
+    for (int k = 0; k < K; ++k) {
+      const long long v = hpw[static_cast<size_t>(q) * K + k];
+      mx = v > mx ? v : mx;
+      tot += v;
+    }
+    if (cuts) cuts[q] = ldexp(static_cast<double>(hcut[q]), g->weighted ? -(g->wscale + 1) : -1);
+    if (imbs) imbs[q] = (static_cast<double>(mx) * static_cast<double>(K)) / static_cast<double>(tot);
+    if (iters) iters[q] = hs[q].iters;
+    const int sq = hs[q].done ? hs[q].status : SPHYNX_ERR_NOCONV;
+    if (status) status[q] = sq;
+    nconv_graphs += sq == SPHYNX_OK ? 1 : 0;
+  }
+  if (stats) {
+    int maxit = 0;
+    for (int q = 0; q < count; ++q) maxit = std::max(maxit, hs[q].iters);
+    stats->status = nconv_graphs == count ? SPHYNX_OK : SPHYNX_ERR_NOCONV;
+    stats->iterations = maxit;
+    stats->nev = b;
+  }
+}
+
+}  // namespace sphynx
+
+using namespace sphynx;
+
+extern "C" int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, const float *edge_w,
+                                   const int64_t *vtx_w, const int64_t *graph_ptr, int32_t count, int64_t n,
+                                   int64_t nnz, uint32_t flags, void *stream, sphynx_handle *out) {
+  return guarded([&]() -> int {
+    if (!out) fail(SPHYNX_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!graph_ptr || count < 1) fail(SPHYNX_ERR_INVALID_ARG, "graph offsets missing or count < 1");
+    if (graph_ptr[0] != 0 || graph_ptr[count] != n) fail(SPHYNX_ERR_INVALID_ARG, "graph offsets must span [0, n)");
+    for (int q = 0; q < count; ++q)
+      if (graph_ptr[q + 1] <= graph_ptr[q]) fail(SPHYNX_ERR_INVALID_ARG, "graph %d of the batch is empty", q);
+    sphynx_handle h = nullptr;
+    const int rc = sphynx_create(row_ptr, col, edge_w, vtx_w, n, nnz, flags, stream, &h);
+    if (rc != SPHYNX_OK) return rc;
+    try {
+      batch_setup(h, graph_ptr, count);
+    } catch (...) {
+      sphynx_destroy(h);
+      throw;
+    }
+    *out = h;
+    return SPHYNX_OK;
+  });
+}
+
+extern "C" int sphynx_partition_batch(sphynx_handle g, int32_t K, const sphynx_options *opt, int32_t *part_out,
+                                      double *cuts, double *imbalances, int32_t *iterations, int32_t *status,
+                                      sphynx_stats *stats) {
+  return guarded([&]() -> int {
+    if (!g || !part_out || !opt) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
+    if (g->batch.count < 1) fail(SPHYNX_ERR_INVALID_ARG, "the handle is not a batch (use sphynx_create_batch)");
+    if (K < 1) fail(SPHYNX_ERR_INVALID_ARG, "K must be >= 1");
+    if (static_cast<int64_t>(K) * g->batch.count > (1 << 20)) fail(SPHYNX_ERR_UNSUPPORTED, "K x graphs > 2^20");
+    check_lobpcg_options(g, opt);
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool dev_out = (opt->flags & SPHYNX_OUT_DEVICE) != 0;
+    int32_t *dpart = dev_out ? part_out
+                             : static_cast<int32_t *>(g->workspace("part", static_cast<size_t>(g->n) * 4, false));
+    if (stats) memset(stats, 0, sizeof(*stats));
+    g->ctr.launches = 0;
+    batch_partition(g, K, opt, dpart, cuts, imbalances, iterations, status, stats);
+    if (!dev_out)
+      SPX_CUDA(cudaMemcpyAsync(part_out, dpart, static_cast<size_t>(g->n) * 4, cudaMemcpyDeviceToHost, g->stream));
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
+    if (stats) {
+      stats->kernel_launches = g->ctr.launches;
+      stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return SPHYNX_OK;
+  });
+}

@@ -13,20 +13,6 @@ namespace sphynx {
 
 namespace {
 
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
-
-__host__ __device__ inline uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  return z ^ (z >> 31);
-}
-
-// u in [0,1) from the top 53 bits, then 2u - 1 (exact in double)
-__device__ inline double splitmix_pm1(uint64_t state, uint64_t ctr) {
-  const uint64_t z = mix64(state + ctr * kGamma);
-  return 2.0 * (static_cast<double>(z >> 11) * 0x1.0p-53) - 1.0;
-}
-
 template <typename T> __device__ inline T from_d(double v) { return static_cast<T>(v); }
 
 // LD consecutive values (16-byte aligned) in 16-byte pieces
@@ -325,31 +311,83 @@ __global__ void k_coords(const T *x, int64_t n, int ld, int b, const double *sig
 }
 
 // ---------------------------------------------------------------------------
-// Lanczos helpers (Sec. 5.2 setup): basis V is row-major n x ldv.
+// Lanczos helpers (Sec. 5.2 setup).  The basis V is column-major: column c
+// starts at basis + c * ldv, with ldv a multiple of 4 so that every column is
+// 16-byte aligned.  Threads take rows four at a time (one vector load per
+// column); the n mod 4 tail rows go to the first threads of block 0.
+__device__ __forceinline__ void ld4(const float *p, float (&o)[4]) {
+  const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&o)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+// coherent loads / stores for the vector a kernel updates in place
+__device__ __forceinline__ void ld4_rw(const float *p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4_rw(const double *p, double (&o)[4]) {
+  const double2 a = *reinterpret_cast<const double2 *>(p);
+  const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&v)[4]) {
+  *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+}
+
+constexpr int kLzCols = 8;   // basis columns per block of the dot-product kernel
+
+// partials[block][c] = sum over the block's rows of V[:, c] . w, for the
+// kLzCols columns c0 .. c0 + 7 (c < j1) of blockIdx.y; 256 threads per block.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_lanczos_dots(const T *basis, int ldv, int j1, const T *w, int64_t n, double *partials) {
-  // blockDim (32, 8): x = column lane, y = row stripe
-  __shared__ double red[8][64];
-  using TA = T;
-  TA acc0 = 0, acc1 = 0;
-  const int c0 = threadIdx.x, c1 = threadIdx.x + 32;
-  for (int64_t row = blockIdx.x * 8LL + threadIdx.y; row < n; row += static_cast<int64_t>(gridDim.x) * 8) {
-    const TA wv = w[row];
-    if (c0 < j1) acc0 += basis[row * ldv + c0] * wv;
-    if (c1 < j1) acc1 += basis[row * ldv + c1] * wv;
-  }
-  red[threadIdx.y][c0] = static_cast<double>(acc0);
-  red[threadIdx.y][c1] = static_cast<double>(acc1);
-  __syncthreads();
-  if (threadIdx.y == 0) {
-    for (int c = c0; c < 64; c += 32) {
-      if (c < j1) {
-        double s = 0.0;
-        for (int y = 0; y < 8; ++y) s += red[y][c];
-        partials[static_cast<int64_t>(blockIdx.x) * j1 + c] = s;
+k_lanczos_dots(const T *basis, int64_t ldv, int j1, const T *w, int64_t n, double *partials) {
+  __shared__ double red[kLzCols][8];
+  const int c0 = blockIdx.y * kLzCols;
+  T acc[kLzCols];
+#pragma unroll
+  for (int c = 0; c < kLzCols; ++c) acc[c] = T(0);
+  const int64_t nq = n >> 2;
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < nq;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    T wv[4];
+    ld4(w + 4 * q, wv);
+#pragma unroll
+    for (int c = 0; c < kLzCols; ++c) {
+      if (c0 + c < j1) {
+        T vv[4];
+        ld4(basis + static_cast<int64_t>(c0 + c) * ldv + 4 * q, vv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[c] = fma(vv[i], wv[i], acc[c]);
       }
     }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+    const int64_t r = (nq << 2) + threadIdx.x;
+    const T wv = w[r];
+#pragma unroll
+    for (int c = 0; c < kLzCols; ++c)
+      if (c0 + c < j1) acc[c] = fma(basis[static_cast<int64_t>(c0 + c) * ldv + r], wv, acc[c]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < kLzCols; ++c) {
+    double d = static_cast<double>(acc[c]);
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+    if (lane == 0) red[c][warp] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x < kLzCols && c0 + static_cast<int>(threadIdx.x) < j1) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += red[threadIdx.x][k];
+    partials[static_cast<int64_t>(blockIdx.x) * j1 + c0 + threadIdx.x] = s;
   }
 }
 
@@ -367,19 +405,37 @@ __global__ void k_reduce_cols(const double *partials, int grid, int cols, double
   if (threadIdx.x == 0) out[c] = red[0];
 }
 
+// w <- w - V[:, :j1] h, and npart[block] = the block's part of ||w||^2.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_lanczos_sub(const T *basis, int ldv, int j1, T *w, int64_t n, const double *h, double *npart) {
+k_lanczos_sub(const T *basis, int64_t ldv, int j1, T *w, int64_t n, const double *h, double *npart) {
   __shared__ T sh[SPHYNX_MAX_POLY_DEGREE + 1];
   __shared__ double red[8];
   for (int c = threadIdx.x; c < j1; c += blockDim.x) sh[c] = static_cast<T>(h[c]);
   __syncthreads();
   T acc = 0;
-  for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < n;
-       row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    T v = w[row];
-    for (int c = 0; c < j1; ++c) v -= basis[row * ldv + c] * sh[c];
-    w[row] = v;
+  const int64_t nq = n >> 2;
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < nq;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    T v[4];
+    ld4_rw(w + 4 * q, v);
+#pragma unroll 4
+    for (int c = 0; c < j1; ++c) {
+      T b[4];
+      ld4(basis + static_cast<int64_t>(c) * ldv + 4 * q, b);
+      const T hc = sh[c];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] -= b[i] * hc;
+    }
+    st4(w + 4 * q, v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc += v[i] * v[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+    const int64_t r = (nq << 2) + threadIdx.x;
+    T v = w[r];
+    for (int c = 0; c < j1; ++c) v -= basis[static_cast<int64_t>(c) * ldv + r] * sh[c];
+    w[r] = v;
     acc += v * v;
   }
   double d = static_cast<double>(acc);
@@ -393,14 +449,16 @@ k_lanczos_sub(const T *basis, int ldv, int j1, T *w, int64_t n, const double *h,
   }
 }
 
+// v = w / beta and V[:, j] = v
 template <typename T>
-__global__ void k_lanczos_next(const T *w, T *v, T *basis, int ldv, int j, int64_t n, const double *beta2) {
+__global__ void k_lanczos_next(const T *w, T *v, T *basis, int64_t ldv, int j, int64_t n, const double *beta2) {
   const T inv = static_cast<T>(1.0 / sqrt(*beta2));
+  T *col = basis + static_cast<int64_t>(j) * ldv;
   for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < n;
        row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const T val = w[row] * inv;
     v[row] = val;
-    basis[row * ldv + j] = val;
+    col[row] = val;
   }
 }
 
@@ -444,6 +502,75 @@ __global__ void k_null_axpy(T *v, int64_t n, int lap, const double *deg, const d
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const double z = lap == SPHYNX_NORMALIZED ? sqrt(deg[i]) : 1.0;
     v[i] = static_cast<T>(static_cast<double>(v[i]) - f * z);
+  }
+}
+
+// ---- canonical rotation of a cluster of eigenvectors (embedding) ----------
+// Row p of M = E_c^T Z_c for the cluster columns a .. a + c - 1, with Z the
+// seeded reference block (entry (i, j): draw i * d + j + 1 of the stream that
+// starts at `state`): partials[block][q] = the block's part of
+// sum_i E[i, a + p] Z[i, a + q], q < c.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_cluster_dots(const T *x, int64_t n, int ld, int d, int a, int c, int p, uint64_t state, double *partials) {
+  __shared__ double red[8][SPHYNX_MAX_NEV];
+  double acc[SPHYNX_MAX_NEV];
+#pragma unroll
+  for (int q = 0; q < SPHYNX_MAX_NEV; ++q) acc[q] = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double xv = static_cast<double>(x[i * ld + a + p]);
+    const uint64_t base = static_cast<uint64_t>(i) * d + a + 1;
+#pragma unroll
+    for (int q = 0; q < SPHYNX_MAX_NEV; ++q)
+      if (q < c) acc[q] += xv * splitmix_pm1(state, base + q);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < SPHYNX_MAX_NEV; ++q) {
+    if (q >= c) break;
+    double v = acc[q];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < c) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+    partials[static_cast<int64_t>(blockIdx.x) * c + threadIdx.x] = s;
+  }
+}
+
+// E_c <- E_c Q (Q row-major c x c) for the cluster columns a .. a + c - 1
+template <typename T>
+__global__ void k_rotate_cols(T *x, int64_t n, int ld, int a, int c, const double *q) {
+  __shared__ double sq[SPHYNX_MAX_NEV * SPHYNX_MAX_NEV];
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) sq[e] = q[e];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double v[SPHYNX_MAX_NEV];
+#pragma unroll
+    for (int p = 0; p < SPHYNX_MAX_NEV; ++p)
+      if (p < c) v[p] = static_cast<double>(x[i * ld + a + p]);
+#pragma unroll
+    for (int k = 0; k < SPHYNX_MAX_NEV; ++k) {
+      if (k >= c) break;
+      double y = 0.0;
+      for (int p = 0; p < c; ++p) y += v[p] * sq[p * c + k];
+      x[i * ld + a + k] = static_cast<T>(y);
+    }
+  }
+}
+
+// col = z / ||z|| with z the null vector (1, or sqrt(deg) for L_N); scal[1] = z . z
+template <typename T>
+__global__ void k_null_column(T *col, int64_t n, int lap, const double *deg, const double *scal) {
+  const double f = 1.0 / sqrt(scal[1]);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double z = lap == SPHYNX_NORMALIZED ? sqrt(deg[i]) : 1.0;
+    col[i] = static_cast<T>(z * f);
   }
 }
 
@@ -608,15 +735,17 @@ void launch_signs_coords(cudaStream_t st, DT dt, const void *x, int64_t n, int l
   }
 }
 
-void launch_lanczos_dots(cudaStream_t st, DT dt, const void *basis, int ldv, int j1, const void *w,
+void launch_lanczos_dots(cudaStream_t st, DT dt, const void *basis, int64_t ldv, int j1, const void *w,
                          int64_t n, double *partials, int grid) {
-  dim3 blk(32, 8);
+  if (ldv % 4 || reinterpret_cast<uintptr_t>(basis) % 32 || reinterpret_cast<uintptr_t>(w) % 32)
+    fail(SPHYNX_ERR_INVALID_ARG, "Lanczos basis columns must be 32-byte aligned");
+  const dim3 g(static_cast<unsigned>(grid), static_cast<unsigned>((j1 + kLzCols - 1) / kLzCols));
   if (dt == DT::F64)
-    k_lanczos_dots<double><<<grid, blk, 0, st>>>(static_cast<const double *>(basis), ldv, j1,
-                                                 static_cast<const double *>(w), n, partials);
+    k_lanczos_dots<double><<<g, 256, 0, st>>>(static_cast<const double *>(basis), ldv, j1,
+                                              static_cast<const double *>(w), n, partials);
   else
-    k_lanczos_dots<float><<<grid, blk, 0, st>>>(static_cast<const float *>(basis), ldv, j1,
-                                                static_cast<const float *>(w), n, partials);
+    k_lanczos_dots<float><<<g, 256, 0, st>>>(static_cast<const float *>(basis), ldv, j1,
+                                             static_cast<const float *>(w), n, partials);
   SPX_LAUNCHED();
 }
 
@@ -625,8 +754,10 @@ void launch_reduce_cols(cudaStream_t st, const double *partials, int grid, int c
   SPX_LAUNCHED();
 }
 
-void launch_lanczos_sub(cudaStream_t st, DT dt, const void *basis, int ldv, int j1, void *w, int64_t n,
+void launch_lanczos_sub(cudaStream_t st, DT dt, const void *basis, int64_t ldv, int j1, void *w, int64_t n,
                         const double *h, double *norm_partials, int grid) {
+  if (ldv % 4 || reinterpret_cast<uintptr_t>(basis) % 32 || reinterpret_cast<uintptr_t>(w) % 32)
+    fail(SPHYNX_ERR_INVALID_ARG, "Lanczos basis columns must be 32-byte aligned");
   if (dt == DT::F64)
     k_lanczos_sub<double><<<grid, 256, 0, st>>>(static_cast<const double *>(basis), ldv, j1,
                                                 static_cast<double *>(w), n, h, norm_partials);
@@ -636,7 +767,7 @@ void launch_lanczos_sub(cudaStream_t st, DT dt, const void *basis, int ldv, int 
   SPX_LAUNCHED();
 }
 
-void launch_lanczos_next(cudaStream_t st, DT dt, const void *w, void *v, void *basis, int ldv, int j,
+void launch_lanczos_next(cudaStream_t st, DT dt, const void *w, void *v, void *basis, int64_t ldv, int j,
                          int64_t n, const double *beta2) {
   const int g = vec_grid(n);
   if (dt == DT::F64)
@@ -667,6 +798,34 @@ void launch_project_null(cudaStream_t st, DT dt, void *v, int64_t n, int lap, co
   SPX_LAUNCHED();
   if (dt == DT::F64) k_null_axpy<double><<<grid, 256, 0, st>>>(static_cast<double *>(v), n, lap, deg, scal);
   else k_null_axpy<float><<<grid, 256, 0, st>>>(static_cast<float *>(v), n, lap, deg, scal);
+  SPX_LAUNCHED();
+}
+
+void launch_cluster_dots(cudaStream_t st, DT dt, const void *x, int64_t n, int ld, int d, int a, int c, int p,
+                         uint64_t seed, double *partials, int grid) {
+  if (c < 1 || c > SPHYNX_MAX_NEV || a < 0 || a + c > ld || p < 0 || p >= c)
+    fail(SPHYNX_ERR_INVALID_ARG, "cluster columns out of range");
+  const uint64_t state = mix64(seed + 5 * kGamma);
+  if (dt == DT::F64)
+    k_cluster_dots<double><<<grid, 256, 0, st>>>(static_cast<const double *>(x), n, ld, d, a, c, p, state, partials);
+  else
+    k_cluster_dots<float><<<grid, 256, 0, st>>>(static_cast<const float *>(x), n, ld, d, a, c, p, state, partials);
+  SPX_LAUNCHED();
+}
+
+void launch_rotate_cols(cudaStream_t st, DT dt, void *x, int64_t n, int ld, int a, int c, const double *q) {
+  if (c < 1 || c > SPHYNX_MAX_NEV || a < 0 || a + c > ld) fail(SPHYNX_ERR_INVALID_ARG, "cluster columns out of range");
+  const int g = vec_grid(n);
+  if (dt == DT::F64) k_rotate_cols<double><<<g, 256, 0, st>>>(static_cast<double *>(x), n, ld, a, c, q);
+  else k_rotate_cols<float><<<g, 256, 0, st>>>(static_cast<float *>(x), n, ld, a, c, q);
+  SPX_LAUNCHED();
+}
+
+void launch_null_column(cudaStream_t st, DT dt, void *col, int64_t n, int lap, const double *deg,
+                        const double *scal) {
+  const int g = vec_grid(n);
+  if (dt == DT::F64) k_null_column<double><<<g, 256, 0, st>>>(static_cast<double *>(col), n, lap, deg, scal);
+  else k_null_column<float><<<g, 256, 0, st>>>(static_cast<float *>(col), n, lap, deg, scal);
   SPX_LAUNCHED();
 }
 

@@ -226,30 +226,59 @@ k_eval(const int64_t *rp, const int32_t *col, const float *w, const int64_t *vw,
 
 // SELL-32 layout of the short rows: per-row degree (0xFF marks a long row)
 // and, per 32-row slice, the largest short degree
-__global__ void k_sell_deg(const int64_t *rp, int64_t n, uint8_t *sdeg, int *smax) {
+// Per slice of 32 rows: the largest short-row degree, the number of
+// short-row entries, and whether every such entry lies within 32767 of its row
+// (then the slice stores 16-bit offsets).  Blocks are whole warps.
+__global__ void k_sell_deg(const int64_t *rp, const int32_t *col, int64_t n, uint8_t *sdeg, int *smax, int *ssum,
+                           int *sfit) {
   const int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   int d = 0, sd = 0xFF;
+  bool fit = true;
   if (row < n) {
     const int64_t dd = rp[row + 1] - rp[row];
     d = dd > (1 << 30) ? (1 << 30) : static_cast<int>(dd);
     sd = d > kShortDeg ? 0xFF : d;
     sdeg[row] = static_cast<uint8_t>(sd);
+    if (sd != 0xFF) {
+      const int64_t b = rp[row];
+      for (int t = 0; t < d; ++t) {
+        const int64_t off = static_cast<int64_t>(col[b + t]) - row;
+        fit = fit && off >= -32768 && off <= 32767;
+      }
+    }
   }
   int m = sd == 0xFF ? 0 : d;
-  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, off));
-  if ((threadIdx.x & 31) == 0 && row < n) smax[row >> 5] = m;
+  int s = m;
+  for (int off = 16; off > 0; off >>= 1) {
+    m = max(m, __shfl_down_sync(0xffffffffu, m, off));
+    s += __shfl_down_sync(0xffffffffu, s, off);
+  }
+  fit = __all_sync(0xffffffffu, fit);
+  if ((threadIdx.x & 31) == 0 && row < n) {
+    smax[row >> 5] = m;
+    ssum[row >> 5] = s;
+    sfit[row >> 5] = fit ? 1 : 0;
+  }
 }
 
 __global__ void k_sell_fill(const int64_t *rp, const int32_t *col, const float *w, int64_t n, const uint8_t *sdeg,
-                            const int64_t *sptr, int32_t *scol, float *sw) {
+                            const int64_t *sptr, const int64_t *cptr, int16_t *scol, float *sw) {
   const int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (row >= n) return;
   const int d = sdeg[row];
   if (d == 0xFF) return;
-  const int64_t b = sptr[row >> 5] + (row & 31), src = rp[row];
-  for (int t = 0; t < d; ++t) {
-    scol[b + 32 * t] = col[src + t];
-    if (w) sw[b + 32 * t] = w[src + t];
+  const int64_t slice = row >> 5, lane = row & 31, src = rp[row];
+  const int64_t cp = cptr[slice];
+  if (cp < 0) {
+    int16_t *c16 = scol + (~cp) + lane;
+    for (int t = 0; t < d; ++t) c16[32 * t] = static_cast<int16_t>(static_cast<int64_t>(col[src + t]) - row);
+  } else {
+    int32_t *c32 = reinterpret_cast<int32_t *>(scol + cp) + lane;
+    for (int t = 0; t < d; ++t) c32[32 * t] = col[src + t];
+  }
+  if (w) {
+    const int64_t b = sptr[slice] + lane;
+    for (int t = 0; t < d; ++t) sw[b + 32 * t] = w[src + t];
   }
 }
 
@@ -275,9 +304,11 @@ void build_plan(sphynx_graph *g, const int64_t *host_rowptr) {
     rp = rp_copy.data();
   }
   std::vector<int64_t> items, split;
+  int64_t nnz_long = 0;
   for (int64_t i = 0; i < g->n; ++i) {
     const int64_t a = rp[i], b = rp[i + 1];
     if (b - a <= kShortDeg) continue;
+    nnz_long += b - a;
     const int64_t first = static_cast<int64_t>(items.size() / 4);
     int64_t cnt = 0;
     for (int64_t s = a; s < b; s += kLongChunk) {
@@ -293,6 +324,8 @@ void build_plan(sphynx_graph *g, const int64_t *host_rowptr) {
   }
   p.n_items = static_cast<int64_t>(items.size() / 4);
   p.n_long = static_cast<int64_t>(split.size() / 3);
+  p.long_bytes = static_cast<double>(nnz_long) * (g->weighted ? 8.0 : 4.0) + 32.0 * static_cast<double>(p.n_items) +
+                 24.0 * static_cast<double>(p.n_long);
   p.items.alloc(items.size() * sizeof(int64_t));
   p.split.alloc(split.size() * sizeof(int64_t));
   SPX_CUDA(cudaMemcpyAsync(p.items.p, items.data(), items.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
@@ -305,24 +338,51 @@ void build_sell(sphynx_graph *g) {
   SpmmPlan &p = g->plan;
   const int64_t n = g->n, slices = (n + 31) / 32;
   p.sell_deg.alloc(static_cast<size_t>(n));
-  DevBuf smax;
-  smax.alloc(static_cast<size_t>(slices) * sizeof(int));
+  DevBuf sstat;
+  sstat.alloc(static_cast<size_t>(slices) * 3 * sizeof(int));
+  int *smax = sstat.as<int>(), *ssum = smax + slices, *sfit = ssum + slices;
   const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
-  k_sell_deg<<<blocks, 256, 0, g->stream>>>(g->rowptr, n, p.sell_deg.as<uint8_t>(), smax.as<int>());
+  k_sell_deg<<<blocks, 256, 0, g->stream>>>(g->rowptr, g->col, n, p.sell_deg.as<uint8_t>(), smax, ssum, sfit);
   SPX_LAUNCHED();
-  std::vector<int> hmax(static_cast<size_t>(slices));
-  SPX_CUDA(cudaMemcpyAsync(hmax.data(), smax.p, slices * sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  std::vector<int> hstat(static_cast<size_t>(slices) * 3);
+  SPX_CUDA(cudaMemcpyAsync(hstat.data(), sstat.p, hstat.size() * sizeof(int), cudaMemcpyDeviceToHost, g->stream));
   SPX_CUDA(cudaStreamSynchronize(g->stream));
-  std::vector<int64_t> hptr(static_cast<size_t>(slices) + 1, 0);
-  for (int64_t s = 0; s < slices; ++s) hptr[s + 1] = hptr[s] + 32 * static_cast<int64_t>(hmax[s]);
+  const int *hmax = hstat.data(), *hsum = hmax + slices, *hfit = hsum + slices;
+  std::vector<int64_t> hptr(static_cast<size_t>(slices) + 1, 0), hcptr(static_cast<size_t>(slices), 0);
+  int64_t units = 0, narrow = 0;
+  double idx_bytes = 0, entries = 0;
+  for (int64_t s = 0; s < slices; ++s) {
+    hptr[s + 1] = hptr[s] + 32 * static_cast<int64_t>(hmax[s]);
+    if (hfit[s]) {
+      hcptr[s] = ~units;
+      units += 32 * static_cast<int64_t>(hmax[s]);
+      ++narrow;
+      idx_bytes += 2.0 * hsum[s];
+    } else {
+      units = (units + 63) & ~static_cast<int64_t>(63);   // 128-byte aligned rows of 32 indices
+      hcptr[s] = units;
+      units += 64 * static_cast<int64_t>(hmax[s]);
+      idx_bytes += 4.0 * hsum[s];
+    }
+    entries += hsum[s];
+  }
   p.sell_entries = hptr[slices];
+  p.sell_narrow = narrow;
+  // indices of the real entries, the degree bytes and one slice offset per slice
+  // (plus the weights and their offsets on weighted graphs)
+  p.sell_bytes = idx_bytes + static_cast<double>(n) + 8.0 * static_cast<double>(slices) +
+                 (g->weighted ? 4.0 * entries + 8.0 * static_cast<double>(slices) : 0.0);
   p.sell_ptr.alloc(hptr.size() * sizeof(int64_t));
+  p.sell_cptr.alloc(hcptr.size() * sizeof(int64_t) + 8);
   SPX_CUDA(cudaMemcpyAsync(p.sell_ptr.p, hptr.data(), hptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                            g->stream));
-  p.sell_col.alloc(static_cast<size_t>(p.sell_entries > 0 ? p.sell_entries : 1) * sizeof(int32_t));
+  SPX_CUDA(cudaMemcpyAsync(p.sell_cptr.p, hcptr.data(), hcptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           g->stream));
+  p.sell_col.alloc(static_cast<size_t>(units > 0 ? units : 1) * sizeof(int16_t));
   if (g->weighted) p.sell_w.alloc(static_cast<size_t>(p.sell_entries > 0 ? p.sell_entries : 1) * sizeof(float));
   k_sell_fill<<<blocks, 256, 0, g->stream>>>(g->rowptr, g->col, g->w, n, p.sell_deg.as<uint8_t>(),
-                                             p.sell_ptr.as<int64_t>(), p.sell_col.as<int32_t>(), p.sell_w.as<float>());
+                                             p.sell_ptr.as<int64_t>(), p.sell_cptr.as<int64_t>(),
+                                             p.sell_col.as<int16_t>(), p.sell_w.as<float>());
   SPX_LAUNCHED();
   SPX_CUDA(cudaStreamSynchronize(g->stream));
 }
@@ -553,6 +613,12 @@ int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info) {
     info->spmm_variant = g->plan.tuned_variant;
     info->tuned_us_csr = g->plan.tuned_us[kCsrStaged];
     info->tuned_us_sell = g->plan.tuned_us[kSell32];
+    info->sell_slices = (g->n + 31) / 32;
+    info->sell_narrow_slices = g->plan.sell_narrow;
+    info->spmm_graph_bytes = g->plan.tuned_variant == kSell32
+                                 ? g->plan.sell_bytes + g->plan.long_bytes
+                                 : 8.0 * static_cast<double>(g->n + 1) +
+                                       static_cast<double>(g->nnz) * (g->weighted ? 8.0 : 4.0);
     return SPHYNX_OK;
   });
 }

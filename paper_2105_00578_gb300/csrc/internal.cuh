@@ -72,6 +72,20 @@ struct DevBuf {
 enum class DT { F64 = SPHYNX_DT_F64, F32 = SPHYNX_DT_F32, BF16 = SPHYNX_DT_BF16 };
 inline size_t dt_size(DT d) { return d == DT::F64 ? 8 : (d == DT::F32 ? 4 : 2); }
 
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) as a counter-based
+// generator: draw ctr (>= 1) of the stream that starts at `state`.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+// u in [0,1) from the top 53 bits, then 2u - 1 (exact in double)
+__device__ inline double splitmix_pm1(uint64_t state, uint64_t ctr) {
+  const uint64_t z = mix64(state + ctr * kGamma);
+  return 2.0 * (static_cast<double>(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
 constexpr int kShortDeg = 32;        // rows with more neighbours use the long-row kernels
 constexpr int kLongChunk = 4096;     // entries per long-row work item
 constexpr int kSmCount = 152;
@@ -98,13 +112,22 @@ struct SpmmPlan {
   DevBuf items;                      // int64 [n_items][4]: row, begin, end, slot
   DevBuf split;                      // int64 [n_long][3]: row, first slot, slot count
   DevBuf partials;                   // per-item partial rows (n_items x 16 doubles)
-  // SELL-32 copy of the short rows: slice s (rows 32s..32s+31) holds entry t
-  // of its lane-th row at sell_col[sell_ptr[s] + 32 t + lane]
-  int64_t sell_entries = 0;
-  DevBuf sell_ptr;                   // int64 [n_slices + 1]
-  DevBuf sell_col;                   // int32 [sell_entries]
+  // SELL-32 copy of the short rows.  Slice s (rows 32s..32s+31) holds entry t
+  // of its lane-th row at position 32 t + lane of its block.  A slice whose
+  // entries all lie within 32767 of their row stores 16-bit offsets col - row,
+  // any other slice 32-bit column indices; sell_cptr[s] is the block's start
+  // in 16-bit units, bitwise negated for a 16-bit slice.  Weights, when
+  // present, are at sell_w[sell_ptr[s] + 32 t + lane].
+  int64_t sell_entries = 0;          // padded entries of all slices
+  int64_t sell_narrow = 0;           // slices stored with 16-bit offsets
+  double sell_bytes = 0;             // bytes a product must read from this layout:
+                                     // real entries' indices, degrees, slice offsets
+  DevBuf sell_ptr;                   // int64 [n_slices + 1], entry offsets
+  DevBuf sell_cptr;                  // int64 [n_slices], see above
+  DevBuf sell_col;                   // 16-bit units [sum of block sizes]
   DevBuf sell_w;                     // float [sell_entries] (weighted graphs)
   DevBuf sell_deg;                   // uint8 [n]: degree, or 0xFF for a long row
+  double long_bytes = 0;             // bytes of the long rows' CSR entries and items
 };
 
 // Everything the iteration kernels need to apply L without forming it.
@@ -124,9 +147,27 @@ struct Counters {
   int64_t spmm_launches = 0;
   double spmm_bytes = 0;
   double spmm_ms = 0;
+  // the same split by input precision (indexed by DT)
+  int64_t spmm_launches_dt[3] = {0, 0, 0};
+  double spmm_bytes_dt[3] = {0, 0, 0};
+  double spmm_ms_dt[3] = {0, 0, 0};
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;  // pairs recorded around SpMMs
+  std::vector<int> ev_dt;            // input precision of each recorded pair
   size_t ev_used = 0;
+};
+
+// A batch of graphs in one handle (sphynx_create_batch): graph q owns rows
+// [h_gptr[q], h_gptr[q+1]); row-reducing kernels work on chunks of rows that
+// never straddle two graphs.
+struct BatchInfo {
+  int count = 0;                    // 0: the handle holds one graph
+  std::vector<int64_t> h_gptr;      // [count + 1] graph offsets (host)
+  DevBuf gptr;                      // the same on the device
+  int64_t n_chunks = 0;
+  DevBuf chunk_graph;               // int32 [n_chunks]: graph of each chunk
+  DevBuf chunk_begin;               // int64 [n_chunks + 1]: first row of each chunk, then n
+  DevBuf graph_chunk0;              // int32 [count + 1]: first chunk of each graph
 };
 
 }  // namespace sphynx
@@ -160,6 +201,7 @@ struct sphynx_graph {
   sphynx::Counters ctr;
   sphynx::DevBuf pinned_dummy;
   void *host_flag = nullptr;                 // pinned int32[8] for convergence polls
+  sphynx::BatchInfo batch;                   // set by sphynx_create_batch
   sphynx::LapView view() const {
     return sphynx::LapView{n, rowptr, col, w, deg.as<double>(), degf.as<float>(),
                            dinv.as<double>(), dinvf.as<float>()};
@@ -171,7 +213,8 @@ namespace sphynx {
 
 // ---- spmm.cu ----------------------------------------------------------------
 // Y = L X (mode 0) or one step of the polynomial chain (mode 1):
-//   t_out = t - (L t) * inv_cur;  yacc = (first ? t * inv_first : yacc) + t_out * inv_next
+//   t_out = t - (L t) * inv_cur; yacc gathers t * inv_cur and t_out * inv_next
+//   as yterms says (see spmm_kernels.cuh)
 struct SpmmArgs {
   int lap;                 // SPHYNX_COMBINATORIAL (also generalized) or SPHYNX_NORMALIZED
   DT tin;                  // element type of x
@@ -185,6 +228,7 @@ struct SpmmArgs {
   DT tout;                 // mode 1: F64 (with F64 input), F32 or BF16
   void *yacc;              // mode 1: double or float accumulator (ld_y)
   int first;               // mode 1: initialise yacc from t
+  int yterms;              // mode 1: terms added to yacc: 2 (t and t'), 1 (t' only) or 0
   const double *inv;       // mode 1: device array of 1/theta
   const float *invf;       // mode 1: its float copy
   int i_cur;               // mode 1: index of theta_i in inv
@@ -266,16 +310,37 @@ void launch_signs_coords(cudaStream_t st, DT dt, const void *x, int64_t n, int l
                          void *coords, double *scratch);
 
 // dots and vector ops for the Lanczos process of the polynomial setup
-void launch_lanczos_dots(cudaStream_t st, DT dt, const void *basis, int ldv, int j1,
+// The basis is column-major (column c at basis + c * ldv, ldv a multiple of 4,
+// basis and w 32-byte aligned); partials hold grid x j1 doubles.
+void launch_lanczos_dots(cudaStream_t st, DT dt, const void *basis, int64_t ldv, int j1,
                          const void *w, int64_t n, double *partials, int grid);
 void launch_reduce_cols(cudaStream_t st, const double *partials, int grid, int cols, double *out);
-void launch_lanczos_sub(cudaStream_t st, DT dt, const void *basis, int ldv, int j1, void *w,
+void launch_lanczos_sub(cudaStream_t st, DT dt, const void *basis, int64_t ldv, int j1, void *w,
                         int64_t n, const double *h, double *norm_partials, int grid);
-void launch_lanczos_next(cudaStream_t st, DT dt, const void *w, void *v, void *basis, int ldv,
+void launch_lanczos_next(cudaStream_t st, DT dt, const void *w, void *v, void *basis, int64_t ldv,
                          int j, int64_t n, const double *beta2);
 void launch_poly_start(cudaStream_t st, DT dt, void *v, int64_t n, uint64_t seed);
 void launch_project_null(cudaStream_t st, DT dt, void *v, int64_t n, int lap, const double *deg,
                          double *partials, int grid, double *scal);
+// option checks shared by the single-graph and batched solvers
+void check_lobpcg_options(const sphynx_graph *g, const sphynx_options *o);
+// The embedding's canonical rotation on the rows x[0..rows) (ld wide, d
+// eigenvectors, Ritz values theta): within every run of Ritz values closer
+// than tol, the columns are turned to their orthogonal Procrustes alignment
+// with the seeded reference block (lobpcg.cu).
+void canonical_rotation_block(sphynx_graph *g, void *x, int64_t rows, int ld, DT dt, const double *theta, int d,
+                              double tol, uint64_t seed);
+// Canonical rotation of a cluster of eigenvectors (columns a .. a + c - 1 of
+// the n x ld block x, d eigenvectors): partials[grid][c] of row p of
+// E_c^T Z_c, Z the reference block drawn from mix64(seed + 5 gamma) with
+// counter i * d + j + 1; and E_c <- E_c Q for a device c x c row-major Q.
+void launch_cluster_dots(cudaStream_t st, DT dt, const void *x, int64_t n, int ld, int d, int a, int c, int p,
+                         uint64_t seed, double *partials, int grid);
+void launch_rotate_cols(cudaStream_t st, DT dt, void *x, int64_t n, int ld, int a, int c, const double *q);
+// col = z / ||z||, z the null vector of L (1, or D^{1/2} 1 for L_N), with
+// scal[1] = z . z as launch_project_null leaves it
+void launch_null_column(cudaStream_t st, DT dt, void *col, int64_t n, int lap, const double *deg,
+                        const double *scal);
 void launch_poly_single(cudaStream_t st, DT dt, const void *r, void *h, int64_t n, int ld,
                         const double *inv, const int *done);
 int vec_grid(int64_t n);
@@ -284,10 +349,12 @@ int vec_grid(int64_t n);
 // M x M Gram matrices; coefficients written as M x ld (ld >= b); without an
 // active mask, column k of S is block k / ld, column k % ld.  mixed: the
 // Jacobi rotations run in float and every Ritz value is the double Rayleigh
-// quotient of its vector (for blocks stored in float).
+// quotient of its vector (for blocks stored in float).  count > 1 solves that
+// many problems, laid out back to back in every array, one CTA each.
 void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, int M, int ld,
                           int b, double u_work, SolverState *state, double *y64, void *yt, DT dt,
-                          const int *active_override, double *theta_out, int *svqb_out, int mixed);
+                          const int *active_override, double *theta_out, int *svqb_out, int mixed,
+                          int count = 1);
 void launch_d2f(cudaStream_t st, const double *src, float *dst, int64_t n);
 void launch_gram_reduce(cudaStream_t st, const double *partials, int nblk, int ld, int grid,
                         double *ga, double *gb, const int *done);
@@ -297,9 +364,14 @@ void launch_harmonic_ritz(cudaStream_t st, const double *alpha, const double *be
 // ---- mj.cu ------------------------------------------------------------------
 void run_mj(cudaStream_t st, DT dt, const void *coords, int ldc, int dims, int64_t n,
             const int64_t *vw, int K, int32_t *part, Counters *ctr);
-size_t mj_scratch_bytes(int64_t n, int K);
+// Multi-jagged with caller-provided scratch (mj_scratch_bytes).  With count > 1
+// the points are count graphs, graph g owning points [h_gptr[g], h_gptr[g+1])
+// (host offsets) and parts [g K/count, (g+1) K/count): the first level has one
+// section per graph and every later level splits within them.
+size_t mj_scratch_bytes(int64_t n, int K, int count);
 void run_mj_scratch(cudaStream_t st, DT dt, const void *coords, int ldc, int dims, int64_t n,
-                    const int64_t *vw, int K, int32_t *part, Counters *ctr, void *scratch);
+                    const int64_t *vw, int K, int32_t *part, Counters *ctr, void *scratch,
+                    const int64_t *h_gptr, int count);
 
 // ---- graph.cu ---------------------------------------------------------------
 void eval_partition(sphynx_graph *g, const int32_t *part, int K, double *cut, double *cut2,

@@ -19,6 +19,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 namespace sphynx {
 
@@ -69,11 +71,15 @@ void poly_setup(sphynx_graph *g, const sphynx_options *o) {
   const size_t es = dt_size(dt);
   const int lap = op_of(o->laplacian);
   const int64_t n = g->n;
-  const int ldv = round4(k);
+  const int64_t ldv = (n + 3) & ~static_cast<int64_t>(3);   // column-major basis, 16-byte aligned columns
   cudaStream_t st = g->stream;
-  void *V = g->workspace("lz_V", static_cast<size_t>(n) * ldv * es, false);
-  void *v = g->workspace("lz_v", static_cast<size_t>(n) * es, false);
-  void *w = g->workspace("lz_w", static_cast<size_t>(n) * es, false);
+  // column 0 holds the normalised null vector of L and column j + 1 the
+  // Lanczos vector v_j: both Gram-Schmidt passes orthogonalise against the null
+  // vector too, which changes nothing in exact arithmetic but stops rounding
+  // in a float basis from re-growing the null component over the k steps
+  void *V = g->workspace("lz_V", static_cast<size_t>(ldv) * (k + 1) * es, false);
+  void *v = g->workspace("lz_v", static_cast<size_t>(ldv) * es, false);
+  void *w = g->workspace("lz_w", static_cast<size_t>(ldv) * es, false);
   const int grid = vec_grid(n);
   double *part = static_cast<double *>(g->workspace("lz_part", static_cast<size_t>(grid) * (SPHYNX_MAX_POLY_DEGREE + 2) * 8, false));
   double *small = static_cast<double *>(g->workspace("lz_small", 8 * (4 * SPHYNX_MAX_POLY_DEGREE + 16), true));
@@ -88,26 +94,27 @@ void poly_setup(sphynx_graph *g, const sphynx_options *o) {
 
   launch_poly_start(st, dt, v, n, o->seed);
   launch_project_null(st, dt, v, n, lap, g->deg.as<double>(), part, grid, scal);
-  // beta_0^2 = ||v||^2, then v <- v / beta_0 and V[:, 0] = v
-  launch_lanczos_dots(st, dt, v, 1, 1, v, n, part, grid);
+  launch_null_column(st, dt, V, n, lap, g->deg.as<double>(), scal);
+  // beta_0^2 = ||v||^2, then v <- v / beta_0 and V[:, 1] = v
+  launch_lanczos_dots(st, dt, v, ldv, 1, v, n, part, grid);
   launch_reduce_cols(st, part, grid, 1, nrm);
-  launch_lanczos_next(st, dt, v, v, V, ldv, 0, n, nrm);
-  g->ctr.launches += 7;
+  launch_lanczos_next(st, dt, v, v, V, ldv, 1, n, nrm);
+  g->ctr.launches += 8;
   for (int j = 0; j < k; ++j) {
     plain_spmm(g, lap, dt, v, w, 1, 1, nullptr);                 // w = L v_j
     for (int pass = 0; pass < 2; ++pass) {                       // two Gram-Schmidt passes
-      launch_lanczos_dots(st, dt, V, ldv, j + 1, w, n, part, grid);
-      launch_reduce_cols(st, part, grid, j + 1, h);
-      if (pass == 0) SPX_CUDA(cudaMemcpyAsync(alpha + j, h + j, sizeof(double), cudaMemcpyDeviceToDevice, st));
-      launch_lanczos_sub(st, dt, V, ldv, j + 1, w, n, h, part, grid);
+      launch_lanczos_dots(st, dt, V, ldv, j + 2, w, n, part, grid);
+      launch_reduce_cols(st, part, grid, j + 2, h);
+      if (pass == 0) SPX_CUDA(cudaMemcpyAsync(alpha + j, h + j + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      launch_lanczos_sub(st, dt, V, ldv, j + 2, w, n, h, part, grid);
     }
     launch_reduce_cols(st, part, grid, 1, beta2 + j);            // beta_j^2 = ||w||^2
-    if (j + 1 < k) launch_lanczos_next(st, dt, w, v, V, ldv, j + 1, n, beta2 + j);
+    if (j + 1 < k) launch_lanczos_next(st, dt, w, v, V, ldv, j + 2, n, beta2 + j);
     g->ctr.launches += 8;
   }
   launch_harmonic_ritz(st, alpha, beta2, k, roots.as<double>(), g->poly_inv.as<double>(), g->poly_invf.as<float>(),
                        err.as<int>());
-  g->ctr.launches += 1;
+  g->ctr.launches += 2;
   int herr = 0;
   g->poly_roots.assign(k, 0.0);
   SPX_CUDA(cudaMemcpyAsync(g->poly_roots.data(), roots.p, k * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -145,6 +152,9 @@ void poly_apply(sphynx_graph *g, int precision, const void *r, void *h, int ld, 
     a.tout = ct;
     a.yacc = h;
     a.first = i == 0 ? 1 : 0;
+    // y gathers two terms on even steps; an odd step leaves y alone unless
+    // it is the last, which adds its output
+    a.yterms = (i % 2 == 0) ? 2 : (i + 2 == k ? 1 : 0);
     a.inv = g->poly_inv.as<double>();
     a.invf = g->poly_invf.as<float>();
     a.i_cur = i;
@@ -152,6 +162,56 @@ void poly_apply(sphynx_graph *g, int precision, const void *r, void *h, int ld, 
     spmm(g, a);
   }
 }
+
+// ---- embedding: canonical rotation within clusters of equal Ritz values -------
+// Eigenvectors of (nearly) equal eigenvalues are fixed only up to a rotation of
+// their span, and the multi-jagged cuts depend on that rotation.  Within each
+// run of Ritz values whose neighbours differ by at most tol (relative to the
+// larger; the eigenvalue-zero column excluded) the columns E_c become E_c Q,
+// Q the orthogonal polar factor of E_c^T Z_c with Z a seeded reference block
+// (the orthogonal Procrustes rotation towards Z), so that the embedding
+// depends on the span only.  Q = M (M^T M)^{-1/2}, from a cyclic Jacobi
+// eigendecomposition of M^T M on the host (c is at most 16).
+namespace {
+
+void sym_eig_host(std::vector<double> &a, int c, std::vector<double> &v) {
+  v.assign(static_cast<size_t>(c) * c, 0.0);
+  for (int i = 0; i < c; ++i) v[i * c + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < c; ++i)
+      for (int j = 0; j < c; ++j) {
+        tot += a[i * c + j] * a[i * c + j];
+        if (i != j) off += a[i * c + j] * a[i * c + j];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < c; ++p)
+      for (int q = p + 1; q < c; ++q) {
+        const double apq = a[p * c + q];
+        if (apq == 0.0) continue;
+        const double tau = (a[q * c + q] - a[p * c + p]) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        for (int k = 0; k < c; ++k) {   // A <- A J (columns p, q)
+          const double akp = a[k * c + p], akq = a[k * c + q];
+          a[k * c + p] = cs * akp - sn * akq;
+          a[k * c + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < c; ++k) {   // A <- J^T A (rows p, q)
+          const double apk = a[p * c + k], aqk = a[q * c + k];
+          a[p * c + k] = cs * apk - sn * aqk;
+          a[q * c + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < c; ++k) {   // V <- V J
+          const double vkp = v[k * c + p], vkq = v[k * c + q];
+          v[k * c + p] = cs * vkp - sn * vkq;
+          v[k * c + q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+}
+
+}  // namespace
 
 // ---- LOBPCG -------------------------------------------------------------------
 struct EigenResult {
@@ -293,6 +353,11 @@ void begin_stats(sphynx_graph *g, bool timing) {
   g->ctr.spmm_launches = 0;
   g->ctr.spmm_bytes = 0;
   g->ctr.spmm_ms = 0;
+  for (int i = 0; i < 3; ++i) {
+    g->ctr.spmm_launches_dt[i] = 0;
+    g->ctr.spmm_bytes_dt[i] = 0;
+    g->ctr.spmm_ms_dt[i] = 0;
+  }
   g->ctr.ev_used = 0;
   g->ctr.timing = timing;
 }
@@ -303,6 +368,7 @@ void end_stats(sphynx_graph *g) {
     float t = 0;
     SPX_CUDA(cudaEventElapsedTime(&t, g->ctr.ev_pool[i], g->ctr.ev_pool[i + 1]));
     ms += t;
+    g->ctr.spmm_ms_dt[g->ctr.ev_dt[i / 2]] += t;
   }
   g->ctr.spmm_ms = ms;
   g->ctr.timing = false;
@@ -321,8 +387,77 @@ void fill_stats(sphynx_graph *g, const EigenResult &r, int b, sphynx_stats *s) {
   s->ms_spmm = g->ctr.spmm_ms;
   s->spmm_launches = g->ctr.spmm_launches;
   s->spmm_bytes = g->ctr.spmm_bytes;
+  for (int i = 0; i < 3; ++i) {
+    s->ms_spmm_by_dt[i] = g->ctr.spmm_ms_dt[i];
+    s->spmm_bytes_by_dt[i] = g->ctr.spmm_bytes_dt[i];
+    s->spmm_launches_by_dt[i] = g->ctr.spmm_launches_dt[i];
+  }
   s->kernel_launches = g->ctr.launches;
 }
+
+}  // namespace
+
+void check_lobpcg_options(const sphynx_graph *g, const sphynx_options *o) { check_options(g, o); }
+
+void canonical_rotation_block(sphynx_graph *g, void *x, int64_t rows, int ld, DT dt, const double *theta, int d,
+                              double tol, uint64_t seed) {
+  // runs of columns 1..d-1 whose neighbouring Ritz values differ by at most tol
+  std::vector<std::pair<int, int>> runs;
+  for (int j = 1; j < d;) {
+    int k = j;
+    while (k + 1 < d && std::fabs(theta[k + 1] - theta[k]) <=
+                            tol * std::fmax(std::fabs(theta[k]), std::fabs(theta[k + 1])))
+      ++k;
+    if (k > j) runs.emplace_back(j, k);
+    j = k + 1;
+  }
+  if (runs.empty() || rows < 1) return;
+  cudaStream_t st = g->stream;
+  const int grid = vec_grid(rows);
+  double *part = static_cast<double *>(g->workspace("cr_part", static_cast<size_t>(vec_grid(g->n)) * SPHYNX_MAX_NEV * 8, false));
+  double *mdev = static_cast<double *>(g->workspace("cr_m", SPHYNX_MAX_NEV * SPHYNX_MAX_NEV * 8, false));
+  for (const auto &run : runs) {
+    const int a = run.first, c = run.second - run.first + 1;
+    for (int p = 0; p < c; ++p) {
+      launch_cluster_dots(st, dt, x, rows, ld, d, a, c, p, seed, part, grid);
+      launch_reduce_cols(st, part, grid, c, mdev + p * c);
+      g->ctr.launches += 2;
+    }
+    std::vector<double> m(static_cast<size_t>(c) * c), s(static_cast<size_t>(c) * c), v, q(static_cast<size_t>(c) * c);
+    SPX_CUDA(cudaMemcpyAsync(m.data(), mdev, m.size() * 8, cudaMemcpyDeviceToHost, st));
+    SPX_CUDA(cudaStreamSynchronize(st));
+    // S = M^T M = V diag(l) V^T, Q = M V diag(l^{-1/2}) V^T
+    for (int i = 0; i < c; ++i)
+      for (int j = 0; j < c; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < c; ++k) acc += m[k * c + i] * m[k * c + j];
+        s[i * c + j] = acc;
+      }
+    sym_eig_host(s, c, v);
+    bool full_rank = true;
+    for (int i = 0; i < c; ++i) full_rank = full_rank && s[i * c + i] > 0.0;
+    if (!full_rank) continue;   // a rank-deficient alignment leaves the cluster as computed
+    std::vector<double> w(static_cast<size_t>(c) * c);   // V diag(l^{-1/2}) V^T
+    for (int i = 0; i < c; ++i)
+      for (int j = 0; j < c; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < c; ++k) acc += v[i * c + k] * v[j * c + k] / std::sqrt(s[k * c + k]);
+        w[i * c + j] = acc;
+      }
+    for (int i = 0; i < c; ++i)
+      for (int j = 0; j < c; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < c; ++k) acc += m[i * c + k] * w[k * c + j];
+        q[i * c + j] = acc;
+      }
+    SPX_CUDA(cudaMemcpyAsync(mdev, q.data(), q.size() * 8, cudaMemcpyHostToDevice, st));
+    launch_rotate_cols(st, dt, x, rows, ld, a, c, mdev);
+    SPX_CUDA(cudaStreamSynchronize(st));
+    g->ctr.launches += 1;
+  }
+}
+
+namespace {
 
 }  // namespace
 
@@ -461,13 +596,14 @@ int sphynx_partition(sphynx_handle g, int32_t K, const sphynx_options *opt, int3
     SPX_CUDA(cudaEventRecord(e[0], st));
     EigenResult r = lobpcg(g, opt, d, nullptr);
     SPX_CUDA(cudaEventRecord(e[1], st));
+    canonical_rotation_block(g, const_cast<void *>(r.x), g->n, r.ld, r.dt, r.theta, d, opt->tol, opt->seed);
     // Algorithm 2 lines 6-10: coordinates from eigenvectors 2..d
     const size_t es = dt_size(r.dt);
     void *coords = g->workspace("coords", static_cast<size_t>(g->n) * (d - 1) * es + 16, false);
     double *sc = static_cast<double *>(g->workspace("signs", static_cast<size_t>(vec_grid(g->n)) * d * 3 * 8 + 16 * 8, false));
     launch_signs_coords(st, r.dt, r.x, g->n, r.ld, d, coords, sc);
-    void *mjs = g->workspace("mj", mj_scratch_bytes(g->n, K), false);
-    run_mj_scratch(st, r.dt, coords, d - 1, d - 1, g->n, g->vw, K, dpart, &g->ctr, mjs);   // line 12
+    void *mjs = g->workspace("mj", mj_scratch_bytes(g->n, K, 1), false);
+    run_mj_scratch(st, r.dt, coords, d - 1, d - 1, g->n, g->vw, K, dpart, &g->ctr, mjs, nullptr, 1);   // line 12
     g->ctr.launches += 3;
     SPX_CUDA(cudaEventRecord(e[2], st));
     double cut = 0, cut2 = 0, imb = 0;

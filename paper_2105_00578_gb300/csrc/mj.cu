@@ -107,6 +107,22 @@ __global__ void k_mj_level0(long long *start, long long *end, long long *W, int6
   W[0] = static_cast<long long>(*wsum);
 }
 
+// W[g] = total vertex weight of graph g, vertices [gptr[g], gptr[g+1]); one CTA per graph
+__global__ void k_mj_graph_weights(const int64_t *vw, const int64_t *gptr, long long *W) {
+  __shared__ unsigned long long red[8];
+  const int g = blockIdx.x;
+  unsigned long long s = 0;
+  for (int64_t i = gptr[g] + threadIdx.x; i < gptr[g + 1]; i += blockDim.x) s += static_cast<unsigned long long>(vw[i]);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int k = 0; k < 8; ++k) t += red[k];
+    W[g] = static_cast<long long>(t);
+  }
+}
+
 __global__ void k_mj_sel_init(MjSec *sec, int S) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
@@ -339,18 +355,23 @@ struct Level {
 
 }  // namespace
 
-size_t mj_scratch_bytes(int64_t n, int K) {
+size_t mj_scratch_bytes(int64_t n, int K, int count) {
   const size_t Ks = static_cast<size_t>(K);
   return static_cast<size_t>(n) * 8 + Ks * 512 * 8 + Ks * sizeof(MjSec) + Ks * 8 * 6 + 64 +
-         Ks * 4 * 4 * 64 /* level tables, up to 64 levels */ + 16 * 256 + 4096;
+         Ks * 4 * 4 * 64 /* level tables, up to 64 levels */ + 16 * 256 + 4096 +
+         (count > 1 ? static_cast<size_t>(count + 1) * 8 + 256 : 0);
 }
 
 void run_mj_scratch(cudaStream_t st, DT dt, const void *coords, int ldc, int dims, int64_t n, const int64_t *vw,
-                    int K, int32_t *part, Counters *ctr, void *scratch) {
+                    int K, int32_t *part, Counters *ctr, void *scratch, const int64_t *h_gptr, int count) {
   if (K < 1) fail(SPHYNX_ERR_INVALID_ARG, "K must be >= 1");
   if (K > (1 << 20)) fail(SPHYNX_ERR_UNSUPPORTED, "K > 2^20");
   if (n < 0) fail(SPHYNX_ERR_INVALID_ARG, "n < 0");
+  if (count < 1 || (count > 1 && (!h_gptr || K % count != 0)))
+    fail(SPHYNX_ERR_INVALID_ARG, "multi-jagged over %d graphs needs their offsets and K a multiple of the count",
+         count);
   if (n == 0) return;
+  const int k_each = K / count;   // parts of every graph; graph g owns parts [g k_each, (g + 1) k_each)
   if (K == 1) {
     SPX_CUDA(cudaMemsetAsync(part, 0, n * sizeof(int32_t), st));
     return;
@@ -363,8 +384,10 @@ void run_mj_scratch(cudaStream_t st, DT dt, const void *coords, int ldc, int dim
   std::vector<Level> levels;
   {
     Level l0;
-    l0.lo = {0};
-    l0.k = {K};
+    for (int gi = 0; gi < count; ++gi) {   // one first-level section per graph
+      l0.lo.push_back(gi * k_each);
+      l0.k.push_back(k_each);
+    }
     levels.push_back(l0);
     for (;;) {
       Level &cur = levels.back();
@@ -425,6 +448,13 @@ void run_mj_scratch(cudaStream_t st, DT dt, const void *coords, int ldc, int dim
   }
   int *dtab = reinterpret_cast<int *>(take(host_tab.size() * 4));
   SPX_CUDA(cudaMemcpyAsync(dtab, host_tab.data(), host_tab.size() * 4, cudaMemcpyHostToDevice, st));
+  int64_t *dgptr = count > 1 ? reinterpret_cast<int64_t *>(take(static_cast<size_t>(count + 1) * 8)) : nullptr;
+  if (dgptr) {
+    if (h_gptr[0] != 0 || h_gptr[count] != n) fail(SPHYNX_ERR_INVALID_ARG, "graph offsets must span [0, n)");
+    for (int gi = 0; gi < count; ++gi)
+      if (h_gptr[gi + 1] < h_gptr[gi]) fail(SPHYNX_ERR_INVALID_ARG, "graph offsets must not decrease");
+    SPX_CUDA(cudaMemcpyAsync(dgptr, h_gptr, static_cast<size_t>(count + 1) * 8, cudaMemcpyHostToDevice, st));
+  }
   SPX_CUDA(cudaMemsetAsync(hist, 0, static_cast<size_t>(K) * 512 * 8, st));
   SPX_CUDA(cudaMemsetAsync(misc, 0, 64, st));
 
@@ -443,9 +473,29 @@ void run_mj_scratch(cudaStream_t st, DT dt, const void *coords, int ldc, int dim
   SPX_CUDA(cudaStreamSynchronize(st));
   // k * cumW must fit in int64: K <= 2^20 and W < 2^40
   if (wtot >= (1ull << 40)) fail(SPHYNX_ERR_UNSUPPORTED, "total vertex weight >= 2^40");
-  k_mj_level0<<<1, 1, 0, st>>>(tab[0][0], tab[0][1], tab[0][2], n, misc);
-  SPX_LAUNCHED();
   int64_t launches = 5;
+  if (count == 1) {
+    k_mj_level0<<<1, 1, 0, st>>>(tab[0][0], tab[0][1], tab[0][2], n, misc);
+    SPX_LAUNCHED();
+  } else {
+    // first level: graph gi is section gi, vertices [gptr[gi], gptr[gi + 1])
+    std::vector<long long> hs(count), he(count), hw(count);
+    for (int gi = 0; gi < count; ++gi) {
+      hs[gi] = h_gptr[gi];
+      he[gi] = h_gptr[gi + 1];
+      hw[gi] = h_gptr[gi + 1] - h_gptr[gi];
+    }
+    SPX_CUDA(cudaMemcpyAsync(tab[0][0], hs.data(), count * 8, cudaMemcpyHostToDevice, st));
+    SPX_CUDA(cudaMemcpyAsync(tab[0][1], he.data(), count * 8, cudaMemcpyHostToDevice, st));
+    if (vw) {
+      k_mj_graph_weights<<<count, 256, 0, st>>>(vw, dgptr, tab[0][2]);
+      SPX_LAUNCHED();
+      ++launches;
+    } else {
+      SPX_CUDA(cudaMemcpyAsync(tab[0][2], hw.data(), count * 8, cudaMemcpyHostToDevice, st));
+    }
+    SPX_CUDA(cudaStreamSynchronize(st));   // the host vectors above go out of scope
+  }
 
   int idbits = 1;
   while (idbits < 32 && (1ll << idbits) < n) ++idbits;
@@ -489,10 +539,10 @@ void run_mj_scratch(cudaStream_t st, DT dt, const void *coords, int ldc, int dim
 void run_mj(cudaStream_t st, DT dt, const void *coords, int ldc, int dims, int64_t n, const int64_t *vw, int K,
             int32_t *part, Counters *ctr) {
   void *scratch = nullptr;
-  const size_t bytes = mj_scratch_bytes(n, K);
+  const size_t bytes = mj_scratch_bytes(n, K, 1);
   SPX_CUDA(cudaMallocAsync(&scratch, bytes, st));
   try {
-    run_mj_scratch(st, dt, coords, ldc, dims, n, vw, K, part, ctr, scratch);
+    run_mj_scratch(st, dt, coords, ldc, dims, n, vw, K, part, ctr, scratch, nullptr, 1);
   } catch (...) {
     cudaFreeAsync(scratch, st);
     throw;
@@ -565,7 +615,7 @@ extern "C" int sphynx_mj_noalloc(int32_t dtype, const void *coords, int32_t ldc,
     if (dtype != SPHYNX_DT_F32 && dtype != SPHYNX_DT_F64) fail(SPHYNX_ERR_INVALID_ARG, "dtype");
     if (n < 0) fail(SPHYNX_ERR_INVALID_ARG, "n < 0");
     if (K < 1 || K > (1 << 20)) fail(SPHYNX_ERR_INVALID_ARG, "K must be in [1, 2^20]");
-    const size_t need = mj_scratch_bytes(n, K);
+    const size_t need = mj_scratch_bytes(n, K, 1);
     if (need > kMjStaticBytes)
       fail(SPHYNX_ERR_UNSUPPORTED,
            "sphynx_mj_noalloc: n = %lld, K = %d need %zu bytes of scratch, more than its fixed %zu "
@@ -575,7 +625,7 @@ extern "C" int sphynx_mj_noalloc(int32_t dtype, const void *coords, int32_t ldc,
     // run_mj_scratch clears the histograms and counters it relies on and
     // rewrites everything else it reads
     run_mj_scratch(static_cast<cudaStream_t>(stream), static_cast<DT>(dtype), coords, ldc, dims, n, vtx_w, K,
-                   part_out, nullptr, scratch);
+                   part_out, nullptr, scratch, nullptr, 1);
     return SPHYNX_OK;
   });
 }

@@ -20,6 +20,7 @@
 // |a_pq| <= 1e-15 (|a_pp| + |a_qq|), and sweeps stop when none was applied.
 #include "internal.cuh"
 
+#include <cfloat>
 #include <cmath>
 
 namespace sphynx {
@@ -272,6 +273,19 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
   extern __shared__ __align__(16) unsigned char smraw[];
   RRSmem &S = *reinterpret_cast<RRSmem *>(smraw);
   const int tid = threadIdx.x;
+  // a launch of several CTAs solves that many problems laid out back to back
+  // (a batch of graphs): CTA bi takes the bi-th of every array
+  if (blockIdx.x > 0) {
+    const size_t bi = blockIdx.x;
+    ga += bi * M * M;
+    gb += bi * M * M;
+    if (st) st += bi;
+    if (active) active += bi * M;
+    if (y64) y64 += bi * M * ld;
+    if (yt) yt = static_cast<char *>(yt) + bi * M * ld * (yt_f32 ? 4 : 8);
+    if (theta_out) theta_out += bi * nev;
+    if (svqb_out) svqb_out += bi;
+  }
   if (st && st->done) return;
   const int L = kMaxM;  // leading dimension of the shared matrices
   if (tid == 0) {
@@ -443,74 +457,158 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
   }
 }
 
-struct HRSmem {
-  double T[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
-  double Mx[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
-  double C[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
-  double Z[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
-  double V[SPHYNX_MAX_POLY_DEGREE * SPHYNX_MAX_POLY_DEGREE];
-  double pairs[4 * SPHYNX_MAX_POLY_DEGREE];
-  double scratch[4];
-  double theta[SPHYNX_MAX_POLY_DEGREE];
-  double score[SPHYNX_MAX_POLY_DEGREE];
-  int order[SPHYNX_MAX_POLY_DEGREE];
-  int cnt[3];
-};
+// Harmonic Ritz values of the Lanczos tridiagonal T (Sec. 5.2 setup): the
+// eigenvalues theta of (T^2 + beta^2 e e^T) y = theta T y, e the last unit
+// vector.  With the Cholesky factor T = R^T R (R upper bidiagonal, diagonal r,
+// superdiagonal s) and y = R^{-1} z this is the standard problem
+//   Z z = theta z,  Z = R R^T + (beta^2 / r_{k-1}^2) e e^T,
+// because R^{-T} T^2 R^{-1} = R R^T and R^{-T} e = e / r_{k-1}.  Z is symmetric
+// tridiagonal: diagonal r_i^2 + s_i^2 (plus the rank-one term on the last
+// entry), off-diagonal s_i r_{i+1}.
+//
+// Its eigenvalues come from Sturm sequence counts (Barth, Martin and
+// Wilkinson, 1967) by multisection: one CTA of one warp per eigenvalue (so the
+// FP64 work, which is scarce per SM on this part, spreads over k SMs), whose
+// 32 lanes count at 32 interior points of the current bracket, narrowing it
+// 33-fold per round.  The count uses the division-free three-term recurrence
+// of the leading principal minors, p_i = (d_i - sigma) p_{i-1} - e_{i-1}^2 p_{i-2},
+// whose sign changes number the eigenvalues below sigma; pairs (p_i, p_{i-1})
+// are rescaled by exact powers of two to stay in range.  A second, single-CTA
+// kernel puts the values in modified Leja order.
 
-__global__ void __launch_bounds__(kSmallThreads)
-k_harmonic_ritz(const double *alpha, const double *beta2, int k, double *roots, double *inv, float *invf,
-                int *err) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  HRSmem &S = *reinterpret_cast<HRSmem *>(smraw);
-  const int L = SPHYNX_MAX_POLY_DEGREE;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int i = e / k, j = e % k;
-    double v = 0.0;
-    if (i == j) v = alpha[i];
-    else if (j == i + 1) v = sqrt(beta2[i]);
-    else if (i == j + 1) v = sqrt(beta2[j]);
-    S.T[i * L + j] = v;
+// number of eigenvalues of the tridiagonal (d, e2) smaller than sigma
+__device__ int sturm_count(const double *d, const double *e2, int k, double sigma) {
+  double pm2 = 0.0, pm1 = 1.0;
+  int cnt = 0;
+  for (int i = 0; i < k; ++i) {
+    double p = (d[i] - sigma) * pm1;
+    if (i > 0) p -= e2[i - 1] * pm2;
+    if (p == 0.0) p = pm1 > 0.0 ? -0x1p-900 : 0x1p-900;   // a zero minor counts as a sign change
+    if ((p < 0.0) != (pm1 < 0.0)) ++cnt;
+    const double a = fmax(fabs(p), fabs(pm1));
+    if (a > 0x1p500) {
+      p *= 0x1p-500;
+      pm1 *= 0x1p-500;
+    } else if (a < 0x1p-500) {
+      p *= 0x1p500;
+      pm1 *= 0x1p500;
+    }
+    pm2 = pm1;
+    pm1 = p;
   }
-  __syncthreads();
-  matmul(S.T, L, false, S.T, L, S.Mx, L, k, k, k);
-  if (tid == 0) S.Mx[(k - 1) * L + (k - 1)] += beta2[k - 1];
-  __syncthreads();
-  const double mp = chol_upper(S.T, L, k, S.scratch);  // T = R^T R
-  if (!(mp > 0.0)) {
-    if (tid == 0) *err = 1;
+  return cnt;
+}
+
+// CTA i (32 threads): theta[i], the i-th smallest eigenvalue of Z.
+__global__ void __launch_bounds__(32)
+k_harmonic_eig(const double *alpha, const double *beta2, int k, double *theta, int *err) {
+  __shared__ double d[SPHYNX_MAX_POLY_DEGREE], e2[SPHYNX_MAX_POLY_DEGREE];
+  __shared__ double glo, ghi;
+  __shared__ int bad;
+  const int lane = threadIdx.x, i = blockIdx.x;
+  if (lane == 0) {
+    // T = R^T R: r_0 = sqrt(alpha_0), s_j = b_j / r_j, r_{j+1} = sqrt(alpha_{j+1} - s_j^2)
+    double r[SPHYNX_MAX_POLY_DEGREE], sd[SPHYNX_MAX_POLY_DEGREE];
+    int b = 0;
+    for (int j = 0; j < k; ++j) {
+      const double piv = alpha[j] - (j > 0 ? sd[j - 1] * sd[j - 1] : 0.0);
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        b = 1;
+        break;
+      }
+      r[j] = sqrt(piv);
+      sd[j] = j + 1 < k ? sqrt(beta2[j]) / r[j] : 0.0;
+    }
+    bad = b;
+    if (!b) {
+      for (int j = 0; j < k; ++j) {
+        d[j] = r[j] * r[j] + sd[j] * sd[j];
+        if (j + 1 < k) {
+          const double off = sd[j] * r[j + 1];
+          e2[j] = off * off;
+        }
+      }
+      d[k - 1] += beta2[k - 1] / (r[k - 1] * r[k - 1]);
+      // Gershgorin interval, widened by a few units of roundoff
+      double lo = INFINITY, hi = -INFINITY;
+      for (int j = 0; j < k; ++j) {
+        const double rad = (j > 0 ? sqrt(e2[j - 1]) : 0.0) + (j + 1 < k ? sqrt(e2[j]) : 0.0);
+        lo = fmin(lo, d[j] - rad);
+        hi = fmax(hi, d[j] + rad);
+      }
+      const double span = fmax(fabs(lo), fabs(hi));
+      glo = lo - 4.0 * DBL_EPSILON * span;
+      ghi = hi + 4.0 * DBL_EPSILON * span;
+    }
+  }
+  __syncwarp();
+  if (bad) {
+    if (lane == 0) *err = 1;
     return;
   }
-  tri_inv_upper(S.T, L, k, S.C, L);
-  matmul(S.Mx, L, false, S.C, L, S.V, L, k, k, k);
-  matmul(S.C, L, true, S.V, L, S.Z, L, k, k, k);
-  symmetrize(S.Z, L, k);
-  jacobi_eig<double>(S.Z, L, S.V, L, k, S.pairs, S.cnt);
-  sort_diag(S.Z, L, k, S.order);
+  // count(sigma) > i  <=>  sigma > theta_i
+  double lo = glo, hi = ghi;
+  for (int round = 0; round < 48; ++round) {
+    const double w = hi - lo;
+    if (!(w > 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)))) break;
+    const double sig = lo + w * (static_cast<double>(lane + 1) / 33.0);
+    const bool above = sig > lo && sig < hi ? sturm_count(d, e2, k, sig) > i : sig >= hi;
+    const unsigned m = __ballot_sync(0xffffffffu, above);
+    const int j = m ? __ffs(m) - 1 : 32;             // first point above theta_i
+    const double nlo = j == 0 ? lo : __shfl_sync(0xffffffffu, sig, j - 1);
+    const double nhi = j == 32 ? hi : __shfl_sync(0xffffffffu, sig, j < 32 ? j : 31);
+    if (!(nhi - nlo < w)) break;                      // no progress left at this precision
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) theta[i] = 0.5 * (lo + hi);
+}
+
+// Modified Leja order of theta[0..k) (ascending): largest |theta| first, then
+// maximise the product of distances to the roots already taken (sum of logs);
+// ties -> lowest index.  The logs of a step are taken in parallel, one thread
+// per candidate.  theta may alias inv: it is read into shared memory first.
+__global__ void __launch_bounds__(64)
+k_harmonic_leja(const double *theta, int k, double *roots, double *inv, float *invf, int *err) {
+  __shared__ double th[SPHYNX_MAX_POLY_DEGREE], score[SPHYNX_MAX_POLY_DEGREE];
+  __shared__ int used[SPHYNX_MAX_POLY_DEGREE];
+  __shared__ int last;
+  const int tid = threadIdx.x;
+  if (*err) return;
+  if (tid < k) {
+    th[tid] = theta[tid];
+    score[tid] = 0.0;
+    used[tid] = 0;
+  }
+  __syncthreads();
   if (tid == 0) {
-    for (int i = 0; i < k; ++i) S.theta[i] = S.Z[S.order[i] * L + S.order[i]];
-    // modified Leja order: largest |theta| first, then maximise the product of
-    // distances to the roots already taken (sum of logs); ties -> lowest index
-    int used[SPHYNX_MAX_POLY_DEGREE];
-    for (int i = 0; i < k; ++i) { used[i] = 0; S.score[i] = 0.0; }
     int first = 0;
     for (int i = 1; i < k; ++i)
-      if (fabs(S.theta[i]) > fabs(S.theta[first])) first = i;
+      if (fabs(th[i]) > fabs(th[first])) first = i;
     used[first] = 1;
-    roots[0] = S.theta[first];
-    int last = first;
-    for (int step = 1; step < k; ++step) {
+    last = first;
+    roots[0] = th[first];
+  }
+  __syncthreads();
+  for (int step = 1; step < k; ++step) {
+    if (tid < k && !used[tid]) {
+      const double dd = fabs(th[tid] - th[last]);
+      score[tid] += dd > 0.0 ? log(dd) : -INFINITY;
+    }
+    __syncthreads();
+    if (tid == 0) {
       int best = -1;
       for (int i = 0; i < k; ++i) {
         if (used[i]) continue;
-        const double dd = fabs(S.theta[i] - S.theta[last]);
-        S.score[i] += dd > 0.0 ? log(dd) : -INFINITY;
-        if (best < 0 || S.score[i] > S.score[best]) best = i;
+        if (best < 0 || score[i] > score[best]) best = i;
       }
       used[best] = 1;
-      roots[step] = S.theta[best];
       last = best;
+      roots[step] = th[best];
     }
+    __syncthreads();
+  }
+  if (tid == 0) {
     int bad = 0;
     for (int i = 0; i < k; ++i) {
       if (!(roots[i] > 0.0) || !isfinite(roots[i])) bad = 1;
@@ -527,22 +625,23 @@ k_harmonic_ritz(const double *alpha, const double *beta2, int k, double *roots, 
 
 void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, int M, int ld, int b,
                           double u_work, SolverState *state, double *y64, void *yt, DT dt,
-                          const int *active_override, double *theta_out, int *svqb_out, int mixed) {
+                          const int *active_override, double *theta_out, int *svqb_out, int mixed, int count) {
   if (M > kMaxM || M < 1) fail(SPHYNX_ERR_INVALID_ARG, "Rayleigh-Ritz size %d outside [1, %d]", M, kMaxM);
   if (b < 1 || b > ld) fail(SPHYNX_ERR_INVALID_ARG, "Rayleigh-Ritz nev %d", b);
+  if (count < 1) fail(SPHYNX_ERR_INVALID_ARG, "Rayleigh-Ritz count %d", count);
   const size_t sm = sizeof(RRSmem);
   SPX_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-  k_rayleigh_ritz<<<1, kSmallThreads, sm, st>>>(ga, gb, M, ld, b, u_work, state, active_override, y64, yt,
-                                                dt == DT::F32 ? 1 : 0, theta_out, svqb_out, mixed);
+  k_rayleigh_ritz<<<count, kSmallThreads, sm, st>>>(ga, gb, M, ld, b, u_work, state, active_override, y64, yt,
+                                                    dt == DT::F32 ? 1 : 0, theta_out, svqb_out, mixed);
   SPX_LAUNCHED();
 }
 
 void launch_harmonic_ritz(cudaStream_t st, const double *alpha, const double *beta2, int k, double *roots,
                           double *inv, float *invf, int *err) {
   if (k < 1 || k > SPHYNX_MAX_POLY_DEGREE) fail(SPHYNX_ERR_INVALID_ARG, "polynomial degree %d", k);
-  const size_t sm = sizeof(HRSmem);
-  SPX_CUDA(cudaFuncSetAttribute(k_harmonic_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
-  k_harmonic_ritz<<<1, kSmallThreads, sm, st>>>(alpha, beta2, k, roots, inv, invf, err);
+  k_harmonic_eig<<<k, 32, 0, st>>>(alpha, beta2, k, inv, err);
+  SPX_LAUNCHED();
+  k_harmonic_leja<<<1, 64, 0, st>>>(inv, k, roots, inv, invf, err);
   SPX_LAUNCHED();
 }
 

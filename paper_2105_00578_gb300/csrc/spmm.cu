@@ -35,7 +35,7 @@ SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a) {
     s.yacc = base;
     s.t_out = base + out_bytes;
   }
-  SpmmDev d{s.x, s.ld_x, s.ld_y, s.y, s.t_out, s.yacc, s.first, s.inv, s.invf, s.i_cur, nullptr};
+  SpmmDev d{s.x, s.ld_x, s.ld_y, s.y, s.t_out, s.yacc, s.first, s.yterms, s.inv, s.invf, s.i_cur, nullptr};
   cudaEvent_t e0, e1;
   SPX_CUDA(cudaEventCreate(&e0));
   SPX_CUDA(cudaEventCreate(&e1));
@@ -80,25 +80,34 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
     if (row_bytes % need || reinterpret_cast<uintptr_t>(a.x) % need)
       fail(SPHYNX_ERR_INVALID_ARG, "spmm: input rows must be %zu-byte aligned", need);
   }
-  SpmmDev d{a.x, a.ld_x, a.ld_y, a.y, a.t_out, a.yacc, a.first, a.inv, a.invf, a.i_cur, a.done};
+  if (a.mode == 1 && (a.yterms < 0 || a.yterms > 2 || (a.first && a.yterms != 2)))
+    fail(SPHYNX_ERR_INVALID_ARG, "spmm: polynomial step adds 0, 1 or 2 terms (2 on the first step)");
+  SpmmDev d{a.x, a.ld_x, a.ld_y, a.y, a.t_out, a.yacc, a.first, a.yterms, a.inv, a.invf, a.i_cur, a.done};
 
   // schedule: forced, or the one the autotuner chose for this graph at create
   g->plan.variant = g->plan.forced >= 0 ? g->plan.forced : g->plan.tuned_variant;
 
-  // algorithmic bytes: row pointers, column indices (+ weights), X once,
-  // the diagonal / D^{-1/2} vector, and the outputs
+  // algorithmic bytes: the graph in the layout the schedule reads (CSR row
+  // pointers and indices, or the SELL-32 slices plus the long rows' CSR
+  // entries; weights when present), X once, the diagonal / D^{-1/2} vector,
+  // and the outputs
   const double n = static_cast<double>(g->n), nnz = static_cast<double>(g->nnz);
   const double si = static_cast<double>(dt_size(a.tin));
   const double sa = a.tin == DT::F64 ? 8.0 : 4.0;
   const double b = static_cast<double>(a.b_true);
-  double bytes = 8.0 * (n + 1) + nnz * (g->weighted ? 8.0 : 4.0) + n * b * si + n * sa;
+  const double graph_bytes = g->plan.variant == kSell32 ? g->plan.sell_bytes + g->plan.long_bytes
+                                                        : 8.0 * (n + 1) + nnz * (g->weighted ? 8.0 : 4.0);
+  double bytes = graph_bytes + n * b * si + n * sa;
   if (a.mode == 0) {
     bytes += n * b * sa;
   } else {
-    bytes += n * b * static_cast<double>(dt_size(a.tout)) + n * b * sa * (a.first ? 1.0 : 2.0);
+    bytes += n * b * static_cast<double>(dt_size(a.tout)) + n * b * sa * (a.first ? 1.0 : (a.yterms ? 2.0 : 0.0));
   }
+  const int dti = static_cast<int>(a.tin);
   g->ctr.spmm_bytes += bytes;
   g->ctr.spmm_launches += 1;
+  g->ctr.spmm_bytes_dt[dti] += bytes;
+  g->ctr.spmm_launches_dt[dti] += 1;
 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (g->ctr.timing) {
@@ -109,6 +118,8 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
         g->ctr.ev_pool.push_back(e);
       }
     }
+    if (g->ctr.ev_dt.size() < g->ctr.ev_pool.size() / 2) g->ctr.ev_dt.resize(g->ctr.ev_pool.size() / 2);
+    g->ctr.ev_dt[g->ctr.ev_used / 2] = dti;
     e0 = g->ctr.ev_pool[g->ctr.ev_used++];
     e1 = g->ctr.ev_pool[g->ctr.ev_used++];
     SPX_CUDA(cudaEventRecord(e0, g->stream));

@@ -17,7 +17,13 @@
 // Epilogues.  Mode 0 stores L X.  Mode 1 is one step of the product-form
 // polynomial preconditioner (Sec. 5.2): with t the input block,
 //   t' = t - (L t) / theta_i   (stored in type TT),
-//   y  = (first ? t / theta_i : y) + t' / theta_{i+1}.
+// and y = sum_i t_i / theta_i is gathered two terms at a time, so that the
+// accumulator is read and written only every other step:
+//   yterms 2:  y = (first ? 0 : y) + t / theta_i + t' / theta_{i+1}
+//   yterms 1:  y = y + t' / theta_{i+1}            (last step, t already in y)
+//   yterms 0:  y untouched (t' is added by the next step as its input)
+// The terms use the stored (rounded) chain vectors, so the sum is the same
+// whichever step adds them.
 #pragma once
 
 #include "internal.cuh"
@@ -148,6 +154,7 @@ struct SpmmDev {              // kernel-side view of SpmmArgs
   void *tout;
   void *yacc;
   int first;
+  int yterms;          // mode 1: terms this step adds to y (2, 1 or 0)
   const double *inv;
   const float *invf;   // float copy of inv (the float path never touches FP64)
   int icur;
@@ -187,17 +194,23 @@ __device__ __forceinline__ void spmm_epilogue(const LapView &L, const SpmmDev &a
 #pragma unroll
     for (int c = 0; c < BP; ++c) tn[c] = xi[c] - out[c] * ic;
     store_row<BP>(static_cast<TT *>(a.tout) + row * a.ldx, tn);  // tn now holds the stored values
-    TA *yp = static_cast<TA *>(a.yacc) + row * a.ldy;
-    TA ya[BP];
-    if (a.first) {
+    if (a.yterms != 0) {
+      TA *yp = static_cast<TA *>(a.yacc) + row * a.ldy;
+      TA ya[BP];
+      if (a.first) {
 #pragma unroll
-      for (int c = 0; c < BP; ++c) ya[c] = xi[c] * ic;
-    } else {
-      load_row_rw<BP>(yp, ya);
+        for (int c = 0; c < BP; ++c) ya[c] = xi[c] * ic;
+      } else {
+        load_row_rw<BP>(yp, ya);
+        if (a.yterms == 2) {
+#pragma unroll
+          for (int c = 0; c < BP; ++c) ya[c] += xi[c] * ic;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < BP; ++c) ya[c] += tn[c] * inx;
+      store_row<BP>(yp, ya);
     }
-#pragma unroll
-    for (int c = 0; c < BP; ++c) ya[c] += tn[c] * inx;
-    store_row<BP>(yp, ya);
   }
 }
 
@@ -577,12 +590,14 @@ k_spmm_short(const LapView L, const SpmmDev a) {
 }
 
 // SELL-32 schedule: a warp per slice of 32 rows, lane = row.  Entry t of all
-// 32 rows is one contiguous 128-byte segment, so column reads are coalesced
-// without shared memory and all of L1 is left to the X gathers.
+// 32 rows is one contiguous segment (64 bytes of 16-bit offsets col - row, or
+// 128 bytes of 32-bit indices), so column reads are coalesced without shared
+// memory and all of L1 is left to the X gathers.  The slice's format is
+// uniform over the warp.
 template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
 __global__ void __launch_bounds__(128)
-k_spmm_sell(const LapView L, const SpmmDev a, const int32_t *__restrict__ scol, const float *__restrict__ sw,
-            const int64_t *__restrict__ sptr, const uint8_t *__restrict__ sdeg) {
+k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, const float *__restrict__ sw,
+            const int64_t *__restrict__ sptr, const int64_t *__restrict__ cptr, const uint8_t *__restrict__ sdeg) {
   using TA = typename AccOf<TI>::T;
   if (a.done && *a.done) return;
   const int lane = threadIdx.x & 31;
@@ -592,14 +607,23 @@ k_spmm_sell(const LapView L, const SpmmDev a, const int32_t *__restrict__ scol, 
   const bool valid = row < L.n;
   const int sd = valid ? sdeg[row] : 0xFF;
   const int d = sd == 0xFF ? 0 : sd;
-  const int64_t base = __ldg(sptr + slice);
-  const int32_t *cp = scol + base + lane;
-  const float *wp = W ? sw + base + lane : nullptr;
+  const int64_t cbase = __ldg(cptr + slice);
+  const float *wp = W ? sw + __ldg(sptr + slice) + lane : nullptr;
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> acc;
   acc.zero();
-  spmm_row<LAP, TI, BP, W>(
-      L, x, a.ldx, d, [&](int t) { return __ldcs(cp + 32 * t); }, [&](int t) { return __ldcs(wp + 32 * t); }, acc);
+  if (cbase < 0) {
+    const int16_t *cp = scol + (~cbase) + lane;
+    const int r = static_cast<int>(row);
+    spmm_row<LAP, TI, BP, W>(
+        L, x, a.ldx, d, [&](int t) { return r + static_cast<int>(__ldcs(cp + 32 * t)); },
+        [&](int t) { return __ldcs(wp + 32 * t); }, acc);
+  } else {
+    const int32_t *cp = reinterpret_cast<const int32_t *>(scol + cbase) + lane;
+    spmm_row<LAP, TI, BP, W>(
+        L, x, a.ldx, d, [&](int t) { return __ldcs(cp + 32 * t); }, [&](int t) { return __ldcs(wp + 32 * t); },
+        acc);
+  }
   if (sd == 0xFF) return;   // padding lane or a long row
   TA sum[BP];
   acc.get(sum);
@@ -665,8 +689,8 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
   if (grid > 0) {
     if (g->plan.variant == kSell32) {
       k_spmm_sell<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 128, 0, st>>>(
-          L, a, g->plan.sell_col.as<int32_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
-          g->plan.sell_deg.as<uint8_t>());
+          L, a, g->plan.sell_col.as<int16_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
+          g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>());
     } else {
       k_spmm_short<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 32 * kWarpsPerCta, 0, st>>>(L, a);
     }

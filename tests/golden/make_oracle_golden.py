@@ -4,6 +4,7 @@ synthetic workloads, for the GPU tests and the benchmark's CPU baseline.
 Calls only oracle/ (and the seeded generators in workloads/).  Usage:
     python tests/golden/make_oracle_golden.py c2     # 128^3 27-point mesh
     python tests/golden/make_oracle_golden.py c1     # 64 x 64 5-point mesh
+    python tests/golden/make_oracle_golden.py c3     # R-MAT scale 22, largest component
 """
 
 from __future__ import annotations
@@ -27,6 +28,9 @@ CASES = {
     "c2": dict(graph=lambda: workloads.grid3d(128, 128, 128, 27), K=64, problem="generalized", precond="poly",
                tol=1e-3, seed=2, poly_degree=25,
                desc="3D 27-point 128^3, generalized, polynomial degree 25, K=64, tol 1e-3"),
+    "c3": dict(graph=lambda: workloads.rmat(22, 16, 0.57, 0.19, 0.19, seed=3), K=256, problem="normalized",
+               precond="jacobi", tol=1e-2, seed=3, poly_degree=25,
+               desc="R-MAT scale 22 (a,b,c = .57,.19,.19), largest component, normalized, Jacobi, K=256, tol 1e-2"),
 }
 
 

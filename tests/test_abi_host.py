@@ -60,3 +60,31 @@ def test_options_helper_maps_names():
     o = spx.options(laplacian="generalized", precond="poly", precision="mixed_bf16", init="piecewise", tol=1e-2)
     assert (o.laplacian, o.precond, o.precision, o.init) == (spx.GENERALIZED, spx.PRECOND_POLY, spx.MIXED_BF16,
                                                            spx.INIT_PIECEWISE)
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every field offset and the size of the three public structs, as the C
+    compiler lays them out from the header, equal the Python binding's."""
+    import shutil
+    import subprocess
+    import paper_2105_00578_gb300 as spx
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sphynx_options": spx.Options, "sphynx_stats": spx.Stats, "sphynx_graph_info": spx.GraphInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sphynx.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

@@ -81,13 +81,23 @@ def test_rayleigh_ritz_rank_deficient_and_masked():
     assert np.all(y[[2, 5]] == 0)
 
 
+@pytest.mark.parametrize("k", [2, 3, 10, 25])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed_bf16"])
 @pytest.mark.parametrize("lap", ["combinatorial", "normalized", "generalized"])
-def test_poly_setup_and_apply(precision, lap):
+def test_poly_setup_and_apply(precision, lap, k):
+    # the chain adds y's terms two at a time; even and odd degrees end the
+    # chain on a two-term and a one-term step respectively
     import paper_2105_00578_gb300 as spx
     torch = torch_mod()
+    if precision != "fp64" and k in (2, 3):
+        pytest.skip("short chains are checked in FP64")
     g = W.largest_component(W.rmat(11, seed=3)) if lap != "combinatorial" else W.grid2d(50, 37)
-    k = 10
+    if lap == "generalized" and k > 10:
+        # a degree-25 product chain over L_C of this hub-heavy graph (roots from
+        # 1.5 to 809) amplifies rounding about 1e13-fold: a one-ulp change per
+        # step moves the result by 1e-2, so no two implementations agree there.
+        # The 27-point mesh (the class of the benchmark) is stable to 1e-15.
+        g = W.grid3d(12, 12, 12, 27)
     opt = spx.options(laplacian=lap, precond="poly", poly_degree=k, precision=precision, seed=4)
     h = spx.sphynx_create(g.row_ptr, g.col, None, None)
     try:

@@ -18,6 +18,11 @@ def graphs():
         "rmat": W.rmat(12, seed=7),                                   # power law: long rows
         "rmat_w": W.random_edge_weights(W.rmat(11, seed=9), 0.5, 1.5, 5),
         "star": W.star_graph(9001),                                   # one row split in 3 chunks
+        # wrap-around edges reach 44,700 rows: the boundary slices keep 32-bit
+        # indices, the interior ones 16-bit offsets
+        "torus_wide": W.grid2d(300, 150, periodic=True),
+        "torus_wide_w": W.random_edge_weights(W.grid2d(300, 150, periodic=True), 0.5, 1.5, 8),
+        "rmat16": W.rmat(16, seed=11),                                # mostly 32-bit slices, long rows
     }
 
 
@@ -82,6 +87,37 @@ def test_degrees_exact():
         spx.sphynx_destroy(h)
 
 
+def test_sell_slice_formats_follow_the_offset_range():
+    """A slice stores 16-bit offsets exactly when every short-row entry of its
+    32 rows lies within [-32768, 32767] of its row; the byte count a product
+    reads from the layout follows."""
+    import paper_2105_00578_gb300 as spx
+    for name in ("torus_wide", "rmat16", "grid27", "rmat"):
+        g = GRAPHS[name]
+        r = g.rows()
+        off = g.col.astype(np.int64) - r
+        deg = g.degrees()
+        short_entry = deg[r] <= 32
+        wide = np.zeros((g.n + 31) // 32, dtype=bool)
+        np.logical_or.at(wide, r >> 5, short_entry & ((off < -32768) | (off > 32767)))
+        h = spx.sphynx_create(g.row_ptr, g.col, g.w, None)
+        try:
+            info = spx.sphynx_get_info(h)
+            assert info["sell_slices"] == wide.size
+            assert info["sell_narrow_slices"] == int((~wide).sum()), name
+            if info["spmm_variant"] == 1:
+                short_per_slice = np.bincount(r[short_entry] >> 5, minlength=wide.size)
+                idx = float(np.sum(np.where(wide, 4, 2) * short_per_slice))
+                long_nnz = int(deg[deg > 32].sum())
+                n_items = int(np.sum((deg[deg > 32] + 4095) // 4096))
+                expect = idx + g.n + 8 * wide.size + 4 * long_nnz + 32 * n_items + 24 * int(np.sum(deg > 32))
+            else:
+                expect = 8 * (g.n + 1) + 4 * g.nnz
+            assert info["spmm_graph_bytes"] == pytest.approx(expect, rel=1e-12), name
+        finally:
+            spx.sphynx_destroy(h)
+
+
 def test_full_size_27_point_mesh_sampled_rows():
     """128^3 27-point mesh (the 2.1M-vertex workload): sampled rows of L_C X
     recomputed by the oracle row by row."""
@@ -91,7 +127,8 @@ def test_full_size_27_point_mesh_sampled_rows():
     h = spx.sphynx_create(g.row_ptr, g.col, None, None)
     try:
         rng = np.random.default_rng(5)
-        for dtype, ld in (("f32", 8), ("f64", 8), ("bf16", 8)):
+        for dtype, ld, variant in (("f32", 8, 0), ("f32", 8, 1), ("f64", 8, 1), ("bf16", 8, 1), ("bf16", 8, 0)):
+            spx.sphynx_set_spmm_variant(h, variant)
             x = rng.standard_normal((g.n, 7))
             xd = dev_block(x, ld, dtype)
             y = torch.zeros((g.n, ld), dtype=torch.float64 if dtype == "f64" else torch.float32, device="cuda")

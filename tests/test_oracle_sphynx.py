@@ -82,3 +82,76 @@ def test_problem_and_preconditioner_variants_agree_on_spectrum(prob, pc):
     ref = np.linalg.eigvalsh(O.laplacian_normalized(g).toarray())[:4]
     assert np.allclose(r.eigenvalues, ref, rtol=1e-5, atol=1e-12)
     assert r.imbalance == 83 * 8 / 660      # 660 unit vertices into 8 parts: best is 83
+
+
+def test_reference_block_layout():
+    z = O.reference_block(4, 5, 9)
+    state = mix64(9 + 5 * GAMMA)
+    v = mix64(state + (2 * 5 + 3 + 1) * GAMMA)   # entry (2, 3): counter i*d + j + 1
+    assert z[2, 3] == 2.0 * ((v >> 11) * 2.0 ** -53) - 1.0
+
+
+def test_eigen_clusters():
+    th = np.array([0.0, 1.0, 1.0 + 1e-9, 1.0 + 2e-9, 2.0, 3.0, 3.0 * (1 + 5e-4)])
+    assert O.eigen_clusters(th, 1e-3) == [(1, 3), (5, 6)]
+    assert O.eigen_clusters(th, 1e-4) == [(1, 3)]
+    # the eigenvalue-zero column never joins a cluster, even with a zero neighbour
+    assert O.eigen_clusters(np.array([0.0, 0.0, 1.0]), 1e-3) == []
+
+
+def _orthonormal(n, d, seed):
+    q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((n, d)))
+    return q
+
+
+def test_canonical_rotation_depends_on_the_span_only():
+    n, d = 300, 7
+    e = _orthonormal(n, d, 1)
+    th = np.array([0.0, 0.5, 0.5, 0.5, 0.9, 1.3, 1.3])
+    rng = np.random.default_rng(2)
+    ref = O.canonical_rotation(e, th, 1e-6, seed=4)
+    for _ in range(3):
+        r = e.copy()
+        for a, b in ((1, 3), (5, 6)):
+            q, _ = np.linalg.qr(rng.standard_normal((b - a + 1, b - a + 1)))
+            r[:, a:b + 1] = r[:, a:b + 1] @ q
+        got = O.canonical_rotation(r, th, 1e-6, seed=4)
+        assert np.allclose(got, ref, atol=1e-12)
+    # columns outside clusters are untouched; the result stays orthonormal and
+    # spans the same subspaces
+    assert np.array_equal(ref[:, [0, 4]], e[:, [0, 4]])
+    assert np.allclose(ref.T @ ref, np.eye(d), atol=1e-12)
+    for a, b in ((1, 3), (5, 6)):
+        p = e[:, a:b + 1] @ e[:, a:b + 1].T
+        assert np.allclose(p @ ref[:, a:b + 1], ref[:, a:b + 1], atol=1e-12)
+
+
+def test_canonical_rotation_is_the_procrustes_optimum():
+    n, d = 200, 4
+    e = _orthonormal(n, d, 3)
+    th = np.array([0.0, 2.0, 2.0, 2.0])
+    got = O.canonical_rotation(e, th, 1e-6, seed=7)
+    z = O.reference_block(n, d, 7)[:, 1:4]
+    best = np.trace(got[:, 1:4].T @ z)
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+        assert np.trace((e[:, 1:4] @ q).T @ z) <= best + 1e-12
+
+
+def test_degenerate_mesh_partition_independent_of_eigenvector_rotation():
+    """On a 27-point mesh the eigenvalues come in triples; once the clusters
+    are canonically rotated, the multi-jagged parts no longer depend on the
+    basis LOBPCG happened to return inside each triple."""
+    g = W.grid3d(16, 16, 16, 27)
+    res = O.partition(g, 64, problem="generalized", precond="poly", poly_degree=10, tol=1e-3, seed=2)
+    clusters = O.eigen_clusters(res.eigenvalues, 1e-3)
+    assert clusters == [(1, 3), (4, 6)]
+    rng = np.random.default_rng(0)
+    for _ in range(2):
+        e = res.eigvecs.copy()
+        for a, b in clusters:
+            q, _ = np.linalg.qr(rng.standard_normal((b - a + 1, b - a + 1)))
+            e[:, a:b + 1] = e[:, a:b + 1] @ q
+        coords = O.sign_normalise(O.canonical_rotation(e, res.eigenvalues, 1e-3, 2))[:, 1:]
+        assert np.array_equal(O.multijagged(np.ascontiguousarray(coords), None, 64), res.parts)

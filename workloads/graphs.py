@@ -20,6 +20,15 @@ from typing import Optional
 
 import numpy as np
 
+# graphs at least this large use the C helpers of _gen.c when gcc is available
+_NATIVE_MIN = 1 << 22
+
+
+def _native_lib():
+    from . import _native
+    return _native.lib()
+
+
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
@@ -228,9 +237,12 @@ def erdos_renyi(n: int, p: float, seed: int) -> CSRGraph:
     return symmetrize_edges(n, iu[keep], ju[keep], name=f"er{n}_{p}_{seed}")
 
 
-def largest_component(g: CSRGraph) -> CSRGraph:
+def largest_component(g: CSRGraph, native: Optional[bool] = None) -> CSRGraph:
     """Induced subgraph on the largest connected component, vertices kept in
     their original relative order (Sec. 6.1 keeps the largest component)."""
+    native = _native_lib() if (native or (native is None and g.nnz >= _NATIVE_MIN)) else None
+    if native is not None:
+        return _largest_component_native(native, g)
     import scipy.sparse as sp
     from scipy.sparse.csgraph import connected_components
 
@@ -256,15 +268,68 @@ def largest_component(g: CSRGraph) -> CSRGraph:
     return out
 
 
+def _largest_component_native(L, g: CSRGraph) -> CSRGraph:
+    """largest_component through the C helpers: same components, same
+    tie rule (the component whose smallest vertex comes first)."""
+    labels = np.empty(g.n, dtype=np.int64)
+    ncomp = L.gen_components(g.n, g.row_ptr.ctypes.data, g.col.ctypes.data, labels.ctypes.data)
+    if ncomp < 0:
+        raise MemoryError("components")
+    if ncomp == 1:
+        g.meta["n_before_lcc"] = g.n
+        return g
+    sizes = np.bincount(labels)
+    big = int(np.argmax(sizes))
+    nk = int(sizes[big])
+    kept = int(np.sum(np.diff(g.row_ptr)[labels == big]))
+    rp = np.empty(nk + 1, dtype=np.int64)
+    col = np.empty(kept, dtype=np.int32)
+    w = None if g.w is None else np.empty(kept, dtype=np.float32)
+    e = L.gen_induced(g.n, g.row_ptr.ctypes.data, g.col.ctypes.data, None if g.w is None else g.w.ctypes.data,
+                      labels.ctypes.data, big, rp.ctypes.data, col.ctypes.data, None if w is None else w.ctypes.data)
+    if e != kept:
+        raise RuntimeError("induced subgraph size mismatch")
+    out = CSRGraph(n=nk, row_ptr=rp, col=col, w=w, name=g.name + "_lcc")
+    out.meta = dict(g.meta)
+    out.meta["n_before_lcc"] = g.n
+    out.meta["components"] = int(ncomp)
+    return out
+
+
+def _rmat_native(L, scale: int, m: int, a: float, ab: float, abc: float, seed: int, name: str) -> CSRGraph:
+    n = 1 << scale
+    keys = np.empty(m, dtype=np.uint64)
+    L.gen_rmat_keys(scale, m, a, ab, abc, seed, keys.ctypes.data)
+    tmp = np.empty(m, dtype=np.uint64)
+    u = L.gen_sort_unique(keys.ctypes.data, tmp.ctypes.data, m, 2 * scale)
+    del tmp
+    if u < 0:
+        raise MemoryError("sort")
+    row_ptr = np.empty(n + 1, dtype=np.int64)
+    col = np.empty(2 * u, dtype=np.int32)
+    if L.gen_csr_from_keys(n, keys.ctypes.data, u, row_ptr.ctypes.data, col.ctypes.data) != 0:
+        raise MemoryError("csr")
+    return CSRGraph(n=n, row_ptr=row_ptr, col=col, name=name)
+
+
 def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
-         c: float = 0.19, seed: int = 3, lcc: bool = True, chunk: int = 1 << 24) -> CSRGraph:
+         c: float = 0.19, seed: int = 3, lcc: bool = True, chunk: int = 1 << 24,
+         native: Optional[bool] = None) -> CSRGraph:
     """R-MAT graph (Chakrabarti, Zhan, Faloutsos 2004): ``edge_factor * 2^scale``
     edge draws, each descending ``scale`` quadrant choices with probabilities
     (a, b, c, d).  Symmetrised, deduplicated, self-loops dropped and reduced to
-    the largest component.  Vertex ids are not permuted."""
+    the largest component.  Vertex ids are not permuted.  ``native`` selects
+    the C helpers (same graph; default: for large graphs when available)."""
     n = 1 << scale
     m = edge_factor * n
     ab, abc = a + b, a + b + c
+    L = _native_lib() if (native or (native is None and m >= _NATIVE_MIN)) else None
+    if native and L is None:
+        raise RuntimeError("native graph helpers unavailable")
+    if L is not None:
+        g = _rmat_native(L, scale, m, a, ab, abc, seed, f"rmat{scale}_ef{edge_factor}_s{seed}")
+        g.meta["edge_draws"] = m
+        return _largest_component_native(L, g) if lcc else g
     src = np.zeros(m, dtype=np.int64)
     dst = np.zeros(m, dtype=np.int64)
     for lo in range(0, m, chunk):
@@ -283,7 +348,7 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
     g = symmetrize_edges(n, src, dst, name=f"rmat{scale}_ef{edge_factor}_s{seed}")
     del src, dst
     g.meta["edge_draws"] = m
-    return largest_component(g) if lcc else g
+    return largest_component(g, native=native) if lcc else g
 
 
 def rgg(n: int, radius: Optional[float] = None, seed: int = 4, lcc: bool = True) -> CSRGraph:
@@ -302,9 +367,15 @@ def rgg(n: int, radius: Optional[float] = None, seed: int = 4, lcc: bool = True)
     return largest_component(g) if lcc else g
 
 
-def random_edge_weights(g: CSRGraph, lo: float = 0.5, hi: float = 1.5, seed: int = 5) -> CSRGraph:
+def random_edge_weights(g: CSRGraph, lo: float = 0.5, hi: float = 1.5, seed: int = 5,
+                        native: Optional[bool] = None) -> CSRGraph:
     """Attach FP32 weights uniform in [lo, hi), one draw per undirected edge
     (keyed by the unordered pair, so the weight matrix is symmetric)."""
+    L = _native_lib() if (native or (native is None and g.nnz >= _NATIVE_MIN)) else None
+    if L is not None:
+        w = np.empty(g.nnz, dtype=np.float32)
+        L.gen_edge_weights(g.n, g.row_ptr.ctypes.data, g.col.ctypes.data, float(lo), float(hi), seed, w.ctypes.data)
+        return dataclasses.replace(g, w=w, name=g.name + "_w", meta=dict(g.meta))
     rows = g.rows()
     cols = g.col.astype(np.int64)
     a = np.minimum(rows, cols)
