@@ -44,6 +44,11 @@ WORKLOADS = {
                     "dropped, largest component; normalized Laplacian, Jacobi, K=256 (d=9), tol 1e-2",
                K=256, laplacian="normalized", precond="jacobi", poly_degree=25, tol=1e-2, seed=3,
                precision="fp32", golden="c3_oracle.json"),
+    "c4": dict(desc="2000 random geometric graphs in one batched call (n log-uniform in [1e3, 2e5], mean degree "
+                    "about 8, largest component each), combinatorial Laplacian, Jacobi, K=8 (d=4) each, FP32 blocks "
+                    "with FP64 Rayleigh-Ritz, tol 1e-3; all LOBPCG iterations in one captured graph launch",
+               K=8, laplacian="combinatorial", precond="jacobi", poly_degree=25, tol=1e-3, seed=4,
+               precision="fp32", golden=None, batch=2000),
     "c5": dict(desc="R-MAT scale 24 (edge factor 16, a=.57 b=.19 c=.19), largest component, FP32 edge weights "
                     "uniform in [0.5, 1.5); normalized Laplacian, polynomial preconditioner degree 10, K=1024 "
                     "(d=11), BF16 polynomial chain, tol 1e-2",
@@ -181,10 +186,16 @@ def run_reference(args, world, rank):
     vals = []
     total_s = 0.0
     sample = ""
+    graphs = None
+    if w.get("batch"):
+        import workloads
+        graphs = workloads.rgg_batch(w["batch"])
     for _ in range(args.steps):
-        v, sample, s = oracle_sample(args.workload)
+        if graphs is not None:
+            v, sample = oracle_batch_sample(graphs, w, budget_s=20.0)
+        else:
+            v, sample, s = oracle_sample(args.workload)
         vals.append(v)
-        total_s += s
     value = float(np.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
@@ -194,6 +205,130 @@ def run_reference(args, world, rank):
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def oracle_batch_sample(graphs, w, budget_s: float = 20.0):
+    """The oracle on the batch's first graphs (in order, until about budget_s
+    of CPU work), extrapolated to the whole batch by vertex count."""
+    import oracle
+    done_n, t_used, used = 0, 0.0, 0
+    for gq in graphs:
+        t = time.perf_counter()
+        oracle.partition(gq, w["K"], problem=w["laplacian"], precond=w["precond"], tol=w["tol"], seed=w["seed"])
+        t_used += time.perf_counter() - t
+        done_n += gq.n
+        used += 1
+        if t_used >= budget_s:
+            break
+    total_n = sum(gq.n for gq in graphs)
+    est = t_used * total_n / done_n
+    sample = (f"oracle.partition on the first {used} graphs ({done_n} vertices, {t_used:.1f} s), extrapolated "
+              f"to the batch's {total_n} vertices by vertex count")
+    return len(graphs) / est, sample
+
+
+def run_batch(args, world, rank, local):
+    """The batch workload: all graphs partitioned by one sphynx_partition_batch
+    call per step (replicas on N > 1 GPUs)."""
+    import torch
+    import workloads
+    import paper_2105_00578_gb300 as spx
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WORKLOADS[args.workload]
+    precision = args.precision or w["precision"]
+    graphs = workloads.rgg_batch(w["batch"])
+    big, gptr = workloads.concat_graphs(graphs)
+    count = len(graphs)
+    stream = torch.cuda.current_stream()
+    h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr, stream=stream)
+    part = torch.empty(big.n, dtype=torch.int32, device="cuda")
+    opt = spx.options(laplacian=w["laplacian"], precond=w["precond"], precision=precision, tol=w["tol"],
+                      seed=w["seed"], out_device=True)
+
+    def step():
+        return spx.sphynx_partition_batch(h, w["K"], opt, part, count)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    res = []
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            res.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * count / (ms / 1000.0)
+    code, cuts, imbs, eigs, iters, status, st = res[-1]
+
+    # end to end: create from pinned host CSR, partition, read the part ids back
+    rp = torch.from_numpy(big.row_ptr).pin_memory()
+    cl = torch.from_numpy(big.col).pin_memory()
+    hp = torch.empty(big.n, dtype=torch.int32).pin_memory()
+    o_host = spx.options(laplacian=w["laplacian"], precond=w["precond"], precision=precision, tol=w["tol"],
+                         seed=w["seed"])
+    torch.cuda.synchronize()
+    barrier()
+    t = time.perf_counter()
+    e2e_steps = max(1, args.steps)
+    for _ in range(e2e_steps):
+        h2 = spx.sphynx_create_batch(rp.data_ptr(), cl.data_ptr(), gptr, stream=stream)
+        spx.sphynx_partition_batch(h2, w["K"], o_host, hp.data_ptr(), count)
+        spx.sphynx_destroy(h2)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample = oracle_batch_sample(graphs, w)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if precision != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": w["desc"], "K": w["K"], "graphs": count, "vertices": big.n, "nnz": big.nnz,
+                       "precision": precision,
+                       "l2": f"inputs larger than L2 (CSR column array {big.col.nbytes / 1e6:.0f} MB > 129 MB)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "graphs_converged": int(np.sum(status == 0)), "max_iterations": int(iters.max()),
+            "median_iterations": float(np.median(iters)), "mean_cut": float(np.mean(cuts)),
+            "max_imbalance": float(np.max(imbs)),
+            "roofline": None,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * count / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(big.row_ptr.nbytes + big.col.nbytes),
+                    "d2h_bytes_per_step": int(big.n * 4)},
+            "gpu_launches": int(st["kernel_launches"]),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    spx.sphynx_destroy(h)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -385,6 +520,8 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if WORKLOADS[args.workload].get("batch"):
+        return run_batch(args, world, rank, local)
     return run_ours(args, world, rank, local)
 
 

@@ -285,6 +285,39 @@ int sphynx_eval(sphynx_handle g, const int32_t *part, int32_t K, double *cut,
 int sphynx_partition(sphynx_handle g, int32_t K, const sphynx_options *opt, int32_t *part_out,
                      double *cut_out, double *imbalance_out, sphynx_stats *stats);
 
+/* A batch of graphs in one handle, for partitioning thousands of graphs of
+ * uneven sizes in one call (Algorithm 2 applied to every graph; the paper
+ * has no batched form).  The graphs come as one block-diagonal CSR over
+ * n = all vertices: graph q owns vertices [graph_ptr[q], graph_ptr[q+1]) and
+ * every edge of a graph stays inside that range (checked: INVALID_ARG).
+ * graph_ptr: host int64[count + 1], graph_ptr[0] = 0, graph_ptr[count] = n,
+ * every graph non-empty.  The other arguments, ownership and errors are
+ * those of sphynx_create; the handle also serves the single-step calls,
+ * which see the block-diagonal graph. */
+int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, const float *edge_w,
+                        const int64_t *vtx_w, const int64_t *graph_ptr, int32_t count, int64_t n,
+                        int64_t nnz, uint32_t flags, void *stream, sphynx_handle *out);
+
+/* Partition every graph of a batch handle into K parts: each graph gets its
+ * own LOBPCG (Algorithm 1: its own Ritz values, convergence test and soft
+ * locking), embedding and multi-jagged partition, as a single-graph call
+ * with the same options would; its random initial block is the one that call
+ * would draw.  The LOBPCG iterations of all graphs run as one CUDA graph
+ * launch whose conditional loop repeats on the device until every graph has
+ * converged or reached max_iter; a converged graph drops out.  Jacobi or no
+ * preconditioner, random initial block.
+ * part_out: int32[n] part ids local to each graph (0..K-1), host memory
+ * unless opt->flags has SPHYNX_OUT_DEVICE.  cuts, imbalances (double[count]),
+ * eigenvalues (double[count * d], d = floor(log2 K) + 1, each graph's Ritz
+ * values ascending), iterations and status (int32[count], OK or NOCONV per
+ * graph): host arrays, each may be NULL.  stats (may be NULL): status OK only if every graph
+ * converged, iterations = the largest.  Errors: INVALID_ARG (not a batch
+ * handle), UNSUPPORTED (polynomial preconditioner, piecewise start,
+ * K x count > 2^20), CUDA, OOM. */
+int sphynx_partition_batch(sphynx_handle g, int32_t K, const sphynx_options *opt, int32_t *part_out,
+                           double *cuts, double *imbalances, double *eigenvalues, int32_t *iterations,
+                           int32_t *status, sphynx_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,8 @@ def _load():
         "sphynx_eigensolve": (C.c_int, [vp, C.POINTER(Options), i32, pd, vp, i32, pd, pd, C.POINTER(Stats)]),
         "sphynx_mj": (C.c_int, [i32, vp, i32, i32, i64, vp, i32, vp, vp]),
         "sphynx_mj_noalloc": (C.c_int, [i32, vp, i32, i32, i64, vp, i32, vp, vp]),
+        "sphynx_create_batch": (C.c_int, [vp, vp, vp, vp, vp, i32, i64, i64, C.c_uint32, vp, C.POINTER(vp)]),
+        "sphynx_partition_batch": (C.c_int, [vp, i32, C.POINTER(Options), vp, vp, vp, vp, vp, vp, C.POINTER(Stats)]),
         "sphynx_eval": (C.c_int, [vp, vp, i32, pd, pd, pd]),
         "sphynx_partition": (C.c_int, [vp, i32, C.POINTER(Options), vp, pd, pd, C.POINTER(Stats)]),
     }
@@ -282,6 +284,38 @@ def sphynx_partition(h, K, opt: Options, part_out):
     code = check(LIB.sphynx_partition(h, K, C.byref(opt), ptr(part_out), C.byref(cut), C.byref(imb), C.byref(st)),
                  allow=(ERR_NOCONV, ERR_BREAKDOWN))
     return code, cut.value, imb.value, st.as_dict()
+
+
+def sphynx_create_batch(row_ptr, col, graph_ptr, edge_w=None, vtx_w=None, flags=HOST_PTRS, stream=None) -> int:
+    """Batch handle over a block-diagonal CSR; graph_ptr (host int64[count + 1])
+    gives each graph's vertex range."""
+    graph_ptr = np.ascontiguousarray(graph_ptr, np.int64)
+    n = int(graph_ptr[-1])
+    nnz = len(col) if not (flags & DEVICE_PTRS) else int(row_ptr[-1])
+    if not (flags & DEVICE_PTRS):
+        row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+        col = np.ascontiguousarray(col, np.int32)
+        edge_w = None if edge_w is None else np.ascontiguousarray(edge_w, np.float32)
+        vtx_w = None if vtx_w is None else np.ascontiguousarray(vtx_w, np.int64)
+    h = C.c_void_p()
+    check(LIB.sphynx_create_batch(ptr(row_ptr), ptr(col), ptr(edge_w), ptr(vtx_w), ptr(graph_ptr),
+                                  len(graph_ptr) - 1, n, int(nnz), int(flags), _stream(stream), C.byref(h)))
+    return h.value
+
+
+def sphynx_partition_batch(h, K, opt: Options, part_out, count):
+    """Partition every graph of a batch handle; returns (code, cuts, imbalances,
+    eigenvalues [count x d], iterations, status, stats) with per-graph numpy arrays."""
+    d = int(K).bit_length()
+    cuts = np.zeros(count)
+    imbs = np.zeros(count)
+    eigs = np.zeros((count, d))
+    iters = np.zeros(count, dtype=np.int32)
+    status = np.zeros(count, dtype=np.int32)
+    st = Stats()
+    code = check(LIB.sphynx_partition_batch(h, K, C.byref(opt), ptr(part_out), ptr(cuts), ptr(imbs), ptr(eigs),
+                                            ptr(iters), ptr(status), C.byref(st)))
+    return code, cuts, imbs, eigs, iters, status, st.as_dict()
 
 
 class Graph:

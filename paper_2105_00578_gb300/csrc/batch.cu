@@ -518,7 +518,7 @@ void batch_setup(sphynx_graph *g, const int64_t *h_gptr, int count) {
 // The batched partition: every graph's LOBPCG in one captured graph launch,
 // then the per-graph embedding, multi-jagged and metrics.
 void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *dpart, double *cuts, double *imbs,
-                     int32_t *iters, int32_t *status, sphynx_stats *stats) {
+                     double *eigs, int32_t *iters, int32_t *status, sphynx_stats *stats) {
   BatchInfo &B = g->batch;
   const int count = B.count;
   if (o->precond == SPHYNX_PRECOND_POLY)
@@ -534,6 +534,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     for (int q = 0; q < count; ++q) {
       if (cuts) cuts[q] = 0.0;
       if (imbs) imbs[q] = 1.0;
+      if (eigs) eigs[q] = 0.0;
       if (iters) iters[q] = 0;
       if (status) status[q] = SPHYNX_OK;
     }
@@ -767,6 +768,8 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     if (cuts) cuts[q] = ldexp(static_cast<double>(hcut[q]), g->weighted ? -(g->wscale + 1) : -1);
     if (imbs) imbs[q] = (static_cast<double>(mx) * static_cast<double>(K)) / static_cast<double>(tot);
     if (iters) iters[q] = hs[q].iters;
+    if (eigs)
+      for (int j = 0; j < d; ++j) eigs[static_cast<size_t>(q) * d + j] = hs[q].theta[j];
     const int sq = hs[q].done ? hs[q].status : SPHYNX_ERR_NOCONV;
     if (status) status[q] = sq;
     nconv_graphs += sq == SPHYNX_OK ? 1 : 0;
@@ -809,8 +812,8 @@ extern "C" int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, c
 }
 
 extern "C" int sphynx_partition_batch(sphynx_handle g, int32_t K, const sphynx_options *opt, int32_t *part_out,
-                                      double *cuts, double *imbalances, int32_t *iterations, int32_t *status,
-                                      sphynx_stats *stats) {
+                                      double *cuts, double *imbalances, double *eigenvalues, int32_t *iterations,
+                                      int32_t *status, sphynx_stats *stats) {
   return guarded([&]() -> int {
     if (!g || !part_out || !opt) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
     if (g->batch.count < 1) fail(SPHYNX_ERR_INVALID_ARG, "the handle is not a batch (use sphynx_create_batch)");
@@ -823,7 +826,7 @@ extern "C" int sphynx_partition_batch(sphynx_handle g, int32_t K, const sphynx_o
                              : static_cast<int32_t *>(g->workspace("part", static_cast<size_t>(g->n) * 4, false));
     if (stats) memset(stats, 0, sizeof(*stats));
     g->ctr.launches = 0;
-    batch_partition(g, K, opt, dpart, cuts, imbalances, iterations, status, stats);
+    batch_partition(g, K, opt, dpart, cuts, imbalances, eigenvalues, iterations, status, stats);
     if (!dev_out)
       SPX_CUDA(cudaMemcpyAsync(part_out, dpart, static_cast<size_t>(g->n) * 4, cudaMemcpyDeviceToHost, g->stream));
     SPX_CUDA(cudaStreamSynchronize(g->stream));

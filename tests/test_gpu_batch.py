@@ -1,0 +1,114 @@
+"""Batched partitions (many graphs in one call, one captured graph launch for
+all LOBPCG iterations) against the FP64 oracle run on every graph alone."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import torch_mod
+
+pytestmark = pytest.mark.gpu
+
+
+def _rggs(sizes, seed0):
+    return [W.rgg(n, seed=seed0 + i) for i, n in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_matches_oracle_per_graph(precision):
+    import paper_2105_00578_gb300 as spx
+    graphs = _rggs([300, 517, 1000, 1500, 2200, 2999, 800, 1200, 650], 40)
+    big, gptr = W.concat_graphs(graphs)
+    h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr, flags=spx.HOST_PTRS | spx.VALIDATE)
+    try:
+        opt = spx.options(laplacian="combinatorial", precond="jacobi", precision=precision, tol=1e-3, seed=4)
+        parts = np.full(big.n, -1, dtype=np.int32)
+        code, cuts, imbs, eigs, iters, status, st = spx.sphynx_partition_batch(h, 8, opt, parts, len(graphs))
+        assert code == 0 and st["status"] == 0
+        rtol = 1e-6 if precision == "fp64" else 1e-3
+        for q, gq in enumerate(graphs):
+            pq = parts[gptr[q]:gptr[q + 1]]
+            assert status[q] == 0
+            assert pq.min() >= 0 and pq.max() < 8
+            c, _ = O.cutsize(gq, pq)
+            assert c == cuts[q]
+            assert imbs[q] == O.imbalance(pq, None, 8)
+            ref = O.partition(gq, 8, problem="combinatorial", precond="jacobi", tol=1e-3, seed=4)
+            assert np.allclose(eigs[q, 1:], ref.eigenvalues[1:], rtol=rtol), q
+            assert abs(cuts[q] - ref.cut) <= 0.02 * ref.cut, (q, cuts[q], ref.cut)
+    finally:
+        spx.sphynx_destroy(h)
+
+
+def test_batch_graph_equals_its_single_graph_partition():
+    """A graph partitioned inside a batch draws the same initial block and
+    follows the same iteration as when partitioned alone (only the order of
+    reductions differs): iteration counts within two, converged Ritz values
+    within the accuracy of the solve."""
+    import paper_2105_00578_gb300 as spx
+    graphs = _rggs([700, 1800, 400], 60) + [W.grid2d(30, 20)]
+    big, gptr = W.concat_graphs(graphs)
+    h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr)
+    try:
+        opt = spx.options(laplacian="normalized", precond="jacobi", precision="fp64", tol=1e-3, seed=9)
+        parts = np.zeros(big.n, dtype=np.int32)
+        code, cuts, imbs, eigs, iters, status, _ = spx.sphynx_partition_batch(h, 4, opt, parts, len(graphs))
+        for q, gq in enumerate(graphs):
+            single = spx.Graph(gq)
+            p1, cut1, imb1, st1, code1 = single.partition(4, laplacian="normalized", precond="jacobi",
+                                                          precision="fp64", tol=1e-3, seed=9)
+            single.close()
+            assert code1 == 0 and status[q] == 0
+            assert abs(int(iters[q]) - st1["iterations"]) <= 2
+            assert np.allclose(eigs[q], st1["eigenvalues"], rtol=1e-5, atol=1e-12)
+    finally:
+        spx.sphynx_destroy(h)
+
+
+def test_batch_weighted_generalized_and_vertex_weights():
+    import paper_2105_00578_gb300 as spx
+    graphs = [W.random_edge_weights(g, 0.5, 1.5, 7) for g in _rggs([900, 1300, 500], 80)]
+    big, gptr = W.concat_graphs(graphs)
+    vw = W.random_vertex_weights(big.n, 1, 4, 3)
+    h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr, edge_w=big.w, vtx_w=vw)
+    try:
+        opt = spx.options(laplacian="generalized", precond="jacobi", precision="fp64", tol=1e-3, seed=2)
+        parts = np.zeros(big.n, dtype=np.int32)
+        code, cuts, imbs, eigs, iters, status, _ = spx.sphynx_partition_batch(h, 4, opt, parts, len(graphs))
+        for q, gq in enumerate(graphs):
+            pq = parts[gptr[q]:gptr[q + 1]]
+            vq = vw[gptr[q]:gptr[q + 1]]
+            ref = O.partition(gq, 4, problem="generalized", precond="jacobi", tol=1e-3, seed=2, vwts=vq)
+            assert np.allclose(eigs[q, 1:], ref.eigenvalues[1:], rtol=1e-6)
+            assert O.cutsize(gq, pq)[0] == cuts[q]
+            assert imbs[q] == O.imbalance(pq, vq, 4)
+    finally:
+        spx.sphynx_destroy(h)
+
+
+def test_batch_rejects_crossing_edges_and_unsupported_options():
+    import paper_2105_00578_gb300 as spx
+    a, b = W.grid2d(4, 4), W.grid2d(3, 3)
+    big, gptr = W.concat_graphs([a, b])
+    with pytest.raises(spx.SphynxError) as e:                 # offsets that cut a graph in two
+        spx.sphynx_create_batch(big.row_ptr, big.col, np.array([0, 10, big.n]))
+    assert e.value.code == spx.ERR_INVALID_ARG
+    h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr)
+    try:
+        parts = np.zeros(big.n, dtype=np.int32)
+        with pytest.raises(spx.SphynxError) as e:
+            spx.sphynx_partition_batch(h, 2, spx.options(precond="poly"), parts, 2)
+        assert e.value.code == spx.ERR_UNSUPPORTED
+        # K = 1: every vertex in part 0 of its graph
+        code, cuts, imbs, eigs, iters, status, _ = spx.sphynx_partition_batch(h, 1, spx.options(), parts, 2)
+        assert np.all(parts == 0) and np.all(cuts == 0) and np.all(imbs == 1.0)
+    finally:
+        spx.sphynx_destroy(h)
+    single = spx.sphynx_create(a.row_ptr, a.col)
+    try:
+        with pytest.raises(spx.SphynxError) as e:
+            spx.sphynx_partition_batch(single, 2, spx.options(), np.zeros(a.n, dtype=np.int32), 1)
+        assert e.value.code == spx.ERR_INVALID_ARG
+    finally:
+        spx.sphynx_destroy(single)

@@ -67,3 +67,11 @@ def test_native_largest_component_matches_numpy(native):
 def test_native_edge_weights_match_numpy(native):
     g = W.rmat(12, seed=9, native=False)
     _same(W.random_edge_weights(g, 0.5, 1.5, 5, native=False), W.random_edge_weights(g, 0.5, 1.5, 5, native=True))
+
+
+@pytest.mark.parametrize("n,seed", [(500, 4), (3000, 17), (20000, 5)])
+def test_native_rgg_matches_numpy(native, n, seed):
+    g = W.rgg(n, seed=seed, native=False)
+    h = W.rgg(n, seed=seed, native=True)
+    _same(g, h)
+    _simple_undirected(h)

@@ -22,4 +22,6 @@ from .graphs import (  # noqa: F401
     random_coords,
     random_vertex_weights,
     random_edge_weights,
+    concat_graphs,
+    rgg_batch,
 )

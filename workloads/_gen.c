@@ -187,3 +187,70 @@ void gen_edge_weights(int64_t n, const int64_t *row_ptr, const int32_t *col, dou
       w[k] = (float)(lo + (hi - lo) * u);
     }
 }
+
+/* Random geometric graph: points (x_i, y_i) = draw i + 1 of streams 21 and 22
+ * (as graphs.rgg draws them), joined when their distance is at most r.
+ * Pairs are found through a uniform grid of cells of side >= r and written as
+ * keys min * n + max (each pair once, unsorted).  Returns the number of keys,
+ * or -1 if more than cap would be written (or memory runs out). */
+int64_t gen_rgg_keys(int64_t n, double r, uint64_t seed, uint64_t *keys, int64_t cap) {
+  if (n < 1) return 0;
+  const uint64_t kx = stream_key(seed, 21), ky = stream_key(seed, 22);
+  double *x = (double *)malloc(sizeof(double) * (size_t)n), *y = (double *)malloc(sizeof(double) * (size_t)n);
+  int64_t nc = (int64_t)(1.0 / r);
+  if (nc < 1) nc = 1;
+  if (nc > 65536) nc = 65536;
+  const int64_t ncell = nc * nc;
+  int64_t *start = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
+  int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)n), *cell = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  if (!x || !y || !start || !order || !cell) {
+    free(x); free(y); free(start); free(order); free(cell);
+    return -1;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    x[i] = u01(kx, (uint64_t)i + 1);
+    y[i] = u01(ky, (uint64_t)i + 1);
+    int64_t cx = (int64_t)(x[i] * (double)nc), cy = (int64_t)(y[i] * (double)nc);
+    if (cx >= nc) cx = nc - 1;
+    if (cy >= nc) cy = nc - 1;
+    cell[i] = cy * nc + cx;
+    start[cell[i] + 1]++;
+  }
+  for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+  {
+    int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+    if (!cur) {
+      free(x); free(y); free(start); free(order); free(cell);
+      return -1;
+    }
+    memcpy(cur, start, sizeof(int64_t) * (size_t)ncell);
+    for (int64_t i = 0; i < n; ++i) order[cur[cell[i]]++] = i;
+    free(cur);
+  }
+  const double r2 = r * r;
+  int64_t m = 0;
+  for (int64_t i = 0; i < n && m >= 0; ++i) {
+    const int64_t cx = cell[i] % nc, cy = cell[i] / nc;
+    for (int64_t dy = -1; dy <= 1 && m >= 0; ++dy)
+      for (int64_t dx = -1; dx <= 1; ++dx) {
+        const int64_t ax = cx + dx, ay = cy + dy;
+        if (ax < 0 || ay < 0 || ax >= nc || ay >= nc) continue;
+        const int64_t c = ay * nc + ax;
+        for (int64_t k = start[c]; k < start[c + 1]; ++k) {
+          const int64_t j = order[k];
+          if (j <= i) continue;
+          const double ddx = x[i] - x[j], ddy = y[i] - y[j];
+          if (ddx * ddx + ddy * ddy <= r2) {
+            if (m >= cap) {
+              m = -1;
+              break;
+            }
+            keys[m++] = (uint64_t)i * (uint64_t)n + (uint64_t)j;
+          }
+        }
+        if (m < 0) break;
+      }
+  }
+  free(x); free(y); free(start); free(order); free(cell);
+  return m;
+}

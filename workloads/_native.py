@@ -58,5 +58,7 @@ def lib():
         L.gen_induced.restype = i64
         L.gen_edge_weights.argtypes = [i64, vp, vp, dbl, dbl, u64, vp]
         L.gen_edge_weights.restype = None
+        L.gen_rgg_keys.argtypes = [i64, dbl, u64, vp, i64]
+        L.gen_rgg_keys.restype = i64
         _LIB = L
         return _LIB

@@ -351,13 +351,34 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
     return largest_component(g, native=native) if lcc else g
 
 
-def rgg(n: int, radius: Optional[float] = None, seed: int = 4, lcc: bool = True) -> CSRGraph:
+def rgg(n: int, radius: Optional[float] = None, seed: int = 4, lcc: bool = True,
+        native: Optional[bool] = None) -> CSRGraph:
     """Random geometric graph: n points uniform in the unit square, joined
-    when closer than ``radius`` (default sqrt(8 / (pi n)), mean degree ~8)."""
-    from scipy.spatial import cKDTree
-
+    when at most ``radius`` apart (default sqrt(8 / (pi n)), mean degree ~8).
+    ``native`` selects the C helpers (same graph; default: when available)."""
     if radius is None:
         radius = float(np.sqrt(8.0 / (np.pi * n)))
+    L = _native_lib() if (native or native is None) else None
+    if native and L is None:
+        raise RuntimeError("native graph helpers unavailable")
+    if L is not None:
+        cap = 16 * n + 1024
+        while True:
+            keys = np.empty(cap, dtype=np.uint64)
+            m = L.gen_rgg_keys(n, radius, seed, keys.ctypes.data, cap)
+            if m >= 0:
+                break
+            cap *= 2
+        keys = keys[:m].copy()
+        tmp = np.empty(max(m, 1), dtype=np.uint64)
+        u = L.gen_sort_unique(keys.ctypes.data, tmp.ctypes.data, m, 2 * max(1, int(n - 1).bit_length()))
+        row_ptr = np.empty(n + 1, dtype=np.int64)
+        col = np.empty(2 * u, dtype=np.int32)
+        L.gen_csr_from_keys(n, keys.ctypes.data, u, row_ptr.ctypes.data, col.ctypes.data)
+        g = CSRGraph(n=n, row_ptr=row_ptr, col=col, name=f"rgg{n}_s{seed}")
+        g.meta["radius"] = radius
+        return _largest_component_native(L, g) if lcc else g
+    from scipy.spatial import cKDTree
     x = uniform01(seed, 21, n)
     y = uniform01(seed, 22, n)
     pts = np.stack([x, y], axis=1)
@@ -365,6 +386,40 @@ def rgg(n: int, radius: Optional[float] = None, seed: int = 4, lcc: bool = True)
     g = symmetrize_edges(n, pairs[:, 0], pairs[:, 1], name=f"rgg{n}_s{seed}")
     g.meta["radius"] = radius
     return largest_component(g) if lcc else g
+
+
+def rgg_batch(count: int = 2000, n_min: float = 1e3, n_max: float = 2e5, seed: int = 4) -> list:
+    """The batch workload: ``count`` random geometric graphs with sizes
+    log-uniform in [n_min, n_max] (n_i = floor(exp(ln n_min + u_i ln(n_max /
+    n_min))), u_i draw i + 1 of stream 61), radius sqrt(8 / (pi n_i)) (mean
+    degree about 8), graph i drawn with seed + i and reduced to its largest
+    component."""
+    u = uniform01(seed, 61, count)
+    sizes = np.floor(np.exp(np.log(n_min) + u * np.log(n_max / n_min))).astype(np.int64)
+    return [rgg(int(n), seed=seed + i) for i, n in enumerate(sizes)]
+
+
+def concat_graphs(graphs) -> tuple:
+    """Block-diagonal union of graphs (vertex ids shifted, weights kept when
+    every graph has them) and the offsets graph_ptr[count + 1] of each
+    graph's vertex range: the input of a batched partition."""
+    gptr = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for i, g in enumerate(graphs):
+        gptr[i + 1] = gptr[i] + g.n
+    eptr = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for i, g in enumerate(graphs):
+        eptr[i + 1] = eptr[i] + g.nnz
+    row_ptr = np.zeros(int(gptr[-1]) + 1, dtype=np.int64)
+    col = np.empty(int(eptr[-1]), dtype=np.int32)
+    weighted = all(g.w is not None for g in graphs)
+    w = np.empty(int(eptr[-1]), dtype=np.float32) if weighted else None
+    for i, g in enumerate(graphs):
+        row_ptr[gptr[i] + 1:gptr[i + 1] + 1] = g.row_ptr[1:] + eptr[i]
+        col[eptr[i]:eptr[i + 1]] = g.col + np.int32(gptr[i])
+        if weighted:
+            w[eptr[i]:eptr[i + 1]] = g.w
+    out = CSRGraph(n=int(gptr[-1]), row_ptr=row_ptr, col=col, w=w, name=f"batch{len(graphs)}")
+    return out, gptr
 
 
 def random_edge_weights(g: CSRGraph, lo: float = 0.5, hi: float = 1.5, seed: int = 5,
