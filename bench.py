@@ -292,7 +292,7 @@ def run_batch(args, world, rank, local):
     t = time.perf_counter()
     e2e_steps = max(1, args.steps)
     for _ in range(e2e_steps):
-        h2 = spx.sphynx_create_batch(rp.data_ptr(), cl.data_ptr(), gptr, stream=stream)
+        h2 = spx.sphynx_create_batch(rp.data_ptr(), cl.data_ptr(), gptr, stream=stream, nnz=big.nnz)
         spx.sphynx_partition_batch(h2, w["K"], o_host, hp.data_ptr(), count)
         spx.sphynx_destroy(h2)
     torch.cuda.synchronize()

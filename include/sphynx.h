@@ -156,10 +156,26 @@ typedef struct {
                                 column indices                                      */
   double spmm_graph_bytes;   /* bytes of graph structure one product reads with the
                                 chosen schedule (indices, weights, row metadata)   */
+  int32_t regular;           /* 1 if max degree <= 10 x average degree (Sec. 6.1)  */
+  int32_t spmm_med_max;      /* the autotuner's choice: rows with 33 to this many
+                                neighbours use the medium-row kernel (a lane per
+                                row), longer rows the long-row kernels (a warp per
+                                4096-entry piece); 32 means none are medium         */
 } sphynx_graph_info;
 
 /* Fill *opt with the defaults listed in sphynx_options. */
 void sphynx_default_options(sphynx_options *opt);
+
+/* Fill *opt with Sphynx's defaults for this graph and preconditioner
+ * (Sec. 6.3.1, decision flow of Fig. 2): the graph is regular when its
+ * largest degree is at most 10 times its average degree (Sec. 6.1; compared
+ * exactly as max_degree * n <= 10 * nnz).  Regular graphs get the
+ * combinatorial problem, tol 1e-3 and the random start; irregular graphs get
+ * the generalized problem (Jacobi or no preconditioner) or the normalized one
+ * (polynomial), tol 1e-2 and the piecewise-constant start (Sec. 6.2.1).
+ * precond: SPHYNX_PRECOND_*.  Other fields as sphynx_default_options.
+ * Errors: INVALID_ARG. */
+int sphynx_default_options_for(sphynx_handle g, int32_t precond, sphynx_options *opt);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *sphynx_last_error(void);
@@ -185,6 +201,13 @@ int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info);
  * sphynx_create does).  Both give the same products up to rounding order.
  * Errors: INVALID_ARG. */
 int sphynx_set_spmm_variant(sphynx_handle g, int32_t variant);
+
+/* Override the autotuner's medium-row ceiling: rows with 33 to med_max
+ * neighbours use the medium-row kernel, longer rows the long-row kernels
+ * (med_max in [32, 4096]; 32: no medium rows).  Rebuilds the handle's plan
+ * (reads row_ptr back from the device).  For tests and profiling.
+ * Errors: INVALID_ARG. */
+int sphynx_set_spmm_med_max(sphynx_handle g, int32_t med_max);
 
 /* Weighted degrees deg(v_i) (Sec. 3.2: the diagonal of L_C) into a device
  * double[n]. */

@@ -33,6 +33,25 @@ from .precond import jacobi_diag, gmres_poly_roots, poly_apply
 from .rng import reference_block, splitmix64_block
 
 
+def is_regular(g) -> bool:
+    """Sec. 6.1: a graph is regular when its largest degree is at most 10
+    times its average degree (degrees count neighbours)."""
+    deg = np.diff(g.row_ptr)
+    return int(deg.max()) * g.n <= 10 * int(g.row_ptr[-1])
+
+
+def default_options(g, precond: str) -> dict:
+    """Sphynx's defaults (Sec. 6.3.1, Fig. 2; initial vectors Sec. 6.2.1):
+    regular graphs use the combinatorial problem with tol 1e-3 (Jacobi and
+    polynomial preconditioners) and random initial vectors; irregular graphs
+    use the generalized problem (Jacobi) or the normalized problem
+    (polynomial), tol 1e-2 and piecewise-constant initial vectors."""
+    if is_regular(g):
+        return dict(problem=COMBINATORIAL, tol=1e-3, init="random", precond=precond)
+    return dict(problem=NORMALIZED if precond == "poly" else GENERALIZED, tol=1e-2, init="piecewise",
+                precond=precond)
+
+
 def num_eigenvectors(num_parts: int) -> int:
     """Eq. 4: d = floor(log2 K) + 1."""
     if num_parts < 1:

@@ -65,7 +65,8 @@ class GraphInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("max_degree", C.c_int64), ("max_wdegree", C.c_double),
                 ("total_vweight", C.c_int64), ("long_rows", C.c_int64), ("weighted", C.c_int32),
                 ("spmm_variant", C.c_int32), ("tuned_us_csr", C.c_float), ("tuned_us_sell", C.c_float),
-                ("sell_slices", C.c_int64), ("sell_narrow_slices", C.c_int64), ("spmm_graph_bytes", C.c_double)]
+                ("sell_slices", C.c_int64), ("sell_narrow_slices", C.c_int64), ("spmm_graph_bytes", C.c_double),
+                ("regular", C.c_int32), ("spmm_med_max", C.c_int32)]
 
 
 def _load():
@@ -90,6 +91,8 @@ def _load():
         "sphynx_eigensolve": (C.c_int, [vp, C.POINTER(Options), i32, pd, vp, i32, pd, pd, C.POINTER(Stats)]),
         "sphynx_mj": (C.c_int, [i32, vp, i32, i32, i64, vp, i32, vp, vp]),
         "sphynx_mj_noalloc": (C.c_int, [i32, vp, i32, i32, i64, vp, i32, vp, vp]),
+        "sphynx_set_spmm_med_max": (C.c_int, [vp, i32]),
+        "sphynx_default_options_for": (C.c_int, [vp, i32, C.POINTER(Options)]),
         "sphynx_create_batch": (C.c_int, [vp, vp, vp, vp, vp, i32, i64, i64, C.c_uint32, vp, C.POINTER(vp)]),
         "sphynx_partition_batch": (C.c_int, [vp, i32, C.POINTER(Options), vp, vp, vp, vp, vp, vp, C.POINTER(Stats)]),
         "sphynx_eval": (C.c_int, [vp, vp, i32, pd, pd, pd]),
@@ -204,6 +207,10 @@ def sphynx_set_spmm_variant(h, variant: int) -> None:
     check(LIB.sphynx_set_spmm_variant(h, variant))
 
 
+def sphynx_set_spmm_med_max(h, med_max: int) -> None:
+    check(LIB.sphynx_set_spmm_med_max(h, med_max))
+
+
 def sphynx_degrees(h, deg_out) -> None:
     check(LIB.sphynx_degrees(h, ptr(deg_out)))
 
@@ -286,13 +293,23 @@ def sphynx_partition(h, K, opt: Options, part_out):
     return code, cut.value, imb.value, st.as_dict()
 
 
-def sphynx_create_batch(row_ptr, col, graph_ptr, edge_w=None, vtx_w=None, flags=HOST_PTRS, stream=None) -> int:
+def sphynx_default_options_for(h, precond: str = "jacobi") -> "Options":
+    """Sphynx's defaults for this graph and preconditioner (Sec. 6.3.1)."""
+    o = Options()
+    check(LIB.sphynx_default_options_for(h, PRECONDS[precond], C.byref(o)))
+    return o
+
+
+def sphynx_create_batch(row_ptr, col, graph_ptr, edge_w=None, vtx_w=None, flags=HOST_PTRS, stream=None,
+                        nnz=None) -> int:
     """Batch handle over a block-diagonal CSR; graph_ptr (host int64[count + 1])
-    gives each graph's vertex range."""
+    gives each graph's vertex range.  nnz is needed when the arrays are given
+    as raw addresses."""
     graph_ptr = np.ascontiguousarray(graph_ptr, np.int64)
     n = int(graph_ptr[-1])
-    nnz = len(col) if not (flags & DEVICE_PTRS) else int(row_ptr[-1])
-    if not (flags & DEVICE_PTRS):
+    if nnz is None:
+        nnz = len(col)
+    if not (flags & DEVICE_PTRS) and not isinstance(col, int):
         row_ptr = np.ascontiguousarray(row_ptr, np.int64)
         col = np.ascontiguousarray(col, np.int32)
         edge_w = None if edge_w is None else np.ascontiguousarray(edge_w, np.float32)

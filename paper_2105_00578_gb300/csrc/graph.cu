@@ -3,6 +3,8 @@
 // (Eq. 1 cutsize and the imbalance of Sec. 3.1).
 #include "internal.cuh"
 
+#include <algorithm>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -187,6 +189,7 @@ __global__ void k_degrees(const int64_t *rp, const float *w, const int64_t *vw, 
 }
 
 // ---- Eq. 1 cutsize and part weights ----------------------------------------
+constexpr int kEvalRun = 64;   // entries per thread step of the cut
 __global__ void __launch_bounds__(256)
 k_eval(const int64_t *rp, const int32_t *col, const float *w, const int64_t *vw, int64_t n,
        const int32_t *part, int K, int wscale, unsigned long long *cut2, long long *pw, unsigned *badpart,
@@ -198,17 +201,32 @@ k_eval(const int64_t *rp, const int32_t *col, const float *w, const int64_t *vw,
   }
   unsigned long long acc = 0;
   unsigned bad = 0;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t tid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  // part weights: one vertex per thread step
+  for (int64_t i = tid; i < n; i += nthreads) {
     const int32_t pi = part[i];
     if (pi < 0 || pi >= K) { bad = 1; continue; }
     const long long wv = vw ? vw[i] : 1;
     if (use_smem) atomicAdd(reinterpret_cast<unsigned long long *>(&spw[pi]), static_cast<unsigned long long>(wv));
     else atomicAdd(reinterpret_cast<unsigned long long *>(&pw[pi]), static_cast<unsigned long long>(wv));
-    const int64_t a = rp[i], b = rp[i + 1];
-    for (int64_t e = a; e < b; ++e) {
-      const int32_t pj = part[col[e]];
-      if (pj != pi) {
+  }
+  // cut: runs of kEvalRun consecutive entries per thread step, whatever the
+  // row lengths; the run's first row comes from a binary search of row_ptr
+  const int64_t nnz = rp[n];
+  for (int64_t e0 = tid * kEvalRun; e0 < nnz; e0 += nthreads * kEvalRun) {
+    int64_t lo = 0, hi = n - 1;                 // last row with rp[row] <= e0
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (rp[mid] <= e0) lo = mid;
+      else hi = mid - 1;
+    }
+    int64_t row = lo;
+    const int64_t e1 = e0 + kEvalRun < nnz ? e0 + kEvalRun : nnz;
+    for (int64_t e = e0; e < e1; ++e) {
+      while (rp[row + 1] <= e) ++row;
+      const int32_t pi = part[row], pj = part[col[e]];
+      if (pi != pj && pi >= 0 && pi < K) {
         if (w) acc += static_cast<unsigned long long>(llrint(ldexp(static_cast<double>(w[e]), wscale)));
         else acc += 1;
       }
@@ -289,10 +307,33 @@ int grid_for(int64_t n) {
   return static_cast<int>(g);
 }
 
-void build_plan(sphynx_graph *g, const int64_t *host_rowptr) {
+// medium rows into their slices (one thread per lane slot)
+__global__ void k_med_fill(const int64_t *rp, const int32_t *col, const float *w, const int32_t *mrow,
+                           const int32_t *mdeg, const int64_t *mptr, int64_t nslices, int32_t *mcol, float *mw) {
+  const int64_t slot = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (slot >= nslices * 32) return;
+  const int row = mrow[slot];
+  if (row < 0) return;
+  const int d = mdeg[slot];
+  const int64_t src = rp[row], dst = mptr[slot >> 5] + (slot & 31);
+  for (int t = 0; t < d; ++t) {
+    mcol[dst + 32 * t] = col[src + t];
+    if (w) mw[dst + 32 * t] = w[src + t];
+  }
+}
+
+// Rows with more than kShortDeg neighbours: those with at most med_max go to
+// the medium slices (a lane per row), the rest to long-row work items (a warp
+// per 4096-entry item).  med_max = kShortDeg sends them all to the items.
+void build_plan(sphynx_graph *g, const int64_t *host_rowptr, int med_max) {
   SpmmPlan &p = g->plan;
   p.n_long = 0;
   p.n_items = 0;
+  p.n_med = 0;
+  p.n_med_slices = 0;
+  p.med_bytes = 0;
+  p.long_bytes = 0;
+  p.med_max = med_max;
   if (g->max_degree <= kShortDeg) return;
   std::vector<int64_t> rp_copy;
   const int64_t *rp = host_rowptr;
@@ -303,11 +344,47 @@ void build_plan(sphynx_graph *g, const int64_t *host_rowptr) {
     SPX_CUDA(cudaStreamSynchronize(g->stream));
     rp = rp_copy.data();
   }
+  // medium rows: sorted by degree, 32 to a slice
+  std::vector<std::pair<int64_t, int32_t>> med;   // (-degree, row)
+  for (int64_t i = 0; i < g->n; ++i) {
+    const int64_t dg = rp[i + 1] - rp[i];
+    if (dg > kShortDeg && dg <= med_max) med.emplace_back(-dg, static_cast<int32_t>(i));
+  }
+  std::sort(med.begin(), med.end());
+  p.n_med = static_cast<int64_t>(med.size());
+  p.n_med_slices = (p.n_med + 31) / 32;
+  if (p.n_med_slices > 0) {
+    const int64_t ns = p.n_med_slices;
+    std::vector<int32_t> mrow(static_cast<size_t>(ns) * 32, -1), mdeg(static_cast<size_t>(ns) * 32, 0);
+    std::vector<int64_t> mptr(static_cast<size_t>(ns) + 1, 0);
+    double entries = 0;
+    for (int64_t k = 0; k < p.n_med; ++k) {
+      mrow[k] = med[k].second;
+      mdeg[k] = static_cast<int32_t>(-med[k].first);
+      entries += static_cast<double>(-med[k].first);
+    }
+    for (int64_t s = 0; s < ns; ++s) mptr[s + 1] = mptr[s] + 32 * static_cast<int64_t>(mdeg[s * 32]);   // first lane: largest
+    p.med_row.alloc(mrow.size() * sizeof(int32_t));
+    p.med_deg.alloc(mdeg.size() * sizeof(int32_t));
+    p.med_ptr.alloc(mptr.size() * sizeof(int64_t));
+    p.med_col.alloc(static_cast<size_t>(mptr[ns]) * sizeof(int32_t));
+    if (g->weighted) p.med_w.alloc(static_cast<size_t>(mptr[ns]) * sizeof(float));
+    SPX_CUDA(cudaMemcpyAsync(p.med_row.p, mrow.data(), mrow.size() * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+    SPX_CUDA(cudaMemcpyAsync(p.med_deg.p, mdeg.data(), mdeg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
+    SPX_CUDA(cudaMemcpyAsync(p.med_ptr.p, mptr.data(), mptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
+    k_med_fill<<<static_cast<unsigned>((ns * 32 + 255) / 256), 256, 0, g->stream>>>(
+        g->rowptr, g->col, g->w, p.med_row.as<int32_t>(), p.med_deg.as<int32_t>(), p.med_ptr.as<int64_t>(), ns,
+        p.med_col.as<int32_t>(), p.med_w.as<float>());
+    SPX_LAUNCHED();
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
+    // real entries' indices (and weights), row ids and degrees of the lane slots, slice offsets
+    p.med_bytes = entries * (g->weighted ? 8.0 : 4.0) + static_cast<double>(ns) * (32.0 * 8.0 + 8.0);
+  }
   std::vector<int64_t> items, split;
   int64_t nnz_long = 0;
   for (int64_t i = 0; i < g->n; ++i) {
     const int64_t a = rp[i], b = rp[i + 1];
-    if (b - a <= kShortDeg) continue;
+    if (b - a <= med_max) continue;
     nnz_long += b - a;
     const int64_t first = static_cast<int64_t>(items.size() / 4);
     int64_t cnt = 0;
@@ -326,12 +403,16 @@ void build_plan(sphynx_graph *g, const int64_t *host_rowptr) {
   p.n_long = static_cast<int64_t>(split.size() / 3);
   p.long_bytes = static_cast<double>(nnz_long) * (g->weighted ? 8.0 : 4.0) + 32.0 * static_cast<double>(p.n_items) +
                  24.0 * static_cast<double>(p.n_long);
-  p.items.alloc(items.size() * sizeof(int64_t));
-  p.split.alloc(split.size() * sizeof(int64_t));
-  SPX_CUDA(cudaMemcpyAsync(p.items.p, items.data(), items.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
-  SPX_CUDA(cudaMemcpyAsync(p.split.p, split.data(), split.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
-  p.partials.alloc(static_cast<size_t>(p.n_items) * 16 * sizeof(double));
-  SPX_CUDA(cudaStreamSynchronize(g->stream));
+  if (p.n_items > 0) {
+    p.items.alloc(items.size() * sizeof(int64_t));
+    p.split.alloc(split.size() * sizeof(int64_t));
+    SPX_CUDA(cudaMemcpyAsync(p.items.p, items.data(), items.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                             g->stream));
+    SPX_CUDA(cudaMemcpyAsync(p.split.p, split.data(), split.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                             g->stream));
+    p.partials.alloc(static_cast<size_t>(p.n_items) * 16 * sizeof(double));
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
+  }
 }
 
 void build_sell(sphynx_graph *g) {
@@ -368,6 +449,7 @@ void build_sell(sphynx_graph *g) {
   }
   p.sell_entries = hptr[slices];
   p.sell_narrow = narrow;
+  p.short_entries = entries;
   // indices of the real entries, the degree bytes and one slice offset per slice
   // (plus the weights and their offsets on weighted graphs)
   p.sell_bytes = idx_bytes + static_cast<double>(n) + 8.0 * static_cast<double>(slices) +
@@ -390,7 +472,10 @@ void build_sell(sphynx_graph *g) {
 // The short-row schedule is a property of the graph's structure: both are
 // timed at create on a float 8-column product and the faster serves every
 // later product of the handle.
-void autotune_spmm(sphynx_graph *g) {
+// The autotuner: at create, times both short-row schedules and, on graphs with
+// rows longer than kShortDeg, the medium-row ceilings {kShortDeg, 128, kMedDeg}
+// on a float 8-column product, and keeps the fastest combination.
+void autotune_spmm(sphynx_graph *g, const int64_t *host_rowptr) {
   const int64_t n = g->n;
   const int ld = 8;
   DevBuf x, y;
@@ -406,10 +491,33 @@ void autotune_spmm(sphynx_graph *g) {
   a.b_true = ld;
   a.x = x.p;
   a.y = y.p;
-  const SpmmTuning t = spmm_tune(g, a);
-  g->plan.tuned_variant = t.variant;
-  g->plan.tuned_us[kCsrStaged] = t.us[kCsrStaged];
-  g->plan.tuned_us[kSell32] = t.us[kSell32];
+  std::vector<int> ceilings{kMedDeg};
+  if (g->max_degree > kShortDeg) ceilings = {kShortDeg, 128, kMedDeg};
+  std::vector<int64_t> rp_copy;
+  const int64_t *rp = host_rowptr;
+  if (!rp && ceilings.size() > 1) {
+    rp_copy.resize(static_cast<size_t>(n) + 1);
+    SPX_CUDA(cudaMemcpyAsync(rp_copy.data(), g->rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream));
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
+    rp = rp_copy.data();
+  }
+  float best = 1e30f;
+  int best_ceiling = kMedDeg;
+  SpmmTuning best_t{};
+  for (int c : ceilings) {
+    if (ceilings.size() > 1) build_plan(g, rp, c);
+    const SpmmTuning t = spmm_tune(g, a);
+    const float us = t.us[t.variant];
+    if (us < best) {
+      best = us;
+      best_ceiling = c;
+      best_t = t;
+    }
+  }
+  if (ceilings.size() > 1 && best_ceiling != ceilings.back()) build_plan(g, rp, best_ceiling);
+  g->plan.tuned_variant = best_t.variant;
+  g->plan.tuned_us[kCsrStaged] = best_t.us[kCsrStaged];
+  g->plan.tuned_us[kSell32] = best_t.us[kSell32];
   SPX_CUDA(cudaStreamSynchronize(g->stream));
 }
 
@@ -583,9 +691,9 @@ int sphynx_create(const int64_t *row_ptr, const int32_t *col, const float *edge_
       const double top = ldexp(1.0, h.max_exp + g->wscale) * static_cast<double>(nnz);
       g->wexact = top < 9.0e18;
     }
-    build_plan(g.get(), dev ? nullptr : row_ptr);
+    build_plan(g.get(), dev ? nullptr : row_ptr, kMedDeg);
     build_sell(g.get());
-    autotune_spmm(g.get());
+    autotune_spmm(g.get(), dev ? nullptr : row_ptr);
     *out = g.release();
     return SPHYNX_OK;
   });
@@ -608,17 +716,49 @@ int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info) {
     info->max_degree = g->max_degree;
     info->max_wdegree = g->max_wdeg;
     info->total_vweight = g->total_vw;
-    info->long_rows = g->plan.n_long;
+    info->long_rows = g->plan.n_med + g->plan.n_long;
     info->weighted = g->weighted ? 1 : 0;
     info->spmm_variant = g->plan.tuned_variant;
     info->tuned_us_csr = g->plan.tuned_us[kCsrStaged];
     info->tuned_us_sell = g->plan.tuned_us[kSell32];
+    info->regular = g->max_degree * g->n <= 10 * g->nnz ? 1 : 0;
+    info->spmm_med_max = g->plan.med_max;
     info->sell_slices = (g->n + 31) / 32;
     info->sell_narrow_slices = g->plan.sell_narrow;
-    info->spmm_graph_bytes = g->plan.tuned_variant == kSell32
-                                 ? g->plan.sell_bytes + g->plan.long_bytes
-                                 : 8.0 * static_cast<double>(g->n + 1) +
-                                       static_cast<double>(g->nnz) * (g->weighted ? 8.0 : 4.0);
+    info->spmm_graph_bytes = (g->plan.tuned_variant == kSell32
+                                  ? g->plan.sell_bytes
+                                  : 8.0 * static_cast<double>(g->n + 1) +
+                                        g->plan.short_entries * (g->weighted ? 8.0 : 4.0)) +
+                             g->plan.med_bytes + g->plan.long_bytes;
+    return SPHYNX_OK;
+  });
+}
+
+int sphynx_default_options_for(sphynx_handle g, int32_t precond, sphynx_options *opt) {
+  return guarded([&]() -> int {
+    if (!g || !opt) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
+    if (precond < SPHYNX_PRECOND_NONE || precond > SPHYNX_PRECOND_POLY) fail(SPHYNX_ERR_INVALID_ARG, "precond");
+    sphynx_default_options(opt);
+    opt->precond = precond;
+    const bool regular = g->max_degree * g->n <= 10 * g->nnz;   // max deg <= 10 x (nnz / n), exactly
+    if (regular) {
+      opt->laplacian = SPHYNX_COMBINATORIAL;
+      opt->tol = 1e-3;
+      opt->init = SPHYNX_INIT_RANDOM;
+    } else {
+      opt->laplacian = precond == SPHYNX_PRECOND_POLY ? SPHYNX_NORMALIZED : SPHYNX_GENERALIZED;
+      opt->tol = 1e-2;
+      opt->init = SPHYNX_INIT_PIECEWISE;
+    }
+    return SPHYNX_OK;
+  });
+}
+
+int sphynx_set_spmm_med_max(sphynx_handle g, int32_t med_max) {
+  return guarded([&]() -> int {
+    if (!g) fail(SPHYNX_ERR_INVALID_ARG, "NULL handle");
+    if (med_max < kShortDeg || med_max > kMedDeg) fail(SPHYNX_ERR_INVALID_ARG, "med_max %d", med_max);
+    build_plan(g, nullptr, med_max);
     return SPHYNX_OK;
   });
 }
@@ -628,7 +768,7 @@ int sphynx_set_spmm_variant(sphynx_handle g, int32_t variant) {
     if (!g) fail(SPHYNX_ERR_INVALID_ARG, "NULL handle");
     if (variant == -1) {
       g->plan.forced = -1;
-      autotune_spmm(g);
+      autotune_spmm(g, nullptr);
     } else if (variant == kCsrStaged || variant == kSell32) {
       g->plan.forced = variant;
     } else {

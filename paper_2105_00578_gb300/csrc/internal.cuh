@@ -86,7 +86,8 @@ __device__ inline double splitmix_pm1(uint64_t state, uint64_t ctr) {
   return 2.0 * (static_cast<double>(z >> 11) * 0x1.0p-53) - 1.0;
 }
 
-constexpr int kShortDeg = 32;        // rows with more neighbours use the long-row kernels
+constexpr int kShortDeg = 32;        // rows with more neighbours are medium or long rows
+constexpr int kMedDeg = 4096;        // rows with more neighbours than this are long rows
 constexpr int kLongChunk = 4096;     // entries per long-row work item
 constexpr int kSmCount = 152;
 
@@ -107,7 +108,7 @@ struct SpmmPlan {
   int tuned_variant = kCsrStaged;    // the autotuner's choice for this graph
   float tuned_us[2] = {0.f, 0.f};    // its timings of both schedules
   DevBuf tune_scratch;
-  int64_t n_long = 0;                // rows with degree > kShortDeg
+  int64_t n_long = 0;                // long rows: degree > kMedDeg
   int64_t n_items = 0;               // long-row work items
   DevBuf items;                      // int64 [n_items][4]: row, begin, end, slot
   DevBuf split;                      // int64 [n_long][3]: row, first slot, slot count
@@ -120,6 +121,7 @@ struct SpmmPlan {
   // present, are at sell_w[sell_ptr[s] + 32 t + lane].
   int64_t sell_entries = 0;          // padded entries of all slices
   int64_t sell_narrow = 0;           // slices stored with 16-bit offsets
+  double short_entries = 0;          // entries of the rows with at most kShortDeg neighbours
   double sell_bytes = 0;             // bytes a product must read from this layout:
                                      // real entries' indices, degrees, slice offsets
   DevBuf sell_ptr;                   // int64 [n_slices + 1], entry offsets
@@ -128,6 +130,18 @@ struct SpmmPlan {
   DevBuf sell_w;                     // float [sell_entries] (weighted graphs)
   DevBuf sell_deg;                   // uint8 [n]: degree, or 0xFF for a long row
   double long_bytes = 0;             // bytes of the long rows' CSR entries and items
+  // Medium rows (kShortDeg < degree <= kMedDeg), sorted by degree (descending,
+  // row id on ties) and packed 32 to a slice: lane l of slice s is row
+  // med_row[32 s + l] (-1: padding) with med_deg[32 s + l] entries, entry t at
+  // med_col[med_ptr[s] + 32 t + l] (weights likewise in med_w).
+  int med_max = kMedDeg;             // largest degree of a medium row (the autotuner's choice)
+  int64_t n_med = 0, n_med_slices = 0;
+  DevBuf med_row;                    // int32 [32 n_med_slices]
+  DevBuf med_deg;                    // int32 [32 n_med_slices]
+  DevBuf med_ptr;                    // int64 [n_med_slices + 1]
+  DevBuf med_col;                    // int32 [padded entries]
+  DevBuf med_w;                      // float [padded entries] (weighted graphs)
+  double med_bytes = 0;              // bytes a product reads from the medium slices
 };
 
 // Everything the iteration kernels need to apply L without forming it.

@@ -95,8 +95,10 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
   const double si = static_cast<double>(dt_size(a.tin));
   const double sa = a.tin == DT::F64 ? 8.0 : 4.0;
   const double b = static_cast<double>(a.b_true);
-  const double graph_bytes = g->plan.variant == kSell32 ? g->plan.sell_bytes + g->plan.long_bytes
-                                                        : 8.0 * (n + 1) + nnz * (g->weighted ? 8.0 : 4.0);
+  const double graph_bytes =
+      (g->plan.variant == kSell32 ? g->plan.sell_bytes
+                                  : 8.0 * (n + 1) + g->plan.short_entries * (g->weighted ? 8.0 : 4.0)) +
+      g->plan.med_bytes + g->plan.long_bytes;
   double bytes = graph_bytes + n * b * si + n * sa;
   if (a.mode == 0) {
     bytes += n * b * sa;

@@ -378,6 +378,11 @@ template <typename TI, int BP> struct RowAcc {
       }
     }
   }
+  __device__ __forceinline__ void merge(const RowAcc &o) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) v[q] = add2(v[q], o.v[q]);
+    s += o.s;
+  }
   __device__ __forceinline__ void get(float (&o)[BP]) const {
     if constexpr (BP == 1) {
       o[0] = s;
@@ -391,6 +396,70 @@ template <typename TI, int BP> struct RowAcc {
     }
   }
 };
+// bfloat16 inputs: plain float accumulators.  Unpacking a bfloat16 pair costs
+// two integer operations either way, and two scalar adds issue faster here than
+// packing the pair and one add.f32x2 (measured on the 27-point mesh chain step).
+template <int BP> struct RowAcc<__nv_bfloat16, BP> {
+  float a[BP];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int c = 0; c < BP; ++c) a[c] = 0.f;
+  }
+  // NW words of 2 values each (low half first) into columns c0, c0 + 1, ...
+  template <bool COEF, int NW>
+  __device__ __forceinline__ void add_words(const unsigned *w, int c0, float coef) {
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      if (c0 + 2 * i >= BP) break;
+      const float lo = __uint_as_float(w[i] << 16), hi = __uint_as_float(w[i] & 0xffff0000u);
+      a[c0 + 2 * i] = COEF ? fmaf(coef, lo, a[c0 + 2 * i]) : a[c0 + 2 * i] + lo;
+      a[c0 + 2 * i + 1] = COEF ? fmaf(coef, hi, a[c0 + 2 * i + 1]) : a[c0 + 2 * i + 1] + hi;
+    }
+  }
+  template <bool COEF>
+  __device__ __forceinline__ void add(const __nv_bfloat16 *__restrict__ p, float coef) {
+    if constexpr (BP % 8 == 0) {
+#pragma unroll
+      for (int c = 0; c < BP; c += 8) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p + c));
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+        add_words<COEF, 4>(w, c, coef);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < BP; c += 4) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p + c));
+        const unsigned w[2] = {q.x, q.y};
+        add_words<COEF, 2>(w, c, coef);
+      }
+    }
+  }
+  template <bool COEF>
+  __device__ __forceinline__ void accum(const RawRow<__nv_bfloat16, BP> &r, float coef) {
+    if constexpr (RawRow<__nv_bfloat16, BP>::kWide) {
+#pragma unroll
+      for (int k = 0; k < BP / 8; ++k) {
+        const unsigned w[4] = {r.q[k].x, r.q[k].y, r.q[k].z, r.q[k].w};
+        add_words<COEF, 4>(w, 8 * k, coef);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < BP / 4; ++k) {
+        const unsigned w[2] = {r.h[k].x, r.h[k].y};
+        add_words<COEF, 2>(w, 4 * k, coef);
+      }
+    }
+  }
+  __device__ __forceinline__ void merge(const RowAcc &o) {
+#pragma unroll
+    for (int c = 0; c < BP; ++c) a[c] += o.a[c];
+  }
+  __device__ __forceinline__ void get(float (&o)[BP]) const {
+#pragma unroll
+    for (int c = 0; c < BP; ++c) o[c] = a[c];
+  }
+};
+
 template <int BP> struct RowAcc<double, BP> {
   double v[BP];
   __device__ __forceinline__ void zero() {
@@ -408,6 +477,10 @@ template <int BP> struct RowAcc<double, BP> {
   __device__ __forceinline__ void accum(const RawRow<double, BP> &r, double coef) {
 #pragma unroll
     for (int c = 0; c < BP; ++c) v[c] = COEF ? fma(coef, r.v[c], v[c]) : v[c] + r.v[c];
+  }
+  __device__ __forceinline__ void merge(const RowAcc &o) {
+#pragma unroll
+    for (int c = 0; c < BP; ++c) v[c] += o.v[c];
   }
   __device__ __forceinline__ void get(double (&o)[BP]) const {
 #pragma unroll
@@ -594,8 +667,18 @@ k_spmm_short(const LapView L, const SpmmDev a) {
 // 128 bytes of 32-bit indices), so column reads are coalesced without shared
 // memory and all of L1 is left to the X gathers.  The slice's format is
 // uniform over the warp.
+// Resident 128-thread blocks the gather-latency-bound SELL kernel asks for:
+// 16 (32 registers a thread, every warp slot of the SM) for rows of at most
+// 16 bytes, 8 (64 registers) for 32-byte float rows.
+template <typename TI, int BP> struct SellOccupancy {
+  static constexpr int blocks =
+      ((std::is_same<TI, __nv_bfloat16>::value && BP <= 8) || (std::is_same<TI, float>::value && BP <= 4))
+          ? 16
+          : (std::is_same<TI, float>::value && BP == 8 ? 8 : 1);
+};
+
 template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, SellOccupancy<TI, BP>::blocks)
 k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, const float *__restrict__ sw,
             const int64_t *__restrict__ sptr, const int64_t *__restrict__ cptr, const uint8_t *__restrict__ sdeg) {
   using TA = typename AccOf<TI>::T;
@@ -625,6 +708,47 @@ k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, 
         acc);
   }
   if (sd == 0xFF) return;   // padding lane or a long row
+  TA sum[BP];
+  acc.get(sum);
+  spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
+}
+
+// Medium rows (kShortDeg < degree <= kMedDeg): a warp per slice of 32 rows of
+// similar degree (sorted at create), lane = row, entry t of the 32 rows one
+// contiguous 128-byte segment; the row's result goes to its own index.  A lane
+// sums its row in blocks of kShortDeg entries and then adds the block sums, so
+// rounding grows with d / 32 + 32 rather than with d (a row's products must
+// cancel to rounding level for the Laplacian's null vector).
+template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
+__global__ void __launch_bounds__(128)
+k_spmm_med(const LapView L, const SpmmDev a, const int32_t *__restrict__ mcol, const float *__restrict__ mw,
+           const int64_t *__restrict__ mptr, const int32_t *__restrict__ mrow, const int32_t *__restrict__ mdeg,
+           int64_t nslices) {
+  using TA = typename AccOf<TI>::T;
+  if (a.done && *a.done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t slice = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (slice >= nslices) return;  // uniform per warp
+  const int row = mrow[slice * 32 + lane];
+  const int d = row >= 0 ? mdeg[slice * 32 + lane] : 0;
+  const int64_t base = __ldg(mptr + slice);
+  const int32_t *cp = mcol + base + lane;
+  const float *wp = W ? mw + base + lane : nullptr;
+  const TI *__restrict__ x = static_cast<const TI *>(a.x);
+  RowAcc<TI, BP> acc;
+  acc.zero();
+  for (int t0 = 0; t0 < d; t0 += kShortDeg) {
+    RowAcc<TI, BP> blk;
+    blk.zero();
+    const int dd = d - t0 < kShortDeg ? d - t0 : kShortDeg;
+    const int32_t *cpb = cp + 32 * t0;
+    const float *wpb = W ? wp + 32 * t0 : nullptr;
+    spmm_row<LAP, TI, BP, W>(
+        L, x, a.ldx, dd, [&](int t) { return __ldcs(cpb + 32 * t); }, [&](int t) { return __ldcs(wpb + 32 * t); },
+        blk);
+    acc.merge(blk);
+  }
+  if (row < 0) return;
   TA sum[BP];
   acc.get(sum);
   spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
@@ -694,6 +818,14 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
     } else {
       k_spmm_short<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 32 * kWarpsPerCta, 0, st>>>(L, a);
     }
+    SPX_LAUNCHED();
+    g->ctr.launches++;
+  }
+  if (g->plan.n_med_slices > 0) {
+    const int64_t gm = (g->plan.n_med_slices * 32 + 127) / 128;
+    k_spmm_med<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(gm), 128, 0, st>>>(
+        L, a, g->plan.med_col.as<int32_t>(), g->plan.med_w.as<float>(), g->plan.med_ptr.as<int64_t>(),
+        g->plan.med_row.as<int32_t>(), g->plan.med_deg.as<int32_t>(), g->plan.n_med_slices);
     SPX_LAUNCHED();
     g->ctr.launches++;
   }

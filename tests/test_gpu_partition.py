@@ -153,3 +153,20 @@ def test_c2_full_size_mixed_and_fp64():
         for j in range(1, 7):
             assert got[j] <= 1e-3 * abs(theta[j]) + floor, (precision, j, got[j], theta[j])
     graph.close()
+
+
+def test_default_options_follow_the_oracle_decision_flow():
+    import paper_2105_00578_gb300 as spx
+    names = {spx.COMBINATORIAL: "combinatorial", spx.GENERALIZED: "generalized", spx.NORMALIZED: "normalized"}
+    inits = {spx.INIT_RANDOM: "random", spx.INIT_PIECEWISE: "piecewise"}
+    for g in (W.grid3d(6, 5, 4, 27), W.star_graph(20), W.star_graph(21), W.rmat(12, seed=3)):
+        h = spx.sphynx_create(g.row_ptr, g.col)
+        try:
+            assert spx.sphynx_get_info(h)["regular"] == int(O.is_regular(g))
+            for pc in ("jacobi", "poly", "none"):
+                o = spx.sphynx_default_options_for(h, pc)
+                ref = O.default_options(g, pc)
+                assert (names[o.laplacian], o.tol, inits[o.init]) == (ref["problem"], ref["tol"], ref["init"])
+                assert o.precond == spx.PRECONDS[pc]
+        finally:
+            spx.sphynx_destroy(h)

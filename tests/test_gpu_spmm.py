@@ -51,13 +51,18 @@ def test_spmm_matches_oracle(gname, lap, dtype, ncols):
         xin = x if dtype == "f64" else (x.astype(np.float32).astype(np.float64) if dtype == "f32" else bf16_round(x))
         ref = O.operator_for(g, lap) @ xin
         tol = 1e-13 if dtype == "f64" else 2e-6
-        for variant in (0, 1):                 # CSR staged, SELL-32
-            spx.sphynx_set_spmm_variant(h, variant)
-            y.zero_()
-            spx.sphynx_laplacian_apply(h, lap, dt, xd, ld, y, ld, ncols)
-            torch.cuda.synchronize()
-            got = y.cpu().numpy().astype(np.float64)[:, :ncols]
-            assert rel_err(got, ref) < tol, variant
+        # every short-row schedule and, on graphs with longer rows, every
+        # medium-row ceiling the autotuner chooses from
+        ceilings = (32, 128, 4096) if int(g.degrees().max()) > 32 else (4096,)
+        for med_max in ceilings:
+            spx.sphynx_set_spmm_med_max(h, med_max)
+            for variant in (0, 1):                 # CSR staged, SELL-32
+                spx.sphynx_set_spmm_variant(h, variant)
+                y.zero_()
+                spx.sphynx_laplacian_apply(h, lap, dt, xd, ld, y, ld, ncols)
+                torch.cuda.synchronize()
+                got = y.cpu().numpy().astype(np.float64)[:, :ncols]
+                assert rel_err(got, ref) < tol, (variant, med_max)
             # padding columns stay zero when the input padding is zero
             if ld > ncols and ncols > 1:
                 assert np.all(y.cpu().numpy()[:, ncols:] == 0)
@@ -105,17 +110,58 @@ def test_sell_slice_formats_follow_the_offset_range():
             info = spx.sphynx_get_info(h)
             assert info["sell_slices"] == wide.size
             assert info["sell_narrow_slices"] == int((~wide).sum()), name
+            # medium rows (33 to the tuned ceiling): their entries, row id and
+            # degree per lane slot of 32-row slices, one offset per slice; long
+            # rows: CSR entries, 32 bytes per 4096-entry item and 24 per row
+            mm = info["spmm_med_max"]
+            assert mm in (32, 128, 4096)
+            med = (deg > 32) & (deg <= mm)
+            n_ms = (int(med.sum()) + 31) // 32
+            med_bytes = 4.0 * deg[med].sum() + n_ms * (32 * 8 + 8)
+            lng = deg > mm
+            long_bytes = 4.0 * deg[lng].sum() + 32 * int(np.sum((deg[lng] + 4095) // 4096)) + 24 * int(lng.sum())
             if info["spmm_variant"] == 1:
                 short_per_slice = np.bincount(r[short_entry] >> 5, minlength=wide.size)
                 idx = float(np.sum(np.where(wide, 4, 2) * short_per_slice))
-                long_nnz = int(deg[deg > 32].sum())
-                n_items = int(np.sum((deg[deg > 32] + 4095) // 4096))
-                expect = idx + g.n + 8 * wide.size + 4 * long_nnz + 32 * n_items + 24 * int(np.sum(deg > 32))
+                expect = idx + g.n + 8 * wide.size
             else:
-                expect = 8 * (g.n + 1) + 4 * g.nnz
+                expect = 8 * (g.n + 1) + 4 * deg[deg <= 32].sum()
+            expect += med_bytes + long_bytes
             assert info["spmm_graph_bytes"] == pytest.approx(expect, rel=1e-12), name
         finally:
             spx.sphynx_destroy(h)
+
+
+@pytest.mark.parametrize("lap", ["normalized", "combinatorial"])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_null_vector_is_annihilated_to_rounding(lap, dtype):
+    """L D^{1/2} 1 = 0 (L_N) and L 1 = 0 (L_C): the products of a row must
+    cancel to rounding level even for rows of thousands of entries (LOBPCG
+    recognises the eigenvalue-zero column by it).  Bound: about (32 + d / 32)
+    roundings of a row's largest term, as the blocked per-lane summation
+    gives, times a safety factor of 4."""
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    g = W.random_edge_weights(GRAPHS["rmat16"], 0.5, 1.5, 3) if lap == "combinatorial" else GRAPHS["rmat16"]
+    deg = O.weighted_degree(g)
+    z = np.sqrt(deg) if lap == "normalized" else np.ones(g.n)
+    h = spx.sphynx_create(g.row_ptr, g.col, g.w, None)
+    try:
+        xd = dev_block(z[:, None], 1, dtype)
+        y = torch.zeros((g.n, 1), dtype=torch.float64 if dtype == "f64" else torch.float32, device="cuda")
+        for variant, med_max in ((0, 4096), (1, 4096), (1, 128), (1, 32)):
+            spx.sphynx_set_spmm_med_max(h, med_max)
+            spx.sphynx_set_spmm_variant(h, variant)
+            spx.sphynx_laplacian_apply(h, lap, spx.DT_F64 if dtype == "f64" else spx.DT_F32, xd, 1, y, 1, 1)
+            torch.cuda.synchronize()
+            got = np.abs(y.cpu().numpy().astype(np.float64)[:, 0])
+            u = 2.0 ** -24 if dtype == "f32" else 2.0 ** -53
+            d = np.diff(g.row_ptr)
+            scale = z if lap == "normalized" else deg     # size of a row's largest partial sums
+            bound = 4 * u * (32 + d / 32 + 1) * np.maximum(scale, 1.0)
+            assert np.all(got <= bound), (variant, float(np.max(got / bound)))
+    finally:
+        spx.sphynx_destroy(h)
 
 
 def test_full_size_27_point_mesh_sampled_rows():

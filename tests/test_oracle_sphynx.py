@@ -155,3 +155,25 @@ def test_degenerate_mesh_partition_independent_of_eigenvector_rotation():
             e[:, a:b + 1] = e[:, a:b + 1] @ q
         coords = O.sign_normalise(O.canonical_rotation(e, res.eigenvalues, 1e-3, 2))[:, 1:]
         assert np.array_equal(O.multijagged(np.ascontiguousarray(coords), None, 64), res.parts)
+
+
+def test_graph_type_and_defaults_follow_the_decision_flow():
+    # meshes: max/avg degree near 1 (Sec. 6.1 quotes 1.00 to 4.36 for its regular graphs)
+    mesh = W.grid3d(6, 5, 4, 27)
+    assert O.is_regular(mesh)
+    assert O.default_options(mesh, "jacobi") == dict(problem="combinatorial", tol=1e-3, init="random",
+                                                     precond="jacobi")
+    assert O.default_options(mesh, "poly")["problem"] == "combinatorial"
+    # a star: one vertex adjacent to all others, ratio about n / 2
+    star = W.star_graph(100)
+    assert not O.is_regular(star)
+    assert O.default_options(star, "jacobi") == dict(problem="generalized", tol=1e-2, init="piecewise",
+                                                     precond="jacobi")
+    assert O.default_options(star, "poly")["problem"] == "normalized"
+    # the boundary: max degree exactly 10 x average is still regular
+    # (star of 11 vertices: max 10, average 20 / 11; ratio 5.5 -> regular)
+    assert O.is_regular(W.star_graph(11))
+    # 20 vertices: max 19, average 38 / 20, ratio exactly 10 -> regular
+    assert O.is_regular(W.star_graph(20))
+    # 21 vertices: max 20, average 40 / 21, ratio 10.5 -> irregular
+    assert not O.is_regular(W.star_graph(21))
