@@ -48,7 +48,7 @@ WORKLOADS = {
                     "about 8, largest component each), combinatorial Laplacian, Jacobi, K=8 (d=4) each, FP32 blocks "
                     "with FP64 Rayleigh-Ritz, tol 1e-3; all LOBPCG iterations in one captured graph launch",
                K=8, laplacian="combinatorial", precond="jacobi", poly_degree=25, tol=1e-3, seed=4,
-               precision="fp32", golden=None, batch=2000),
+               precision="fp32", golden=None, batch=2000, stall_window=50),
     "c5": dict(desc="R-MAT scale 24 (edge factor 16, a=.57 b=.19 c=.19), largest component, FP32 edge weights "
                     "uniform in [0.5, 1.5); normalized Laplacian, polynomial preconditioner degree 10, K=1024 "
                     "(d=11), BF16 polynomial chain, tol 1e-2",
@@ -133,6 +133,23 @@ class Clocks:
         reasons = sorted({names[i - 5] for r in rows for i in range(5, 9) if "Active" in r[i] and "Not" not in r[i]})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The largest of every rank's value (the slowest rank sets the job's
+    time); the value itself on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1000.0)
 
 
 def dist_env():
@@ -248,7 +265,7 @@ def run_batch(args, world, rank, local):
     h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr, stream=stream)
     part = torch.empty(big.n, dtype=torch.int32, device="cuda")
     opt = spx.options(laplacian=w["laplacian"], precond=w["precond"], precision=precision, tol=w["tol"],
-                      seed=w["seed"], out_device=True)
+                      seed=w["seed"], out_device=True, stall_window=w.get("stall_window", 0))
 
     def step():
         return spx.sphynx_partition_batch(h, w["K"], opt, part, count)
@@ -273,12 +290,8 @@ def run_batch(args, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * count / (ms / 1000.0)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    value = job_throughput(count, ms, world)
     code, cuts, imbs, eigs, iters, status, st = res[-1]
 
     # end to end: create from pinned host CSR, partition, read the part ids back
@@ -286,7 +299,7 @@ def run_batch(args, world, rank, local):
     cl = torch.from_numpy(big.col).pin_memory()
     hp = torch.empty(big.n, dtype=torch.int32).pin_memory()
     o_host = spx.options(laplacian=w["laplacian"], precond=w["precond"], precision=precision, tol=w["tol"],
-                         seed=w["seed"])
+                         seed=w["seed"], stall_window=w.get("stall_window", 0))
     torch.cuda.synchronize()
     barrier()
     t = time.perf_counter()
@@ -296,11 +309,7 @@ def run_batch(args, world, rank, local):
         spx.sphynx_partition_batch(h2, w["K"], o_host, hp.data_ptr(), count)
         spx.sphynx_destroy(h2)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t) / e2e_steps, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample = oracle_batch_sample(graphs, w)
@@ -314,7 +323,9 @@ def run_batch(args, world, rank, local):
                        "precision": precision,
                        "l2": f"inputs larger than L2 (CSR column array {big.col.nbytes / 1e6:.0f} MB > 129 MB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "graphs_converged": int(np.sum(status == 0)), "max_iterations": int(iters.max()),
+            "graphs_converged": int(np.sum(status == 0)),
+            "graphs_stalled": int(np.sum((status != 0) & (iters < 1000))),
+            "stall_window": w.get("stall_window", 0), "max_iterations": int(iters.max()),
             "median_iterations": float(np.median(iters)), "mean_cut": float(np.mean(cuts)),
             "max_imbalance": float(np.max(imbs)),
             "roofline": None,
@@ -380,12 +391,8 @@ def run_ours(args, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world / (ms / 1000.0)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    value = job_throughput(1, ms, world)
 
     spmm_ms = sum(s[3]["ms_spmm"] for s in stats)
     spmm_bytes = sum(s[3]["spmm_bytes"] for s in stats)
@@ -450,11 +457,7 @@ def run_ours(args, world, rank, local):
         spx.sphynx_partition(h, w["K"], o_host, hp.data_ptr())
         spx.sphynx_destroy(h)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t) / e2e_steps, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -106,7 +106,13 @@ typedef struct {
   uint64_t seed;       /* seeds the random block and the polynomial start      */
   uint32_t flags;      /* SPHYNX_OUT_DEVICE                                    */
   int32_t sync_every;  /* iterations between host convergence checks (0=auto)  */
-  int32_t reserved[6];
+  int32_t stall_window;/* 0 (default): iterate until converged or max_iter.
+                          w > 0: also stop, with NOCONV and the best iterate,
+                          once every unconverged column has gone w iterations
+                          without its residual falling below 0.9 x its best so
+                          far (FP32 blocks cannot reach tol * theta when that is
+                          below the FP32 rounding of L x)                     */
+  int32_t reserved[5];
 } sphynx_options;
 
 typedef struct {

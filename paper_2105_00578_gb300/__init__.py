@@ -40,7 +40,7 @@ class Options(C.Structure):
     _fields_ = [("laplacian", C.c_int32), ("precond", C.c_int32), ("poly_degree", C.c_int32),
                 ("precision", C.c_int32), ("init", C.c_int32), ("max_iter", C.c_int32),
                 ("tol", C.c_double), ("seed", C.c_uint64), ("flags", C.c_uint32),
-                ("sync_every", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("sync_every", C.c_int32), ("stall_window", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Stats(C.Structure):
@@ -144,7 +144,7 @@ def _dptr(a: np.ndarray):
 
 
 def options(laplacian="combinatorial", precond="jacobi", poly_degree=25, precision="fp64", init="random",
-            max_iter=1000, tol=1e-3, seed=1, out_device=False, sync_every=0) -> Options:
+            max_iter=1000, tol=1e-3, seed=1, out_device=False, sync_every=0, stall_window=0) -> Options:
     o = Options()
     LIB.sphynx_default_options(C.byref(o))
     o.laplacian = LAPLACIANS.get(laplacian, laplacian)
@@ -157,6 +157,7 @@ def options(laplacian="combinatorial", precond="jacobi", poly_degree=25, precisi
     o.seed = seed
     o.flags = OUT_DEVICE if out_device else 0
     o.sync_every = sync_every
+    o.stall_window = stall_window
     return o
 
 

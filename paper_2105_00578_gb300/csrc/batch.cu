@@ -243,7 +243,8 @@ k_bresidual(ChunkView cv, const SolverState *states, const T *x, const T *lx, co
 // ---- convergence per graph (the single-graph test), and the loop condition ----
 // ctl[0]: graphs not done; ctl[1]: iterations of the batch loop
 __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int count, const double *partials, int b,
-                            int ld, double tol, double floor_abs, int count_iteration, int maxit, int *ctl) {
+                            int ld, double tol, double floor_abs, int count_iteration, int maxit, int stall_window,
+                            int *ctl) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
   SolverState *st = states + q;
@@ -265,12 +266,14 @@ __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int cou
     st->iters += 1;
     st->pvalid = 1;
   }
+  const bool stalled = stall_check(st, b, stall_window, count_iteration);
   if (nconv == b) {
     st->done = 1;
     st->status = SPHYNX_OK;
-  } else if (st->iters >= maxit) {
+  } else if (st->iters >= maxit || stalled) {
     st->done = 1;
     st->status = SPHYNX_ERR_NOCONV;
+    st->stalled = stalled ? 1 : 0;
   }
   if (st->done) atomicSub(&ctl[0], 1);
 }
@@ -598,7 +601,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   };
   auto converge = [&](int count_iteration) {
     k_bconverge<<<(count + 127) / 128, 128, 0, st>>>(gc0, states, count, npart, b, ld, o->tol, floor_abs,
-                                                      count_iteration, o->max_iter, ctl);
+                                                      count_iteration, o->max_iter, o->stall_window, ctl);
     SPX_LAUNCHED();
   };
   auto spmm_block = [&](const void *x, void *y) {

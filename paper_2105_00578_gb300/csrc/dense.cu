@@ -204,7 +204,7 @@ k_residual(int64_t n, const T *x, const T *lx, const double *theta, const T *bdi
 
 // Convergence test (lines 10-11): ||r||_{B^-1} <= tol |theta| or below the floor.
 __global__ void k_converge(SolverState *st, const double *partials, int grid, int b, int ld,
-                           double tol, double floor_abs, int count_iteration, int maxit) {
+                           double tol, double floor_abs, int count_iteration, int maxit, int stall_window) {
   __shared__ double part[16][17];
   if (st->done) return;
   const int t = threadIdx.x;     // 256 threads: column t % 16, stripe t / 16
@@ -232,12 +232,14 @@ __global__ void k_converge(SolverState *st, const double *partials, int grid, in
       st->iters += 1;
       st->pvalid = 1;
     }
+    const bool stalled = stall_check(st, b, stall_window, count_iteration);
     if (nconv == b) {
       st->done = 1;
       st->status = SPHYNX_OK;
-    } else if (st->iters >= maxit) {
+    } else if (st->iters >= maxit || stalled) {
       st->done = 1;
       st->status = SPHYNX_ERR_NOCONV;
+      st->stalled = stalled ? 1 : 0;
     }
   }
 }
@@ -706,8 +708,8 @@ void launch_residual(cudaStream_t st, const ResidualArgs &a, int grid) {
 }
 
 void launch_converge(cudaStream_t st, SolverState *state, const double *partials, int grid, int b,
-                     int ld, double tol, double floor_abs, int count_iteration, int maxit) {
-  k_converge<<<1, 256, 0, st>>>(state, partials, grid, b, ld, tol, floor_abs, count_iteration, maxit);
+                     int ld, double tol, double floor_abs, int count_iteration, int maxit, int stall_window) {
+  k_converge<<<1, 256, 0, st>>>(state, partials, grid, b, ld, tol, floor_abs, count_iteration, maxit, stall_window);
   SPX_LAUNCHED();
 }
 

@@ -315,10 +315,32 @@ struct SolverState {         // device-resident LOBPCG bookkeeping
   int status;
   int svqb_steps;
   int nconv;
-  int pad[2];
+  int stalled;                     // stopped by the stall window
+  int pad;
+  double best_res[SPHYNX_MAX_NEV]; // smallest residual so far per column (0: none yet)
+  int since_best[SPHYNX_MAX_NEV];  // iterations since it last fell below 0.9 x best
 };
+// Stall window: true once every unconverged column has gone `window`
+// iterations without its residual falling below 0.9 x its best so far.
+__device__ inline bool stall_check(SolverState *st, int b, int window, int count_iteration) {
+  if (window <= 0 || !count_iteration) return false;
+  bool all = true;
+  for (int j = 0; j < b; ++j) {
+    if (st->conv[j]) continue;
+    const double r = st->resnorm[j];
+    if (st->best_res[j] == 0.0 || r < 0.9 * st->best_res[j]) {
+      st->best_res[j] = r;
+      st->since_best[j] = 0;
+    } else {
+      st->since_best[j] += 1;
+    }
+    all = all && st->since_best[j] >= window;
+  }
+  return all;
+}
+
 void launch_converge(cudaStream_t st, SolverState *state, const double *partials, int grid, int b,
-                     int ld, double tol, double floor_abs, int count_iteration, int maxit);
+                     int ld, double tol, double floor_abs, int count_iteration, int maxit, int stall_window = 0);
 
 void launch_signs_coords(cudaStream_t st, DT dt, const void *x, int64_t n, int ld, int b,
                          void *coords, double *scratch);

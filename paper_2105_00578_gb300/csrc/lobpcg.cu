@@ -43,6 +43,7 @@ void check_options(const sphynx_graph *g, const sphynx_options *o) {
   if (o->precond == SPHYNX_PRECOND_POLY && (o->poly_degree < 1 || o->poly_degree > SPHYNX_MAX_POLY_DEGREE))
     fail(SPHYNX_ERR_INVALID_ARG, "poly_degree %d", o->poly_degree);
   if (o->max_iter < 0) fail(SPHYNX_ERR_INVALID_ARG, "max_iter < 0");
+  if (o->stall_window < 0) fail(SPHYNX_ERR_INVALID_ARG, "stall_window < 0");
   if (!(o->tol >= 0.0)) fail(SPHYNX_ERR_INVALID_ARG, "tol");
   if (o->laplacian != SPHYNX_COMBINATORIAL && g->isolated > 0)
     fail(SPHYNX_ERR_ISOLATED, "%lld vertices without edges: the %s problem needs deg > 0",
@@ -318,7 +319,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
     r3.x = X[nx];
     r3.lx = LX[nx];
     launch_residual(st, r3, rgrid);
-    launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_abs, 1, o->max_iter);  // lines 10-11
+    launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_abs, 1, o->max_iter, o->stall_window);  // lines 10-11
     g->ctr.launches += 6;
     cur = nx;
     if ((it + 1) % sync_every == 0 || it + 1 == o->max_iter) {

@@ -170,3 +170,17 @@ def test_default_options_follow_the_oracle_decision_flow():
                 assert o.precond == spx.PRECONDS[pc]
         finally:
             spx.sphynx_destroy(h)
+
+
+def test_stall_window_stops_an_unreachable_fp32_target():
+    """tol 1e-6 relative is below what FP32 blocks can resolve on this grid:
+    without a stall window the solve runs to max_iter; with one it stops as
+    soon as every unconverged column stopped improving, still NOCONV, with a
+    valid partition of its best iterate."""
+    g = W.grid2d(120, 100)
+    kw = dict(laplacian="combinatorial", precond="jacobi", precision="fp32", tol=1e-6, seed=1, max_iter=600)
+    _, _, _, st0, code0 = _gpu_partition(g, 4, **kw)
+    assert code0 != 0 and st0["iterations"] == 600
+    parts, cut, imb, st1, code1 = _gpu_partition(g, 4, stall_window=20, **kw)
+    assert code1 != 0 and st1["iterations"] < 600
+    assert O.cutsize(g, parts)[0] == cut and imb == O.imbalance(parts, None, 4)
