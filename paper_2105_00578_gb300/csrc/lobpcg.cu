@@ -486,6 +486,15 @@ int sphynx_laplacian_apply(sphynx_handle g, int32_t laplacian, int32_t dtype, co
         fail(SPHYNX_ERR_INVALID_ARG, "blocks must be 16-byte aligned row by row");
     }
     if (laplacian != SPHYNX_COMBINATORIAL && g->isolated > 0) fail(SPHYNX_ERR_ISOLATED, "vertex without edges");
+    // the SpMM reads X rows exactly bp apart: pack a wider X into scratch first
+    if (ldx != bp) {
+      const size_t es = dt_size(static_cast<DT>(dtype));
+      void *packed = g->workspace("la_x", static_cast<size_t>(g->n) * bp * es, false);
+      SPX_CUDA(cudaMemcpy2DAsync(packed, bp * es, x, static_cast<size_t>(ldx) * es, bp * es, g->n,
+                                 cudaMemcpyDeviceToDevice, g->stream));
+      x = packed;
+      ldx = bp;
+    }
     SpmmArgs a{};
     a.lap = op_of(laplacian);
     a.tin = static_cast<DT>(dtype);

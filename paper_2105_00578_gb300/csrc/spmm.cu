@@ -69,7 +69,11 @@ SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a) {
 void spmm(sphynx_graph *g, const SpmmArgs &a) {
   if (!(a.bp == 1 || a.bp == 4 || a.bp == 8 || a.bp == 12 || a.bp == 16))
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: block width %d", a.bp);
-  if (a.ld_x < a.bp || (a.mode == 0 && a.ld_y < a.bp) || (a.mode == 1 && a.ld_y < a.bp))
+  // the kernels index X (and the chain's output) with the compile-time width:
+  // a runtime stride costs a 64-bit multiply per gather (about a third of the
+  // chain step's time)
+  if (a.ld_x != a.bp) fail(SPHYNX_ERR_INVALID_ARG, "spmm: input rows must be exactly the block width apart");
+  if ((a.mode == 0 && a.ld_y < a.bp) || (a.mode == 1 && a.ld_y < a.bp))
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: leading dimension smaller than block width");
   if (a.mode == 1 && a.tin == DT::F64 && a.tout != DT::F64)
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: double chain must stay double");

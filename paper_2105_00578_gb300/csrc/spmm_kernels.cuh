@@ -168,7 +168,7 @@ __device__ __forceinline__ void spmm_epilogue(const LapView &L, const SpmmDev &a
   using TA = typename AccOf<TI>::T;
   const TI *x = static_cast<const TI *>(a.x);
   TA xi[BP];
-  load_row<BP>(x + row * a.ldx, xi);
+  load_row<BP>(x + row * BP, xi);
   TA out[BP];
   if constexpr (LAP == SPHYNX_NORMALIZED) {
     const TA s = dinv_of<TA>(L, row);
@@ -193,7 +193,7 @@ __device__ __forceinline__ void spmm_epilogue(const LapView &L, const SpmmDev &a
     TA tn[BP];
 #pragma unroll
     for (int c = 0; c < BP; ++c) tn[c] = xi[c] - out[c] * ic;
-    store_row<BP>(static_cast<TT *>(a.tout) + row * a.ldx, tn);  // tn now holds the stored values
+    store_row<BP>(static_cast<TT *>(a.tout) + row * BP, tn);  // tn now holds the stored values
     if (a.yterms != 0) {
       TA *yp = static_cast<TA *>(a.yacc) + row * a.ldy;
       TA ya[BP];
@@ -489,10 +489,10 @@ template <int BP> struct RowAcc<double, BP> {
 };
 
 template <int LAP, typename TI, int BP, bool W>
-__device__ __forceinline__ void spmm_accumulate(const LapView &L, const TI *__restrict__ x, int ldx,
+__device__ __forceinline__ void spmm_accumulate(const LapView &L, const TI *__restrict__ x,
                                                 int j, float wv, RowAcc<TI, BP> &acc) {
   using TA = typename AccOf<TI>::T;
-  const TI *p = x + static_cast<int64_t>(j) * ldx;
+  const TI *p = x + static_cast<int64_t>(j) * BP;   // rows exactly BP wide
   if constexpr (LAP == SPHYNX_NORMALIZED || W) {
     TA coef = W ? static_cast<TA>(wv) : TA(1);
     if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, j);
@@ -505,7 +505,7 @@ __device__ __forceinline__ void spmm_accumulate(const LapView &L, const TI *__re
 // One row's d entries in batches: U column indices, then U gathers in flight
 // together, then U accumulations.  col_at(t) / w_at(t) read entry t < d.
 template <int LAP, typename TI, int BP, bool W, class ColAt, class WAt>
-__device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict__ x, int ldx, int d,
+__device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict__ x, int d,
                                          ColAt col_at, WAt w_at, RowAcc<TI, BP> &acc) {
   using TA = typename AccOf<TI>::T;
   constexpr int U = GatherBatch<TI, BP>::U;
@@ -519,7 +519,7 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
       for (int u = 0; u < U; ++u) jj[u] = col_at(t0 + u);
       RawRow<TI, BP> rr[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) rr[u].load(x + static_cast<int64_t>(jj[u]) * ldx);
+      for (int u = 0; u < U; ++u) rr[u].load(x + static_cast<int64_t>(jj[u]) * BP);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if constexpr (LAP == SPHYNX_NORMALIZED || W) {
@@ -538,7 +538,7 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
       RawRow<TI, BP> rr[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (jj[u] >= 0) rr[u].load(x + static_cast<int64_t>(jj[u]) * ldx);
+        if (jj[u] >= 0) rr[u].load(x + static_cast<int64_t>(jj[u]) * BP);
         else rr[u].zero();
       }
 #pragma unroll
@@ -583,7 +583,7 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
     RawRow<TI, BP> rr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (jj[u] >= 0) rr[u].load(x + static_cast<int64_t>(jj[u]) * ldx);
+      if (jj[u] >= 0) rr[u].load(x + static_cast<int64_t>(jj[u]) * BP);
       else rr[u].zero();
     }
 #pragma unroll
@@ -650,12 +650,12 @@ k_spmm_short(const LapView L, const SpmmDev a) {
     const int *sc = &s_col[wid][rb - base];
     const float *sw = W ? &s_w[wid][rb - base] : nullptr;
     spmm_row<LAP, TI, BP, W>(
-        L, x, a.ldx, len, [&](int t) { return sc[t]; }, [&](int t) { return sw[t]; }, acc);
+        L, x, len, [&](int t) { return sc[t]; }, [&](int t) { return sw[t]; }, acc);
   } else {
     const int32_t *gc = L.col + rb;
     const float *gw = W ? L.w + rb : nullptr;
     spmm_row<LAP, TI, BP, W>(
-        L, x, a.ldx, len, [&](int t) { return __ldg(gc + t); }, [&](int t) { return __ldg(gw + t); }, acc);
+        L, x, len, [&](int t) { return __ldg(gc + t); }, [&](int t) { return __ldg(gw + t); }, acc);
   }
   TA sum[BP];
   acc.get(sum);
@@ -677,7 +677,8 @@ template <typename TI, int BP> struct SellOccupancy {
           : (std::is_same<TI, float>::value && BP == 8 ? 8 : 1);
 };
 
-template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
+// NARROW: every slice of the graph stores 16-bit offsets (no 32-bit branch).
+template <int LAP, typename TI, typename TT, int BP, bool W, int MODE, bool NARROW>
 __global__ void __launch_bounds__(128, SellOccupancy<TI, BP>::blocks)
 k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, const float *__restrict__ sw,
             const int64_t *__restrict__ sptr, const int64_t *__restrict__ cptr, const uint8_t *__restrict__ sdeg) {
@@ -695,16 +696,16 @@ k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, 
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> acc;
   acc.zero();
-  if (cbase < 0) {
+  if (NARROW || cbase < 0) {
     const int16_t *cp = scol + (~cbase) + lane;
     const int r = static_cast<int>(row);
     spmm_row<LAP, TI, BP, W>(
-        L, x, a.ldx, d, [&](int t) { return r + static_cast<int>(__ldcs(cp + 32 * t)); },
+        L, x, d, [&](int t) { return r + static_cast<int>(__ldcs(cp + 32 * t)); },
         [&](int t) { return __ldcs(wp + 32 * t); }, acc);
   } else {
     const int32_t *cp = reinterpret_cast<const int32_t *>(scol + cbase) + lane;
     spmm_row<LAP, TI, BP, W>(
-        L, x, a.ldx, d, [&](int t) { return __ldcs(cp + 32 * t); }, [&](int t) { return __ldcs(wp + 32 * t); },
+        L, x, d, [&](int t) { return __ldcs(cp + 32 * t); }, [&](int t) { return __ldcs(wp + 32 * t); },
         acc);
   }
   if (sd == 0xFF) return;   // padding lane or a long row
@@ -744,7 +745,7 @@ k_spmm_med(const LapView L, const SpmmDev a, const int32_t *__restrict__ mcol, c
     const int32_t *cpb = cp + 32 * t0;
     const float *wpb = W ? wp + 32 * t0 : nullptr;
     spmm_row<LAP, TI, BP, W>(
-        L, x, a.ldx, dd, [&](int t) { return __ldcs(cpb + 32 * t); }, [&](int t) { return __ldcs(wpb + 32 * t); },
+        L, x, dd, [&](int t) { return __ldcs(cpb + 32 * t); }, [&](int t) { return __ldcs(wpb + 32 * t); },
         blk);
     acc.merge(blk);
   }
@@ -769,7 +770,7 @@ k_spmm_long(const LapView L, const SpmmDev a, const int64_t *__restrict__ items,
   RowAcc<TI, BP> racc;
   racc.zero();
   for (int64_t k = b + lane; k < e; k += 32)
-    spmm_accumulate<LAP, TI, BP, W>(L, x, a.ldx, __ldcs(L.col + k), W ? __ldcs(L.w + k) : 0.f, racc);
+    spmm_accumulate<LAP, TI, BP, W>(L, x, __ldcs(L.col + k), W ? __ldcs(L.w + k) : 0.f, racc);
   TA acc[BP];
   racc.get(acc);
 #pragma unroll
@@ -812,9 +813,14 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
   const int64_t grid = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
   if (grid > 0) {
     if (g->plan.variant == kSell32) {
-      k_spmm_sell<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 128, 0, st>>>(
-          L, a, g->plan.sell_col.as<int16_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
-          g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>());
+      if (g->plan.sell_narrow == (g->n + 31) / 32)
+        k_spmm_sell<LAP, TI, TT, BP, W, MODE, true><<<static_cast<unsigned>(grid), 128, 0, st>>>(
+            L, a, g->plan.sell_col.as<int16_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
+            g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>());
+      else
+        k_spmm_sell<LAP, TI, TT, BP, W, MODE, false><<<static_cast<unsigned>(grid), 128, 0, st>>>(
+            L, a, g->plan.sell_col.as<int16_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
+            g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>());
     } else {
       k_spmm_short<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 32 * kWarpsPerCta, 0, st>>>(L, a);
     }

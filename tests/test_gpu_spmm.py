@@ -164,6 +164,28 @@ def test_null_vector_is_annihilated_to_rounding(lap, dtype):
         spx.sphynx_destroy(h)
 
 
+def test_input_rows_wider_than_the_block_are_packed():
+    """sphynx_laplacian_apply accepts X rows further apart than the block
+    width (the kernels read them exactly bp apart, so the call packs X first):
+    same result as the packed layout."""
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    g = GRAPHS["rmat"]
+    h = spx.sphynx_create(g.row_ptr, g.col, g.w, None)
+    try:
+        x = np.random.default_rng(4).standard_normal((g.n, 7))
+        packed = dev_block(x, 8, "f32")
+        wide = dev_block(x, 12, "f32")
+        y1 = torch.zeros((g.n, 8), dtype=torch.float32, device="cuda")
+        y2 = torch.zeros((g.n, 8), dtype=torch.float32, device="cuda")
+        spx.sphynx_laplacian_apply(h, "normalized", spx.DT_F32, packed, 8, y1, 8, 7)
+        spx.sphynx_laplacian_apply(h, "normalized", spx.DT_F32, wide, 12, y2, 8, 7)
+        torch.cuda.synchronize()
+        assert torch.equal(y1, y2)
+    finally:
+        spx.sphynx_destroy(h)
+
+
 def test_full_size_27_point_mesh_sampled_rows():
     """128^3 27-point mesh (the 2.1M-vertex workload): sampled rows of L_C X
     recomputed by the oracle row by row."""
