@@ -239,7 +239,7 @@ int sphynx_precond_setup(sphynx_handle g, const sphynx_options *opt, double *roo
 int sphynx_precond_apply(sphynx_handle g, const sphynx_options *opt, const void *r, void *h,
                          int32_t ld, int32_t ncols);
 
-/* Gram matrices of Rayleigh-Ritz (Sec. 3.3, Algorithm 1 line 7):
+/* Gram matrices of Rayleigh-Ritz (Sec. 3.3, the Rayleigh-Ritz step of Algorithm 1):
  * G_A = S^T (L S) and G_B = S^T B S, where S = [S_0 | S_1 | S_2] and
  * LS = [LS_0 | LS_1 | LS_2] are given as nblk (1..3) device n x ld blocks of
  * dtype F32 or F64 (each ld columns wide, 4 | ld, ld <= 16), and B is

@@ -55,7 +55,7 @@ def laplacian_normalized(g) -> sp.csr_matrix:
 
 def operator_for(g, problem: str) -> sp.csr_matrix:
     """The matrix LOBPCG is applied to: L_C for the combinatorial and the
-    generalized problems, L_N for the normalized one (Sec. 4, Alg. 2 line 1)."""
+    generalized problems, L_N for the normalized one (Sec. 4, the first step of Algorithm 2)."""
     if problem in (COMBINATORIAL, GENERALIZED):
         return laplacian_combinatorial(g)
     if problem == NORMALIZED:

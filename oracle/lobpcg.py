@@ -5,17 +5,17 @@ L x = lambda B x with B diagonal (B = I, or B = D for the generalized
 Laplacian problem), with B-inner products throughout.  The steps, in the
 paper's order:
 
-* line 1-2: initial guess X~, Rayleigh-Ritz on span(X~), X0 = X~ Y;
-* line 3:   R = L X0 - B X0 Theta0 (a fresh product with L);
-* line 6:   H_I = M R_I for the unconverged columns I;
-* line 7:   S = [X, H_I, P_I], (Y, Theta) = RR(S, nev);
-* line 8:   X <- S Y;
-* line 9:   R <- L X - B X Theta (a fresh product with L);
-* line 10-11: I <- unconverged columns, Y_I the matching columns of Y;
-* line 12:  P_I <- [0, H_I, P_I] Y_I (and L P by the same combination).
+* start:         initial guess X~, Rayleigh-Ritz on span(X~), X0 = X~ Y;
+* first residual: R = L X0 - B X0 Theta0 (a fresh product with L);
+* precondition:  H_I = M R_I for the unconverged columns I;
+* Rayleigh-Ritz: S = [X, H_I, P_I], (Y, Theta) = RR(S, nev);
+* update:        X <- S Y;
+* residual:      R <- L X - B X Theta (a fresh product with L);
+* lock:          I <- unconverged columns, Y_I the matching columns of Y;
+* direction:     P_I <- [0, H_I, P_I] Y_I (and L P by the same combination).
 
 Converged columns stay in X and in every Rayleigh-Ritz step but get no new
-H or P columns (soft locking, lines 10-12).
+H or P columns (soft locking: the lock and direction steps).
 
 Rayleigh-Ritz RR(S, nev) (Sec. 3.3): with G_A = S^T L S and G_B = S^T B S
 (both symmetrised), scale to unit diagonal, B-orthonormalise the basis in the
@@ -130,7 +130,7 @@ def lobpcg(apply_l, bdiag, apply_m, x0: np.ndarray, tol: float, maxit: int,
         res = residual_norms(r, bdiag)
         return res, (res <= tol * np.abs(th)) | ((np.abs(th) <= floor) & (res <= floor))
 
-    # lines 1-3
+    # start and first residual
     lx0 = apply_l(x0)
     th, y, svqb = rayleigh_ritz(x0.T @ lx0, x0.T @ bmul(x0), nev, u_work)
     svqb_steps = int(svqb)
@@ -144,19 +144,19 @@ def lobpcg(apply_l, bdiag, apply_m, x0: np.ndarray, tol: float, maxit: int,
     while not conv.all() and it < maxit:
         idx = np.nonzero(~conv)[0]
         ri = r[:, idx]
-        h = ri.copy() if apply_m is None else apply_m(ri)          # line 6
+        h = ri.copy() if apply_m is None else apply_m(ri)          # precondition
         lh = apply_l(h)
-        s = np.concatenate([x, h, p], axis=1)                      # line 7
+        s = np.concatenate([x, h, p], axis=1)                      # Rayleigh-Ritz
         ls = np.concatenate([lx, lh, lp], axis=1)
         th, y, svqb = rayleigh_ritz(s.T @ ls, s.T @ bmul(s), nev, u_work)
         svqb_steps += int(svqb)
-        xn = s @ y                                                 # line 8
-        lxn = apply_l(xn)                                          # line 9
+        xn = s @ y                                                 # update
+        lxn = apply_l(xn)                                          # residual
         r = lxn - bmul(xn) * th[None, :]
         res, conv = test(r, th)
-        idx2 = np.nonzero(~conv)[0]                                # lines 10-11
+        idx2 = np.nonzero(~conv)[0]                                # lock
         yp = y[:, idx2].copy()
-        yp[:nev, :] = 0.0                                          # line 12
+        yp[:nev, :] = 0.0                                          # direction
         p = s @ yp
         lp = ls @ yp
         x, lx = xn, lxn

@@ -618,7 +618,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     spmm(g, a);
   };
 
-  // line 1: every graph's random block on its local rows; lines 2-3
+  // every graph's random block on its local rows; then the first Rayleigh-Ritz and residual
   if (dt == DT::F64)
     k_brandom<double><<<cgrid, 256, 0, st>>>(static_cast<double *>(X[0]), view_of(g), B.gptr.as<int64_t>(), b, ld,
                                              mix64(o->seed + kGamma));
@@ -718,7 +718,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     canonical_rotation_block(g, static_cast<char *>(X[0]) + static_cast<size_t>(r0) * ld * es, rows, ld, dt,
                              hs[q].theta, d, o->tol, o->seed);
   }
-  // embedding (Algorithm 2 lines 6-10), signs per graph
+  // embedding (Algorithm 2), signs per graph
   double *pval = static_cast<double *>(g->workspace("bsg_val", static_cast<size_t>(nch) * b * 2 * 8, false));
   int64_t *pidx = static_cast<int64_t *>(g->workspace("bsg_idx", static_cast<size_t>(nch) * b * 8, false));
   double *sign = static_cast<double *>(g->workspace("bsg", static_cast<size_t>(count) * b * 8, false));

@@ -1,6 +1,6 @@
 // capi.cu -- step-level entry points that work on caller buffers without a
 // graph handle: the Rayleigh-Ritz Gram products and the FP64 Rayleigh-Ritz
-// solve (Sec. 3.3, Algorithm 1 line 7).
+// solve (Sec. 3.3, the Rayleigh-Ritz step of Algorithm 1).
 #include "internal.cuh"
 
 #include <cstring>
@@ -41,8 +41,8 @@ int sphynx_gram(int32_t dtype, const void *const *s_blocks, const void *const *l
         a.s[k] = k < nblk ? s_blocks[k] : nullptr;
         a.ls[k] = k < nblk ? ls_blocks[k] : nullptr;
       }
-      launch_gram(st, a, grid);
-      launch_gram_reduce(st, part, nblk, ld, grid, ga, gb, nullptr);
+      const int pg = launch_gram(st, a, grid);
+      launch_gram_reduce(st, part, nblk, ld, pg, ga, gb, nullptr);
       SPX_CUDA(cudaMemcpyAsync(ga_out, ga, static_cast<size_t>(M) * M * 8, cudaMemcpyDeviceToHost, st));
       SPX_CUDA(cudaMemcpyAsync(gb_out, gb, static_cast<size_t>(M) * M * 8, cudaMemcpyDeviceToHost, st));
       SPX_CUDA(cudaStreamSynchronize(st));

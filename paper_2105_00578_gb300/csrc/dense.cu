@@ -106,7 +106,7 @@ __global__ void k_to_f64(const T *x, double *dst, int64_t n, int b, int ld) {
 }
 
 // ---------------------------------------------------------------------------
-// X' = S Y, P' = [0 H P] Y, LP' = [0 LH LP] Y  (Algorithm 1 lines 8 and 12)
+// X' = S Y, P' = [0 H P] Y, LP' = [0 LH LP] Y  (Algorithm 1: the update and the new search directions)
 template <typename T, int LD, int NBLK>
 __global__ void __launch_bounds__(256)
 k_update(int64_t n, const T *s0, const T *s1, const T *s2, const T *l1, const T *l2, const T *y,
@@ -155,7 +155,7 @@ k_update(int64_t n, const T *s0, const T *s1, const T *s2, const T *l1, const T 
 }
 
 // ---------------------------------------------------------------------------
-// R = L X - B X Theta (Algorithm 1 line 9), ||r_c||^2_{B^-1} partials, and
+// R = L X - B X Theta (Algorithm 1: the residual), ||r_c||^2_{B^-1} partials, and
 // the Jacobi scaling H = diag(L)^{-1} R (Sec. 5.1) when jinv is given.
 template <typename T, int LD>
 __global__ void __launch_bounds__(256)
@@ -202,7 +202,7 @@ k_residual(int64_t n, const T *x, const T *lx, const double *theta, const T *bdi
   }
 }
 
-// Convergence test (lines 10-11): ||r||_{B^-1} <= tol |theta| or below the floor.
+// Convergence test (Algorithm 1, soft locking): ||r||_{B^-1} <= tol |theta| or below the floor.
 __global__ void k_converge(SolverState *st, const double *partials, int grid, int b, int ld,
                            double tol, double floor_abs, int count_iteration, int maxit, int stall_window) {
   __shared__ double part[16][17];
@@ -246,8 +246,8 @@ __global__ void k_converge(SolverState *st, const double *partials, int grid, in
 
 // ---------------------------------------------------------------------------
 // embedding signs: entry of largest magnitude of each column made positive
-// (lowest row on ties), then coords[i][j] = sign_{j+1} X[i][j+1] (Algorithm 2
-// lines 6-10).
+// (lowest row on ties), then coords[i][j] = sign_{j+1} X[i][j+1] (the
+// embedding of Algorithm 2).
 template <typename T>
 __global__ void k_argmax_partial(const T *x, int64_t n, int ld, int b, double *pval, int64_t *pidx) {
   __shared__ double sv[256];

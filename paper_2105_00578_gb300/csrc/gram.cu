@@ -1,12 +1,13 @@
-// gram.cu -- Gram matrices of the Rayleigh-Ritz step (Sec. 3.3, Algorithm 1
-// line 7): G_A = S^T (L S) and G_B = S^T B S for the tall-skinny block
+// gram.cu -- Gram matrices of the Rayleigh-Ritz step (Sec. 3.3, Algorithm
+// 1): G_A = S^T (L S) and G_B = S^T B S for the tall-skinny block
 // S = [S_0 | S_1 | S_2] (n x M, M = nblk * ld <= 48) and its L-image.
 //
 // Both matrices are symmetric (L and B are), so only their upper triangles
-// are formed, in 4 x 4 output tiles: NB = mb (mb + 1) tiles with mb = M / 4.
-// A CTA streams slabs of TR rows of S, LS and diag(B) into shared memory with
-// cp.async 16-byte copies, double-buffered so that the next slab is in flight
-// while the current one is multiplied.  Its 256 threads form
+// are formed.  Float blocks use k_gram8 below (8 x 8 tiles per thread); the
+// double path uses k_gram, in 4 x 4 output tiles: NB = mb (mb + 1) tiles with
+// mb = M / 4.  A CTA streams slabs of TR rows of S, LS and diag(B) into shared
+// memory with cp.async 16-byte copies, multi-buffered so that the next slabs
+// are in flight while the current one is multiplied.  Its 256 threads form
 // floor(256 / NB) groups of NB threads, thread t of a group owning tile t and
 // the group owning rows grp, grp + ngroups, ...  Per row a thread does two
 // 16-byte shared loads and 16 FMAs (B applied on the fly for G_B tiles).
@@ -22,6 +23,7 @@ namespace sphynx {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kFoldRows = 4096;   // rows a thread of the 8 x 8 kernel adds into one float running sum
 
 template <typename T> struct Tile {
   static constexpr int rows = 64;
@@ -283,21 +285,229 @@ k_gram(int64_t n, const T *s0, const T *s1, const T *s2, const T *l0, const T *l
   }
 }
 
-// partials [grid][nb * 16] -> symmetric G_A and G_B (M x M); 8 threads per entry
-__global__ void k_gram_reduce(const double *partials, int M, int grid, double *ga, double *gb, const int *done) {
-  __shared__ double red[32][9];
+// ---- float blocks: 8 x 8 register tiles ------------------------------------
+//
+// The 4 x 4 tiles above cost two 16-byte shared loads (eight quarter-warp
+// wavefronts per warp) for 16 FMAs, which leaves the kernel bound by shared
+// memory at about half the FMA rate.  Here a thread owns an 8 x 8 tile: four
+// 16-byte loads for 64 FMAs.  The columns are cut into 4-wide chunks (MC =
+// M / 4); tile row bi covers chunks 2 bi and 2 bi + 1, the second one absent
+// (zero) when MC is odd.  A row group is nb = 2 nbu threads (nbu upper tiles
+// per matrix), groups are contiguous in the thread index, and G groups take
+// the rows of a slab in turn.  Block k of a slab starts at a 16-byte slot
+// chosen so that the chunks one quarter warp reads (two adjacent rows when a
+// group straddles it) fall in different banks; for b = 7 (ld 8, three
+// blocks) the placement (slots 0, 1, 4, 3, 4, 5 modulo 8) was found by
+// exhaustive search over the thread-to-tile map below.
+//
+// Summation: a thread adds the products of up to 64 of its rows in float,
+// then adds that sum into a float running sum.  The launch gives every thread
+// at most kFoldRows = 4096 rows (64 such folds), so each entry of a thread's
+// running sum is within (64 + 64) u of the exact sum of its |terms| (u = 2^-24);
+// threads are then added in double.  (A TwoSum-compensated running sum would
+// cost 64 more registers or shared floats per thread; that halved the resident
+// warps and made the kernel slower than the 4 x 4 one.)  The result is written
+// in the 4 x 4 kernel's partial layout, so one reduction serves both.
+template <int LD, int NBLK>
+struct G8 {
+  static constexpr int M = LD * NBLK;
+  static constexpr int MC = M / 4;
+  static constexpr int mb = (MC + 1) / 2;
+  static constexpr int nbu = mb * (mb + 1) / 2;
+  static constexpr int nb = 2 * nbu;
+  static constexpr int G = nb >= 96 ? 1 : 96 / nb;
+  static constexpr int threads = nb * G;
+  static constexpr int TR = 64;
+  static constexpr int stages = 2;                     // two slabs: more resident CTAs beat a deeper ring
+  static constexpr int blkw = TR * LD + 32;            // floats per block, with room for the slot shift
+  static constexpr int elems = 2 * NBLK * blkw + TR;   // S blocks, LS blocks, diag(B)
+  static constexpr int nbu4 = MC * (MC + 1) / 2;       // upper 4 x 4 tiles of one matrix
+  // shared bytes: the slab ring, reused at the end for the nb x 64 tile sums
+  static constexpr size_t smem_bytes = static_cast<size_t>(stages) * elems * 4 > static_cast<size_t>(nb) * 64 * 8
+                                           ? static_cast<size_t>(stages) * elems * 4
+                                           : static_cast<size_t>(nb) * 64 * 8;
+  __host__ __device__ static constexpr int slot(int k) {
+    return (LD == 8 && NBLK == 3) ? (k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 4 : k == 3 ? 3 : k == 4 ? 4 : 5) : k;
+  }
+  __host__ __device__ static constexpr int block_off(int k) { return k * blkw + 4 * slot(k); }
+  // offset of 4-column chunk q (q < MC) of S (ls = false) or LS in a slab row 0
+  __host__ __device__ static constexpr int chunk_off(int q, bool ls) {
+    return block_off((ls ? NBLK : 0) + (4 * q) / LD) + (4 * q) % LD;
+  }
+};
+
+template <int LD, int NBLK>
+__device__ __forceinline__ void stage8(float *buf, int64_t r0, int64_t n, const float *const (&srcS)[3],
+                                       const float *const (&srcL)[3], const float *bdiag) {
+  using C = G8<LD, NBLK>;
+  constexpr int chunks = C::TR * LD / 4;   // 16-byte copies per block
+#pragma unroll
+  for (int blk = 0; blk < NBLK; ++blk) {
+    for (int i = threadIdx.x; i < 2 * chunks; i += C::threads) {
+      const int arr = i / chunks, c = i - arr * chunks;
+      const int r = c * 4 / LD;
+      const bool ok = r0 + r < n;
+      const float *src = (arr == 0 ? srcS[blk] : srcL[blk]) + (ok ? r0 * LD + c * 4 : 0);
+      cp16(buf + C::block_off(arr * NBLK + blk) + c * 4, src, ok ? 16 : 0);
+    }
+  }
+  if (bdiag) {
+    for (int c = threadIdx.x; c < C::TR / 4; c += C::threads) {
+      const int r = c * 4;
+      const int64_t left = n - r0 - r;
+      const int bytes = left >= 4 ? 16 : (left > 0 ? static_cast<int>(left) * 4 : 0);
+      cp16(buf + 2 * NBLK * C::blkw + r, bdiag + (bytes ? r0 + r : 0), bytes);
+    }
+  }
+}
+
+__device__ __forceinline__ Q4<float> ld4z(const float *p, bool ok) {
+  return ok ? ld4(p) : Q4<float>{0.f, 0.f, 0.f, 0.f};
+}
+
+// u-th upper 4 x 4 tile (row-major upper triangle of an mc x mc tile grid)
+__device__ __forceinline__ int upper_index(int bi, int bj, int mc) { return bi * mc - bi * (bi - 1) / 2 + (bj - bi); }
+
+template <int LD, int NBLK>
+__global__ void __launch_bounds__(G8<LD, NBLK>::threads, 3)
+k_gram8(int64_t n, const float *s0, const float *s1, const float *s2, const float *l0, const float *l1,
+        const float *l2, const float *bdiag, double *partials, const int *done) {
+  using C = G8<LD, NBLK>;
+  constexpr int TR = C::TR, NS = C::stages;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (done && *done) return;
+  float *const base = reinterpret_cast<float *>(smem_raw);
+  const int tid = threadIdx.x;
+  const int grp = tid / C::nb, t = tid - (tid / C::nb) * C::nb;
+  const bool isA = t < C::nbu;
+  int bi, bj;
+  upper_tile(isA ? t : t - C::nbu, C::mb, bi, bj);
+  const bool a1 = 2 * bi + 1 < C::MC, c1 = 2 * bj + 1 < C::MC;
+  const int oa0 = C::chunk_off(2 * bi, false), oa1 = a1 ? C::chunk_off(2 * bi + 1, false) : oa0;
+  const int oc0 = C::chunk_off(2 * bj, isA), oc1 = c1 ? C::chunk_off(2 * bj + 1, isA) : oc0;
+  const float *const srcS[3] = {s0, s1, s2};
+  const float *const srcL[3] = {l0, l1, l2};
+  const bool useB = !isA && bdiag != nullptr;
+  unsigned long long acc[8][4];   // (a_i c_2p, a_i c_2p+1), up to 64 rows
+  float hi[64];                   // running sums of the folded blocks
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc[i][p] = 0ull;
+#pragma unroll
+  for (int q = 0; q < 64; ++q) hi[q] = 0.f;
+  const int64_t ntile = (n + TR - 1) / TR;
+  int since_flush = 0;
+  int64_t tile = blockIdx.x;
+#pragma unroll
+  for (int s = 0; s < NS - 1; ++s) {
+    const int64_t tl = tile + static_cast<int64_t>(s) * gridDim.x;
+    if (tl < ntile) stage8<LD, NBLK>(base + s * C::elems, tl * TR, n, srcS, srcL, bdiag);
+    cp_commit();
+  }
+  for (int it = 0; tile < ntile; tile += gridDim.x, ++it) {
+    const int64_t ahead = tile + static_cast<int64_t>(NS - 1) * gridDim.x;
+    if (ahead < ntile) stage8<LD, NBLK>(base + ((it + NS - 1) % NS) * C::elems, ahead * TR, n, srcS, srcL, bdiag);
+    cp_commit();
+    cp_wait<NS - 1>();
+    __syncthreads();
+    const float *buf = base + (it % NS) * C::elems;
+    const float *bd = buf + 2 * NBLK * C::blkw;
+#pragma unroll 1
+    for (int r = grp; r < TR; r += C::G) {
+      const Q4<float> x0 = ld4(buf + oa0 + r * LD), x1 = ld4z(buf + oa1 + r * LD, a1);
+      const Q4<float> y0 = ld4(buf + oc0 + r * LD), y1 = ld4z(buf + oc1 + r * LD, c1);
+      float av[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      if (useB) {
+        const float b = bd[r];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) av[i] *= b;
+      }
+      const unsigned long long cp[4] = {pk2(y0.x, y0.y), pk2(y0.z, y0.w), pk2(y1.x, y1.y), pk2(y1.z, y1.w)};
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const unsigned long long ai = pk2(av[i], av[i]);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[i][p] = fma2(ai, cp[p], acc[i][p]);
+      }
+    }
+    since_flush += (TR - grp + C::G - 1) / C::G;
+    if (since_flush >= 64) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const float2 f = upk2(acc[i][p]);
+          hi[8 * i + 2 * p] += f.x;
+          hi[8 * i + 2 * p + 1] += f.y;
+          acc[i][p] = 0ull;
+        }
+      since_flush = 0;
+    }
+    __syncthreads();
+  }
+  cp_wait<0>();
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float2 f = upk2(acc[i][p]);
+      hi[8 * i + 2 * p] += f.x;
+      hi[8 * i + 2 * p + 1] += f.y;
+    }
+  // groups add their tile sums into red [nb][64] one after another
+  double *red = reinterpret_cast<double *>(smem_raw);
+  for (int g = 0; g < C::G; ++g) {
+    if (grp == g) {
+#pragma unroll
+      for (int q = 0; q < 64; ++q) {
+        const double v = static_cast<double>(hi[q]);
+        red[t * 64 + q] = g ? red[t * 64 + q] + v : v;
+      }
+    }
+    __syncthreads();
+  }
+  double *out = partials + static_cast<int64_t>(blockIdx.x) * 2 * C::nbu4 * 16;
+  for (int o = tid; o < C::nb * 64; o += C::threads) {
+    const int tt = o / 64, e = o % 64, i = e / 8, j = e % 8;
+    const bool tA = tt < C::nbu;
+    int ti, tj;
+    upper_tile(tA ? tt : tt - C::nbu, C::mb, ti, tj);
+    const int bi4 = 2 * ti + i / 4, bj4 = 2 * tj + j / 4;
+    if (bi4 >= C::MC || bj4 >= C::MC || bi4 > bj4) continue;
+    out[((tA ? 0 : C::nbu4) + upper_index(bi4, bj4, C::MC)) * 16 + (i % 4) * 4 + j % 4] = red[tt * 64 + e];
+  }
+}
+
+// partials [grid][nb * 16] -> symmetric G_A and G_B (M x M).  A block takes
+// 32 entries; its eight warps add every eighth partial row with four
+// independent sums each (so the loads overlap), and warp 0 adds the eight
+// warp sums in a fixed order.
+__global__ void __launch_bounds__(256) k_gram_reduce(const double *partials, int M, int grid, double *ga, double *gb,
+                                                     const int *done) {
+  __shared__ double red[8][33];
   if (done && *done) return;
   const Shape sh = shape_of(M);
-  const int lo = threadIdx.x & 7, oi = threadIdx.x >> 3;
-  const int o = blockIdx.x * 32 + oi;
-  double s = 0.0;
-  if (o < sh.nb * 16)
-    for (int g = lo; g < grid; g += 8) s += partials[static_cast<int64_t>(g) * sh.nb * 16 + o];
-  red[oi][lo] = s;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lane;
+  const int64_t stride = static_cast<int64_t>(sh.nb) * 16;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (o < sh.nb * 16) {
+    int g = w;
+    for (; g + 24 < grid; g += 32) {
+      s0 += partials[g * stride + o];
+      s1 += partials[(g + 8) * stride + o];
+      s2 += partials[(g + 16) * stride + o];
+      s3 += partials[(g + 24) * stride + o];
+    }
+    for (; g < grid; g += 8) s0 += partials[g * stride + o];
+  }
+  red[w][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
-  if (lo == 0 && o < sh.nb * 16) {
+  if (w == 0 && o < sh.nb * 16) {
     double tot = 0.0;
-    for (int k = 0; k < 8; ++k) tot += red[oi][k];
+    for (int k = 0; k < 8; ++k) tot += red[k][lane];
     const int tile = o / 16, q = o % 16, i = q / 4, j = q % 4;
     const bool isA = tile < sh.nbu;
     int bi, bj;
@@ -312,52 +522,83 @@ __global__ void k_gram_reduce(const double *partials, int M, int grid, double *g
 }
 
 template <typename T, int LD, int NBLK>
-void launch_t(cudaStream_t st, const GramArgs &a, const T *bd, int grid) {
-  constexpr int M = LD * NBLK;
-  const Shape sh = shape_of(M);
-  const size_t slabs = static_cast<size_t>(Tile<T>::stages) * Slab<T, LD, NBLK>::elems * sizeof(T);
-  const size_t red = static_cast<size_t>(sh.ngroups) * sh.nb * 16 * sizeof(double);
-  const size_t sm = slabs > red ? slabs : red;
-  if (sm > 48 * 1024)
-    SPX_CUDA(cudaFuncSetAttribute(k_gram<T, LD, NBLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(sm)));
+int launch_t(cudaStream_t st, const GramArgs &a, const T *bd, int grid) {
   auto p = [&](int k) { return k < NBLK ? static_cast<const T *>(a.s[k]) : nullptr; };
   auto q = [&](int k) { return k < NBLK ? static_cast<const T *>(a.ls[k]) : nullptr; };
-  k_gram<T, LD, NBLK><<<grid, kThreads, sm, st>>>(a.n, p(0), p(1), p(2), q(0), q(1), q(2), bd, a.partials, a.done);
-  SPX_LAUNCHED();
-}
-
-template <typename T, int NBLK>
-void launch_ld(cudaStream_t st, const GramArgs &a, const T *bd, int grid) {
-  switch (a.ld) {
-    case 4: launch_t<T, 4, NBLK>(st, a, bd, grid); break;
-    case 8: launch_t<T, 8, NBLK>(st, a, bd, grid); break;
-    case 12: launch_t<T, 12, NBLK>(st, a, bd, grid); break;
-    case 16: launch_t<T, 16, NBLK>(st, a, bd, grid); break;
-    default: fail(SPHYNX_ERR_INVALID_ARG, "gram: ld %d", a.ld);
+  if constexpr (std::is_same<T, float>::value) {
+    using C = G8<LD, NBLK>;
+    const size_t sm = C::smem_bytes;
+    // one wave of resident CTAs: each walks the slabs with a grid stride
+    SPX_CUDA(cudaFuncSetAttribute(k_gram8<LD, NBLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(sm)));
+    static int per_sm = 0;
+    if (per_sm == 0) {
+      int b = 0;
+      SPX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_gram8<LD, NBLK>, C::threads, sm));
+      per_sm = b > 0 ? b : 1;
+    }
+    // whole waves of resident CTAs, enough of them that no thread takes more
+    // than kFoldRows rows
+    const int64_t wave = static_cast<int64_t>(per_sm) * kSmCount;
+    const int64_t need = (a.n + static_cast<int64_t>(kFoldRows) * C::G - 1) / (static_cast<int64_t>(kFoldRows) * C::G);
+    int64_t g64 = (need + wave - 1) / wave * wave;
+    if (g64 > grid) g64 = grid;
+    const int g = static_cast<int>(g64);
+    k_gram8<LD, NBLK><<<g, C::threads, sm, st>>>(a.n, p(0), p(1), p(2), q(0), q(1), q(2), bd, a.partials, a.done);
+    SPX_LAUNCHED();
+    return g;
+  } else {
+    constexpr int M = LD * NBLK;
+    const Shape sh = shape_of(M);
+    const size_t slabs = static_cast<size_t>(Tile<T>::stages) * Slab<T, LD, NBLK>::elems * sizeof(T);
+    const size_t red = static_cast<size_t>(sh.ngroups) * sh.nb * 16 * sizeof(double);
+    const size_t sm = slabs > red ? slabs : red;
+    if (sm > 48 * 1024)
+      SPX_CUDA(cudaFuncSetAttribute(k_gram<T, LD, NBLK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(sm)));
+    // two waves of the 2 resident CTAs per SM; the compensated sums take any row count
+    const int g = grid < 4 * kSmCount ? grid : 4 * kSmCount;
+    k_gram<T, LD, NBLK><<<g, kThreads, sm, st>>>(a.n, p(0), p(1), p(2), q(0), q(1), q(2), bd, a.partials, a.done);
+    SPX_LAUNCHED();
+    return g;
   }
 }
 
+template <typename T, int NBLK>
+int launch_ld(cudaStream_t st, const GramArgs &a, const T *bd, int grid) {
+  switch (a.ld) {
+    case 4: return launch_t<T, 4, NBLK>(st, a, bd, grid);
+    case 8: return launch_t<T, 8, NBLK>(st, a, bd, grid);
+    case 12: return launch_t<T, 12, NBLK>(st, a, bd, grid);
+    case 16: return launch_t<T, 16, NBLK>(st, a, bd, grid);
+    default: fail(SPHYNX_ERR_INVALID_ARG, "gram: ld %d", a.ld);
+  }
+  return 0;
+}
+
 template <typename T>
-void launch_typed(cudaStream_t st, const GramArgs &a, const T *bd, int grid) {
+int launch_typed(cudaStream_t st, const GramArgs &a, const T *bd, int grid) {
   // 16-byte copies need 16-byte aligned blocks and diagonal
   for (int k = 0; k < a.nblk; ++k)
     if (reinterpret_cast<uintptr_t>(a.s[k]) % 16 || reinterpret_cast<uintptr_t>(a.ls[k]) % 16)
       fail(SPHYNX_ERR_INVALID_ARG, "gram: blocks must be 16-byte aligned");
   if (reinterpret_cast<uintptr_t>(bd) % 16) fail(SPHYNX_ERR_INVALID_ARG, "gram: B diagonal must be 16-byte aligned");
   switch (a.nblk) {
-    case 1: launch_ld<T, 1>(st, a, bd, grid); break;
-    case 2: launch_ld<T, 2>(st, a, bd, grid); break;
-    case 3: launch_ld<T, 3>(st, a, bd, grid); break;
+    case 1: return launch_ld<T, 1>(st, a, bd, grid);
+    case 2: return launch_ld<T, 2>(st, a, bd, grid);
+    case 3: return launch_ld<T, 3>(st, a, bd, grid);
     default: fail(SPHYNX_ERR_INVALID_ARG, "gram: nblk %d", a.nblk);
   }
+  return 0;
 }
 
 }  // namespace
 
 int gram_grid(int64_t n) {
-  int64_t g = (n + 63) / 64;
-  if (g > 4 * kSmCount) g = 4 * kSmCount;
+  // enough CTAs for both kernels: two waves of the 4 x 4 kernel, and for the
+  // 8 x 8 kernel (at least two row groups a CTA) at most kFoldRows rows a thread
+  int64_t g = (n + 2 * kFoldRows - 1) / (2 * kFoldRows) + 8 * kSmCount;
+  if (g > (n + 63) / 64) g = (n + 63) / 64;
   if (g < 1) g = 1;
   return static_cast<int>(g);
 }
@@ -366,9 +607,9 @@ size_t gram_partials_size(int nblk, int ld, int grid) {
   return static_cast<size_t>(grid) * shape_of(nblk * ld).nb * 16;
 }
 
-void launch_gram(cudaStream_t st, const GramArgs &a, int grid) {
-  if (a.dt == DT::F64) launch_typed<double>(st, a, a.bdiag, grid);
-  else launch_typed<float>(st, a, a.bdiagf, grid);
+int launch_gram(cudaStream_t st, const GramArgs &a, int grid) {
+  if (a.dt == DT::F64) return launch_typed<double>(st, a, a.bdiag, grid);
+  return launch_typed<float>(st, a, a.bdiagf, grid);
 }
 
 void launch_gram_reduce(cudaStream_t st, const double *partials, int nblk, int ld, int grid, double *ga,

@@ -274,7 +274,8 @@ struct GramArgs {
 };
 int gram_grid(int64_t n);
 size_t gram_partials_size(int nblk, int ld, int grid);
-void launch_gram(cudaStream_t st, const GramArgs &a, int grid);
+// launches at most `grid` CTAs and returns how many partial rows it wrote
+int launch_gram(cudaStream_t st, const GramArgs &a, int grid);
 
 struct UpdateArgs {
   DT dt;

@@ -271,7 +271,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   // the residual kernel writes H directly unless the polynomial needs R
   void *res_out = o->precond == SPHYNX_PRECOND_POLY ? R : H;
 
-  // line 1: initial block
+  // initial block
   if (x0_host) {
     DevBuf tmp;
     tmp.alloc(static_cast<size_t>(n) * b * sizeof(double));
@@ -283,11 +283,11 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   } else {
     launch_random_block(st, dt, X[0], n, b, ld, o->seed);
   }
-  // line 2: Rayleigh-Ritz on span(X~); line 3: R = L X0 - B X0 Theta0
+  // Rayleigh-Ritz on span(X~), then R = L X0 - B X0 Theta0
   plain_spmm(g, lap, dt, X[0], LX[0], ld, b, nullptr);
   GramArgs ga1{dt, 1, ld, n, {X[0], nullptr, nullptr}, {LX[0], nullptr, nullptr}, bd, bdf, gpart, ga, gb, done};
-  launch_gram(st, ga1, ggrid);
-  launch_gram_reduce(st, gpart, 1, ld, ggrid, ga, gb, done);
+  const int pg1 = launch_gram(st, ga1, ggrid);
+  launch_gram_reduce(st, gpart, 1, ld, pg1, ga, gb, done);
   launch_rayleigh_ritz(st, ga, gb, ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr,
                        o->precision != SPHYNX_FP64);
   UpdateArgs up1{dt, 1, ld, n, {X[0], nullptr, nullptr}, {nullptr, nullptr, nullptr}, yt, X[1], nullptr, nullptr, done};
@@ -305,21 +305,21 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   int *hflag = static_cast<int *>(g->host_flag);
   for (int it = 0; it < o->max_iter; ++it) {
     const int nx = cur ^ 1;
-    if (o->precond == SPHYNX_PRECOND_POLY) poly_apply(g, o->precision, R, H, ld, b, done);   // line 6
+    if (o->precond == SPHYNX_PRECOND_POLY) poly_apply(g, o->precision, R, H, ld, b, done);   // precondition
     plain_spmm(g, lap, dt, H, LH, ld, b, done);
     GramArgs g3{dt, 3, ld, n, {X[cur], H, P[cur]}, {LX[cur], LH, LP[cur]}, bd, bdf, gpart, ga, gb, done};
-    launch_gram(st, g3, ggrid);                                                        // line 7
-    launch_gram_reduce(st, gpart, 3, ld, ggrid, ga, gb, done);
+    const int pg3 = launch_gram(st, g3, ggrid);                                        // Rayleigh-Ritz
+    launch_gram_reduce(st, gpart, 3, ld, pg3, ga, gb, done);
     launch_rayleigh_ritz(st, ga, gb, 3 * ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr,
                        o->precision != SPHYNX_FP64);
     UpdateArgs u3{dt, 3, ld, n, {X[cur], H, P[cur]}, {nullptr, LH, LP[cur]}, yt, X[nx], P[nx], LP[nx], done};
-    launch_update(st, u3);                                                             // lines 8, 12
-    plain_spmm(g, lap, dt, X[nx], LX[nx], ld, b, done);                                 // line 9
+    launch_update(st, u3);                                                             // update, direction
+    plain_spmm(g, lap, dt, X[nx], LX[nx], ld, b, done);                                 // residual
     ResidualArgs r3 = ra;
     r3.x = X[nx];
     r3.lx = LX[nx];
     launch_residual(st, r3, rgrid);
-    launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_abs, 1, o->max_iter, o->stall_window);  // lines 10-11
+    launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_abs, 1, o->max_iter, o->stall_window);  // lock
     g->ctr.launches += 6;
     cur = nx;
     if ((it + 1) % sync_every == 0 || it + 1 == o->max_iter) {
@@ -607,13 +607,13 @@ int sphynx_partition(sphynx_handle g, int32_t K, const sphynx_options *opt, int3
     EigenResult r = lobpcg(g, opt, d, nullptr);
     SPX_CUDA(cudaEventRecord(e[1], st));
     canonical_rotation_block(g, const_cast<void *>(r.x), g->n, r.ld, r.dt, r.theta, d, opt->tol, opt->seed);
-    // Algorithm 2 lines 6-10: coordinates from eigenvectors 2..d
+    // Algorithm 2: coordinates from eigenvectors 2..d
     const size_t es = dt_size(r.dt);
     void *coords = g->workspace("coords", static_cast<size_t>(g->n) * (d - 1) * es + 16, false);
     double *sc = static_cast<double *>(g->workspace("signs", static_cast<size_t>(vec_grid(g->n)) * d * 3 * 8 + 16 * 8, false));
     launch_signs_coords(st, r.dt, r.x, g->n, r.ld, d, coords, sc);
     void *mjs = g->workspace("mj", mj_scratch_bytes(g->n, K, 1), false);
-    run_mj_scratch(st, r.dt, coords, d - 1, d - 1, g->n, g->vw, K, dpart, &g->ctr, mjs, nullptr, 1);   // line 12
+    run_mj_scratch(st, r.dt, coords, d - 1, d - 1, g->n, g->vw, K, dpart, &g->ctr, mjs, nullptr, 1);   // multi-jagged partition
     g->ctr.launches += 3;
     SPX_CUDA(cudaEventRecord(e[2], st));
     double cut = 0, cut2 = 0, imb = 0;

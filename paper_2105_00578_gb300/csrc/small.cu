@@ -1,6 +1,6 @@
 // small.cu -- FP64 small dense algebra on the GPU, one CTA per problem.
 //
-// * Rayleigh-Ritz (Sec. 3.3; Algorithm 1 lines 2 and 7): with G_A = S^T L S
+// * Rayleigh-Ritz (Sec. 3.3; the Rayleigh-Ritz steps of Algorithm 1): with G_A = S^T L S
 //   and G_B = S^T B S restricted to the active columns of S and symmetrised,
 //   scale to unit diagonal (D), factor D G_B D = R^T R (Cholesky, the small
 //   half of Cholesky-QR) and take C = R^{-1}; if a pivot falls below

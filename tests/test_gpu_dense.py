@@ -13,12 +13,22 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("nblk,ld", [(1, 4), (3, 4), (3, 8), (2, 12), (3, 16)])
+@pytest.mark.parametrize("nblk,ld", [(1, 4), (3, 4), (2, 8), (3, 8), (2, 12), (3, 12), (3, 16)])
 @pytest.mark.parametrize("withb", [False, True])
 def test_gram_matches_numpy(dtype, nblk, ld, withb):
+    _gram_case(dtype, nblk, ld, withb, 10007)
+
+
+@pytest.mark.parametrize("nblk,ld", [(3, 8), (3, 12)])
+def test_gram_many_slabs_per_cta(nblk, ld):
+    """Enough rows that every CTA walks many 64-row slabs and folds its float
+    sums into the compensated pair several times, with a ragged last slab."""
+    _gram_case("f32", nblk, ld, True, 300007)
+
+
+def _gram_case(dtype, nblk, ld, withb, n):
     import paper_2105_00578_gb300 as spx
     torch = torch_mod()
-    n = 10007
     rng = np.random.default_rng(nblk * 100 + ld)
     s = [rng.standard_normal((n, ld)) for _ in range(nblk)]
     ls = [rng.standard_normal((n, ld)) for _ in range(nblk)]
