@@ -110,8 +110,9 @@ typedef struct {
                           w > 0: also stop, with NOCONV and the best iterate,
                           once every unconverged column has gone w iterations
                           without its residual falling below 0.9 x its best so
-                          far (FP32 blocks cannot reach tol * theta when that is
-                          below the FP32 rounding of L x)                     */
+                          far, its best residual being under the noise floor
+                          10 u rho (FP32 blocks cannot reach tol * theta when
+                          that is below the FP32 rounding of L x)             */
   int32_t reserved[5];
 } sphynx_options;
 

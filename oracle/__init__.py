@@ -36,4 +36,4 @@ from .lobpcg import lobpcg, rayleigh_ritz, LobpcgResult  # noqa: F401
 from .mj import multijagged, coord_sort_key  # noqa: F401
 from .metrics import cutsize, imbalance, part_weights  # noqa: F401
 from .sphynx import (partition, num_eigenvectors, initial_block, canonical_rotation, eigen_clusters,  # noqa: F401
-                     sign_normalise, is_regular, default_options)
+                     sign_normalise, is_regular, default_options, gershgorin_rho, max_row_terms)

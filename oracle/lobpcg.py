@@ -27,11 +27,14 @@ eigenvector of the projected problem is given the sign that makes its entry
 of largest magnitude positive (first such entry on ties).
 
 Convergence (the paper names the tolerance but not the test): column i has
-converged when ||r_i||_{B^-1} <= tol |theta_i|, or when both |theta_i| and
-||r_i||_{B^-1} are below the noise floor 10 u_work rho, rho = 2 for L_N and the
-generalized problem and 2 max deg for L_C (a Gershgorin bound); x_i is
-B-normalised by RR.  The floor thus only admits the eigenvalue-zero vector,
-whose relative test can never be met.
+converged when ||r_i||_{B^-1} <= tol |theta_i|, or when |theta_i| <= 10 u_work
+rho and ||r_i||_{B^-1} <= 10 u_work rho t, with rho = 2 for L_N and the
+generalized problem and 2 max deg for L_C (a Gershgorin bound) and t the most
+terms in a row of L (max degree + 1); x_i is B-normalised by RR.  The theta
+bound only admits the eigenvalue-zero vector, whose relative test can never
+be met; the residual bound is the rounding error of one product L x, which
+grows with the terms a row adds up (a hub row of 10^5 entries leaves about
+3e-15 in FP64, above 10 u rho).
 
 Pins (tests/test_oracle_lobpcg.py): closed-form path, cycle and grid spectra,
 dense ``eigh`` on small graphs (eigenvalues and subspace angles), the
@@ -113,22 +116,23 @@ def residual_norms(r: np.ndarray, bdiag) -> np.ndarray:
 
 
 def lobpcg(apply_l, bdiag, apply_m, x0: np.ndarray, tol: float, maxit: int,
-           rho: float, u_work: float = U_FP64) -> LobpcgResult:
+           rho: float, u_work: float = U_FP64, row_terms: int = 1) -> LobpcgResult:
     """Algorithm 1 for the nev = x0.shape[1] smallest eigenpairs of L x = lambda B x.
 
     apply_l(V): L V;  bdiag: diagonal of B or None;  apply_m(R): preconditioner
     (None for no preconditioning);  rho: the Gershgorin bound used by the
-    noise floor."""
+    noise floor;  row_terms: the most terms in a row of L (max degree + 1)."""
     n, nev = x0.shape
 
     def bmul(v):
         return v if bdiag is None else bdiag[:, None] * v
 
-    floor = 10.0 * u_work * rho
+    floor_th = 10.0 * u_work * rho
+    floor_res = floor_th * row_terms
 
     def test(r, th):
         res = residual_norms(r, bdiag)
-        return res, (res <= tol * np.abs(th)) | ((np.abs(th) <= floor) & (res <= floor))
+        return res, (res <= tol * np.abs(th)) | ((np.abs(th) <= floor_th) & (res <= floor_res))
 
     # start and first residual
     lx0 = apply_l(x0)

@@ -122,6 +122,11 @@ def gershgorin_rho(g, problem: str) -> float:
     return 2.0
 
 
+def max_row_terms(g) -> int:
+    """Most terms a row of the Laplacian adds up: max degree + 1."""
+    return int(np.diff(g.row_ptr).max()) + 1 if g.n else 1
+
+
 @dataclasses.dataclass
 class PartitionResult:
     parts: np.ndarray
@@ -168,7 +173,7 @@ def partition(g, num_parts: int, problem: str = COMBINATORIAL, precond: str = "j
     else:
         raise ValueError(precond)
     x0 = initial_block(g, problem, d, init, seed)
-    res = lobpcg(apply_l, bdiag, apply_m, x0, tol, maxit, gershgorin_rho(g, problem), u_work)
+    res = lobpcg(apply_l, bdiag, apply_m, x0, tol, maxit, gershgorin_rho(g, problem), u_work, max_row_terms(g))
     e = sign_normalise(canonical_rotation(res.x, res.theta, tol, seed))
     coords = np.ascontiguousarray(e[:, 1:d])
     parts = multijagged(coords, vwts, num_parts)

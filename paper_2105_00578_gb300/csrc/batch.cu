@@ -242,14 +242,21 @@ k_bresidual(ChunkView cv, const SolverState *states, const T *x, const T *lx, co
 
 // ---- convergence per graph (the single-graph test), and the loop condition ----
 // ctl[0]: graphs not done; ctl[1]: iterations of the batch loop
+// floors per graph, as the single-graph test takes them from that graph alone:
+// theta within 10 u rho (rho = 2 max weighted degree for L_C, else 2) and the
+// residual within 10 u rho (max degree + 1)
 __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int count, const double *partials, int b,
-                            int ld, double tol, double floor_abs, int count_iteration, int maxit, int stall_window,
+                            int ld, double tol, double u_work, int rho_from_degree,
+                            const unsigned long long *gmax, int count_iteration, int maxit, int stall_window,
                             int *ctl) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
   SolverState *st = states + q;
   if (st->done) return;
   const int c0 = gchunk0[q], c1 = gchunk0[q + 1];
+  const double rho = rho_from_degree ? 2.0 * __longlong_as_double(static_cast<long long>(gmax[2 * q + 1])) : 2.0;
+  const double floor_th = 10.0 * u_work * rho;
+  const double floor_res = floor_th * static_cast<double>(gmax[2 * q] + 1);
   int nconv = 0;
   for (int j = 0; j < b; ++j) {
     double tot = 0.0;
@@ -257,7 +264,7 @@ __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int cou
     const double res = sqrt(tot);
     st->resnorm[j] = res;
     const double th = fabs(st->theta[j]);
-    const bool ok = (res <= tol * th) || (th <= floor_abs && res <= floor_abs);
+    const bool ok = (res <= tol * th) || (th <= floor_th && res <= floor_res);
     st->conv[j] = ok ? 1 : 0;
     nconv += ok ? 1 : 0;
   }
@@ -266,7 +273,7 @@ __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int cou
     st->iters += 1;
     st->pvalid = 1;
   }
-  const bool stalled = stall_check(st, b, stall_window, count_iteration);
+  const bool stalled = stall_check(st, b, stall_window, count_iteration, floor_th);
   if (nconv == b) {
     st->done = 1;
     st->status = SPHYNX_OK;
@@ -404,6 +411,40 @@ __global__ void k_check_blocks(ChunkView cv, const int64_t *gptr, const int64_t 
   if (b) atomicOr(bad, 1u);
 }
 
+// per-graph maxima over the rows of each chunk: entries per row (the most
+// terms a row of L adds) and weighted degree (non-negative doubles order like
+// their bit patterns)
+__global__ void k_bgraph_max(ChunkView cv, const int64_t *rp, const double *deg, unsigned long long *gmax) {
+  __shared__ unsigned long long red[2][32];
+  const int c = blockIdx.x, q = cv.graph[c];
+  unsigned long long md = 0, mw = 0;
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x) {
+    const unsigned long long d = static_cast<unsigned long long>(rp[i + 1] - rp[i]);
+    const unsigned long long w = static_cast<unsigned long long>(__double_as_longlong(deg[i]));
+    md = d > md ? d : md;
+    mw = w > mw ? w : mw;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, md, o), b = __shfl_xor_sync(0xffffffffu, mw, o);
+    md = a > md ? a : md;
+    mw = b > mw ? b : mw;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][w] = md;
+    red[1][w] = mw;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < static_cast<int>(blockDim.x >> 5); ++k) {
+      md = red[0][k] > md ? red[0][k] : md;
+      mw = red[1][k] > mw ? red[1][k] : mw;
+    }
+    atomicMax(&gmax[2 * q], md);
+    atomicMax(&gmax[2 * q + 1], mw);
+  }
+}
+
 ChunkView view_of(const sphynx_graph *g) {
   return ChunkView{g->batch.chunk_graph.as<int32_t>(), g->batch.chunk_begin.as<int64_t>()};
 }
@@ -516,6 +557,11 @@ void batch_setup(sphynx_graph *g, const int64_t *h_gptr, int count) {
   SPX_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(hb), cudaMemcpyDeviceToHost, g->stream));
   SPX_CUDA(cudaStreamSynchronize(g->stream));
   if (hb) fail(SPHYNX_ERR_INVALID_ARG, "a graph of the batch has an edge leaving its own vertex range");
+  B.graph_max.alloc(static_cast<size_t>(count) * 2 * sizeof(unsigned long long));
+  SPX_CUDA(cudaMemsetAsync(B.graph_max.p, 0, static_cast<size_t>(count) * 2 * sizeof(unsigned long long), g->stream));
+  k_bgraph_max<<<static_cast<unsigned>(B.n_chunks), 256, 0, g->stream>>>(view_of(g), g->rowptr, g->deg.as<double>(),
+                                                                       B.graph_max.as<unsigned long long>());
+  SPX_LAUNCHED();
 }
 
 // The batched partition: every graph's LOBPCG in one captured graph launch,
@@ -554,8 +600,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   const int lap = o->laplacian == SPHYNX_NORMALIZED ? SPHYNX_NORMALIZED : SPHYNX_COMBINATORIAL;
   const bool gen = o->laplacian == SPHYNX_GENERALIZED;
   const double u_work = o->precision == SPHYNX_FP64 ? 0x1.0p-53 : 0x1.0p-24;
-  const double rho = lap == SPHYNX_COMBINATORIAL && !gen ? 2.0 * g->max_wdeg : 2.0;
-  const double floor_abs = 10.0 * u_work * rho;
+  const int rho_from_degree = lap == SPHYNX_COMBINATORIAL && !gen ? 1 : 0;        // noise floors, per graph
   const bool jac = o->precond == SPHYNX_PRECOND_JACOBI && lap == SPHYNX_COMBINATORIAL;
   const size_t blk = static_cast<size_t>(n) * ld * es;
   const int64_t nch = B.n_chunks;
@@ -600,7 +645,8 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     else launch_bresidual_ld<float>(st, g, states, ld, x, lx, bd, jv, out, npart);
   };
   auto converge = [&](int count_iteration) {
-    k_bconverge<<<(count + 127) / 128, 128, 0, st>>>(gc0, states, count, npart, b, ld, o->tol, floor_abs,
+    k_bconverge<<<(count + 127) / 128, 128, 0, st>>>(gc0, states, count, npart, b, ld, o->tol, u_work, rho_from_degree,
+                                                      B.graph_max.as<unsigned long long>(),
                                                       count_iteration, o->max_iter, o->stall_window, ctl);
     SPX_LAUNCHED();
   };

@@ -182,6 +182,7 @@ struct BatchInfo {
   DevBuf chunk_graph;               // int32 [n_chunks]: graph of each chunk
   DevBuf chunk_begin;               // int64 [n_chunks + 1]: first row of each chunk, then n
   DevBuf graph_chunk0;              // int32 [count + 1]: first chunk of each graph
+  DevBuf graph_max;                 // uint64 [count][2]: max degree, max weighted degree (double bits)
 };
 
 }  // namespace sphynx
@@ -323,7 +324,7 @@ struct SolverState {         // device-resident LOBPCG bookkeeping
 };
 // Stall window: true once every unconverged column has gone `window`
 // iterations without its residual falling below 0.9 x its best so far.
-__device__ inline bool stall_check(SolverState *st, int b, int window, int count_iteration) {
+__device__ inline bool stall_check(SolverState *st, int b, int window, int count_iteration, double floor_th) {
   if (window <= 0 || !count_iteration) return false;
   bool all = true;
   for (int j = 0; j < b; ++j) {
@@ -335,13 +336,15 @@ __device__ inline bool stall_check(SolverState *st, int b, int window, int count
     } else {
       st->since_best[j] += 1;
     }
-    all = all && st->since_best[j] >= window;
+    // a column still far above the noise floor is converging slowly, not stalled
+    all = all && st->since_best[j] >= window && st->best_res[j] <= floor_th;
   }
   return all;
 }
 
 void launch_converge(cudaStream_t st, SolverState *state, const double *partials, int grid, int b,
-                     int ld, double tol, double floor_abs, int count_iteration, int maxit, int stall_window = 0);
+                     int ld, double tol, double floor_th, double floor_res, int count_iteration, int maxit,
+                     int stall_window = 0);
 
 void launch_signs_coords(cudaStream_t st, DT dt, const void *x, int64_t n, int ld, int b,
                          void *coords, double *scratch);

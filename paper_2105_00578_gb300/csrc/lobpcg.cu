@@ -239,7 +239,10 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   const bool gen = o->laplacian == SPHYNX_GENERALIZED;
   const double u_work = o->precision == SPHYNX_FP64 ? 0x1.0p-53 : 0x1.0p-24;
   const double rho = lap == SPHYNX_COMBINATORIAL && !gen ? 2.0 * g->max_wdeg : 2.0;
-  const double floor_abs = 10.0 * u_work * rho;
+  // noise floors of the eigenvalue-zero vector: |theta| within 10 u rho, and
+  // ||r|| within the rounding bound of one row of L x, 10 u rho (d_max + 1)
+  const double floor_th = 10.0 * u_work * rho;
+  const double floor_res = floor_th * static_cast<double>(g->max_degree + 1);
   const size_t blk = static_cast<size_t>(n) * ld * es;
 
   cudaEvent_t ev0, ev1;
@@ -296,7 +299,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   ResidualArgs ra{dt, ld, n, X[1], LX[1], state->theta, bd, bdf, jac ? g->jinv.as<double>() : nullptr,
                   jac ? g->jinvf.as<float>() : nullptr, res_out, npart, done};
   launch_residual(st, ra, rgrid);
-  launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_abs, 0, o->max_iter);
+  launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_th, floor_res, 0, o->max_iter);
   g->ctr.launches += 8;
 
   int sync_every = o->sync_every;
@@ -319,7 +322,8 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
     r3.x = X[nx];
     r3.lx = LX[nx];
     launch_residual(st, r3, rgrid);
-    launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_abs, 1, o->max_iter, o->stall_window);  // lock
+    launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_th, floor_res, 1, o->max_iter,
+                    o->stall_window);  // lock
     g->ctr.launches += 6;
     cur = nx;
     if ((it + 1) % sync_every == 0 || it + 1 == o->max_iter) {

@@ -46,13 +46,15 @@ __device__ double chol_upper(double *B, int ld, int m, double *scratch) {
         scratch[0] = -1.0;
       } else {
         if (d < scratch[0]) scratch[0] = d;
-        B[k * ld + k] = sqrt(d);
+        const double r = rsqrt(d);   // 1 / R_kk; R_kk = d r (the row below is scaled by r, not divided)
+        B[k * ld + k] = d * r;
+        scratch[1] = r;
       }
     }
     __syncthreads();
     if (scratch[0] < 0.0) return -1.0;
-    const double rkk = B[k * ld + k];
-    for (int j = k + 1 + tid; j < m; j += blockDim.x) B[k * ld + j] /= rkk;
+    const double rinv = scratch[1];
+    for (int j = k + 1 + tid; j < m; j += blockDim.x) B[k * ld + j] *= rinv;
     __syncthreads();
     const int rem = m - k - 1;
     for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
@@ -67,15 +69,24 @@ __device__ double chol_upper(double *B, int ld, int m, double *scratch) {
 }
 
 // C = R^{-1} for upper-triangular R (leading m x m, ld); C is upper triangular.
-__device__ void tri_inv_upper(const double *R, int ld, int m, double *C, int ldc) {
+// Thread j solves column j by back substitution; the pivot reciprocals are
+// formed first, in parallel, so that no division sits on the column's
+// dependent chain, and each dot product runs in two independent halves.
+__device__ void tri_inv_upper(const double *R, int ld, int m, double *C, int ldc, double *rinv) {
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) C[(idx / m) * ldc + idx % m] = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) rinv[j] = 1.0 / R[j * ld + j];
   __syncthreads();
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    C[j * ldc + j] = 1.0 / R[j * ld + j];
+    C[j * ldc + j] = rinv[j];
     for (int i = j - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1; k <= j; ++k) s += R[i * ld + k] * C[k * ldc + j];
-      C[i * ldc + j] = -s / R[i * ld + i];
+      double s0 = 0.0, s1 = 0.0;
+      int k = i + 1;
+      for (; k + 1 <= j; k += 2) {
+        s0 += R[i * ld + k] * C[k * ldc + j];
+        s1 += R[i * ld + k + 1] * C[(k + 1) * ldc + j];
+      }
+      if (k <= j) s0 += R[i * ld + k] * C[k * ldc + j];
+      C[i * ldc + j] = -(s0 + s1) * rinv[i];
     }
   }
   __syncthreads();
@@ -113,11 +124,28 @@ __device__ __forceinline__ double abs_t(double v) { return fabs(v); }
 __device__ __forceinline__ float abs_t(float v) { return fabsf(v); }
 
 // Cyclic Jacobi: A (m x m, ld) -> diagonal of eigenvalues, V (ld) eigenvectors
-// in columns, in double or float.  `pairs` needs 4 * kMaxM entries, `cnt`
-// three ints.  A rotation is skipped below rel * (|a_pp| + |a_qq|), rel a few
-// units of the type's rounding.
+// in columns, in double or float.  `cs` needs 2 * kMaxM entries of T, `pq`
+// 2 * kMaxM ints.  A rotation is skipped below rel * (|a_pp| + |a_qq|), rel a
+// few units of the type's rounding.  A round is two block barriers: the first
+// (__syncthreads_count) publishes the rotations and counts them, the second
+// ends their application.  The rounds' critical path is the rotation angle,
+// so everything else is hoisted out of it: a thread decodes its share of the
+// update once per call, and the round-robin partners advance by one with a
+// wrap instead of a modulo.  In float the angle uses the fast reciprocal and
+// reciprocal square root, whose rounding only perturbs the angle:
+// c = rsqrt(1 + t^2), s = t c keep the rotation orthogonal to working accuracy.
+__device__ __forceinline__ double jrcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float jrcp(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double jsqrt1(double x) { return sqrt(x); }
+__device__ __forceinline__ float jsqrt1(float x) { return x * rsqrtf(x); }   // x >= 1
+
+// update items per thread: np^2 blocks of A plus m np entries of V, at most
+// 24 * 24 + 48 * 24 = 1728 for m = kMaxM, over kSmallThreads threads
+constexpr int kJacobiItems = (24 * 24 + 48 * 24 + 255) / 256;
+static_assert(kMaxM == 48 && kSmallThreads == 256, "kJacobiItems assumes m <= 48 and 256 threads");
+
 template <typename T>
-__device__ void jacobi_eig(T *A, int ld, T *V, int ldv, int m, T *pairs, int *cnt) {
+__device__ void jacobi_eig(T *A, int ld, T *V, int ldv, int m, T *cs, int *pq) {
   const T rel = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
   const int tid = threadIdx.x;
   for (int idx = tid; idx < m * m; idx += blockDim.x) {
@@ -128,83 +156,97 @@ __device__ void jacobi_eig(T *A, int ld, T *V, int ldv, int m, T *pairs, int *cn
   if (m < 2) return;
   const int mp = m + (m & 1);
   const int np = mp / 2;
-  // cnt[0]: rotations this sweep; cnt[1 + (r & 1)]: rotations of round r.
-  // Each counter is reset only after a barrier that follows its last read.
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    __syncthreads();
-    if (tid == 0) {
-      cnt[0] = 0;
-      cnt[1] = 0;
-      cnt[2] = 0;
+  // this thread's update items: 2 x 2 blocks (k, l) of A, then entries (i, l) of V
+  int ik[kJacobiItems], il[kJacobiItems];
+  int nitems = 0;
+#pragma unroll
+  for (int u = 0; u < kJacobiItems; ++u) {
+    const int idx = tid + u * static_cast<int>(blockDim.x);
+    ik[u] = -1;
+    il[u] = 0;
+    if (idx < np * np) {
+      ik[u] = idx / np;
+      il[u] = idx - (idx / np) * np;
+      nitems = u + 1;
+    } else if (idx < np * np + m * np) {
+      const int it = idx - np * np;
+      ik[u] = np + it / np;   // >= np marks a V row: i = ik - np
+      il[u] = it - (it / np) * np;
+      nitems = u + 1;
     }
-    __syncthreads();
+  }
+  // round-robin partners of pair k (thread k < np): position 0 stays, the
+  // others cycle through 1 .. mp - 1
+  const int k2 = mp - 1 - tid;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    int rotations = 0;   // the same in every thread: a sum of block-wide counts
+    int a0 = tid == 0 ? 0 : ((tid - 1) % (mp - 1)) + 1;
+    int a1 = tid < np ? ((k2 - 1) % (mp - 1)) + 1 : 0;
     for (int r = 0; r < mp - 1; ++r) {
-      int *rc = &cnt[1 + (r & 1)];
+      int rot = 0;
       if (tid < np) {
-        const int k = tid;
-        const int a0 = k == 0 ? 0 : ((k - 1 + r) % (mp - 1)) + 1;
-        const int k2 = mp - 1 - k;
-        const int a1 = k2 == 0 ? 0 : ((k2 - 1 + r) % (mp - 1)) + 1;
         const int p = a0 < a1 ? a0 : a1, q = a0 < a1 ? a1 : a0;
         T c = T(1), s = T(0);
         if (q < m) {
           const T app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
           if (apq != T(0) && abs_t(apq) > rel * (abs_t(app) + abs_t(aqq))) {
-            const T tau = (aqq - app) / (T(2) * apq);
-            const T t = tau == T(0) ? T(1) : (tau > T(0) ? T(1) : T(-1)) / (abs_t(tau) + sqrt_t(T(1) + tau * tau));
+            const T tau = (aqq - app) * T(0.5) * jrcp(apq);
+            const T t = tau == T(0) ? T(1)
+                                    : (tau > T(0) ? T(1) : T(-1)) * jrcp(abs_t(tau) + jsqrt1(T(1) + tau * tau));
             c = inv_sqrt(T(1) + t * t);
             s = t * c;
-            atomicAdd(rc, 1);
+            rot = 1;
           }
         }
-        pairs[4 * k] = c;
-        pairs[4 * k + 1] = s;
-        pairs[4 * k + 2] = static_cast<T>(p);
-        pairs[4 * k + 3] = static_cast<T>(q);
+        cs[2 * tid] = c;
+        cs[2 * tid + 1] = s;
+        pq[2 * tid] = p;
+        pq[2 * tid + 1] = q;
+        if (tid != 0) a0 = a0 == mp - 1 ? 1 : a0 + 1;
+        a1 = a1 == mp - 1 ? 1 : a1 + 1;
       }
-      __syncthreads();
-      const int rot = *rc;                              // same value in every thread
-      if (tid == 0) cnt[1 + ((r + 1) & 1)] = 0;         // next round's counter, last read a round ago
+      const int nrot = __syncthreads_count(rot);
+      rotations += nrot;
       // A <- J^T A J one 2 x 2 block per pair of rotation pairs (the pairs are
       // disjoint, so the blocks are too), and V <- V J
-      for (int idx = rot ? tid : np * np + m * np; idx < np * np + m * np; idx += blockDim.x) {
-        if (idx < np * np) {
-          const int k = idx / np, l = idx - (idx / np) * np;
-          const T ck = pairs[4 * k], sk = pairs[4 * k + 1];
-          const T cl = pairs[4 * l], sl = pairs[4 * l + 1];
-          if (sk == T(0) && sl == T(0)) continue;
-          const int pk = static_cast<int>(pairs[4 * k + 2]), qk = static_cast<int>(pairs[4 * k + 3]);
-          const int pl = static_cast<int>(pairs[4 * l + 2]), ql = static_cast<int>(pairs[4 * l + 3]);
-          const bool hk = qk < m, hl = ql < m;
-          const T a = A[pk * ld + pl];
-          const T b = hl ? A[pk * ld + ql] : T(0);
-          const T c = hk ? A[qk * ld + pl] : T(0);
-          const T d = (hk && hl) ? A[qk * ld + ql] : T(0);
-          // rows (J_k^T), then columns (J_l)
-          const T r0a = ck * a - sk * c, r0b = ck * b - sk * d;
-          const T r1a = sk * a + ck * c, r1b = sk * b + ck * d;
-          A[pk * ld + pl] = cl * r0a - sl * r0b;
-          if (hl) A[pk * ld + ql] = (k == l) ? T(0) : sl * r0a + cl * r0b;
-          if (hk) A[qk * ld + pl] = (k == l) ? T(0) : cl * r1a - sl * r1b;
-          if (hk && hl) A[qk * ld + ql] = sl * r1a + cl * r1b;
-        } else {
-          const int it = idx - np * np;
-          const int i = it / np, l = it - (it / np) * np;
-          const T cl = pairs[4 * l], sl = pairs[4 * l + 1];
-          const int pl = static_cast<int>(pairs[4 * l + 2]), ql = static_cast<int>(pairs[4 * l + 3]);
-          if (sl == T(0) || ql >= m) continue;
-          const T vp = V[i * ldv + pl], vq = V[i * ldv + ql];
-          V[i * ldv + pl] = cl * vp - sl * vq;
-          V[i * ldv + ql] = sl * vp + cl * vq;
+      if (nrot) {
+#pragma unroll
+        for (int u = 0; u < kJacobiItems; ++u) {
+          if (u >= nitems) break;
+          const int k = ik[u], l = il[u];
+          if (k < np) {
+            const T ck = cs[2 * k], sk = cs[2 * k + 1];
+            const T cl = cs[2 * l], sl = cs[2 * l + 1];
+            if (sk == T(0) && sl == T(0)) continue;
+            const int pk = pq[2 * k], qk = pq[2 * k + 1];
+            const int pl = pq[2 * l], ql = pq[2 * l + 1];
+            const bool hk = qk < m, hl = ql < m;
+            const T a = A[pk * ld + pl];
+            const T b = hl ? A[pk * ld + ql] : T(0);
+            const T c = hk ? A[qk * ld + pl] : T(0);
+            const T d = (hk && hl) ? A[qk * ld + ql] : T(0);
+            // rows (J_k^T), then columns (J_l)
+            const T r0a = ck * a - sk * c, r0b = ck * b - sk * d;
+            const T r1a = sk * a + ck * c, r1b = sk * b + ck * d;
+            A[pk * ld + pl] = cl * r0a - sl * r0b;
+            if (hl) A[pk * ld + ql] = (k == l) ? T(0) : sl * r0a + cl * r0b;
+            if (hk) A[qk * ld + pl] = (k == l) ? T(0) : cl * r1a - sl * r1b;
+            if (hk && hl) A[qk * ld + ql] = sl * r1a + cl * r1b;
+          } else if (k >= np) {
+            const int i = k - np;
+            const T cl = cs[2 * l], sl = cs[2 * l + 1];
+            const int pl = pq[2 * l], ql = pq[2 * l + 1];
+            if (sl == T(0) || ql >= m) continue;
+            const T vp = V[i * ldv + pl], vq = V[i * ldv + ql];
+            V[i * ldv + pl] = cl * vp - sl * vq;
+            V[i * ldv + ql] = sl * vp + cl * vq;
+          }
         }
       }
-      if (tid == 0) cnt[0] += rot;
       __syncthreads();
     }
-    __syncthreads();
-    if (cnt[0] == 0) break;   // read by all threads between two barriers: uniform
+    if (rotations == 0) break;   // uniform: every thread summed the same counts
   }
-  __syncthreads();
 }
 
 // order[0..m) = indices of diag(A) sorted ascending (stable on equal values)
@@ -230,18 +272,22 @@ struct RRSmem {
   double W[kMaxM * kMaxM];   // projected matrix -> eigenvalues on diagonal
   double V[kMaxM * kMaxM];   // eigenvectors of W
   double Bh[kMaxM * kMaxM];  // scaled G_B, kept for the Rayleigh quotients
-  float A32[kMaxM * kMaxM];  // float copies for the mixed-precision solve
-  float V32[kMaxM * kMaxM];
-  float pairs32[4 * kMaxM];
+  float A32[kMaxM * (kMaxM + 1)];  // float copies for the mixed-precision solve (odd leading dimension)
+  float V32[kMaxM * (kMaxM + 1)];
+  float cs32[2 * kMaxM];
+  int pq32[2 * kMaxM];
   double d[kMaxM];
-  double pairs[4 * kMaxM];
+  double rinv[kMaxM];        // reciprocal Cholesky pivots
+  double cs[2 * kMaxM];      // Jacobi rotations (c, s) and pairs (p, q)
+  int pq[2 * kMaxM];
   double qa[SPHYNX_MAX_NEV], qb[SPHYNX_MAX_NEV];
   double scratch[4];
   int idx[kMaxM];            // active column -> full index
   int order[kMaxM];
   int keep[kMaxM];
   int sel[SPHYNX_MAX_NEV];
-  int m, m2, cnt[3], fail, svqb;
+  unsigned amask[2];         // active columns, one ballot per warp
+  int m, m2, fail, svqb;
 };
 
 // Symmetric eigendecomposition of the leading m x m of A (ld kMaxM) into
@@ -249,17 +295,18 @@ struct RRSmem {
 __device__ void eig_sym(RRSmem &S, double *A, double *V, int m, bool mixed) {
   const int L = kMaxM;
   if (!mixed) {
-    jacobi_eig<double>(A, L, V, L, m, S.pairs, S.cnt);
+    jacobi_eig<double>(A, L, V, L, m, S.cs, S.pq);
     return;
   }
+  constexpr int L32 = kMaxM + 1;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x)
-    S.A32[(e / m) * L + e % m] = static_cast<float>(A[(e / m) * L + e % m]);
+    S.A32[(e / m) * L32 + e % m] = static_cast<float>(A[(e / m) * L + e % m]);
   __syncthreads();
-  jacobi_eig<float>(S.A32, L, S.V32, L, m, S.pairs32, S.cnt);
+  jacobi_eig<float>(S.A32, L32, S.V32, L32, m, S.cs32, S.pq32);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e % m;
-    V[i * L + j] = static_cast<double>(S.V32[i * L + j]);
-    A[i * L + j] = i == j ? static_cast<double>(S.A32[i * L + j]) : 0.0;
+    V[i * L + j] = static_cast<double>(S.V32[i * L32 + j]);
+    A[i * L + j] = i == j ? static_cast<double>(S.A32[i * L32 + j]) : 0.0;
   }
   __syncthreads();
 }
@@ -288,10 +335,11 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
   }
   if (st && st->done) return;
   const int L = kMaxM;  // leading dimension of the shared matrices
-  if (tid == 0) {
-    int m = 0;
-    for (int k = 0; k < M; ++k) {
-      bool a;
+  // active columns: thread k < M tests column k, two warp ballots compact them
+  if (tid < 64) {
+    const int k = tid;
+    bool a = false;
+    if (k < M) {
       if (active) {
         a = active[k] != 0;
       } else {
@@ -299,11 +347,21 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
         a = c < nev && (blk == 0 || (!st->conv[c] && (blk == 1 || st->pvalid)));
       }
       const double dg = gb[k * M + k];
-      if (a && isfinite(dg) && dg > 0.0) S.idx[m++] = k;
+      a = a && isfinite(dg) && dg > 0.0;
     }
-    S.m = m;
+    const unsigned bal = __ballot_sync(0xffffffffu, a);
+    if ((tid & 31) == 0) S.amask[tid >> 5] = bal;
+  }
+  if (tid == 0) {
     S.fail = 0;
     S.svqb = 0;
+  }
+  __syncthreads();
+  if (tid < 64) {
+    const unsigned m0 = S.amask[0], mine = tid < 32 ? m0 : S.amask[1];
+    const int lane = tid & 31;
+    if ((mine >> lane) & 1u) S.idx[(tid < 32 ? 0 : __popc(m0)) + __popc(mine & ((1u << lane) - 1u))] = tid;
+    if (tid == 0) S.m = __popc(m0) + __popc(S.amask[1]);
   }
   __syncthreads();
   const int m = S.m;
@@ -328,7 +386,7 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
   const double minpiv = chol_upper(S.B, L, m, S.scratch);
   int m2 = m;
   if (minpiv >= tau) {
-    tri_inv_upper(S.B, L, m, S.C, L);
+    tri_inv_upper(S.B, L, m, S.C, L, S.rinv);
   } else {
     // SVQB: eigendecomposition of the scaled G_B (copy in T)
     if (tid == 0) S.svqb = 1;

@@ -97,3 +97,32 @@ def test_convergence_test_uses_relative_theta_and_floor():
     assert res.resnorm[0] <= floor and abs(res.theta[0]) <= floor  # the null vector converges on the floor
     # every other column meets the relative test itself
     assert np.all(res.resnorm[1:] <= 1e-2 * np.abs(res.theta[1:]))
+
+
+def test_null_vector_rounding_grows_with_row_terms():
+    """The exact eigenvalue-zero vector of L_N, multiplied out in FP64, leaves a
+    residual that grows with the entries of the longest row (the hub of a
+    star): above 10 u rho already at 999 leaves, and inside the residual floor
+    10 u rho (d_max + 1) at every size."""
+    u = 2.0 ** -53
+    for nv in (1000, 20000):
+        g = W.star_graph(nv)                 # a hub joined to nv - 1 leaves
+        lmat = O.operator_for(g, O.NORMALIZED)
+        x = np.sqrt(O.weighted_degree(g))
+        x /= np.linalg.norm(x)
+        r = np.linalg.norm(lmat @ x)
+        assert O.max_row_terms(g) == nv
+        assert r > 10 * u * 2.0
+        assert r <= 10 * u * 2.0 * O.max_row_terms(g)
+
+
+def test_hub_graph_converges_and_floor_admits_only_theta_zero():
+    """On an R-MAT graph with hub rows the FP64 solve converges: the null vector
+    on the residual floor, every other column on its relative test."""
+    g = W.largest_component(W.rmat(12, seed=7))
+    assert O.max_row_terms(g) > 200
+    res = O.partition(g, 8, problem=O.NORMALIZED, precond="jacobi", tol=1e-3, seed=1)
+    assert res.status == "ok"
+    floor_th = 10 * 2.0 ** -53 * 2.0
+    assert abs(res.eigenvalues[0]) <= floor_th
+    assert np.all(res.resnorm[1:] <= 1e-3 * np.abs(res.eigenvalues[1:]))
