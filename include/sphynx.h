@@ -168,6 +168,11 @@ typedef struct {
                                 neighbours use the medium-row kernel (a lane per
                                 row), longer rows the long-row kernels (a warp per
                                 4096-entry piece); 32 means none are medium         */
+  int32_t sell_stride;       /* the autotuner's SELL-32 slice order: the four warps
+                                of a block take slices this many apart (1, 2, 4, 8
+                                or 16), so that on a mesh a block's rows can lie
+                                on neighbouring grid lines and share gathered rows
+                                of X in L1                                          */
 } sphynx_graph_info;
 
 /* Fill *opt with the defaults listed in sphynx_options. */
@@ -215,6 +220,14 @@ int sphynx_set_spmm_variant(sphynx_handle g, int32_t variant);
  * (reads row_ptr back from the device).  For tests and profiling.
  * Errors: INVALID_ARG. */
 int sphynx_set_spmm_med_max(sphynx_handle g, int32_t med_max);
+
+/* Override the autotuner's SELL-32 slice order: the four warps of a block take
+ * slices `stride` rows-of-32 apart (1, 2, 4, 8 or 16), or -1 to time every
+ * stride on a float 8-column product again and keep the fastest (what
+ * sphynx_create does when it picks SELL-32).  The order changes which block
+ * computes a row, never the row's value.  For tests and profiling.
+ * Errors: INVALID_ARG, OOM (-1 allocates two n x 8 float blocks while it runs). */
+int sphynx_set_spmm_sell_stride(sphynx_handle g, int32_t stride);
 
 /* Weighted degrees deg(v_i) (Sec. 3.2: the diagonal of L_C) into a device
  * double[n]. */

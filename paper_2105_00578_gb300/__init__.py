@@ -66,7 +66,7 @@ class GraphInfo(C.Structure):
                 ("total_vweight", C.c_int64), ("long_rows", C.c_int64), ("weighted", C.c_int32),
                 ("spmm_variant", C.c_int32), ("tuned_us_csr", C.c_float), ("tuned_us_sell", C.c_float),
                 ("sell_slices", C.c_int64), ("sell_narrow_slices", C.c_int64), ("spmm_graph_bytes", C.c_double),
-                ("regular", C.c_int32), ("spmm_med_max", C.c_int32)]
+                ("regular", C.c_int32), ("spmm_med_max", C.c_int32), ("sell_stride", C.c_int32)]
 
 
 def _load():
@@ -82,6 +82,7 @@ def _load():
         "sphynx_destroy": (None, [vp]),
         "sphynx_get_info": (C.c_int, [vp, C.POINTER(GraphInfo)]),
         "sphynx_set_spmm_variant": (C.c_int, [vp, i32]),
+        "sphynx_set_spmm_sell_stride": (C.c_int, [vp, i32]),
         "sphynx_degrees": (C.c_int, [vp, vp]),
         "sphynx_laplacian_apply": (C.c_int, [vp, i32, i32, vp, i32, vp, i32, i32]),
         "sphynx_precond_setup": (C.c_int, [vp, C.POINTER(Options), pd]),
@@ -206,6 +207,10 @@ def sphynx_get_info(h) -> dict:
 
 def sphynx_set_spmm_variant(h, variant: int) -> None:
     check(LIB.sphynx_set_spmm_variant(h, variant))
+
+
+def sphynx_set_spmm_sell_stride(h, stride: int) -> None:
+    check(LIB.sphynx_set_spmm_sell_stride(h, stride))
 
 
 def sphynx_set_spmm_med_max(h, med_max: int) -> None:

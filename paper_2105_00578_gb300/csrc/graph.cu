@@ -474,7 +474,8 @@ void build_sell(sphynx_graph *g) {
 // later product of the handle.
 // The autotuner: at create, times both short-row schedules and, on graphs with
 // rows longer than kShortDeg, the medium-row ceilings {kShortDeg, 128, kMedDeg}
-// on a float 8-column product, and keeps the fastest combination.
+// on a float 8-column product, and keeps the fastest combination; when that is
+// SELL-32, it then times the slice strides 1 .. 16 and keeps the fastest.
 void autotune_spmm(sphynx_graph *g, const int64_t *host_rowptr) {
   const int64_t n = g->n;
   const int ld = 8;
@@ -504,6 +505,7 @@ void autotune_spmm(sphynx_graph *g, const int64_t *host_rowptr) {
   float best = 1e30f;
   int best_ceiling = kMedDeg;
   SpmmTuning best_t{};
+  g->plan.sell_ls = 0;   // schedules and ceilings are compared in natural slice order
   for (int c : ceilings) {
     if (ceilings.size() > 1) build_plan(g, rp, c);
     const SpmmTuning t = spmm_tune(g, a);
@@ -518,6 +520,8 @@ void autotune_spmm(sphynx_graph *g, const int64_t *host_rowptr) {
   g->plan.tuned_variant = best_t.variant;
   g->plan.tuned_us[kCsrStaged] = best_t.us[kCsrStaged];
   g->plan.tuned_us[kSell32] = best_t.us[kSell32];
+  for (float &u : g->plan.tuned_ls_us) u = 0.f;
+  if (best_t.variant == kSell32) spmm_tune_sell_stride(g, a);
   SPX_CUDA(cudaStreamSynchronize(g->stream));
 }
 
@@ -723,6 +727,7 @@ int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info) {
     info->tuned_us_sell = g->plan.tuned_us[kSell32];
     info->regular = g->max_degree * g->n <= 10 * g->nnz ? 1 : 0;
     info->spmm_med_max = g->plan.med_max;
+    info->sell_stride = 1 << g->plan.sell_ls;
     info->sell_slices = (g->n + 31) / 32;
     info->sell_narrow_slices = g->plan.sell_narrow;
     info->spmm_graph_bytes = (g->plan.tuned_variant == kSell32
@@ -774,6 +779,33 @@ int sphynx_set_spmm_variant(sphynx_handle g, int32_t variant) {
     } else {
       fail(SPHYNX_ERR_INVALID_ARG, "variant %d", variant);
     }
+    return SPHYNX_OK;
+  });
+}
+
+int sphynx_set_spmm_sell_stride(sphynx_handle g, int32_t stride) {
+  return guarded([&]() -> int {
+    if (!g) fail(SPHYNX_ERR_INVALID_ARG, "NULL handle");
+    if (stride == -1) {
+      SpmmArgs a{};
+      DevBuf x, y;
+      const size_t bytes = static_cast<size_t>(g->n) * 8 * sizeof(float);
+      x.alloc(bytes);
+      y.alloc(bytes);
+      SPX_CUDA(cudaMemsetAsync(x.p, 0, bytes, g->stream));
+      a.lap = SPHYNX_COMBINATORIAL;
+      a.tin = DT::F32;
+      a.ld_x = a.ld_y = a.bp = a.b_true = 8;
+      a.x = x.p;
+      a.y = y.p;
+      spmm_tune_sell_stride(g, a);
+      SPX_CUDA(cudaStreamSynchronize(g->stream));
+      return SPHYNX_OK;
+    }
+    int ls = 0;
+    while (ls < kSellLsCount && (1 << ls) != stride) ++ls;
+    if (ls == kSellLsCount) fail(SPHYNX_ERR_INVALID_ARG, "SELL slice stride %d", stride);
+    g->plan.sell_ls = ls;
     return SPHYNX_OK;
   });
 }

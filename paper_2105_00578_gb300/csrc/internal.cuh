@@ -97,6 +97,8 @@ enum SpmmVariant : int {
   kSell32 = 1,      // SELL-32: columns stored slice-major, read straight from global memory
 };
 
+constexpr int kSellLsCount = 5;      // slice strides 1, 2, 4, 8, 16 the autotuner times
+
 struct SpmmTuning {
   int variant;
   float us[2];                       // measured time of each schedule
@@ -107,6 +109,8 @@ struct SpmmPlan {
   int forced = -1;                   // >= 0: every product uses this schedule
   int tuned_variant = kCsrStaged;    // the autotuner's choice for this graph
   float tuned_us[2] = {0.f, 0.f};    // its timings of both schedules
+  int sell_ls = 0;                   // SELL blocks: warps take slices 2^sell_ls apart
+  float tuned_ls_us[kSellLsCount] = {};   // the autotuner's time for each sell_ls
   DevBuf tune_scratch;
   int64_t n_long = 0;                // long rows: degree > kMedDeg
   int64_t n_items = 0;               // long-row work items
@@ -252,6 +256,8 @@ struct SpmmArgs {
 void spmm(sphynx_graph *g, const SpmmArgs &a);
 // both short-row schedules timed on this product (scratch outputs)
 SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a);
+// every SELL slice stride timed on this product; sets plan.sell_ls to the fastest
+void spmm_tune_sell_stride(sphynx_graph *g, const SpmmArgs &a);
 
 // ---- dense.cu ---------------------------------------------------------------
 void launch_random_block(cudaStream_t s, DT dt, void *x, int64_t n, int b, int ld, uint64_t seed);

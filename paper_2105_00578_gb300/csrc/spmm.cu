@@ -15,27 +15,32 @@ void dispatch(sphynx_graph *g, const SpmmArgs &a, const SpmmDev &d) {
   }
 }
 
-}  // namespace
-
-// Time both short-row schedules for this product with the caller's input
-// and scratch outputs (a polynomial step's accumulator is read and written,
-// so the real one must not be touched), alternating them over five rounds,
-// and return the faster.
-SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a) {
+// The caller's product redirected to scratch outputs (a polynomial step's
+// accumulator is read and written, so the real one must not be touched).
+SpmmDev tune_args(sphynx_graph *g, const SpmmArgs &a) {
   const size_t out_bytes = static_cast<size_t>(g->n) * a.ld_y * 8 + 256;
   const size_t t_bytes = static_cast<size_t>(g->n) * a.ld_x * 8 + 256;
   if (g->plan.tune_scratch.bytes < out_bytes + t_bytes) g->plan.tune_scratch.alloc(out_bytes + t_bytes);
   char *base = g->plan.tune_scratch.as<char>();
   SPX_CUDA(cudaMemsetAsync(base, 0, out_bytes + t_bytes, g->stream));
   SpmmArgs s = a;
-  s.done = nullptr;
   if (a.mode == 0) {
     s.y = base;
   } else {
     s.yacc = base;
     s.t_out = base + out_bytes;
   }
-  SpmmDev d{s.x, s.ld_x, s.ld_y, s.y, s.t_out, s.yacc, s.first, s.yterms, s.inv, s.invf, s.i_cur, nullptr};
+  return SpmmDev{s.x, s.ld_x, s.ld_y, s.y, s.t_out, s.yacc, s.first, s.yterms, s.inv, s.invf, s.i_cur, nullptr};
+}
+
+}  // namespace
+
+// Time both short-row schedules for this product with the caller's input
+// and scratch outputs, alternating them over five rounds, and return the
+// faster.
+SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a) {
+  const SpmmArgs &s = a;
+  const SpmmDev d = tune_args(g, a);
   cudaEvent_t e0, e1;
   SPX_CUDA(cudaEventCreate(&e0));
   SPX_CUDA(cudaEventCreate(&e1));
@@ -64,6 +69,48 @@ SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a) {
   cudaEventDestroy(e1);
   t.variant = t.us[kSell32] < t.us[kCsrStaged] ? kSell32 : kCsrStaged;
   return t;
+}
+
+// Time the SELL schedule under every slice stride 2^ls (ls < kSellLsCount),
+// rotating the order over five rounds, and keep the fastest in plan.sell_ls.
+// Strides change only which block runs a slice, never a product's value.
+void spmm_tune_sell_stride(sphynx_graph *g, const SpmmArgs &a) {
+  const SpmmDev d = tune_args(g, a);
+  cudaEvent_t e0, e1;
+  SPX_CUDA(cudaEventCreate(&e0));
+  SPX_CUDA(cudaEventCreate(&e1));
+  const int64_t launches = g->ctr.launches;
+  const int variant = g->plan.variant;
+  g->plan.variant = kSell32;
+  float us[kSellLsCount];
+  for (int k = 0; k < kSellLsCount; ++k) {   // warm-up of each
+    us[k] = 1e30f;
+    g->plan.sell_ls = k;
+    dispatch(g, a, d);
+  }
+  for (int round = 0; round < 5; ++round) {
+    for (int k = 0; k < kSellLsCount; ++k) {
+      const int ls = (round + k) % kSellLsCount;
+      g->plan.sell_ls = ls;
+      SPX_CUDA(cudaEventRecord(e0, g->stream));
+      dispatch(g, a, d);
+      SPX_CUDA(cudaEventRecord(e1, g->stream));
+      SPX_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      SPX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      us[ls] = ms * 1000.f < us[ls] ? ms * 1000.f : us[ls];
+    }
+  }
+  g->ctr.launches = launches;
+  g->plan.variant = variant;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int best = 0;
+  for (int k = 0; k < kSellLsCount; ++k) {
+    g->plan.tuned_ls_us[k] = us[k];
+    if (us[k] < us[best]) best = k;
+  }
+  g->plan.sell_ls = best;
 }
 
 void spmm(sphynx_graph *g, const SpmmArgs &a) {

@@ -502,8 +502,46 @@ __device__ __forceinline__ void spmm_accumulate(const LapView &L, const TI *__re
   }
 }
 
-// One row's d entries in batches: U column indices, then U gathers in flight
-// together, then U accumulations.  col_at(t) / w_at(t) read entry t < d.
+// N consecutive entries t0 .. t0 + N - 1 of a row: N column indices, then N
+// gathers in flight together, then N accumulations in entry order.
+template <int N, int LAP, typename TI, int BP, bool W, class ColAt, class WAt>
+__device__ __forceinline__ void spmm_batch(const LapView &L, const TI *__restrict__ x, int t0, ColAt col_at,
+                                           WAt w_at, RowAcc<TI, BP> &acc) {
+  using TA = typename AccOf<TI>::T;
+  int jj[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) jj[u] = col_at(t0 + u);
+  RawRow<TI, BP> rr[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) rr[u].load(x + static_cast<int64_t>(jj[u]) * BP);
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    if constexpr (LAP == SPHYNX_NORMALIZED || W) {
+      TA coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
+      if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
+      acc.template accum<true>(rr[u], coef);
+    } else {
+      acc.template accum<false>(rr[u], TA(1));
+    }
+  }
+}
+
+// The last rem <= R entries of a row as one batch of exactly rem (selected
+// among 1 .. R at run time), so that no gather slot is padded with zeros.
+template <int R, int LAP, typename TI, int BP, bool W, class ColAt, class WAt>
+__device__ __forceinline__ void spmm_tail(const LapView &L, const TI *__restrict__ x, int t0, int rem,
+                                          ColAt col_at, WAt w_at, RowAcc<TI, BP> &acc) {
+  if constexpr (R > 0) {
+    if (rem == R) {
+      spmm_batch<R, LAP, TI, BP, W>(L, x, t0, col_at, w_at, acc);
+      return;
+    }
+    spmm_tail<R - 1, LAP, TI, BP, W>(L, x, t0, rem, col_at, w_at, acc);
+  }
+}
+
+// One row's d entries in batches of U (see spmm_batch); col_at(t) / w_at(t)
+// read entry t < d.
 template <int LAP, typename TI, int BP, bool W, class ColAt, class WAt>
 __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict__ x, int d,
                                          ColAt col_at, WAt w_at, RowAcc<TI, BP> &acc) {
@@ -513,48 +551,14 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
     // narrow rows (16 bytes or less): plain batches keep the register count,
     // hence the number of resident warps, high
     int t0 = 0;
-    for (; t0 + U <= d; t0 += U) {
-      int jj[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) jj[u] = col_at(t0 + u);
-      RawRow<TI, BP> rr[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) rr[u].load(x + static_cast<int64_t>(jj[u]) * BP);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if constexpr (LAP == SPHYNX_NORMALIZED || W) {
-          TA coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
-          if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
-          acc.template accum<true>(rr[u], coef);
-        } else {
-          acc.template accum<false>(rr[u], TA(1));
-        }
-      }
+    for (; t0 + U <= d; t0 += U) spmm_batch<U, LAP, TI, BP, W>(L, x, t0, col_at, w_at, acc);
+    // the remainder (< U entries): a batch of 4 if at least 4 are left, then
+    // one batch of exactly what is left
+    if (d - t0 >= 4) {
+      spmm_batch<4, LAP, TI, BP, W>(L, x, t0, col_at, w_at, acc);
+      t0 += 4;
     }
-    if (t0 < d) {
-      int jj[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) jj[u] = t0 + u < d ? col_at(t0 + u) : -1;
-      RawRow<TI, BP> rr[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (jj[u] >= 0) rr[u].load(x + static_cast<int64_t>(jj[u]) * BP);
-        else rr[u].zero();
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if constexpr (LAP == SPHYNX_NORMALIZED || W) {
-          TA coef = TA(0);
-          if (jj[u] >= 0) {
-            coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
-            if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
-          }
-          acc.template accum<true>(rr[u], coef);
-        } else {
-          acc.template accum<false>(rr[u], TA(1));
-        }
-      }
-    }
+    spmm_tail<3, LAP, TI, BP, W>(L, x, t0, d - t0, col_at, w_at, acc);
     return;
   }
   // wide rows: software pipeline -- the next batch's column indices (and
@@ -667,6 +671,11 @@ k_spmm_short(const LapView L, const SpmmDev a) {
 // 128 bytes of 32-bit indices), so column reads are coalesced without shared
 // memory and all of L1 is left to the X gathers.  The slice's format is
 // uniform over the warp.
+// Slice order: the four warps of a block take slices 2^ls apart, and 2^ls
+// consecutive blocks cover a group of 4 * 2^ls slices.  On a mesh whose grid
+// lines are 32 * 2^ls rows long, a block's 128 rows then lie on four
+// neighbouring lines instead of one, so the X rows its gathers touch overlap
+// far more and L1 serves more of them.  The autotuner picks ls per graph.
 // Resident 128-thread blocks the gather-latency-bound SELL kernel asks for:
 // 16 (32 registers a thread, every warp slot of the SM) for rows of at most
 // 16 bytes, 8 (64 registers) for 32-byte float rows.
@@ -681,11 +690,13 @@ template <typename TI, int BP> struct SellOccupancy {
 template <int LAP, typename TI, typename TT, int BP, bool W, int MODE, bool NARROW>
 __global__ void __launch_bounds__(128, SellOccupancy<TI, BP>::blocks)
 k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, const float *__restrict__ sw,
-            const int64_t *__restrict__ sptr, const int64_t *__restrict__ cptr, const uint8_t *__restrict__ sdeg) {
+            const int64_t *__restrict__ sptr, const int64_t *__restrict__ cptr, const uint8_t *__restrict__ sdeg,
+            int ls) {
   using TA = typename AccOf<TI>::T;
   if (a.done && *a.done) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t slice = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t blk = blockIdx.x;
+  const int64_t slice = ((blk >> ls) << (ls + 2)) + (blk & ((1 << ls) - 1)) + (static_cast<int64_t>(wid) << ls);
   if (slice * 32 >= L.n) return;  // uniform per warp
   const int64_t row = slice * 32 + lane;
   const bool valid = row < L.n;
@@ -813,14 +824,17 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
   const int64_t grid = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
   if (grid > 0) {
     if (g->plan.variant == kSell32) {
+      // whole groups of 4 * 2^ls slices, 2^ls blocks each
+      const int ls = g->plan.sell_ls;
+      const int64_t sgrid = ((warps + (int64_t{4} << ls) - 1) >> (ls + 2)) << ls;
       if (g->plan.sell_narrow == (g->n + 31) / 32)
-        k_spmm_sell<LAP, TI, TT, BP, W, MODE, true><<<static_cast<unsigned>(grid), 128, 0, st>>>(
+        k_spmm_sell<LAP, TI, TT, BP, W, MODE, true><<<static_cast<unsigned>(sgrid), 128, 0, st>>>(
             L, a, g->plan.sell_col.as<int16_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
-            g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>());
+            g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>(), ls);
       else
-        k_spmm_sell<LAP, TI, TT, BP, W, MODE, false><<<static_cast<unsigned>(grid), 128, 0, st>>>(
+        k_spmm_sell<LAP, TI, TT, BP, W, MODE, false><<<static_cast<unsigned>(sgrid), 128, 0, st>>>(
             L, a, g->plan.sell_col.as<int16_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
-            g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>());
+            g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>(), ls);
     } else {
       k_spmm_short<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 32 * kWarpsPerCta, 0, st>>>(L, a);
     }

@@ -56,13 +56,21 @@ def test_spmm_matches_oracle(gname, lap, dtype, ncols):
         ceilings = (32, 128, 4096) if int(g.degrees().max()) > 32 else (4096,)
         for med_max in ceilings:
             spx.sphynx_set_spmm_med_max(h, med_max)
-            for variant in (0, 1):                 # CSR staged, SELL-32
+            # CSR staged; SELL-32 under every slice stride (slices a block's
+            # warps take apart), which must not change any row's value
+            for variant, stride in ((0, 1), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16)):
                 spx.sphynx_set_spmm_variant(h, variant)
+                spx.sphynx_set_spmm_sell_stride(h, stride)
                 y.zero_()
                 spx.sphynx_laplacian_apply(h, lap, dt, xd, ld, y, ld, ncols)
                 torch.cuda.synchronize()
                 got = y.cpu().numpy().astype(np.float64)[:, :ncols]
-                assert rel_err(got, ref) < tol, (variant, med_max)
+                assert rel_err(got, ref) < tol, (variant, stride, med_max)
+                if variant == 1 and stride == 1:
+                    first = got
+                elif variant == 1:
+                    # the same sums in the same order, whichever block runs them
+                    assert np.array_equal(got, first), stride
             # padding columns stay zero when the input padding is zero
             if ld > ncols and ncols > 1:
                 assert np.all(y.cpu().numpy()[:, ncols:] == 0)
@@ -89,6 +97,9 @@ def test_degrees_exact():
         assert info["spmm_variant"] in (0, 1) and info["tuned_us_csr"] > 0 and info["tuned_us_sell"] > 0
         # the tuner kept the faster schedule
         assert (info["tuned_us_sell"] < info["tuned_us_csr"]) == (info["spmm_variant"] == 1)
+        assert info["sell_stride"] in (1, 2, 4, 8, 16)
+        if info["spmm_variant"] == 0:
+            assert info["sell_stride"] == 1
         spx.sphynx_destroy(h)
 
 
@@ -195,8 +206,10 @@ def test_full_size_27_point_mesh_sampled_rows():
     h = spx.sphynx_create(g.row_ptr, g.col, None, None)
     try:
         rng = np.random.default_rng(5)
-        for dtype, ld, variant in (("f32", 8, 0), ("f32", 8, 1), ("f64", 8, 1), ("bf16", 8, 1), ("bf16", 8, 0)):
+        for dtype, ld, variant, stride in (("f32", 8, 0, 1), ("f32", 8, 1, 1), ("f32", 8, 1, 4), ("f64", 8, 1, 4),
+                                           ("bf16", 8, 1, 4), ("bf16", 8, 1, 16), ("bf16", 8, 0, 1)):
             spx.sphynx_set_spmm_variant(h, variant)
+            spx.sphynx_set_spmm_sell_stride(h, stride)
             x = rng.standard_normal((g.n, 7))
             xd = dev_block(x, ld, dtype)
             y = torch.zeros((g.n, ld), dtype=torch.float64 if dtype == "f64" else torch.float32, device="cuda")
@@ -237,4 +250,8 @@ def test_invalid_inputs_are_rejected():
     with pytest.raises(spx.SphynxError) as e:
         spx.sphynx_partition(h, 2, spx.options(laplacian="normalized"), parts)
     assert e.value.code == spx.ERR_ISOLATED
+    for stride in (0, 3, 32):                          # slice strides are 1, 2, 4, 8, 16 (or -1: tune)
+        with pytest.raises(spx.SphynxError) as e:
+            spx.sphynx_set_spmm_sell_stride(h, stride)
+        assert e.value.code == spx.ERR_INVALID_ARG
     spx.sphynx_destroy(h)
