@@ -356,8 +356,15 @@ def run_ours(args, world, rank, local):
     g = make_graph(args.workload)
     stream = torch.cuda.current_stream()
     graph = spx.Graph(g, stream=stream)
-    if args.spmm_variant is not None:
-        spx.sphynx_set_spmm_variant(graph.h, {"csr": 0, "sell": 1}[args.spmm_variant])
+
+    def pin(h):
+        # profiler captures pin the schedule: under a profiler the tuner's timings are distorted
+        if args.spmm_variant is not None:
+            spx.sphynx_set_spmm_variant(h, {"csr": 0, "sell": 1}[args.spmm_variant])
+        if args.sell_stride is not None:
+            spx.sphynx_set_spmm_sell_stride(h, args.sell_stride)
+
+    pin(graph.h)
     n = g.n
     part = torch.empty(n, dtype=torch.int32, device="cuda")
 
@@ -454,6 +461,7 @@ def run_ours(args, world, rank, local):
     for _ in range(e2e_steps):
         h = spx.sphynx_create(rp.data_ptr(), cl.data_ptr(), None if wp is None else wp.data_ptr(), None, n, g.nnz,
                               spx.HOST_PTRS, stream)
+        pin(h)
         spx.sphynx_partition(h, w["K"], o_host, hp.data_ptr())
         spx.sphynx_destroy(h)
     torch.cuda.synchronize()
@@ -479,7 +487,7 @@ def run_ours(args, world, rank, local):
             "max_resnorm_over_tol_theta": _res_ratio(last[3], w["tol"]),
             "spmm": {"gbs": achieved_all, "launches_per_step": spmm_launches / args.steps,
                      "ms_per_step": spmm_ms / args.steps, "by_input_precision": by_dt,
-                     "schedule": schedule},
+                     "schedule": schedule, "sell_stride": info["sell_stride"] if schedule == "k_spmm_sell" else None},
             "fp64": fp64,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
@@ -519,6 +527,8 @@ def main():
     ap.add_argument("--spmm-variant", default=None, choices=[None, "csr", "sell"],
                     help="pin the short-row SpMM schedule instead of the one tuned at create "
                          "(used for profiler captures, where tuning times are distorted)")
+    ap.add_argument("--sell-stride", type=int, default=None, choices=[1, 2, 4, 8, 16],
+                    help="pin the SELL-32 slice stride instead of the one tuned at create (profiler captures)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":

@@ -705,6 +705,19 @@ k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, 
   const int64_t cbase = __ldg(cptr + slice);
   const float *wp = W ? sw + __ldg(sptr + slice) + lane : nullptr;
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
+  {
+    // One bulk L2 prefetch of the slice's whole index block (dmax segments of
+    // 64 or 128 bytes, contiguous, 64-byte aligned).  Without it every batch
+    // of the row loop waits on DRAM for its segments before it can gather;
+    // with it only the first batch does (9 % off the mesh's chain step).
+    const int dmax = __reduce_max_sync(kFull, d);
+    if (dmax > 0 && lane == 0) {
+      const bool nar = NARROW || cbase < 0;
+      const void *blk = nar ? static_cast<const void *>(scol + (~cbase)) : static_cast<const void *>(scol + cbase);
+      const unsigned bytes = static_cast<unsigned>(dmax) * (nar ? 64u : 128u);
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(blk), "r"(bytes) : "memory");
+    }
+  }
   RowAcc<TI, BP> acc;
   acc.zero();
   if (NARROW || cbase < 0) {
