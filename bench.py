@@ -194,6 +194,27 @@ def oracle_sample(name: str, steps: int = 1):
     return 1.0 / est, sample, t0 + t1
 
 
+def vs_oracle(w, st, cut, precision):
+    """Eigenvalue, residual and cut of one GPU partition against the FP64
+    oracle's full run of the same workload and seed (tests/golden, written by
+    oracle code only).  The eigenvalue-zero vector is compared absolutely, the
+    others relatively; the tolerances are those the parity tests use."""
+    if not w.get("golden"):
+        return None
+    p = os.path.join(ROOT, "tests", "golden", w["golden"])
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    ev, ev_o = st["eigenvalues"], d["eigenvalues"]
+    rel = [abs(a - b) / abs(b) for a, b in zip(ev[1:], ev_o[1:])]
+    return {"source": f"tests/golden/{w['golden']}", "oracle_iterations": d["iterations"],
+            "eigenvalue_max_rel_err": max(rel) if rel else None, "eigenvalue_rel_tol": 1e-6 if precision == "fp64" else 1e-3,
+            "null_eigenvalue_abs": abs(ev[0]),
+            "max_resnorm_over_tol_theta": _res_ratio(st, w["tol"]),
+            "oracle_cut": d["cut"], "cut_rel_err": abs(cut - d["cut"]) / d["cut"], "cut_rel_tol": 0.02}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -444,6 +465,7 @@ def run_ours(args, world, rank, local):
         s64 = fst[-1][3]
         fp64 = {"ms_per_partition": fms, "partitions_per_s": 1000.0 / fms, "iterations": s64["iterations"],
                 "max_resnorm_over_tol_theta": _res_ratio(s64, w["tol"]), "cut": fst[-1][1],
+                "vs_oracle": vs_oracle(w, s64, fst[-1][1], "fp64"),
                 "status": fst[-1][0], "speedup_of_mixed": fms / ms}
 
     # end to end through the C ABI with host buffers: create (H2D of the CSR
@@ -485,6 +507,7 @@ def run_ours(args, world, rank, local):
             "iterations": last[3]["iterations"], "status": last[0], "cut": last[1], "imbalance": last[2],
             "eigenvalues": last[3]["eigenvalues"],
             "max_resnorm_over_tol_theta": _res_ratio(last[3], w["tol"]),
+            "vs_oracle": vs_oracle(w, last[3], last[1], precision),
             "spmm": {"gbs": achieved_all, "launches_per_step": spmm_launches / args.steps,
                      "ms_per_step": spmm_ms / args.steps, "by_input_precision": by_dt,
                      "schedule": schedule, "sell_stride": info["sell_stride"] if schedule == "k_spmm_sell" else None},
