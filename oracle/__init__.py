@@ -13,6 +13,8 @@ Modules and the parts of the paper they follow:
   (SplitMix64, counter based; the paper leaves the distribution open).
 * ``precond``    Jacobi (Sec. 5.1) and the GMRES polynomial preconditioner
   (Sec. 5.2): Lanczos, harmonic Ritz values, Leja order, product form.
+* ``amg``        the aggregation multigrid preconditioner of Sec. 5.3 with the
+  parameters of Sec. 6.2.2 (Chebyshev smoothing, plain aggregation).
 * ``lobpcg``     Algorithm 1 (LOBPCG with Rayleigh-Ritz and soft locking),
   generalized to a diagonal B.
 * ``mj``         the multi-jagged multisection of Sec. 4 with an exact,
@@ -33,6 +35,8 @@ from .laplacian import (  # noqa: F401
 from .rng import splitmix64_block, poly_start_vector, reference_block  # noqa: F401
 from .precond import jacobi_diag, gmres_poly_roots, poly_apply, leja_order  # noqa: F401
 from .lobpcg import lobpcg, rayleigh_ritz, LobpcgResult  # noqa: F401
+from .amg import (aggregate, mis2_roots, coarse_graph, build_hierarchy, vcycle, chebyshev,  # noqa: F401
+                  power_lambda_max, vertex_keys)
 from .mj import multijagged, coord_sort_key  # noqa: F401
 from .metrics import cutsize, imbalance, part_weights  # noqa: F401
 from .sphynx import (partition, num_eigenvectors, initial_block, canonical_rotation, eigen_clusters,  # noqa: F401

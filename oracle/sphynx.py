@@ -30,6 +30,7 @@ from .lobpcg import lobpcg, U_FP64
 from .mj import multijagged
 from .metrics import cutsize, imbalance
 from .precond import jacobi_diag, gmres_poly_roots, poly_apply
+from .amg import build_hierarchy, vcycle
 from .rng import reference_block, splitmix64_block
 
 
@@ -43,11 +44,12 @@ def is_regular(g) -> bool:
 def default_options(g, precond: str) -> dict:
     """Sphynx's defaults (Sec. 6.3.1, Fig. 2; initial vectors Sec. 6.2.1):
     regular graphs use the combinatorial problem with tol 1e-3 (Jacobi and
-    polynomial preconditioners) and random initial vectors; irregular graphs
-    use the generalized problem (Jacobi) or the normalized problem
-    (polynomial), tol 1e-2 and piecewise-constant initial vectors."""
+    polynomial preconditioners; 1e-2 with multigrid) and random initial
+    vectors; irregular graphs use the generalized problem (Jacobi, multigrid)
+    or the normalized problem (polynomial), tol 1e-2 and piecewise-constant
+    initial vectors."""
     if is_regular(g):
-        return dict(problem=COMBINATORIAL, tol=1e-3, init="random", precond=precond)
+        return dict(problem=COMBINATORIAL, tol=1e-2 if precond == "amg" else 1e-3, init="random", precond=precond)
     return dict(problem=NORMALIZED if precond == "poly" else GENERALIZED, tol=1e-2, init="piecewise",
                 precond=precond)
 
@@ -168,6 +170,13 @@ def partition(g, num_parts: int, problem: str = COMBINATORIAL, precond: str = "j
 
         def apply_m(r):
             return poly_apply(apply_l, roots, r)
+    elif precond == "amg":
+        if problem == NORMALIZED:
+            raise ValueError("the multigrid preconditioner approximates L_C^{-1}: combinatorial or generalized only")
+        levels = build_hierarchy(g, seed)
+
+        def apply_m(r):
+            return vcycle(levels, r)
     elif precond == "none":
         apply_m = None
     else:

@@ -170,6 +170,10 @@ def test_graph_type_and_defaults_follow_the_decision_flow():
     assert O.default_options(star, "jacobi") == dict(problem="generalized", tol=1e-2, init="piecewise",
                                                      precond="jacobi")
     assert O.default_options(star, "poly")["problem"] == "normalized"
+    # multigrid (MueLu): tol 1e-2 on regular graphs too, the generalized problem on irregular ones
+    assert O.default_options(mesh, "amg") == dict(problem="combinatorial", tol=1e-2, init="random", precond="amg")
+    assert O.default_options(star, "amg") == dict(problem="generalized", tol=1e-2, init="piecewise",
+                                                  precond="amg")
     # the boundary: max degree exactly 10 x average is still regular
     # (star of 11 vertices: max 10, average 20 / 11; ratio 5.5 -> regular)
     assert O.is_regular(W.star_graph(11))
