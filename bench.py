@@ -49,6 +49,11 @@ WORKLOADS = {
                     "with FP64 Rayleigh-Ritz, tol 1e-3; all LOBPCG iterations in one captured graph launch",
                K=8, laplacian="combinatorial", precond="jacobi", poly_degree=25, tol=1e-3, seed=4,
                precision="fp32", golden=None, batch=2000, stall_window=50),
+    "amg": dict(desc="3D 27-point mesh 128^3 (2,097,152 vertices), combinatorial Laplacian, aggregation multigrid "
+                     "preconditioner (plain aggregation, degree-3 Chebyshev, ratio 7, <= 5 levels), K=64 (d=7), "
+                     "LOBPCG tol 1e-2 (Sphynx's default for regular graphs with multigrid), FP32 blocks",
+                K=64, laplacian="combinatorial", precond="amg", poly_degree=25, tol=1e-2, seed=2,
+                precision="fp32", golden=None),
     "c5": dict(desc="R-MAT scale 24 (edge factor 16, a=.57 b=.19 c=.19), largest component, FP32 edge weights "
                     "uniform in [0.5, 1.5); normalized Laplacian, polynomial preconditioner degree 10, K=1024 "
                     "(d=11), BF16 polynomial chain, tol 1e-2",
@@ -59,7 +64,7 @@ WORKLOADS = {
 
 def make_graph(name: str):
     import workloads
-    if name == "c2":
+    if name in ("c2", "amg"):
         return workloads.grid3d(128, 128, 128, 27)
     if name == "c1":
         return workloads.grid2d(64, 64)

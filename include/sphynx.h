@@ -64,11 +64,19 @@ extern "C" {
 #define SPHYNX_COMBINATORIAL 0
 #define SPHYNX_GENERALIZED 1
 #define SPHYNX_NORMALIZED 2
-/* Preconditioner (Sec. 5): none, Jacobi M = diag(L)^-1 (Sec. 5.1), or the
- * GMRES polynomial p_k(L) (Sec. 5.2). */
+/* Preconditioner (Sec. 5): none, Jacobi M = diag(L)^-1 (Sec. 5.1), the
+ * GMRES polynomial p_k(L) (Sec. 5.2), or aggregation multigrid (Sec. 5.3,
+ * parameters of Sec. 6.2.2): one symmetric V-cycle on L_C per application,
+ * plain aggregation, degree-3 Chebyshev smoothing (eigenvalue ratio 7,
+ * lambda_max from 10 power-iteration steps, 100 on the coarsest level), at
+ * most 5 levels, and a Chebyshev coarse solve.  The multigrid preconditioner
+ * approximates L_C^{-1}, so it takes the combinatorial and generalized
+ * problems (INVALID_ARG with the normalized one) and single graphs
+ * (UNSUPPORTED in sphynx_partition_batch). */
 #define SPHYNX_PRECOND_NONE 0
 #define SPHYNX_PRECOND_JACOBI 1
 #define SPHYNX_PRECOND_POLY 2
+#define SPHYNX_PRECOND_AMG 3
 /* Arithmetic.  FP64: every block and product in double.  FP32: blocks in
  * float with float products; Gram matrices accumulated to double, the
  * Cholesky / Rayleigh-Ritz small problems and the residual norms in double.
@@ -244,7 +252,11 @@ int sphynx_laplacian_apply(sphynx_handle g, int32_t laplacian, int32_t dtype, co
 /* Set up the preconditioner of `opt` (Sec. 5) and, for the polynomial,
  * return its roots theta_1..theta_k in application order (harmonic Ritz
  * values of k Lanczos steps, Leja ordered) in host double[poly_degree]
- * (may be NULL).  Jacobi and none need no setup. */
+ * (may be NULL).  For multigrid, build the level hierarchy for opt->seed
+ * (kept by the handle and reused while the seed is the same); errors:
+ * UNSUPPORTED when an aggregate's rows hold more than 8192 entries (graphs
+ * with hubs of that size take Jacobi or the polynomial).  Jacobi and none
+ * need no setup. */
 int sphynx_precond_setup(sphynx_handle g, const sphynx_options *opt, double *roots_out);
 
 /* H = M R for the preconditioner set up by the last sphynx_precond_setup
@@ -252,6 +264,27 @@ int sphynx_precond_setup(sphynx_handle g, const sphynx_options *opt, double *roo
  * MIXED_BF16 precision) or double (FP64); ncols <= 16. */
 int sphynx_precond_apply(sphynx_handle g, const sphynx_options *opt, const void *r, void *h,
                          int32_t ld, int32_t ncols);
+
+/* One level of the multigrid hierarchy built by sphynx_precond_setup (or by
+ * a partition with SPHYNX_PRECOND_AMG): level 0 is the graph itself, level
+ * l + 1 the aggregate graph of level l, whose edge (I, J) weighs the sum of
+ * the weights of level l's edges between aggregates I and J, so that its
+ * combinatorial Laplacian is the Galerkin product P^T L_C P (Sec. 5.3).
+ * info (host, may be NULL) receives the level count, the level's size, its
+ * aggregate count (0 on the coarsest level) and its Chebyshev lambda_max.
+ * The device outputs may be NULL: agg_out int32[n] (the aggregate of each
+ * vertex; INVALID_ARG on the coarsest level), row_ptr_out int64[n + 1],
+ * col_out int32[nnz] (sorted within each row), w_out float[nnz] (levels >= 1).
+ * Errors: INVALID_ARG (no hierarchy, level out of range). */
+typedef struct {
+  int32_t levels;      /* levels in the hierarchy                        */
+  int32_t reserved;
+  int64_t n, nnz;      /* this level's vertices and stored entries       */
+  int64_t n_next;      /* aggregates (vertices of the next level), 0 on the coarsest */
+  double lambda_max;   /* Chebyshev interval top: min(1.1 x power estimate, 2) */
+} sphynx_amg_level_info;
+int sphynx_amg_level(sphynx_handle g, int32_t level, sphynx_amg_level_info *info, int32_t *agg_out,
+                     int64_t *row_ptr_out, int32_t *col_out, float *w_out);
 
 /* Gram matrices of Rayleigh-Ritz (Sec. 3.3, the Rayleigh-Ritz step of Algorithm 1):
  * G_A = S^T (L S) and G_B = S^T B S, where S = [S_0 | S_1 | S_2] and

@@ -36,7 +36,9 @@ readings (the GPU library implements the same ones independently):
   i + 1.  The interval is [lambda_max / 7, lambda_max].
 * Cycle.  Symmetric V-cycle: pre-smooth from zero, restrict the residual
   with P^T, recurse, prolong with P, post-smooth with the same polynomial;
-  the coarsest level applies its Chebyshev polynomial once from zero.
+  the coarsest level applies its Chebyshev polynomial once from zero.  A
+  level without edges (one aggregate holding a whole graph) has
+  lambda_max = 0, and its smoother leaves x unchanged.
 
 Pins (tests/test_oracle_amg.py): the distance-2 independence and maximality of
 the roots by breadth-first search; every vertex in one connected aggregate;
@@ -152,7 +154,10 @@ def power_lambda_max(g, iters: int, seed: int, level: int) -> float:
     with np.errstate(over="ignore"):
         v = (_mix64_np(np.uint64(state) + ctr * np.uint64(GAMMA)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
     v = 2.0 * v - 1.0
-    v /= np.sqrt(np.sum(deg * v * v))
+    nrm = np.sqrt(np.sum(deg * v * v))
+    if nrm == 0:
+        return 0.0                              # a level without edges
+    v /= nrm
     lam = 0.0
     for _ in range(iters):
         y = lmat @ v
@@ -166,7 +171,10 @@ def power_lambda_max(g, iters: int, seed: int, level: int) -> float:
 
 
 def chebyshev(lmat, dinv: np.ndarray, lam_max: float, b: np.ndarray, x=None, degree: int = CHEB_DEGREE):
-    """Chebyshev acceleration of D^{-1} A x = D^{-1} b on [lam_max/ratio, lam_max] (Saad, Alg. 12.1)."""
+    """Chebyshev acceleration of D^{-1} A x = D^{-1} b on [lam_max/ratio, lam_max] (Saad, Alg. 12.1).
+    A level without edges (lam_max = 0) leaves x as it is (zero from a zero start)."""
+    if not lam_max > 0:
+        return np.zeros_like(b) if x is None else x.copy()
     lam_min = lam_max / CHEB_RATIO
     theta, delta = 0.5 * (lam_max + lam_min), 0.5 * (lam_max - lam_min)
     sigma = theta / delta

@@ -22,7 +22,7 @@ OK, ERR_INVALID_ARG, ERR_NOT_SYMMETRIC, ERR_ISOLATED, ERR_OOM, ERR_CUDA, ERR_NOC
     ERR_UNSUPPORTED = range(9)
 HOST_PTRS, DEVICE_PTRS, VALIDATE = 0, 1, 2
 COMBINATORIAL, GENERALIZED, NORMALIZED = 0, 1, 2
-PRECOND_NONE, PRECOND_JACOBI, PRECOND_POLY = 0, 1, 2
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_POLY, PRECOND_AMG = 0, 1, 2, 3
 FP64, FP32, MIXED_BF16 = 0, 1, 2
 INIT_RANDOM, INIT_PIECEWISE = 0, 1
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
@@ -31,7 +31,7 @@ MAX_NEV = 16
 MAX_POLY_DEGREE = 64
 
 LAPLACIANS = {"combinatorial": COMBINATORIAL, "generalized": GENERALIZED, "normalized": NORMALIZED}
-PRECONDS = {"none": PRECOND_NONE, "jacobi": PRECOND_JACOBI, "poly": PRECOND_POLY}
+PRECONDS = {"none": PRECOND_NONE, "jacobi": PRECOND_JACOBI, "poly": PRECOND_POLY, "amg": PRECOND_AMG}
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed_bf16": MIXED_BF16}
 INITS = {"random": INIT_RANDOM, "piecewise": INIT_PIECEWISE}
 
@@ -69,6 +69,11 @@ class GraphInfo(C.Structure):
                 ("regular", C.c_int32), ("spmm_med_max", C.c_int32), ("sell_stride", C.c_int32)]
 
 
+class AmgLevelInfo(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("reserved", C.c_int32), ("n", C.c_int64), ("nnz", C.c_int64),
+                ("n_next", C.c_int64), ("lambda_max", C.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_2105_00578_gb300.build.build()")
@@ -93,6 +98,7 @@ def _load():
         "sphynx_mj": (C.c_int, [i32, vp, i32, i32, i64, vp, i32, vp, vp]),
         "sphynx_mj_noalloc": (C.c_int, [i32, vp, i32, i32, i64, vp, i32, vp, vp]),
         "sphynx_set_spmm_med_max": (C.c_int, [vp, i32]),
+        "sphynx_amg_level": (C.c_int, [vp, i32, C.POINTER(AmgLevelInfo), vp, vp, vp, vp]),
         "sphynx_default_options_for": (C.c_int, [vp, i32, C.POINTER(Options)]),
         "sphynx_create_batch": (C.c_int, [vp, vp, vp, vp, vp, i32, i64, i64, C.c_uint32, vp, C.POINTER(vp)]),
         "sphynx_partition_batch": (C.c_int, [vp, i32, C.POINTER(Options), vp, vp, vp, vp, vp, vp, C.POINTER(Stats)]),
@@ -234,6 +240,14 @@ def sphynx_precond_setup(h, opt: Options) -> np.ndarray:
 
 def sphynx_precond_apply(h, opt: Options, r, hout, ld, ncols) -> None:
     check(LIB.sphynx_precond_apply(h, C.byref(opt), ptr(r), ptr(hout), ld, ncols))
+
+
+def sphynx_amg_level(h, level: int, agg=None, row_ptr=None, col=None, w=None) -> dict:
+    """Sizes of one multigrid level; fills the given device tensors (agg int32[n],
+    row_ptr int64[n + 1], col int32[nnz], w float32[nnz])."""
+    info = AmgLevelInfo()
+    check(LIB.sphynx_amg_level(h, level, C.byref(info), ptr(agg), ptr(row_ptr), ptr(col), ptr(w)))
+    return {f: getattr(info, f) for f, _ in info._fields_ if f != "reserved"}
 
 
 def sphynx_gram(dtype, s_blocks, ls_blocks, ld, n, bdiag=None, stream=None):

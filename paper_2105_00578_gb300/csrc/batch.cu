@@ -570,7 +570,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
                      double *eigs, int32_t *iters, int32_t *status, sphynx_stats *stats) {
   BatchInfo &B = g->batch;
   const int count = B.count;
-  if (o->precond == SPHYNX_PRECOND_POLY)
+  if (o->precond == SPHYNX_PRECOND_POLY || o->precond == SPHYNX_PRECOND_AMG)
     fail(SPHYNX_ERR_UNSUPPORTED, "batched partitions take the Jacobi preconditioner or none");
   if (o->init != SPHYNX_INIT_RANDOM) fail(SPHYNX_ERR_UNSUPPORTED, "batched partitions start from the random block");
   for (int q = 0; q < count; ++q)

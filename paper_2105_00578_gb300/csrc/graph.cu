@@ -706,6 +706,7 @@ int sphynx_create(const int64_t *row_ptr, const int32_t *col, const float *edge_
 void sphynx_destroy(sphynx_handle g) {
   if (!g) return;
   cudaStreamSynchronize(g->stream);
+  if (g->amg) amg_free(g->amg);
   for (auto e : g->ctr.ev_pool) cudaEventDestroy(e);
   if (g->host_flag) cudaFreeHost(g->host_flag);
   delete g;
@@ -742,13 +743,13 @@ int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info) {
 int sphynx_default_options_for(sphynx_handle g, int32_t precond, sphynx_options *opt) {
   return guarded([&]() -> int {
     if (!g || !opt) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
-    if (precond < SPHYNX_PRECOND_NONE || precond > SPHYNX_PRECOND_POLY) fail(SPHYNX_ERR_INVALID_ARG, "precond");
+    if (precond < SPHYNX_PRECOND_NONE || precond > SPHYNX_PRECOND_AMG) fail(SPHYNX_ERR_INVALID_ARG, "precond");
     sphynx_default_options(opt);
     opt->precond = precond;
     const bool regular = g->max_degree * g->n <= 10 * g->nnz;   // max deg <= 10 x (nnz / n), exactly
     if (regular) {
       opt->laplacian = SPHYNX_COMBINATORIAL;
-      opt->tol = 1e-3;
+      opt->tol = precond == SPHYNX_PRECOND_AMG ? 1e-2 : 1e-3;
       opt->init = SPHYNX_INIT_RANDOM;
     } else {
       opt->laplacian = precond == SPHYNX_PRECOND_POLY ? SPHYNX_NORMALIZED : SPHYNX_GENERALIZED;

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/sphynx.h"
@@ -189,6 +190,10 @@ struct BatchInfo {
   DevBuf graph_max;                 // uint64 [count][2]: max degree, max weighted degree (double bits)
 };
 
+// aggregation multigrid hierarchy (amg.cu), owned by the handle
+struct AmgHierarchy;
+void amg_free(AmgHierarchy *h);
+
 }  // namespace sphynx
 
 struct sphynx_graph {
@@ -221,6 +226,7 @@ struct sphynx_graph {
   sphynx::DevBuf pinned_dummy;
   void *host_flag = nullptr;                 // pinned int32[8] for convergence polls
   sphynx::BatchInfo batch;                   // set by sphynx_create_batch
+  sphynx::AmgHierarchy *amg = nullptr;       // multigrid preconditioner (Sec. 5.3), built on demand
   sphynx::LapView view() const {
     return sphynx::LapView{n, rowptr, col, w, deg.as<double>(), degf.as<float>(),
                            dinv.as<double>(), dinvf.as<float>()};
@@ -258,6 +264,15 @@ void spmm(sphynx_graph *g, const SpmmArgs &a);
 SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a);
 // every SELL slice stride timed on this product; sets plan.sell_ls to the fastest
 void spmm_tune_sell_stride(sphynx_graph *g, const SpmmArgs &a);
+
+// ---- amg.cu -----------------------------------------------------------------
+// build (or reuse, for the same seed) the aggregation hierarchy of g
+void amg_setup(sphynx_graph *g, int64_t seed);
+// h = one V-cycle applied to the n x ld block r (F32 or F64); launches skip once *done
+void amg_apply(sphynx_graph *g, DT dt, const void *r, void *h, int ld, const int *done);
+int amg_levels(const sphynx_graph *g);
+void amg_level_info(sphynx_graph *g, int level, sphynx_amg_level_info *info, int32_t *agg_out, int64_t *rowptr_out,
+                    int32_t *col_out, float *w_out);
 
 // ---- dense.cu ---------------------------------------------------------------
 void launch_random_block(cudaStream_t s, DT dt, void *x, int64_t n, int b, int ld, uint64_t seed);

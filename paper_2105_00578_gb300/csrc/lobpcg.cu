@@ -4,7 +4,8 @@
 //
 // All iteration state lives on the GPU.  One LOBPCG iteration is a fixed
 // sequence of launches on the handle's stream:
-//   [polynomial chain: k-1 fused SpMM steps]  H = M R
+//   [polynomial chain: k-1 fused SpMM steps,
+//    or one multigrid V-cycle]                H = M R
 //   SpMM                                       LH = L H
 //   Gram + fixed-order reduction               G_A = S^T L S, G_B = S^T B S, S = [X H P]
 //   Rayleigh-Ritz (one CTA, FP64)              Y, Theta
@@ -37,7 +38,10 @@ int op_of(int laplacian) { return laplacian == SPHYNX_NORMALIZED ? SPHYNX_NORMAL
 void check_options(const sphynx_graph *g, const sphynx_options *o) {
   if (!o) fail(SPHYNX_ERR_INVALID_ARG, "options are NULL");
   if (o->laplacian < 0 || o->laplacian > 2) fail(SPHYNX_ERR_INVALID_ARG, "laplacian %d", o->laplacian);
-  if (o->precond < 0 || o->precond > 2) fail(SPHYNX_ERR_INVALID_ARG, "precond %d", o->precond);
+  if (o->precond < 0 || o->precond > 3) fail(SPHYNX_ERR_INVALID_ARG, "precond %d", o->precond);
+  if (o->precond == SPHYNX_PRECOND_AMG && o->laplacian == SPHYNX_NORMALIZED)
+    fail(SPHYNX_ERR_INVALID_ARG, "the multigrid preconditioner approximates L_C^{-1}: combinatorial or generalized "
+         "problem only");
   if (o->precision < 0 || o->precision > 2) fail(SPHYNX_ERR_INVALID_ARG, "precision %d", o->precision);
   if (o->init < 0 || o->init > 1) fail(SPHYNX_ERR_INVALID_ARG, "init %d", o->init);
   if (o->precond == SPHYNX_PRECOND_POLY && (o->poly_degree < 1 || o->poly_degree > SPHYNX_MAX_POLY_DEGREE))
@@ -250,6 +254,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   SPX_CUDA(cudaEventCreate(&ev1));
   SPX_CUDA(cudaEventRecord(ev0, st));
   if (o->precond == SPHYNX_PRECOND_POLY) poly_setup(g, o);
+  if (o->precond == SPHYNX_PRECOND_AMG) amg_setup(g, o->seed);
   SPX_CUDA(cudaEventRecord(ev1, st));
 
   void *X[2] = {g->workspace("X0", blk, false), g->workspace("X1", blk, false)};
@@ -271,8 +276,9 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   const double *bd = gen ? g->deg.as<double>() : nullptr;
   const float *bdf = gen ? g->degf.as<float>() : nullptr;
   const bool jac = o->precond == SPHYNX_PRECOND_JACOBI && lap == SPHYNX_COMBINATORIAL;
-  // the residual kernel writes H directly unless the polynomial needs R
-  void *res_out = o->precond == SPHYNX_PRECOND_POLY ? R : H;
+  // the residual kernel writes H directly unless the polynomial or the multigrid cycle needs R
+  const bool pre_r = o->precond == SPHYNX_PRECOND_POLY || o->precond == SPHYNX_PRECOND_AMG;
+  void *res_out = pre_r ? R : H;
 
   // initial block
   if (x0_host) {
@@ -309,6 +315,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   for (int it = 0; it < o->max_iter; ++it) {
     const int nx = cur ^ 1;
     if (o->precond == SPHYNX_PRECOND_POLY) poly_apply(g, o->precision, R, H, ld, b, done);   // precondition
+    if (o->precond == SPHYNX_PRECOND_AMG) amg_apply(g, dt, R, H, ld, done);
     plain_spmm(g, lap, dt, H, LH, ld, b, done);
     GramArgs g3{dt, 3, ld, n, {X[cur], H, P[cur]}, {LX[cur], LH, LP[cur]}, bd, bdf, gpart, ga, gb, done};
     const int pg3 = launch_gram(st, g3, ggrid);                                        // Rayleigh-Ritz
@@ -517,6 +524,10 @@ int sphynx_precond_setup(sphynx_handle g, const sphynx_options *opt, double *roo
   return guarded([&]() -> int {
     if (!g) fail(SPHYNX_ERR_INVALID_ARG, "NULL handle");
     check_options(g, opt);
+    if (opt->precond == SPHYNX_PRECOND_AMG) {
+      amg_setup(g, opt->seed);
+      return SPHYNX_OK;
+    }
     if (opt->precond != SPHYNX_PRECOND_POLY) return SPHYNX_OK;
     poly_setup(g, opt);
     if (roots_out) memcpy(roots_out, g->poly_roots.data(), g->poly_k * sizeof(double));
@@ -540,6 +551,12 @@ int sphynx_precond_apply(sphynx_handle g, const sphynx_options *opt, const void 
       poly_apply(g, opt->precision, r, h, ld, ncols, nullptr);
       return SPHYNX_OK;
     }
+    if (opt->precond == SPHYNX_PRECOND_AMG) {
+      if (ld != round4(ncols)) fail(SPHYNX_ERR_INVALID_ARG, "multigrid apply needs ld = round4(ncols)");
+      amg_setup(g, opt->seed);
+      amg_apply(g, dt, r, h, ld, nullptr);
+      return SPHYNX_OK;
+    }
     // Jacobi (identity for L_N) or none: H = diag^{-1} R through the residual
     // kernel with X = 0 (R = LX - 0 = the input block)
     const size_t bytes = static_cast<size_t>(g->n) * ld * dt_size(dt);
@@ -551,6 +568,15 @@ int sphynx_precond_apply(sphynx_handle g, const sphynx_options *opt, const void 
     ResidualArgs ra{dt, ld, g->n, zero, r, theta, nullptr, nullptr, jac ? g->jinv.as<double>() : nullptr,
                     jac ? g->jinvf.as<float>() : nullptr, h, np, nullptr};
     launch_residual(g->stream, ra, grid);
+    return SPHYNX_OK;
+  });
+}
+
+int sphynx_amg_level(sphynx_handle g, int32_t level, sphynx_amg_level_info *info, int32_t *agg_out,
+                     int64_t *row_ptr_out, int32_t *col_out, float *w_out) {
+  return guarded([&]() -> int {
+    if (!g) fail(SPHYNX_ERR_INVALID_ARG, "NULL handle");
+    amg_level_info(g, level, info, agg_out, row_ptr_out, col_out, w_out);
     return SPHYNX_OK;
   });
 }

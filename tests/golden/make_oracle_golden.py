@@ -5,6 +5,7 @@ Calls only oracle/ (and the seeded generators in workloads/).  Usage:
     python tests/golden/make_oracle_golden.py c2     # 128^3 27-point mesh
     python tests/golden/make_oracle_golden.py c1     # 64 x 64 5-point mesh
     python tests/golden/make_oracle_golden.py c3     # R-MAT scale 22, largest component
+    python tests/golden/make_oracle_golden.py amg    # 128^3 27-point mesh, multigrid preconditioner
 """
 
 from __future__ import annotations
@@ -31,6 +32,9 @@ CASES = {
     "c3": dict(graph=lambda: workloads.rmat(22, 16, 0.57, 0.19, 0.19, seed=3), K=256, problem="normalized",
                precond="jacobi", tol=1e-2, seed=3, poly_degree=25,
                desc="R-MAT scale 22 (a,b,c = .57,.19,.19), largest component, normalized, Jacobi, K=256, tol 1e-2"),
+    "amg": dict(graph=lambda: workloads.grid3d(128, 128, 128, 27), K=64, problem="combinatorial", precond="amg",
+                tol=1e-2, seed=2, poly_degree=25,
+                desc="3D 27-point 128^3, combinatorial, aggregation multigrid, K=64, tol 1e-2"),
 }
 
 

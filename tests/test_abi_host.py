@@ -63,7 +63,7 @@ def test_options_helper_maps_names():
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):
-    """Every field offset and the size of the three public structs, as the C
+    """Every field offset and the size of the public structs, as the C
     compiler lays them out from the header, equal the Python binding's."""
     import shutil
     import subprocess
@@ -71,7 +71,8 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = {"sphynx_options": spx.Options, "sphynx_stats": spx.Stats, "sphynx_graph_info": spx.GraphInfo}
+    structs = {"sphynx_options": spx.Options, "sphynx_stats": spx.Stats, "sphynx_graph_info": spx.GraphInfo,
+               "sphynx_amg_level_info": spx.AmgLevelInfo}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sphynx.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')

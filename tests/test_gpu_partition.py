@@ -163,7 +163,7 @@ def test_default_options_follow_the_oracle_decision_flow():
         h = spx.sphynx_create(g.row_ptr, g.col)
         try:
             assert spx.sphynx_get_info(h)["regular"] == int(O.is_regular(g))
-            for pc in ("jacobi", "poly", "none"):
+            for pc in ("jacobi", "poly", "none", "amg"):
                 o = spx.sphynx_default_options_for(h, pc)
                 ref = O.default_options(g, pc)
                 assert (names[o.laplacian], o.tol, inits[o.init]) == (ref["problem"], ref["tol"], ref["init"])
