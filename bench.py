@@ -53,7 +53,7 @@ WORKLOADS = {
                      "preconditioner (plain aggregation, degree-3 Chebyshev, ratio 7, <= 5 levels), K=64 (d=7), "
                      "LOBPCG tol 1e-2 (Sphynx's default for regular graphs with multigrid), FP32 blocks",
                 K=64, laplacian="combinatorial", precond="amg", poly_degree=25, tol=1e-2, seed=2,
-                precision="fp32", golden=None),
+                precision="fp32", golden="amg_oracle.json"),
     "c5": dict(desc="R-MAT scale 24 (edge factor 16, a=.57 b=.19 c=.19), largest component, FP32 edge weights "
                     "uniform in [0.5, 1.5); normalized Laplacian, polynomial preconditioner degree 10, K=1024 "
                     "(d=11), BF16 polynomial chain, tol 1e-2",
