@@ -689,16 +689,38 @@ void coarse_level(AmgLevel &L, AmgLevel &C) {
     SPX_CUDA(cudaMemcpyAsync(llarge, large.data(), large.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   SPX_CUDA(cudaMemsetAsync(cur.p, 0, sizeof(unsigned long long), st));
   if (!small.empty()) {
-    int64_t cap = 64;
-    while (cap < mx_s) cap <<= 1;
-    const size_t sm = static_cast<size_t>(cap) * (sizeof(unsigned long long) + sizeof(float));
+    // one launch per power-of-two size class, so that a row sorts at the
+    // capacity of its own class rather than of the largest aggregate
+    int64_t cap0 = 64;
+    while (cap0 < mx_s) cap0 <<= 1;
+    const size_t smax = static_cast<size_t>(cap0) * (sizeof(unsigned long long) + sizeof(float));
     SPX_CUDA(cudaFuncSetAttribute(k_coarse_row<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(sm)));
-    k_coarse_row<128><<<static_cast<unsigned>(small.size()), 128, sm, st>>>(
-        lsmall, L.mem_ptr.as<int64_t>(), L.mem.as<int32_t>(), g->rowptr, g->col, g->w, L.agg.as<int32_t>(), cap,
-        rc.as<int64_t>(), rs.as<int64_t>(), cur.as<unsigned long long>(), tcol.as<int32_t>(), tw.as<float>(), nullptr,
-        nullptr);
-    SPX_LAUNCHED();
+                                  static_cast<int>(smax)));
+    std::vector<int32_t> order;
+    std::vector<std::pair<int64_t, size_t>> classes;   // (cap, count), caps increasing
+    order.reserve(small.size());
+    for (int64_t cap = 64, lo = 0; lo < mx_s || cap == 64; lo = cap, cap <<= 1) {
+      const size_t first = order.size();
+      for (int32_t I : small) {
+        const int64_t e = hent[static_cast<size_t>(I)];
+        if (e <= cap && (cap == 64 || e > lo)) order.push_back(I);
+      }
+      if (order.size() > first) classes.emplace_back(cap, order.size() - first);
+      if (cap >= cap0) break;
+    }
+    if (order.size() != small.size()) fail(SPHYNX_ERR_CUDA, "multigrid: size classes lost an aggregate");
+    SPX_CUDA(cudaMemcpyAsync(lsmall, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    size_t off = 0;
+    for (const auto &c : classes) {
+      const size_t sm = static_cast<size_t>(c.first) * (sizeof(unsigned long long) + sizeof(float));
+      k_coarse_row<128><<<static_cast<unsigned>(c.second), 128, sm, st>>>(
+          lsmall + off, L.mem_ptr.as<int64_t>(), L.mem.as<int32_t>(), g->rowptr, g->col, g->w, L.agg.as<int32_t>(),
+          c.first, rc.as<int64_t>(), rs.as<int64_t>(), cur.as<unsigned long long>(), tcol.as<int32_t>(),
+          tw.as<float>(), nullptr, nullptr);
+      SPX_LAUNCHED();
+      off += c.second;
+    }
+    SPX_CUDA(cudaStreamSynchronize(st));   // `order` feeds an asynchronous copy
   }
   if (!large.empty()) {
     int64_t cap = 64;
@@ -816,10 +838,11 @@ void ensure_blocks(AmgHierarchy &H, DT dt, int ld) {
 
 }  // namespace
 
-// Build (or reuse) the hierarchy of g for this seed.
-void amg_setup(sphynx_graph *g, int64_t seed) {
+// Build the hierarchy of g for this seed (rebuild = false: keep one built
+// for the same seed).
+void amg_setup(sphynx_graph *g, int64_t seed, bool rebuild) {
   if (g->batch.count > 0) fail(SPHYNX_ERR_UNSUPPORTED, "the multigrid preconditioner takes single graphs");
-  if (g->amg && g->amg->seed == seed) return;
+  if (!rebuild && g->amg && g->amg->seed == seed) return;
   if (g->amg) {
     amg_free(g->amg);
     g->amg = nullptr;

@@ -266,8 +266,8 @@ SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a);
 void spmm_tune_sell_stride(sphynx_graph *g, const SpmmArgs &a);
 
 // ---- amg.cu -----------------------------------------------------------------
-// build (or reuse, for the same seed) the aggregation hierarchy of g
-void amg_setup(sphynx_graph *g, int64_t seed);
+// build the aggregation hierarchy of g (rebuild = false: keep one built for the same seed)
+void amg_setup(sphynx_graph *g, int64_t seed, bool rebuild);
 // h = one V-cycle applied to the n x ld block r (F32 or F64); launches skip once *done
 void amg_apply(sphynx_graph *g, DT dt, const void *r, void *h, int ld, const int *done);
 int amg_levels(const sphynx_graph *g);

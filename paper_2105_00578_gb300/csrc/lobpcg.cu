@@ -254,7 +254,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   SPX_CUDA(cudaEventCreate(&ev1));
   SPX_CUDA(cudaEventRecord(ev0, st));
   if (o->precond == SPHYNX_PRECOND_POLY) poly_setup(g, o);
-  if (o->precond == SPHYNX_PRECOND_AMG) amg_setup(g, o->seed);
+  if (o->precond == SPHYNX_PRECOND_AMG) amg_setup(g, o->seed, true);   // part of every partition, like the polynomial
   SPX_CUDA(cudaEventRecord(ev1, st));
 
   void *X[2] = {g->workspace("X0", blk, false), g->workspace("X1", blk, false)};
@@ -525,7 +525,7 @@ int sphynx_precond_setup(sphynx_handle g, const sphynx_options *opt, double *roo
     if (!g) fail(SPHYNX_ERR_INVALID_ARG, "NULL handle");
     check_options(g, opt);
     if (opt->precond == SPHYNX_PRECOND_AMG) {
-      amg_setup(g, opt->seed);
+      amg_setup(g, opt->seed, true);
       return SPHYNX_OK;
     }
     if (opt->precond != SPHYNX_PRECOND_POLY) return SPHYNX_OK;
@@ -553,7 +553,7 @@ int sphynx_precond_apply(sphynx_handle g, const sphynx_options *opt, const void 
     }
     if (opt->precond == SPHYNX_PRECOND_AMG) {
       if (ld != round4(ncols)) fail(SPHYNX_ERR_INVALID_ARG, "multigrid apply needs ld = round4(ncols)");
-      amg_setup(g, opt->seed);
+      amg_setup(g, opt->seed, false);
       amg_apply(g, dt, r, h, ld, nullptr);
       return SPHYNX_OK;
     }
