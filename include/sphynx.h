@@ -356,8 +356,11 @@ int sphynx_eval(sphynx_handle g, const int32_t *part, int32_t K, double *cut,
 
 /* Algorithm 2: K-way partition.  part_out: int32[n], host memory unless
  * opt->flags has SPHYNX_OUT_DEVICE.  cut_out / imbalance_out / stats may be
- * NULL.  Returns OK, or NOCONV / BREAKDOWN with a valid partition of the
- * last iterate. */
+ * NULL.  Every call sets up its preconditioner anew (the polynomial's roots,
+ * the multigrid hierarchy), and stats->ms_setup times that setup.  Returns
+ * OK, or NOCONV / BREAKDOWN with a valid partition of the last iterate;
+ * INVALID_ARG for bad options (among them the multigrid preconditioner with
+ * the normalized problem). */
 int sphynx_partition(sphynx_handle g, int32_t K, const sphynx_options *opt, int32_t *part_out,
                      double *cut_out, double *imbalance_out, sphynx_stats *stats);
 
@@ -388,7 +391,7 @@ int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, const float 
  * values ascending), iterations and status (int32[count], OK or NOCONV per
  * graph): host arrays, each may be NULL.  stats (may be NULL): status OK only if every graph
  * converged, iterations = the largest.  Errors: INVALID_ARG (not a batch
- * handle), UNSUPPORTED (polynomial preconditioner, piecewise start,
+ * handle), UNSUPPORTED (polynomial or multigrid preconditioner, piecewise start,
  * K x count > 2^20), CUDA, OOM. */
 int sphynx_partition_batch(sphynx_handle g, int32_t K, const sphynx_options *opt, int32_t *part_out,
                            double *cuts, double *imbalances, double *eigenvalues, int32_t *iterations,
