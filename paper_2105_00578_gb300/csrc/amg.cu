@@ -892,8 +892,6 @@ void amg_apply(sphynx_graph *g, DT dt, const void *r, void *h, int ld, const int
     vcycle<float>(H, 0, dt, ld, static_cast<const float *>(r), static_cast<float *>(h), done);
 }
 
-int amg_levels(const sphynx_graph *g) { return g->amg ? static_cast<int>(g->amg->lv.size()) : 0; }
-
 // sizes of one level and, on request, its aggregates and CSR (device outputs)
 void amg_level_info(sphynx_graph *g, int level, sphynx_amg_level_info *info, int32_t *agg_out, int64_t *rowptr_out,
                     int32_t *col_out, float *w_out) {

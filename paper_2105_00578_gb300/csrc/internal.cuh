@@ -270,7 +270,6 @@ void spmm_tune_sell_stride(sphynx_graph *g, const SpmmArgs &a);
 void amg_setup(sphynx_graph *g, int64_t seed, bool rebuild);
 // h = one V-cycle applied to the n x ld block r (F32 or F64); launches skip once *done
 void amg_apply(sphynx_graph *g, DT dt, const void *r, void *h, int ld, const int *done);
-int amg_levels(const sphynx_graph *g);
 void amg_level_info(sphynx_graph *g, int level, sphynx_amg_level_info *info, int32_t *agg_out, int64_t *rowptr_out,
                     int32_t *col_out, float *w_out);
 
