@@ -50,3 +50,24 @@ def test_single_rank_passes_values_through():
     import bench
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.job_throughput(3, 500.0, 1) == pytest.approx(6.0)
+
+
+def test_oracle_comparison_of_a_bench_line():
+    """The bench line's vs_oracle block: relative eigenvalue error (the null
+    eigenvalue left out), residual ratio and relative cut error against the
+    stored oracle run, or None where no oracle run is stored."""
+    import json
+
+    import bench
+    w = bench.WORKLOADS["c2"]
+    gold = json.load(open(os.path.join(bench.ROOT, "tests", "golden", w["golden"])))
+    ev = list(gold["eigenvalues"])
+    ev[2] *= 1.0 + 3e-4                               # one perturbed eigenvalue
+    st = {"eigenvalues": ev, "resnorm": [0.0] + [0.5 * w["tol"] * abs(t) for t in ev[1:]]}
+    v = bench.vs_oracle(w, st, gold["cut"] * 1.01, "mixed_bf16")
+    assert v["eigenvalue_max_rel_err"] == pytest.approx(3e-4, rel=1e-9)
+    assert v["eigenvalue_rel_tol"] == 1e-3 and v["cut_rel_tol"] == 0.02
+    assert v["cut_rel_err"] == pytest.approx(0.01, rel=1e-9)
+    assert v["max_resnorm_over_tol_theta"] == pytest.approx(0.5, rel=1e-12)
+    assert bench.vs_oracle(w, st, gold["cut"], "fp64")["eigenvalue_rel_tol"] == 1e-6
+    assert bench.vs_oracle(bench.WORKLOADS["c5"], st, 1.0, "mixed_bf16") is None
