@@ -17,6 +17,8 @@ N > 1 runs N independent replicas ("scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import csv
+import hashlib
 import json
 import math
 import os
@@ -84,18 +86,89 @@ def peaks() -> dict:
     return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-def profiled_traffic(kernel: str, workload: str):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if any."""
-    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+# sources whose change invalidates a stored DRAM-traffic figure of the SpMM kernels
+TRAFFIC_SOURCES = ("paper_2105_00578_gb300/csrc/spmm_kernels.cuh", "paper_2105_00578_gb300/csrc/spmm.cu",
+                   "paper_2105_00578_gb300/csrc/spmm_bf16.cu", "paper_2105_00578_gb300/csrc/spmm_f32.cu",
+                   "paper_2105_00578_gb300/csrc/spmm_f64.cu", "paper_2105_00578_gb300/csrc/graph.cu")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_path(workload: str) -> str:
+    return os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the workload's dominant kernel, from the JSON
+    that `--ingest-ncu` wrote from an ncu capture; None when there is none or
+    when the kernel sources changed after the capture."""
+    p = traffic_path(workload)
     if not os.path.exists(p):
-        return None
-    for line in open(p):
-        if line.startswith("traffic_bytes_per_launch:"):
-            try:
-                return float(line.split(":", 1)[1].strip())
-            except ValueError:
-                return None
-    return None
+        return None, None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None, d
+    return float(d["traffic_bytes_per_launch"]), d
+
+
+_UNITS = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12,
+          "KB": 1e3, "MB": 1e6, "GB": 1e9, "B": 1.0}
+
+
+def ingest_ncu(csv_path: str, kernel_regex: str, workload: str, command: str) -> dict:
+    """Mean dram__bytes_read.sum + dram__bytes_write.sum per launch of the
+    kernels matching kernel_regex in an ncu --csv log (metrics page), written
+    to profiles/traffic_<workload>.json with the hash of the SpMM sources."""
+    import re
+    pat = re.compile(kernel_regex)
+    per = {}
+    with open(csv_path, newline="") as f:
+        rows = [r for r in csv.reader(f) if r]
+    head = next(i for i, r in enumerate(rows) if "Metric Name" in r and "Kernel Name" in r)
+    cols = rows[head]
+    ci = {c: cols.index(c) for c in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
+    for r in rows[head + 1:]:
+        if len(r) < len(cols) or not pat.search(r[ci["Kernel Name"]]):
+            continue
+        name = r[ci["Metric Name"]]
+        if name not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        val = float(r[ci["Metric Value"]].replace(",", "")) * _UNITS.get(r[ci["Metric Unit"]], 1.0)
+        d = per.setdefault(r[ci["ID"]], {})
+        d[name] = val
+    launches = [v["dram__bytes_read.sum"] + v["dram__bytes_write.sum"] for v in per.values() if len(v) == 2]
+    if not launches:
+        raise SystemExit(f"no launch of {kernel_regex!r} with both DRAM metrics in {csv_path}")
+    out = {"workload": workload, "kernel_regex": kernel_regex, "launches": len(launches),
+           "traffic_bytes_per_launch": float(np.mean(launches)),
+           "traffic_bytes_min": float(np.min(launches)), "traffic_bytes_max": float(np.max(launches)),
+           "source_hash": kernel_source_hash(), "command": command, "csv": os.path.basename(csv_path)}
+    with open(traffic_path(workload), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    return out
+
+
+def survey_bytes(n: int, nnz: int, b: int, s_in: int, s_out: int, s_diag: int, weighted: bool) -> float:
+    """Algorithmic bytes of one Laplacian product as the scope table states
+    them: 8 (n + 1) row offsets, nnz (4 + s_w) column indices and weights, the
+    input and output blocks n b s and the diagonal n s_diag (X counted once)."""
+    return 8.0 * (n + 1) + nnz * (4.0 + (4.0 if weighted else 0.0)) + n * b * (s_in + s_out) + n * s_diag
+
+
+def config_of(w: dict, precision: str, col_bytes: float, world: int) -> dict:
+    """The bench line's config (both arms print the same one)."""
+    return {"workload": w["desc"], "K": w["K"], "precision": precision,
+            "l2": (f"inputs larger than L2 (CSR column array {col_bytes / 1e6:.0f} MB > 129 MB)"
+                   if col_bytes > 129e6 else "inputs within L2, no flush"),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 class Clocks:
@@ -164,39 +237,55 @@ def dist_env():
     return world, rank, local
 
 
-def oracle_sample(name: str, steps: int = 1):
-    """The FP64 oracle on the same workload, bounded: one run with the
-    iteration cap at 0 (setup, initial Rayleigh-Ritz, embedding, MJ, cut) and
-    one with the cap at 1; partitions/s are extrapolated with the oracle's
-    own full-run iteration count from tests/golden (written by oracle code)."""
+def oracle_timed_run(name: str, iterations: int):
+    """One run of the FP64 oracle on the workload with the LOBPCG cap at
+    `iterations`, timed piece by piece through the oracle's iteration
+    callback: the fixed part (operator, preconditioner setup, initial
+    Rayleigh-Ritz, embedding, multi-jagged and cut) and each iteration."""
     import oracle
     w = WORKLOADS[name]
     g = make_graph(name)
-    kw = dict(problem=w["laplacian"], precond=w["precond"], tol=w["tol"], seed=w["seed"],
-              poly_degree=w["poly_degree"])
-    t0s, t1s = [], []
-    for _ in range(steps):
-        t = time.perf_counter()
-        oracle.partition(g, w["K"], maxit=0, **kw)
-        t0s.append(time.perf_counter() - t)
-        t = time.perf_counter()
-        oracle.partition(g, w["K"], maxit=1, **kw)
-        t1s.append(time.perf_counter() - t)
-    t0, t1 = float(np.median(t0s)), float(np.median(t1s))
-    iters = None
-    if w["golden"]:
-        p = os.path.join(ROOT, "tests", "golden", w["golden"])
-        if os.path.exists(p):
-            with open(p) as f:
-                iters = json.load(f)["iterations"]
-    if iters is None:
-        iters = 1
-    per_iter = max(t1 - t0, 0.0)
-    est = t0 + iters * per_iter
-    sample = (f"oracle.partition with the LOBPCG cap at 0 ({t0:.1f} s) and 1 ({t1:.1f} s) iterations, "
-              f"extrapolated to the oracle's {iters} iterations (tests/golden/{w['golden']}); "
-              f"scipy sparse products single-threaded, numpy BLAS on all cores")
-    return 1.0 / est, sample, t0 + t1
+    marks = []
+    t0 = time.perf_counter()
+    oracle.partition(g, w["K"], problem=w["laplacian"], precond=w["precond"], tol=w["tol"], seed=w["seed"],
+                     poly_degree=w["poly_degree"], maxit=iterations,
+                     on_iteration=lambda it: marks.append(time.perf_counter()))
+    t_end = time.perf_counter()
+    iters = [b - a for a, b in zip(marks[:-1], marks[1:])]
+    fixed = (marks[0] - t0) + (t_end - marks[-1])
+    return fixed, iters, g
+
+
+def oracle_iterations(name: str):
+    """The oracle's own iteration count for the workload, from its full run
+    stored in tests/golden (written by oracle code only), or None."""
+    w = WORKLOADS[name]
+    if not w.get("golden"):
+        return None
+    p = os.path.join(ROOT, "tests", "golden", w["golden"])
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f)["iterations"]
+
+
+ORACLE_THREADS = ("scipy sparse products single-threaded; numpy BLAS (the small dense algebra) on up to "
+                  f"{os.cpu_count()} threads")
+
+
+def oracle_sample(name: str):
+    """The FP64 oracle on the same workload, bounded to about 10-30 s: one
+    run with the iteration cap at 2 gives the fixed part and the time of an
+    iteration; partitions/s is extrapolated to the oracle's own iteration
+    count (labelled as such)."""
+    fixed, iters, _ = oracle_timed_run(name, 2)
+    n_it = oracle_iterations(name) or len(iters)
+    per_iter = float(np.mean(iters)) if iters else 0.0
+    est = fixed + n_it * per_iter
+    sample = (f"EXTRAPOLATED from one oracle.partition run with the LOBPCG cap at 2: fixed part {fixed:.1f} s "
+              f"(operator, preconditioner setup, initial Rayleigh-Ritz, embedding, multi-jagged, cut) plus the "
+              f"oracle's own {n_it} iterations at the measured {per_iter:.2f} s each; {ORACLE_THREADS}")
+    return 1.0 / est, sample, fixed + sum(iters)
 
 
 def vs_oracle(w, st, cut, precision):
@@ -221,29 +310,67 @@ def vs_oracle(w, st, cut, precision):
 
 
 def run_reference(args, world, rank):
+    """The oracle arm, on the same workload, metric and config as ours.  A
+    whole oracle partition of the large workloads takes minutes, so a step is
+    one real piece of one oracle run: a single run with the LOBPCG cap at
+    warmup + steps iterations, whose first `warmup` iterations are untimed
+    warm-up and whose next `steps` iterations are the timed steps.  The fixed
+    part of the same run (operator, preconditioner setup, initial
+    Rayleigh-Ritz, embedding, multi-jagged, cut) is timed too, and the value
+    is partitions/s for the fixed part plus the oracle's own iteration count
+    at the measured per-iteration time.  Workloads whose whole oracle
+    partition is short (the 64x64 mesh) time whole partitions per step."""
     if rank != 0:
         return 0
     w = WORKLOADS[args.workload]
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; its samples are timed below
-    vals = []
-    total_s = 0.0
-    sample = ""
-    graphs = None
+    precision = args.precision or w["precision"]
     if w.get("batch"):
         import workloads
         graphs = workloads.rgg_batch(w["batch"])
-    for _ in range(args.steps):
-        if graphs is not None:
-            v, sample = oracle_batch_sample(graphs, w, budget_s=20.0)
-        else:
-            v, sample, s = oracle_sample(args.workload)
-        vals.append(v)
-    value = float(np.median(vals))
+        vals = []
+        sample = ""
+        for _ in range(args.steps):
+            v, sample = oracle_batch_sample(graphs, w, budget_s=max(1.0, 150.0 / max(1, args.steps)))
+            vals.append(v)
+        value = float(np.median(vals))
+        ms_step = 1000.0 * len(graphs) / value
+        step_kind = "EXTRAPOLATED: the oracle on the batch's first graphs per step, scaled to the whole batch"
+        col_bytes = sum(gq.col.nbytes for gq in graphs)
+    elif args.workload == "c1":
+        import oracle
+        g = make_graph("c1")
+        kw = dict(problem=w["laplacian"], precond=w["precond"], tol=w["tol"], seed=w["seed"])
+        for _ in range(args.warmup):
+            oracle.partition(g, w["K"], **kw)
+        times = []
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            oracle.partition(g, w["K"], **kw)
+            times.append(time.perf_counter() - t)
+        ms_step = 1000.0 * float(np.mean(times))
+        value = 1000.0 / ms_step
+        sample = f"whole oracle partitions, one per step (timed, not extrapolated); {ORACLE_THREADS}"
+        step_kind = "one whole oracle partition"
+        col_bytes = g.col.nbytes
+    else:
+        fixed, iters, g = oracle_timed_run(args.workload, args.warmup + args.steps)
+        timed = iters[args.warmup:args.warmup + args.steps]
+        if len(timed) < args.steps:
+            raise SystemExit("the oracle converged before the requested steps; use fewer steps")
+        per_iter = float(np.mean(timed))
+        n_it = oracle_iterations(args.workload) or len(iters)
+        value = 1.0 / (fixed + n_it * per_iter)
+        ms_step = 1000.0 * per_iter
+        sample = (f"one oracle.partition run with the LOBPCG cap at {args.warmup}+{args.steps} iterations: the "
+                  f"first {args.warmup} untimed, the next {args.steps} the timed steps ({per_iter:.2f} s each); "
+                  f"value EXTRAPOLATED to a whole partition = fixed part {fixed:.1f} s (timed in the same run) + "
+                  f"the oracle's own {n_it} iterations (tests/golden/{w['golden']}); {ORACLE_THREADS}")
+        step_kind = "one LOBPCG iteration of the oracle's partition of this workload"
+        col_bytes = g.col.nbytes
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["desc"], "K": w["K"]},
+            "config": config_of(w, precision, col_bytes, world), "step": step_kind,
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": os.cpu_count(),
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -448,9 +575,37 @@ def run_ours(args, world, rank, local):
     info = spx.sphynx_get_info(graph.h)
     schedule = "k_spmm_sell" if (args.spmm_variant or "").startswith("sell") or \
         (args.spmm_variant is None and info["spmm_variant"] == 1) else "k_spmm_short"
-    achieved = by_dt[dom]["gbs"] if dom else None
     kernel_name = f"{schedule}<{dom} in>"
-    traffic = profiled_traffic(f"spmm_{dom}", args.workload) if dom else None
+    traffic, traffic_meta = profiled_traffic(args.workload)
+    # achieved: the scope table's algorithmic bytes of one launch of the
+    # dominant kernel (X read once and written once at the true block width b,
+    # 8-byte row offsets, 4-byte column indices, 4-byte weights if any, the
+    # diagonal) over its mean launch time from CUDA events on its stream
+    roof = None
+    if dom:
+        s = {"f64": 8, "f32": 4, "bf16": 2}[dom]
+        d_true = int(w["K"]).bit_length()
+        sb = survey_bytes(g.n, g.nnz, d_true, s, s, 8 if dom == "f64" else 4, g.w is not None)
+        us = by_dt[dom]["us_per_launch"]
+        achieved = sb / (us * 1e-6) / 1e9
+        layout_gbs = by_dt[dom]["gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "frac_survey": achieved / pk["hbm_gbs"],
+                "frac_of_nominal_8tbs": achieved / 8000.0,
+                "peak_source": pk["src"] + " (MEASURED_PEAKS.json copy bandwidth)" if pk["src"] == "measured"
+                else pk["src"],
+                "kernel": kernel_name, "us_per_launch": us,
+                "algorithmic_bytes_per_launch": sb,
+                "algorithmic_bytes_formula": (f"8(n+1) + nnz(4+s_w) + n b (s_in+s_out) + n s_diag with n={g.n}, "
+                                              f"nnz={g.nnz}, b={d_true}, s_in=s_out={s}, "
+                                              f"s_w={4 if g.w is not None else 0}, "
+                                              f"s_diag={8 if dom == 'f64' else 4}"),
+                "layout_bytes_per_launch": by_dt[dom]["bytes_per_launch"],
+                "achieved_layout": layout_gbs,
+                "frac_layout": layout_gbs / pk["hbm_gbs"] if layout_gbs else None,
+                "traffic": traffic,
+                "traffic_source": (f"profiles/traffic_{args.workload}.json" if traffic is not None else
+                                   ("stale: the SpMM sources changed after the capture" if traffic_meta else None))}
 
     # plain FP64 path at the same tolerance
     fp64 = None
@@ -497,7 +652,8 @@ def run_ours(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, sample, _ = oracle_sample(args.workload)
-        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
+               "threads": {"sparse_products": 1, "dense_blas": os.cpu_count()}}
 
     if rank == 0:
         line = {
@@ -505,10 +661,7 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if precision != "fp64" else "f64",
             "data": "synthetic",
-            "config": {"workload": w["desc"], "K": w["K"], "precision": precision,
-                       "l2": (f"inputs larger than L2 (CSR column array {g.col.nbytes / 1e6:.0f} MB > 129 MB)"
-                              if g.col.nbytes > 129e6 else "inputs within L2, no flush"),
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": config_of(w, precision, g.col.nbytes, world),
             "iterations": last[3]["iterations"], "status": last[0], "cut": last[1], "imbalance": last[2],
             "eigenvalues": last[3]["eigenvalues"],
             "max_resnorm_over_tol_theta": _res_ratio(last[3], w["tol"]),
@@ -517,11 +670,7 @@ def run_ours(args, world, rank, local):
                      "ms_per_step": spmm_ms / args.steps, "by_input_precision": by_dt,
                      "schedule": schedule, "sell_stride": info["sell_stride"] if schedule == "k_spmm_sell" else None},
             "fp64": fp64,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": (achieved / pk["hbm_gbs"]) if achieved else None,
-                         "peak_source": pk["src"], "kernel": kernel_name,
-                         "algorithmic_bytes_per_launch": by_dt[dom]["bytes_per_launch"] if dom else None,
-                         "traffic": traffic},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": world / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + (0 if g.w is None else g.w.nbytes)),
@@ -557,7 +706,17 @@ def main():
                          "(used for profiler captures, where tuning times are distorted)")
     ap.add_argument("--sell-stride", type=int, default=None, choices=[1, 2, 4, 8, 16],
                     help="pin the SELL-32 slice stride instead of the one tuned at create (profiler captures)")
+    ap.add_argument("--ingest-ncu", default=None, metavar="CSV",
+                    help="no benchmark: read the per-launch dram__bytes_read.sum / dram__bytes_write.sum of an ncu "
+                         "--csv log and write profiles/traffic_<workload>.json, which later runs report as "
+                         "roofline.traffic")
+    ap.add_argument("--kernel-regex", default=r"k_spmm_sell<(\(int\))?0, __nv_bfloat16, __nv_bfloat16",
+                    help="kernels of the ncu log that --ingest-ncu averages")
+    ap.add_argument("--ncu-command", default="", help="the ncu command that wrote the log (recorded by --ingest-ncu)")
     args = ap.parse_args()
+    if args.ingest_ncu:
+        print(json.dumps(ingest_ncu(args.ingest_ncu, args.kernel_regex, args.workload, args.ncu_command)))
+        return 0
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)

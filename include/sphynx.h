@@ -92,6 +92,13 @@ extern "C" {
 #define SPHYNX_DT_F64 0
 #define SPHYNX_DT_F32 1
 #define SPHYNX_DT_BF16 2
+/* Convergence test of a Ritz pair (Sec. 6.3.2 names the tolerance, not the
+ * test; x_i is B-normalised): REL_THETA ||r_i||_{B^-1} <= tol |theta_i|, or
+ * ABS ||r_i||_{B^-1} <= tol.  Under both, the eigenvalue-zero vector is also
+ * accepted at the rounding floor (|theta| <= 10 u rho and ||r|| <= 10 u rho
+ * (max degree + 1), rho a Gershgorin bound of the operator). */
+#define SPHYNX_CONV_REL_THETA 0
+#define SPHYNX_CONV_ABS 1
 /* sphynx_options.flags */
 #define SPHYNX_OUT_DEVICE 1u    /* part_out of sphynx_partition is a device pointer */
 
@@ -121,7 +128,8 @@ typedef struct {
                           far, its best residual being under the noise floor
                           10 u rho (FP32 blocks cannot reach tol * theta when
                           that is below the FP32 rounding of L x)             */
-  int32_t reserved[5];
+  int32_t conv;        /* SPHYNX_CONV_REL_THETA (default) | SPHYNX_CONV_ABS     */
+  int32_t reserved[4];
 } sphynx_options;
 
 typedef struct {
@@ -249,14 +257,35 @@ int sphynx_degrees(sphynx_handle g, double *deg_out);
 int sphynx_laplacian_apply(sphynx_handle g, int32_t laplacian, int32_t dtype, const void *x,
                            int32_t ldx, void *y, int32_t ldy, int32_t ncols);
 
+/* One step of the polynomial preconditioner's product form (Sec. 5.2), the
+ * fused kernel every application of the polynomial runs k - 1 times: with t
+ * the input block and L the operator of `laplacian` (L_C for the generalized
+ * problem),
+ *   t_out = t - (L t) / theta_cur
+ * and the accumulator y of p(L) t gathers the step's terms:
+ *   yterms 2: y = (first ? 0 : y) + t / theta_cur + t_out / theta_next
+ *   yterms 1: y = y + t_out / theta_next
+ *   yterms 0: y unchanged.
+ * The terms use the stored (rounded) t_out.  t, t_out: device n x ld blocks
+ * (ld = round4(ncols), rows exactly ld apart) of dtype_in / dtype_out: F64 ->
+ * F64, F32 -> F32 or BF16, BF16 -> BF16; y: device n x ld block of double (F64)
+ * or float.  Float and bfloat16 steps multiply by the float-rounded
+ * reciprocals of the roots and accumulate in float.  first = 1 needs
+ * yterms = 2.  Synchronises the handle's stream.  Errors: INVALID_ARG,
+ * ISOLATED. */
+int sphynx_poly_step(sphynx_handle g, int32_t laplacian, int32_t dtype_in, const void *t, int32_t dtype_out,
+                     void *t_out, void *y, int32_t ld, int32_t ncols, double theta_cur, double theta_next,
+                     int32_t yterms, int32_t first);
+
 /* Set up the preconditioner of `opt` (Sec. 5) and, for the polynomial,
  * return its roots theta_1..theta_k in application order (harmonic Ritz
  * values of k Lanczos steps, Leja ordered) in host double[poly_degree]
  * (may be NULL).  For multigrid, build the level hierarchy for opt->seed
- * (kept by the handle and reused while the seed is the same); errors:
- * UNSUPPORTED when an aggregate's rows hold more than 8192 entries (graphs
- * with hubs of that size take Jacobi or the polynomial).  Jacobi and none
- * need no setup. */
+ * (kept by the handle and reused while the seed is the same); a coarse row
+ * sorts its entries in shared memory when its aggregate's rows hold at most
+ * 8192 of them and in global scratch (chunks of at most 512 MiB) otherwise;
+ * errors: UNSUPPORTED when an aggregate's rows hold 2^31 or more entries.
+ * Jacobi and none need no setup. */
 int sphynx_precond_setup(sphynx_handle g, const sphynx_options *opt, double *roots_out);
 
 /* H = M R for the preconditioner set up by the last sphynx_precond_setup
@@ -331,20 +360,24 @@ int sphynx_eigensolve(sphynx_handle g, const sphynx_options *opt, int32_t nev, c
 int sphynx_mj(int32_t dtype, const void *coords, int32_t ldc, int32_t dims, int64_t n,
               const int64_t *vtx_w, int32_t K, int32_t *part_out, void *stream);
 
-/* sphynx_mj without any device allocation (the paper has no counterpart;
- * this serves callers that cannot let a library call cudaMalloc, such as
- * frameworks that own the whole device memory pool through their own
- * allocator, or latency-bound loops that must not pay cudaMalloc's cost and
- * its implicit synchronisation).  Same arguments, same bit-exact result as
- * sphynx_mj; part_out and every input stay caller-owned.  Scratch lives in a
- * fixed 16 MiB array in device memory that every GPU loading the library
- * holds until the process exits; calls needing more (roughly
+/* sphynx_mj without any device allocation (the paper has no counterpart).
+ * It serves callers that cannot let a library allocate device memory: a
+ * framework whose own caching allocator has already reserved the device's
+ * memory, or an application that budgets all device memory at start-up and
+ * allows no allocation afterwards.  Same arguments and the same bit-exact
+ * result as sphynx_mj; part_out and every input stay caller-owned.  Scratch
+ * lives in a fixed 16 MiB array in device memory that every GPU loading the
+ * library holds until the process exits; calls needing more (roughly
  * 8 n + 5200 K bytes; n <= 2^20 with K <= 1024 fits) fail with
- * SPHYNX_ERR_UNSUPPORTED.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and should therefore come before any
- * stream capture.  All calls share the one array and each call clears what
- * it needs cleared: calls whose GPU work overlaps (different streams, or
- * concurrent host threads) race and must be serialised by the caller. */
+ * SPHYNX_ERR_UNSUPPORTED, as K > 2^20 does in both entry points.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should therefore come before any stream
+ * capture.  Like sphynx_mj, every call reads two values back to the host (a
+ * NaN / vertex-weight flag and the total vertex weight), so it synchronises
+ * `stream` twice, and it uploads its section tables from pageable host
+ * memory.  All calls share the one array and each call clears what it needs
+ * cleared: calls whose GPU work overlaps (different streams, or concurrent
+ * host threads) race and must be serialised by the caller. */
 int sphynx_mj_noalloc(int32_t dtype, const void *coords, int32_t ldc, int32_t dims, int64_t n,
                       const int64_t *vtx_w, int32_t K, int32_t *part_out, void *stream);
 

@@ -27,7 +27,8 @@ eigenvector of the projected problem is given the sign that makes its entry
 of largest magnitude positive (first such entry on ties).
 
 Convergence (the paper names the tolerance but not the test): column i has
-converged when ||r_i||_{B^-1} <= tol |theta_i|, or when |theta_i| <= 10 u_work
+converged when ||r_i||_{B^-1} <= tol |theta_i| (conv="rel_theta", the default;
+conv="abs" asks ||r_i||_{B^-1} <= tol instead), or when |theta_i| <= 10 u_work
 rho and ||r_i||_{B^-1} <= 10 u_work rho t, with rho = 2 for L_N and the
 generalized problem and 2 max deg for L_C (a Gershgorin bound) and t the most
 terms in a row of L (max degree + 1); x_i is B-normalised by RR.  The theta
@@ -116,12 +117,19 @@ def residual_norms(r: np.ndarray, bdiag) -> np.ndarray:
 
 
 def lobpcg(apply_l, bdiag, apply_m, x0: np.ndarray, tol: float, maxit: int,
-           rho: float, u_work: float = U_FP64, row_terms: int = 1) -> LobpcgResult:
+           rho: float, u_work: float = U_FP64, row_terms: int = 1, conv: str = "rel_theta",
+           on_iteration=None) -> LobpcgResult:
     """Algorithm 1 for the nev = x0.shape[1] smallest eigenpairs of L x = lambda B x.
 
     apply_l(V): L V;  bdiag: diagonal of B or None;  apply_m(R): preconditioner
     (None for no preconditioning);  rho: the Gershgorin bound used by the
-    noise floor;  row_terms: the most terms in a row of L (max degree + 1)."""
+    noise floor;  row_terms: the most terms in a row of L (max degree + 1);
+    conv: "rel_theta" or "abs" (see the module notes);  on_iteration(it): an
+    optional callback before the first iteration (it = 0) and after every
+    iteration it (timing only, no effect on the arithmetic)."""
+    if conv not in ("rel_theta", "abs"):
+        raise ValueError(conv)
+    abs_test = conv == "abs"
     n, nev = x0.shape
 
     def bmul(v):
@@ -132,7 +140,8 @@ def lobpcg(apply_l, bdiag, apply_m, x0: np.ndarray, tol: float, maxit: int,
 
     def test(r, th):
         res = residual_norms(r, bdiag)
-        return res, (res <= tol * np.abs(th)) | ((np.abs(th) <= floor_th) & (res <= floor_res))
+        bound = tol if abs_test else tol * np.abs(th)
+        return res, (res <= bound) | ((np.abs(th) <= floor_th) & (res <= floor_res))
 
     # start and first residual
     lx0 = apply_l(x0)
@@ -145,6 +154,8 @@ def lobpcg(apply_l, bdiag, apply_m, x0: np.ndarray, tol: float, maxit: int,
     p = np.zeros((n, 0))
     lp = np.zeros((n, 0))
     it = 0
+    if on_iteration is not None:
+        on_iteration(0)
     while not conv.all() and it < maxit:
         idx = np.nonzero(~conv)[0]
         ri = r[:, idx]
@@ -165,5 +176,7 @@ def lobpcg(apply_l, bdiag, apply_m, x0: np.ndarray, tol: float, maxit: int,
         lp = ls @ yp
         x, lx = xn, lxn
         it += 1
+        if on_iteration is not None:
+            on_iteration(it)
     return LobpcgResult(x=x, theta=th, resnorm=res, converged=conv, iterations=it,
                         svqb_steps=svqb_steps, status="ok" if conv.all() else "noconv")

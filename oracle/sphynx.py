@@ -146,7 +146,8 @@ class PartitionResult:
 
 def partition(g, num_parts: int, problem: str = COMBINATORIAL, precond: str = "jacobi",
               tol: float = 1e-3, maxit: int = 1000, init: str = "random", seed: int = 1,
-              poly_degree: int = 25, vwts=None, u_work: float = U_FP64) -> PartitionResult:
+              poly_degree: int = 25, vwts=None, u_work: float = U_FP64, conv: str = "rel_theta",
+              on_iteration=None) -> PartitionResult:
     """K-way partition of g by Algorithm 2."""
     if num_parts == 1:
         z = np.zeros(g.n, dtype=np.int32)
@@ -182,7 +183,8 @@ def partition(g, num_parts: int, problem: str = COMBINATORIAL, precond: str = "j
     else:
         raise ValueError(precond)
     x0 = initial_block(g, problem, d, init, seed)
-    res = lobpcg(apply_l, bdiag, apply_m, x0, tol, maxit, gershgorin_rho(g, problem), u_work, max_row_terms(g))
+    res = lobpcg(apply_l, bdiag, apply_m, x0, tol, maxit, gershgorin_rho(g, problem), u_work, max_row_terms(g),
+                 conv, on_iteration)
     e = sign_normalise(canonical_rotation(res.x, res.theta, tol, seed))
     coords = np.ascontiguousarray(e[:, 1:d])
     parts = multijagged(coords, vwts, num_parts)

@@ -25,6 +25,7 @@ COMBINATORIAL, GENERALIZED, NORMALIZED = 0, 1, 2
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_POLY, PRECOND_AMG = 0, 1, 2, 3
 FP64, FP32, MIXED_BF16 = 0, 1, 2
 INIT_RANDOM, INIT_PIECEWISE = 0, 1
+CONV_REL_THETA, CONV_ABS = 0, 1
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 OUT_DEVICE = 1
 MAX_NEV = 16
@@ -34,13 +35,15 @@ LAPLACIANS = {"combinatorial": COMBINATORIAL, "generalized": GENERALIZED, "norma
 PRECONDS = {"none": PRECOND_NONE, "jacobi": PRECOND_JACOBI, "poly": PRECOND_POLY, "amg": PRECOND_AMG}
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed_bf16": MIXED_BF16}
 INITS = {"random": INIT_RANDOM, "piecewise": INIT_PIECEWISE}
+CONVS = {"rel_theta": CONV_REL_THETA, "abs": CONV_ABS}
 
 
 class Options(C.Structure):
     _fields_ = [("laplacian", C.c_int32), ("precond", C.c_int32), ("poly_degree", C.c_int32),
                 ("precision", C.c_int32), ("init", C.c_int32), ("max_iter", C.c_int32),
                 ("tol", C.c_double), ("seed", C.c_uint64), ("flags", C.c_uint32),
-                ("sync_every", C.c_int32), ("stall_window", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("sync_every", C.c_int32), ("stall_window", C.c_int32), ("conv", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class Stats(C.Structure):
@@ -91,6 +94,7 @@ def _load():
         "sphynx_degrees": (C.c_int, [vp, vp]),
         "sphynx_laplacian_apply": (C.c_int, [vp, i32, i32, vp, i32, vp, i32, i32]),
         "sphynx_precond_setup": (C.c_int, [vp, C.POINTER(Options), pd]),
+        "sphynx_poly_step": (C.c_int, [vp, i32, i32, vp, i32, vp, vp, i32, i32, dbl, dbl, i32, i32]),
         "sphynx_precond_apply": (C.c_int, [vp, C.POINTER(Options), vp, vp, i32, i32]),
         "sphynx_gram": (C.c_int, [i32, C.POINTER(vp), C.POINTER(vp), i32, i32, i64, vp, pd, pd, vp]),
         "sphynx_rayleigh_ritz": (C.c_int, [pd, pd, pi32, i32, i32, dbl, pd, pd, pi32, vp]),
@@ -151,7 +155,8 @@ def _dptr(a: np.ndarray):
 
 
 def options(laplacian="combinatorial", precond="jacobi", poly_degree=25, precision="fp64", init="random",
-            max_iter=1000, tol=1e-3, seed=1, out_device=False, sync_every=0, stall_window=0) -> Options:
+            max_iter=1000, tol=1e-3, seed=1, out_device=False, sync_every=0, stall_window=0,
+            conv="rel_theta") -> Options:
     o = Options()
     LIB.sphynx_default_options(C.byref(o))
     o.laplacian = LAPLACIANS.get(laplacian, laplacian)
@@ -165,6 +170,7 @@ def options(laplacian="combinatorial", precond="jacobi", poly_degree=25, precisi
     o.flags = OUT_DEVICE if out_device else 0
     o.sync_every = sync_every
     o.stall_window = stall_window
+    o.conv = CONVS.get(conv, conv)
     return o
 
 
@@ -230,6 +236,12 @@ def sphynx_degrees(h, deg_out) -> None:
 def sphynx_laplacian_apply(h, laplacian, dtype, x, ldx, y, ldy, ncols) -> None:
     check(LIB.sphynx_laplacian_apply(h, LAPLACIANS.get(laplacian, laplacian), dtype, ptr(x), ldx, ptr(y), ldy,
                                      ncols))
+
+
+def sphynx_poly_step(h, laplacian, dtype_in, t, dtype_out, t_out, y, ld, ncols, theta_cur, theta_next, yterms,
+                     first=0) -> None:
+    check(LIB.sphynx_poly_step(h, LAPLACIANS.get(laplacian, laplacian), dtype_in, ptr(t), dtype_out, ptr(t_out),
+                               ptr(y), ld, ncols, float(theta_cur), float(theta_next), yterms, first))
 
 
 def sphynx_precond_setup(h, opt: Options) -> np.ndarray:

@@ -29,6 +29,8 @@
 // by sorting (column, position) keys.
 #include "internal.cuh"
 
+#include <algorithm>
+
 #include <cmath>
 #include <vector>
 
@@ -723,17 +725,42 @@ void coarse_level(AmgLevel &L, AmgLevel &C) {
     SPX_CUDA(cudaStreamSynchronize(st));   // `order` feeds an asynchronous copy
   }
   if (!large.empty()) {
-    int64_t cap = 64;
-    while (cap < mx_l) cap <<= 1;
+    // hub aggregates sort in global scratch, grouped by their own power-of-two
+    // capacity and launched in chunks whose scratch (12 bytes a key slot) stays
+    // within a fixed budget, so that a few huge aggregates cannot size the
+    // scratch of all the others
+    constexpr size_t kHubBudget = size_t(512) << 20;
+    std::vector<std::pair<int64_t, int32_t>> byc;   // (cap, aggregate), caps increasing
+    byc.reserve(large.size());
+    int64_t capmax = 64;
+    for (int32_t I : large) {
+      int64_t cap = 64;
+      while (cap < hent[static_cast<size_t>(I)]) cap <<= 1;
+      byc.emplace_back(cap, I);
+      capmax = cap > capmax ? cap : capmax;
+    }
+    std::sort(byc.begin(), byc.end());
+    std::vector<int32_t> order(byc.size());
+    for (size_t q = 0; q < byc.size(); ++q) order[q] = byc[q].second;
+    SPX_CUDA(cudaMemcpyAsync(llarge, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const size_t slot = sizeof(unsigned long long) + sizeof(float);
+    const size_t budget = std::max(kHubBudget, static_cast<size_t>(capmax) * slot);
     DevBuf gk, gwb;
-    gk.alloc(large.size() * static_cast<size_t>(cap) * sizeof(unsigned long long));
-    gwb.alloc(large.size() * static_cast<size_t>(cap) * sizeof(float));
-    k_coarse_row<1024><<<static_cast<unsigned>(large.size()), 1024, 0, st>>>(
-        llarge, L.mem_ptr.as<int64_t>(), L.mem.as<int32_t>(), g->rowptr, g->col, g->w, L.agg.as<int32_t>(), cap,
-        rc.as<int64_t>(), rs.as<int64_t>(), cur.as<unsigned long long>(), tcol.as<int32_t>(), tw.as<float>(),
-        gk.as<unsigned long long>(), gwb.as<float>());
-    SPX_LAUNCHED();
-    SPX_CUDA(cudaStreamSynchronize(st));   // the scratch is freed when this scope ends
+    gk.alloc(budget / slot * sizeof(unsigned long long));
+    gwb.alloc(budget / slot * sizeof(float));
+    for (size_t q0 = 0; q0 < byc.size();) {
+      const int64_t cap = byc[q0].first;
+      const size_t per = std::max<size_t>(1, budget / (static_cast<size_t>(cap) * slot));
+      size_t q1 = q0;
+      while (q1 < byc.size() && byc[q1].first == cap && q1 - q0 < per) ++q1;
+      k_coarse_row<1024><<<static_cast<unsigned>(q1 - q0), 1024, 0, st>>>(
+          llarge + q0, L.mem_ptr.as<int64_t>(), L.mem.as<int32_t>(), g->rowptr, g->col, g->w, L.agg.as<int32_t>(),
+          cap, rc.as<int64_t>(), rs.as<int64_t>(), cur.as<unsigned long long>(), tcol.as<int32_t>(), tw.as<float>(),
+          gk.as<unsigned long long>(), gwb.as<float>());
+      SPX_LAUNCHED();
+      q0 = q1;
+    }
+    SPX_CUDA(cudaStreamSynchronize(st));   // `order` feeds an asynchronous copy; the scratch is freed below
   }
   C.rowptr.alloc((nc + 1) * sizeof(int64_t));
   const int64_t nnz = scan_excl(st, rc.as<int64_t>(), C.rowptr.as<int64_t>(), nc);

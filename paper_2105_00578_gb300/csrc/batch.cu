@@ -248,7 +248,7 @@ k_bresidual(ChunkView cv, const SolverState *states, const T *x, const T *lx, co
 __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int count, const double *partials, int b,
                             int ld, double tol, double u_work, int rho_from_degree,
                             const unsigned long long *gmax, int count_iteration, int maxit, int stall_window,
-                            int *ctl) {
+                            int abs_test, int *ctl) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
   SolverState *st = states + q;
@@ -264,7 +264,7 @@ __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int cou
     const double res = sqrt(tot);
     st->resnorm[j] = res;
     const double th = fabs(st->theta[j]);
-    const bool ok = (res <= tol * th) || (th <= floor_th && res <= floor_res);
+    const bool ok = (res <= (abs_test ? tol : tol * th)) || (th <= floor_th && res <= floor_res);
     st->conv[j] = ok ? 1 : 0;
     nconv += ok ? 1 : 0;
   }
@@ -647,7 +647,8 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   auto converge = [&](int count_iteration) {
     k_bconverge<<<(count + 127) / 128, 128, 0, st>>>(gc0, states, count, npart, b, ld, o->tol, u_work, rho_from_degree,
                                                       B.graph_max.as<unsigned long long>(),
-                                                      count_iteration, o->max_iter, o->stall_window, ctl);
+                                                      count_iteration, o->max_iter, o->stall_window,
+                                                      o->conv == SPHYNX_CONV_ABS ? 1 : 0, ctl);
     SPX_LAUNCHED();
   };
   auto spmm_block = [&](const void *x, void *y) {

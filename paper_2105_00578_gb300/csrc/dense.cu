@@ -202,11 +202,12 @@ k_residual(int64_t n, const T *x, const T *lx, const double *theta, const T *bdi
   }
 }
 
-// Convergence test (Algorithm 1, soft locking): ||r||_{B^-1} <= tol |theta|, or
-// |theta| <= floor_th and ||r||_{B^-1} <= floor_res (the eigenvalue-zero vector).
+// Convergence test (Algorithm 1, soft locking): ||r||_{B^-1} <= tol |theta|
+// (abs_test: <= tol), or |theta| <= floor_th and ||r||_{B^-1} <= floor_res (the
+// eigenvalue-zero vector).
 __global__ void k_converge(SolverState *st, const double *partials, int grid, int b, int ld,
                            double tol, double floor_th, double floor_res, int count_iteration, int maxit,
-                           int stall_window) {
+                           int stall_window, int abs_test) {
   __shared__ double part[16][17];
   if (st->done) return;
   const int t = threadIdx.x;     // 256 threads: column t % 16, stripe t / 16
@@ -225,7 +226,7 @@ __global__ void k_converge(SolverState *st, const double *partials, int grid, in
       st->resnorm[j] = res;
       // the floor only admits the eigenvalue-zero vector (|theta| itself below it)
       const double th = fabs(st->theta[j]);
-      const bool ok = (res <= tol * th) || (th <= floor_th && res <= floor_res);
+      const bool ok = (res <= (abs_test ? tol : tol * th)) || (th <= floor_th && res <= floor_res);
       st->conv[j] = ok ? 1 : 0;
       nconv += ok ? 1 : 0;
     }
@@ -711,9 +712,9 @@ void launch_residual(cudaStream_t st, const ResidualArgs &a, int grid) {
 
 void launch_converge(cudaStream_t st, SolverState *state, const double *partials, int grid, int b,
                      int ld, double tol, double floor_th, double floor_res, int count_iteration, int maxit,
-                     int stall_window) {
+                     int stall_window, int abs_test) {
   k_converge<<<1, 256, 0, st>>>(state, partials, grid, b, ld, tol, floor_th, floor_res, count_iteration, maxit,
-                                stall_window);
+                                stall_window, abs_test);
   SPX_LAUNCHED();
 }
 

@@ -594,6 +594,7 @@ void sphynx_default_options(sphynx_options *opt) {
   opt->seed = 1;
   opt->flags = 0;
   opt->sync_every = 0;
+  opt->conv = SPHYNX_CONV_REL_THETA;
 }
 
 int sphynx_create(const int64_t *row_ptr, const int32_t *col, const float *edge_w, const int64_t *vtx_w,

@@ -364,7 +364,7 @@ __device__ inline bool stall_check(SolverState *st, int b, int window, int count
 
 void launch_converge(cudaStream_t st, SolverState *state, const double *partials, int grid, int b,
                      int ld, double tol, double floor_th, double floor_res, int count_iteration, int maxit,
-                     int stall_window = 0);
+                     int stall_window = 0, int abs_test = 0);
 
 void launch_signs_coords(cudaStream_t st, DT dt, const void *x, int64_t n, int ld, int b,
                          void *coords, double *scratch);

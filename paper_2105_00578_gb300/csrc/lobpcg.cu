@@ -48,6 +48,7 @@ void check_options(const sphynx_graph *g, const sphynx_options *o) {
     fail(SPHYNX_ERR_INVALID_ARG, "poly_degree %d", o->poly_degree);
   if (o->max_iter < 0) fail(SPHYNX_ERR_INVALID_ARG, "max_iter < 0");
   if (o->stall_window < 0) fail(SPHYNX_ERR_INVALID_ARG, "stall_window < 0");
+  if (o->conv != SPHYNX_CONV_REL_THETA && o->conv != SPHYNX_CONV_ABS) fail(SPHYNX_ERR_INVALID_ARG, "conv %d", o->conv);
   if (!(o->tol >= 0.0)) fail(SPHYNX_ERR_INVALID_ARG, "tol");
   if (o->laplacian != SPHYNX_COMBINATORIAL && g->isolated > 0)
     fail(SPHYNX_ERR_ISOLATED, "%lld vertices without edges: the %s problem needs deg > 0",
@@ -305,7 +306,8 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   ResidualArgs ra{dt, ld, n, X[1], LX[1], state->theta, bd, bdf, jac ? g->jinv.as<double>() : nullptr,
                   jac ? g->jinvf.as<float>() : nullptr, res_out, npart, done};
   launch_residual(st, ra, rgrid);
-  launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_th, floor_res, 0, o->max_iter);
+  const int abs_test = o->conv == SPHYNX_CONV_ABS ? 1 : 0;
+  launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_th, floor_res, 0, o->max_iter, 0, abs_test);
   g->ctr.launches += 8;
 
   int sync_every = o->sync_every;
@@ -330,7 +332,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
     r3.lx = LX[nx];
     launch_residual(st, r3, rgrid);
     launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_th, floor_res, 1, o->max_iter,
-                    o->stall_window);  // lock
+                    o->stall_window, abs_test);  // lock
     g->ctr.launches += 6;
     cur = nx;
     if ((it + 1) % sync_every == 0 || it + 1 == o->max_iter) {
@@ -516,6 +518,53 @@ int sphynx_laplacian_apply(sphynx_handle g, int32_t laplacian, int32_t dtype, co
     a.x = x;
     a.y = y;
     spmm(g, a);
+    return SPHYNX_OK;
+  });
+}
+
+int sphynx_poly_step(sphynx_handle g, int32_t laplacian, int32_t dtype_in, const void *t, int32_t dtype_out,
+                     void *t_out, void *y, int32_t ld, int32_t ncols, double theta_cur, double theta_next,
+                     int32_t yterms, int32_t first) {
+  return guarded([&]() -> int {
+    if (!g || !t || !t_out || !y) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
+    if (laplacian < 0 || laplacian > 2) fail(SPHYNX_ERR_INVALID_ARG, "laplacian %d", laplacian);
+    if (dtype_in < 0 || dtype_in > 2 || dtype_out < 0 || dtype_out > 2)
+      fail(SPHYNX_ERR_INVALID_ARG, "dtype %d -> %d", dtype_in, dtype_out);
+    const bool ok_types = (dtype_in == SPHYNX_DT_F64 && dtype_out == SPHYNX_DT_F64) ||
+                          (dtype_in == SPHYNX_DT_F32 && dtype_out != SPHYNX_DT_F64) ||
+                          (dtype_in == SPHYNX_DT_BF16 && dtype_out == SPHYNX_DT_BF16);
+    if (!ok_types) fail(SPHYNX_ERR_INVALID_ARG, "chain types %d -> %d", dtype_in, dtype_out);
+    if (ncols < 1 || ncols > SPHYNX_MAX_NEV || ld != round4(ncols))
+      fail(SPHYNX_ERR_INVALID_ARG, "ncols %d / ld %d (ld must be round4(ncols))", ncols, ld);
+    if (!(theta_cur != 0.0) || !(theta_next != 0.0) || !std::isfinite(theta_cur) || !std::isfinite(theta_next))
+      fail(SPHYNX_ERR_INVALID_ARG, "roots must be finite and nonzero");
+    if (laplacian != SPHYNX_COMBINATORIAL && g->isolated > 0) fail(SPHYNX_ERR_ISOLATED, "vertex without edges");
+    double *inv = static_cast<double *>(g->workspace("ps_inv", 4 * sizeof(double), false));
+    float *invf = static_cast<float *>(g->workspace("ps_invf", 4 * sizeof(float), false));
+    const double hinv[2] = {1.0 / theta_cur, 1.0 / theta_next};
+    const float hinvf[2] = {static_cast<float>(hinv[0]), static_cast<float>(hinv[1])};
+    SPX_CUDA(cudaMemcpyAsync(inv, hinv, sizeof(hinv), cudaMemcpyHostToDevice, g->stream));
+    SPX_CUDA(cudaMemcpyAsync(invf, hinvf, sizeof(hinvf), cudaMemcpyHostToDevice, g->stream));
+    SpmmArgs a{};
+    a.lap = op_of(laplacian);
+    a.tin = static_cast<DT>(dtype_in);
+    a.ld_x = ld;
+    a.ld_y = ld;
+    a.bp = ld;
+    a.b_true = ncols;
+    a.x = t;
+    a.mode = 1;
+    a.t_out = t_out;
+    a.tout = static_cast<DT>(dtype_out);
+    a.yacc = y;
+    a.first = first;
+    a.yterms = yterms;
+    a.inv = inv;
+    a.invf = invf;
+    a.i_cur = 0;
+    spmm(g, a);
+    // the host arrays above must outlive their asynchronous copies
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
     return SPHYNX_OK;
   });
 }

@@ -559,6 +559,10 @@ extern "C" int sphynx_mj(int32_t dtype, const void *coords, int32_t ldc, int32_t
     if (n > 0 && (!coords || !part_out)) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
     if (ldc < dims) fail(SPHYNX_ERR_INVALID_ARG, "ldc < dims");
     if (dtype != SPHYNX_DT_F32 && dtype != SPHYNX_DT_F64) fail(SPHYNX_ERR_INVALID_ARG, "dtype");
+    // sizes are checked before the scratch is sized from them
+    if (n < 0) fail(SPHYNX_ERR_INVALID_ARG, "n < 0");
+    if (K < 1) fail(SPHYNX_ERR_INVALID_ARG, "K must be >= 1");
+    if (K > (1 << 20)) fail(SPHYNX_ERR_UNSUPPORTED, "K > 2^20");
     if (n >= (1LL << 31)) fail(SPHYNX_ERR_UNSUPPORTED, "n >= 2^31");
     run_mj(static_cast<cudaStream_t>(stream), static_cast<DT>(dtype), coords, ldc, dims, n, vtx_w, K, part_out,
            nullptr);
@@ -568,13 +572,14 @@ extern "C" int sphynx_mj(int32_t dtype, const void *coords, int32_t ldc, int32_t
 
 // ---- multi-jagged without any device allocation ------------------------------
 //
-// Some callers cannot let a library call cudaMalloc: frameworks that own the
-// whole device memory pool through their own allocator, and latency-bound
-// loops that must not pay cudaMalloc's cost or its implicit device-wide
-// synchronisation.  For them sphynx_mj_noalloc does the same work as
+// Some callers cannot let a library call cudaMalloc: a framework whose own
+// caching allocator has already reserved the device's memory, or an
+// application that budgets all device memory at start-up and allows no
+// allocation afterwards.  For them sphynx_mj_noalloc does the same work as
 // sphynx_mj with its scratch (permutations, histograms, section tables) in
 // this file-scope device array.  Every GPU that loads the library holds the
-// array until the process exits.
+// array until the process exits.  The call still synchronises its stream
+// twice (run_mj_scratch reads a flag and the total vertex weight back).
 
 constexpr size_t kMjStaticBytes = size_t(16) << 20;   // 16 MiB
 static __device__ __align__(256) unsigned char g_mj_static_scratch[kMjStaticBytes];
@@ -614,7 +619,8 @@ extern "C" int sphynx_mj_noalloc(int32_t dtype, const void *coords, int32_t ldc,
     if (ldc < dims) fail(SPHYNX_ERR_INVALID_ARG, "ldc < dims");
     if (dtype != SPHYNX_DT_F32 && dtype != SPHYNX_DT_F64) fail(SPHYNX_ERR_INVALID_ARG, "dtype");
     if (n < 0) fail(SPHYNX_ERR_INVALID_ARG, "n < 0");
-    if (K < 1 || K > (1 << 20)) fail(SPHYNX_ERR_INVALID_ARG, "K must be in [1, 2^20]");
+    if (K < 1) fail(SPHYNX_ERR_INVALID_ARG, "K must be >= 1");
+    if (K > (1 << 20)) fail(SPHYNX_ERR_UNSUPPORTED, "K > 2^20");
     const size_t need = mj_scratch_bytes(n, K, 1);
     if (need > kMjStaticBytes)
       fail(SPHYNX_ERR_UNSUPPORTED,

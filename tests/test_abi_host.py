@@ -32,7 +32,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("sphynx_create", "sphynx_partition", "sphynx_eval", "sphynx_destroy", "sphynx_last_error",
                      "sphynx_laplacian_apply", "sphynx_mj", "sphynx_gram", "sphynx_rayleigh_ritz",
-                     "sphynx_eigensolve", "sphynx_precond_setup", "sphynx_precond_apply"):
+                     "sphynx_eigensolve", "sphynx_precond_setup", "sphynx_precond_apply", "sphynx_poly_step",
+                     "sphynx_mj_noalloc"):
         assert required in names
 
 
@@ -49,6 +50,7 @@ def test_default_options_and_error_string(lib_path):
     assert (o.laplacian, o.precond, o.poly_degree, o.precision, o.init, o.max_iter) == (
         spx.COMBINATORIAL, spx.PRECOND_JACOBI, 25, spx.FP64, spx.INIT_RANDOM, 1000)
     assert o.tol == 1e-3
+    assert o.conv == spx.CONV_REL_THETA and o.stall_window == 0
     assert spx.last_error() == ""
     # struct layouts agree with the header's field order and sizes
     assert ctypes.sizeof(spx.Options) == 4 * 6 + 8 + 8 + 4 + 4 + 4 * 6

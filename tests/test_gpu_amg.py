@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 import oracle.amg as A
 import workloads as W
-from gpu_helpers import dev_block, rel_err, torch_mod
+from gpu_helpers import assert_elementwise, dev_block, torch_mod
 
 pytestmark = pytest.mark.gpu
 
@@ -20,6 +20,9 @@ def graphs():
         "grid27": W.grid3d(31, 29, 27, 27),                           # 24,273 vertices: three levels
         "weighted": W.random_edge_weights(W.grid2d(80, 61), 0.5, 1.5, 8),
         "rmat": W.rmat(13, seed=7),                                   # irregular, small hubs
+        # a dozen aggregates hold more than 8192 entries (up to 340,000): their
+        # coarse rows sort in global scratch, grouped by their own size class
+        "rmat16": W.rmat(16, seed=7),
     }
 
 
@@ -75,11 +78,12 @@ def test_hierarchy_matches_the_oracle_level_by_level(name):
         spx.sphynx_destroy(h)
 
 
-@pytest.mark.parametrize("name", ["grid2d", "grid27", "weighted", "rmat", "star"])
+@pytest.mark.parametrize("name", ["grid2d", "grid27", "weighted", "rmat", "rmat16", "star"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_one_vcycle_matches_the_oracle(name, precision):
     """"star": one aggregate holds the whole graph (its 18,000 entries take the
-    global-memory sort) and the coarse level has no edges."""
+    global-memory sort) and the coarse level has no edges.  "rmat16": a dozen
+    hub aggregates of up to 340,000 entries sort in global scratch."""
     import paper_2105_00578_gb300 as spx
     torch = torch_mod()
     g = W.star_graph(9001) if name == "star" else GRAPHS[name]
@@ -101,10 +105,14 @@ def test_one_vcycle_matches_the_oracle(name, precision):
             rin = rd.double().cpu().numpy()[:, :ncols]
             ref = A.vcycle(levels, rin)
             got = hd.double().cpu().numpy()
-            # the library stores coarse edge weights in float (its edge-weight type):
-            # exact for unit fine weights, one float rounding per coarse weight otherwise
-            tol = (1e-9 if g.w is None else 1e-6) if precision == "fp64" else 2e-5
-            assert rel_err(got[:, :ncols], ref) < tol, (ncols, rel_err(got[:, :ncols], ref))
+            # element by element, against each column's largest entry (a V-cycle
+            # mixes every entry with its neighbourhood, so no entry has a scale
+            # of its own).  The library stores coarse edge weights in float (its
+            # edge-weight type): exact for unit fine weights, one float rounding
+            # per coarse weight otherwise
+            tol = (1e-8 if g.w is None else 1e-5) if precision == "fp64" else 2e-4
+            colmax = np.max(np.abs(ref), axis=0, keepdims=True)
+            assert_elementwise(got[:, :ncols], ref, tol * colmax, f"{name} {precision} ncols {ncols}")
             assert np.all(got[:, ncols:] == 0)                        # zero padding columns stay zero
     finally:
         spx.sphynx_destroy(h)
@@ -150,3 +158,4 @@ def test_multigrid_rejects_what_it_does_not_cover():
         assert e.value.code == spx.ERR_INVALID_ARG
     finally:
         spx.sphynx_destroy(h)
+

@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_helpers import bf16_round, dev_block, rel_err, torch_mod
+from gpu_helpers import abs_operator, assert_elementwise, bf16_round, dev_block, spmm_bound, torch_mod
 
 pytestmark = pytest.mark.gpu
 
@@ -49,8 +49,12 @@ def test_spmm_matches_oracle(gname, lap, dtype, ncols):
         y = torch.zeros((g.n, ld), dtype=ydt, device="cuda")
         dt = {"f64": spx.DT_F64, "f32": spx.DT_F32, "bf16": spx.DT_BF16}[dtype]
         xin = x if dtype == "f64" else (x.astype(np.float32).astype(np.float64) if dtype == "f32" else bf16_round(x))
-        ref = O.operator_for(g, lap) @ xin
-        tol = 1e-13 if dtype == "f64" else 2e-6
+        lmat = O.operator_for(g, lap)
+        ref = lmat @ xin
+        # element by element: the rounding bound of each row's sum (FP64: both
+        # the library's and the oracle's own rounding)
+        u = 2.0 ** -53 if dtype == "f64" else 2.0 ** -24
+        bound = spmm_bound(lmat, xin, u, c=3.0 if dtype == "f64" else 2.0)
         # every short-row schedule and, on graphs with longer rows, every
         # medium-row ceiling the autotuner chooses from
         ceilings = (32, 128, 4096) if int(g.degrees().max()) > 32 else (4096,)
@@ -65,7 +69,7 @@ def test_spmm_matches_oracle(gname, lap, dtype, ncols):
                 spx.sphynx_laplacian_apply(h, lap, dt, xd, ld, y, ld, ncols)
                 torch.cuda.synchronize()
                 got = y.cpu().numpy().astype(np.float64)[:, :ncols]
-                assert rel_err(got, ref) < tol, (variant, stride, med_max)
+                assert_elementwise(got, ref, bound, f"variant {variant} stride {stride} med_max {med_max}")
                 if variant == 1 and stride == 1:
                     first = got
                 elif variant == 1:
@@ -219,11 +223,16 @@ def test_full_size_27_point_mesh_sampled_rows():
             rows = np.concatenate([np.arange(5), rng.integers(0, g.n, 2000), [g.n - 1]])
             got = y.cpu().numpy().astype(np.float64)[rows, :7]
             ref = np.zeros_like(got)
+            mag = np.zeros_like(got)
             for k, i in enumerate(rows):
                 nb = g.col[g.row_ptr[i]:g.row_ptr[i + 1]]
                 ref[k] = len(nb) * xin[i] - xin[nb].sum(axis=0)
-            tol = 1e-13 if dtype == "f64" else 2e-6
-            assert rel_err(got, ref) < tol
+                mag[k] = len(nb) * np.abs(xin[i]) + np.abs(xin[nb]).sum(axis=0)
+            # element by element: c (t + 6) u (|L| |X|) for the row's t terms
+            u = 2.0 ** -53 if dtype == "f64" else 2.0 ** -24
+            terms = np.diff(g.row_ptr)[rows].astype(np.float64)
+            bound = (3.0 if dtype == "f64" else 2.0) * u * (terms + 6.0)[:, None] * mag
+            assert_elementwise(got, ref, bound, f"{dtype} variant {variant} stride {stride}")
     finally:
         spx.sphynx_destroy(h)
 
@@ -255,3 +264,70 @@ def test_invalid_inputs_are_rejected():
             spx.sphynx_set_spmm_sell_stride(h, stride)
         assert e.value.code == spx.ERR_INVALID_ARG
     spx.sphynx_destroy(h)
+
+
+@pytest.mark.parametrize("dtype_in,dtype_out", [("bf16", "bf16"), ("f32", "bf16"), ("f32", "f32"), ("f64", "f64")])
+def test_polynomial_chain_step_full_size_mesh_elementwise(dtype_in, dtype_out):
+    """One product-form step of the polynomial preconditioner (Sec. 5.2) on the
+    full 128^3 27-point mesh (2,097,152 rows), every row and column checked
+    element by element, in the schedule the autotuner picks at create (the
+    launch configuration of the benchmark) and in the CSR-staged one.  With
+    t the exact input block:
+      t_out = t - (L t) / theta_cur: float (or double) rounding of each row's
+        sum, c (t_i + 6) u (|t| + |L| |t| / theta_cur), then one rounding to the
+        stored type, u_out |ref|;
+      y (two terms): y0 + t / theta_cur + t_out / theta_next with the library's
+        own stored t_out, three roundings of the magnitudes;
+      y (no term): unchanged bit for bit.
+    Float steps use the float-rounded reciprocals of the roots, so the oracle
+    side uses the same reciprocals."""
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    g = W.grid3d(128, 128, 128, 27)
+    lmat = O.operator_for(g, "combinatorial")
+    alap = abs_operator(lmat)
+    terms = np.diff(lmat.indptr).astype(np.float64)[:, None]
+    codes = {"f64": spx.DT_F64, "f32": spx.DT_F32, "bf16": spx.DT_BF16}
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+    u_acc = 2.0 ** -53 if dtype_in == "f64" else 2.0 ** -24
+    u_out = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "bf16": 2.0 ** -8}[dtype_out]
+    theta_cur, theta_next = 3.7, 11.3
+    if dtype_in == "f64":
+        ic, inx = 1.0 / theta_cur, 1.0 / theta_next
+    else:
+        ic, inx = float(np.float32(1.0 / theta_cur)), float(np.float32(1.0 / theta_next))
+    rng = np.random.default_rng(21)
+    ncols, ld = 7, 8
+    h = spx.sphynx_create(g.row_ptr, g.col, None, None)
+    try:
+        td = dev_block(rng.standard_normal((g.n, ncols)), ld, dtype_in)
+        tin = td.double().cpu().numpy()[:, :ncols]
+        ref_t = tin - (lmat @ tin) * ic
+        mag_t = np.abs(tin) + (alap @ np.abs(tin)) * ic
+        c = 3.0 if dtype_in == "f64" else 2.0
+        bound_t = u_out * np.abs(ref_t) + (1 + u_out) * c * u_acc * (terms + 6.0) * mag_t
+        ydt = torch.float64 if dtype_in == "f64" else torch.float32
+        y0 = torch.from_numpy(rng.standard_normal((g.n, ld))).to(device="cuda", dtype=ydt)
+        for variant in ("tuned", "csr"):
+            if variant == "csr":
+                spx.sphynx_set_spmm_variant(h, 0)
+            for yterms, first in ((2, 0), (2, 1), (1, 0), (0, 0)):
+                tout = torch.zeros((g.n, ld), dtype=tdt[dtype_out], device="cuda")
+                y = y0.clone()
+                spx.sphynx_poly_step(h, "combinatorial", codes[dtype_in], td, codes[dtype_out], tout, y, ld, ncols,
+                                     theta_cur, theta_next, yterms, first)
+                torch.cuda.synchronize()
+                tg = tout.double().cpu().numpy()[:, :ncols]
+                what = f"{dtype_in}->{dtype_out} {variant} yterms {yterms} first {first}"
+                assert_elementwise(tg, ref_t, bound_t, "t_out " + what)
+                yg = y.double().cpu().numpy()[:, :ncols]
+                yin = y0.double().cpu().numpy()[:, :ncols]
+                if yterms == 0:
+                    assert np.array_equal(yg, yin), what
+                    continue
+                base = np.zeros_like(yin) if first else yin
+                ref_y = base + (tin * ic if yterms == 2 else 0.0) + tg * inx
+                mag_y = np.abs(base) + (np.abs(tin) * ic if yterms == 2 else 0.0) + np.abs(tg) * inx
+                assert_elementwise(yg, ref_y, 4.0 * u_acc * mag_y, "y " + what)
+    finally:
+        spx.sphynx_destroy(h)

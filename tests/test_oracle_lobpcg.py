@@ -126,3 +126,31 @@ def test_hub_graph_converges_and_floor_admits_only_theta_zero():
     floor_th = 10 * 2.0 ** -53 * 2.0
     assert abs(res.eigenvalues[0]) <= floor_th
     assert np.all(res.resnorm[1:] <= 1e-3 * np.abs(res.eigenvalues[1:]))
+
+
+def test_absolute_convergence_test_meets_its_bound_and_orders_the_iteration_counts():
+    """conv="abs" stops at ||r_i||_{B^-1} <= tol.  On a grid whose wanted
+    eigenvalues are all below 1, that bound is looser than tol |theta_i|, so
+    the absolute test stops no later than the relative one; every returned
+    residual meets its own test, and Bauer-Fike still bounds each eigenvalue's
+    error by its residual (dense eigh as the reference)."""
+    g = W.grid2d(23, 19)
+    lmat = O.operator_for(g, O.COMBINATORIAL)
+    exact = np.linalg.eigvalsh(lmat.toarray())[:4]
+    x0 = O.splitmix64_block(g.n, 4, 3)
+    rho = 2.0 * O.weighted_degree(g).max()
+    jd = O.jacobi_diag(g, O.COMBINATORIAL)
+    m = lambda r: jd[:, None] * r  # noqa: E731
+    tol = 1e-4
+    rel = lobpcg(lambda v: lmat @ v, None, m, x0, tol, 3000, rho, conv="rel_theta")
+    ab = lobpcg(lambda v: lmat @ v, None, m, x0, tol, 3000, rho, conv="abs")
+    assert rel.status == "ok" and ab.status == "ok"
+    assert np.all(exact < 1.0)
+    assert ab.iterations <= rel.iterations
+    assert np.all(ab.resnorm <= tol)
+    ok_rel = (rel.resnorm[1:] <= tol * np.abs(rel.theta[1:]))
+    assert np.all(ok_rel)
+    assert np.all(np.abs(ab.theta - exact) <= ab.resnorm + 1e-14)
+    # the absolute test with tol below every |theta| * tol_rel stops later
+    tight = lobpcg(lambda v: lmat @ v, None, m, x0, tol * 1e-3, 3000, rho, conv="abs")
+    assert tight.iterations >= ab.iterations and np.all(tight.resnorm <= tol * 1e-3)
