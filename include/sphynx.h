@@ -170,7 +170,7 @@ typedef struct {
   int32_t spmm_variant;      /* short-row schedule the autotuner chose at create
                                 from a float 8-column product and uses for every
                                 product: 0 = CSR staged in shared memory,
-                                1 = SELL-32                                         */
+                                1 = SELL-32, 2 = SELL-32 with shared-pattern slices */
   float tuned_us_csr;        /* the two schedules' times for that product (us)    */
   float tuned_us_sell;
   int64_t sell_slices;       /* SELL-32 slices (32 rows each)                      */
@@ -189,6 +189,12 @@ typedef struct {
                                 or 16), so that on a mesh a block's rows can lie
                                 on neighbouring grid lines and share gathered rows
                                 of X in L1                                          */
+  float tuned_us_pattern;    /* the shared-pattern schedule's time (0: not built)  */
+  int64_t sell_pattern_slices;/* slices whose 32 rows' offsets col - row take at
+                                most 31 distinct 16-bit values (unweighted graphs):
+                                the shared-pattern schedule (spmm_variant 2) stores
+                                that union once per slice plus a 32-bit entry mask
+                                per row instead of one offset per entry           */
 } sphynx_graph_info;
 
 /* Fill *opt with the defaults listed in sphynx_options. */
@@ -225,8 +231,10 @@ void sphynx_destroy(sphynx_handle g);
 int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info);
 
 /* Pin the short-row SpMM schedule of the handle: 0 = CSR staged in shared
- * memory, 1 = SELL-32, -1 = time both again and keep the faster (what
- * sphynx_create does).  Both give the same products up to rounding order.
+ * memory, 1 = SELL-32, 2 = SELL-32 with shared-pattern slices (only when the
+ * graph has such slices, see sphynx_graph_info), -1 = time them again and keep
+ * the fastest (what sphynx_create does).  All give the same products up to
+ * rounding order; 1 and 2 sum every row in the same order.
  * Errors: INVALID_ARG. */
 int sphynx_set_spmm_variant(sphynx_handle g, int32_t variant);
 
@@ -271,8 +279,9 @@ int sphynx_laplacian_apply(sphynx_handle g, int32_t laplacian, int32_t dtype, co
  * F64, F32 -> F32 or BF16, BF16 -> BF16; y: device n x ld block of double (F64)
  * or float.  Float and bfloat16 steps multiply by the float-rounded
  * reciprocals of the roots and accumulate in float.  first = 1 needs
- * yterms = 2.  Synchronises the handle's stream.  Errors: INVALID_ARG,
- * ISOLATED. */
+ * yterms = 2.  Asynchronous on the handle's stream; the reciprocals are
+ * uploaded only when the roots differ from the previous call's.  Errors:
+ * INVALID_ARG, ISOLATED. */
 int sphynx_poly_step(sphynx_handle g, int32_t laplacian, int32_t dtype_in, const void *t, int32_t dtype_out,
                      void *t_out, void *y, int32_t ld, int32_t ncols, double theta_cur, double theta_next,
                      int32_t yterms, int32_t first);

@@ -69,7 +69,8 @@ class GraphInfo(C.Structure):
                 ("total_vweight", C.c_int64), ("long_rows", C.c_int64), ("weighted", C.c_int32),
                 ("spmm_variant", C.c_int32), ("tuned_us_csr", C.c_float), ("tuned_us_sell", C.c_float),
                 ("sell_slices", C.c_int64), ("sell_narrow_slices", C.c_int64), ("spmm_graph_bytes", C.c_double),
-                ("regular", C.c_int32), ("spmm_med_max", C.c_int32), ("sell_stride", C.c_int32)]
+                ("regular", C.c_int32), ("spmm_med_max", C.c_int32), ("sell_stride", C.c_int32),
+                ("tuned_us_pattern", C.c_float), ("sell_pattern_slices", C.c_int64)]
 
 
 class AmgLevelInfo(C.Structure):

@@ -622,7 +622,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   int *ctl = static_cast<int *>(g->workspace("bctl", 4 * sizeof(int), false));
   const void *bd = gen ? (dt == DT::F64 ? static_cast<const void *>(g->deg.p) : g->degf.p) : nullptr;
   const void *jv = jac ? (dt == DT::F64 ? static_cast<const void *>(g->jinv.p) : g->jinvf.p) : nullptr;
-  const int mixed = o->precision != SPHYNX_FP64;
+  const int mixed = 0;   // the m x m eigenproblem is solved in FP64 for every block precision
   const int32_t *gc0 = B.graph_chunk0.as<int32_t>();
   const unsigned cgrid = static_cast<unsigned>(nch);
   const int hctl[4] = {count, 0, 0, 0};

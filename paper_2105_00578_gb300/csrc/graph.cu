@@ -300,6 +300,70 @@ __global__ void k_sell_fill(const int64_t *rp, const int32_t *col, const float *
   }
 }
 
+// Shared-pattern test of one 32-row slice (a warp per slice): the lanes walk
+// their rows' sorted short-row offsets col - row in step, and each round takes
+// the smallest head among the lanes as the next union value U[k]; a lane whose
+// head equals it sets bit k of its mask and advances.  Returns the union size
+// (at most 31) or -1 when the union is larger or an offset needs more than 16
+// bits.  Long rows and padding lanes take no part (bit 31 of their mask).
+__device__ int slice_pattern(const int64_t *rp, const int32_t *col, int64_t n, const uint8_t *sdeg, int64_t slice,
+                             int lane, unsigned *mask_out, int *u_out) {
+  const int64_t row = slice * 32 + lane;
+  const bool short_row = row < n && sdeg[row] != 0xFF;
+  const int d = short_row ? sdeg[row] : 0;
+  const int64_t rb = short_row ? rp[row] : 0;
+  unsigned mk = short_row ? 0u : 0x80000000u;
+  int myu = 0, nu = 0, t = 0;
+  bool ok = true;
+  for (;;) {
+    int cand = 0x7fffffff;
+    if (t < d) {
+      const int64_t off = static_cast<int64_t>(col[rb + t]) - row;
+      if (off < -32768 || off > 32767) ok = false;
+      cand = static_cast<int>(off);
+    }
+    if (!__all_sync(0xffffffffu, ok)) return -1;
+    const int m = __reduce_min_sync(0xffffffffu, cand);
+    if (m == 0x7fffffff) break;
+    if (nu == 31) return -1;
+    if (lane == nu) myu = m;
+    if (cand == m) {
+      mk |= 1u << nu;
+      ++t;
+    }
+    ++nu;
+  }
+  *mask_out = mk;
+  *u_out = myu;
+  return nu;
+}
+
+__global__ void k_sell_pattern(const int64_t *rp, const int32_t *col, int64_t n, const uint8_t *sdeg, int *nu_out) {
+  const int64_t slice = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (slice * 32 >= n) return;   // uniform per warp
+  unsigned mk;
+  int u;
+  const int nu = slice_pattern(rp, col, n, sdeg, slice, lane, &mk, &u);
+  if (lane == 0) nu_out[slice] = nu;
+}
+
+// writes the shared-pattern blocks: U (32 int16) then the 32 lane masks
+__global__ void k_pat_fill(const int64_t *rp, const int32_t *col, int64_t n, const uint8_t *sdeg,
+                           const int64_t *pcptr, int16_t *pcol) {
+  const int64_t slice = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (slice * 32 >= n) return;   // uniform per warp
+  const int64_t cp = pcptr[slice];
+  if (cp < kPatternTag) return;
+  unsigned mk;
+  int u;
+  const int nu = slice_pattern(rp, col, n, sdeg, slice, lane, &mk, &u);
+  int16_t *blk = pcol + (cp - kPatternTag);
+  blk[lane] = static_cast<int16_t>(lane < nu ? u : 0);
+  reinterpret_cast<unsigned *>(blk + 32)[lane] = mk;
+}
+
 int grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g > 8 * kSmCount) g = 8 * kSmCount;
@@ -466,6 +530,48 @@ void build_sell(sphynx_graph *g) {
                                              p.sell_ptr.as<int64_t>(), p.sell_cptr.as<int64_t>(),
                                              p.sell_col.as<int16_t>(), p.sell_w.as<float>());
   SPX_LAUNCHED();
+  // the shared-pattern variant (unweighted graphs with at least one such slice)
+  p.pat_slices = 0;
+  p.pat_all = false;
+  p.pat_cptr.release();
+  p.pat_col.release();
+  if (!g->weighted && slices > 0) {
+    DevBuf nub;
+    nub.alloc(static_cast<size_t>(slices) * sizeof(int));
+    const unsigned wblocks = static_cast<unsigned>((slices * 32 + 255) / 256);
+    k_sell_pattern<<<wblocks, 256, 0, g->stream>>>(g->rowptr, g->col, n, p.sell_deg.as<uint8_t>(), nub.as<int>());
+    SPX_LAUNCHED();
+    std::vector<int> hnu(static_cast<size_t>(slices));
+    SPX_CUDA(cudaMemcpyAsync(hnu.data(), nub.p, hnu.size() * sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    SPX_CUDA(cudaStreamSynchronize(g->stream));
+    std::vector<int64_t> pc(static_cast<size_t>(slices));
+    int64_t punits = 0, npat = 0;
+    double pbytes = 0;
+    for (int64_t s = 0; s < slices; ++s) {
+      if (hnu[s] >= 0) {
+        pc[s] = kPatternTag | punits;
+        punits += 96;   // 64 bytes of offsets, 128 bytes of masks
+        pbytes += 192.0;
+        ++npat;
+      } else {
+        pc[s] = hcptr[s];
+        const double rows = static_cast<double>(std::min<int64_t>(32, n - 32 * s));
+        pbytes += (hcptr[s] < 0 ? 2.0 : 4.0) * hsum[s] + rows;
+      }
+    }
+    if (npat > 0) {
+      p.pat_slices = npat;
+      p.pat_all = npat == slices;
+      p.pat_bytes = pbytes + 8.0 * static_cast<double>(slices);
+      p.pat_cptr.alloc(pc.size() * sizeof(int64_t));
+      p.pat_col.alloc(static_cast<size_t>(punits) * sizeof(int16_t));
+      SPX_CUDA(cudaMemcpyAsync(p.pat_cptr.p, pc.data(), pc.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                               g->stream));
+      k_pat_fill<<<wblocks, 256, 0, g->stream>>>(g->rowptr, g->col, n, p.sell_deg.as<uint8_t>(),
+                                                 p.pat_cptr.as<int64_t>(), p.pat_col.as<int16_t>());
+      SPX_LAUNCHED();
+    }
+  }
   SPX_CUDA(cudaStreamSynchronize(g->stream));
 }
 
@@ -518,10 +624,9 @@ void autotune_spmm(sphynx_graph *g, const int64_t *host_rowptr) {
   }
   if (ceilings.size() > 1 && best_ceiling != ceilings.back()) build_plan(g, rp, best_ceiling);
   g->plan.tuned_variant = best_t.variant;
-  g->plan.tuned_us[kCsrStaged] = best_t.us[kCsrStaged];
-  g->plan.tuned_us[kSell32] = best_t.us[kSell32];
+  for (int v = 0; v < kSpmmVariants; ++v) g->plan.tuned_us[v] = best_t.us[v];
   for (float &u : g->plan.tuned_ls_us) u = 0.f;
-  if (best_t.variant == kSell32) spmm_tune_sell_stride(g, a);
+  if (best_t.variant != kCsrStaged) spmm_tune_sell_stride(g, a);
   SPX_CUDA(cudaStreamSynchronize(g->stream));
 }
 
@@ -727,6 +832,8 @@ int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info) {
     info->spmm_variant = g->plan.tuned_variant;
     info->tuned_us_csr = g->plan.tuned_us[kCsrStaged];
     info->tuned_us_sell = g->plan.tuned_us[kSell32];
+    info->tuned_us_pattern = g->plan.pat_slices > 0 ? g->plan.tuned_us[kSellPattern] : 0.f;
+    info->sell_pattern_slices = g->plan.pat_slices;
     info->regular = g->max_degree * g->n <= 10 * g->nnz ? 1 : 0;
     info->spmm_med_max = g->plan.med_max;
     info->sell_stride = 1 << g->plan.sell_ls;
@@ -734,8 +841,10 @@ int sphynx_get_info(sphynx_handle g, sphynx_graph_info *info) {
     info->sell_narrow_slices = g->plan.sell_narrow;
     info->spmm_graph_bytes = (g->plan.tuned_variant == kSell32
                                   ? g->plan.sell_bytes
-                                  : 8.0 * static_cast<double>(g->n + 1) +
-                                        g->plan.short_entries * (g->weighted ? 8.0 : 4.0)) +
+                                  : g->plan.tuned_variant == kSellPattern
+                                        ? g->plan.pat_bytes
+                                        : 8.0 * static_cast<double>(g->n + 1) +
+                                              g->plan.short_entries * (g->weighted ? 8.0 : 4.0)) +
                              g->plan.med_bytes + g->plan.long_bytes;
     return SPHYNX_OK;
   });
@@ -776,7 +885,7 @@ int sphynx_set_spmm_variant(sphynx_handle g, int32_t variant) {
     if (variant == -1) {
       g->plan.forced = -1;
       autotune_spmm(g, nullptr);
-    } else if (variant == kCsrStaged || variant == kSell32) {
+    } else if (variant == kCsrStaged || variant == kSell32 || (variant == kSellPattern && g->plan.pat_slices > 0)) {
       g->plan.forced = variant;
     } else {
       fail(SPHYNX_ERR_INVALID_ARG, "variant %d", variant);

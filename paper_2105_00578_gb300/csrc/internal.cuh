@@ -96,20 +96,24 @@ constexpr int kSmCount = 152;
 enum SpmmVariant : int {
   kCsrStaged = 0,   // CSR: a warp stages its 32 rows' columns in shared memory
   kSell32 = 1,      // SELL-32: columns stored slice-major, read straight from global memory
+  kSellPattern = 2, // SELL-32 whose shared-pattern slices store one offset list per slice
 };
+constexpr int kSpmmVariants = 3;
+// sell_cptr / pat_cptr tag of a shared-pattern slice (the start follows in the low bits)
+constexpr int64_t kPatternTag = int64_t{1} << 62;
 
 constexpr int kSellLsCount = 5;      // slice strides 1, 2, 4, 8, 16 the autotuner times
 
 struct SpmmTuning {
   int variant;
-  float us[2];                       // measured time of each schedule
+  float us[kSpmmVariants];           // measured time of each schedule (1e30: not available)
 };
 
 struct SpmmPlan {
   int variant = kCsrStaged;          // schedule of the launch being issued
   int forced = -1;                   // >= 0: every product uses this schedule
   int tuned_variant = kCsrStaged;    // the autotuner's choice for this graph
-  float tuned_us[2] = {0.f, 0.f};    // its timings of both schedules
+  float tuned_us[kSpmmVariants] = {0.f, 0.f, 0.f};   // its timings of the schedules
   int sell_ls = 0;                   // SELL blocks: warps take slices 2^sell_ls apart
   float tuned_ls_us[kSellLsCount] = {};   // the autotuner's time for each sell_ls
   DevBuf tune_scratch;
@@ -134,6 +138,20 @@ struct SpmmPlan {
   DevBuf sell_col;                   // 16-bit units [sum of block sizes]
   DevBuf sell_w;                     // float [sell_entries] (weighted graphs)
   DevBuf sell_deg;                   // uint8 [n]: degree, or 0xFF for a long row
+  // Shared-pattern slices (unweighted graphs): a slice whose 32 rows' short-row
+  // offsets col - row take at most 31 distinct values, all within 16 bits,
+  // stores that sorted union U once (32 int16, zero padded: 64 bytes) and one
+  // 32-bit mask per row (128 bytes): bit k says the row has the entry
+  // row + U[k], bit 31 marks a lane without a short row (a long row or a
+  // padding lane).  A row's entries in mask order are its CSR entries in
+  // order, so its sum is the explicit slice's sum.  pat_cptr[s] is
+  // kPatternTag | (start in pat_col, 16-bit units) for such a slice and
+  // sell_cptr[s] (the explicit slice in sell_col) for the others.
+  int64_t pat_slices = 0;            // shared-pattern slices (0: the variant is not built)
+  bool pat_all = false;              // every slice is a shared-pattern slice
+  double pat_bytes = 0;              // bytes a product reads from this layout
+  DevBuf pat_cptr;                   // int64 [n_slices]
+  DevBuf pat_col;                    // 16-bit units, 96 per shared-pattern slice
   double long_bytes = 0;             // bytes of the long rows' CSR entries and items
   // Medium rows (kShortDeg < degree <= kMedDeg), sorted by degree (descending,
   // row id on ties) and packed 32 to a slice: lane l of slice s is row
@@ -221,6 +239,7 @@ struct sphynx_graph {
   sphynx::DevBuf poly_inv;   // double[k]: 1 / theta_i
   sphynx::DevBuf poly_invf;  // float[k]
   std::vector<double> poly_roots;
+  double step_theta[2] = {0.0, 0.0};         // roots whose reciprocals sphynx_poly_step last uploaded
   std::map<std::string, sphynx::DevBuf> ws;  // named workspaces, grown on demand
   sphynx::Counters ctr;
   sphynx::DevBuf pinned_dummy;
@@ -258,6 +277,8 @@ struct SpmmArgs {
   const float *invf;       // mode 1: its float copy
   int i_cur;               // mode 1: index of theta_i in inv
   const int *done;         // device flag: skip the launch when nonzero (may be NULL)
+  const int32_t *row_graph = nullptr;  // mode 1 on a batch: graph of each row; its roots
+  int inv_stride = 0;                  // are inv[row_graph[row] * inv_stride + i]
 };
 void spmm(sphynx_graph *g, const SpmmArgs &a);
 // both short-row schedules timed on this product (scratch outputs)

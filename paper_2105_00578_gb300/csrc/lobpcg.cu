@@ -299,7 +299,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   const int pg1 = launch_gram(st, ga1, ggrid);
   launch_gram_reduce(st, gpart, 1, ld, pg1, ga, gb, done);
   launch_rayleigh_ritz(st, ga, gb, ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr,
-                       o->precision != SPHYNX_FP64);
+                       0);
   UpdateArgs up1{dt, 1, ld, n, {X[0], nullptr, nullptr}, {nullptr, nullptr, nullptr}, yt, X[1], nullptr, nullptr, done};
   launch_update(st, up1);
   plain_spmm(g, lap, dt, X[1], LX[1], ld, b, done);
@@ -323,7 +323,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
     const int pg3 = launch_gram(st, g3, ggrid);                                        // Rayleigh-Ritz
     launch_gram_reduce(st, gpart, 3, ld, pg3, ga, gb, done);
     launch_rayleigh_ritz(st, ga, gb, 3 * ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr,
-                       o->precision != SPHYNX_FP64);
+                       0);
     UpdateArgs u3{dt, 3, ld, n, {X[cur], H, P[cur]}, {nullptr, LH, LP[cur]}, yt, X[nx], P[nx], LP[nx], done};
     launch_update(st, u3);                                                             // update, direction
     plain_spmm(g, lap, dt, X[nx], LX[nx], ld, b, done);                                 // residual
@@ -541,10 +541,15 @@ int sphynx_poly_step(sphynx_handle g, int32_t laplacian, int32_t dtype_in, const
     if (laplacian != SPHYNX_COMBINATORIAL && g->isolated > 0) fail(SPHYNX_ERR_ISOLATED, "vertex without edges");
     double *inv = static_cast<double *>(g->workspace("ps_inv", 4 * sizeof(double), false));
     float *invf = static_cast<float *>(g->workspace("ps_invf", 4 * sizeof(float), false));
-    const double hinv[2] = {1.0 / theta_cur, 1.0 / theta_next};
-    const float hinvf[2] = {static_cast<float>(hinv[0]), static_cast<float>(hinv[1])};
-    SPX_CUDA(cudaMemcpyAsync(inv, hinv, sizeof(hinv), cudaMemcpyHostToDevice, g->stream));
-    SPX_CUDA(cudaMemcpyAsync(invf, hinvf, sizeof(hinvf), cudaMemcpyHostToDevice, g->stream));
+    if (g->step_theta[0] != theta_cur || g->step_theta[1] != theta_next) {
+      // a copy from pageable memory has left the host buffer when it returns
+      const double hinv[2] = {1.0 / theta_cur, 1.0 / theta_next};
+      const float hinvf[2] = {static_cast<float>(hinv[0]), static_cast<float>(hinv[1])};
+      SPX_CUDA(cudaMemcpyAsync(inv, hinv, sizeof(hinv), cudaMemcpyHostToDevice, g->stream));
+      SPX_CUDA(cudaMemcpyAsync(invf, hinvf, sizeof(hinvf), cudaMemcpyHostToDevice, g->stream));
+      g->step_theta[0] = theta_cur;
+      g->step_theta[1] = theta_next;
+    }
     SpmmArgs a{};
     a.lap = op_of(laplacian);
     a.tin = static_cast<DT>(dtype_in);
@@ -563,8 +568,6 @@ int sphynx_poly_step(sphynx_handle g, int32_t laplacian, int32_t dtype_in, const
     a.invf = invf;
     a.i_cur = 0;
     spmm(g, a);
-    // the host arrays above must outlive their asynchronous copies
-    SPX_CUDA(cudaStreamSynchronize(g->stream));
     return SPHYNX_OK;
   });
 }

@@ -30,7 +30,8 @@ SpmmDev tune_args(sphynx_graph *g, const SpmmArgs &a) {
     s.yacc = base;
     s.t_out = base + out_bytes;
   }
-  return SpmmDev{s.x, s.ld_x, s.ld_y, s.y, s.t_out, s.yacc, s.first, s.yterms, s.inv, s.invf, s.i_cur, nullptr};
+  return SpmmDev{s.x,    s.ld_x, s.ld_y, s.y,       s.t_out,      s.yacc,      s.first,
+                 s.yterms, s.inv, s.invf, s.i_cur, nullptr, s.row_graph, s.inv_stride};
 }
 
 }  // namespace
@@ -44,16 +45,17 @@ SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a) {
   cudaEvent_t e0, e1;
   SPX_CUDA(cudaEventCreate(&e0));
   SPX_CUDA(cudaEventCreate(&e1));
-  SpmmTuning t{kCsrStaged, {1e30f, 1e30f}};
+  SpmmTuning t{kCsrStaged, {1e30f, 1e30f, 1e30f}};
   const int64_t launches = g->ctr.launches;
-  for (int v = 0; v < 2; ++v) {   // warm-up of both
+  const int nv = g->plan.pat_slices > 0 ? 3 : 2;   // the shared-pattern layout exists on some graphs only
+  for (int v = 0; v < nv; ++v) {   // warm-up of each
     g->plan.variant = v;
     dispatch(g, s, d);
   }
   // alternate the schedules so that neither always runs on a warmer L2
   for (int round = 0; round < 5; ++round) {
-    for (int k = 0; k < 2; ++k) {
-      const int v = (round + k) & 1;
+    for (int k = 0; k < nv; ++k) {
+      const int v = (round + k) % nv;
       g->plan.variant = v;
       SPX_CUDA(cudaEventRecord(e0, g->stream));
       dispatch(g, s, d);
@@ -67,7 +69,9 @@ SpmmTuning spmm_tune(sphynx_graph *g, const SpmmArgs &a) {
   g->ctr.launches = launches;   // tuning launches are not part of the caller's work
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  t.variant = t.us[kSell32] < t.us[kCsrStaged] ? kSell32 : kCsrStaged;
+  t.variant = kCsrStaged;
+  for (int v = 1; v < nv; ++v)
+    if (t.us[v] < t.us[t.variant]) t.variant = v;
   return t;
 }
 
@@ -81,7 +85,9 @@ void spmm_tune_sell_stride(sphynx_graph *g, const SpmmArgs &a) {
   SPX_CUDA(cudaEventCreate(&e1));
   const int64_t launches = g->ctr.launches;
   const int variant = g->plan.variant;
-  g->plan.variant = kSell32;
+  // the SELL schedule in force (pinned, else tuned); plain SELL-32 when that is CSR
+  const int sv = g->plan.forced > 0 ? g->plan.forced : g->plan.tuned_variant;
+  g->plan.variant = sv == kSellPattern ? kSellPattern : kSell32;
   float us[kSellLsCount];
   for (int k = 0; k < kSellLsCount; ++k) {   // warm-up of each
     us[k] = 1e30f;
@@ -133,7 +139,8 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
   }
   if (a.mode == 1 && (a.yterms < 0 || a.yterms > 2 || (a.first && a.yterms != 2)))
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: polynomial step adds 0, 1 or 2 terms (2 on the first step)");
-  SpmmDev d{a.x, a.ld_x, a.ld_y, a.y, a.t_out, a.yacc, a.first, a.yterms, a.inv, a.invf, a.i_cur, a.done};
+  SpmmDev d{a.x,      a.ld_x, a.ld_y, a.y,       a.t_out, a.yacc,       a.first,
+            a.yterms, a.inv,  a.invf, a.i_cur, a.done,  a.row_graph, a.inv_stride};
 
   // schedule: forced, or the one the autotuner chose for this graph at create
   g->plan.variant = g->plan.forced >= 0 ? g->plan.forced : g->plan.tuned_variant;
@@ -147,8 +154,10 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
   const double sa = a.tin == DT::F64 ? 8.0 : 4.0;
   const double b = static_cast<double>(a.b_true);
   const double graph_bytes =
-      (g->plan.variant == kSell32 ? g->plan.sell_bytes
-                                  : 8.0 * (n + 1) + g->plan.short_entries * (g->weighted ? 8.0 : 4.0)) +
+      (g->plan.variant == kSell32
+           ? g->plan.sell_bytes
+           : g->plan.variant == kSellPattern ? g->plan.pat_bytes
+                                             : 8.0 * (n + 1) + g->plan.short_entries * (g->weighted ? 8.0 : 4.0)) +
       g->plan.med_bytes + g->plan.long_bytes;
   double bytes = graph_bytes + n * b * si + n * sa;
   if (a.mode == 0) {

@@ -159,6 +159,8 @@ struct SpmmDev {              // kernel-side view of SpmmArgs
   const float *invf;   // float copy of inv (the float path never touches FP64)
   int icur;
   const int *done;
+  const int32_t *row_graph;  // batches: graph of every row, whose roots start at
+  int inv_stride;            // inv[row_graph[row] * inv_stride] (NULL: one graph)
 };
 
 // acc = sum_j w_ij (s_j) X_j of row `row`; epilogue applies the diagonal part.
@@ -183,12 +185,13 @@ __device__ __forceinline__ void spmm_epilogue(const LapView &L, const SpmmDev &a
     store_row<BP>(static_cast<TA *>(a.y) + row * a.ldy, out);
   } else {
     TA ic, inx;
+    const int64_t ib = a.icur + (a.row_graph ? static_cast<int64_t>(__ldg(a.row_graph + row)) * a.inv_stride : 0);
     if constexpr (std::is_same<TA, double>::value) {
-      ic = a.inv[a.icur];
-      inx = a.inv[a.icur + 1];
+      ic = a.inv[ib];
+      inx = a.inv[ib + 1];
     } else {
-      ic = a.invf[a.icur];
-      inx = a.invf[a.icur + 1];
+      ic = a.invf[ib];
+      inx = a.invf[ib + 1];
     }
     TA tn[BP];
 #pragma unroll
@@ -606,6 +609,62 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
   }
 }
 
+// A row of a shared-pattern slice: entry k of the slice's union U is the
+// column row + U[k], present where bit k of the row's mask is set.  Lane k
+// holds U[k] (myoff), so each offset reaches the warp by one shuffle and the
+// gathers of a batch depend on no load.  Absent entries gather nothing and add
+// zero, so the row's sum is the explicit layout's sum, term for term.
+template <int R, int LAP, typename TI, int BP>
+__device__ __forceinline__ void pattern_batch(const LapView &L, const TI *__restrict__ x, int row, int myoff,
+                                              unsigned mk, int k0, RowAcc<TI, BP> &acc) {
+  using TA = typename AccOf<TI>::T;
+  int jj[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int k = k0 + u;
+    const int off = __shfl_sync(kFull, myoff, k);
+    jj[u] = ((mk >> k) & 1u) ? row + off : -1;
+  }
+  RawRow<TI, BP> rr[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    if (jj[u] >= 0) rr[u].load(x + static_cast<int64_t>(jj[u]) * BP);
+    else rr[u].zero();
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    if constexpr (LAP == SPHYNX_NORMALIZED) {
+      const TA coef = jj[u] >= 0 ? dinv_of<TA>(L, jj[u]) : TA(0);
+      acc.template accum<true>(rr[u], coef);
+    } else {
+      acc.template accum<false>(rr[u], TA(1));
+    }
+  }
+}
+
+template <int R, int LAP, typename TI, int BP>
+__device__ __forceinline__ void pattern_tail(const LapView &L, const TI *__restrict__ x, int row, int myoff,
+                                             unsigned mk, int k0, int rem, RowAcc<TI, BP> &acc) {
+  if constexpr (R > 0) {
+    if (rem == R) {
+      pattern_batch<R, LAP, TI, BP>(L, x, row, myoff, mk, k0, acc);
+      return;
+    }
+    pattern_tail<R - 1, LAP, TI, BP>(L, x, row, myoff, mk, k0, rem, acc);
+  }
+}
+
+// nu (<= 31, warp-uniform) union entries in batches of the gather width, the
+// last batch exactly as long as what is left
+template <int LAP, typename TI, int BP>
+__device__ __forceinline__ void spmm_pattern_row(const LapView &L, const TI *__restrict__ x, int row, int myoff,
+                                                 unsigned mk, int nu, RowAcc<TI, BP> &acc) {
+  constexpr int U = GatherBatch<TI, BP>::U;
+  int k0 = 0;
+  for (; k0 + U <= nu; k0 += U) pattern_batch<U, LAP, TI, BP>(L, x, row, myoff, mk, k0, acc);
+  pattern_tail<U - 1, LAP, TI, BP>(L, x, row, myoff, mk, k0, nu - k0, acc);
+}
+
 template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_spmm_short(const LapView L, const SpmmDev a) {
@@ -686,12 +745,15 @@ template <typename TI, int BP> struct SellOccupancy {
           : (std::is_same<TI, float>::value && BP == 8 ? 8 : 1);
 };
 
-// NARROW: every slice of the graph stores 16-bit offsets (no 32-bit branch).
-template <int LAP, typename TI, typename TT, int BP, bool W, int MODE, bool NARROW>
+// Slice kinds a launch may meet.  KIND 0: explicit slices of 16- or 32-bit
+// indices; 1: only 16-bit ones; 2: shared-pattern slices (kPatternTag in the
+// slice offset, block in pcol) besides explicit ones; 3: only shared-pattern
+// slices.
+template <int LAP, typename TI, typename TT, int BP, bool W, int MODE, int KIND>
 __global__ void __launch_bounds__(128, SellOccupancy<TI, BP>::blocks)
 k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, const float *__restrict__ sw,
             const int64_t *__restrict__ sptr, const int64_t *__restrict__ cptr, const uint8_t *__restrict__ sdeg,
-            int ls) {
+            const int16_t *__restrict__ pcol, int ls) {
   using TA = typename AccOf<TI>::T;
   if (a.done && *a.done) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -699,43 +761,61 @@ k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, 
   const int64_t slice = ((blk >> ls) << (ls + 2)) + (blk & ((1 << ls) - 1)) + (static_cast<int64_t>(wid) << ls);
   if (slice * 32 >= L.n) return;  // uniform per warp
   const int64_t row = slice * 32 + lane;
-  const bool valid = row < L.n;
-  const int sd = valid ? sdeg[row] : 0xFF;
-  const int d = sd == 0xFF ? 0 : sd;
   const int64_t cbase = __ldg(cptr + slice);
-  const float *wp = W ? sw + __ldg(sptr + slice) + lane : nullptr;
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
-  {
-    // One bulk L2 prefetch of the slice's whole index block (dmax segments of
-    // 64 or 128 bytes, contiguous, 64-byte aligned).  Without it every batch
-    // of the row loop waits on DRAM for its segments before it can gather;
-    // with it only the first batch does (9 % off the mesh's chain step).
-    const int dmax = __reduce_max_sync(kFull, d);
-    if (dmax > 0 && lane == 0) {
-      const bool nar = NARROW || cbase < 0;
-      const void *blk = nar ? static_cast<const void *>(scol + (~cbase)) : static_cast<const void *>(scol + cbase);
-      const unsigned bytes = static_cast<unsigned>(dmax) * (nar ? 64u : 128u);
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(blk), "r"(bytes) : "memory");
-    }
-  }
   RowAcc<TI, BP> acc;
   acc.zero();
-  if (NARROW || cbase < 0) {
-    const int16_t *cp = scol + (~cbase) + lane;
-    const int r = static_cast<int>(row);
-    spmm_row<LAP, TI, BP, W>(
-        L, x, d, [&](int t) { return r + static_cast<int>(__ldcs(cp + 32 * t)); },
-        [&](int t) { return __ldcs(wp + 32 * t); }, acc);
-  } else {
-    const int32_t *cp = reinterpret_cast<const int32_t *>(scol + cbase) + lane;
-    spmm_row<LAP, TI, BP, W>(
-        L, x, d, [&](int t) { return __ldcs(cp + 32 * t); }, [&](int t) { return __ldcs(wp + 32 * t); },
-        acc);
+  if constexpr (KIND >= 2 && !W) {
+    if (KIND == 3 || cbase >= kPatternTag) {
+      // one 64-byte offset list and one mask per lane: no per-entry index stream
+      const int16_t *pb = pcol + (cbase - kPatternTag);
+      const int myoff = __ldg(pb + lane);
+      const unsigned mk = __ldg(reinterpret_cast<const unsigned *>(pb + 32) + lane);
+      const unsigned any = __reduce_or_sync(kFull, mk & 0x7fffffffu);
+      const int nu = 32 - __clz(any);
+      spmm_pattern_row<LAP, TI, BP>(L, x, static_cast<int>(row), myoff, mk, nu, acc);
+      if (mk >> 31) return;   // long row or padding lane
+      TA sum[BP];
+      acc.get(sum);
+      spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
+      return;
+    }
   }
-  if (sd == 0xFF) return;   // padding lane or a long row
-  TA sum[BP];
-  acc.get(sum);
-  spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
+  if constexpr (KIND != 3) {
+    const bool valid = row < L.n;
+    const int sd = valid ? sdeg[row] : 0xFF;
+    const int d = sd == 0xFF ? 0 : sd;
+    const float *wp = W ? sw + __ldg(sptr + slice) + lane : nullptr;
+    {
+      // One bulk L2 prefetch of the slice's whole index block (dmax segments of
+      // 64 or 128 bytes, contiguous, 64-byte aligned).  Without it every batch
+      // of the row loop waits on DRAM for its segments before it can gather;
+      // with it only the first batch does (9 % off the mesh's chain step).
+      const int dmax = __reduce_max_sync(kFull, d);
+      if (dmax > 0 && lane == 0) {
+        const bool nar = KIND == 1 || cbase < 0;
+        const void *blkp = nar ? static_cast<const void *>(scol + (~cbase)) : static_cast<const void *>(scol + cbase);
+        const unsigned bytes = static_cast<unsigned>(dmax) * (nar ? 64u : 128u);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(blkp), "r"(bytes) : "memory");
+      }
+    }
+    if (KIND == 1 || cbase < 0) {
+      const int16_t *cp = scol + (~cbase) + lane;
+      const int r = static_cast<int>(row);
+      spmm_row<LAP, TI, BP, W>(
+          L, x, d, [&](int t) { return r + static_cast<int>(__ldcs(cp + 32 * t)); },
+          [&](int t) { return __ldcs(wp + 32 * t); }, acc);
+    } else {
+      const int32_t *cp = reinterpret_cast<const int32_t *>(scol + cbase) + lane;
+      spmm_row<LAP, TI, BP, W>(
+          L, x, d, [&](int t) { return __ldcs(cp + 32 * t); }, [&](int t) { return __ldcs(wp + 32 * t); },
+          acc);
+    }
+    if (sd == 0xFF) return;   // padding lane or a long row
+    TA sum[BP];
+    acc.get(sum);
+    spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
+  }
 }
 
 // Medium rows (kShortDeg < degree <= kMedDeg): a warp per slice of 32 rows of
@@ -836,18 +916,35 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
   const int64_t warps = (g->n + 31) / 32;
   const int64_t grid = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
   if (grid > 0) {
-    if (g->plan.variant == kSell32) {
+    const SpmmPlan &p = g->plan;
+    if (p.variant == kSell32 || (p.variant == kSellPattern && !W)) {
       // whole groups of 4 * 2^ls slices, 2^ls blocks each
-      const int ls = g->plan.sell_ls;
-      const int64_t sgrid = ((warps + (int64_t{4} << ls) - 1) >> (ls + 2)) << ls;
-      if (g->plan.sell_narrow == (g->n + 31) / 32)
-        k_spmm_sell<LAP, TI, TT, BP, W, MODE, true><<<static_cast<unsigned>(sgrid), 128, 0, st>>>(
-            L, a, g->plan.sell_col.as<int16_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
-            g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>(), ls);
-      else
-        k_spmm_sell<LAP, TI, TT, BP, W, MODE, false><<<static_cast<unsigned>(sgrid), 128, 0, st>>>(
-            L, a, g->plan.sell_col.as<int16_t>(), g->plan.sell_w.as<float>(), g->plan.sell_ptr.as<int64_t>(),
-            g->plan.sell_cptr.as<int64_t>(), g->plan.sell_deg.as<uint8_t>(), ls);
+      const int ls = p.sell_ls;
+      const unsigned gs = static_cast<unsigned>(((warps + (int64_t{4} << ls) - 1) >> (ls + 2)) << ls);
+      const int16_t *sc = p.sell_col.as<int16_t>();
+      const float *swp = p.sell_w.as<float>();
+      const int64_t *sp = p.sell_ptr.as<int64_t>();
+      const uint8_t *sd = p.sell_deg.as<uint8_t>();
+      bool launched = false;
+      if constexpr (!W) {
+        if (p.variant == kSellPattern) {
+          const int64_t *pc = p.pat_cptr.as<int64_t>();
+          const int16_t *pcl = p.pat_col.as<int16_t>();
+          if (p.pat_all)
+            k_spmm_sell<LAP, TI, TT, BP, W, MODE, 3><<<gs, 128, 0, st>>>(L, a, sc, swp, sp, pc, sd, pcl, ls);
+          else
+            k_spmm_sell<LAP, TI, TT, BP, W, MODE, 2><<<gs, 128, 0, st>>>(L, a, sc, swp, sp, pc, sd, pcl, ls);
+          launched = true;
+        }
+      }
+      if (!launched) {
+        if (p.sell_narrow == (g->n + 31) / 32)
+          k_spmm_sell<LAP, TI, TT, BP, W, MODE, 1><<<gs, 128, 0, st>>>(L, a, sc, swp, sp, p.sell_cptr.as<int64_t>(),
+                                                                       sd, nullptr, ls);
+        else
+          k_spmm_sell<LAP, TI, TT, BP, W, MODE, 0><<<gs, 128, 0, st>>>(L, a, sc, swp, sp, p.sell_cptr.as<int64_t>(),
+                                                                       sd, nullptr, ls);
+      }
     } else {
       k_spmm_short<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 32 * kWarpsPerCta, 0, st>>>(L, a);
     }

@@ -61,8 +61,13 @@ def test_spmm_matches_oracle(gname, lap, dtype, ncols):
         for med_max in ceilings:
             spx.sphynx_set_spmm_med_max(h, med_max)
             # CSR staged; SELL-32 under every slice stride (slices a block's
-            # warps take apart), which must not change any row's value
-            for variant, stride in ((0, 1), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16)):
+            # warps take apart), which must not change any row's value; and the
+            # shared-pattern slices where the graph has them, which sum every
+            # row in the explicit slices' order
+            schedules = [(0, 1), (1, 1), (1, 2), (1, 4), (1, 8), (1, 16)]
+            if spx.sphynx_get_info(h)["sell_pattern_slices"] > 0:
+                schedules += [(2, 1), (2, 4), (2, 16)]
+            for variant, stride in schedules:
                 spx.sphynx_set_spmm_variant(h, variant)
                 spx.sphynx_set_spmm_sell_stride(h, stride)
                 y.zero_()
@@ -72,9 +77,9 @@ def test_spmm_matches_oracle(gname, lap, dtype, ncols):
                 assert_elementwise(got, ref, bound, f"variant {variant} stride {stride} med_max {med_max}")
                 if variant == 1 and stride == 1:
                     first = got
-                elif variant == 1:
+                elif variant >= 1:
                     # the same sums in the same order, whichever block runs them
-                    assert np.array_equal(got, first), stride
+                    assert np.array_equal(got, first), (variant, stride)
             # padding columns stay zero when the input padding is zero
             if ld > ncols and ncols > 1:
                 assert np.all(y.cpu().numpy()[:, ncols:] == 0)
@@ -107,6 +112,28 @@ def test_degrees_exact():
         spx.sphynx_destroy(h)
 
 
+def pattern_slices(g) -> np.ndarray:
+    """Per 32-row slice: True when the offsets col - row of its short rows (at
+    most 32 neighbours) all fit 16 bits and take at most 31 distinct values
+    (unweighted graphs only), written from that definition."""
+    n_sl = (g.n + 31) // 32
+    if g.w is not None:
+        return np.zeros(n_sl, dtype=bool)
+    deg = g.degrees()
+    r = g.rows()
+    off = g.col.astype(np.int64) - r
+    keep = deg[r] <= 32
+    out = np.ones(n_sl, dtype=bool)
+    sl = r[keep] >> 5
+    o = off[keep]
+    bad = (o < -32768) | (o > 32767)
+    out[np.unique(sl[bad])] = False
+    pairs = np.unique(np.stack([sl, o]), axis=1)
+    cnt = np.bincount(pairs[0], minlength=n_sl)
+    out[cnt > 31] = False
+    return out
+
+
 def test_sell_slice_formats_follow_the_offset_range():
     """A slice stores 16-bit offsets exactly when every short-row entry of its
     32 rows lies within [-32768, 32767] of its row; the byte count a product
@@ -135,10 +162,16 @@ def test_sell_slice_formats_follow_the_offset_range():
             med_bytes = 4.0 * deg[med].sum() + n_ms * (32 * 8 + 8)
             lng = deg > mm
             long_bytes = 4.0 * deg[lng].sum() + 32 * int(np.sum((deg[lng] + 4095) // 4096)) + 24 * int(lng.sum())
+            short_per_slice = np.bincount(r[short_entry] >> 5, minlength=wide.size)
+            pat = pattern_slices(g)
+            assert info["sell_pattern_slices"] == int(pat.sum()), name
             if info["spmm_variant"] == 1:
-                short_per_slice = np.bincount(r[short_entry] >> 5, minlength=wide.size)
                 idx = float(np.sum(np.where(wide, 4, 2) * short_per_slice))
                 expect = idx + g.n + 8 * wide.size
+            elif info["spmm_variant"] == 2:
+                rows_in = np.minimum(32, g.n - 32 * np.arange(wide.size))
+                idx = np.where(pat, 192.0, np.where(wide, 4, 2) * short_per_slice + rows_in)
+                expect = float(idx.sum()) + 8 * wide.size
             else:
                 expect = 8 * (g.n + 1) + 4 * deg[deg <= 32].sum()
             expect += med_bytes + long_bytes
