@@ -131,18 +131,31 @@ def ingest_ncu(csv_path: str, kernel_regex: str, workload: str, command: str) ->
     per = {}
     with open(csv_path, newline="") as f:
         rows = [r for r in csv.reader(f) if r]
-    head = next(i for i, r in enumerate(rows) if "Metric Name" in r and "Kernel Name" in r)
-    cols = rows[head]
-    ci = {c: cols.index(c) for c in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
-    for r in rows[head + 1:]:
-        if len(r) < len(cols) or not pat.search(r[ci["Kernel Name"]]):
-            continue
-        name = r[ci["Metric Name"]]
-        if name not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            continue
-        val = float(r[ci["Metric Value"]].replace(",", "")) * _UNITS.get(r[ci["Metric Unit"]], 1.0)
-        d = per.setdefault(r[ci["ID"]], {})
-        d[name] = val
+    names = ("dram__bytes_read.sum", "dram__bytes_write.sum")
+    head = next((i for i, r in enumerate(rows) if "Metric Name" in r and "Kernel Name" in r), None)
+    if head is not None:
+        # the details page: one row per (launch, metric)
+        cols = rows[head]
+        ci = {c: cols.index(c) for c in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
+        for r in rows[head + 1:]:
+            if len(r) < len(cols) or not pat.search(r[ci["Kernel Name"]]):
+                continue
+            name = r[ci["Metric Name"]]
+            if name not in names:
+                continue
+            val = float(r[ci["Metric Value"]].replace(",", "")) * _UNITS.get(r[ci["Metric Unit"]], 1.0)
+            per.setdefault(r[ci["ID"]], {})[name] = val
+    else:
+        # the raw page: one row per launch, metrics as columns, their units in the next row
+        head = next(i for i, r in enumerate(rows) if "Kernel Name" in r and names[0] in r)
+        cols, units = rows[head], rows[head + 1]
+        ki, ii = cols.index("Kernel Name"), cols.index("ID")
+        for r in rows[head + 2:]:
+            if len(r) < len(cols) or not pat.search(r[ki]):
+                continue
+            for name in names:
+                j = cols.index(name)
+                per.setdefault(r[ii], {})[name] = float(r[j].replace(",", "")) * _UNITS.get(units[j], 1.0)
     launches = [v["dram__bytes_read.sum"] + v["dram__bytes_write.sum"] for v in per.values() if len(v) == 2]
     if not launches:
         raise SystemExit(f"no launch of {kernel_regex!r} with both DRAM metrics in {csv_path}")
@@ -513,7 +526,7 @@ def run_ours(args, world, rank, local):
     def pin(h):
         # profiler captures pin the schedule: under a profiler the tuner's timings are distorted
         if args.spmm_variant is not None:
-            spx.sphynx_set_spmm_variant(h, {"csr": 0, "sell": 1}[args.spmm_variant])
+            spx.sphynx_set_spmm_variant(h, {"csr": 0, "sell": 1, "pattern": 2}[args.spmm_variant])
         if args.sell_stride is not None:
             spx.sphynx_set_spmm_sell_stride(h, args.sell_stride)
 
@@ -573,8 +586,8 @@ def run_ours(args, world, rank, local):
     # the dominant kernel: the SpMM flavour with the most device time
     dom = max(by_dt, key=lambda k: by_dt[k]["us_per_launch"] * by_dt[k]["launches_per_step"]) if by_dt else None
     info = spx.sphynx_get_info(graph.h)
-    schedule = "k_spmm_sell" if (args.spmm_variant or "").startswith("sell") or \
-        (args.spmm_variant is None and info["spmm_variant"] == 1) else "k_spmm_short"
+    variant = {"csr": 0, "sell": 1, "pattern": 2}.get(args.spmm_variant, info["spmm_variant"])
+    schedule = {0: "k_spmm_short", 1: "k_spmm_sell", 2: "k_spmm_sell (shared-pattern slices)"}[variant]
     kernel_name = f"{schedule}<{dom} in>"
     traffic, traffic_meta = profiled_traffic(args.workload)
     # achieved: the scope table's algorithmic bytes of one launch of the
@@ -668,7 +681,8 @@ def run_ours(args, world, rank, local):
             "vs_oracle": vs_oracle(w, last[3], last[1], precision),
             "spmm": {"gbs": achieved_all, "launches_per_step": spmm_launches / args.steps,
                      "ms_per_step": spmm_ms / args.steps, "by_input_precision": by_dt,
-                     "schedule": schedule, "sell_stride": info["sell_stride"] if schedule == "k_spmm_sell" else None},
+                     "schedule": schedule, "sell_stride": info["sell_stride"] if variant > 0 else None,
+                     "sell_pattern_slices": info["sell_pattern_slices"]},
             "fp64": fp64,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -701,7 +715,7 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "mixed_bf16"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--spmm-variant", default=None, choices=[None, "csr", "sell"],
+    ap.add_argument("--spmm-variant", default=None, choices=[None, "csr", "sell", "pattern"],
                     help="pin the short-row SpMM schedule instead of the one tuned at create "
                          "(used for profiler captures, where tuning times are distorted)")
     ap.add_argument("--sell-stride", type=int, default=None, choices=[1, 2, 4, 8, 16],

@@ -425,16 +425,19 @@ int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, const float 
  * with the same options would; its random initial block is the one that call
  * would draw.  The LOBPCG iterations of all graphs run as one CUDA graph
  * launch whose conditional loop repeats on the device until every graph has
- * converged or reached max_iter; a converged graph drops out.  Jacobi or no
- * preconditioner, random initial block.
+ * converged or reached max_iter; a converged graph drops out.  Jacobi, the
+ * polynomial (degree >= 2: every graph's own roots from its own Lanczos
+ * steps, Sec. 5.2, applied with one chain over all graphs) or no
+ * preconditioner; random initial block.
  * part_out: int32[n] part ids local to each graph (0..K-1), host memory
  * unless opt->flags has SPHYNX_OUT_DEVICE.  cuts, imbalances (double[count]),
  * eigenvalues (double[count * d], d = floor(log2 K) + 1, each graph's Ritz
  * values ascending), iterations and status (int32[count], OK or NOCONV per
  * graph): host arrays, each may be NULL.  stats (may be NULL): status OK only if every graph
  * converged, iterations = the largest.  Errors: INVALID_ARG (not a batch
- * handle), UNSUPPORTED (polynomial or multigrid preconditioner, piecewise start,
- * K x count > 2^20), CUDA, OOM. */
+ * handle), UNSUPPORTED (multigrid preconditioner, polynomial of degree 1,
+ * piecewise start, K x count > 2^20), BREAKDOWN (a graph's polynomial setup
+ * failed), CUDA, OOM. */
 int sphynx_partition_batch(sphynx_handle g, int32_t K, const sphynx_options *opt, int32_t *part_out,
                            double *cuts, double *imbalances, double *eigenvalues, int32_t *iterations,
                            int32_t *status, sphynx_stats *stats);

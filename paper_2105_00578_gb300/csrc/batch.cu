@@ -449,6 +449,271 @@ ChunkView view_of(const sphynx_graph *g) {
   return ChunkView{g->batch.chunk_graph.as<int32_t>(), g->batch.chunk_begin.as<int64_t>()};
 }
 
+// ---- polynomial preconditioner of every graph (Sec. 5.2) ----------------------
+// The single-graph setup restated per graph: k Lanczos steps on each graph's
+// own L with two classical Gram-Schmidt passes against its basis (its
+// normalised null vector in column 0), then its harmonic Ritz values in
+// modified Leja order.  Dots reduce per 1024-row chunk, then per graph over
+// its chunks in chunk order.  The basis is column-major over all rows.
+
+// the start vector: graph q's rows draw the single-graph stream at their local index
+template <typename T>
+__global__ void k_bz_start(ChunkView cv, const int64_t *gptr, T *v, uint64_t state) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  const int64_t base = gptr[q];
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x)
+    v[i] = static_cast<T>(splitmix_pm1(state, static_cast<uint64_t>(i - base + 1)));
+}
+
+__device__ __forceinline__ double null_entry(int lap, const double *deg, int64_t i) {
+  return lap == SPHYNX_NORMALIZED ? sqrt(deg[i]) : 1.0;
+}
+
+// per chunk: z . v and z . z (z the null vector of L)
+template <typename T>
+__global__ void __launch_bounds__(256) k_bz_null_dots(ChunkView cv, const T *v, int lap, const double *deg,
+                                                      double *partials) {
+  __shared__ double r0[8], r1[8];
+  const int c = blockIdx.x;
+  double a0 = 0.0, a1 = 0.0;
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x) {
+    const double z = null_entry(lap, deg, i);
+    a0 += z * static_cast<double>(v[i]);
+    a1 += z * z;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    a0 += __shfl_down_sync(0xffffffffu, a0, off);
+    a1 += __shfl_down_sync(0xffffffffu, a1, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r0[threadIdx.x >> 5] = a0;
+    r1[threadIdx.x >> 5] = a1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = 0; k < 8; ++k) {
+      s0 += r0[k];
+      s1 += r1[k];
+    }
+    partials[2 * static_cast<int64_t>(c)] = s0;
+    partials[2 * static_cast<int64_t>(c) + 1] = s1;
+  }
+}
+
+// out[q][col] (row stride ostride) = sum over graph q's chunks, in chunk order,
+// of partials[chunk][col], col < cols
+__global__ void k_bz_reduce(const int32_t *gchunk0, int count, const double *partials, int cols, double *out,
+                            int ostride) {
+  const int q = blockIdx.x;
+  for (int col = threadIdx.x; col < cols; col += blockDim.x) {
+    double s = 0.0;
+    for (int c = gchunk0[q]; c < gchunk0[q + 1]; ++c) s += partials[static_cast<int64_t>(c) * cols + col];
+    out[static_cast<int64_t>(q) * ostride + col] = s;
+  }
+}
+
+// v <- v - (z.v / z.z) z  (scal[q] = {z.v, z.z}, stride 2)
+template <typename T>
+__global__ void k_bz_null_axpy(ChunkView cv, T *v, int lap, const double *deg, const double *scal) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  const double f = scal[2 * q] / scal[2 * q + 1];
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x)
+    v[i] = static_cast<T>(static_cast<double>(v[i]) - f * null_entry(lap, deg, i));
+}
+
+// col = z / ||z||
+template <typename T>
+__global__ void k_bz_null_column(ChunkView cv, T *col, int lap, const double *deg, const double *scal) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  const double f = 1.0 / sqrt(scal[2 * q + 1]);
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x)
+    col[i] = static_cast<T>(null_entry(lap, deg, i) * f);
+}
+
+// per chunk: the dots of w with basis columns 0 .. j1 - 1, eight at a time
+template <typename T>
+__global__ void __launch_bounds__(256) k_bz_dots(ChunkView cv, const T *basis, int64_t ldv, int j1, const T *w,
+                                                 double *partials) {
+  __shared__ double red[8][8];
+  const int c = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < j1; c0 += 8) {
+    T acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = T(0);
+    for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x) {
+      const T wv = w[i];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (c0 + k < j1) acc[k] = fma(basis[static_cast<int64_t>(c0 + k) * ldv + i], wv, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double d = static_cast<double>(acc[k]);
+      for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+      if (lane == 0) red[k][warp] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && c0 + static_cast<int>(threadIdx.x) < j1) {
+      double s = 0.0;
+      for (int k = 0; k < 8; ++k) s += red[threadIdx.x][k];
+      partials[static_cast<int64_t>(c) * j1 + c0 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// w <- w - V[:, :j1] h_q, and npart[chunk] = the chunk's part of ||w||^2
+template <typename T>
+__global__ void __launch_bounds__(256) k_bz_sub(ChunkView cv, const T *basis, int64_t ldv, int j1, T *w,
+                                                const double *h, int hstride, double *npart) {
+  __shared__ T sh[SPHYNX_MAX_POLY_DEGREE + 2];
+  __shared__ double red[8];
+  const int c = blockIdx.x, q = cv.graph[c];
+  for (int k = threadIdx.x; k < j1; k += blockDim.x) sh[k] = static_cast<T>(h[static_cast<int64_t>(q) * hstride + k]);
+  __syncthreads();
+  T acc = T(0);
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x) {
+    T v = w[i];
+    for (int k = 0; k < j1; ++k) v -= basis[static_cast<int64_t>(k) * ldv + i] * sh[k];
+    w[i] = v;
+    acc += v * v;
+  }
+  double d = static_cast<double>(acc);
+  for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += red[k];
+    npart[c] = s;
+  }
+}
+
+// v = w / sqrt(beta2_q) and V[:, col] = v (beta2 of graph q at beta2[q * bstride])
+template <typename T>
+__global__ void k_bz_next(ChunkView cv, const T *w, T *v, T *basis, int64_t ldv, int col, const double *beta2,
+                          int bstride) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  const T inv = static_cast<T>(1.0 / sqrt(beta2[static_cast<int64_t>(q) * bstride]));
+  T *bc = basis + static_cast<int64_t>(col) * ldv;
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x) {
+    const T val = w[i] * inv;
+    v[i] = val;
+    bc[i] = val;
+  }
+}
+
+// dst[q * dstride] = src[q * sstride] for every graph
+__global__ void k_bz_take(int count, const double *src, int sstride, double *dst, int dstride) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < count) dst[static_cast<int64_t>(q) * dstride] = src[static_cast<int64_t>(q) * sstride];
+}
+
+__global__ void k_row_graph(ChunkView cv, int32_t *rg) {
+  const int c = blockIdx.x, q = cv.graph[c];
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x) rg[i] = q;
+}
+
+template <typename T>
+void batch_poly_setup_t(sphynx_graph *g, int k, int lap, uint64_t seed) {
+  BatchInfo &B = g->batch;
+  const int count = B.count;
+  cudaStream_t st = g->stream;
+  const int64_t n = g->n;
+  const int64_t ldv = (n + 3) & ~static_cast<int64_t>(3);
+  const unsigned cg = static_cast<unsigned>(B.n_chunks);
+  const ChunkView cv = view_of(g);
+  const int32_t *gc0 = B.graph_chunk0.as<int32_t>();
+  const double *deg = g->deg.as<double>();
+  T *V = static_cast<T *>(g->workspace("bz_V", static_cast<size_t>(ldv) * (k + 1) * sizeof(T), false));
+  T *v = static_cast<T *>(g->workspace("bz_v", static_cast<size_t>(ldv) * sizeof(T), false));
+  T *w = static_cast<T *>(g->workspace("bz_w", static_cast<size_t>(ldv) * sizeof(T), false));
+  const int S = SPHYNX_MAX_POLY_DEGREE + 2;   // per-graph stride of the small arrays
+  double *part = static_cast<double *>(g->workspace("bz_part", static_cast<size_t>(B.n_chunks) * S * 8, false));
+  double *small = static_cast<double *>(g->workspace("bz_small", static_cast<size_t>(count) * S * 5 * 8, true));
+  double *alpha = small, *beta2 = small + static_cast<size_t>(count) * S, *h = beta2 + static_cast<size_t>(count) * S;
+  double *scal = h + static_cast<size_t>(count) * S, *roots = scal + static_cast<size_t>(count) * S;
+  int *err = static_cast<int *>(g->workspace("bz_err", static_cast<size_t>(count) * sizeof(int), true));
+  const int KS = k + 1;
+  B.poly_inv.alloc(static_cast<size_t>(count) * KS * sizeof(double));
+  B.poly_invf.alloc(static_cast<size_t>(count) * KS * sizeof(float));
+  if (!B.row_graph.p) {
+    B.row_graph.alloc(static_cast<size_t>(n) * sizeof(int32_t));
+    k_row_graph<<<cg, 256, 0, st>>>(cv, B.row_graph.as<int32_t>());
+    SPX_LAUNCHED();
+  }
+  // start vector, null column, projection, normalisation
+  k_bz_start<T><<<cg, 256, 0, st>>>(cv, B.gptr.as<int64_t>(), v, mix64(seed + 3 * kGamma));
+  SPX_LAUNCHED();
+  k_bz_null_dots<T><<<cg, 256, 0, st>>>(cv, v, lap, deg, part);
+  SPX_LAUNCHED();
+  k_bz_reduce<<<count, 32, 0, st>>>(gc0, count, part, 2, scal, 2);
+  SPX_LAUNCHED();
+  k_bz_null_axpy<T><<<cg, 256, 0, st>>>(cv, v, lap, deg, scal);
+  SPX_LAUNCHED();
+  k_bz_null_column<T><<<cg, 256, 0, st>>>(cv, V, lap, deg, scal);
+  SPX_LAUNCHED();
+  k_bz_dots<T><<<cg, 256, 0, st>>>(cv, v, ldv, 1, v, part);
+  SPX_LAUNCHED();
+  k_bz_reduce<<<count, 32, 0, st>>>(gc0, count, part, 1, h, S);
+  SPX_LAUNCHED();
+  k_bz_next<T><<<cg, 256, 0, st>>>(cv, v, v, V, ldv, 1, h, S);
+  SPX_LAUNCHED();
+  g->ctr.launches += 9;
+  for (int j = 0; j < k; ++j) {
+    SpmmArgs a{};                                        // w = L v_j (every graph at once)
+    a.lap = lap;
+    a.tin = std::is_same<T, double>::value ? DT::F64 : DT::F32;
+    a.ld_x = a.ld_y = a.bp = a.b_true = 1;
+    a.x = v;
+    a.y = w;
+    spmm(g, a);
+    for (int pass = 0; pass < 2; ++pass) {               // two Gram-Schmidt passes
+      k_bz_dots<T><<<cg, 256, 0, st>>>(cv, V, ldv, j + 2, w, part);
+      SPX_LAUNCHED();
+      k_bz_reduce<<<count, 32, 0, st>>>(gc0, count, part, j + 2, h, S);
+      SPX_LAUNCHED();
+      if (pass == 0) {
+        k_bz_take<<<(count + 127) / 128, 128, 0, st>>>(count, h + j + 1, S, alpha + j, S);
+        SPX_LAUNCHED();
+      }
+      k_bz_sub<T><<<cg, 256, 0, st>>>(cv, V, ldv, j + 2, w, h, S, part);
+      SPX_LAUNCHED();
+    }
+    k_bz_reduce<<<count, 32, 0, st>>>(gc0, count, part, 1, beta2 + j, S);   // beta_j^2 = ||w||^2
+    SPX_LAUNCHED();
+    if (j + 1 < k) {
+      k_bz_next<T><<<cg, 256, 0, st>>>(cv, w, v, V, ldv, j + 2, beta2 + j, S);
+      SPX_LAUNCHED();
+    }
+    g->ctr.launches += 9;
+  }
+  launch_harmonic_ritz_batch(st, alpha, beta2, k, count, S, roots, h, reinterpret_cast<float *>(scal), err);
+  // roots in application order -> per-graph 1/theta arrays of stride k + 1 (double and float)
+  std::vector<double> hinv(static_cast<size_t>(count) * S);
+  std::vector<int> herr(static_cast<size_t>(count));
+  SPX_CUDA(cudaMemcpyAsync(hinv.data(), h, hinv.size() * 8, cudaMemcpyDeviceToHost, st));
+  SPX_CUDA(cudaMemcpyAsync(herr.data(), err, herr.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPX_CUDA(cudaStreamSynchronize(st));
+  for (int q = 0; q < count; ++q)
+    if (herr[q]) fail(SPHYNX_ERR_BREAKDOWN, "polynomial setup of graph %d: Lanczos tridiagonal not positive definite "
+                      "(%d)", q, herr[q]);
+  std::vector<double> inv(static_cast<size_t>(count) * KS);
+  std::vector<float> invf(inv.size());
+  for (int q = 0; q < count; ++q)
+    for (int i = 0; i < KS; ++i) {
+      inv[static_cast<size_t>(q) * KS + i] = hinv[static_cast<size_t>(q) * S + i];
+      invf[static_cast<size_t>(q) * KS + i] = static_cast<float>(inv[static_cast<size_t>(q) * KS + i]);
+    }
+  SPX_CUDA(cudaMemcpyAsync(B.poly_inv.p, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, st));
+  SPX_CUDA(cudaMemcpyAsync(B.poly_invf.p, invf.data(), invf.size() * 4, cudaMemcpyHostToDevice, st));
+  SPX_CUDA(cudaStreamSynchronize(st));   // the host vectors above feed asynchronous copies
+  B.poly_k = k;
+  B.poly_lap = lap;
+}
+
 template <typename T>
 void launch_bgram_t(cudaStream_t st, const sphynx_graph *g, const SolverState *states, int nb, int ld,
                     const void *const *s, const void *const *ls, const void *bdiag, double *partials) {
@@ -570,8 +835,10 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
                      double *eigs, int32_t *iters, int32_t *status, sphynx_stats *stats) {
   BatchInfo &B = g->batch;
   const int count = B.count;
-  if (o->precond == SPHYNX_PRECOND_POLY || o->precond == SPHYNX_PRECOND_AMG)
-    fail(SPHYNX_ERR_UNSUPPORTED, "batched partitions take the Jacobi preconditioner or none");
+  if (o->precond == SPHYNX_PRECOND_AMG)
+    fail(SPHYNX_ERR_UNSUPPORTED, "batched partitions take the Jacobi or polynomial preconditioner, or none");
+  if (o->precond == SPHYNX_PRECOND_POLY && o->poly_degree < 2)
+    fail(SPHYNX_ERR_UNSUPPORTED, "batched polynomial preconditioning needs degree >= 2");
   if (o->init != SPHYNX_INIT_RANDOM) fail(SPHYNX_ERR_UNSUPPORTED, "batched partitions start from the random block");
   for (int q = 0; q < count; ++q)
     if (B.h_gptr[q + 1] - B.h_gptr[q] < 2) fail(SPHYNX_ERR_INVALID_ARG, "graph %d of the batch has < 2 vertices", q);
@@ -602,8 +869,14 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   const double u_work = o->precision == SPHYNX_FP64 ? 0x1.0p-53 : 0x1.0p-24;
   const int rho_from_degree = lap == SPHYNX_COMBINATORIAL && !gen ? 1 : 0;        // noise floors, per graph
   const bool jac = o->precond == SPHYNX_PRECOND_JACOBI && lap == SPHYNX_COMBINATORIAL;
+  const bool poly = o->precond == SPHYNX_PRECOND_POLY;
   const size_t blk = static_cast<size_t>(n) * ld * es;
   const int64_t nch = B.n_chunks;
+  if (poly) {   // every graph's polynomial (Sec. 5.2), set up anew as a single-graph partition does
+    if (dt == DT::F64) batch_poly_setup_t<double>(g, o->poly_degree, lap, o->seed);
+    else batch_poly_setup_t<float>(g, o->poly_degree, lap, o->seed);
+  }
+  const DT ct = o->precision == SPHYNX_FP64 ? DT::F64 : (o->precision == SPHYNX_MIXED_BF16 ? DT::BF16 : DT::F32);
 
   void *X[2] = {g->workspace("X0", blk, false), g->workspace("X1", blk, false)};
   void *LX[2] = {g->workspace("LX0", blk, false), g->workspace("LX1", blk, false)};
@@ -611,6 +884,13 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   void *LP[2] = {g->workspace("LP0", blk, true), g->workspace("LP1", blk, true)};
   void *H = g->workspace("H", blk, true);
   void *LH = g->workspace("LH", blk, true);
+  // the residual goes to H directly (Jacobi, none) or to R, from which the chain makes H
+  void *R = poly ? g->workspace("bR", blk, true) : H;
+  void *chain[2] = {nullptr, nullptr};
+  if (poly) {
+    chain[0] = g->workspace("chain0", static_cast<size_t>(n) * ld * dt_size(ct), false);
+    chain[1] = g->workspace("chain1", static_cast<size_t>(n) * ld * dt_size(ct), false);
+  }
   const size_t ntot3 = static_cast<size_t>(M3) * (M3 + 1);
   double *gpart = static_cast<double *>(g->workspace("bgram_part", static_cast<size_t>(nch) * ntot3 * 8, false));
   double *ga = static_cast<double *>(g->workspace("bga", static_cast<size_t>(count) * M3 * M3 * 8, true));
@@ -651,6 +931,31 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
                                                       o->conv == SPHYNX_CONV_ABS ? 1 : 0, ctl);
     SPX_LAUNCHED();
   };
+  // H = p(L) R with each row's graph's roots: the single-graph product-form chain
+  auto precondition = [&]() {
+    if (!poly) return;
+    const int k = B.poly_k;
+    for (int i = 0; i + 1 < k; ++i) {
+      SpmmArgs a{};
+      a.lap = lap;
+      a.tin = i == 0 ? dt : ct;
+      a.ld_x = a.ld_y = a.bp = ld;
+      a.b_true = b;
+      a.x = i == 0 ? R : chain[(i - 1) & 1];
+      a.mode = 1;
+      a.t_out = chain[i & 1];
+      a.tout = ct;
+      a.yacc = H;
+      a.first = i == 0 ? 1 : 0;
+      a.yterms = (i % 2 == 0) ? 2 : (i + 2 == k ? 1 : 0);
+      a.inv = B.poly_inv.as<double>();
+      a.invf = B.poly_invf.as<float>();
+      a.i_cur = i;
+      a.row_graph = B.row_graph.as<int32_t>();
+      a.inv_stride = k + 1;
+      spmm(g, a);
+    }
+  };
   auto spmm_block = [&](const void *x, void *y) {
     SpmmArgs a{};
     a.lap = lap;
@@ -686,7 +991,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     update(1, s1, l1, X[1], nullptr, nullptr);
   }
   spmm_block(X[1], LX[1]);
-  residual(X[1], LX[1], H);
+  residual(X[1], LX[1], R);
   converge(0);
   SPX_CUDA(cudaStreamSynchronize(st));
 
@@ -713,6 +1018,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     SPX_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     for (int half = 0; half < 2; ++half) {   // X[1] -> X[0] -> X[1]: two iterations per body
       const int cur = half == 0 ? 1 : 0, nx = cur ^ 1;
+      precondition();
       spmm_block(H, LH);
       const void *s3[3] = {X[cur], H, P[cur]}, *l3[3] = {LX[cur], LH, LP[cur]};
       gram(3, s3, l3);
@@ -720,7 +1026,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
                            count);
       update(3, s3, l3, X[nx], P[nx], LP[nx]);
       spmm_block(X[nx], LX[nx]);
-      residual(X[nx], LX[nx], H);
+      residual(X[nx], LX[nx], R);
       converge(1);
     }
     k_bloop_condition<<<1, 1, 0, cs>>>(ctl, (o->max_iter + 1) / 2, cond);

@@ -206,6 +206,12 @@ struct BatchInfo {
   DevBuf chunk_begin;               // int64 [n_chunks + 1]: first row of each chunk, then n
   DevBuf graph_chunk0;              // int32 [count + 1]: first chunk of each graph
   DevBuf graph_max;                 // uint64 [count][2]: max degree, max weighted degree (double bits)
+  DevBuf row_graph;                 // int32 [n]: graph of every row (the chain reads its roots)
+  // polynomial preconditioner of every graph (Sec. 5.2), set up per partition
+  int poly_k = 0;                   // degree (0: none set up)
+  int poly_lap = -1;
+  DevBuf poly_inv;                  // double [count][poly_k + 1]: 1 / theta in application order, then 0
+  DevBuf poly_invf;                 // float copy
 };
 
 // aggregation multigrid hierarchy (amg.cu), owned by the handle
@@ -441,6 +447,9 @@ void launch_gram_reduce(cudaStream_t st, const double *partials, int nblk, int l
                         double *ga, double *gb, const int *done);
 void launch_harmonic_ritz(cudaStream_t st, const double *alpha, const double *beta2, int k,
                           double *roots, double *inv, float *invf, int *err);
+// count problems, problem q's arrays `stride` (>= k + 1) apart, err[count]
+void launch_harmonic_ritz_batch(cudaStream_t st, const double *alpha, const double *beta2, int k, int count,
+                                int stride, double *roots, double *inv, float *invf, int *err);
 
 // ---- mj.cu ------------------------------------------------------------------
 void run_mj(cudaStream_t st, DT dt, const void *coords, int ldc, int dims, int64_t n,

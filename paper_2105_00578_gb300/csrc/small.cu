@@ -557,13 +557,18 @@ __device__ int sturm_count(const double *d, const double *e2, int k, double sigm
   return cnt;
 }
 
-// CTA i (32 threads): theta[i], the i-th smallest eigenvalue of Z.
+// CTA i (32 threads): theta[i], the i-th smallest eigenvalue of Z.  Problem
+// blockIdx.y of a batch reads and writes its arrays `stride` further on.
 __global__ void __launch_bounds__(32)
-k_harmonic_eig(const double *alpha, const double *beta2, int k, double *theta, int *err) {
+k_harmonic_eig(const double *alpha, const double *beta2, int k, double *theta, int *err, int stride) {
   __shared__ double d[SPHYNX_MAX_POLY_DEGREE], e2[SPHYNX_MAX_POLY_DEGREE];
   __shared__ double glo, ghi;
   __shared__ int bad;
   const int lane = threadIdx.x, i = blockIdx.x;
+  alpha += static_cast<int64_t>(blockIdx.y) * stride;
+  beta2 += static_cast<int64_t>(blockIdx.y) * stride;
+  theta += static_cast<int64_t>(blockIdx.y) * stride;
+  err += blockIdx.y;
   if (lane == 0) {
     // T = R^T R: r_0 = sqrt(alpha_0), s_j = b_j / r_j, r_{j+1} = sqrt(alpha_{j+1} - s_j^2)
     double r[SPHYNX_MAX_POLY_DEGREE], sd[SPHYNX_MAX_POLY_DEGREE];
@@ -627,11 +632,17 @@ k_harmonic_eig(const double *alpha, const double *beta2, int k, double *theta, i
 // ties -> lowest index.  The logs of a step are taken in parallel, one thread
 // per candidate.  theta may alias inv: it is read into shared memory first.
 __global__ void __launch_bounds__(64)
-k_harmonic_leja(const double *theta, int k, double *roots, double *inv, float *invf, int *err) {
+k_harmonic_leja(const double *theta, int k, double *roots, double *inv, float *invf, int *err, int stride) {
   __shared__ double th[SPHYNX_MAX_POLY_DEGREE], score[SPHYNX_MAX_POLY_DEGREE];
   __shared__ int used[SPHYNX_MAX_POLY_DEGREE];
   __shared__ int last;
   const int tid = threadIdx.x;
+  const int64_t o = static_cast<int64_t>(blockIdx.x) * stride;   // problem blockIdx.x of a batch
+  theta += o;
+  roots += o;
+  inv += o;
+  invf += o;
+  err += blockIdx.x;
   if (*err) return;
   if (tid < k) {
     th[tid] = theta[tid];
@@ -697,9 +708,20 @@ void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, i
 void launch_harmonic_ritz(cudaStream_t st, const double *alpha, const double *beta2, int k, double *roots,
                           double *inv, float *invf, int *err) {
   if (k < 1 || k > SPHYNX_MAX_POLY_DEGREE) fail(SPHYNX_ERR_INVALID_ARG, "polynomial degree %d", k);
-  k_harmonic_eig<<<k, 32, 0, st>>>(alpha, beta2, k, inv, err);
+  k_harmonic_eig<<<k, 32, 0, st>>>(alpha, beta2, k, inv, err, 0);
   SPX_LAUNCHED();
-  k_harmonic_leja<<<1, 64, 0, st>>>(inv, k, roots, inv, invf, err);
+  k_harmonic_leja<<<1, 64, 0, st>>>(inv, k, roots, inv, invf, err, 0);
+  SPX_LAUNCHED();
+}
+
+void launch_harmonic_ritz_batch(cudaStream_t st, const double *alpha, const double *beta2, int k, int count,
+                                int stride, double *roots, double *inv, float *invf, int *err) {
+  if (k < 1 || k > SPHYNX_MAX_POLY_DEGREE || stride < k + 1 || count < 1)
+    fail(SPHYNX_ERR_INVALID_ARG, "polynomial degree %d, stride %d, count %d", k, stride, count);
+  if (count > 65535) fail(SPHYNX_ERR_UNSUPPORTED, "more than 65535 polynomial setups in one launch");
+  k_harmonic_eig<<<dim3(k, count), 32, 0, st>>>(alpha, beta2, k, inv, err, stride);
+  SPX_LAUNCHED();
+  k_harmonic_leja<<<count, 64, 0, st>>>(inv, k, roots, inv, invf, err, stride);
   SPX_LAUNCHED();
 }
 

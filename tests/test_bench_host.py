@@ -61,3 +61,18 @@ def test_committed_traffic_json_names_its_capture():
             d = json.load(open(os.path.join(bench.ROOT, "profiles", name)))
             assert d["traffic_bytes_per_launch"] > 0 and d["launches"] >= 1
             assert "ncu" in d["command"] and "--clock-control none" in d["command"]
+
+
+def test_ingest_ncu_reads_the_raw_page_too(tmp_path, monkeypatch):
+    k = "void k_spmm_sell<0, __nv_bfloat16, __nv_bfloat16, 8, 0, 1, 3>(LapView, SpmmDev, ...)"
+    lines = ['"ID","Process ID","Kernel Name","dram__bytes_read.sum","dram__bytes_write.sum","gpu__time_duration.sum"',
+             '"","","","Mbyte","Kbyte","usecond"',
+             f'"0","7","{k}","100.5","2,000","60.1"',
+             '"1","7","void k_gram8<8, 3>(...)","400","1","150"',
+             f'"2","7","{k}","120.5","4,000","61.0"']
+    p = tmp_path / "raw.csv"
+    p.write_text("\n".join(lines) + "\n")
+    monkeypatch.setattr(bench, "traffic_path", lambda w: str(tmp_path / f"traffic_{w}.json"))
+    out = bench.ingest_ncu(str(p), r"k_spmm_sell<(\(int\))?0, __nv_bfloat16, __nv_bfloat16", "c2", "ncu x")
+    assert out["launches"] == 2
+    assert out["traffic_bytes_per_launch"] == pytest.approx((102.5e6 + 124.5e6) / 2)

@@ -105,9 +105,10 @@ def test_batch_rejects_crossing_edges_and_unsupported_options():
     h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr)
     try:
         parts = np.zeros(big.n, dtype=np.int32)
-        with pytest.raises(spx.SphynxError) as e:
-            spx.sphynx_partition_batch(h, 2, spx.options(precond="poly"), parts, 2)
-        assert e.value.code == spx.ERR_UNSUPPORTED
+        for bad in (spx.options(precond="poly", poly_degree=1), spx.options(precond="amg")):
+            with pytest.raises(spx.SphynxError) as e:
+                spx.sphynx_partition_batch(h, 2, bad, parts, 2)
+            assert e.value.code == spx.ERR_UNSUPPORTED
         # K = 1: every vertex in part 0 of its graph
         code, cuts, imbs, eigs, iters, status, _ = spx.sphynx_partition_batch(h, 1, spx.options(), parts, 2)
         assert np.all(parts == 0) and np.all(cuts == 0) and np.all(imbs == 1.0)
@@ -120,3 +121,35 @@ def test_batch_rejects_crossing_edges_and_unsupported_options():
         assert e.value.code == spx.ERR_INVALID_ARG
     finally:
         spx.sphynx_destroy(single)
+
+
+@pytest.mark.parametrize("precision,lap,k", [("fp64", "combinatorial", 25), ("fp64", "normalized", 10),
+                                             ("fp32", "combinatorial", 25), ("mixed_bf16", "combinatorial", 25)])
+def test_batch_polynomial_matches_oracle_per_graph(precision, lap, k):
+    """Every graph of the batch gets its own GMRES polynomial (Sec. 5.2: its
+    own Lanczos steps and harmonic Ritz roots) and the chain runs once over
+    all graphs with each row's own roots: per graph, the Ritz values and the
+    cut match the oracle's single-graph partition with the same polynomial."""
+    import paper_2105_00578_gb300 as spx
+    graphs = _rggs([400, 1000, 2500, 700, 1900], 120) + [W.grid2d(40, 31)]
+    big, gptr = W.concat_graphs(graphs)
+    h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr)
+    try:
+        opt = spx.options(laplacian=lap, precond="poly", poly_degree=k, precision=precision, tol=1e-3, seed=6)
+        parts = np.full(big.n, -1, dtype=np.int32)
+        code, cuts, imbs, eigs, iters, status, st = spx.sphynx_partition_batch(h, 8, opt, parts, len(graphs))
+        assert code == 0
+        rtol = 1e-6 if precision == "fp64" else 1e-3
+        for q, gq in enumerate(graphs):
+            assert status[q] == spx.OK, (q, status[q], iters[q])
+            pq = parts[gptr[q]:gptr[q + 1]]
+            assert O.cutsize(gq, pq)[0] == cuts[q] and imbs[q] == O.imbalance(pq, None, 8)
+            ref = O.partition(gq, 8, problem=lap, precond="poly", poly_degree=k, tol=1e-3, seed=6)
+            assert np.allclose(eigs[q, 1:], ref.eigenvalues[1:], rtol=rtol), (q, eigs[q], ref.eigenvalues)
+            assert abs(cuts[q] - ref.cut) <= 0.02 * ref.cut, (q, cuts[q], ref.cut)
+            if precision == "fp64":
+                # the same algorithm from the same start: iteration counts agree closely
+                assert abs(int(iters[q]) - ref.iterations) <= max(2, ref.iterations // 10), (q, iters[q],
+                                                                                              ref.iterations)
+    finally:
+        spx.sphynx_destroy(h)

@@ -103,9 +103,16 @@ def test_degrees_exact():
         info = spx.sphynx_get_info(h)
         assert info["max_degree"] == int(g.degrees().max())
         assert info["long_rows"] == int(np.sum(g.degrees() > 32))
-        assert info["spmm_variant"] in (0, 1) and info["tuned_us_csr"] > 0 and info["tuned_us_sell"] > 0
-        # the tuner kept the faster schedule
-        assert (info["tuned_us_sell"] < info["tuned_us_csr"]) == (info["spmm_variant"] == 1)
+        assert info["spmm_variant"] in (0, 1, 2) and info["tuned_us_csr"] > 0 and info["tuned_us_sell"] > 0
+        # the tuner kept the fastest schedule it timed (the shared-pattern one
+        # only where the graph has such slices)
+        times = [info["tuned_us_csr"], info["tuned_us_sell"]]
+        if info["sell_pattern_slices"] > 0:
+            assert info["tuned_us_pattern"] > 0
+            times.append(info["tuned_us_pattern"])
+        else:
+            assert info["tuned_us_pattern"] == 0 and info["spmm_variant"] != 2
+        assert info["spmm_variant"] == int(np.argmin(times))
         assert info["sell_stride"] in (1, 2, 4, 8, 16)
         if info["spmm_variant"] == 0:
             assert info["sell_stride"] == 1
