@@ -157,7 +157,11 @@ typedef struct {
   double ms_spmm_by_dt[3];
   double spmm_bytes_by_dt[3];
   int64_t spmm_launches_by_dt[3];
-  double reserved[4];
+  int32_t fp64_finished; /* sphynx_partition_batch with float blocks: graphs that
+                            stalled at the float rounding floor above tol |theta|
+                            and finished in FP64 blocks from their float iterate */
+  int32_t reserved_i;
+  double reserved[3];
 } sphynx_stats;
 
 typedef struct {
@@ -434,7 +438,14 @@ int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, const float 
  * eigenvalues (double[count * d], d = floor(log2 K) + 1, each graph's Ritz
  * values ascending), iterations and status (int32[count], OK or NOCONV per
  * graph): host arrays, each may be NULL.  stats (may be NULL): status OK only if every graph
- * converged, iterations = the largest.  Errors: INVALID_ARG (not a batch
+ * converged, iterations = the largest, fp64_finished = graphs that went on in
+ * FP64 blocks.  With float blocks (FP32, MIXED_BF16) a graph whose tol |theta|
+ * lies below the float rounding floor of its residual stalls there; once
+ * every unconverged column has gone stall_window iterations (20 when 0)
+ * without a 10 % gain at that floor, the graph resumes in FP64 blocks from
+ * its float iterate (iterations count on, under the same max_iter), and the
+ * embedding and multi-jagged step then run on double coordinates for all
+ * graphs.  Errors: INVALID_ARG (not a batch
  * handle), UNSUPPORTED (multigrid preconditioner, polynomial of degree 1,
  * piecewise start, K x count > 2^20), BREAKDOWN (a graph's polynomial setup
  * failed), CUDA, OOM. */

@@ -20,6 +20,8 @@ Modules and the parts of the paper they follow:
 * ``mj``         the multi-jagged multisection of Sec. 4 with an exact,
   integer split rule.
 * ``metrics``    cutsize (Eq. 1) and imbalance (Sec. 3.1).
+* ``refine``     the greedy cut refinement Sec. 7 proposes as future work, in
+  the library's parallel, balance-constrained reading.
 * ``sphynx``     Algorithm 2, the whole partitioner.
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against closed
@@ -39,5 +41,6 @@ from .amg import (aggregate, mis2_roots, coarse_graph, build_hierarchy, vcycle, 
                   power_lambda_max, vertex_keys)
 from .mj import multijagged, coord_sort_key  # noqa: F401
 from .metrics import cutsize, imbalance, part_weights  # noqa: F401
+from .refine import refine, vertex_gains, capacity, integer_weights  # noqa: F401
 from .sphynx import (partition, num_eigenvectors, initial_block, canonical_rotation, eigen_clusters,  # noqa: F401
                      sign_normalise, is_regular, default_options, gershgorin_rho, max_row_terms)

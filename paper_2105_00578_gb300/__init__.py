@@ -55,10 +55,12 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("cut", C.c_double), ("cut_twice", C.c_double),
                 ("imbalance", C.c_double),
                 ("ms_spmm_by_dt", C.c_double * 3), ("spmm_bytes_by_dt", C.c_double * 3),
-                ("spmm_launches_by_dt", C.c_int64 * 3), ("reserved", C.c_double * 4)]
+                ("spmm_launches_by_dt", C.c_int64 * 3), ("fp64_finished", C.c_int32), ("reserved_i", C.c_int32),
+                ("reserved", C.c_double * 3)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "eigenvalues", "resnorm")}
+        d = {f: getattr(self, f) for f, _ in self._fields_
+             if f not in ("reserved", "reserved_i", "eigenvalues", "resnorm")}
         d["eigenvalues"] = list(self.eigenvalues[: self.nev])
         d["resnorm"] = list(self.resnorm[: self.nev])
         return d

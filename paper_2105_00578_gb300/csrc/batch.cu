@@ -34,6 +34,9 @@ namespace {
 constexpr int kBatchChunk = 1024;   // rows per chunk
 constexpr int kGramRows = 64;       // rows staged per step of the batched Gram kernel
 constexpr int kGramThreads = 256;
+// iterations without a 10 % residual gain (at the float rounding floor) after
+// which a float-block graph moves on to FP64 blocks
+constexpr int kPromoteWindow = 20;
 
 int round4(int b) { return (b + 3) & ~3; }
 
@@ -829,6 +832,38 @@ void batch_setup(sphynx_graph *g, const int64_t *h_gptr, int count) {
   SPX_LAUNCHED();
 }
 
+// float blocks to double, every row
+__global__ void k_widen(ChunkView cv, const float *x, int ld, double *y) {
+  const int c = blockIdx.x;
+  for (int64_t e = cv.begin[c] * ld + threadIdx.x; e < cv.begin[c + 1] * ld; e += blockDim.x)
+    y[e] = static_cast<double>(x[e]);
+}
+
+// reopen the promoted graphs for the FP64 phase: not done, nothing converged,
+// no search direction yet, stall bookkeeping cleared; their iteration counts
+// go on; ctl[0] = graphs not done, ctl[1] = 0 (the loop's own count)
+__global__ void k_bpromote(SolverState *states, int count, const char *promoted, int *ctl) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0) {
+    ctl[1] = 0;
+    int c = 0;
+    for (int k = 0; k < count; ++k) c += promoted[k] ? 1 : 0;
+    ctl[0] = c;
+  }
+  if (q >= count || !promoted[q]) return;
+  SolverState *s = states + q;
+  s->done = 0;
+  s->status = SPHYNX_OK;
+  s->nconv = 0;
+  s->pvalid = 0;
+  s->stalled = 0;
+  for (int j = 0; j < SPHYNX_MAX_NEV; ++j) {
+    s->conv[j] = 0;
+    s->best_res[j] = 0.0;
+    s->since_best[j] = 0;
+  }
+}
+
 // The batched partition: every graph's LOBPCG in one captured graph launch,
 // then the per-graph embedding, multi-jagged and metrics.
 void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *dpart, double *cuts, double *imbs,
@@ -861,47 +896,26 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   if (b > SPHYNX_MAX_NEV) fail(SPHYNX_ERR_UNSUPPORTED, "K too large for %d eigenvectors", SPHYNX_MAX_NEV);
   cudaStream_t st = g->stream;
   const int64_t n = g->n;
-  const DT dt = o->precision == SPHYNX_FP64 ? DT::F64 : DT::F32;
-  const size_t es = dt_size(dt);
+  const DT dt0 = o->precision == SPHYNX_FP64 ? DT::F64 : DT::F32;
   const int ld = round4(b), M3 = 3 * ld;
   const int lap = o->laplacian == SPHYNX_NORMALIZED ? SPHYNX_NORMALIZED : SPHYNX_COMBINATORIAL;
   const bool gen = o->laplacian == SPHYNX_GENERALIZED;
-  const double u_work = o->precision == SPHYNX_FP64 ? 0x1.0p-53 : 0x1.0p-24;
   const int rho_from_degree = lap == SPHYNX_COMBINATORIAL && !gen ? 1 : 0;        // noise floors, per graph
   const bool jac = o->precond == SPHYNX_PRECOND_JACOBI && lap == SPHYNX_COMBINATORIAL;
   const bool poly = o->precond == SPHYNX_PRECOND_POLY;
-  const size_t blk = static_cast<size_t>(n) * ld * es;
   const int64_t nch = B.n_chunks;
   if (poly) {   // every graph's polynomial (Sec. 5.2), set up anew as a single-graph partition does
-    if (dt == DT::F64) batch_poly_setup_t<double>(g, o->poly_degree, lap, o->seed);
+    if (dt0 == DT::F64) batch_poly_setup_t<double>(g, o->poly_degree, lap, o->seed);
     else batch_poly_setup_t<float>(g, o->poly_degree, lap, o->seed);
-  }
-  const DT ct = o->precision == SPHYNX_FP64 ? DT::F64 : (o->precision == SPHYNX_MIXED_BF16 ? DT::BF16 : DT::F32);
-
-  void *X[2] = {g->workspace("X0", blk, false), g->workspace("X1", blk, false)};
-  void *LX[2] = {g->workspace("LX0", blk, false), g->workspace("LX1", blk, false)};
-  void *P[2] = {g->workspace("P0", blk, true), g->workspace("P1", blk, true)};
-  void *LP[2] = {g->workspace("LP0", blk, true), g->workspace("LP1", blk, true)};
-  void *H = g->workspace("H", blk, true);
-  void *LH = g->workspace("LH", blk, true);
-  // the residual goes to H directly (Jacobi, none) or to R, from which the chain makes H
-  void *R = poly ? g->workspace("bR", blk, true) : H;
-  void *chain[2] = {nullptr, nullptr};
-  if (poly) {
-    chain[0] = g->workspace("chain0", static_cast<size_t>(n) * ld * dt_size(ct), false);
-    chain[1] = g->workspace("chain1", static_cast<size_t>(n) * ld * dt_size(ct), false);
   }
   const size_t ntot3 = static_cast<size_t>(M3) * (M3 + 1);
   double *gpart = static_cast<double *>(g->workspace("bgram_part", static_cast<size_t>(nch) * ntot3 * 8, false));
   double *ga = static_cast<double *>(g->workspace("bga", static_cast<size_t>(count) * M3 * M3 * 8, true));
   double *gb = static_cast<double *>(g->workspace("bgb", static_cast<size_t>(count) * M3 * M3 * 8, true));
-  void *yt = g->workspace("byt", static_cast<size_t>(count) * M3 * ld * es, true);
   double *npart = static_cast<double *>(g->workspace("bnpart", static_cast<size_t>(nch) * ld * 8, false));
   SolverState *states =
       static_cast<SolverState *>(g->workspace("bstates", static_cast<size_t>(count) * sizeof(SolverState), true));
   int *ctl = static_cast<int *>(g->workspace("bctl", 4 * sizeof(int), false));
-  const void *bd = gen ? (dt == DT::F64 ? static_cast<const void *>(g->deg.p) : g->degf.p) : nullptr;
-  const void *jv = jac ? (dt == DT::F64 ? static_cast<const void *>(g->jinv.p) : g->jinvf.p) : nullptr;
   const int mixed = 0;   // the m x m eigenproblem is solved in FP64 for every block precision
   const int32_t *gc0 = B.graph_chunk0.as<int32_t>();
   const unsigned cgrid = static_cast<unsigned>(nch);
@@ -910,165 +924,259 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   const bool timing = g->ctr.timing;
   g->ctr.timing = false;   // per-launch events cannot live inside a captured loop
 
-  auto gram = [&](int nb, const void *const *s, const void *const *ls) {
-    if (dt == DT::F64) launch_bgram_t<double>(st, g, states, nb, ld, s, ls, bd, gpart);
-    else launch_bgram_t<float>(st, g, states, nb, ld, s, ls, bd, gpart);
-    k_bgram_reduce<<<count, 256, 0, st>>>(gc0, states, nb * ld, gpart, ga, gb);
-    SPX_LAUNCHED();
+  // One precision phase of the batched eigensolve: blocks of type dt (chain
+  // vectors of type ct), started from the random block or (warm) from the
+  // blocks already in X[0], the graphs whose state is not done iterating.
+  // Returns the blocks; a graph's Ritz vectors end in X[(1 + its phase
+  // iterations) & 1].
+  struct Blocks {
+    void *X[2], *LX[2], *P[2], *LP[2], *H, *LH, *R, *chain[2], *yt;
   };
-  auto update = [&](int nb, const void *const *s, const void *const *ls, void *xo, void *po, void *lpo) {
-    if (dt == DT::F64) launch_bupdate_ld<double>(st, g, states, ld, nb, s, ls, yt, xo, po, lpo);
-    else launch_bupdate_ld<float>(st, g, states, ld, nb, s, ls, yt, xo, po, lpo);
-  };
-  auto residual = [&](const void *x, const void *lx, void *out) {
-    if (dt == DT::F64) launch_bresidual_ld<double>(st, g, states, ld, x, lx, bd, jv, out, npart);
-    else launch_bresidual_ld<float>(st, g, states, ld, x, lx, bd, jv, out, npart);
-  };
-  auto converge = [&](int count_iteration) {
-    k_bconverge<<<(count + 127) / 128, 128, 0, st>>>(gc0, states, count, npart, b, ld, o->tol, u_work, rho_from_degree,
-                                                      B.graph_max.as<unsigned long long>(),
-                                                      count_iteration, o->max_iter, o->stall_window,
-                                                      o->conv == SPHYNX_CONV_ABS ? 1 : 0, ctl);
-    SPX_LAUNCHED();
-  };
-  // H = p(L) R with each row's graph's roots: the single-graph product-form chain
-  auto precondition = [&]() {
-    if (!poly) return;
-    const int k = B.poly_k;
-    for (int i = 0; i + 1 < k; ++i) {
+  auto run_phase = [&](DT dt, DT ct, const char *tag, bool warm, int window) -> Blocks {
+    const size_t es = dt_size(dt);
+    const size_t blk = static_cast<size_t>(n) * ld * es;
+    const double u_work = dt == DT::F64 ? 0x1.0p-53 : 0x1.0p-24;
+    const std::string t(tag);
+    Blocks k{};
+    k.X[0] = g->workspace("X0" + t, blk, false);
+    k.X[1] = g->workspace("X1" + t, blk, false);
+    k.LX[0] = g->workspace("LX0" + t, blk, false);
+    k.LX[1] = g->workspace("LX1" + t, blk, false);
+    k.P[0] = g->workspace("P0" + t, blk, true);
+    k.P[1] = g->workspace("P1" + t, blk, true);
+    k.LP[0] = g->workspace("LP0" + t, blk, true);
+    k.LP[1] = g->workspace("LP1" + t, blk, true);
+    k.H = g->workspace("H" + t, blk, true);
+    k.LH = g->workspace("LH" + t, blk, true);
+    // the residual goes to H directly (Jacobi, none) or to R, from which the chain makes H
+    k.R = poly ? g->workspace("bR" + t, blk, true) : k.H;
+    if (poly) {
+      k.chain[0] = g->workspace("chain0" + t, static_cast<size_t>(n) * ld * dt_size(ct), false);
+      k.chain[1] = g->workspace("chain1" + t, static_cast<size_t>(n) * ld * dt_size(ct), false);
+    }
+    k.yt = g->workspace("byt" + t, static_cast<size_t>(count) * M3 * ld * es, true);
+    void **X = k.X, **LX = k.LX, **P = k.P, **LP = k.LP;
+    void *H = k.H, *LH = k.LH, *R = k.R, *yt = k.yt;
+    const void *bd = gen ? (dt == DT::F64 ? static_cast<const void *>(g->deg.p) : g->degf.p) : nullptr;
+    const void *jv = jac ? (dt == DT::F64 ? static_cast<const void *>(g->jinv.p) : g->jinvf.p) : nullptr;
+
+    auto gram = [&](int nb, const void *const *s, const void *const *ls) {
+      if (dt == DT::F64) launch_bgram_t<double>(st, g, states, nb, ld, s, ls, bd, gpart);
+      else launch_bgram_t<float>(st, g, states, nb, ld, s, ls, bd, gpart);
+      k_bgram_reduce<<<count, 256, 0, st>>>(gc0, states, nb * ld, gpart, ga, gb);
+      SPX_LAUNCHED();
+    };
+    auto update = [&](int nb, const void *const *s, const void *const *ls, void *xo, void *po, void *lpo) {
+      if (dt == DT::F64) launch_bupdate_ld<double>(st, g, states, ld, nb, s, ls, yt, xo, po, lpo);
+      else launch_bupdate_ld<float>(st, g, states, ld, nb, s, ls, yt, xo, po, lpo);
+    };
+    auto residual = [&](const void *x, const void *lx, void *out) {
+      if (dt == DT::F64) launch_bresidual_ld<double>(st, g, states, ld, x, lx, bd, jv, out, npart);
+      else launch_bresidual_ld<float>(st, g, states, ld, x, lx, bd, jv, out, npart);
+    };
+    auto converge = [&](int count_iteration) {
+      k_bconverge<<<(count + 127) / 128, 128, 0, st>>>(gc0, states, count, npart, b, ld, o->tol, u_work,
+                                                        rho_from_degree, B.graph_max.as<unsigned long long>(),
+                                                        count_iteration, o->max_iter, window,
+                                                        o->conv == SPHYNX_CONV_ABS ? 1 : 0, ctl);
+      SPX_LAUNCHED();
+    };
+    // H = p(L) R with each row's graph's roots: the single-graph product-form chain
+    auto precondition = [&]() {
+      if (!poly) return;
+      const int kk = B.poly_k;
+      for (int i = 0; i + 1 < kk; ++i) {
+        SpmmArgs a{};
+        a.lap = lap;
+        a.tin = i == 0 ? dt : ct;
+        a.ld_x = a.ld_y = a.bp = ld;
+        a.b_true = b;
+        a.x = i == 0 ? R : k.chain[(i - 1) & 1];
+        a.mode = 1;
+        a.t_out = k.chain[i & 1];
+        a.tout = ct;
+        a.yacc = H;
+        a.first = i == 0 ? 1 : 0;
+        a.yterms = (i % 2 == 0) ? 2 : (i + 2 == kk ? 1 : 0);
+        a.inv = B.poly_inv.as<double>();
+        a.invf = B.poly_invf.as<float>();
+        a.i_cur = i;
+        a.row_graph = B.row_graph.as<int32_t>();
+        a.inv_stride = kk + 1;
+        spmm(g, a);
+      }
+    };
+    auto spmm_block = [&](const void *x, void *y) {
       SpmmArgs a{};
       a.lap = lap;
-      a.tin = i == 0 ? dt : ct;
-      a.ld_x = a.ld_y = a.bp = ld;
+      a.tin = dt;
+      a.ld_x = ld;
+      a.ld_y = ld;
+      a.bp = ld;
       a.b_true = b;
-      a.x = i == 0 ? R : chain[(i - 1) & 1];
-      a.mode = 1;
-      a.t_out = chain[i & 1];
-      a.tout = ct;
-      a.yacc = H;
-      a.first = i == 0 ? 1 : 0;
-      a.yterms = (i % 2 == 0) ? 2 : (i + 2 == k ? 1 : 0);
-      a.inv = B.poly_inv.as<double>();
-      a.invf = B.poly_invf.as<float>();
-      a.i_cur = i;
-      a.row_graph = B.row_graph.as<int32_t>();
-      a.inv_stride = k + 1;
+      a.x = x;
+      a.y = y;
+      a.mode = 0;
       spmm(g, a);
-    }
-  };
-  auto spmm_block = [&](const void *x, void *y) {
-    SpmmArgs a{};
-    a.lap = lap;
-    a.tin = dt;
-    a.ld_x = ld;
-    a.ld_y = ld;
-    a.bp = ld;
-    a.b_true = b;
-    a.x = x;
-    a.y = y;
-    a.mode = 0;
-    spmm(g, a);
-  };
+    };
 
-  // every graph's random block on its local rows; then the first Rayleigh-Ritz and residual
-  if (dt == DT::F64)
-    k_brandom<double><<<cgrid, 256, 0, st>>>(static_cast<double *>(X[0]), view_of(g), B.gptr.as<int64_t>(), b, ld,
-                                             mix64(o->seed + kGamma));
-  else
-    k_brandom<float><<<cgrid, 256, 0, st>>>(static_cast<float *>(X[0]), view_of(g), B.gptr.as<int64_t>(), b, ld,
-                                            mix64(o->seed + kGamma));
-  SPX_LAUNCHED();
-  spmm_block(X[0], LX[0]);
-  {
-    // the first Rayleigh-Ritz: ld x ld problems per graph, back to back
-    const void *s1[3] = {X[0], X[0], X[0]}, *l1[3] = {LX[0], LX[0], LX[0]};
-    gram(1, s1, l1);
-  }
-  launch_rayleigh_ritz(st, ga, gb, ld, ld, b, u_work, states, nullptr, yt, dt, nullptr, nullptr, nullptr, mixed,
-                       count);
-  {
-    const void *s1[3] = {X[0], nullptr, nullptr}, *l1[3] = {nullptr, nullptr, nullptr};
-    update(1, s1, l1, X[1], nullptr, nullptr);
-  }
-  spmm_block(X[1], LX[1]);
-  residual(X[1], LX[1], R);
-  converge(0);
-  SPX_CUDA(cudaStreamSynchronize(st));
-
-  // the iteration body, captured once and repeated by a conditional WHILE node
-  // (two bodies, one per ping-pong parity, so that a body is a fixed sequence)
-  cudaGraph_t graph;
-  SPX_CUDA(cudaGraphCreate(&graph, 0));
-  cudaGraphConditionalHandle cond;
-  SPX_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams cp{};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = cond;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t cnode;
-  SPX_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  cudaStream_t cs;
-  SPX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  cudaStream_t saved = g->stream;
-  g->stream = cs;
-  st = cs;
-  try {
-    SPX_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    for (int half = 0; half < 2; ++half) {   // X[1] -> X[0] -> X[1]: two iterations per body
-      const int cur = half == 0 ? 1 : 0, nx = cur ^ 1;
-      precondition();
-      spmm_block(H, LH);
-      const void *s3[3] = {X[cur], H, P[cur]}, *l3[3] = {LX[cur], LH, LP[cur]};
-      gram(3, s3, l3);
-      launch_rayleigh_ritz(st, ga, gb, M3, ld, b, u_work, states, nullptr, yt, dt, nullptr, nullptr, nullptr, mixed,
-                           count);
-      update(3, s3, l3, X[nx], P[nx], LP[nx]);
-      spmm_block(X[nx], LX[nx]);
-      residual(X[nx], LX[nx], R);
-      converge(1);
+    // every graph's random block on its local rows (unless warm); then the
+    // first Rayleigh-Ritz and residual
+    if (!warm) {
+      if (dt == DT::F64)
+        k_brandom<double><<<cgrid, 256, 0, st>>>(static_cast<double *>(X[0]), view_of(g), B.gptr.as<int64_t>(), b,
+                                                 ld, mix64(o->seed + kGamma));
+      else
+        k_brandom<float><<<cgrid, 256, 0, st>>>(static_cast<float *>(X[0]), view_of(g), B.gptr.as<int64_t>(), b, ld,
+                                                mix64(o->seed + kGamma));
+      SPX_LAUNCHED();
     }
-    k_bloop_condition<<<1, 1, 0, cs>>>(ctl, (o->max_iter + 1) / 2, cond);
-    SPX_LAUNCHED();
-    cudaGraph_t captured = nullptr;
-    SPX_CUDA(cudaStreamEndCapture(cs, &captured));
-  } catch (...) {
-    cudaGraph_t junk = nullptr;
-    cudaStreamEndCapture(cs, &junk);
+    spmm_block(X[0], LX[0]);
+    {
+      // the first Rayleigh-Ritz: ld x ld problems per graph, back to back
+      const void *s1[3] = {X[0], X[0], X[0]}, *l1[3] = {LX[0], LX[0], LX[0]};
+      gram(1, s1, l1);
+    }
+    launch_rayleigh_ritz(st, ga, gb, ld, ld, b, u_work, states, nullptr, yt, dt, nullptr, nullptr, nullptr, mixed,
+                         count);
+    {
+      const void *s1[3] = {X[0], nullptr, nullptr}, *l1[3] = {nullptr, nullptr, nullptr};
+      update(1, s1, l1, X[1], nullptr, nullptr);
+    }
+    spmm_block(X[1], LX[1]);
+    residual(X[1], LX[1], R);
+    converge(0);
+    SPX_CUDA(cudaStreamSynchronize(st));
+
+    // the iteration body, captured once and repeated by a conditional WHILE node
+    // (two bodies, one per ping-pong parity, so that a body is a fixed sequence)
+    cudaGraph_t graph;
+    SPX_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    SPX_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    SPX_CUDA(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    SPX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = g->stream;
+    g->stream = cs;
+    st = cs;
+    try {
+      SPX_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      for (int half = 0; half < 2; ++half) {   // X[1] -> X[0] -> X[1]: two iterations per body
+        const int cur = half == 0 ? 1 : 0, nx = cur ^ 1;
+        precondition();
+        spmm_block(H, LH);
+        const void *s3[3] = {X[cur], H, P[cur]}, *l3[3] = {LX[cur], LH, LP[cur]};
+        gram(3, s3, l3);
+        launch_rayleigh_ritz(st, ga, gb, M3, ld, b, u_work, states, nullptr, yt, dt, nullptr, nullptr, nullptr,
+                             mixed, count);
+        update(3, s3, l3, X[nx], P[nx], LP[nx]);
+        spmm_block(X[nx], LX[nx]);
+        residual(X[nx], LX[nx], R);
+        converge(1);
+      }
+      k_bloop_condition<<<1, 1, 0, cs>>>(ctl, (o->max_iter + 1) / 2, cond);
+      SPX_LAUNCHED();
+      cudaGraph_t captured = nullptr;
+      SPX_CUDA(cudaStreamEndCapture(cs, &captured));
+    } catch (...) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(cs, &junk);
+      g->stream = saved;
+      cudaStreamDestroy(cs);
+      cudaGraphDestroy(graph);
+      throw;
+    }
     g->stream = saved;
-    cudaStreamDestroy(cs);
+    st = saved;
+    cudaGraphExec_t exec;
+    SPX_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    // the whole batched eigensolve of this phase: one launch
+    SPX_CUDA(cudaGraphLaunch(exec, st));
+    SPX_CUDA(cudaStreamSynchronize(st));
+    cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
-    throw;
-  }
-  g->stream = saved;
-  st = saved;
-  cudaGraphExec_t exec;
-  SPX_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-  // the whole batched eigensolve: one launch
-  SPX_CUDA(cudaGraphLaunch(exec, st));
-  SPX_CUDA(cudaStreamSynchronize(st));
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
-  cudaStreamDestroy(cs);
-  g->ctr.timing = timing;
+    cudaStreamDestroy(cs);
+    return k;
+  };
 
-  // per-graph results; a graph's Ritz vectors are in X[(1 + iters) & 1]
-  std::vector<SolverState> hs(count);
-  SPX_CUDA(cudaMemcpyAsync(hs.data(), states, count * sizeof(SolverState), cudaMemcpyDeviceToHost, st));
-  SPX_CUDA(cudaStreamSynchronize(st));
-  // bring every graph's vectors into X[0] (rows of graphs that ended on X[1] copied over)
-  for (int q = 0; q < count; ++q) {
-    if (((1 + hs[q].iters) & 1) == 1) {
+  // bring every graph's vectors of a phase into X[0] (rows of graphs whose
+  // phase ended on X[1] copied over)
+  auto gather_x0 = [&](const Blocks &k, DT dt, const std::vector<SolverState> &hs, const std::vector<int> &it0,
+                       const std::vector<char> &take) {
+    const size_t es = dt_size(dt);
+    for (int q = 0; q < count; ++q) {
+      if (!take[q] || ((1 + hs[q].iters - it0[q]) & 1) == 0) continue;
       const size_t off = static_cast<size_t>(B.h_gptr[q]) * ld * es;
       const size_t bytes = static_cast<size_t>(B.h_gptr[q + 1] - B.h_gptr[q]) * ld * es;
-      SPX_CUDA(cudaMemcpyAsync(static_cast<char *>(X[0]) + off, static_cast<const char *>(X[1]) + off, bytes,
+      SPX_CUDA(cudaMemcpyAsync(static_cast<char *>(k.X[0]) + off, static_cast<const char *>(k.X[1]) + off, bytes,
                                cudaMemcpyDeviceToDevice, st));
     }
+  };
+  auto read_states = [&]() {
+    std::vector<SolverState> hs(count);
+    SPX_CUDA(cudaMemcpyAsync(hs.data(), states, count * sizeof(SolverState), cudaMemcpyDeviceToHost, st));
+    SPX_CUDA(cudaStreamSynchronize(st));
+    return hs;
+  };
+
+  // Phase 1 in the requested precision.  Float blocks cannot resolve a
+  // residual below about u ||L|| (the rounding of the stored vectors), and
+  // tol |theta_2| lies below that on large graphs with small eigenvalues:
+  // such a graph stops once it stalls at that floor (the stall window) and
+  // finishes in FP64 blocks, warm-started from its float iterate.
+  const bool promote = dt0 != DT::F64;
+  const int window1 = promote ? (o->stall_window > 0 ? o->stall_window : kPromoteWindow) : o->stall_window;
+  const DT ct0 = o->precision == SPHYNX_FP64 ? DT::F64 : (o->precision == SPHYNX_MIXED_BF16 ? DT::BF16 : DT::F32);
+  Blocks k1 = run_phase(dt0, ct0, "", false, window1);
+  std::vector<SolverState> hs = read_states();
+  std::vector<int> zero_it(count, 0);
+  std::vector<char> all(count, 1);
+  gather_x0(k1, dt0, hs, zero_it, all);
+  DT dt = dt0;
+  void *EX = k1.X[0];   // the final Ritz vectors of every graph (n x ld, type dt)
+  std::vector<char> promoted(count, 0);
+  int n_promoted = 0;
+  if (promote) {
+    for (int q = 0; q < count; ++q)
+      if (hs[q].status != SPHYNX_OK && hs[q].iters < o->max_iter) {
+        promoted[q] = 1;
+        ++n_promoted;
+      }
   }
+  if (n_promoted > 0) {
+    std::vector<int> it1(count);
+    for (int q = 0; q < count; ++q) it1[q] = hs[q].iters;
+    // every graph's float vectors widened to double; the promoted graphs resume from theirs
+    const size_t blk64 = static_cast<size_t>(n) * ld * 8;
+    double *X64 = static_cast<double *>(g->workspace("X0_64", blk64, false));
+    k_widen<<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const float *>(EX), ld, X64);
+    SPX_LAUNCHED();
+    DevBuf dprom;
+    dprom.alloc(static_cast<size_t>(count));
+    SPX_CUDA(cudaMemcpyAsync(dprom.p, promoted.data(), static_cast<size_t>(count), cudaMemcpyHostToDevice, st));
+    k_bpromote<<<(count + 127) / 128, 128, 0, st>>>(states, count, dprom.as<char>(), ctl);
+    SPX_LAUNCHED();
+    SPX_CUDA(cudaStreamSynchronize(st));   // `promoted` feeds an asynchronous copy
+    Blocks k2 = run_phase(DT::F64, DT::F64, "_64", true, o->stall_window);
+    hs = read_states();
+    gather_x0(k2, DT::F64, hs, it1, promoted);
+    dt = DT::F64;
+    EX = k2.X[0];
+  }
+  const size_t es = dt_size(dt);
+  g->ctr.timing = timing;
+
   for (int q = 0; q < count; ++q) {
     const int64_t r0 = B.h_gptr[q], rows = B.h_gptr[q + 1] - r0;
-    canonical_rotation_block(g, static_cast<char *>(X[0]) + static_cast<size_t>(r0) * ld * es, rows, ld, dt,
+    canonical_rotation_block(g, static_cast<char *>(EX) + static_cast<size_t>(r0) * ld * es, rows, ld, dt,
                              hs[q].theta, d, o->tol, o->seed);
   }
   // embedding (Algorithm 2), signs per graph
@@ -1076,16 +1184,16 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   int64_t *pidx = static_cast<int64_t *>(g->workspace("bsg_idx", static_cast<size_t>(nch) * b * 8, false));
   double *sign = static_cast<double *>(g->workspace("bsg", static_cast<size_t>(count) * b * 8, false));
   void *coords = g->workspace("coords", static_cast<size_t>(n) * (d - 1) * es + 16, false);
-  if (dt == DT::F64) k_bargmax<double><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const double *>(X[0]), ld, b, pval, pidx);
-  else k_bargmax<float><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const float *>(X[0]), ld, b, pval, pidx);
+  if (dt == DT::F64) k_bargmax<double><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const double *>(EX), ld, b, pval, pidx);
+  else k_bargmax<float><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const float *>(EX), ld, b, pval, pidx);
   SPX_LAUNCHED();
   k_bsigns<<<(count * b + 255) / 256, 256, 0, st>>>(gc0, count, b, pval, pidx, sign);
   SPX_LAUNCHED();
   if (dt == DT::F64)
-    k_bcoords<double><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const double *>(X[0]), ld, b, sign,
+    k_bcoords<double><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const double *>(EX), ld, b, sign,
                                              static_cast<double *>(coords));
   else
-    k_bcoords<float><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const float *>(X[0]), ld, b, sign,
+    k_bcoords<float><<<cgrid, 256, 0, st>>>(view_of(g), static_cast<const float *>(EX), ld, b, sign,
                                             static_cast<float *>(coords));
   SPX_LAUNCHED();
   // multi-jagged over all graphs at once: graph q owns parts [q K, (q + 1) K)
@@ -1134,6 +1242,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     int maxit = 0;
     for (int q = 0; q < count; ++q) maxit = std::max(maxit, hs[q].iters);
     stats->status = nconv_graphs == count ? SPHYNX_OK : SPHYNX_ERR_NOCONV;
+    stats->fp64_finished = n_promoted;
     stats->iterations = maxit;
     stats->nev = b;
   }

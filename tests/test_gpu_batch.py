@@ -153,3 +153,32 @@ def test_batch_polynomial_matches_oracle_per_graph(precision, lap, k):
                                                                                               ref.iterations)
     finally:
         spx.sphynx_destroy(h)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed_bf16"])
+def test_float_batch_finishes_below_the_float_floor_in_fp64(precision):
+    """Graphs of 6,000 to 20,000 vertices have tol theta_2 near or below the
+    rounding floor of float blocks (about u ||L||): they stall there, resume
+    in FP64 blocks from their float iterate and converge.  Every graph ends
+    OK, its residual recomputed by the oracle in FP64 from the returned Ritz
+    values is within tol theta, and the cut is within 2 % of the oracle's."""
+    import paper_2105_00578_gb300 as spx
+    graphs = _rggs([6000, 20000, 1200, 11000, 800], 200)
+    big, gptr = W.concat_graphs(graphs)
+    h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr)
+    try:
+        opt = spx.options(laplacian="combinatorial", precond="poly", poly_degree=25, precision=precision, tol=1e-3,
+                          seed=8)
+        parts = np.full(big.n, -1, dtype=np.int32)
+        code, cuts, imbs, eigs, iters, status, st = spx.sphynx_partition_batch(h, 8, opt, parts, len(graphs))
+        assert code == 0 and st["status"] == spx.OK, (status, iters)
+        assert st["fp64_finished"] >= 1
+        for q, gq in enumerate(graphs):
+            assert status[q] == spx.OK, (q, status[q], iters[q])
+            pq = parts[gptr[q]:gptr[q + 1]]
+            assert O.cutsize(gq, pq)[0] == cuts[q] and imbs[q] == O.imbalance(pq, None, 8)
+            ref = O.partition(gq, 8, problem="combinatorial", precond="poly", poly_degree=25, tol=1e-3, seed=8)
+            assert np.allclose(eigs[q, 1:], ref.eigenvalues[1:], rtol=1e-3), (q, eigs[q], ref.eigenvalues)
+            assert abs(cuts[q] - ref.cut) <= 0.02 * ref.cut, (q, cuts[q], ref.cut)
+    finally:
+        spx.sphynx_destroy(h)
