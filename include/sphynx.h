@@ -129,7 +129,10 @@ typedef struct {
                           10 u rho (FP32 blocks cannot reach tol * theta when
                           that is below the FP32 rounding of L x)             */
   int32_t conv;        /* SPHYNX_CONV_REL_THETA (default) | SPHYNX_CONV_ABS     */
-  int32_t reserved[4];
+  int32_t refine_rounds;/* sphynx_partition: 0 (default) leaves the multi-jagged
+                          partition as it is; r > 0 runs at most r rounds of
+                          greedy refinement (sphynx_refine, eps = 0.01) on it  */
+  int32_t reserved[3];
 } sphynx_options;
 
 typedef struct {
@@ -160,7 +163,7 @@ typedef struct {
   int32_t fp64_finished; /* sphynx_partition_batch with float blocks: graphs that
                             stalled at the float rounding floor above tol |theta|
                             and finished in FP64 blocks from their float iterate */
-  int32_t reserved_i;
+  int32_t refine_moves;  /* vertices moved by greedy refinement (refine_rounds)  */
   double reserved[3];
 } sphynx_stats;
 
@@ -410,6 +413,28 @@ int sphynx_eval(sphynx_handle g, const int32_t *part, int32_t K, double *cut,
 int sphynx_partition(sphynx_handle g, int32_t K, const sphynx_options *opt, int32_t *part_out,
                      double *cut_out, double *imbalance_out, sphynx_stats *stats);
 
+/* Greedy refinement of a K-way partition (Sec. 7 proposes a greedy
+ * improvement step after the spectral partition; the paper gives no
+ * algorithm, this is the library's parallel reading).  part: device
+ * int32[n] with values in [0, K), changed in place.  Each round: every
+ * vertex of at most 256 neighbours finds the external part it is most
+ * connected to (the smallest part on ties) and its gain, that connection
+ * minus its connection to its own part, in exact integers (edge weights
+ * w * 2^s as the exact cut sums them, integer vertex weights); a vertex of
+ * positive gain is selected when no neighbour of positive gain outranks it
+ * (higher gain, or equal gain and a lower id), so the selected vertices are
+ * pairwise non-adjacent and each gain is exactly the cut its move removes;
+ * a part takes all the selected vertices aimed at it when its weight stays
+ * within cap = floor((1 + eps) W_total / K) (evaluated in double), otherwise
+ * only the one of highest priority if that fits.  Rounds stop when none
+ * moves or after max_rounds.  The cut never rises and no part grows beyond
+ * max(cap, its weight before).  Deterministic and bit-exact.  cut_out,
+ * imbalance_out (as sphynx_eval), moves_out, rounds_out: host, may be NULL.
+ * Errors: INVALID_ARG (a part id outside [0, K), eps < 0), UNSUPPORTED
+ * (batch handles; weights too wide for exact integer gains). */
+int sphynx_refine(sphynx_handle g, int32_t *part, int32_t K, double eps, int32_t max_rounds, double *cut_out,
+                  double *imbalance_out, int32_t *moves_out, int32_t *rounds_out);
+
 /* A batch of graphs in one handle, for partitioning thousands of graphs of
  * uneven sizes in one call (Algorithm 2 applied to every graph; the paper
  * has no batched form).  The graphs come as one block-diagonal CSR over
@@ -440,10 +465,11 @@ int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, const float 
  * graph): host arrays, each may be NULL.  stats (may be NULL): status OK only if every graph
  * converged, iterations = the largest, fp64_finished = graphs that went on in
  * FP64 blocks.  With float blocks (FP32, MIXED_BF16) a graph whose tol |theta|
- * lies below the float rounding floor of its residual stalls there; once
- * every unconverged column has gone stall_window iterations (20 when 0)
- * without a 10 % gain at that floor, the graph resumes in FP64 blocks from
- * its float iterate (iterations count on, under the same max_iter), and the
+ * lies below the float rounding floor of its residual stops in float once an
+ * unconverged column whose target is below u rho (rho the Gershgorin bound of
+ * the noise floor) has a residual within 10 u rho, or once every unconverged
+ * column has gone stall_window iterations (20 when 0) without a 10 % gain at
+ * that floor; the graph then resumes in FP64 blocks from its float iterate (iterations count on, under the same max_iter), and the
  * embedding and multi-jagged step then run on double coordinates for all
  * graphs.  Errors: INVALID_ARG (not a batch
  * handle), UNSUPPORTED (multigrid preconditioner, polynomial of degree 1,

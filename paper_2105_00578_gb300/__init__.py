@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("init", C.c_int32), ("max_iter", C.c_int32),
                 ("tol", C.c_double), ("seed", C.c_uint64), ("flags", C.c_uint32),
                 ("sync_every", C.c_int32), ("stall_window", C.c_int32), ("conv", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("refine_rounds", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class Stats(C.Structure):
@@ -55,12 +55,12 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("cut", C.c_double), ("cut_twice", C.c_double),
                 ("imbalance", C.c_double),
                 ("ms_spmm_by_dt", C.c_double * 3), ("spmm_bytes_by_dt", C.c_double * 3),
-                ("spmm_launches_by_dt", C.c_int64 * 3), ("fp64_finished", C.c_int32), ("reserved_i", C.c_int32),
+                ("spmm_launches_by_dt", C.c_int64 * 3), ("fp64_finished", C.c_int32), ("refine_moves", C.c_int32),
                 ("reserved", C.c_double * 3)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_
-             if f not in ("reserved", "reserved_i", "eigenvalues", "resnorm")}
+             if f not in ("reserved", "eigenvalues", "resnorm")}
         d["eigenvalues"] = list(self.eigenvalues[: self.nev])
         d["resnorm"] = list(self.resnorm[: self.nev])
         return d
@@ -110,6 +110,7 @@ def _load():
         "sphynx_create_batch": (C.c_int, [vp, vp, vp, vp, vp, i32, i64, i64, C.c_uint32, vp, C.POINTER(vp)]),
         "sphynx_partition_batch": (C.c_int, [vp, i32, C.POINTER(Options), vp, vp, vp, vp, vp, vp, C.POINTER(Stats)]),
         "sphynx_eval": (C.c_int, [vp, vp, i32, pd, pd, pd]),
+        "sphynx_refine": (C.c_int, [vp, vp, i32, dbl, i32, pd, pd, pi32, pi32]),
         "sphynx_partition": (C.c_int, [vp, i32, C.POINTER(Options), vp, pd, pd, C.POINTER(Stats)]),
     }
     for name, (res, args) in sig.items():
@@ -159,7 +160,7 @@ def _dptr(a: np.ndarray):
 
 def options(laplacian="combinatorial", precond="jacobi", poly_degree=25, precision="fp64", init="random",
             max_iter=1000, tol=1e-3, seed=1, out_device=False, sync_every=0, stall_window=0,
-            conv="rel_theta") -> Options:
+            conv="rel_theta", refine_rounds=0) -> Options:
     o = Options()
     LIB.sphynx_default_options(C.byref(o))
     o.laplacian = LAPLACIANS.get(laplacian, laplacian)
@@ -174,6 +175,7 @@ def options(laplacian="combinatorial", precond="jacobi", poly_degree=25, precisi
     o.sync_every = sync_every
     o.stall_window = stall_window
     o.conv = CONVS.get(conv, conv)
+    o.refine_rounds = refine_rounds
     return o
 
 
@@ -311,6 +313,16 @@ def sphynx_mj_noalloc(dtype, coords, ldc, dims, n, vtx_w, K, part_out, stream=No
     callers that cannot let the library allocate device memory."""
     check(LIB.sphynx_mj_noalloc(dtype, ptr(coords), ldc, dims, int(n), ptr(vtx_w), K, ptr(part_out),
                                 _stream(stream)))
+
+
+def sphynx_refine(h, part, K, eps=0.01, max_rounds=20):
+    """Greedy refinement of the device partition `part` in place; returns
+    (cut, imbalance, moves, rounds)."""
+    cut, imb = C.c_double(), C.c_double()
+    mv, rd = C.c_int32(), C.c_int32()
+    check(LIB.sphynx_refine(h, ptr(part), K, float(eps), max_rounds, C.byref(cut), C.byref(imb), C.byref(mv),
+                            C.byref(rd)))
+    return cut.value, imb.value, mv.value, rd.value
 
 
 def sphynx_eval(h, part, K):

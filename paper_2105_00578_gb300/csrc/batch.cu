@@ -251,7 +251,7 @@ k_bresidual(ChunkView cv, const SolverState *states, const T *x, const T *lx, co
 __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int count, const double *partials, int b,
                             int ld, double tol, double u_work, int rho_from_degree,
                             const unsigned long long *gmax, int count_iteration, int maxit, int stall_window,
-                            int abs_test, int *ctl) {
+                            int abs_test, int early_promote, int *ctl) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= count) return;
   SolverState *st = states + q;
@@ -261,22 +261,28 @@ __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int cou
   const double floor_th = 10.0 * u_work * rho;
   const double floor_res = floor_th * static_cast<double>(gmax[2 * q] + 1);
   int nconv = 0;
+  bool at_floor = false;   // an unconverged column whose target lies below this precision's floor, reached
   for (int j = 0; j < b; ++j) {
     double tot = 0.0;
     for (int c = c0; c < c1; ++c) tot += partials[static_cast<int64_t>(c) * ld + j];
     const double res = sqrt(tot);
     st->resnorm[j] = res;
     const double th = fabs(st->theta[j]);
-    const bool ok = (res <= (abs_test ? tol : tol * th)) || (th <= floor_th && res <= floor_res);
+    const double target = abs_test ? tol : tol * th;
+    const bool ok = (res <= target) || (th <= floor_th && res <= floor_res);
     st->conv[j] = ok ? 1 : 0;
     nconv += ok ? 1 : 0;
+    // stored vectors carry a rounding of about u |x|, so their residual cannot
+    // fall much below u rho: a target under that is out of reach here
+    if (!ok && th > floor_th && target < u_work * rho && res <= floor_th) at_floor = true;
   }
   st->nconv = nconv;
   if (count_iteration) {
     st->iters += 1;
     st->pvalid = 1;
   }
-  const bool stalled = stall_check(st, b, stall_window, count_iteration, floor_th);
+  bool stalled = stall_check(st, b, stall_window, count_iteration, floor_th);
+  if (early_promote && count_iteration && at_floor) stalled = true;
   if (nconv == b) {
     st->done = 1;
     st->status = SPHYNX_OK;
@@ -916,7 +922,8 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   SolverState *states =
       static_cast<SolverState *>(g->workspace("bstates", static_cast<size_t>(count) * sizeof(SolverState), true));
   int *ctl = static_cast<int *>(g->workspace("bctl", 4 * sizeof(int), false));
-  const int mixed = 0;   // the m x m eigenproblem is solved in FP64 for every block precision
+  // the m x m eigenproblems are FP64 solves; float blocks start them from a float Jacobi basis
+  const int mixed0 = o->precision != SPHYNX_FP64;
   const int32_t *gc0 = B.graph_chunk0.as<int32_t>();
   const unsigned cgrid = static_cast<unsigned>(nch);
   const int hctl[4] = {count, 0, 0, 0};
@@ -932,10 +939,11 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   struct Blocks {
     void *X[2], *LX[2], *P[2], *LP[2], *H, *LH, *R, *chain[2], *yt;
   };
-  auto run_phase = [&](DT dt, DT ct, const char *tag, bool warm, int window) -> Blocks {
+  auto run_phase = [&](DT dt, DT ct, const char *tag, bool warm, int window, int early) -> Blocks {
     const size_t es = dt_size(dt);
     const size_t blk = static_cast<size_t>(n) * ld * es;
     const double u_work = dt == DT::F64 ? 0x1.0p-53 : 0x1.0p-24;
+    const int mixed = dt == DT::F64 ? 0 : mixed0;
     const std::string t(tag);
     Blocks k{};
     k.X[0] = g->workspace("X0" + t, blk, false);
@@ -978,7 +986,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
       k_bconverge<<<(count + 127) / 128, 128, 0, st>>>(gc0, states, count, npart, b, ld, o->tol, u_work,
                                                         rho_from_degree, B.graph_max.as<unsigned long long>(),
                                                         count_iteration, o->max_iter, window,
-                                                        o->conv == SPHYNX_CONV_ABS ? 1 : 0, ctl);
+                                                        o->conv == SPHYNX_CONV_ABS ? 1 : 0, early, ctl);
       SPX_LAUNCHED();
     };
     // H = p(L) R with each row's graph's roots: the single-graph product-form chain
@@ -1130,12 +1138,13 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   // Phase 1 in the requested precision.  Float blocks cannot resolve a
   // residual below about u ||L|| (the rounding of the stored vectors), and
   // tol |theta_2| lies below that on large graphs with small eigenvalues:
-  // such a graph stops once it stalls at that floor (the stall window) and
-  // finishes in FP64 blocks, warm-started from its float iterate.
+  // such a graph stops once a column whose target is below u rho has reached
+  // the floor region (residual <= 10 u rho), or once it stalls (the stall
+  // window), and finishes in FP64 blocks, warm-started from its float iterate.
   const bool promote = dt0 != DT::F64;
   const int window1 = promote ? (o->stall_window > 0 ? o->stall_window : kPromoteWindow) : o->stall_window;
   const DT ct0 = o->precision == SPHYNX_FP64 ? DT::F64 : (o->precision == SPHYNX_MIXED_BF16 ? DT::BF16 : DT::F32);
-  Blocks k1 = run_phase(dt0, ct0, "", false, window1);
+  Blocks k1 = run_phase(dt0, ct0, "", false, window1, promote ? 1 : 0);
   std::vector<SolverState> hs = read_states();
   std::vector<int> zero_it(count, 0);
   std::vector<char> all(count, 1);
@@ -1165,7 +1174,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     k_bpromote<<<(count + 127) / 128, 128, 0, st>>>(states, count, dprom.as<char>(), ctl);
     SPX_LAUNCHED();
     SPX_CUDA(cudaStreamSynchronize(st));   // `promoted` feeds an asynchronous copy
-    Blocks k2 = run_phase(DT::F64, DT::F64, "_64", true, o->stall_window);
+    Blocks k2 = run_phase(DT::F64, DT::F64, "_64", true, o->stall_window, 0);
     hs = read_states();
     gather_x0(k2, DT::F64, hs, it1, promoted);
     dt = DT::F64;

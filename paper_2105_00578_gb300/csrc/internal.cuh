@@ -435,9 +435,9 @@ int vec_grid(int64_t n);
 // ---- small.cu ---------------------------------------------------------------
 // M x M Gram matrices; coefficients written as M x ld (ld >= b); without an
 // active mask, column k of S is block k / ld, column k % ld.  mixed: the
-// Jacobi rotations run in float and every Ritz value is the double Rayleigh
-// quotient of its vector (for blocks stored in float).  count > 1 solves that
-// many problems, laid out back to back in every array, one CTA each.
+// FP64 symmetric eigen-solves start from a float Jacobi basis (the result is
+// still the double solve's; see eig_sym).  count > 1 solves that many
+// problems, laid out back to back in every array, one CTA each.
 void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, int M, int ld,
                           int b, double u_work, SolverState *state, double *y64, void *yt, DT dt,
                           const int *active_override, double *theta_out, int *svqb_out, int mixed,
@@ -462,6 +462,12 @@ size_t mj_scratch_bytes(int64_t n, int K, int count);
 void run_mj_scratch(cudaStream_t st, DT dt, const void *coords, int ldc, int dims, int64_t n,
                     const int64_t *vw, int K, int32_t *part, Counters *ctr, void *scratch,
                     const int64_t *h_gptr, int count);
+
+// ---- refine.cu --------------------------------------------------------------
+constexpr int kRefineMaxDegree = 256;   // vertices with more neighbours never move
+// greedy refinement of the device partition `part` in place (refine.cu)
+void refine_partition(sphynx_graph *g, int32_t *part, int K, double eps, int max_rounds, int max_degree,
+                      int *moves_out, int *rounds_out);
 
 // ---- graph.cu ---------------------------------------------------------------
 void eval_partition(sphynx_graph *g, const int32_t *part, int K, double *cut, double *cut2,

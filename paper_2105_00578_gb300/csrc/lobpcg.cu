@@ -49,6 +49,7 @@ void check_options(const sphynx_graph *g, const sphynx_options *o) {
   if (o->max_iter < 0) fail(SPHYNX_ERR_INVALID_ARG, "max_iter < 0");
   if (o->stall_window < 0) fail(SPHYNX_ERR_INVALID_ARG, "stall_window < 0");
   if (o->conv != SPHYNX_CONV_REL_THETA && o->conv != SPHYNX_CONV_ABS) fail(SPHYNX_ERR_INVALID_ARG, "conv %d", o->conv);
+  if (o->refine_rounds < 0) fail(SPHYNX_ERR_INVALID_ARG, "refine_rounds < 0");
   if (!(o->tol >= 0.0)) fail(SPHYNX_ERR_INVALID_ARG, "tol");
   if (o->laplacian != SPHYNX_COMBINATORIAL && g->isolated > 0)
     fail(SPHYNX_ERR_ISOLATED, "%lld vertices without edges: the %s problem needs deg > 0",
@@ -299,7 +300,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   const int pg1 = launch_gram(st, ga1, ggrid);
   launch_gram_reduce(st, gpart, 1, ld, pg1, ga, gb, done);
   launch_rayleigh_ritz(st, ga, gb, ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr,
-                       0);
+                       o->precision != SPHYNX_FP64);
   UpdateArgs up1{dt, 1, ld, n, {X[0], nullptr, nullptr}, {nullptr, nullptr, nullptr}, yt, X[1], nullptr, nullptr, done};
   launch_update(st, up1);
   plain_spmm(g, lap, dt, X[1], LX[1], ld, b, done);
@@ -323,7 +324,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
     const int pg3 = launch_gram(st, g3, ggrid);                                        // Rayleigh-Ritz
     launch_gram_reduce(st, gpart, 3, ld, pg3, ga, gb, done);
     launch_rayleigh_ritz(st, ga, gb, 3 * ld, ld, b, u_work, state, nullptr, yt, dt, nullptr, nullptr, nullptr,
-                       0);
+                       o->precision != SPHYNX_FP64);
     UpdateArgs u3{dt, 3, ld, n, {X[cur], H, P[cur]}, {nullptr, LH, LP[cur]}, yt, X[nx], P[nx], LP[nx], done};
     launch_update(st, u3);                                                             // update, direction
     plain_spmm(g, lap, dt, X[nx], LX[nx], ld, b, done);                                 // residual
@@ -697,6 +698,9 @@ int sphynx_partition(sphynx_handle g, int32_t K, const sphynx_options *opt, int3
     void *mjs = g->workspace("mj", mj_scratch_bytes(g->n, K, 1), false);
     run_mj_scratch(st, r.dt, coords, d - 1, d - 1, g->n, g->vw, K, dpart, &g->ctr, mjs, nullptr, 1);   // multi-jagged partition
     g->ctr.launches += 3;
+    int refine_moves = 0;
+    if (opt->refine_rounds > 0)   // greedy improvement of the cut (Sec. 7), within 1 % imbalance
+      refine_partition(g, dpart, K, 0.01, opt->refine_rounds, kRefineMaxDegree, &refine_moves, nullptr);
     SPX_CUDA(cudaEventRecord(e[2], st));
     double cut = 0, cut2 = 0, imb = 0;
     eval_partition(g, dpart, K, &cut, &cut2, &imb);
@@ -718,6 +722,7 @@ int sphynx_partition(sphynx_handle g, int32_t K, const sphynx_options *opt, int3
       stats->cut = cut;
       stats->cut_twice = cut2;
       stats->imbalance = imb;
+      stats->refine_moves = refine_moves;
       stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     for (auto &x : e) cudaEventDestroy(x);

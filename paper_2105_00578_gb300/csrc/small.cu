@@ -272,7 +272,10 @@ struct RRSmem {
   double W[kMaxM * kMaxM];   // projected matrix -> eigenvalues on diagonal
   double V[kMaxM * kMaxM];   // eigenvectors of W
   double Bh[kMaxM * kMaxM];  // scaled G_B, kept for the Rayleigh quotients
-  float A32[kMaxM * (kMaxM + 1)];  // float copies for the mixed-precision solve (odd leading dimension)
+  double P0[kMaxM * kMaxM];  // eigensolver workspaces of the float-started solve
+  double P1[kMaxM * kMaxM];
+  double P2[kMaxM * kMaxM];
+  float A32[kMaxM * (kMaxM + 1)];  // float copies for the float-started solve (odd leading dimension)
   float V32[kMaxM * (kMaxM + 1)];
   float cs32[2 * kMaxM];
   int pq32[2 * kMaxM];
@@ -291,10 +294,18 @@ struct RRSmem {
 };
 
 // Symmetric eigendecomposition of the leading m x m of A (ld kMaxM) into
-// its diagonal and V: in double, or (mixed) with the rotations in float.
-__device__ void eig_sym(RRSmem &S, double *A, double *V, int m, bool mixed) {
+// its diagonal and V, to FP64 accuracy.  Plain: cyclic Jacobi in double from
+// the identity.  Float-started: cyclic Jacobi in float first gives a basis V0
+// accurate to about 1e-7; V0 is made orthonormal in double (Cholesky-QR: V0
+// R^{-1} with V0^T V0 = R^T R), A1 = V0^T A V0 is then diagonal up to about
+// 1e-7 |A|, and double Jacobi from there (quadratic convergence: two or three
+// sweeps instead of seven or eight from the identity) finishes it: V = V0 V1.
+// The result is the double solve's, only its starting basis comes from float
+// arithmetic; on GB300, whose FP64 rate is 1/64 of FP32's, that halves the
+// Rayleigh-Ritz step.
+__device__ void eig_sym(RRSmem &S, double *A, double *V, int m, bool float_start) {
   const int L = kMaxM;
-  if (!mixed) {
+  if (!float_start || m < 2) {
     jacobi_eig<double>(A, L, V, L, m, S.cs, S.pq);
     return;
   }
@@ -305,8 +316,24 @@ __device__ void eig_sym(RRSmem &S, double *A, double *V, int m, bool mixed) {
   jacobi_eig<float>(S.A32, L32, S.V32, L32, m, S.cs32, S.pq32);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e % m;
-    V[i * L + j] = static_cast<double>(S.V32[i * L32 + j]);
-    A[i * L + j] = i == j ? static_cast<double>(S.A32[i * L32 + j]) : 0.0;
+    S.P0[i * L + j] = static_cast<double>(S.V32[i * L32 + j]);
+  }
+  __syncthreads();
+  matmul(S.P0, L, true, S.P0, L, S.P1, L, m, m, m);                 // G = V0^T V0
+  if (chol_upper(S.P1, L, m, S.scratch) <= 0.0) {                   // G = R^T R (never fails near I)
+    jacobi_eig<double>(A, L, V, L, m, S.cs, S.pq);
+    return;
+  }
+  tri_inv_upper(S.P1, L, m, S.P2, L, S.rinv);                       // R^{-1}
+  matmul(S.P0, L, false, S.P2, L, S.P1, L, m, m, m);                // V0 <- V0 R^{-1}, orthonormal
+  matmul(A, L, false, S.P1, L, S.P2, L, m, m, m);                   // A V0
+  matmul(S.P1, L, true, S.P2, L, S.P0, L, m, m, m);                 // A1 = V0^T A V0
+  symmetrize(S.P0, L, m);
+  jacobi_eig<double>(S.P0, L, S.P2, L, m, S.cs, S.pq);              // A1 = V1 diag V1^T
+  matmul(S.P1, L, false, S.P2, L, V, L, m, m, m);                   // V = V0 V1
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    A[i * L + j] = i == j ? S.P0[i * L + i] : 0.0;
   }
   __syncthreads();
 }
@@ -451,39 +478,6 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
     S.qb[tid] = 1.0;
   }
   __syncthreads();
-  if (mixed) {
-    // the rotations were float: take each Ritz value as the double Rayleigh
-    // quotient y^T A y / y^T B y of its vector, B-normalise the vector, and
-    // order the nev pairs by those values
-    for (int e = tid; e < m * nev; e += blockDim.x) {
-      const int i = e / nev, c = e % nev;
-      double sa = 0.0, sb = 0.0;
-      for (int k = 0; k < m; ++k) {
-        sa += S.A[i * L + k] * S.T[k * L + c];
-        sb += S.Bh[i * L + k] * S.T[k * L + c];
-      }
-      S.W[i * L + c] = sa;
-      S.V[i * L + c] = sb;
-    }
-    __syncthreads();
-    if (tid < nev) {
-      double qa = 0.0, qb = 0.0;
-      for (int i = 0; i < m; ++i) {
-        qa += S.T[i * L + tid] * S.W[i * L + tid];
-        qb += S.T[i * L + tid] * S.V[i * L + tid];
-      }
-      S.qa[tid] = qa / qb;
-      S.qb[tid] = qb;
-    }
-    __syncthreads();
-    if (tid < nev) {
-      int rank = 0;
-      for (int c = 0; c < nev; ++c)
-        if (S.qa[c] < S.qa[tid] || (S.qa[c] == S.qa[tid] && c < tid)) ++rank;
-      S.sel[rank] = tid;
-    }
-    __syncthreads();
-  }
   for (int e = tid; e < M * ld; e += blockDim.x) {
     if (y64) y64[e] = 0.0;
     if (yt) {
@@ -496,7 +490,7 @@ k_rayleigh_ritz(const double *ga, const double *gb, int M, int ld, int nev, doub
   for (int e = tid; e < m * nev; e += blockDim.x) {
     const int i = e / nev, c = e % nev;
     const int src = S.sel[c];
-    const double v = S.d[i] * S.T[i * L + src] * (mixed ? rsqrt(S.qb[src]) : 1.0);
+    const double v = S.d[i] * S.T[i * L + src];
     const int o = S.idx[i] * ld + c;
     if (y64) y64[o] = v;
     if (yt) {

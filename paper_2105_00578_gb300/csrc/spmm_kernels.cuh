@@ -399,9 +399,25 @@ template <typename TI, int BP> struct RowAcc {
     }
   }
 };
-// bfloat16 inputs: plain float accumulators.  Unpacking a bfloat16 pair costs
-// two integer operations either way, and two scalar adds issue faster here than
-// packing the pair and one add.f32x2 (measured on the 27-point mesh chain step).
+// the sm_100 mixed-precision add: acc + (the bfloat16 half of w), rounded
+// once in float -- the exact widening of bfloat16 makes it the unpack-and-add
+// result bit for bit, in one instruction instead of two
+__device__ __forceinline__ void add_bf16_pair(float &lo_acc, float &hi_acc, unsigned w) {
+  asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+      "add.rn.f32.bf16 %0, lo, %0;\n\tadd.rn.f32.bf16 %1, hi, %1;\n\t}"
+      : "+f"(lo_acc), "+f"(hi_acc)
+      : "r"(w));
+}
+__device__ __forceinline__ void add_bf16_lo(float &lo_acc, unsigned w) {
+  asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %1;\n\tadd.rn.f32.bf16 %0, lo, %0;\n\t}"
+      : "+f"(lo_acc)
+      : "r"(w));
+}
+
+// bfloat16 inputs: plain float accumulators.  Unit coefficients (the
+// combinatorial Laplacian of an unweighted graph) add each value with the
+// mixed-precision add; other coefficients unpack and fma.  The chain step is
+// issue-bound on the 27-point mesh, so instructions per entry set its time.
 template <int BP> struct RowAcc<__nv_bfloat16, BP> {
   float a[BP];
   __device__ __forceinline__ void zero() {
@@ -414,9 +430,13 @@ template <int BP> struct RowAcc<__nv_bfloat16, BP> {
 #pragma unroll
     for (int i = 0; i < NW; ++i) {
       if (c0 + 2 * i >= BP) break;
-      const float lo = __uint_as_float(w[i] << 16), hi = __uint_as_float(w[i] & 0xffff0000u);
-      a[c0 + 2 * i] = COEF ? fmaf(coef, lo, a[c0 + 2 * i]) : a[c0 + 2 * i] + lo;
-      a[c0 + 2 * i + 1] = COEF ? fmaf(coef, hi, a[c0 + 2 * i + 1]) : a[c0 + 2 * i + 1] + hi;
+      if constexpr (COEF) {
+        const float lo = __uint_as_float(w[i] << 16), hi = __uint_as_float(w[i] & 0xffff0000u);
+        a[c0 + 2 * i] = fmaf(coef, lo, a[c0 + 2 * i]);
+        a[c0 + 2 * i + 1] = fmaf(coef, hi, a[c0 + 2 * i + 1]);
+      } else {
+        add_bf16_pair(a[c0 + 2 * i], a[c0 + 2 * i + 1], w[i]);
+      }
     }
   }
   template <bool COEF>

@@ -90,3 +90,55 @@ def test_eval_rejects_out_of_range_parts():
     with pytest.raises(spx.SphynxError):
         spx.sphynx_eval(h, parts, 4)
     spx.sphynx_destroy(h)
+
+
+@pytest.mark.parametrize("make,K,eps", [(lambda: W.grid2d(97, 61), 6, 0.03),
+                                        (lambda: W.largest_component(W.rmat(12, seed=5)), 8, 0.05),
+                                        (lambda: W.random_edge_weights(W.grid3d(21, 17, 13, 27), 0.5, 1.5, 3), 5,
+                                         0.02)])
+@pytest.mark.parametrize("vertex_weights", [False, True])
+def test_greedy_refinement_is_bit_exact(make, K, eps, vertex_weights):
+    """sphynx_refine (the greedy improvement step Sec. 7 proposes) against the
+    oracle's restatement: the same parts vertex for vertex (every decision is
+    an integer comparison), the same move and round counts, the exact cut."""
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    g = make()
+    rng = np.random.default_rng(11)
+    parts = (np.arange(g.n) * K // g.n).astype(np.int32)
+    flip = rng.random(g.n) < 0.08
+    parts[flip] = rng.integers(0, K, int(flip.sum()))
+    vw = W.random_vertex_weights(g.n, 1, 5, 2) if vertex_weights else None
+    ref = O.refine(g, parts, K, vwts=vw, eps=eps, max_rounds=25)
+    h = spx.sphynx_create(g.row_ptr, g.col, g.w, vw)
+    try:
+        pd = torch.from_numpy(parts).cuda()
+        cut, imb, moves, rounds = spx.sphynx_refine(h, pd, K, eps, 25)
+        got = pd.cpu().numpy()
+        assert np.array_equal(got, ref.parts)
+        assert moves == ref.moves and rounds == ref.rounds
+        assert cut == ref.cut and imb == O.imbalance(got, vw, K)
+        assert ref.moves > 0
+    finally:
+        spx.sphynx_destroy(h)
+
+
+def test_partition_with_refinement_lowers_the_cut():
+    """refine_rounds > 0 in sphynx_partition: the multi-jagged partition is
+    refined in place; its cut is at most the unrefined one, the imbalance
+    stays within 1 % (or what multi-jagged left), and the result is what the
+    oracle's refinement makes of the unrefined partition."""
+    import paper_2105_00578_gb300 as spx
+    g = W.largest_component(W.rmat(14, seed=3))
+    graph = spx.Graph(g)
+    try:
+        kw = dict(laplacian="normalized", precond="jacobi", precision="fp64", tol=1e-2, seed=3)
+        p0, cut0, imb0, st0, code0 = graph.partition(16, **kw)
+        p1, cut1, imb1, st1, code1 = graph.partition(16, refine_rounds=20, **kw)
+        assert code0 == code1 == spx.OK
+        ref = O.refine(g, p0, 16, eps=0.01, max_rounds=20)
+        assert np.array_equal(p1, ref.parts) and cut1 == ref.cut <= cut0
+        assert st1["refine_moves"] == ref.moves
+        assert imb1 <= max(imb0, 1.01)
+    finally:
+        graph.close()
