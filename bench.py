@@ -47,10 +47,12 @@ WORKLOADS = {
                K=256, laplacian="normalized", precond="jacobi", poly_degree=25, tol=1e-2, seed=3,
                precision="fp32", golden="c3_oracle.json"),
     "c4": dict(desc="2000 random geometric graphs in one batched call (n log-uniform in [1e3, 2e5], mean degree "
-                    "about 8, largest component each), combinatorial Laplacian, Jacobi, K=8 (d=4) each, FP32 blocks "
-                    "with FP64 Rayleigh-Ritz, tol 1e-3; all LOBPCG iterations in one captured graph launch",
-               K=8, laplacian="combinatorial", precond="jacobi", poly_degree=25, tol=1e-3, seed=4,
-               precision="fp32", golden=None, batch=2000, stall_window=50),
+                    "about 8, largest component each), combinatorial Laplacian, polynomial preconditioner degree 25 "
+                    "per graph, K=8 (d=4) each, FP32 blocks (graphs whose tol theta lies below the float floor "
+                    "finish in FP64 blocks) with FP64 Rayleigh-Ritz, tol 1e-3; each phase's LOBPCG iterations in "
+                    "one captured graph launch",
+               K=8, laplacian="combinatorial", precond="poly", poly_degree=25, tol=1e-3, seed=4,
+               precision="fp32", golden="c4_oracle.json", batch=2000, stall_window=0, max_iter=3000),
     "amg": dict(desc="3D 27-point mesh 128^3 (2,097,152 vertices), combinatorial Laplacian, aggregation multigrid "
                      "preconditioner (plain aggregation, degree-3 Chebyshev, ratio 7, <= 5 levels), K=64 (d=7), "
                      "LOBPCG tol 1e-2 (Sphynx's default for regular graphs with multigrid), FP32 blocks",
@@ -411,6 +413,28 @@ def oracle_batch_sample(graphs, w, budget_s: float = 20.0):
     return len(graphs) / est, sample
 
 
+def batch_vs_oracle(w, eigs, cuts, status):
+    """Per graph of the oracle's stored runs (tests/golden, written by oracle
+    code only): eigenvalue and cut errors of the batch's result."""
+    if not w.get("golden"):
+        return None
+    p = os.path.join(ROOT, "tests", "golden", w["golden"])
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    out = []
+    for gq in d["graphs"]:
+        q = gq["index"]
+        ev, ev_o = eigs[q], gq["eigenvalues"]
+        rel = max(abs(a - b) / abs(b) for a, b in zip(ev[1:], ev_o[1:]))
+        out.append({"graph": q, "n": gq["n"], "status": int(status[q]), "eigenvalue_max_rel_err": rel,
+                    "cut": float(cuts[q]), "oracle_cut": gq["cut"],
+                    "cut_rel_err": abs(float(cuts[q]) - gq["cut"]) / gq["cut"]})
+    return {"source": f"tests/golden/{w['golden']}", "eigenvalue_rel_tol": 1e-3, "cut_rel_tol": 0.02,
+            "graphs": out}
+
+
 def run_batch(args, world, rank, local):
     """The batch workload: all graphs partitioned by one sphynx_partition_batch
     call per step (replicas on N > 1 GPUs)."""
@@ -430,8 +454,9 @@ def run_batch(args, world, rank, local):
     stream = torch.cuda.current_stream()
     h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr, stream=stream)
     part = torch.empty(big.n, dtype=torch.int32, device="cuda")
-    opt = spx.options(laplacian=w["laplacian"], precond=w["precond"], precision=precision, tol=w["tol"],
-                      seed=w["seed"], out_device=True, stall_window=w.get("stall_window", 0))
+    opt = spx.options(laplacian=w["laplacian"], precond=w["precond"], poly_degree=w["poly_degree"],
+                      precision=precision, tol=w["tol"], seed=w["seed"], out_device=True,
+                      stall_window=w.get("stall_window", 0), max_iter=w.get("max_iter", 1000))
 
     def step():
         return spx.sphynx_partition_batch(h, w["K"], opt, part, count)
@@ -464,8 +489,9 @@ def run_batch(args, world, rank, local):
     rp = torch.from_numpy(big.row_ptr).pin_memory()
     cl = torch.from_numpy(big.col).pin_memory()
     hp = torch.empty(big.n, dtype=torch.int32).pin_memory()
-    o_host = spx.options(laplacian=w["laplacian"], precond=w["precond"], precision=precision, tol=w["tol"],
-                         seed=w["seed"], stall_window=w.get("stall_window", 0))
+    o_host = spx.options(laplacian=w["laplacian"], precond=w["precond"], poly_degree=w["poly_degree"],
+                         precision=precision, tol=w["tol"], seed=w["seed"], stall_window=w.get("stall_window", 0),
+                         max_iter=w.get("max_iter", 1000))
     torch.cuda.synchronize()
     barrier()
     t = time.perf_counter()
@@ -490,8 +516,11 @@ def run_batch(args, world, rank, local):
                        "l2": f"inputs larger than L2 (CSR column array {big.col.nbytes / 1e6:.0f} MB > 129 MB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "graphs_converged": int(np.sum(status == 0)),
-            "graphs_stalled": int(np.sum((status != 0) & (iters < 1000))),
-            "stall_window": w.get("stall_window", 0), "max_iterations": int(iters.max()),
+            "graphs_finished_in_fp64": int(st.get("fp64_finished", 0)),
+            "graphs_noconv": int(np.sum(status != 0)),
+            "vs_oracle": batch_vs_oracle(w, eigs, cuts, status),
+            "stall_window": w.get("stall_window", 0), "max_iter": w.get("max_iter", 1000),
+            "max_iterations": int(iters.max()),
             "median_iterations": float(np.median(iters)), "mean_cut": float(np.mean(cuts)),
             "max_imbalance": float(np.max(imbs)),
             "roofline": None,

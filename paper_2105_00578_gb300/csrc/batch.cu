@@ -845,6 +845,22 @@ __global__ void k_widen(ChunkView cv, const float *x, int ld, double *y) {
     y[e] = static_cast<double>(x[e]);
 }
 
+// double blocks rounded to float, the rows of graphs still iterating
+__global__ void k_narrow(ChunkView cv, const SolverState *states, const double *x, int ld, float *y) {
+  const int c = blockIdx.x;
+  if (states[cv.graph[c]].done) return;
+  for (int64_t e = cv.begin[c] * ld + threadIdx.x; e < cv.begin[c + 1] * ld; e += blockDim.x)
+    y[e] = static_cast<float>(x[e]);
+}
+
+// float blocks to double, the rows of graphs still iterating
+__global__ void k_widen_active(ChunkView cv, const SolverState *states, const float *x, int ld, double *y) {
+  const int c = blockIdx.x;
+  if (states[cv.graph[c]].done) return;
+  for (int64_t e = cv.begin[c] * ld + threadIdx.x; e < cv.begin[c + 1] * ld; e += blockDim.x)
+    y[e] = static_cast<double>(x[e]);
+}
+
 // reopen the promoted graphs for the FP64 phase: not done, nothing converged,
 // no search direction yet, stall bookkeeping cleared; their iteration counts
 // go on; ctl[0] = graphs not done, ctl[1] = 0 (the loop's own count)
@@ -939,7 +955,11 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   struct Blocks {
     void *X[2], *LX[2], *P[2], *LP[2], *H, *LH, *R, *chain[2], *yt;
   };
-  auto run_phase = [&](DT dt, DT ct, const char *tag, bool warm, int window, int early) -> Blocks {
+  // pt: the precision the preconditioner works in (its input and accumulator);
+  // a preconditioner only shapes the search directions, so the FP64 phase
+  // applies the polynomial in float and widens H (the eigenpairs' accuracy
+  // rests on X, L X, the Gram matrices and the residual, all in dt)
+  auto run_phase = [&](DT dt, DT ct, DT pt, const char *tag, bool warm, int window, int early) -> Blocks {
     const size_t es = dt_size(dt);
     const size_t blk = static_cast<size_t>(n) * ld * es;
     const double u_work = dt == DT::F64 ? 0x1.0p-53 : 0x1.0p-24;
@@ -958,9 +978,14 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     k.LH = g->workspace("LH" + t, blk, true);
     // the residual goes to H directly (Jacobi, none) or to R, from which the chain makes H
     k.R = poly ? g->workspace("bR" + t, blk, true) : k.H;
+    void *R_lo = nullptr, *H_lo = nullptr;
     if (poly) {
       k.chain[0] = g->workspace("chain0" + t, static_cast<size_t>(n) * ld * dt_size(ct), false);
       k.chain[1] = g->workspace("chain1" + t, static_cast<size_t>(n) * ld * dt_size(ct), false);
+      if (pt != dt) {
+        R_lo = g->workspace("bR_lo" + t, static_cast<size_t>(n) * ld * dt_size(pt), false);
+        H_lo = g->workspace("bH_lo" + t, static_cast<size_t>(n) * ld * dt_size(pt), false);
+      }
     }
     k.yt = g->workspace("byt" + t, static_cast<size_t>(count) * M3 * ld * es, true);
     void **X = k.X, **LX = k.LX, **P = k.P, **LP = k.LP;
@@ -993,17 +1018,23 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     auto precondition = [&]() {
       if (!poly) return;
       const int kk = B.poly_k;
+      const bool low = pt != dt;   // FP64 phase: the polynomial in float, H widened
+      if (low) {
+        k_narrow<<<cgrid, 256, 0, st>>>(view_of(g), states, static_cast<const double *>(R), ld,
+                                        static_cast<float *>(R_lo));
+        SPX_LAUNCHED();
+      }
       for (int i = 0; i + 1 < kk; ++i) {
         SpmmArgs a{};
         a.lap = lap;
-        a.tin = i == 0 ? dt : ct;
+        a.tin = i == 0 ? pt : ct;
         a.ld_x = a.ld_y = a.bp = ld;
         a.b_true = b;
-        a.x = i == 0 ? R : k.chain[(i - 1) & 1];
+        a.x = i == 0 ? (low ? R_lo : R) : k.chain[(i - 1) & 1];
         a.mode = 1;
         a.t_out = k.chain[i & 1];
         a.tout = ct;
-        a.yacc = H;
+        a.yacc = low ? H_lo : H;
         a.first = i == 0 ? 1 : 0;
         a.yterms = (i % 2 == 0) ? 2 : (i + 2 == kk ? 1 : 0);
         a.inv = B.poly_inv.as<double>();
@@ -1012,6 +1043,11 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
         a.row_graph = B.row_graph.as<int32_t>();
         a.inv_stride = kk + 1;
         spmm(g, a);
+      }
+      if (low) {
+        k_widen_active<<<cgrid, 256, 0, st>>>(view_of(g), states, static_cast<const float *>(H_lo), ld,
+                                              static_cast<double *>(H));
+        SPX_LAUNCHED();
       }
     };
     auto spmm_block = [&](const void *x, void *y) {
@@ -1144,7 +1180,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   const bool promote = dt0 != DT::F64;
   const int window1 = promote ? (o->stall_window > 0 ? o->stall_window : kPromoteWindow) : o->stall_window;
   const DT ct0 = o->precision == SPHYNX_FP64 ? DT::F64 : (o->precision == SPHYNX_MIXED_BF16 ? DT::BF16 : DT::F32);
-  Blocks k1 = run_phase(dt0, ct0, "", false, window1, promote ? 1 : 0);
+  Blocks k1 = run_phase(dt0, ct0, dt0, "", false, window1, promote ? 1 : 0);
   std::vector<SolverState> hs = read_states();
   std::vector<int> zero_it(count, 0);
   std::vector<char> all(count, 1);
@@ -1174,7 +1210,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     k_bpromote<<<(count + 127) / 128, 128, 0, st>>>(states, count, dprom.as<char>(), ctl);
     SPX_LAUNCHED();
     SPX_CUDA(cudaStreamSynchronize(st));   // `promoted` feeds an asynchronous copy
-    Blocks k2 = run_phase(DT::F64, DT::F64, "_64", true, o->stall_window, 0);
+    Blocks k2 = run_phase(DT::F64, ct0, DT::F32, "_64", true, o->stall_window, 0);
     hs = read_states();
     gather_x0(k2, DT::F64, hs, it1, promoted);
     dt = DT::F64;

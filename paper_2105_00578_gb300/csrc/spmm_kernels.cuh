@@ -348,7 +348,7 @@ template <typename TI, int BP> struct RowAcc {
       }
     }
   }
-  template <bool COEF>
+  template <bool COEF, bool MIX = false>
   __device__ __forceinline__ void accum(const RawRow<TI, BP> &r, float coef) {
     const unsigned long long cc = COEF ? pk2(coef, coef) : 0ull;
     if constexpr (BP == 1) {
@@ -414,10 +414,12 @@ __device__ __forceinline__ void add_bf16_lo(float &lo_acc, unsigned w) {
       : "r"(w));
 }
 
-// bfloat16 inputs: plain float accumulators.  Unit coefficients (the
+// bfloat16 inputs: plain float accumulators.  With MIX, unit coefficients (the
 // combinatorial Laplacian of an unweighted graph) add each value with the
-// mixed-precision add; other coefficients unpack and fma.  The chain step is
-// issue-bound on the 27-point mesh, so instructions per entry set its time.
+// mixed-precision add, one instruction instead of two: the shared-pattern
+// rows take it, being issue-bound (the chain step on the 27-point mesh: 57
+// instead of 64 us); the explicit-slice rows, bound by load latency, ran
+// slower with it (80 instead of 74 us) and unpack and add.
 template <int BP> struct RowAcc<__nv_bfloat16, BP> {
   float a[BP];
   __device__ __forceinline__ void zero() {
@@ -425,15 +427,15 @@ template <int BP> struct RowAcc<__nv_bfloat16, BP> {
     for (int c = 0; c < BP; ++c) a[c] = 0.f;
   }
   // NW words of 2 values each (low half first) into columns c0, c0 + 1, ...
-  template <bool COEF, int NW>
+  template <bool COEF, int NW, bool MIX = false>
   __device__ __forceinline__ void add_words(const unsigned *w, int c0, float coef) {
 #pragma unroll
     for (int i = 0; i < NW; ++i) {
       if (c0 + 2 * i >= BP) break;
-      if constexpr (COEF) {
+      if constexpr (COEF || !MIX) {
         const float lo = __uint_as_float(w[i] << 16), hi = __uint_as_float(w[i] & 0xffff0000u);
-        a[c0 + 2 * i] = fmaf(coef, lo, a[c0 + 2 * i]);
-        a[c0 + 2 * i + 1] = fmaf(coef, hi, a[c0 + 2 * i + 1]);
+        a[c0 + 2 * i] = COEF ? fmaf(coef, lo, a[c0 + 2 * i]) : a[c0 + 2 * i] + lo;
+        a[c0 + 2 * i + 1] = COEF ? fmaf(coef, hi, a[c0 + 2 * i + 1]) : a[c0 + 2 * i + 1] + hi;
       } else {
         add_bf16_pair(a[c0 + 2 * i], a[c0 + 2 * i + 1], w[i]);
       }
@@ -457,19 +459,19 @@ template <int BP> struct RowAcc<__nv_bfloat16, BP> {
       }
     }
   }
-  template <bool COEF>
+  template <bool COEF, bool MIX = false>
   __device__ __forceinline__ void accum(const RawRow<__nv_bfloat16, BP> &r, float coef) {
     if constexpr (RawRow<__nv_bfloat16, BP>::kWide) {
 #pragma unroll
       for (int k = 0; k < BP / 8; ++k) {
         const unsigned w[4] = {r.q[k].x, r.q[k].y, r.q[k].z, r.q[k].w};
-        add_words<COEF, 4>(w, 8 * k, coef);
+        add_words<COEF, 4, MIX>(w, 8 * k, coef);
       }
     } else {
 #pragma unroll
       for (int k = 0; k < BP / 4; ++k) {
         const unsigned w[2] = {r.h[k].x, r.h[k].y};
-        add_words<COEF, 2>(w, 4 * k, coef);
+        add_words<COEF, 2, MIX>(w, 4 * k, coef);
       }
     }
   }
@@ -496,7 +498,7 @@ template <int BP> struct RowAcc<double, BP> {
 #pragma unroll
     for (int c = 0; c < BP; ++c) v[c] = COEF ? fma(coef, xj[c], v[c]) : v[c] + xj[c];
   }
-  template <bool COEF>
+  template <bool COEF, bool MIX = false>
   __device__ __forceinline__ void accum(const RawRow<double, BP> &r, double coef) {
 #pragma unroll
     for (int c = 0; c < BP; ++c) v[c] = COEF ? fma(coef, r.v[c], v[c]) : v[c] + r.v[c];
@@ -657,7 +659,7 @@ __device__ __forceinline__ void pattern_batch(const LapView &L, const TI *__rest
       const TA coef = jj[u] >= 0 ? dinv_of<TA>(L, jj[u]) : TA(0);
       acc.template accum<true>(rr[u], coef);
     } else {
-      acc.template accum<false>(rr[u], TA(1));
+      acc.template accum<false, true>(rr[u], TA(1));
     }
   }
 }

@@ -6,6 +6,7 @@ Calls only oracle/ (and the seeded generators in workloads/).  Usage:
     python tests/golden/make_oracle_golden.py c1     # 64 x 64 5-point mesh
     python tests/golden/make_oracle_golden.py c3     # R-MAT scale 22, largest component
     python tests/golden/make_oracle_golden.py amg    # 128^3 27-point mesh, multigrid preconditioner
+    python tests/golden/make_oracle_golden.py c4     # selected graphs of the 2000-graph RGG batch
 """
 
 from __future__ import annotations
@@ -38,6 +39,43 @@ CASES = {
 }
 
 
+# the 2000-graph batch: the three largest graphs, three of median size and two
+# of the smallest, each partitioned alone by the oracle with the batch's options
+C4 = dict(K=8, problem="combinatorial", precond="poly", poly_degree=25, tol=1e-3, seed=4, count=2000)
+
+
+def c4_sizes() -> np.ndarray:
+    """n_i of the batch (workloads.rgg_batch's rule), without drawing the graphs."""
+    u = workloads.graphs.uniform01(4, 61, C4["count"])
+    return np.floor(np.exp(np.log(1e3) + u * np.log(200.0))).astype(np.int64)
+
+
+def c4_indices() -> list:
+    order = [int(i) for i in np.argsort(c4_sizes(), kind="stable")]
+    mid = len(order) // 2
+    return order[-3:] + order[mid - 1:mid + 2] + order[:2]
+
+
+def run_c4() -> dict:
+    sizes = c4_sizes()
+    graphs = []
+    t0 = time.time()
+    for i in c4_indices():
+        g = workloads.rgg(int(sizes[i]), seed=4 + i)
+        r = oracle.partition(g, C4["K"], problem=C4["problem"], precond=C4["precond"], tol=C4["tol"],
+                             seed=C4["seed"], poly_degree=C4["poly_degree"])
+        graphs.append({"index": i, "n_drawn": int(sizes[i]), "n": g.n, "nnz": g.nnz,
+                       "eigenvalues": [float(v) for v in r.eigenvalues], "iterations": int(r.iterations),
+                       "status": r.status, "cut": float(r.cut), "imbalance": float(r.imbalance)})
+        print(i, g.n, r.iterations, r.status, r.cut, flush=True)
+    out = {"workload": "2000 RGGs (workloads.rgg_batch), combinatorial, polynomial degree 25, K=8, tol 1e-3",
+           **{k: v for k, v in C4.items()}, "graphs": graphs, "oracle_seconds": round(time.time() - t0, 2)}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c4_oracle.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    return out
+
+
 def run(name: str) -> dict:
     c = CASES[name]
     g = c["graph"]()
@@ -61,5 +99,8 @@ def run(name: str) -> dict:
 
 if __name__ == "__main__":
     for name in sys.argv[1:] or ["c1", "c2"]:
+        if name == "c4":
+            run_c4()
+            continue
         res = run(name)
         print(name, res["iterations"], res["eigenvalues"], res["cut"], res["oracle_seconds"])
