@@ -39,7 +39,8 @@ namespace sphynx {
 struct AmgLevel {
   sphynx_graph *g = nullptr;   // level 0: the caller's handle; coarser levels: owned
   bool owned = false;
-  DevBuf rowptr, col, w;       // coarse levels: the CSR their handle adopts
+  DevBuf rowptr, col, w;       // coarse levels: the CSR their handle adopts (float weights)
+  DevBuf w64, deg64;           // coarse levels: the same weights and their row sums in double
   DevBuf dinv, dinvf;          // 1 / deg (0 where deg = 0), double and float
   DevBuf agg;                  // int32 [n]: aggregate of each vertex (empty on the coarsest level)
   DevBuf mem_ptr;              // int64 [nc + 1]: members of each aggregate ...
@@ -305,13 +306,14 @@ __global__ void k_member_entries(int64_t nc, const int64_t *mptr, const int32_t 
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_coarse_row(const int32_t *list, const int64_t *mptr, const int32_t *mem,
                                                         const int64_t *rp, const int32_t *col, const float *w,
-                                                        const int32_t *agg, int64_t cap, int64_t *row_cnt,
-                                                        int64_t *row_start, unsigned long long *cursor, int32_t *tcol,
-                                                        float *tw, unsigned long long *gkey, float *gw) {
+                                                        const double *w64, const int32_t *agg, int64_t cap,
+                                                        int64_t *row_cnt, int64_t *row_start,
+                                                        unsigned long long *cursor, int32_t *tcol, float *tw,
+                                                        double *tw64, unsigned long long *gkey, double *gw) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long *key = gkey ? gkey + static_cast<int64_t>(blockIdx.x) * cap
                                  : reinterpret_cast<unsigned long long *>(smem);
-  float *wv = gkey ? gw + static_cast<int64_t>(blockIdx.x) * cap : reinterpret_cast<float *>(key + cap);
+  double *wv = gkey ? gw + static_cast<int64_t>(blockIdx.x) * cap : reinterpret_cast<double *>(key + cap);
   __shared__ int64_t s_cnt[THREADS];
   __shared__ int64_t s_base;
   const int t = threadIdx.x;
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(THREADS) k_coarse_row(const int32_t *list, con
       const int32_t J = agg[col[e]];
       key[pos] = J != static_cast<int32_t>(I) ? ((static_cast<unsigned long long>(J) << 32) | static_cast<uint32_t>(pos))
                                                : kRootKey;
-      wv[pos] = w ? w[e] : 1.f;
+      wv[pos] = w64 ? w64[e] : (w ? static_cast<double>(w[e]) : 1.0);
     }
     base += re - rb;
   }
@@ -374,25 +376,54 @@ __global__ void __launch_bounds__(THREADS) k_coarse_row(const int32_t *list, con
     if (key[i] == kRootKey) break;
     if (i == 0 || (key[i] >> 32) != (key[i - 1] >> 32)) {
       const unsigned long long J = key[i] >> 32;
-      float s = 0.f;
+      double s = 0.0;
       for (int64_t q = i; q < cap && key[q] != kRootKey && (key[q] >> 32) == J; ++q)
         s += wv[static_cast<uint32_t>(key[q] & 0xffffffffull)];
       tcol[o] = static_cast<int32_t>(J);
-      tw[o] = s;
+      tw[o] = static_cast<float>(s);
+      tw64[o] = s;
       ++o;
     }
   }
 }
 
+// one coarse row per block (64 threads): columns, float and double weights,
+// and the double row sum (thread k adds entries k, k + 64, ...; thread 0 adds
+// those partial sums in order)
 __global__ void k_coarse_place(int64_t nc, const int64_t *row_cnt, const int64_t *row_start, const int64_t *crp,
-                               const int32_t *tcol, const float *tw, int32_t *ccol, float *cw) {
+                               const int32_t *tcol, const float *tw, const double *tw64, int32_t *ccol, float *cw,
+                               double *cw64, double *cdeg64) {
+  __shared__ double part[64];
   const int64_t I = blockIdx.x;
   if (I >= nc) return;
   const int64_t c = row_cnt[I], s = row_start[I], d = crp[I];
+  double acc = 0.0;
   for (int64_t k = threadIdx.x; k < c; k += blockDim.x) {
     ccol[d + k] = tcol[s + k];
     cw[d + k] = tw[s + k];
+    cw64[d + k] = tw64[s + k];
+    acc += tw64[s + k];
   }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 64; ++k) t += part[k];
+    cdeg64[I] = t;
+  }
+}
+
+// y = D x - W x with double weights and degrees (a coarse level in FP64), ld columns
+__global__ void k_level_spmm64(int64_t n, int ld, const int64_t *rp, const int32_t *col, const double *w,
+                               const double *deg, const double *x, double *y, const int *done) {
+  if (done && *done) return;
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= n * ld) return;
+  const int64_t i = e / ld;
+  const int c = static_cast<int>(e - i * ld);
+  double acc = 0.0;
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) acc += w[k] * x[static_cast<int64_t>(col[k]) * ld + c];
+  y[e] = deg[i] * x[e] - acc;
 }
 
 // 1 / deg, 0 where deg = 0
@@ -542,6 +573,23 @@ void level_spmm(sphynx_graph *g, DT dt, const void *x, void *y, int ld, const in
   spmm(g, a);
 }
 
+// y = L_C x on one level: FP64 products of a coarse level use its double
+// weights and degrees (its handle holds them rounded to float); everything
+// else goes through the level's handle and the fused SpMM
+void level_product(AmgLevel &L, DT dt, const void *x, void *y, int ld, const int *done) {
+  if (dt == DT::F64 && L.w64.p) {
+    const int64_t ne = L.n * ld;
+    k_level_spmm64<<<grid1(ne), 256, 0, L.g->stream>>>(L.n, ld, L.rowptr.as<int64_t>(), L.col.as<int32_t>(),
+                                                        L.w64.as<double>(), L.deg64.as<double>(),
+                                                        static_cast<const double *>(x), static_cast<double *>(y),
+                                                        done);
+    SPX_LAUNCHED();
+    L.g->ctr.launches++;
+    return;
+  }
+  level_spmm(L.g, dt, x, y, ld, done);
+}
+
 // largest eigenvalue bound of D^{-1} L_C on one level
 double power_lambda(AmgLevel &L, int iters, uint64_t state) {
   sphynx_graph *g = L.g;
@@ -552,7 +600,7 @@ double power_lambda(AmgLevel &L, int iters, uint64_t state) {
   yb.alloc(static_cast<size_t>(n) * sizeof(double));
   pb.alloc((2 * kRedGrid + 4) * sizeof(double));
   double *v = vb.as<double>(), *y = yb.as<double>(), *part = pb.as<double>(), *scal = part + 2 * kRedGrid;
-  const double *deg = g->deg.as<double>(), *dinv = L.dinv.as<double>();
+  const double *deg = L.deg64.p ? L.deg64.as<double>() : g->deg.as<double>(), *dinv = L.dinv.as<double>();
   k_rand_pm1<<<grid1(n), 256, 0, st>>>(n, state, v);
   SPX_LAUNCHED();
   k_pw_partials<<<kRedGrid, 256, 0, st>>>(n, 0, v, nullptr, deg, dinv, part);
@@ -563,7 +611,7 @@ double power_lambda(AmgLevel &L, int iters, uint64_t state) {
   SPX_LAUNCHED();
   SPX_CUDA(cudaMemsetAsync(scal, 0, 2 * sizeof(double), st));
   for (int it = 0; it < iters; ++it) {
-    level_spmm(g, DT::F64, v, y, 1, nullptr);
+    level_product(L, DT::F64, v, y, 1, nullptr);
     k_pw_partials<<<kRedGrid, 256, 0, st>>>(n, 1, v, y, deg, dinv, part);
     SPX_LAUNCHED();
     k_pw_final<<<1, 32, 0, st>>>(part, kRedGrid, 1, scal);
@@ -677,12 +725,14 @@ void coarse_level(AmgLevel &L, AmgLevel &C) {
   }
   if (mx_l >= (int64_t{1} << 31))
     fail(SPHYNX_ERR_UNSUPPORTED, "multigrid: an aggregate has %lld incident entries", static_cast<long long>(mx_l));
-  DevBuf rc, rs, cur, tcol, tw, lists;
+  DevBuf rc, rs, cur, tcol, tw, tw64, lists;
   rc.alloc(nc * sizeof(int64_t));
   rs.alloc(nc * sizeof(int64_t));
   cur.alloc(sizeof(unsigned long long));
   tcol.alloc((sum > 0 ? sum : 1) * sizeof(int32_t));
   tw.alloc((sum > 0 ? sum : 1) * sizeof(float));
+  tw64.alloc((sum > 0 ? sum : 1) * sizeof(double));
+  const double *fw64 = L.w64.p ? L.w64.as<double>() : nullptr;   // the fine level's double weights (coarse levels)
   lists.alloc((small.size() + large.size() + 1) * sizeof(int32_t));
   int32_t *lsmall = lists.as<int32_t>(), *llarge = lsmall + small.size();
   if (!small.empty())
@@ -695,7 +745,7 @@ void coarse_level(AmgLevel &L, AmgLevel &C) {
     // capacity of its own class rather than of the largest aggregate
     int64_t cap0 = 64;
     while (cap0 < mx_s) cap0 <<= 1;
-    const size_t smax = static_cast<size_t>(cap0) * (sizeof(unsigned long long) + sizeof(float));
+    const size_t smax = static_cast<size_t>(cap0) * (sizeof(unsigned long long) + sizeof(double));
     SPX_CUDA(cudaFuncSetAttribute(k_coarse_row<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(smax)));
     std::vector<int32_t> order;
@@ -714,11 +764,11 @@ void coarse_level(AmgLevel &L, AmgLevel &C) {
     SPX_CUDA(cudaMemcpyAsync(lsmall, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     size_t off = 0;
     for (const auto &c : classes) {
-      const size_t sm = static_cast<size_t>(c.first) * (sizeof(unsigned long long) + sizeof(float));
+      const size_t sm = static_cast<size_t>(c.first) * (sizeof(unsigned long long) + sizeof(double));
       k_coarse_row<128><<<static_cast<unsigned>(c.second), 128, sm, st>>>(
-          lsmall + off, L.mem_ptr.as<int64_t>(), L.mem.as<int32_t>(), g->rowptr, g->col, g->w, L.agg.as<int32_t>(),
-          c.first, rc.as<int64_t>(), rs.as<int64_t>(), cur.as<unsigned long long>(), tcol.as<int32_t>(),
-          tw.as<float>(), nullptr, nullptr);
+          lsmall + off, L.mem_ptr.as<int64_t>(), L.mem.as<int32_t>(), g->rowptr, g->col, g->w, fw64,
+          L.agg.as<int32_t>(), c.first, rc.as<int64_t>(), rs.as<int64_t>(), cur.as<unsigned long long>(),
+          tcol.as<int32_t>(), tw.as<float>(), tw64.as<double>(), nullptr, nullptr);
       SPX_LAUNCHED();
       off += c.second;
     }
@@ -743,20 +793,20 @@ void coarse_level(AmgLevel &L, AmgLevel &C) {
     std::vector<int32_t> order(byc.size());
     for (size_t q = 0; q < byc.size(); ++q) order[q] = byc[q].second;
     SPX_CUDA(cudaMemcpyAsync(llarge, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    const size_t slot = sizeof(unsigned long long) + sizeof(float);
+    const size_t slot = sizeof(unsigned long long) + sizeof(double);
     const size_t budget = std::max(kHubBudget, static_cast<size_t>(capmax) * slot);
     DevBuf gk, gwb;
     gk.alloc(budget / slot * sizeof(unsigned long long));
-    gwb.alloc(budget / slot * sizeof(float));
+    gwb.alloc(budget / slot * sizeof(double));
     for (size_t q0 = 0; q0 < byc.size();) {
       const int64_t cap = byc[q0].first;
       const size_t per = std::max<size_t>(1, budget / (static_cast<size_t>(cap) * slot));
       size_t q1 = q0;
       while (q1 < byc.size() && byc[q1].first == cap && q1 - q0 < per) ++q1;
       k_coarse_row<1024><<<static_cast<unsigned>(q1 - q0), 1024, 0, st>>>(
-          llarge + q0, L.mem_ptr.as<int64_t>(), L.mem.as<int32_t>(), g->rowptr, g->col, g->w, L.agg.as<int32_t>(),
-          cap, rc.as<int64_t>(), rs.as<int64_t>(), cur.as<unsigned long long>(), tcol.as<int32_t>(), tw.as<float>(),
-          gk.as<unsigned long long>(), gwb.as<float>());
+          llarge + q0, L.mem_ptr.as<int64_t>(), L.mem.as<int32_t>(), g->rowptr, g->col, g->w, fw64,
+          L.agg.as<int32_t>(), cap, rc.as<int64_t>(), rs.as<int64_t>(), cur.as<unsigned long long>(),
+          tcol.as<int32_t>(), tw.as<float>(), tw64.as<double>(), gk.as<unsigned long long>(), gwb.as<double>());
       SPX_LAUNCHED();
       q0 = q1;
     }
@@ -766,9 +816,12 @@ void coarse_level(AmgLevel &L, AmgLevel &C) {
   const int64_t nnz = scan_excl(st, rc.as<int64_t>(), C.rowptr.as<int64_t>(), nc);
   C.col.alloc((nnz > 0 ? nnz : 1) * sizeof(int32_t));
   C.w.alloc((nnz > 0 ? nnz : 1) * sizeof(float));
+  C.w64.alloc((nnz > 0 ? nnz : 1) * sizeof(double));
+  C.deg64.alloc((nc > 0 ? nc : 1) * sizeof(double));
   k_coarse_place<<<static_cast<unsigned>(nc), 64, 0, st>>>(nc, rc.as<int64_t>(), rs.as<int64_t>(),
                                                            C.rowptr.as<int64_t>(), tcol.as<int32_t>(), tw.as<float>(),
-                                                           C.col.as<int32_t>(), C.w.as<float>());
+                                                           tw64.as<double>(), C.col.as<int32_t>(), C.w.as<float>(),
+                                                           C.w64.as<double>(), C.deg64.as<double>());
   SPX_LAUNCHED();
   sphynx_handle h = nullptr;
   const int code = sphynx_create(C.rowptr.as<int64_t>(), C.col.as<int32_t>(), C.w.as<float>(), nullptr, nc, nnz,
@@ -782,7 +835,8 @@ void coarse_level(AmgLevel &L, AmgLevel &C) {
 void level_dinv(AmgLevel &L) {
   L.dinv.alloc(L.n * sizeof(double));
   L.dinvf.alloc(L.n * sizeof(float));
-  k_dinv<<<grid1(L.n), 256, 0, L.g->stream>>>(L.n, L.g->deg.as<double>(), L.dinv.as<double>(), L.dinvf.as<float>());
+  const double *deg = L.deg64.p ? L.deg64.as<double>() : L.g->deg.as<double>();
+  k_dinv<<<grid1(L.n), 256, 0, L.g->stream>>>(L.n, deg, L.dinv.as<double>(), L.dinvf.as<float>());
   SPX_LAUNCHED();
 }
 
@@ -816,12 +870,12 @@ void cheb_apply(AmgLevel &L, DT dt, int ld, const T *b, T *x, bool x_zero, T *r,
   const ChebCoef c = cheb_coef(L.lam_max);
   const T *dinv = std::is_same<T, double>::value ? reinterpret_cast<const T *>(L.dinv.p)
                                                  : reinterpret_cast<const T *>(L.dinvf.p);
-  if (!x_zero) level_spmm(g, dt, x, y, ld, done);
+  if (!x_zero) level_product(L, dt, x, y, ld, done);
   k_cheb_start<T><<<grid1(ne), 256, 0, st>>>(L.n, ld, b, x_zero ? nullptr : y, dinv, static_cast<T>(c.inv_theta), r,
                                              d, x, x_zero ? 1 : 0, done);
   SPX_LAUNCHED();
   for (int k = 1; k < kChebDegree; ++k) {
-    level_spmm(g, dt, d, y, ld, done);
+    level_product(L, dt, d, y, ld, done);
     k_cheb_step<T><<<grid1(ne), 256, 0, st>>>(L.n, ld, y, dinv, static_cast<T>(c.c1[k]), static_cast<T>(c.c2[k]), r, d,
                                               x, done);
     SPX_LAUNCHED();
@@ -840,7 +894,7 @@ void vcycle(AmgHierarchy &H, size_t ell, DT dt, int ld, const T *b, T *x, const 
   AmgLevel &C = H.lv[ell + 1];
   cudaStream_t st = L.g->stream;
   cheb_apply<T>(L, dt, ld, b, x, true, r, d, y, done);                       // pre-smooth
-  level_spmm(L.g, dt, x, y, ld, done);                                        // y = A x
+  level_product(L, dt, x, y, ld, done);                                       // y = A x
   T *bc = C.blk[0].as<T>(), *xc = C.blk[1].as<T>();
   k_restrict<T><<<grid1(C.n * ld), 256, 0, st>>>(C.n, ld, L.mem_ptr.as<int64_t>(), L.mem.as<int32_t>(), b, y, bc,
                                                  done);                       // bc = P^T (b - A x)

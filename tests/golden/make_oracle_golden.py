@@ -41,7 +41,7 @@ CASES = {
 
 # the 2000-graph batch: the three largest graphs, three of median size and two
 # of the smallest, each partitioned alone by the oracle with the batch's options
-C4 = dict(K=8, problem="combinatorial", precond="poly", poly_degree=25, tol=1e-3, seed=4, count=2000)
+C4 = dict(K=8, problem="combinatorial", precond="poly", poly_degree=25, tol=1e-3, seed=4, count=2000, maxit=3000)
 
 
 def c4_sizes() -> np.ndarray:
@@ -63,7 +63,7 @@ def run_c4() -> dict:
     for i in c4_indices():
         g = workloads.rgg(int(sizes[i]), seed=4 + i)
         r = oracle.partition(g, C4["K"], problem=C4["problem"], precond=C4["precond"], tol=C4["tol"],
-                             seed=C4["seed"], poly_degree=C4["poly_degree"])
+                             seed=C4["seed"], poly_degree=C4["poly_degree"], maxit=C4["maxit"])
         graphs.append({"index": i, "n_drawn": int(sizes[i]), "n": g.n, "nnz": g.nnz,
                        "eigenvalues": [float(v) for v in r.eigenvalues], "iterations": int(r.iterations),
                        "status": r.status, "cut": float(r.cut), "imbalance": float(r.imbalance)})

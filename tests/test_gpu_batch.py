@@ -191,3 +191,37 @@ def test_float_batch_finishes_below_the_float_floor_in_fp64(precision):
             assert abs(cuts[q] - ref.cut) <= 0.02 * ref.cut, (q, cuts[q], ref.cut)
     finally:
         spx.sphynx_destroy(h)
+
+
+def test_largest_graphs_of_the_2000_graph_batch_match_the_oracle():
+    """The batch workload's three largest graphs (up to 199,291 vertices), three
+    of median size and two of the smallest, partitioned together with the
+    benchmark's options (FP32 blocks, every graph's own degree-25 polynomial,
+    tol 1e-3), against the oracle's single-graph runs stored in
+    tests/golden/c4_oracle.json (written by make_oracle_golden.py c4 from
+    oracle code only): every graph converges (most large ones finish in FP64
+    blocks), Ritz values within 1e-3, cut within 2 %."""
+    import json
+    import os
+    import paper_2105_00578_gb300 as spx
+    path = os.path.join(os.path.dirname(__file__), "golden", "c4_oracle.json")
+    gold = json.load(open(path))
+    graphs = [W.rgg(e["n_drawn"], seed=4 + e["index"]) for e in gold["graphs"]]
+    for gq, e in zip(graphs, gold["graphs"]):
+        assert gq.n == e["n"] and gq.nnz == e["nnz"]
+    big, gptr = W.concat_graphs(graphs)
+    h = spx.sphynx_create_batch(big.row_ptr, big.col, gptr)
+    try:
+        opt = spx.options(laplacian=gold["problem"], precond=gold["precond"], poly_degree=gold["poly_degree"],
+                          precision="fp32", tol=gold["tol"], seed=gold["seed"], max_iter=3000)
+        parts = np.full(big.n, -1, dtype=np.int32)
+        code, cuts, imbs, eigs, iters, status, st = spx.sphynx_partition_batch(h, gold["K"], opt, parts, len(graphs))
+        assert code == 0 and st["status"] == spx.OK, (status, iters)
+        assert st["fp64_finished"] >= 3
+        for q, (gq, e) in enumerate(zip(graphs, gold["graphs"])):
+            pq = parts[gptr[q]:gptr[q + 1]]
+            assert O.cutsize(gq, pq)[0] == cuts[q] and imbs[q] == O.imbalance(pq, None, gold["K"])
+            assert np.allclose(eigs[q, 1:], e["eigenvalues"][1:], rtol=1e-3), (q, eigs[q], e["eigenvalues"])
+            assert abs(cuts[q] - e["cut"]) <= 0.02 * e["cut"], (q, cuts[q], e["cut"])
+    finally:
+        spx.sphynx_destroy(h)
