@@ -454,7 +454,10 @@ int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, const float 
  * with the same options would; its random initial block is the one that call
  * would draw.  The LOBPCG iterations of all graphs run as one CUDA graph
  * launch whose conditional loop repeats on the device until every graph has
- * converged or reached max_iter; a converged graph drops out.  Jacobi, the
+ * converged or reached max_iter; a converged graph drops out (after every
+ * convergence test the device rebuilds the lists of row blocks and chunks
+ * that hold graphs still iterating, and every product and reduction of the
+ * next iteration walks those lists with a fixed grid).  Jacobi, the
  * polynomial (degree >= 2: every graph's own roots from its own Lanczos
  * steps, Sec. 5.2, applied with one chain over all graphs) or no
  * preconditioner; random initial block.

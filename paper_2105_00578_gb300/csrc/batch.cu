@@ -37,13 +37,25 @@ constexpr int kGramThreads = 256;
 // iterations without a 10 % residual gain (at the float rounding floor) after
 // which a float-block graph moves on to FP64 blocks
 constexpr int kPromoteWindow = 20;
+// iterations without a 10 % residual gain, anywhere above the floor, after
+// which a float graph is also handed to the FP64 phase: rounding in a float
+// basis can leave the iterate drifting well above the floor
+constexpr int kFloatStuckWindow = 100;
 
 int round4(int b) { return (b + 3) & ~3; }
 
 struct ChunkView {
   const int32_t *graph;   // [n_chunks] graph of each chunk
   const int64_t *begin;   // [n_chunks + 1] first row of each chunk (last entry: n)
+  int n = 0;              // chunks
+  const int32_t *act = nullptr;   // when set: the chunks of graphs still iterating, walked by a
+  const int *nact = nullptr;      // fixed grid (their count in *nact)
 };
+
+// chunk walks of the iteration kernels: every chunk once (grid = chunks), or
+// the active list with a fixed grid
+__device__ __forceinline__ int cv_count(const ChunkView &cv) { return cv.act ? *cv.nact : cv.n; }
+__device__ __forceinline__ int cv_chunk(const ChunkView &cv, int i) { return cv.act ? cv.act[i] : i; }
 
 __device__ __forceinline__ bool chunk_done(const SolverState *st, int q) { return st[q].done != 0; }
 
@@ -72,8 +84,9 @@ __global__ void __launch_bounds__(kGramThreads)
 k_bgram(ChunkView cv, const SolverState *states, int nb, int ld, const T *s0, const T *s1, const T *s2,
         const T *l0, const T *l1, const T *l2, const T *bdiag, double *partials) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int c = blockIdx.x, q = cv.graph[c];
-  if (chunk_done(states, q)) return;
+  for (int ci = blockIdx.x; ci < cv_count(cv); ci += gridDim.x) {
+  const int c = cv_chunk(cv, ci), q = cv.graph[c];
+  if (chunk_done(states, q)) continue;
   const int M = nb * ld, npairs = M * (M + 1) / 2, ntot = 2 * npairs;
   T *ss = reinterpret_cast<T *>(smraw);                     // [kGramRows][M]
   T *sl = ss + kGramRows * M;                               // [kGramRows][M]
@@ -125,6 +138,8 @@ k_bgram(ChunkView cv, const SolverState *states, int nb, int ld, const T *s0, co
     const int p = threadIdx.x + k * kGramThreads;
     if (p < ntot) partials[static_cast<int64_t>(c) * ntot + p] = acc[k];
   }
+  __syncthreads();   // shared buffers are reused by the next chunk
+  }
 }
 
 // per graph: G = sum over its chunks (in chunk order) of the partials, both
@@ -159,8 +174,9 @@ k_bupdate(ChunkView cv, const SolverState *states, const T *s0, const T *s1, con
           const T *l2, const T *yall, T *xo, T *po, T *lpo) {
   constexpr int M = NBLK * LD;
   __shared__ T sy[M * LD];
-  const int c = blockIdx.x, q = cv.graph[c];
-  if (chunk_done(states, q)) return;
+  for (int ci = blockIdx.x; ci < cv_count(cv); ci += gridDim.x) {
+  const int c = cv_chunk(cv, ci), q = cv.graph[c];
+  if (chunk_done(states, q)) continue;
   const T *y = yall + static_cast<size_t>(q) * M * LD;   // Rayleigh-Ritz wrote M x LD per graph
   for (int i = threadIdx.x; i < M * LD; i += blockDim.x) sy[i] = y[i];
   __syncthreads();
@@ -201,6 +217,8 @@ k_bupdate(ChunkView cv, const SolverState *states, const T *s0, const T *s1, con
       }
     }
   }
+  __syncthreads();   // shared buffers are reused by the next chunk
+  }
 }
 
 // ---- residual R = LX - B X Theta (times the Jacobi diagonal), per-chunk norms ----
@@ -209,8 +227,9 @@ __global__ void __launch_bounds__(256)
 k_bresidual(ChunkView cv, const SolverState *states, const T *x, const T *lx, const T *bdiag, const T *jinv,
             T *out, double *partials) {
   __shared__ double red[8][LD];
-  const int c = blockIdx.x, q = cv.graph[c];
-  if (chunk_done(states, q)) return;
+  for (int ci = blockIdx.x; ci < cv_count(cv); ci += gridDim.x) {
+  const int c = cv_chunk(cv, ci), q = cv.graph[c];
+  if (chunk_done(states, q)) continue;
   T th[LD];
 #pragma unroll
   for (int k = 0; k < LD; ++k) th[k] = static_cast<T>(states[q].theta[k]);
@@ -240,6 +259,8 @@ k_bresidual(ChunkView cv, const SolverState *states, const T *x, const T *lx, co
     double s = 0.0;
     for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
     partials[static_cast<int64_t>(c) * LD + threadIdx.x] = s;
+  }
+  __syncthreads();   // shared buffers are reused by the next chunk
   }
 }
 
@@ -283,6 +304,12 @@ __global__ void k_bconverge(const int32_t *gchunk0, SolverState *states, int cou
   }
   bool stalled = stall_check(st, b, stall_window, count_iteration, floor_th);
   if (early_promote && count_iteration && at_floor) stalled = true;
+  if (early_promote && count_iteration && stall_window > 0 && nconv < b) {
+    bool stuck = true;
+    for (int j = 0; j < b; ++j)
+      if (!st->conv[j]) stuck = stuck && st->since_best[j] >= kFloatStuckWindow;
+    if (stuck) stalled = true;
+  }
   if (nconv == b) {
     st->done = 1;
     st->status = SPHYNX_OK;
@@ -455,7 +482,24 @@ __global__ void k_bgraph_max(ChunkView cv, const int64_t *rp, const double *deg,
 }
 
 ChunkView view_of(const sphynx_graph *g) {
-  return ChunkView{g->batch.chunk_graph.as<int32_t>(), g->batch.chunk_begin.as<int64_t>()};
+  ChunkView v{g->batch.chunk_graph.as<int32_t>(), g->batch.chunk_begin.as<int64_t>()};
+  v.n = static_cast<int>(g->batch.n_chunks);
+  return v;
+}
+
+// the iteration kernels' view: the active-chunk list while one is kept
+ChunkView iter_view_of(const sphynx_graph *g) {
+  ChunkView v = view_of(g);
+  if (g->batch.act_chunks.p) {
+    v.act = g->batch.act_chunks.as<int32_t>();
+    v.nact = g->batch.n_act.as<int>() + 1;
+  }
+  return v;
+}
+
+unsigned iter_grid(const sphynx_graph *g) {
+  const int64_t nc = g->batch.n_chunks;
+  return static_cast<unsigned>(g->batch.act_chunks.p && nc > 8 * kSmCount ? 8 * kSmCount : nc);
 }
 
 // ---- polynomial preconditioner of every graph (Sec. 5.2) ----------------------
@@ -648,11 +692,6 @@ void batch_poly_setup_t(sphynx_graph *g, int k, int lap, uint64_t seed) {
   const int KS = k + 1;
   B.poly_inv.alloc(static_cast<size_t>(count) * KS * sizeof(double));
   B.poly_invf.alloc(static_cast<size_t>(count) * KS * sizeof(float));
-  if (!B.row_graph.p) {
-    B.row_graph.alloc(static_cast<size_t>(n) * sizeof(int32_t));
-    k_row_graph<<<cg, 256, 0, st>>>(cv, B.row_graph.as<int32_t>());
-    SPX_LAUNCHED();
-  }
   // start vector, null column, projection, normalisation
   k_bz_start<T><<<cg, 256, 0, st>>>(cv, B.gptr.as<int64_t>(), v, mix64(seed + 3 * kGamma));
   SPX_LAUNCHED();
@@ -728,7 +767,7 @@ void launch_bgram_t(cudaStream_t st, const sphynx_graph *g, const SolverState *s
                     const void *const *s, const void *const *ls, const void *bdiag, double *partials) {
   const int M = nb * ld, ntot = M * (M + 1);
   const size_t sm = static_cast<size_t>(kGramRows) * (2 * M + 1) * sizeof(T) + static_cast<size_t>(ntot) + 16;
-  const unsigned grid = static_cast<unsigned>(g->batch.n_chunks);
+  const unsigned grid = iter_grid(g);
   const T *S[3] = {static_cast<const T *>(s[0]), static_cast<const T *>(s[1]), static_cast<const T *>(s[2])};
   const T *LS[3] = {static_cast<const T *>(ls[0]), static_cast<const T *>(ls[1]), static_cast<const T *>(ls[2])};
   const int ppt = (ntot + kGramThreads - 1) / kGramThreads;
@@ -736,7 +775,7 @@ void launch_bgram_t(cudaStream_t st, const sphynx_graph *g, const SolverState *s
   {                                                                                                        \
     SPX_CUDA(cudaFuncSetAttribute(k_bgram<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
                                   static_cast<int>(sm)));                                                  \
-    k_bgram<T, P><<<grid, kGramThreads, sm, st>>>(view_of(g), states, nb, ld, S[0], S[1], S[2], LS[0],    \
+    k_bgram<T, P><<<grid, kGramThreads, sm, st>>>(iter_view_of(g), states, nb, ld, S[0], S[1], S[2], LS[0],    \
                                                   LS[1], LS[2], static_cast<const T *>(bdiag), partials); \
   }
   if (ppt <= 1) SPX_BGRAM(1)
@@ -751,13 +790,13 @@ void launch_bgram_t(cudaStream_t st, const sphynx_graph *g, const SolverState *s
 template <typename T, int LD>
 void launch_bupdate_t(cudaStream_t st, const sphynx_graph *g, const SolverState *states, int nblk,
                       const void *const *s, const void *const *ls, const void *y, void *xo, void *po, void *lpo) {
-  const unsigned grid = static_cast<unsigned>(g->batch.n_chunks);
+  const unsigned grid = iter_grid(g);
   const T *S[3] = {static_cast<const T *>(s[0]), static_cast<const T *>(s[1]), static_cast<const T *>(s[2])};
   if (nblk == 1)
-    k_bupdate<T, LD, 1><<<grid, 256, 0, st>>>(view_of(g), states, S[0], nullptr, nullptr, nullptr, nullptr,
+    k_bupdate<T, LD, 1><<<grid, 256, 0, st>>>(iter_view_of(g), states, S[0], nullptr, nullptr, nullptr, nullptr,
                                               static_cast<const T *>(y), static_cast<T *>(xo), nullptr, nullptr);
   else
-    k_bupdate<T, LD, 3><<<grid, 256, 0, st>>>(view_of(g), states, S[0], S[1], S[2],
+    k_bupdate<T, LD, 3><<<grid, 256, 0, st>>>(iter_view_of(g), states, S[0], S[1], S[2],
                                               static_cast<const T *>(ls[1]), static_cast<const T *>(ls[2]),
                                               static_cast<const T *>(y), static_cast<T *>(xo), static_cast<T *>(po),
                                               static_cast<T *>(lpo));
@@ -779,15 +818,15 @@ void launch_bupdate_ld(cudaStream_t st, const sphynx_graph *g, const SolverState
 template <typename T>
 void launch_bresidual_ld(cudaStream_t st, const sphynx_graph *g, const SolverState *states, int ld, const void *x,
                          const void *lx, const void *bdiag, const void *jinv, void *out, double *partials) {
-  const unsigned grid = static_cast<unsigned>(g->batch.n_chunks);
+  const unsigned grid = iter_grid(g);
   const T *X = static_cast<const T *>(x), *LX = static_cast<const T *>(lx);
   const T *B = static_cast<const T *>(bdiag), *J = static_cast<const T *>(jinv);
   T *O = static_cast<T *>(out);
   switch (ld) {
-    case 4: k_bresidual<T, 4><<<grid, 256, 0, st>>>(view_of(g), states, X, LX, B, J, O, partials); break;
-    case 8: k_bresidual<T, 8><<<grid, 256, 0, st>>>(view_of(g), states, X, LX, B, J, O, partials); break;
-    case 12: k_bresidual<T, 12><<<grid, 256, 0, st>>>(view_of(g), states, X, LX, B, J, O, partials); break;
-    case 16: k_bresidual<T, 16><<<grid, 256, 0, st>>>(view_of(g), states, X, LX, B, J, O, partials); break;
+    case 4: k_bresidual<T, 4><<<grid, 256, 0, st>>>(iter_view_of(g), states, X, LX, B, J, O, partials); break;
+    case 8: k_bresidual<T, 8><<<grid, 256, 0, st>>>(iter_view_of(g), states, X, LX, B, J, O, partials); break;
+    case 12: k_bresidual<T, 12><<<grid, 256, 0, st>>>(iter_view_of(g), states, X, LX, B, J, O, partials); break;
+    case 16: k_bresidual<T, 16><<<grid, 256, 0, st>>>(iter_view_of(g), states, X, LX, B, J, O, partials); break;
     default: fail(SPHYNX_ERR_UNSUPPORTED, "batched residual: ld %d", ld);
   }
   SPX_LAUNCHED();
@@ -836,6 +875,42 @@ void batch_setup(sphynx_graph *g, const int64_t *h_gptr, int count) {
   k_bgraph_max<<<static_cast<unsigned>(B.n_chunks), 256, 0, g->stream>>>(view_of(g), g->rowptr, g->deg.as<double>(),
                                                                        B.graph_max.as<unsigned long long>());
   SPX_LAUNCHED();
+  // the graph of every row: the products skip finished graphs' rows and the
+  // polynomial chain reads each row's own roots
+  B.row_graph.alloc(static_cast<size_t>(g->n) * sizeof(int32_t));
+  k_row_graph<<<static_cast<unsigned>(B.n_chunks), 256, 0, g->stream>>>(view_of(g), B.row_graph.as<int32_t>());
+  SPX_LAUNCHED();
+}
+
+// the active lists: chunks whose graph still iterates, and 1024-row blocks
+// holding a row of such a graph (a block spans at most a few graphs, each at
+// least two rows; graphs lo .. hi of its first and last rows are checked).
+// One block; the order of the lists does not matter, every consumer writes
+// per-row or per-chunk outputs.
+__global__ void __launch_bounds__(1024) k_build_lists(const SolverState *states, const int32_t *chunk_graph,
+                                                      int n_chunks, const int32_t *row_graph, int64_t n,
+                                                      int32_t *act_chunks, int32_t *act_blocks, int *n_act) {
+  __shared__ int cb, cc;
+  if (threadIdx.x == 0) {
+    cb = 0;
+    cc = 0;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < n_chunks; c += blockDim.x)
+    if (!states[chunk_graph[c]].done) act_chunks[atomicAdd(&cc, 1)] = c;
+  const int64_t nblk = (n + 1023) / 1024;
+  for (int64_t bk = threadIdx.x; bk < nblk; bk += blockDim.x) {
+    const int64_t r0 = bk * 1024, r1 = r0 + 1024 < n ? r0 + 1024 : n;
+    const int glo = row_graph[r0], ghi = row_graph[r1 - 1];
+    bool active = false;
+    for (int q = glo; q <= ghi && !active; ++q) active = !states[q].done;
+    if (active) act_blocks[atomicAdd(&cb, 1)] = static_cast<int32_t>(bk);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    n_act[0] = cb;
+    n_act[1] = cc;
+  }
 }
 
 // float blocks to double, every row
@@ -946,6 +1021,16 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   SPX_CUDA(cudaMemcpyAsync(ctl, hctl, sizeof(hctl), cudaMemcpyHostToDevice, st));
   const bool timing = g->ctr.timing;
   g->ctr.timing = false;   // per-launch events cannot live inside a captured loop
+  const int64_t nblk = (n + 1023) / 1024;
+  B.act_blocks.alloc(static_cast<size_t>(nblk) * sizeof(int32_t) + 4);
+  B.act_chunks.alloc(static_cast<size_t>(nch) * sizeof(int32_t) + 4);
+  B.n_act.alloc(4 * sizeof(int));
+  auto build_lists = [&]() {
+    k_build_lists<<<1, 1024, 0, st>>>(states, B.chunk_graph.as<int32_t>(), static_cast<int>(nch),
+                                      B.row_graph.as<int32_t>(), n, B.act_chunks.as<int32_t>(),
+                                      B.act_blocks.as<int32_t>(), B.n_act.as<int>());
+    SPX_LAUNCHED();
+  };
 
   // One precision phase of the batched eigensolve: blocks of type dt (chain
   // vectors of type ct), started from the random block or (warm) from the
@@ -1013,6 +1098,7 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
                                                         count_iteration, o->max_iter, window,
                                                         o->conv == SPHYNX_CONV_ABS ? 1 : 0, early, ctl);
       SPX_LAUNCHED();
+      build_lists();   // graphs that finished drop out of the next iteration's launches
     };
     // H = p(L) R with each row's graph's roots: the single-graph product-form chain
     auto precondition = [&]() {
@@ -1042,6 +1128,10 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
         a.i_cur = i;
         a.row_graph = B.row_graph.as<int32_t>();
         a.inv_stride = kk + 1;
+        a.gdone = &states->done;   // finished graphs' rows are skipped
+        a.gdone_stride = static_cast<int>(sizeof(SolverState) / sizeof(int));
+        a.act_blocks = B.act_blocks.as<int32_t>();
+        a.n_act = B.n_act.as<int>();
         spmm(g, a);
       }
       if (low) {
@@ -1061,9 +1151,15 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
       a.x = x;
       a.y = y;
       a.mode = 0;
+      a.row_graph = B.row_graph.as<int32_t>();
+      a.gdone = &states->done;   // finished graphs' rows are skipped
+      a.gdone_stride = static_cast<int>(sizeof(SolverState) / sizeof(int));
+      a.act_blocks = B.act_blocks.as<int32_t>();
+      a.n_act = B.n_act.as<int>();
       spmm(g, a);
     };
 
+    build_lists();   // the graphs this phase iterates
     // every graph's random block on its local rows (unless warm); then the
     // first Rayleigh-Ritz and residual
     if (!warm) {
@@ -1218,6 +1314,9 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   }
   const size_t es = dt_size(dt);
   g->ctr.timing = timing;
+  B.act_blocks.release();   // the lists serve the iteration loops only
+  B.act_chunks.release();
+  B.n_act.release();
 
   for (int q = 0; q < count; ++q) {
     const int64_t r0 = B.h_gptr[q], rows = B.h_gptr[q + 1] - r0;

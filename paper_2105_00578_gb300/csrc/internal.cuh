@@ -207,6 +207,11 @@ struct BatchInfo {
   DevBuf graph_chunk0;              // int32 [count + 1]: first chunk of each graph
   DevBuf graph_max;                 // uint64 [count][2]: max degree, max weighted degree (double bits)
   DevBuf row_graph;                 // int32 [n]: graph of every row (the chain reads its roots)
+  // while a batched eigensolve runs: the 1024-row blocks and the chunks that
+  // hold rows of graphs still iterating (rebuilt after every convergence
+  // test), and their counts [blocks, chunks]; the products and the chunk
+  // kernels walk these lists with fixed grids, so finished graphs cost nothing
+  DevBuf act_blocks, act_chunks, n_act;
   // polynomial preconditioner of every graph (Sec. 5.2), set up per partition
   int poly_k = 0;                   // degree (0: none set up)
   int poly_lap = -1;
@@ -283,8 +288,12 @@ struct SpmmArgs {
   const float *invf;       // mode 1: its float copy
   int i_cur;               // mode 1: index of theta_i in inv
   const int *done;         // device flag: skip the launch when nonzero (may be NULL)
-  const int32_t *row_graph = nullptr;  // mode 1 on a batch: graph of each row; its roots
+  const int32_t *row_graph = nullptr;  // batches: graph of each row; in mode 1 its roots
   int inv_stride = 0;                  // are inv[row_graph[row] * inv_stride + i]
+  const int *gdone = nullptr;          // batches: rows of graph q are skipped while
+  int gdone_stride = 0;                // gdone[q * gdone_stride] is nonzero
+  const int32_t *act_blocks = nullptr; // batches: 1024-row blocks holding rows of graphs still
+  const int *n_act = nullptr;          // iterating (device list and count); NULL: every row
 };
 void spmm(sphynx_graph *g, const SpmmArgs &a);
 // both short-row schedules timed on this product (scratch outputs)

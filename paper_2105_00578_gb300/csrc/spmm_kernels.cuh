@@ -161,7 +161,18 @@ struct SpmmDev {              // kernel-side view of SpmmArgs
   const int *done;
   const int32_t *row_graph;  // batches: graph of every row, whose roots start at
   int inv_stride;            // inv[row_graph[row] * inv_stride] (NULL: one graph)
+  const int *gdone;          // batches: a row of graph q is skipped when gdone[q * gdone_stride]
+  int gdone_stride;          // is nonzero (its graph has finished); NULL: no row is skipped
+  const int32_t *act_blocks; // batches: the 1024-row blocks (row >> 10) that hold a row of a graph
+  const int *n_act;          // still iterating, and their count; a fixed grid walks the list
 };
+
+constexpr int kListGrid = kSmCount * 16;   // CTAs of a launch that walks an active-block list
+
+// a row whose graph has finished iterating (batches): no gathers, no output
+__device__ __forceinline__ bool row_idle(const SpmmDev &a, int64_t row) {
+  return a.gdone && a.gdone[static_cast<int64_t>(__ldg(a.row_graph + row)) * a.gdone_stride] != 0;
+}
 
 // acc = sum_j w_ij (s_j) X_j of row `row`; epilogue applies the diagonal part.
 template <int LAP, typename TI, typename TT, int BP, int MODE>
@@ -687,20 +698,17 @@ __device__ __forceinline__ void spmm_pattern_row(const LapView &L, const TI *__r
   pattern_tail<U - 1, LAP, TI, BP>(L, x, row, myoff, mk, k0, nu - k0, acc);
 }
 
+// the warp's 32 rows row0 .. row0 + 31 of the CSR-staged schedule; s_col and
+// s_w are the warp's shared staging areas
 template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
-__global__ void __launch_bounds__(32 * kWarpsPerCta)
-k_spmm_short(const LapView L, const SpmmDev a) {
+__device__ __forceinline__ void short_rows(const LapView &L, const SpmmDev &a, int64_t row0, int lane, int *s_colw,
+                                           float *s_ww) {
   using TA = typename AccOf<TI>::T;
-  // column indices (and weights) of the warp's 32 rows, staged from the
-  // 16-byte-aligned position at or below the window start
-  __shared__ __align__(16) int s_col[kWarpsPerCta][kStageCap + 8];
-  __shared__ __align__(16) float s_w[kWarpsPerCta][W ? kStageCap + 8 : 4];
-  if (a.done && *a.done) return;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t row0 = (static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + wid) * 32;
   if (row0 >= L.n) return;  // uniform per warp
   const int64_t row = row0 + lane;
   const bool valid = row < L.n;
+  const bool idle = valid && row_idle(a, row);
+  if (__all_sync(kFull, !valid || idle)) return;   // every row's graph has finished
   int64_t rb = 0, re = 0;
   if (valid) {
     rb = __ldcs(L.rowptr + row);
@@ -717,23 +725,23 @@ k_spmm_short(const LapView L, const SpmmDev a) {
     const int64_t vend = we & ~static_cast<int64_t>(3);
     const int nvec = static_cast<int>((vend - base) >> 2);
     const int4 *gc = reinterpret_cast<const int4 *>(L.col + base);
-    for (int v = lane; v < nvec; v += 32) *reinterpret_cast<int4 *>(&s_col[wid][4 * v]) = __ldcs(gc + v);
-    for (int64_t gidx = vend + lane; gidx < we; gidx += 32) s_col[wid][gidx - base] = __ldcs(L.col + gidx);
+    for (int v = lane; v < nvec; v += 32) *reinterpret_cast<int4 *>(&s_colw[4 * v]) = __ldcs(gc + v);
+    for (int64_t gidx = vend + lane; gidx < we; gidx += 32) s_colw[gidx - base] = __ldcs(L.col + gidx);
     if constexpr (W) {
       const float4 *gw = reinterpret_cast<const float4 *>(L.w + base);
-      for (int v = lane; v < nvec; v += 32) *reinterpret_cast<float4 *>(&s_w[wid][4 * v]) = __ldcs(gw + v);
-      for (int64_t gidx = vend + lane; gidx < we; gidx += 32) s_w[wid][gidx - base] = __ldcs(L.w + gidx);
+      for (int v = lane; v < nvec; v += 32) *reinterpret_cast<float4 *>(&s_ww[4 * v]) = __ldcs(gw + v);
+      for (int64_t gidx = vend + lane; gidx < we; gidx += 32) s_ww[gidx - base] = __ldcs(L.w + gidx);
     }
   }
   __syncwarp();
-  if (!valid || re - rb > kShortDeg) return;
+  if (!valid || idle || re - rb > kShortDeg) return;
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> acc;
   acc.zero();
   const int len = static_cast<int>(re - rb);
   if (staged) {
-    const int *sc = &s_col[wid][rb - base];
-    const float *sw = W ? &s_w[wid][rb - base] : nullptr;
+    const int *sc = &s_colw[rb - base];
+    const float *sw = W ? &s_ww[rb - base] : nullptr;
     spmm_row<LAP, TI, BP, W>(
         L, x, len, [&](int t) { return sc[t]; }, [&](int t) { return sw[t]; }, acc);
   } else {
@@ -745,6 +753,29 @@ k_spmm_short(const LapView L, const SpmmDev a) {
   TA sum[BP];
   acc.get(sum);
   spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
+}
+
+template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+k_spmm_short(const LapView L, const SpmmDev a) {
+  // column indices (and weights) of each warp's 32 rows, staged from the
+  // 16-byte-aligned position at or below the window start
+  __shared__ __align__(16) int s_col[kWarpsPerCta][kStageCap + 8];
+  __shared__ __align__(16) float s_w[kWarpsPerCta][W ? kStageCap + 8 : 4];
+  if (a.done && *a.done) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (a.act_blocks) {
+    // a batch's active 1024-row blocks, 128 rows to a CTA item
+    const int64_t items = 8 * static_cast<int64_t>(*a.n_act);
+    for (int64_t i = blockIdx.x; i < items; i += gridDim.x) {
+      const int64_t row0 = static_cast<int64_t>(a.act_blocks[i >> 3]) * 1024 + (i & 7) * 128 + wid * 32;
+      short_rows<LAP, TI, TT, BP, W, MODE>(L, a, row0, lane, s_col[wid], s_w[wid]);
+      __syncwarp();
+    }
+    return;
+  }
+  const int64_t row0 = (static_cast<int64_t>(blockIdx.x) * kWarpsPerCta + wid) * 32;
+  short_rows<LAP, TI, TT, BP, W, MODE>(L, a, row0, lane, s_col[wid], s_w[wid]);
 }
 
 // SELL-32 schedule: a warp per slice of 32 rows, lane = row.  Entry t of all
@@ -772,17 +803,15 @@ template <typename TI, int BP> struct SellOccupancy {
 // slice offset, block in pcol) besides explicit ones; 3: only shared-pattern
 // slices.
 template <int LAP, typename TI, typename TT, int BP, bool W, int MODE, int KIND>
-__global__ void __launch_bounds__(128, SellOccupancy<TI, BP>::blocks)
-k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, const float *__restrict__ sw,
-            const int64_t *__restrict__ sptr, const int64_t *__restrict__ cptr, const uint8_t *__restrict__ sdeg,
-            const int16_t *__restrict__ pcol, int ls) {
+__device__ __forceinline__ void sell_slice(const LapView &L, const SpmmDev &a, const int16_t *__restrict__ scol,
+                                           const float *__restrict__ sw, const int64_t *__restrict__ sptr,
+                                           const int64_t *__restrict__ cptr, const uint8_t *__restrict__ sdeg,
+                                           const int16_t *__restrict__ pcol, int64_t slice, int lane) {
   using TA = typename AccOf<TI>::T;
-  if (a.done && *a.done) return;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t blk = blockIdx.x;
-  const int64_t slice = ((blk >> ls) << (ls + 2)) + (blk & ((1 << ls) - 1)) + (static_cast<int64_t>(wid) << ls);
   if (slice * 32 >= L.n) return;  // uniform per warp
   const int64_t row = slice * 32 + lane;
+  const bool idle = row < L.n && row_idle(a, row);
+  if (a.gdone && __all_sync(kFull, row >= L.n || idle)) return;   // every row's graph has finished
   const int64_t cbase = __ldg(cptr + slice);
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> acc;
@@ -792,7 +821,7 @@ k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, 
       // one 64-byte offset list and one mask per lane: no per-entry index stream
       const int16_t *pb = pcol + (cbase - kPatternTag);
       const int myoff = __ldg(pb + lane);
-      const unsigned mk = __ldg(reinterpret_cast<const unsigned *>(pb + 32) + lane);
+      const unsigned mk = idle ? 0x80000000u : __ldg(reinterpret_cast<const unsigned *>(pb + 32) + lane);
       const unsigned any = __reduce_or_sync(kFull, mk & 0x7fffffffu);
       const int nu = 32 - __clz(any);
       spmm_pattern_row<LAP, TI, BP>(L, x, static_cast<int>(row), myoff, mk, nu, acc);
@@ -804,7 +833,7 @@ k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, 
     }
   }
   if constexpr (KIND != 3) {
-    const bool valid = row < L.n;
+    const bool valid = row < L.n && !idle;
     const int sd = valid ? sdeg[row] : 0xFF;
     const int d = sd == 0xFF ? 0 : sd;
     const float *wp = W ? sw + __ldg(sptr + slice) + lane : nullptr;
@@ -840,6 +869,27 @@ k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, 
   }
 }
 
+template <int LAP, typename TI, typename TT, int BP, bool W, int MODE, int KIND>
+__global__ void __launch_bounds__(128, SellOccupancy<TI, BP>::blocks)
+k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, const float *__restrict__ sw,
+            const int64_t *__restrict__ sptr, const int64_t *__restrict__ cptr, const uint8_t *__restrict__ sdeg,
+            const int16_t *__restrict__ pcol, int ls) {
+  if (a.done && *a.done) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (a.act_blocks) {
+    // a batch's active 1024-row blocks: 32 slices each, four to a CTA item
+    const int64_t items = 8 * static_cast<int64_t>(*a.n_act);
+    for (int64_t i = blockIdx.x; i < items; i += gridDim.x) {
+      const int64_t slice = static_cast<int64_t>(a.act_blocks[i >> 3]) * 32 + (i & 7) * 4 + wid;
+      sell_slice<LAP, TI, TT, BP, W, MODE, KIND>(L, a, scol, sw, sptr, cptr, sdeg, pcol, slice, lane);
+    }
+    return;
+  }
+  const int64_t blk = blockIdx.x;
+  const int64_t slice = ((blk >> ls) << (ls + 2)) + (blk & ((1 << ls) - 1)) + (static_cast<int64_t>(wid) << ls);
+  sell_slice<LAP, TI, TT, BP, W, MODE, KIND>(L, a, scol, sw, sptr, cptr, sdeg, pcol, slice, lane);
+}
+
 // Medium rows (kShortDeg < degree <= kMedDeg): a warp per slice of 32 rows of
 // similar degree (sorted at create), lane = row, entry t of the 32 rows one
 // contiguous 128-byte segment; the row's result goes to its own index.  A lane
@@ -857,7 +907,8 @@ k_spmm_med(const LapView L, const SpmmDev a, const int32_t *__restrict__ mcol, c
   const int64_t slice = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (slice >= nslices) return;  // uniform per warp
   const int row = mrow[slice * 32 + lane];
-  const int d = row >= 0 ? mdeg[slice * 32 + lane] : 0;
+  const bool idle = row >= 0 && row_idle(a, row);
+  const int d = row >= 0 && !idle ? mdeg[slice * 32 + lane] : 0;
   const int64_t base = __ldg(mptr + slice);
   const int32_t *cp = mcol + base + lane;
   const float *wp = W ? mw + base + lane : nullptr;
@@ -875,7 +926,7 @@ k_spmm_med(const LapView L, const SpmmDev a, const int32_t *__restrict__ mcol, c
         blk);
     acc.merge(blk);
   }
-  if (row < 0) return;
+  if (row < 0 || idle) return;
   TA sum[BP];
   acc.get(sum);
   spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
@@ -891,6 +942,7 @@ k_spmm_long(const LapView L, const SpmmDev a, const int64_t *__restrict__ items,
   const int lane = threadIdx.x & 31;
   const int64_t item = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (item >= n_items) return;
+  if (row_idle(a, items[item * 4])) return;   // uniform per warp
   const int64_t b = items[item * 4 + 1], e = items[item * 4 + 2];
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> racc;
@@ -920,6 +972,7 @@ k_spmm_finalize(const LapView L, const SpmmDev a, const int64_t *__restrict__ sp
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n_long) return;
   const int64_t row = split[t * 3], first = split[t * 3 + 1], cnt = split[t * 3 + 2];
+  if (row_idle(a, row)) return;
   TA acc[BP];
 #pragma unroll
   for (int c = 0; c < BP; ++c) acc[c] = TA(0);
@@ -942,7 +995,8 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
     if (p.variant == kSell32 || (p.variant == kSellPattern && !W)) {
       // whole groups of 4 * 2^ls slices, 2^ls blocks each
       const int ls = p.sell_ls;
-      const unsigned gs = static_cast<unsigned>(((warps + (int64_t{4} << ls) - 1) >> (ls + 2)) << ls);
+      const unsigned gs = a.act_blocks ? static_cast<unsigned>(kListGrid)
+                                       : static_cast<unsigned>(((warps + (int64_t{4} << ls) - 1) >> (ls + 2)) << ls);
       const int16_t *sc = p.sell_col.as<int16_t>();
       const float *swp = p.sell_w.as<float>();
       const int64_t *sp = p.sell_ptr.as<int64_t>();
@@ -968,7 +1022,8 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
                                                                        sd, nullptr, ls);
       }
     } else {
-      k_spmm_short<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(grid), 32 * kWarpsPerCta, 0, st>>>(L, a);
+      const unsigned gsh = a.act_blocks ? static_cast<unsigned>(kListGrid) : static_cast<unsigned>(grid);
+      k_spmm_short<LAP, TI, TT, BP, W, MODE><<<gsh, 32 * kWarpsPerCta, 0, st>>>(L, a);
     }
     SPX_LAUNCHED();
     g->ctr.launches++;
