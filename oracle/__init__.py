@@ -35,7 +35,7 @@ from .laplacian import (  # noqa: F401
     operator_for, b_diag_for, null_vector,
 )
 from .rng import splitmix64_block, poly_start_vector, reference_block  # noqa: F401
-from .precond import jacobi_diag, gmres_poly_roots, poly_apply, leja_order  # noqa: F401
+from .precond import jacobi_diag, gmres_poly_roots, poly_apply, leja_order, definite_roots, p_on_grid  # noqa: F401
 from .lobpcg import lobpcg, rayleigh_ritz, LobpcgResult  # noqa: F401
 from .amg import (aggregate, mis2_roots, coarse_graph, build_hierarchy, vcycle, chebyshev,  # noqa: F401
                   power_lambda_max, vertex_keys)

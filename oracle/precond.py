@@ -13,6 +13,16 @@ the standard one for a symmetric operator:
    reorthogonalisation (classical Gram-Schmidt, two passes);
 2. the roots of the GMRES residual polynomial are the harmonic Ritz values:
    the eigenvalues theta of (T_k^2 + beta_k^2 e_k e_k^T) y = theta T_k y;
+2b. definiteness: LOBPCG (Algorithm 1) takes a symmetric positive definite
+   preconditioner, and p_k need not be positive on the spectrum:
+   1 - lambda p(lambda) = prod_i (1 - lambda/theta_i) can exceed 1 between the
+   largest roots, where p < 0 (on the batch workload's 2e5-vertex geometric
+   graphs LOBPCG then stalls for thousands of iterations).  While the minimum
+   of p over lambda_j = theta_max j / G, j = 1..G (G = DEFINITE_GRID), is not
+   positive, a second copy of the root nearest the minimising lambda_j is
+   added, at most MAX_ADDED_ROOTS times.  Repeating a root is the device the
+   GMRES-polynomial papers Sec. 5.2 cites use for stability ("adding roots");
+   here it is triggered by the sign of p, a reading (the paper gives no rule);
 3. the roots are put in modified Leja order;
 4. p is applied in product form, 1 - lambda p(lambda) = prod_i (1 - lambda/theta_i):
    y = 0, t = v; for i = 1..k: y += t / theta_i; if i < k: t -= A t / theta_i,
@@ -21,7 +31,10 @@ the standard one for a symmetric operator:
 Pins (tests/test_oracle_precond.py): p(A) v against V diag(p(lambda)) V^T v from
 a dense eigendecomposition; 1 - theta_i p(theta_i) = 0 at every root; the roots
 lie inside the spectrum of A restricted to the complement of its null space;
-Jacobi against the diagonal of the explicit Laplacian.
+the definiteness step against p evaluated from its power-basis coefficients on
+a finer grid (unchanged roots where p > 0 already, one added root on a stored
+indefinite case and on a batch graph); Jacobi against the diagonal of the
+explicit Laplacian.
 """
 
 from __future__ import annotations
@@ -103,13 +116,42 @@ def harmonic_ritz(alpha: np.ndarray, beta: np.ndarray) -> np.ndarray:
     return np.linalg.eigvalsh(z)
 
 
+DEFINITE_GRID = 8192
+MAX_ADDED_ROOTS = 4
+
+
+def p_on_grid(theta: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    """p(lambda) = (1 - prod_i (1 - lambda/theta_i)) / lambda, the factors
+    multiplied in the order of theta."""
+    pi = np.ones_like(lam)
+    for t in theta:
+        pi = pi * (1.0 - lam / t)
+    return (1.0 - pi) / lam
+
+
+def definite_roots(theta: np.ndarray) -> np.ndarray:
+    """Step 2b of the module notes: theta (ascending harmonic Ritz values),
+    followed by the added copies in the order they were added."""
+    base = np.asarray(theta, dtype=np.float64)
+    roots = list(base)
+    lam = (base.max() * np.arange(1, DEFINITE_GRID + 1, dtype=np.float64)) / DEFINITE_GRID
+    for _ in range(MAX_ADDED_ROOTS):
+        p = p_on_grid(np.array(roots), lam)
+        m = int(np.argmin(p))                          # lowest j on ties
+        if p[m] > 0.0:
+            break
+        roots.append(base[int(np.argmin(np.abs(base - lam[m])))])   # nearest root, lowest index on ties
+    return np.array(roots)
+
+
 def gmres_poly_roots(g, problem: str, apply_a, degree: int, seed: int) -> np.ndarray:
-    """Roots theta_1..theta_k of the GMRES residual polynomial, Leja ordered."""
+    """Roots theta_1..theta_k' of the GMRES residual polynomial (k' = degree
+    plus the roots step 2b adds), Leja ordered."""
     v = poly_start_vector(g.n, seed)
     z = null_vector(g, problem)
     v = v - (z @ v) / (z @ z) * z
     alpha, beta = lanczos(apply_a, v, degree)
-    return leja_order(harmonic_ritz(alpha, beta))
+    return leja_order(definite_roots(harmonic_ritz(alpha, beta)))
 
 
 def poly_apply(apply_a, roots: np.ndarray, v: np.ndarray) -> np.ndarray:

@@ -90,3 +90,60 @@ def test_leja_order():
     assert out[0] == 3.0
     assert out[1] == 0.1                      # farthest from 3
     assert sorted(out) == sorted(th)
+
+
+def _harmonic(g, seed, k=25):
+    lmat = O.laplacian_combinatorial(g)
+    v = O.poly_start_vector(g.n, seed)
+    v -= v.mean()
+    alpha, beta = lanczos(lambda x: lmat @ x, v, k)
+    return harmonic_ritz(alpha, beta)
+
+
+def _p_applied(roots, lam):
+    """p(lambda_j) for every point of lam as LOBPCG applies it: the product-form
+    recurrence on the diagonal operator diag(lam)."""
+    return poly_apply(lambda t: lam[:, None] * t, roots, np.ones((lam.size, 1)))[:, 0]
+
+
+def test_definite_roots_leaves_a_positive_polynomial_alone():
+    th = _harmonic(W.grid2d(16, 16), 1, 12)
+    fine = np.linspace(0.0, th.max(), 40001)[1:]
+    assert _p_applied(th, fine).min() > 0.0
+    assert np.array_equal(O.definite_roots(th), th)
+
+
+def test_definite_roots_makes_an_indefinite_polynomial_positive():
+    """A 1000-vertex geometric graph whose degree-25 GMRES polynomial dips far
+    below zero between its largest roots (step 2b of oracle.precond): each
+    added root repeats an existing one, p as applied is positive on a grid
+    five times finer than the one the rule scans, and the residual polynomial
+    still vanishes at every root."""
+    th = _harmonic(W.rgg(1000, seed=11), 27)
+    fine = np.linspace(0.0, th.max(), 5 * O.precond.DEFINITE_GRID + 1)[1:]
+    assert _p_applied(th, fine).min() < -1.0
+    th2 = O.definite_roots(th)
+    added = th2[th.size:]
+    assert np.array_equal(th2[:th.size], th) and 1 <= added.size <= O.precond.MAX_ADDED_ROOTS
+    assert all(np.any(th == r) for r in added)
+    assert _p_applied(th2, fine).min() > 0.0
+    ordered = leja_order(th2)
+    assert np.array_equal(np.sort(ordered), np.sort(th2))
+    for r in th2:
+        assert abs(1.0 - r * _poly_scalar(ordered, r)) < 1e-8
+
+
+def test_definite_roots_adds_the_root_nearest_the_minimum():
+    """Hand-made roots.  With 0.5 and 1, 1 - lambda p = (1 - 2 lambda)(1 - lambda)
+    lies below 1 on all of (0, 1], so nothing is added.  With 0.05, 0.6 and 1
+    the product (1 - 20 lambda)(1 - lambda / 0.6)(1 - lambda) is about
+    (-15.5)(-0.375)(0.175) = 1.017 at lambda = 0.825, so p < 0 there; the root
+    nearest that point is 1, whose second factor (0.175) brings the product
+    under 1."""
+    assert np.array_equal(O.definite_roots(np.array([0.5, 1.0])), [0.5, 1.0])
+    th = np.array([0.05, 0.6, 1.0])
+    lam = np.linspace(0.0, 1.0, 40001)[1:]
+    assert _p_applied(th, lam).min() < 0.0
+    th2 = O.definite_roots(th)
+    assert np.array_equal(th2, [0.05, 0.6, 1.0, 1.0])
+    assert _p_applied(th2, lam).min() > 0.0
