@@ -6,7 +6,8 @@ Calls only oracle/ (and the seeded generators in workloads/).  Usage:
     python tests/golden/make_oracle_golden.py c1     # 64 x 64 5-point mesh
     python tests/golden/make_oracle_golden.py c3     # R-MAT scale 22, largest component
     python tests/golden/make_oracle_golden.py amg    # 128^3 27-point mesh, multigrid preconditioner
-    python tests/golden/make_oracle_golden.py c4     # selected graphs of the 2000-graph RGG batch
+    python tests/golden/make_oracle_golden.py c4 [i ...]  # graphs i of the 2000-graph RGG batch
+                                                          # (default: the largest, median and smallest)
 """
 
 from __future__ import annotations
@@ -56,23 +57,34 @@ def c4_indices() -> list:
     return order[-3:] + order[mid - 1:mid + 2] + order[:2]
 
 
-def run_c4() -> dict:
+def run_c4(indices=None) -> dict:
+    """The oracle on graphs `indices` of the batch (default: c4_indices()),
+    each merged into c4_oracle.json as soon as it finishes (under a file lock,
+    so that several processes can share the list)."""
+    import fcntl
     sizes = c4_sizes()
-    graphs = []
-    t0 = time.time()
-    for i in c4_indices():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c4_oracle.json")
+    out = None
+    for i in (indices if indices else c4_indices()):
         g = workloads.rgg(int(sizes[i]), seed=4 + i)
+        t0 = time.time()
         r = oracle.partition(g, C4["K"], problem=C4["problem"], precond=C4["precond"], tol=C4["tol"],
                              seed=C4["seed"], poly_degree=C4["poly_degree"], maxit=C4["maxit"])
-        graphs.append({"index": i, "n_drawn": int(sizes[i]), "n": g.n, "nnz": g.nnz,
-                       "eigenvalues": [float(v) for v in r.eigenvalues], "iterations": int(r.iterations),
-                       "status": r.status, "cut": float(r.cut), "imbalance": float(r.imbalance)})
-        print(i, g.n, r.iterations, r.status, r.cut, flush=True)
-    out = {"workload": "2000 RGGs (workloads.rgg_batch), combinatorial, polynomial degree 25, K=8, tol 1e-3",
-           **{k: v for k, v in C4.items()}, "graphs": graphs, "oracle_seconds": round(time.time() - t0, 2)}
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c4_oracle.json")
-    with open(path, "w") as f:
-        json.dump(out, f, indent=1)
+        entry = {"index": i, "n_drawn": int(sizes[i]), "n": g.n, "nnz": g.nnz,
+                 "eigenvalues": [float(v) for v in r.eigenvalues], "iterations": int(r.iterations),
+                 "status": r.status, "cut": float(r.cut), "imbalance": float(r.imbalance),
+                 "oracle_seconds": round(time.time() - t0, 2)}
+        print(i, g.n, r.iterations, r.status, r.cut, entry["oracle_seconds"], flush=True)
+        with open(path + ".lock", "w") as lk:
+            fcntl.flock(lk, fcntl.LOCK_EX)
+            out = {"workload": "2000 RGGs (workloads.rgg_batch), combinatorial, polynomial degree 25, K=8, tol 1e-3",
+                   **C4, "graphs": []}
+            if os.path.exists(path):
+                with open(path) as f:
+                    out["graphs"] = [e for e in json.load(f)["graphs"] if e["index"] != i]
+            out["graphs"] = sorted(out["graphs"] + [entry], key=lambda e: -e["n"])
+            with open(path, "w") as f:
+                json.dump(out, f, indent=1)
     return out
 
 
@@ -100,7 +112,7 @@ def run(name: str) -> dict:
 if __name__ == "__main__":
     for name in sys.argv[1:] or ["c1", "c2"]:
         if name == "c4":
-            run_c4()
-            continue
+            run_c4([int(v) for v in sys.argv[2:]])
+            break
         res = run(name)
         print(name, res["iterations"], res["eigenvalues"], res["cut"], res["oracle_seconds"])
