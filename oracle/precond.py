@@ -20,9 +20,15 @@ the standard one for a symmetric operator:
    graphs LOBPCG then stalls for thousands of iterations).  While the minimum
    of p over lambda_j = theta_max j / G, j = 1..G (G = DEFINITE_GRID), is not
    positive, a second copy of the root nearest the minimising lambda_j is
-   added, at most MAX_ADDED_ROOTS times.  Repeating a root is the device the
-   GMRES-polynomial papers Sec. 5.2 cites use for stability ("adding roots");
-   here it is triggered by the sign of p, a reading (the paper gives no rule);
+   added, at most MAX_INTERIOR_ROOTS times.  Above theta_max every factor is
+   negative, so there the product has the sign (-1)^(root count): with an
+   even count it grows past 1 before lambda_max (which theta_max can
+   underestimate by a percent) and p turns negative; so an even count gets
+   one more copy of theta_max, which shrinks the product's magnitude below
+   theta_max and makes p positive above it.  Repeating a root is the device
+   the GMRES-polynomial papers Sec. 5.2 cites use for stability ("adding
+   roots"); here it is triggered by the sign of p, a reading (the paper gives
+   no rule);
 3. the roots are put in modified Leja order;
 4. p is applied in product form, 1 - lambda p(lambda) = prod_i (1 - lambda/theta_i):
    y = 0, t = v; for i = 1..k: y += t / theta_i; if i < k: t -= A t / theta_i,
@@ -117,7 +123,8 @@ def harmonic_ritz(alpha: np.ndarray, beta: np.ndarray) -> np.ndarray:
 
 
 DEFINITE_GRID = 8192
-MAX_ADDED_ROOTS = 4
+MAX_INTERIOR_ROOTS = 4
+MAX_ADDED_ROOTS = MAX_INTERIOR_ROOTS + 1   # and the parity copy
 
 
 def p_on_grid(theta: np.ndarray, lam: np.ndarray) -> np.ndarray:
@@ -135,12 +142,14 @@ def definite_roots(theta: np.ndarray) -> np.ndarray:
     base = np.asarray(theta, dtype=np.float64)
     roots = list(base)
     lam = (base.max() * np.arange(1, DEFINITE_GRID + 1, dtype=np.float64)) / DEFINITE_GRID
-    for _ in range(MAX_ADDED_ROOTS):
+    for _ in range(MAX_INTERIOR_ROOTS):
         p = p_on_grid(np.array(roots), lam)
         m = int(np.argmin(p))                          # lowest j on ties
         if p[m] > 0.0:
             break
         roots.append(base[int(np.argmin(np.abs(base - lam[m])))])   # nearest root, lowest index on ties
+    if len(roots) % 2 == 0:
+        roots.append(base.max())                       # an odd count: p > 0 above theta_max
     return np.array(roots)
 
 

@@ -106,25 +106,40 @@ def _p_applied(roots, lam):
     return poly_apply(lambda t: lam[:, None] * t, roots, np.ones((lam.size, 1)))[:, 0]
 
 
-def test_definite_roots_leaves_a_positive_polynomial_alone():
-    th = _harmonic(W.grid2d(16, 16), 1, 12)
-    fine = np.linspace(0.0, th.max(), 40001)[1:]
+def test_definite_roots_leaves_a_positive_polynomial_of_odd_degree_alone():
+    th = _harmonic(W.grid2d(16, 16), 1, 13)
+    fine = np.linspace(0.0, 1.5 * th.max(), 40001)[1:]
     assert _p_applied(th, fine).min() > 0.0
     assert np.array_equal(O.definite_roots(th), th)
+
+
+def test_definite_roots_makes_an_even_count_odd():
+    """Above the largest root every factor is negative: with an even number of
+    roots the product grows past 1 and p < 0 there (a degree-12 polynomial on
+    a 16 x 16 grid graph, at 1.5 theta_max); the parity copy of theta_max
+    makes p positive above theta_max and keeps it positive below."""
+    th = _harmonic(W.grid2d(16, 16), 1, 12)
+    fine = np.linspace(0.0, 1.5 * th.max(), 40001)[1:]
+    assert _p_applied(th, fine).min() < 0.0
+    th2 = O.definite_roots(th)
+    assert th2.size == 13 and np.array_equal(th2[:12], th) and th2[12] == th.max()
+    assert _p_applied(th2, fine).min() > 0.0
 
 
 def test_definite_roots_makes_an_indefinite_polynomial_positive():
     """A 1000-vertex geometric graph whose degree-25 GMRES polynomial dips far
     below zero between its largest roots (step 2b of oracle.precond): each
-    added root repeats an existing one, p as applied is positive on a grid
-    five times finer than the one the rule scans, and the residual polynomial
-    still vanishes at every root."""
+    added root repeats an existing one, the count ends odd, p as applied is
+    positive on a grid five times finer than the one the rule scans and
+    reaching 1.5 theta_max, and the residual polynomial still vanishes at
+    every root."""
     th = _harmonic(W.rgg(1000, seed=11), 27)
-    fine = np.linspace(0.0, th.max(), 5 * O.precond.DEFINITE_GRID + 1)[1:]
+    fine = np.linspace(0.0, 1.5 * th.max(), 5 * O.precond.DEFINITE_GRID + 1)[1:]
     assert _p_applied(th, fine).min() < -1.0
     th2 = O.definite_roots(th)
     added = th2[th.size:]
     assert np.array_equal(th2[:th.size], th) and 1 <= added.size <= O.precond.MAX_ADDED_ROOTS
+    assert th2.size % 2 == 1
     assert all(np.any(th == r) for r in added)
     assert _p_applied(th2, fine).min() > 0.0
     ordered = leja_order(th2)
@@ -134,16 +149,16 @@ def test_definite_roots_makes_an_indefinite_polynomial_positive():
 
 
 def test_definite_roots_adds_the_root_nearest_the_minimum():
-    """Hand-made roots.  With 0.5 and 1, 1 - lambda p = (1 - 2 lambda)(1 - lambda)
-    lies below 1 on all of (0, 1], so nothing is added.  With 0.05, 0.6 and 1
+    """Hand-made roots.  With 0.5, 0.8 and 1, 1 - lambda p lies below 1 on all
+    of (0, 1] and the count is odd, so nothing is added.  With 0.05, 0.6 and 1
     the product (1 - 20 lambda)(1 - lambda / 0.6)(1 - lambda) is about
     (-15.5)(-0.375)(0.175) = 1.017 at lambda = 0.825, so p < 0 there; the root
     nearest that point is 1, whose second factor (0.175) brings the product
-    under 1."""
-    assert np.array_equal(O.definite_roots(np.array([0.5, 1.0])), [0.5, 1.0])
+    under 1; the count is then 4, and the parity copy of 1 makes it 5."""
+    assert np.array_equal(O.definite_roots(np.array([0.5, 0.8, 1.0])), [0.5, 0.8, 1.0])
     th = np.array([0.05, 0.6, 1.0])
-    lam = np.linspace(0.0, 1.0, 40001)[1:]
+    lam = np.linspace(0.0, 1.5, 60001)[1:]
     assert _p_applied(th, lam).min() < 0.0
     th2 = O.definite_roots(th)
-    assert np.array_equal(th2, [0.05, 0.6, 1.0, 1.0])
+    assert np.array_equal(th2, [0.05, 0.6, 1.0, 1.0, 1.0])
     assert _p_applied(th2, lam).min() > 0.0
