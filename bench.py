@@ -518,6 +518,8 @@ def run_batch(args, world, rank, local):
             "graphs_converged": int(np.sum(status == 0)),
             "graphs_finished_in_fp64": int(st.get("fp64_finished", 0)),
             "graphs_noconv": int(np.sum(status != 0)),
+            "noconv_graph_sizes": sorted((int(graphs[q].n) for q in np.flatnonzero(status != 0)), reverse=True)[:20],
+            "ms_float_phase": float(st["ms_phase"][0]), "ms_fp64_phase": float(st["ms_phase"][1]),
             "vs_oracle": batch_vs_oracle(w, eigs, cuts, status),
             "stall_window": w.get("stall_window", 0), "max_iter": w.get("max_iter", 1000),
             "max_iterations": int(iters.max()),
@@ -728,6 +730,63 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_products(args) -> int:
+    """No partition: time args.products Laplacian products Y = L X of the
+    workload's graph (its Laplacian, blocks of width round4(d) in FP32, or FP64
+    with --precision fp64), with an L2 flush before each, then run two more
+    between cudaProfilerStart and cudaProfilerStop, the launches an
+    `ncu --profile-from-start off` capture sees.  Prints one JSON line."""
+    import torch
+    import paper_2105_00578_gb300 as spx
+    w = WORKLOADS[args.workload]
+    g = make_graph(args.workload)
+    d = int(np.floor(np.log2(w["K"]))) + 1
+    bp = (d + 3) // 4 * 4
+    f64 = args.precision == "fp64"
+    dt, tdt, s = (spx.DT_F64, torch.float64, 8) if f64 else (spx.DT_F32, torch.float32, 4)
+    h = spx.sphynx_create(g.row_ptr, g.col, g.w, None)
+    if args.spmm_variant is not None:
+        spx.sphynx_set_spmm_variant(h, {"csr": 0, "sell": 1, "pattern": 2}[args.spmm_variant])
+    gen = torch.Generator(device="cuda").manual_seed(w["seed"])
+    x = torch.randn(g.n, bp, dtype=tdt, device="cuda", generator=gen)
+    y = torch.empty_like(x)
+    lap = w["laplacian"]
+
+    def apply():
+        spx.sphynx_laplacian_apply(h, lap, dt, x, bp, y, bp, bp)
+
+    for _ in range(3):
+        apply()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # twice L2
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    us = []
+    for _ in range(args.products):
+        flush.fill_(1)
+        e0.record()
+        apply()
+        e1.record()
+        torch.cuda.synchronize()
+        us.append(e0.elapsed_time(e1) * 1000.0)
+    torch.cuda.profiler.start()
+    for _ in range(2):
+        flush.fill_(1)
+        apply()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    info = spx.sphynx_get_info(h)
+    spx.sphynx_destroy(h)
+    med = float(np.median(us))
+    sb = survey_bytes(g.n, g.nnz, d, s, s, s, g.w is not None)
+    pk = peaks()
+    print(json.dumps({
+        "workload": args.workload, "laplacian": lap, "n": g.n, "nnz": g.nnz, "block": d, "width": bp,
+        "dtype": "f64" if f64 else "f32", "products": args.products, "us_median": med, "us_min": float(min(us)),
+        "survey_bytes": sb, "gbs": sb / med / 1e3, "peak_gbs": pk["hbm_gbs"], "frac": sb / med / 1e3 / pk["hbm_gbs"],
+        "l2": "256 MiB written between products",
+        "schedule": {k: info[k] for k in ("spmm_variant", "spmm_med_max", "sell_stride", "long_rows")}}))
+    return 0
+
+
 def _res_ratio(st, tol):
     """max over the non-null columns of ||r|| / (tol |theta|)"""
     vals = [r / (tol * abs(t)) for r, t in zip(st["resnorm"][1:], st["eigenvalues"][1:]) if t != 0]
@@ -756,10 +815,15 @@ def main():
     ap.add_argument("--kernel-regex", default=r"k_spmm_sell<(\(int\))?0, __nv_bfloat16, __nv_bfloat16",
                     help="kernels of the ncu log that --ingest-ncu averages")
     ap.add_argument("--ncu-command", default="", help="the ncu command that wrote the log (recorded by --ingest-ncu)")
+    ap.add_argument("--products", type=int, default=0, metavar="N",
+                    help="no partition: time N Laplacian products of the workload's graph (and profile two more "
+                         "between cudaProfilerStart/Stop)")
     args = ap.parse_args()
     if args.ingest_ncu:
         print(json.dumps(ingest_ncu(args.ingest_ncu, args.kernel_regex, args.workload, args.ncu_command)))
         return 0
+    if args.products > 0:
+        return run_products(args)
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, world, rank)

@@ -107,6 +107,9 @@ extern "C" {
 #define SPHYNX_MAX_NEV 16
 /* Largest polynomial degree (Sec. 5.2 uses 25). */
 #define SPHYNX_MAX_POLY_DEGREE 64
+/* Roots the polynomial setup may add to keep p positive (sphynx_precond_setup):
+ * up to 4 where p dips below zero, and one to make the count odd. */
+#define SPHYNX_MAX_ADDED_ROOTS 5
 
 typedef struct sphynx_graph *sphynx_handle;
 
@@ -164,7 +167,10 @@ typedef struct {
                             stalled at the float rounding floor above tol |theta|
                             and finished in FP64 blocks from their float iterate */
   int32_t refine_moves;  /* vertices moved by greedy refinement (refine_rounds)  */
-  double reserved[3];
+  double ms_phase[2];    /* sphynx_partition_batch: wall time of the eigensolve in
+                            the requested precision and of the FP64 finishing
+                            (0 when no graph was promoted)                      */
+  double reserved[1];
 } sphynx_stats;
 
 typedef struct {
@@ -188,9 +194,10 @@ typedef struct {
                                 chosen schedule (indices, weights, row metadata)   */
   int32_t regular;           /* 1 if max degree <= 10 x average degree (Sec. 6.1)  */
   int32_t spmm_med_max;      /* the autotuner's choice: rows with 33 to this many
-                                neighbours use the medium-row kernel (a lane per
-                                row), longer rows the long-row kernels (a warp per
-                                4096-entry piece); 32 means none are medium         */
+                                neighbours use the medium-row kernel (a group of
+                                lanes per row), longer rows the long-row kernels
+                                (a warp per 1024-entry piece); 32 means none are
+                                medium                                              */
   int32_t sell_stride;       /* the autotuner's SELL-32 slice order: the four warps
                                 of a block take slices this many apart (1, 2, 4, 8
                                 or 16), so that on a mesh a block's rows can lie
@@ -294,9 +301,13 @@ int sphynx_poly_step(sphynx_handle g, int32_t laplacian, int32_t dtype_in, const
                      int32_t yterms, int32_t first);
 
 /* Set up the preconditioner of `opt` (Sec. 5) and, for the polynomial,
- * return its roots theta_1..theta_k in application order (harmonic Ritz
- * values of k Lanczos steps, Leja ordered) in host double[poly_degree]
- * (may be NULL).  For multigrid, build the level hierarchy for opt->seed
+ * return its roots in application order in host
+ * double[poly_degree + SPHYNX_MAX_ADDED_ROOTS] (may be NULL): the harmonic
+ * Ritz values of k = poly_degree Lanczos steps, plus a second copy of a root
+ * for each time p was not positive on a grid over (0, largest root] (at most
+ * 4), plus a copy of the largest root if the count is then even (p is then
+ * positive above the largest root too; LOBPCG needs a positive definite
+ * preconditioner), Leja ordered; the entries after the last root are +inf.  For multigrid, build the level hierarchy for opt->seed
  * (kept by the handle and reused while the seed is the same); a coarse row
  * sorts its entries in shared memory when its aggregate's rows hold at most
  * 8192 of them and in global scratch (chunks of at most 512 MiB) otherwise;

@@ -56,13 +56,14 @@ class Stats(C.Structure):
                 ("imbalance", C.c_double),
                 ("ms_spmm_by_dt", C.c_double * 3), ("spmm_bytes_by_dt", C.c_double * 3),
                 ("spmm_launches_by_dt", C.c_int64 * 3), ("fp64_finished", C.c_int32), ("refine_moves", C.c_int32),
-                ("reserved", C.c_double * 3)]
+                ("ms_phase", C.c_double * 2), ("reserved", C.c_double * 1)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_
              if f not in ("reserved", "eigenvalues", "resnorm")}
         d["eigenvalues"] = list(self.eigenvalues[: self.nev])
         d["resnorm"] = list(self.resnorm[: self.nev])
+        d["ms_phase"] = list(self.ms_phase)
         return d
 
 
@@ -249,10 +250,15 @@ def sphynx_poly_step(h, laplacian, dtype_in, t, dtype_out, t_out, y, ld, ncols, 
                                ptr(y), ld, ncols, float(theta_cur), float(theta_next), yterms, first))
 
 
+MAX_ADDED_ROOTS = 5
+
+
 def sphynx_precond_setup(h, opt: Options) -> np.ndarray:
-    roots = np.zeros(max(1, opt.poly_degree))
+    """Set up the preconditioner; for the polynomial, its roots in application
+    order (the degree plus any roots added to keep it positive)."""
+    roots = np.zeros(max(1, opt.poly_degree) + MAX_ADDED_ROOTS)
     check(LIB.sphynx_precond_setup(h, C.byref(opt), _dptr(roots)))
-    return roots[: opt.poly_degree] if opt.precond == PRECOND_POLY else np.zeros(0)
+    return roots[np.isfinite(roots)] if opt.precond == PRECOND_POLY else np.zeros(0)
 
 
 def sphynx_precond_apply(h, opt: Options, r, hout, ld, ncols) -> None:

@@ -683,15 +683,13 @@ void batch_poly_setup_t(sphynx_graph *g, int k, int lap, uint64_t seed) {
   T *V = static_cast<T *>(g->workspace("bz_V", static_cast<size_t>(ldv) * (k + 1) * sizeof(T), false));
   T *v = static_cast<T *>(g->workspace("bz_v", static_cast<size_t>(ldv) * sizeof(T), false));
   T *w = static_cast<T *>(g->workspace("bz_w", static_cast<size_t>(ldv) * sizeof(T), false));
-  const int S = SPHYNX_MAX_POLY_DEGREE + 2;   // per-graph stride of the small arrays
+  const int S = SPHYNX_MAX_POLY_DEGREE + SPHYNX_MAX_ADDED_ROOTS + 2;   // per-graph stride of the small arrays
   double *part = static_cast<double *>(g->workspace("bz_part", static_cast<size_t>(B.n_chunks) * S * 8, false));
   double *small = static_cast<double *>(g->workspace("bz_small", static_cast<size_t>(count) * S * 5 * 8, true));
   double *alpha = small, *beta2 = small + static_cast<size_t>(count) * S, *h = beta2 + static_cast<size_t>(count) * S;
   double *scal = h + static_cast<size_t>(count) * S, *roots = scal + static_cast<size_t>(count) * S;
-  int *err = static_cast<int *>(g->workspace("bz_err", static_cast<size_t>(count) * sizeof(int), true));
-  const int KS = k + 1;
-  B.poly_inv.alloc(static_cast<size_t>(count) * KS * sizeof(double));
-  B.poly_invf.alloc(static_cast<size_t>(count) * KS * sizeof(float));
+  int *err = static_cast<int *>(g->workspace("bz_err", static_cast<size_t>(count) * 2 * sizeof(int), true));
+  int *kout = err + count;
   // start vector, null column, projection, normalisation
   k_bz_start<T><<<cg, 256, 0, st>>>(cv, B.gptr.as<int64_t>(), v, mix64(seed + 3 * kGamma));
   SPX_LAUNCHED();
@@ -738,16 +736,25 @@ void batch_poly_setup_t(sphynx_graph *g, int k, int lap, uint64_t seed) {
     }
     g->ctr.launches += 9;
   }
-  launch_harmonic_ritz_batch(st, alpha, beta2, k, count, S, roots, h, reinterpret_cast<float *>(scal), err);
-  // roots in application order -> per-graph 1/theta arrays of stride k + 1 (double and float)
+  launch_harmonic_ritz_batch(st, alpha, beta2, k, count, S, roots, h, reinterpret_cast<float *>(scal), err, kout);
+  g->ctr.launches += 3;
+  // roots in application order -> per-graph 1/theta arrays of stride KS (double
+  // and float), KS - 1 the largest root count; a graph with fewer roots has
+  // 1/theta = 0 (an infinite root) on the steps beyond its own
   std::vector<double> hinv(static_cast<size_t>(count) * S);
-  std::vector<int> herr(static_cast<size_t>(count));
+  std::vector<int> herr(static_cast<size_t>(count) * 2);
   SPX_CUDA(cudaMemcpyAsync(hinv.data(), h, hinv.size() * 8, cudaMemcpyDeviceToHost, st));
   SPX_CUDA(cudaMemcpyAsync(herr.data(), err, herr.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
   SPX_CUDA(cudaStreamSynchronize(st));
-  for (int q = 0; q < count; ++q)
+  int kmax = k;
+  for (int q = 0; q < count; ++q) {
     if (herr[q]) fail(SPHYNX_ERR_BREAKDOWN, "polynomial setup of graph %d: Lanczos tridiagonal not positive definite "
                       "(%d)", q, herr[q]);
+    kmax = std::max(kmax, herr[count + q]);
+  }
+  const int KS = kmax + 1;
+  B.poly_inv.alloc(static_cast<size_t>(count) * KS * sizeof(double));
+  B.poly_invf.alloc(static_cast<size_t>(count) * KS * sizeof(float));
   std::vector<double> inv(static_cast<size_t>(count) * KS);
   std::vector<float> invf(inv.size());
   for (int q = 0; q < count; ++q)
@@ -758,7 +765,7 @@ void batch_poly_setup_t(sphynx_graph *g, int k, int lap, uint64_t seed) {
   SPX_CUDA(cudaMemcpyAsync(B.poly_inv.p, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, st));
   SPX_CUDA(cudaMemcpyAsync(B.poly_invf.p, invf.data(), invf.size() * 4, cudaMemcpyHostToDevice, st));
   SPX_CUDA(cudaStreamSynchronize(st));   // the host vectors above feed asynchronous copies
-  B.poly_k = k;
+  B.poly_k = kmax;
   B.poly_lap = lap;
 }
 
@@ -1276,7 +1283,9 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   const bool promote = dt0 != DT::F64;
   const int window1 = promote ? (o->stall_window > 0 ? o->stall_window : kPromoteWindow) : o->stall_window;
   const DT ct0 = o->precision == SPHYNX_FP64 ? DT::F64 : (o->precision == SPHYNX_MIXED_BF16 ? DT::BF16 : DT::F32);
+  auto tp = std::chrono::steady_clock::now();
   Blocks k1 = run_phase(dt0, ct0, dt0, "", false, window1, promote ? 1 : 0);
+  double ms_phase[2] = {std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp).count(), 0.0};
   std::vector<SolverState> hs = read_states();
   std::vector<int> zero_it(count, 0);
   std::vector<char> all(count, 1);
@@ -1306,7 +1315,9 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     k_bpromote<<<(count + 127) / 128, 128, 0, st>>>(states, count, dprom.as<char>(), ctl);
     SPX_LAUNCHED();
     SPX_CUDA(cudaStreamSynchronize(st));   // `promoted` feeds an asynchronous copy
+    tp = std::chrono::steady_clock::now();
     Blocks k2 = run_phase(DT::F64, ct0, DT::F32, "_64", true, o->stall_window, 0);
+    ms_phase[1] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp).count();
     hs = read_states();
     gather_x0(k2, DT::F64, hs, it1, promoted);
     dt = DT::F64;
@@ -1387,6 +1398,8 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     for (int q = 0; q < count; ++q) maxit = std::max(maxit, hs[q].iters);
     stats->status = nconv_graphs == count ? SPHYNX_OK : SPHYNX_ERR_NOCONV;
     stats->fp64_finished = n_promoted;
+    stats->ms_phase[0] = ms_phase[0];
+    stats->ms_phase[1] = ms_phase[1];
     stats->iterations = maxit;
     stats->nev = b;
   }

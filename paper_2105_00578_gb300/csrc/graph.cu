@@ -371,30 +371,16 @@ int grid_for(int64_t n) {
   return static_cast<int>(g);
 }
 
-// medium rows into their slices (one thread per lane slot)
-__global__ void k_med_fill(const int64_t *rp, const int32_t *col, const float *w, const int32_t *mrow,
-                           const int32_t *mdeg, const int64_t *mptr, int64_t nslices, int32_t *mcol, float *mw) {
-  const int64_t slot = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (slot >= nslices * 32) return;
-  const int row = mrow[slot];
-  if (row < 0) return;
-  const int d = mdeg[slot];
-  const int64_t src = rp[row], dst = mptr[slot >> 5] + (slot & 31);
-  for (int t = 0; t < d; ++t) {
-    mcol[dst + 32 * t] = col[src + t];
-    if (w) mw[dst + 32 * t] = w[src + t];
-  }
-}
-
 // Rows with more than kShortDeg neighbours: those with at most med_max go to
-// the medium slices (a lane per row), the rest to long-row work items (a warp
-// per 4096-entry item).  med_max = kShortDeg sends them all to the items.
+// the medium-row units (a group of lanes per row), the rest to long-row work
+// items (a warp per 1024-entry item).  med_max = kShortDeg sends them all to
+// the items.
 void build_plan(sphynx_graph *g, const int64_t *host_rowptr, int med_max) {
   SpmmPlan &p = g->plan;
   p.n_long = 0;
   p.n_items = 0;
   p.n_med = 0;
-  p.n_med_slices = 0;
+  p.n_units = 0;
   p.med_bytes = 0;
   p.long_bytes = 0;
   p.med_max = med_max;
@@ -408,7 +394,9 @@ void build_plan(sphynx_graph *g, const int64_t *host_rowptr, int med_max) {
     SPX_CUDA(cudaStreamSynchronize(g->stream));
     rp = rp_copy.data();
   }
-  // medium rows: sorted by degree, 32 to a slice
+  // medium rows: sorted by degree (descending, row id on ties); a row of d
+  // entries gets G = the smallest power of two with d <= G kGroupPerLane (at
+  // most 32) lanes, and the rows of one G fill warp units of 32 / G rows
   std::vector<std::pair<int64_t, int32_t>> med;   // (-degree, row)
   for (int64_t i = 0; i < g->n; ++i) {
     const int64_t dg = rp[i + 1] - rp[i];
@@ -416,33 +404,40 @@ void build_plan(sphynx_graph *g, const int64_t *host_rowptr, int med_max) {
   }
   std::sort(med.begin(), med.end());
   p.n_med = static_cast<int64_t>(med.size());
-  p.n_med_slices = (p.n_med + 31) / 32;
-  if (p.n_med_slices > 0) {
-    const int64_t ns = p.n_med_slices;
-    std::vector<int32_t> mrow(static_cast<size_t>(ns) * 32, -1), mdeg(static_cast<size_t>(ns) * 32, 0);
-    std::vector<int64_t> mptr(static_cast<size_t>(ns) + 1, 0);
+  if (p.n_med > 0) {
+    std::vector<int32_t> grow(med.size());
+    std::vector<int32_t> units;   // pairs {first, log2 G | count << 8}
     double entries = 0;
-    for (int64_t k = 0; k < p.n_med; ++k) {
-      mrow[k] = med[k].second;
-      mdeg[k] = static_cast<int32_t>(-med[k].first);
-      entries += static_cast<double>(-med[k].first);
+    auto lg_of = [](int64_t d) {
+      int lg = 0;
+      while (lg < 5 && (int64_t{kGroupPerLane} << lg) < d) ++lg;
+      return lg;
+    };
+    for (int64_t k = 0; k < p.n_med;) {
+      const int lg = lg_of(-med[k].first);
+      const int cap = 32 >> lg;
+      int cnt = 0;
+      const int64_t first = k;
+      while (k < p.n_med && cnt < cap && lg_of(-med[k].first) == lg) {
+        grow[k] = med[k].second;
+        entries += static_cast<double>(-med[k].first);
+        ++k;
+        ++cnt;
+      }
+      units.push_back(static_cast<int32_t>(first));
+      units.push_back(lg | (cnt << 8));
     }
-    for (int64_t s = 0; s < ns; ++s) mptr[s + 1] = mptr[s] + 32 * static_cast<int64_t>(mdeg[s * 32]);   // first lane: largest
-    p.med_row.alloc(mrow.size() * sizeof(int32_t));
-    p.med_deg.alloc(mdeg.size() * sizeof(int32_t));
-    p.med_ptr.alloc(mptr.size() * sizeof(int64_t));
-    p.med_col.alloc(static_cast<size_t>(mptr[ns]) * sizeof(int32_t));
-    if (g->weighted) p.med_w.alloc(static_cast<size_t>(mptr[ns]) * sizeof(float));
-    SPX_CUDA(cudaMemcpyAsync(p.med_row.p, mrow.data(), mrow.size() * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
-    SPX_CUDA(cudaMemcpyAsync(p.med_deg.p, mdeg.data(), mdeg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, g->stream));
-    SPX_CUDA(cudaMemcpyAsync(p.med_ptr.p, mptr.data(), mptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream));
-    k_med_fill<<<static_cast<unsigned>((ns * 32 + 255) / 256), 256, 0, g->stream>>>(
-        g->rowptr, g->col, g->w, p.med_row.as<int32_t>(), p.med_deg.as<int32_t>(), p.med_ptr.as<int64_t>(), ns,
-        p.med_col.as<int32_t>(), p.med_w.as<float>());
-    SPX_LAUNCHED();
-    SPX_CUDA(cudaStreamSynchronize(g->stream));
-    // real entries' indices (and weights), row ids and degrees of the lane slots, slice offsets
-    p.med_bytes = entries * (g->weighted ? 8.0 : 4.0) + static_cast<double>(ns) * (32.0 * 8.0 + 8.0);
+    p.n_units = static_cast<int64_t>(units.size() / 2);
+    p.grp_row.alloc(grow.size() * sizeof(int32_t));
+    p.grp_unit.alloc(units.size() * sizeof(int32_t));
+    SPX_CUDA(cudaMemcpyAsync(p.grp_row.p, grow.data(), grow.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             g->stream));
+    SPX_CUDA(cudaMemcpyAsync(p.grp_unit.p, units.data(), units.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             g->stream));
+    SPX_CUDA(cudaStreamSynchronize(g->stream));   // the host vectors go out of scope
+    // real entries' indices (and weights), the row ids and row pointers, the units
+    p.med_bytes = entries * (g->weighted ? 8.0 : 4.0) + static_cast<double>(p.n_med) * 20.0 +
+                  static_cast<double>(p.n_units) * 8.0;
   }
   std::vector<int64_t> items, split;
   int64_t nnz_long = 0;
@@ -802,6 +797,7 @@ int sphynx_create(const int64_t *row_ptr, const int32_t *col, const float *edge_
       g->wexact = top < 9.0e18;
     }
     build_plan(g.get(), dev ? nullptr : row_ptr, kMedDeg);
+    g->plan.prescale = g->max_degree * g->n > 10 * g->nnz;   // irregular: max degree above 10 x the mean
     build_sell(g.get());
     autotune_spmm(g.get(), dev ? nullptr : row_ptr);
     *out = g.release();

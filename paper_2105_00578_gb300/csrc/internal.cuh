@@ -89,7 +89,8 @@ __device__ inline double splitmix_pm1(uint64_t state, uint64_t ctr) {
 
 constexpr int kShortDeg = 32;        // rows with more neighbours are medium or long rows
 constexpr int kMedDeg = 4096;        // rows with more neighbours than this are long rows
-constexpr int kLongChunk = 4096;     // entries per long-row work item
+constexpr int kGroupPerLane = 16;    // medium rows: entries a lane of a row's group takes at most (G < 32)
+constexpr int kLongChunk = 1024;     // entries per long-row work item (32 a lane: short gather chains)
 constexpr int kSmCount = 152;
 
 // Short-row schedules the autotuner chooses between.
@@ -149,22 +150,26 @@ struct SpmmPlan {
   // sell_cptr[s] (the explicit slice in sell_col) for the others.
   int64_t pat_slices = 0;            // shared-pattern slices (0: the variant is not built)
   bool pat_all = false;              // every slice is a shared-pattern slice
+  // Normalized products with float or double input gather rows of
+  // Z = D^{-1/2} X, formed by one pass before the product, instead of X rows
+  // and the neighbour's D^{-1/2} entry: on an irregular graph that second
+  // gather costs a 32-byte sector per entry.  Set at create for irregular
+  // graphs (maximum degree above 10 x the mean).
+  bool prescale = false;
   double pat_bytes = 0;              // bytes a product reads from this layout
   DevBuf pat_cptr;                   // int64 [n_slices]
   DevBuf pat_col;                    // 16-bit units, 96 per shared-pattern slice
   double long_bytes = 0;             // bytes of the long rows' CSR entries and items
-  // Medium rows (kShortDeg < degree <= kMedDeg), sorted by degree (descending,
-  // row id on ties) and packed 32 to a slice: lane l of slice s is row
-  // med_row[32 s + l] (-1: padding) with med_deg[32 s + l] entries, entry t at
-  // med_col[med_ptr[s] + 32 t + l] (weights likewise in med_w).
+  // Medium rows (kShortDeg < degree <= med_max), sorted by degree (descending,
+  // row id on ties) into grp_row, and cut into warp units of rows that share
+  // a group width G (a power of two, G lanes per row): unit u covers rows
+  // grp_row[x .. x + count) with {x, log2 G | count << 8} = grp_unit[u].  Their
+  // entries are read from the graph's own CSR arrays.
   int med_max = kMedDeg;             // largest degree of a medium row (the autotuner's choice)
-  int64_t n_med = 0, n_med_slices = 0;
-  DevBuf med_row;                    // int32 [32 n_med_slices]
-  DevBuf med_deg;                    // int32 [32 n_med_slices]
-  DevBuf med_ptr;                    // int64 [n_med_slices + 1]
-  DevBuf med_col;                    // int32 [padded entries]
-  DevBuf med_w;                      // float [padded entries] (weighted graphs)
-  double med_bytes = 0;              // bytes a product reads from the medium slices
+  int64_t n_med = 0, n_units = 0;
+  DevBuf grp_row;                    // int32 [n_med]
+  DevBuf grp_unit;                   // int2 [n_units]
+  double med_bytes = 0;              // bytes a product reads for the medium rows
 };
 
 // Everything the iteration kernels need to apply L without forming it.
@@ -177,6 +182,7 @@ struct LapView {
   const float *degf;       // weighted degree (float)
   const double *dinv;      // deg^{-1/2}
   const float *dinvf;
+  int gather_scale;        // normalized: scale gathered rows by dinv (0: the input is D^{-1/2} X already)
 };
 
 struct Counters {
@@ -213,7 +219,7 @@ struct BatchInfo {
   // kernels walk these lists with fixed grids, so finished graphs cost nothing
   DevBuf act_blocks, act_chunks, n_act;
   // polynomial preconditioner of every graph (Sec. 5.2), set up per partition
-  int poly_k = 0;                   // degree (0: none set up)
+  int poly_k = 0;                   // chain length: the largest root count of any graph (0: none set up)
   int poly_lap = -1;
   DevBuf poly_inv;                  // double [count][poly_k + 1]: 1 / theta in application order, then 0
   DevBuf poly_invf;                 // float copy
@@ -245,10 +251,11 @@ struct sphynx_graph {
   bool wexact = true;        // the fixed-point sum cannot overflow int64
   sphynx::SpmmPlan plan;
   // polynomial preconditioner state (Sec. 5.2)
-  int poly_k = 0;
+  int poly_k = 0;            // roots (degree plus definiteness copies)
+  int poly_degree = 0;       // the degree it was set up for
   int poly_laplacian = -1;
-  sphynx::DevBuf poly_inv;   // double[k]: 1 / theta_i
-  sphynx::DevBuf poly_invf;  // float[k]
+  sphynx::DevBuf poly_inv;   // double[k + 1]: 1 / theta_i, then 0
+  sphynx::DevBuf poly_invf;  // float[k + 1]
   std::vector<double> poly_roots;
   double step_theta[2] = {0.0, 0.0};         // roots whose reciprocals sphynx_poly_step last uploaded
   std::map<std::string, sphynx::DevBuf> ws;  // named workspaces, grown on demand
@@ -259,7 +266,7 @@ struct sphynx_graph {
   sphynx::AmgHierarchy *amg = nullptr;       // multigrid preconditioner (Sec. 5.3), built on demand
   sphynx::LapView view() const {
     return sphynx::LapView{n, rowptr, col, w, deg.as<double>(), degf.as<float>(),
-                           dinv.as<double>(), dinvf.as<float>()};
+                           dinv.as<double>(), dinvf.as<float>(), 1};
   }
   void *workspace(const std::string &name, size_t bytes, bool zero = false);
 };
@@ -454,11 +461,15 @@ void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, i
 void launch_d2f(cudaStream_t st, const double *src, float *dst, int64_t n);
 void launch_gram_reduce(cudaStream_t st, const double *partials, int nblk, int ld, int grid,
                         double *ga, double *gb, const int *done);
+// Roots of the degree-k GMRES polynomial in application order, with the
+// definiteness copies: kout receives the count k' <= k + SPHYNX_MAX_ADDED_ROOTS;
+// roots[k' .. k + SPHYNX_MAX_ADDED_ROOTS) = +inf, inv / invf = 1 / roots then 0
+// up to index k + SPHYNX_MAX_ADDED_ROOTS.
 void launch_harmonic_ritz(cudaStream_t st, const double *alpha, const double *beta2, int k,
-                          double *roots, double *inv, float *invf, int *err);
-// count problems, problem q's arrays `stride` (>= k + 1) apart, err[count]
+                          double *roots, double *inv, float *invf, int *err, int *kout);
+// count problems, problem q's arrays `stride` (>= k + SPHYNX_MAX_ADDED_ROOTS + 1) apart, err and kout [count]
 void launch_harmonic_ritz_batch(cudaStream_t st, const double *alpha, const double *beta2, int k, int count,
-                                int stride, double *roots, double *inv, float *invf, int *err);
+                                int stride, double *roots, double *inv, float *invf, int *err, int *kout);
 
 // ---- mj.cu ------------------------------------------------------------------
 void run_mj(cudaStream_t st, DT dt, const void *coords, int ldc, int dims, int64_t n,

@@ -92,12 +92,13 @@ void poly_setup(sphynx_graph *g, const sphynx_options *o) {
   double *small = static_cast<double *>(g->workspace("lz_small", 8 * (4 * SPHYNX_MAX_POLY_DEGREE + 16), true));
   double *alpha = small, *beta2 = small + SPHYNX_MAX_POLY_DEGREE, *h = small + 2 * SPHYNX_MAX_POLY_DEGREE;
   double *scal = small + 3 * SPHYNX_MAX_POLY_DEGREE + 2, *nrm = scal + 4;
-  g->poly_inv.alloc((k + 1) * sizeof(double));
-  g->poly_invf.alloc((k + 1) * sizeof(float));
+  const int kcap = k + SPHYNX_MAX_ADDED_ROOTS;
+  g->poly_inv.alloc((kcap + 1) * sizeof(double));
+  g->poly_invf.alloc((kcap + 1) * sizeof(float));
   DevBuf roots, err;
-  roots.alloc(k * sizeof(double));
-  err.alloc(sizeof(int));
-  SPX_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+  roots.alloc(kcap * sizeof(double));
+  err.alloc(2 * sizeof(int));   // error flag, root count
+  SPX_CUDA(cudaMemsetAsync(err.p, 0, 2 * sizeof(int), st));
 
   launch_poly_start(st, dt, v, n, o->seed);
   launch_project_null(st, dt, v, n, lap, g->deg.as<double>(), part, grid, scal);
@@ -120,15 +121,17 @@ void poly_setup(sphynx_graph *g, const sphynx_options *o) {
     g->ctr.launches += 8;
   }
   launch_harmonic_ritz(st, alpha, beta2, k, roots.as<double>(), g->poly_inv.as<double>(), g->poly_invf.as<float>(),
-                       err.as<int>());
-  g->ctr.launches += 2;
-  int herr = 0;
-  g->poly_roots.assign(k, 0.0);
-  SPX_CUDA(cudaMemcpyAsync(g->poly_roots.data(), roots.p, k * sizeof(double), cudaMemcpyDeviceToHost, st));
-  SPX_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+                       err.as<int>(), err.as<int>() + 1);
+  g->ctr.launches += 3;
+  int herr[2] = {0, 0};
+  g->poly_roots.assign(kcap, 0.0);
+  SPX_CUDA(cudaMemcpyAsync(g->poly_roots.data(), roots.p, kcap * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SPX_CUDA(cudaMemcpyAsync(herr, err.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   SPX_CUDA(cudaStreamSynchronize(st));
-  if (herr) fail(SPHYNX_ERR_BREAKDOWN, "polynomial setup: Lanczos tridiagonal not positive definite (%d)", herr);
-  g->poly_k = k;
+  if (herr[0]) fail(SPHYNX_ERR_BREAKDOWN, "polynomial setup: Lanczos tridiagonal not positive definite (%d)", herr[0]);
+  g->poly_roots.resize(herr[1]);
+  g->poly_k = herr[1];
+  g->poly_degree = k;
   g->poly_laplacian = lap;
 }
 
@@ -583,7 +586,10 @@ int sphynx_precond_setup(sphynx_handle g, const sphynx_options *opt, double *roo
     }
     if (opt->precond != SPHYNX_PRECOND_POLY) return SPHYNX_OK;
     poly_setup(g, opt);
-    if (roots_out) memcpy(roots_out, g->poly_roots.data(), g->poly_k * sizeof(double));
+    if (roots_out) {
+      for (int i = 0; i < opt->poly_degree + SPHYNX_MAX_ADDED_ROOTS; ++i)
+        roots_out[i] = i < g->poly_k ? g->poly_roots[i] : INFINITY;
+    }
     return SPHYNX_OK;
   });
 }
@@ -598,7 +604,7 @@ int sphynx_precond_apply(sphynx_handle g, const sphynx_options *opt, const void 
     const DT dt = block_dt(opt->precision);
     const int lap = op_of(opt->laplacian);
     if (opt->precond == SPHYNX_PRECOND_POLY) {
-      if (g->poly_k != opt->poly_degree || g->poly_laplacian != lap)
+      if (g->poly_k == 0 || g->poly_degree != opt->poly_degree || g->poly_laplacian != lap)
         fail(SPHYNX_ERR_INVALID_ARG, "polynomial not set up for these options");
       if (ld != round4(ncols)) fail(SPHYNX_ERR_INVALID_ARG, "polynomial apply needs ld = round4(ncols)");
       poly_apply(g, opt->precision, r, h, ld, ncols, nullptr);

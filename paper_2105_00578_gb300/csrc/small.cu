@@ -21,6 +21,7 @@
 #include "internal.cuh"
 
 #include <cfloat>
+#include <climits>
 #include <cmath>
 
 namespace sphynx {
@@ -621,17 +622,108 @@ k_harmonic_eig(const double *alpha, const double *beta2, int k, double *theta, i
   if (lane == 0) theta[i] = 0.5 * (lo + hi);
 }
 
-// Modified Leja order of theta[0..k) (ascending): largest |theta| first, then
-// maximise the product of distances to the roots already taken (sum of logs);
+// Definiteness (Sec. 5.2 with Algorithm 1, which takes a positive definite
+// preconditioner): p(lambda) = (1 - prod_i (1 - lambda/theta_i)) / lambda is
+// evaluated on lambda_j = theta_max j / G, j = 1..G; while its minimum is not
+// positive, a second copy of the root nearest the minimising lambda_j (lowest
+// index on ties) is appended, at most kInteriorRoots times.  Above theta_max
+// the product has the sign (-1)^(count), so an even count gets one more copy
+// of theta_max, which keeps p positive there (theta_max can lie a percent
+// below lambda_max).  theta holds the k ascending harmonic Ritz values and
+// receives the copies after them; kout the new count.  The factors are
+// multiplied in list order and the minimum is the first in j, one CTA per
+// problem.
+constexpr int kDefiniteGrid = 8192;
+constexpr int kInteriorRoots = SPHYNX_MAX_ADDED_ROOTS - 1;
+constexpr int kRootCap = SPHYNX_MAX_POLY_DEGREE + SPHYNX_MAX_ADDED_ROOTS;
+
+__global__ void __launch_bounds__(256)
+k_harmonic_definite(double *theta, int k, int *kout, const int *err, int stride) {
+  __shared__ double th[kRootCap];
+  __shared__ double wmin[8];
+  __shared__ int warg[8];
+  __shared__ int kk_s, stop;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  theta += static_cast<int64_t>(blockIdx.x) * stride;
+  if (err[blockIdx.x]) {
+    if (tid == 0) kout[blockIdx.x] = k;
+    return;
+  }
+  for (int i = tid; i < k; i += blockDim.x) th[i] = theta[i];
+  if (tid == 0) kk_s = k;
+  __syncthreads();
+  const double tmax = th[k - 1];
+  for (int add = 0; add < kInteriorRoots; ++add) {
+    const int kk = kk_s;
+    double best = INFINITY;
+    int barg = INT_MAX;
+    for (int j = tid + 1; j <= kDefiniteGrid; j += blockDim.x) {
+      const double lam = (tmax * static_cast<double>(j)) / static_cast<double>(kDefiniteGrid);
+      double pi = 1.0;
+      for (int i = 0; i < kk; ++i) pi = pi * (1.0 - lam / th[i]);
+      const double p = (1.0 - pi) / lam;
+      if (p < best) {
+        best = p;
+        barg = j;
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, best, off);
+      const int oa = __shfl_down_sync(0xffffffffu, barg, off);
+      if (ov < best || (ov == best && oa < barg)) {
+        best = ov;
+        barg = oa;
+      }
+    }
+    if (lane == 0) {
+      wmin[wid] = best;
+      warg[wid] = barg;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w)
+        if (wmin[w] < best || (wmin[w] == best && warg[w] < barg)) {
+          best = wmin[w];
+          barg = warg[w];
+        }
+      stop = best > 0.0 ? 1 : 0;
+      if (!stop) {
+        const double lam = (tmax * static_cast<double>(barg)) / static_cast<double>(kDefiniteGrid);
+        int near = 0;
+        for (int i = 1; i < k; ++i)
+          if (fabs(th[i] - lam) < fabs(th[near] - lam)) near = i;
+        th[kk] = th[near];
+        kk_s = kk + 1;
+      }
+    }
+    __syncthreads();
+    if (stop) break;
+  }
+  if (tid == 0 && kk_s % 2 == 0) {
+    th[kk_s] = tmax;
+    kk_s = kk_s + 1;
+  }
+  __syncthreads();
+  for (int i = k + tid; i < kk_s; i += blockDim.x) theta[i] = th[i];
+  if (tid == 0) kout[blockIdx.x] = kk_s;
+}
+
+// Modified Leja order of theta[0..k) (k = kin[problem] when kin is given):
+// largest |theta| first, then maximise the product of distances to the roots
+// already taken (sum of logs; a repeated root scores -inf until the end);
 // ties -> lowest index.  The logs of a step are taken in parallel, one thread
 // per candidate.  theta may alias inv: it is read into shared memory first.
-__global__ void __launch_bounds__(64)
-k_harmonic_leja(const double *theta, int k, double *roots, double *inv, float *invf, int *err, int stride) {
-  __shared__ double th[SPHYNX_MAX_POLY_DEGREE], score[SPHYNX_MAX_POLY_DEGREE];
-  __shared__ int used[SPHYNX_MAX_POLY_DEGREE];
+// roots[k .. kcap) = +inf and inv[k .. kcap] = 0: the product-form steps of
+// an infinite root change nothing, so a batch runs the largest count for all.
+__global__ void __launch_bounds__(128)
+k_harmonic_leja(const double *theta, int k0, const int *kin, int kcap, double *roots, double *inv, float *invf,
+                int *err, int stride) {
+  __shared__ double th[kRootCap], score[kRootCap];
+  __shared__ int used[kRootCap];
   __shared__ int last;
   const int tid = threadIdx.x;
   const int64_t o = static_cast<int64_t>(blockIdx.x) * stride;   // problem blockIdx.x of a batch
+  const int k = kin ? kin[blockIdx.x] : k0;
   theta += o;
   roots += o;
   inv += o;
@@ -678,8 +770,11 @@ k_harmonic_leja(const double *theta, int k, double *roots, double *inv, float *i
       inv[i] = 1.0 / roots[i];
       invf[i] = static_cast<float>(inv[i]);
     }
-    inv[k] = 0.0;   // the chain reads inv[i + 1] on its last step
-    invf[k] = 0.f;
+    for (int i = k; i < kcap; ++i) roots[i] = INFINITY;
+    for (int i = k; i <= kcap; ++i) {   // the chain reads inv[i + 1] on its last step
+      inv[i] = 0.0;
+      invf[i] = 0.f;
+    }
     *err = bad ? 2 : 0;
   }
 }
@@ -700,22 +795,28 @@ void launch_rayleigh_ritz(cudaStream_t st, const double *ga, const double *gb, i
 }
 
 void launch_harmonic_ritz(cudaStream_t st, const double *alpha, const double *beta2, int k, double *roots,
-                          double *inv, float *invf, int *err) {
+                          double *inv, float *invf, int *err, int *kout) {
   if (k < 1 || k > SPHYNX_MAX_POLY_DEGREE) fail(SPHYNX_ERR_INVALID_ARG, "polynomial degree %d", k);
+  const int kcap = k + SPHYNX_MAX_ADDED_ROOTS;
   k_harmonic_eig<<<k, 32, 0, st>>>(alpha, beta2, k, inv, err, 0);
   SPX_LAUNCHED();
-  k_harmonic_leja<<<1, 64, 0, st>>>(inv, k, roots, inv, invf, err, 0);
+  k_harmonic_definite<<<1, 256, 0, st>>>(inv, k, kout, err, 0);
+  SPX_LAUNCHED();
+  k_harmonic_leja<<<1, 128, 0, st>>>(inv, k, kout, kcap, roots, inv, invf, err, 0);
   SPX_LAUNCHED();
 }
 
 void launch_harmonic_ritz_batch(cudaStream_t st, const double *alpha, const double *beta2, int k, int count,
-                                int stride, double *roots, double *inv, float *invf, int *err) {
-  if (k < 1 || k > SPHYNX_MAX_POLY_DEGREE || stride < k + 1 || count < 1)
+                                int stride, double *roots, double *inv, float *invf, int *err, int *kout) {
+  const int kcap = k + SPHYNX_MAX_ADDED_ROOTS;
+  if (k < 1 || k > SPHYNX_MAX_POLY_DEGREE || stride < kcap + 1 || count < 1)
     fail(SPHYNX_ERR_INVALID_ARG, "polynomial degree %d, stride %d, count %d", k, stride, count);
   if (count > 65535) fail(SPHYNX_ERR_UNSUPPORTED, "more than 65535 polynomial setups in one launch");
   k_harmonic_eig<<<dim3(k, count), 32, 0, st>>>(alpha, beta2, k, inv, err, stride);
   SPX_LAUNCHED();
-  k_harmonic_leja<<<count, 64, 0, st>>>(inv, k, roots, inv, invf, err, stride);
+  k_harmonic_definite<<<count, 256, 0, st>>>(inv, k, kout, err, stride);
+  SPX_LAUNCHED();
+  k_harmonic_leja<<<count, 128, 0, st>>>(inv, k, kout, kcap, roots, inv, invf, err, stride);
   SPX_LAUNCHED();
 }
 

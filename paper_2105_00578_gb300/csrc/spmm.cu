@@ -7,6 +7,31 @@ namespace sphynx {
 
 namespace {
 
+// z = D^{-1/2} x for the normalized product's gathers: rows of bp values
+// (bp a multiple of 4, or 1), one 16-byte quarter-row (float) or 16-byte pair
+// (double) a thread
+template <typename T, int V>
+__global__ void k_prescale(const T *__restrict__ x, const T *__restrict__ dinv, int64_t n, int bp, T *__restrict__ z) {
+  const int per_row = bp / V;   // vectors a row
+  const int64_t total = n * per_row;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t row = k / per_row;
+    const T s = __ldg(dinv + row);
+    if constexpr (V == 4) {
+      float4 v = __ldg(reinterpret_cast<const float4 *>(x) + k);
+      v.x *= s; v.y *= s; v.z *= s; v.w *= s;
+      reinterpret_cast<float4 *>(z)[k] = v;
+    } else if constexpr (V == 2) {
+      double2 v = __ldg(reinterpret_cast<const double2 *>(x) + k);
+      v.x *= s; v.y *= s;
+      reinterpret_cast<double2 *>(z)[k] = v;
+    } else {
+      z[k] = s * x[k];
+    }
+  }
+}
+
 void dispatch(sphynx_graph *g, const SpmmArgs &a, const SpmmDev &d) {
   switch (a.tin) {
     case DT::F64: spmm_dispatch_f64(g, a, d); break;
@@ -141,7 +166,8 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: polynomial step adds 0, 1 or 2 terms (2 on the first step)");
   SpmmDev d{a.x,   a.ld_x, a.ld_y, a.y,      a.t_out,    a.yacc,        a.first,  a.yterms,
             a.inv, a.invf, a.i_cur, a.done, a.row_graph, a.inv_stride, a.gdone, a.gdone_stride,
-            a.act_blocks, a.n_act};
+            a.act_blocks, a.n_act, nullptr};
+  const bool prescaled = g->plan.prescale && a.lap == SPHYNX_NORMALIZED && a.tin != DT::BF16 && g->n > 0;
 
   // schedule: forced, or the one the autotuner chose for this graph at create
   g->plan.variant = g->plan.forced >= 0 ? g->plan.forced : g->plan.tuned_variant;
@@ -161,6 +187,7 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
                                              : 8.0 * (n + 1) + g->plan.short_entries * (g->weighted ? 8.0 : 4.0)) +
       g->plan.med_bytes + g->plan.long_bytes;
   double bytes = graph_bytes + n * b * si + n * sa;
+  if (prescaled) bytes += 3.0 * n * b * si;   // the pass reads X and writes Z; the epilogue reads X again
   if (a.mode == 0) {
     bytes += n * b * sa;
   } else {
@@ -186,6 +213,33 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
     e0 = g->ctr.ev_pool[g->ctr.ev_used++];
     e1 = g->ctr.ev_pool[g->ctr.ev_used++];
     SPX_CUDA(cudaEventRecord(e0, g->stream));
+  }
+  if (prescaled) {
+    // sized for double rows of the widest block, so that a graph captured
+    // around this product never sees the buffer move
+    void *z = g->workspace("spmm_prescaled", static_cast<size_t>(g->n) * 16 * 8 + 256, false);
+    const bool vec = a.bp % 4 == 0;   // rows of 4, 8, 12 or 16 values, 16-byte aligned
+    const int64_t total = g->n * (vec ? a.bp / (a.tin == DT::F64 ? 2 : 4) : a.bp);
+    const unsigned grid = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 16 * kSmCount));
+    if (a.tin == DT::F64) {
+      if (vec)
+        k_prescale<double, 2><<<grid, 256, 0, g->stream>>>(static_cast<const double *>(a.x), g->dinv.as<double>(),
+                                                            g->n, a.bp, static_cast<double *>(z));
+      else
+        k_prescale<double, 1><<<grid, 256, 0, g->stream>>>(static_cast<const double *>(a.x), g->dinv.as<double>(),
+                                                            g->n, a.bp, static_cast<double *>(z));
+    } else {
+      if (vec)
+        k_prescale<float, 4><<<grid, 256, 0, g->stream>>>(static_cast<const float *>(a.x), g->dinvf.as<float>(), g->n,
+                                                           a.bp, static_cast<float *>(z));
+      else
+        k_prescale<float, 1><<<grid, 256, 0, g->stream>>>(static_cast<const float *>(a.x), g->dinvf.as<float>(), g->n,
+                                                           a.bp, static_cast<float *>(z));
+    }
+    SPX_LAUNCHED();
+    g->ctr.launches++;
+    d.xe = a.x;
+    d.x = z;
   }
   dispatch(g, a, d);
   if (g->ctr.timing) SPX_CUDA(cudaEventRecord(e1, g->stream));

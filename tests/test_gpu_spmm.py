@@ -159,16 +159,15 @@ def test_sell_slice_formats_follow_the_offset_range():
             info = spx.sphynx_get_info(h)
             assert info["sell_slices"] == wide.size
             assert info["sell_narrow_slices"] == int((~wide).sum()), name
-            # medium rows (33 to the tuned ceiling): their entries, row id and
-            # degree per lane slot of 32-row slices, one offset per slice; long
-            # rows: CSR entries, 32 bytes per 4096-entry item and 24 per row
+            # medium rows (33 to the tuned ceiling): their entries, 20 bytes a
+            # row (id and row pointers), 8 per warp unit; long rows: CSR
+            # entries, 32 bytes per 1024-entry item and 24 per row
             mm = info["spmm_med_max"]
             assert mm in (32, 128, 4096)
             med = (deg > 32) & (deg <= mm)
-            n_ms = (int(med.sum()) + 31) // 32
-            med_bytes = 4.0 * deg[med].sum() + n_ms * (32 * 8 + 8)
+            med_bytes = 4.0 * deg[med].sum() + 20.0 * int(med.sum()) + 8.0 * medium_units(deg[med])
             lng = deg > mm
-            long_bytes = 4.0 * deg[lng].sum() + 32 * int(np.sum((deg[lng] + 4095) // 4096)) + 24 * int(lng.sum())
+            long_bytes = 4.0 * deg[lng].sum() + 32 * int(np.sum((deg[lng] + 1023) // 1024)) + 24 * int(lng.sum())
             short_per_slice = np.bincount(r[short_entry] >> 5, minlength=wide.size)
             pat = pattern_slices(g)
             assert info["sell_pattern_slices"] == int(pat.sum()), name
@@ -185,6 +184,19 @@ def test_sell_slice_formats_follow_the_offset_range():
             assert info["spmm_graph_bytes"] == pytest.approx(expect, rel=1e-12), name
         finally:
             spx.sphynx_destroy(h)
+
+
+def medium_units(degs: np.ndarray) -> int:
+    """Warp units of the medium-row kernel: rows by degree, descending; a row
+    of d entries takes G = 2^lg lanes, the smallest with d <= 16 G (G <= 32),
+    and consecutive rows of one G share a unit up to 32 / G rows."""
+    lg = np.zeros(len(degs), dtype=np.int64)
+    for k in range(5):
+        lg += (16 << k) < degs
+    units = 0
+    for v in np.unique(lg):
+        units += -(-int(np.sum(lg == v)) // (32 >> int(v)))
+    return units
 
 
 @pytest.mark.parametrize("lap", ["normalized", "combinatorial"])
