@@ -520,6 +520,7 @@ def run_batch(args, world, rank, local):
             "graphs_noconv": int(np.sum(status != 0)),
             "noconv_graph_sizes": sorted((int(graphs[q].n) for q in np.flatnonzero(status != 0)), reverse=True)[:20],
             "ms_float_phase": float(st["ms_phase"][0]), "ms_fp64_phase": float(st["ms_phase"][1]),
+            "loop_iterations": [int(v) for v in st["loop_iters"]],
             "vs_oracle": batch_vs_oracle(w, eigs, cuts, status),
             "stall_window": w.get("stall_window", 0), "max_iter": w.get("max_iter", 1000),
             "max_iterations": int(iters.max()),

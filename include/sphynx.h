@@ -170,7 +170,8 @@ typedef struct {
   double ms_phase[2];    /* sphynx_partition_batch: wall time of the eigensolve in
                             the requested precision and of the FP64 finishing
                             (0 when no graph was promoted)                      */
-  double reserved[1];
+  int32_t loop_iters[2]; /* sphynx_partition_batch: LOBPCG iterations each phase's
+                            captured loop ran (the most any graph of it took)   */
 } sphynx_stats;
 
 typedef struct {

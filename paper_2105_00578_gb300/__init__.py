@@ -56,7 +56,7 @@ class Stats(C.Structure):
                 ("imbalance", C.c_double),
                 ("ms_spmm_by_dt", C.c_double * 3), ("spmm_bytes_by_dt", C.c_double * 3),
                 ("spmm_launches_by_dt", C.c_int64 * 3), ("fp64_finished", C.c_int32), ("refine_moves", C.c_int32),
-                ("ms_phase", C.c_double * 2), ("reserved", C.c_double * 1)]
+                ("ms_phase", C.c_double * 2), ("loop_iters", C.c_int32 * 2)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_
@@ -64,6 +64,7 @@ class Stats(C.Structure):
         d["eigenvalues"] = list(self.eigenvalues[: self.nev])
         d["resnorm"] = list(self.resnorm[: self.nev])
         d["ms_phase"] = list(self.ms_phase)
+        d["loop_iters"] = list(self.loop_iters)
         return d
 
 

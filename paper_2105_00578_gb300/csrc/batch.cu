@@ -1286,6 +1286,8 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   auto tp = std::chrono::steady_clock::now();
   Blocks k1 = run_phase(dt0, ct0, dt0, "", false, window1, promote ? 1 : 0);
   double ms_phase[2] = {std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp).count(), 0.0};
+  int loop_bodies[2] = {0, 0};   // each captured body runs two iterations
+  SPX_CUDA(cudaMemcpyAsync(&loop_bodies[0], ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   std::vector<SolverState> hs = read_states();
   std::vector<int> zero_it(count, 0);
   std::vector<char> all(count, 1);
@@ -1318,6 +1320,8 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     tp = std::chrono::steady_clock::now();
     Blocks k2 = run_phase(DT::F64, ct0, DT::F32, "_64", true, o->stall_window, 0);
     ms_phase[1] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp).count();
+    SPX_CUDA(cudaMemcpyAsync(&loop_bodies[1], ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SPX_CUDA(cudaStreamSynchronize(st));
     hs = read_states();
     gather_x0(k2, DT::F64, hs, it1, promoted);
     dt = DT::F64;
@@ -1400,6 +1404,8 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     stats->fp64_finished = n_promoted;
     stats->ms_phase[0] = ms_phase[0];
     stats->ms_phase[1] = ms_phase[1];
+    stats->loop_iters[0] = 2 * loop_bodies[0];
+    stats->loop_iters[1] = 2 * loop_bodies[1];
     stats->iterations = maxit;
     stats->nev = b;
   }
