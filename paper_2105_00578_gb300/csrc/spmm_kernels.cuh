@@ -256,43 +256,15 @@ __device__ __forceinline__ unsigned long long bf2_to_f2(unsigned w) {
   return pk2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
-// L2 eviction hint for gathers (HINT = true): rows of X are kept in L2 ahead
-// of the streamed index arrays (read with evict-first loads).  On a power-law
-// graph X (115 MB for R-MAT scale 22 at 12 floats a row) barely fits L2, and
-// without the hint the index stream evicts it: its rows came back from DRAM
-// about eight times a product.
-__device__ __forceinline__ unsigned long long l2_keep_policy() {
-  unsigned long long pol;
-  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-__device__ __forceinline__ float4 ld_keep(const float4 *p, unsigned long long pol) {
-  float4 v;
-  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ double2 ld_keep(const double2 *p, unsigned long long pol) {
-  double2 v;
-  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
-  return v;
-}
-
 // The raw bits of one gathered row of X (loaded first, converted later, so
 // that a batch of gathers is in flight at once).
 template <typename TI, int BP> struct RawRow;
 template <int BP> struct RawRow<float, BP> {
   static constexpr int N = BP == 1 ? 1 : BP / 4;
   float4 q[N];
-  template <bool HINT = false>
   __device__ __forceinline__ void load(const float *__restrict__ p) {
     if constexpr (BP == 1) {
       q[0].x = __ldg(p);
-    } else if constexpr (HINT) {
-      const unsigned long long pol = l2_keep_policy();
-#pragma unroll
-      for (int k = 0; k < N; ++k) q[k] = ld_keep(reinterpret_cast<const float4 *>(p + 4 * k), pol);
     } else {
 #pragma unroll
       for (int k = 0; k < N; ++k) q[k] = __ldg(reinterpret_cast<const float4 *>(p + 4 * k));
@@ -309,7 +281,6 @@ template <int BP> struct RawRow<__nv_bfloat16, BP> {
   static constexpr int N = kWide ? BP / 8 : BP / 4;
   uint4 q[kWide ? N : 1];
   uint2 h[kWide ? 1 : N];
-  template <bool HINT = false>   // bfloat16 rows take no hint
   __device__ __forceinline__ void load(const __nv_bfloat16 *__restrict__ p) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -327,20 +298,7 @@ template <int BP> struct RawRow<__nv_bfloat16, BP> {
 };
 template <int BP> struct RawRow<double, BP> {
   double v[BP];
-  template <bool HINT = false>
-  __device__ __forceinline__ void load(const double *__restrict__ p) {
-    if constexpr (HINT && BP % 2 == 0) {
-      const unsigned long long pol = l2_keep_policy();
-#pragma unroll
-      for (int c = 0; c < BP; c += 2) {
-        const double2 t = ld_keep(reinterpret_cast<const double2 *>(p + c), pol);
-        v[c] = t.x;
-        v[c + 1] = t.y;
-      }
-    } else {
-      load_row<BP>(p, v);
-    }
-  }
+  __device__ __forceinline__ void load(const double *__restrict__ p) { load_row<BP>(p, v); }
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int c = 0; c < BP; ++c) v[c] = 0.0;
@@ -585,7 +543,7 @@ __device__ __forceinline__ void spmm_accumulate(const LapView &L, const TI *__re
 
 // N consecutive entries t0 .. t0 + N - 1 of a row: N column indices, then N
 // gathers in flight together, then N accumulations in entry order.
-template <int N, int LAP, typename TI, int BP, bool W, bool HINT = false, class ColAt, class WAt>
+template <int N, int LAP, typename TI, int BP, bool W, class ColAt, class WAt>
 __device__ __forceinline__ void spmm_batch(const LapView &L, const TI *__restrict__ x, int t0, ColAt col_at,
                                            WAt w_at, RowAcc<TI, BP> &acc) {
   using TA = typename AccOf<TI>::T;
@@ -594,7 +552,7 @@ __device__ __forceinline__ void spmm_batch(const LapView &L, const TI *__restric
   for (int u = 0; u < N; ++u) jj[u] = col_at(t0 + u);
   RawRow<TI, BP> rr[N];
 #pragma unroll
-  for (int u = 0; u < N; ++u) rr[u].template load<HINT>(x + static_cast<int64_t>(jj[u]) * BP);
+  for (int u = 0; u < N; ++u) rr[u].load(x + static_cast<int64_t>(jj[u]) * BP);
 #pragma unroll
   for (int u = 0; u < N; ++u) {
     if constexpr (LAP == SPHYNX_NORMALIZED || W) {
@@ -611,21 +569,21 @@ __device__ __forceinline__ void spmm_batch(const LapView &L, const TI *__restric
 
 // The last rem <= R entries of a row as one batch of exactly rem (selected
 // among 1 .. R at run time), so that no gather slot is padded with zeros.
-template <int R, int LAP, typename TI, int BP, bool W, bool HINT = false, class ColAt, class WAt>
+template <int R, int LAP, typename TI, int BP, bool W, class ColAt, class WAt>
 __device__ __forceinline__ void spmm_tail(const LapView &L, const TI *__restrict__ x, int t0, int rem,
                                           ColAt col_at, WAt w_at, RowAcc<TI, BP> &acc) {
   if constexpr (R > 0) {
     if (rem == R) {
-      spmm_batch<R, LAP, TI, BP, W, HINT>(L, x, t0, col_at, w_at, acc);
+      spmm_batch<R, LAP, TI, BP, W>(L, x, t0, col_at, w_at, acc);
       return;
     }
-    spmm_tail<R - 1, LAP, TI, BP, W, HINT>(L, x, t0, rem, col_at, w_at, acc);
+    spmm_tail<R - 1, LAP, TI, BP, W>(L, x, t0, rem, col_at, w_at, acc);
   }
 }
 
 // One row's d entries in batches of U (see spmm_batch); col_at(t) / w_at(t)
 // read entry t < d.
-template <int LAP, typename TI, int BP, bool W, bool HINT = false, class ColAt, class WAt>
+template <int LAP, typename TI, int BP, bool W, class ColAt, class WAt>
 __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict__ x, int d,
                                          ColAt col_at, WAt w_at, RowAcc<TI, BP> &acc) {
   using TA = typename AccOf<TI>::T;
@@ -634,14 +592,14 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
     // narrow rows (16 bytes or less): plain batches keep the register count,
     // hence the number of resident warps, high
     int t0 = 0;
-    for (; t0 + U <= d; t0 += U) spmm_batch<U, LAP, TI, BP, W, HINT>(L, x, t0, col_at, w_at, acc);
+    for (; t0 + U <= d; t0 += U) spmm_batch<U, LAP, TI, BP, W>(L, x, t0, col_at, w_at, acc);
     // the remainder (< U entries): a batch of 4 if at least 4 are left, then
     // one batch of exactly what is left
     if (d - t0 >= 4) {
-      spmm_batch<4, LAP, TI, BP, W, HINT>(L, x, t0, col_at, w_at, acc);
+      spmm_batch<4, LAP, TI, BP, W>(L, x, t0, col_at, w_at, acc);
       t0 += 4;
     }
-    spmm_tail<3, LAP, TI, BP, W, HINT>(L, x, t0, d - t0, col_at, w_at, acc);
+    spmm_tail<3, LAP, TI, BP, W>(L, x, t0, d - t0, col_at, w_at, acc);
     return;
   }
   // wide rows: software pipeline -- the next batch's column indices (and
@@ -670,7 +628,7 @@ __device__ __forceinline__ void spmm_row(const LapView &L, const TI *__restrict_
     RawRow<TI, BP> rr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (jj[u] >= 0) rr[u].template load<HINT>(x + static_cast<int64_t>(jj[u]) * BP);
+      if (jj[u] >= 0) rr[u].load(x + static_cast<int64_t>(jj[u]) * BP);
       else rr[u].zero();
     }
 #pragma unroll
@@ -979,7 +937,7 @@ k_spmm_group(const LapView L, const SpmmDev a, const int32_t *__restrict__ grow,
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> acc;
   acc.zero();
-  spmm_row<LAP, TI, BP, W, true>(
+  spmm_row<LAP, TI, BP, W>(
       L, x, nl, [&](int t) { return __ldcs(cp + (static_cast<int64_t>(t) << lg)); },
       [&](int t) { return __ldcs(wp + (static_cast<int64_t>(t) << lg)); }, acc);
   TA sum[BP];
@@ -1011,7 +969,7 @@ k_spmm_long(const LapView L, const SpmmDev a, const int64_t *__restrict__ items,
   const int nl = e - b > lane ? static_cast<int>((e - b - lane - 1) / 32) + 1 : 0;
   const int32_t *cp = L.col + b + lane;
   const float *wp = W ? L.w + b + lane : nullptr;
-  spmm_row<LAP, TI, BP, W, true>(
+  spmm_row<LAP, TI, BP, W>(
       L, x, nl, [&](int t) { return __ldcs(cp + 32 * static_cast<int64_t>(t)); },
       [&](int t) { return __ldcs(wp + 32 * static_cast<int64_t>(t)); }, racc);
   TA acc[BP];
