@@ -435,6 +435,51 @@ def batch_vs_oracle(w, eigs, cuts, status):
             "graphs": out}
 
 
+def batch_chain_roofline(spx, h, w, big, stream, precision):
+    """The batch's dominant kernel, the polynomial chain step over every
+    graph's rows (the captured loop cannot hold per-launch events): 20 steps
+    of sphynx_poly_step on the batch handle with the partition's block width
+    and chain type, alternating the steps that add to y with those that do
+    not, timed with CUDA events on the handle's stream."""
+    import torch
+    d = int(np.floor(np.log2(w["K"]))) + 1
+    bp = (d + 3) // 4 * 4
+    f64 = precision == "fp64"
+    dt, tdt, s = (spx.DT_F64, torch.float64, 8) if f64 else (spx.DT_F32, torch.float32, 4)
+    gen = torch.Generator(device="cuda").manual_seed(w["seed"])
+    t = torch.randn(big.n, bp, dtype=tdt, device="cuda", generator=gen)
+    tout = torch.empty_like(t)
+    y = torch.zeros_like(t)
+    lap = w["laplacian"]
+
+    def chain_step(i):
+        src, dst = (t, tout) if i % 2 == 0 else (tout, t)
+        spx.sphynx_poly_step(h, lap, dt, src, dt, dst, y, bp, d, 2.0 + i, 3.0 + i, 2 if i % 2 == 0 else 0, 0)
+
+    for i in range(4):
+        chain_step(i)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(20):
+        chain_step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1000.0 / 20
+    sb = survey_bytes(big.n, big.nnz, d, s, s, s, False)
+    pk = peaks()
+    return {"bound": "hbm", "achieved": sb / us / 1e3, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": sb / us / 1e3 / pk["hbm_gbs"], "frac_survey": sb / us / 1e3 / pk["hbm_gbs"],
+            "peak_source": f"{pk['src']} (MEASURED_PEAKS.json copy bandwidth)" if pk["src"] == "measured" else pk["src"],
+            "kernel": "polynomial chain step over the whole batch (sphynx_poly_step, %s)" % ("f64" if f64 else "f32"),
+            "us_per_launch": us, "algorithmic_bytes_per_launch": sb,
+            "algorithmic_bytes_formula": "8(n+1) + nnz(4+s_w) + n b (s_in+s_out) + n s_diag with n=%d, nnz=%d, b=%d, "
+                                         "s_in=s_out=%d, s_w=0, s_diag=%d" % (big.n, big.nnz, d, s, s),
+            "traffic": None, "traffic_source": None,
+            "note": "rows in the generator's order: a geometric graph's neighbours have unrelated ids, so every "
+                    "gather of a 16-byte row is its own 32-byte DRAM sector"}
+
+
 def run_batch(args, world, rank, local):
     """The batch workload: all graphs partitioned by one sphynx_partition_batch
     call per step (replicas on N > 1 GPUs)."""
@@ -484,6 +529,7 @@ def run_batch(args, world, rank, local):
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     value = job_throughput(count, ms, world)
     code, cuts, imbs, eigs, iters, status, st = res[-1]
+    roof = batch_chain_roofline(spx, h, w, big, stream, precision)
 
     # end to end: create from pinned host CSR, partition, read the part ids back
     rp = torch.from_numpy(big.row_ptr).pin_memory()
@@ -526,7 +572,7 @@ def run_batch(args, world, rank, local):
             "max_iterations": int(iters.max()),
             "median_iterations": float(np.median(iters)), "mean_cut": float(np.mean(cuts)),
             "max_imbalance": float(np.max(imbs)),
-            "roofline": None,
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": world * count / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(big.row_ptr.nbytes + big.col.nbytes),

@@ -31,7 +31,10 @@ namespace sphynx {
 
 namespace {
 
-constexpr int kBatchChunk = 1024;   // rows per chunk
+// rows per chunk: large enough that a CTA's reduction and its partial
+// outputs are paid for by many rows (with 1024-row chunks, the 2000-graph
+// batch's 75,000 chunks made each reduction kernel launch-overhead-bound)
+constexpr int kBatchChunk = 16384;
 constexpr int kGramRows = 64;       // rows staged per step of the batched Gram kernel
 constexpr int kGramThreads = 256;
 // iterations without a 10 % residual gain (at the float rounding floor) after
@@ -506,8 +509,8 @@ unsigned iter_grid(const sphynx_graph *g) {
 // The single-graph setup restated per graph: k Lanczos steps on each graph's
 // own L with two classical Gram-Schmidt passes against its basis (its
 // normalised null vector in column 0), then its harmonic Ritz values in
-// modified Leja order.  Dots reduce per 1024-row chunk, then per graph over
-// its chunks in chunk order.  The basis is column-major over all rows.
+// modified Leja order.  Dots reduce per chunk, then per graph over its
+// chunks in chunk order.  The basis is column-major over all rows.
 
 // the start vector: graph q's rows draw the single-graph stream at their local index
 template <typename T>
