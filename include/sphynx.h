@@ -454,8 +454,14 @@ int sphynx_refine(sphynx_handle g, int32_t *part, int32_t K, double eps, int32_t
  * every edge of a graph stays inside that range (checked: INVALID_ARG).
  * graph_ptr: host int64[count + 1], graph_ptr[0] = 0, graph_ptr[count] = n,
  * every graph non-empty.  The other arguments, ownership and errors are
- * those of sphynx_create; the handle also serves the single-step calls,
- * which see the block-diagonal graph. */
+ * those of sphynx_create.  With host arrays (SPHYNX_HOST_PTRS) the handle
+ * stores every graph's vertices in reverse Cuthill-McKee order (computed on
+ * the host's cores, within each graph), so that a row's neighbours lie near
+ * it and the products' gathers share cache lines; sphynx_partition_batch
+ * takes and returns everything in the caller's numbering, and draws the
+ * same random numbers per vertex as an unordered batch.  With device arrays
+ * the caller's order is kept.  The handle also serves the single-step
+ * calls, which see the block-diagonal graph in the handle's row order. */
 int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, const float *edge_w,
                         const int64_t *vtx_w, const int64_t *graph_ptr, int32_t count, int64_t n,
                         int64_t nnz, uint32_t flags, void *stream, sphynx_handle *out);

@@ -22,9 +22,11 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 namespace sphynx {
@@ -63,17 +65,39 @@ __device__ __forceinline__ int cv_chunk(const ChunkView &cv, int i) { return cv.
 __device__ __forceinline__ bool chunk_done(const SolverState *st, int q) { return st[q].done != 0; }
 
 // ---- initial block: the single-graph random block of every graph (local rows) ----
+// (orig: the caller's vertex of each row when the batch is reordered, so that
+// a vertex draws the same numbers in any row)
 template <typename T>
-__global__ void k_brandom(T *x, ChunkView cv, const int64_t *gptr, int b, int ld, uint64_t state) {
+__global__ void k_brandom(T *x, ChunkView cv, const int64_t *gptr, const int32_t *orig, int b, int ld,
+                          uint64_t state) {
   const int c = blockIdx.x, q = cv.graph[c];
   const int64_t r0 = cv.begin[c], r1 = cv.begin[c + 1], base = gptr[q];
   for (int64_t e = r0 * ld + threadIdx.x; e < r1 * ld; e += blockDim.x) {
     const int64_t i = e / ld;
     const int j = static_cast<int>(e - i * ld);
+    const int64_t v_id = orig ? static_cast<int64_t>(orig[i]) : i;
     double v = 0.0;
-    if (j < b) v = splitmix_pm1(state, static_cast<uint64_t>((i - base) * b + j + 1));
+    if (j < b) v = splitmix_pm1(state, static_cast<uint64_t>((v_id - base) * b + j + 1));
     x[e] = static_cast<T>(v);
   }
+}
+
+// rows back to the caller's order: y[orig[r]] = x[r] (rows of ld values)
+template <typename T>
+__global__ void k_bto_caller(const int32_t *orig, const T *x, int64_t n, int ld, T *y) {
+  const int64_t total = n * ld;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / ld;
+    y[static_cast<int64_t>(orig[r]) * ld + (e - r * ld)] = x[e];
+  }
+}
+
+// part ids in row order from the caller-order ones: p_row[r] = p_caller[orig[r]]
+__global__ void k_bparts_to_rows(const int32_t *orig, const int32_t *p_caller, int64_t n, int32_t *p_row) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    p_row[r] = p_caller[orig[r]];
 }
 
 // ---- Gram matrices per chunk -------------------------------------------------
@@ -514,11 +538,13 @@ unsigned iter_grid(const sphynx_graph *g) {
 
 // the start vector: graph q's rows draw the single-graph stream at their local index
 template <typename T>
-__global__ void k_bz_start(ChunkView cv, const int64_t *gptr, T *v, uint64_t state) {
+__global__ void k_bz_start(ChunkView cv, const int64_t *gptr, const int32_t *orig, T *v, uint64_t state) {
   const int c = blockIdx.x, q = cv.graph[c];
   const int64_t base = gptr[q];
-  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x)
-    v[i] = static_cast<T>(splitmix_pm1(state, static_cast<uint64_t>(i - base + 1)));
+  for (int64_t i = cv.begin[c] + threadIdx.x; i < cv.begin[c + 1]; i += blockDim.x) {
+    const int64_t v_id = orig ? static_cast<int64_t>(orig[i]) : i;
+    v[i] = static_cast<T>(splitmix_pm1(state, static_cast<uint64_t>(v_id - base + 1)));
+  }
 }
 
 __device__ __forceinline__ double null_entry(int lap, const double *deg, int64_t i) {
@@ -694,7 +720,7 @@ void batch_poly_setup_t(sphynx_graph *g, int k, int lap, uint64_t seed) {
   int *err = static_cast<int *>(g->workspace("bz_err", static_cast<size_t>(count) * 2 * sizeof(int), true));
   int *kout = err + count;
   // start vector, null column, projection, normalisation
-  k_bz_start<T><<<cg, 256, 0, st>>>(cv, B.gptr.as<int64_t>(), v, mix64(seed + 3 * kGamma));
+  k_bz_start<T><<<cg, 256, 0, st>>>(cv, B.gptr.as<int64_t>(), B.orig.as<int32_t>(), v, mix64(seed + 3 * kGamma));
   SPX_LAUNCHED();
   k_bz_null_dots<T><<<cg, 256, 0, st>>>(cv, v, lap, deg, part);
   SPX_LAUNCHED();
@@ -1138,8 +1164,6 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
         a.i_cur = i;
         a.row_graph = B.row_graph.as<int32_t>();
         a.inv_stride = kk + 1;
-        a.gdone = &states->done;   // finished graphs' rows are skipped
-        a.gdone_stride = static_cast<int>(sizeof(SolverState) / sizeof(int));
         a.act_blocks = B.act_blocks.as<int32_t>();
         a.n_act = B.n_act.as<int>();
         spmm(g, a);
@@ -1162,8 +1186,6 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
       a.y = y;
       a.mode = 0;
       a.row_graph = B.row_graph.as<int32_t>();
-      a.gdone = &states->done;   // finished graphs' rows are skipped
-      a.gdone_stride = static_cast<int>(sizeof(SolverState) / sizeof(int));
       a.act_blocks = B.act_blocks.as<int32_t>();
       a.n_act = B.n_act.as<int>();
       spmm(g, a);
@@ -1174,11 +1196,11 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
     // first Rayleigh-Ritz and residual
     if (!warm) {
       if (dt == DT::F64)
-        k_brandom<double><<<cgrid, 256, 0, st>>>(static_cast<double *>(X[0]), view_of(g), B.gptr.as<int64_t>(), b,
-                                                 ld, mix64(o->seed + kGamma));
+        k_brandom<double><<<cgrid, 256, 0, st>>>(static_cast<double *>(X[0]), view_of(g), B.gptr.as<int64_t>(),
+                                                 B.orig.as<int32_t>(), b, ld, mix64(o->seed + kGamma));
       else
-        k_brandom<float><<<cgrid, 256, 0, st>>>(static_cast<float *>(X[0]), view_of(g), B.gptr.as<int64_t>(), b, ld,
-                                                mix64(o->seed + kGamma));
+        k_brandom<float><<<cgrid, 256, 0, st>>>(static_cast<float *>(X[0]), view_of(g), B.gptr.as<int64_t>(),
+                                                B.orig.as<int32_t>(), b, ld, mix64(o->seed + kGamma));
       SPX_LAUNCHED();
     }
     spmm_block(X[0], LX[0]);
@@ -1335,6 +1357,20 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   B.act_blocks.release();   // the lists serve the iteration loops only
   B.act_chunks.release();
   B.n_act.release();
+  // a reordered batch: the Ritz vectors back to the caller's order, where the
+  // embedding and multi-jagged run exactly as on the caller's numbering (their
+  // ties go to the lowest vertex id)
+  const int32_t *orig = B.orig.as<int32_t>();
+  if (orig) {
+    void *EXc = g->workspace("EX_caller", static_cast<size_t>(n) * ld * es, false);
+    const unsigned gr = static_cast<unsigned>(std::min<int64_t>((n * ld + 255) / 256, 16 * kSmCount));
+    if (dt == DT::F64)
+      k_bto_caller<double><<<gr, 256, 0, st>>>(orig, static_cast<const double *>(EX), n, ld, static_cast<double *>(EXc));
+    else
+      k_bto_caller<float><<<gr, 256, 0, st>>>(orig, static_cast<const float *>(EX), n, ld, static_cast<float *>(EXc));
+    SPX_LAUNCHED();
+    EX = EXc;
+  }
 
   for (int q = 0; q < count; ++q) {
     const int64_t r0 = B.h_gptr[q], rows = B.h_gptr[q + 1] - r0;
@@ -1361,7 +1397,8 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   // multi-jagged over all graphs at once: graph q owns parts [q K, (q + 1) K)
   const int ktot = count * K;
   void *mjs = g->workspace("mj", mj_scratch_bytes(n, ktot, count), false);
-  run_mj_scratch(st, dt, coords, d - 1, d - 1, n, g->vw, ktot, dpart, &g->ctr, mjs, B.h_gptr.data(), count);
+  const int64_t *vw_caller = orig && B.vw_orig.p ? B.vw_orig.as<int64_t>() : g->vw;
+  run_mj_scratch(st, dt, coords, d - 1, d - 1, n, vw_caller, ktot, dpart, &g->ctr, mjs, B.h_gptr.data(), count);
   // metrics per graph
   if (g->weighted && !g->wexact)
     fail(SPHYNX_ERR_UNSUPPORTED, "edge weights span too many binary orders for an exact cut");
@@ -1371,7 +1408,14 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
   unsigned *dbad = reinterpret_cast<unsigned *>(ws);
   unsigned long long *dcut = reinterpret_cast<unsigned long long *>(ws + 64);
   long long *dpw = reinterpret_cast<long long *>(ws + 64 + static_cast<size_t>(count) * 8);
-  k_beval<<<cgrid, 256, 0, st>>>(view_of(g), g->rowptr, g->col, g->w, g->vw, dpart, K, g->wscale, dcut, dpw, dbad);
+  int32_t *prow = dpart;   // the part of every row, in the handle's row order
+  if (orig) {
+    prow = static_cast<int32_t *>(g->workspace("bparts_rows", static_cast<size_t>(n) * sizeof(int32_t), false));
+    k_bparts_to_rows<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 16 * kSmCount)), 256, 0, st>>>(
+        orig, dpart, n, prow);
+    SPX_LAUNCHED();
+  }
+  k_beval<<<cgrid, 256, 0, st>>>(view_of(g), g->rowptr, g->col, g->w, g->vw, prow, K, g->wscale, dcut, dpw, dbad);
   SPX_LAUNCHED();
   k_blocal<<<cgrid, 256, 0, st>>>(view_of(g), dpart, K);
   SPX_LAUNCHED();
@@ -1416,6 +1460,152 @@ void batch_partition(sphynx_graph *g, int K, const sphynx_options *o, int32_t *d
 
 }  // namespace sphynx
 
+namespace sphynx {
+void batch_parts_to_rows(sphynx_graph *g, const int32_t *p_caller, int32_t *p_rows) {
+  const int64_t n = g->n;
+  k_bparts_to_rows<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 16 * kSmCount)), 256, 0, g->stream>>>(
+      g->batch.orig.as<int32_t>(), p_caller, n, p_rows);
+  SPX_LAUNCHED();
+}
+}  // namespace sphynx
+
+namespace sphynx {
+namespace {
+
+// Run f(q) for q in [0, count) on the host's cores, graphs handed out in order.
+template <class F>
+void for_each_graph(int count, F f) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = static_cast<int>(std::min<unsigned>(hw, static_cast<unsigned>(count)));
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int q = next++; q < count; q = next++) f(q);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto &t : pool) t.join();
+}
+
+// Reverse Cuthill-McKee order of the vertices [g0, g1) of one graph, into
+// order[g0 .. g1): a breadth-first order from a pseudo-peripheral vertex
+// (the minimum-degree vertex of the last level of a search, twice, from the
+// component's lowest vertex), neighbours taken by increasing degree (lowest
+// id on ties), every component in turn, then reversed.
+// Edges that leave the range are ignored here (create rejects them later).
+void rcm_graph(const int64_t *rp, const int32_t *col, int64_t g0, int64_t g1, std::vector<char> &seen,
+               int32_t *order) {
+  const int64_t nl = g1 - g0;
+  auto deg = [&](int64_t v) { return rp[v + 1] - rp[v]; };
+  std::vector<int32_t> queue;
+  queue.reserve(static_cast<size_t>(nl));
+  std::vector<std::pair<int64_t, int32_t>> nb;
+  // breadth-first levels from s over unvisited vertices, marking with `mark`; returns the last level's start
+  auto bfs_last = [&](int32_t s, char mark) {
+    queue.clear();
+    queue.push_back(s);
+    seen[s] = mark;
+    size_t head = 0, level = 0;
+    while (head < queue.size()) {
+      level = head;
+      const size_t end = queue.size();
+      for (; head < end; ++head) {
+        const int32_t v = queue[head];
+        for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+          const int32_t u = col[k];
+          if (u < g0 || u >= g1 || seen[u] == mark || seen[u] == 2) continue;
+          seen[u] = mark;
+          queue.push_back(u);
+        }
+      }
+    }
+    return level;
+  };
+  int64_t placed = 0;
+  for (int64_t cursor = g0; cursor < g1; ++cursor) {
+    if (seen[cursor] == 2) continue;
+    int32_t s = static_cast<int32_t>(cursor);   // a vertex of the next component
+    for (int pass = 0; pass < 2; ++pass) {
+      const char mark = static_cast<char>(3 + pass);
+      const size_t lv = bfs_last(s, mark);
+      int32_t best = queue[lv];
+      for (size_t i = lv; i < queue.size(); ++i)
+        if (deg(queue[i]) < deg(best) || (deg(queue[i]) == deg(best) && queue[i] < best)) best = queue[i];
+      for (int32_t v : queue) seen[v] = 0;
+      s = best;
+    }
+    // Cuthill-McKee from s
+    size_t head = static_cast<size_t>(placed);
+    order[g0 + placed++] = s;
+    seen[s] = 2;
+    while (head < static_cast<size_t>(placed)) {
+      const int32_t v = order[g0 + head++];
+      nb.clear();
+      for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+        const int32_t u = col[k];
+        if (u < g0 || u >= g1 || seen[u] == 2) continue;
+        seen[u] = 2;
+        nb.emplace_back(deg(u), u);
+      }
+      std::sort(nb.begin(), nb.end());
+      for (const auto &e : nb) order[g0 + placed++] = e.second;
+    }
+  }
+  std::reverse(order + g0, order + g1);
+}
+
+// The batch in reverse Cuthill-McKee order: rows permuted within each graph
+// (order[r] = the caller's vertex at row r), columns renumbered and sorted in
+// each row, weights carried along.
+struct PermutedCsr {
+  std::vector<int32_t> order;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> col;
+  std::vector<float> w;
+  std::vector<int64_t> vw;
+};
+
+PermutedCsr permute_batch(const int64_t *rp, const int32_t *col, const float *w, const int64_t *vw,
+                          const int64_t *gptr, int count, int64_t n) {
+  PermutedCsr P;
+  P.order.resize(static_cast<size_t>(n));
+  std::vector<char> seen(static_cast<size_t>(n), 0);
+  for_each_graph(count, [&](int q) { rcm_graph(rp, col, gptr[q], gptr[q + 1], seen, P.order.data()); });
+  std::vector<int32_t> pos(static_cast<size_t>(n));
+  for (int64_t r = 0; r < n; ++r) pos[P.order[r]] = static_cast<int32_t>(r);
+  P.rp.resize(static_cast<size_t>(n) + 1);
+  P.rp[0] = 0;
+  for (int64_t r = 0; r < n; ++r) P.rp[r + 1] = P.rp[r] + (rp[P.order[r] + 1] - rp[P.order[r]]);
+  const int64_t nnz = P.rp[n];
+  P.col.resize(static_cast<size_t>(nnz));
+  if (w) P.w.resize(static_cast<size_t>(nnz));
+  if (vw) {
+    P.vw.resize(static_cast<size_t>(n));
+    for (int64_t r = 0; r < n; ++r) P.vw[r] = vw[P.order[r]];
+  }
+  for_each_graph(count, [&](int q) {
+    std::vector<std::pair<int32_t, float>> row;
+    for (int64_t r = gptr[q]; r < gptr[q + 1]; ++r) {
+      const int32_t v = P.order[r];
+      row.clear();
+      for (int64_t k = rp[v]; k < rp[v + 1]; ++k) row.emplace_back(pos[col[k]], w ? w[k] : 0.f);
+      std::sort(row.begin(), row.end(), [](const std::pair<int32_t, float> &a, const std::pair<int32_t, float> &b) {
+        return a.first < b.first;
+      });
+      int64_t o = P.rp[r];
+      for (const auto &e : row) {
+        P.col[o] = e.first;
+        if (w) P.w[o] = e.second;
+        ++o;
+      }
+    }
+  });
+  return P;
+}
+
+}  // namespace
+}  // namespace sphynx
+
 using namespace sphynx;
 
 extern "C" int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, const float *edge_w,
@@ -1429,10 +1619,41 @@ extern "C" int sphynx_create_batch(const int64_t *row_ptr, const int32_t *col, c
     for (int q = 0; q < count; ++q)
       if (graph_ptr[q + 1] <= graph_ptr[q]) fail(SPHYNX_ERR_INVALID_ARG, "graph %d of the batch is empty", q);
     sphynx_handle h = nullptr;
-    const int rc = sphynx_create(row_ptr, col, edge_w, vtx_w, n, nnz, flags, stream, &h);
+    // host arrays: every graph's vertices go to reverse Cuthill-McKee order,
+    // so that a row's neighbours lie close to it and the products' gathers
+    // share cache lines (the caller's ids of a geometric graph are unrelated
+    // to its geometry); partition_batch maps its inputs and outputs back
+    const bool reorder = !(flags & SPHYNX_DEVICE_PTRS);
+    PermutedCsr P;
+    if (reorder) {
+      if (!row_ptr || !col || n < 1) fail(SPHYNX_ERR_INVALID_ARG, "NULL CSR array or empty batch");
+      if (row_ptr[0] != 0 || row_ptr[n] != nnz) fail(SPHYNX_ERR_INVALID_ARG, "row_ptr must run from 0 to nnz");
+      for (int64_t r = 0; r < n; ++r)
+        if (row_ptr[r + 1] < row_ptr[r]) fail(SPHYNX_ERR_INVALID_ARG, "row_ptr decreases at row %lld",
+                                                static_cast<long long>(r));
+      for (int64_t k = 0; k < nnz; ++k)
+        if (col[k] < 0 || col[k] >= n) fail(SPHYNX_ERR_INVALID_ARG, "column index out of range at entry %lld",
+                                            static_cast<long long>(k));
+      P = permute_batch(row_ptr, col, edge_w, vtx_w, graph_ptr, count, n);
+    }
+    const int rc = reorder ? sphynx_create(P.rp.data(), P.col.data(), edge_w ? P.w.data() : nullptr,
+                                           vtx_w ? P.vw.data() : nullptr, n, nnz, flags, stream, &h)
+                           : sphynx_create(row_ptr, col, edge_w, vtx_w, n, nnz, flags, stream, &h);
     if (rc != SPHYNX_OK) return rc;
     try {
       batch_setup(h, graph_ptr, count);
+      if (reorder) {
+        BatchInfo &B = h->batch;
+        B.orig.alloc(static_cast<size_t>(n) * sizeof(int32_t));
+        SPX_CUDA(cudaMemcpyAsync(B.orig.p, P.order.data(), static_cast<size_t>(n) * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, h->stream));
+        if (vtx_w) {
+          B.vw_orig.alloc(static_cast<size_t>(n) * sizeof(int64_t));
+          SPX_CUDA(cudaMemcpyAsync(B.vw_orig.p, vtx_w, static_cast<size_t>(n) * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, h->stream));
+        }
+        SPX_CUDA(cudaStreamSynchronize(h->stream));   // the host arrays above go out of scope
+      }
     } catch (...) {
       sphynx_destroy(h);
       throw;

@@ -929,6 +929,12 @@ int sphynx_eval(sphynx_handle g, const int32_t *part, int32_t K, double *cut, do
                 double *imbalance) {
   return guarded([&]() -> int {
     if (!g || !part) fail(SPHYNX_ERR_INVALID_ARG, "NULL argument");
+    if (g->batch.orig.p) {   // a reordered batch: the caller's part ids to row order first
+      int32_t *rows = static_cast<int32_t *>(g->workspace("eval_rows", static_cast<size_t>(g->n) * 4, false));
+      batch_parts_to_rows(g, part, rows);
+      eval_partition(g, rows, K, cut, cut_twice, imbalance);
+      return SPHYNX_OK;
+    }
     eval_partition(g, part, K, cut, cut_twice, imbalance);
     return SPHYNX_OK;
   });

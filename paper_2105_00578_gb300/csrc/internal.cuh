@@ -213,6 +213,11 @@ struct BatchInfo {
   DevBuf graph_chunk0;              // int32 [count + 1]: first chunk of each graph
   DevBuf graph_max;                 // uint64 [count][2]: max degree, max weighted degree (double bits)
   DevBuf row_graph;                 // int32 [n]: graph of every row (the chain reads its roots)
+  // rows in reverse Cuthill-McKee order within each graph (batches created
+  // from host arrays): orig[r] = the caller's vertex at internal row r, and
+  // the caller's vertex weights in the caller's order (multi-jagged runs there)
+  DevBuf orig;                      // int32 [n], empty: the caller's order
+  DevBuf vw_orig;                   // int64 [n] (vertex-weighted batches)
   // while a batched eigensolve runs: the 1024-row blocks and the chunks that
   // hold rows of graphs still iterating (rebuilt after every convergence
   // test), and their counts [blocks, chunks]; the products and the chunk
@@ -465,6 +470,9 @@ void launch_gram_reduce(cudaStream_t st, const double *partials, int nblk, int l
 // definiteness copies: kout receives the count k' <= k + SPHYNX_MAX_ADDED_ROOTS;
 // roots[k' .. k + SPHYNX_MAX_ADDED_ROOTS) = +inf, inv / invf = 1 / roots then 0
 // up to index k + SPHYNX_MAX_ADDED_ROOTS.
+// a reordered batch (sphynx_create_batch from host arrays): p_rows[r] =
+// p_caller[orig[r]] on the handle's stream (device arrays of n)
+void batch_parts_to_rows(sphynx_graph *g, const int32_t *p_caller, int32_t *p_rows);
 void launch_harmonic_ritz(cudaStream_t st, const double *alpha, const double *beta2, int k,
                           double *roots, double *inv, float *invf, int *err, int *kout);
 // count problems, problem q's arrays `stride` (>= k + SPHYNX_MAX_ADDED_ROOTS + 1) apart, err and kout [count]
