@@ -302,8 +302,6 @@ struct SpmmArgs {
   const int *done;         // device flag: skip the launch when nonzero (may be NULL)
   const int32_t *row_graph = nullptr;  // batches: graph of each row; in mode 1 its roots
   int inv_stride = 0;                  // are inv[row_graph[row] * inv_stride + i]
-  const int *gdone = nullptr;          // batches: rows of graph q are skipped while
-  int gdone_stride = 0;                // gdone[q * gdone_stride] is nonzero
   const int32_t *act_blocks = nullptr; // batches: 1024-row blocks holding rows of graphs still
   const int *n_act = nullptr;          // iterating (device list and count); NULL: every row
 };

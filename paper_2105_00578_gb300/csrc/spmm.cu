@@ -56,7 +56,7 @@ SpmmDev tune_args(sphynx_graph *g, const SpmmArgs &a) {
     s.t_out = base + out_bytes;
   }
   return SpmmDev{s.x,      s.ld_x, s.ld_y, s.y,     s.t_out,      s.yacc,       s.first,   s.yterms,
-                 s.inv,    s.invf, s.i_cur, nullptr, s.row_graph, s.inv_stride, nullptr, 0, nullptr, nullptr, s.x};
+                 s.inv,    s.invf, s.i_cur, nullptr, s.row_graph, s.inv_stride, nullptr, nullptr, s.x};
 }
 
 }  // namespace
@@ -165,8 +165,7 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
   if (a.mode == 1 && (a.yterms < 0 || a.yterms > 2 || (a.first && a.yterms != 2)))
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: polynomial step adds 0, 1 or 2 terms (2 on the first step)");
   SpmmDev d{a.x,   a.ld_x, a.ld_y, a.y,      a.t_out,    a.yacc,        a.first,  a.yterms,
-            a.inv, a.invf, a.i_cur, a.done, a.row_graph, a.inv_stride, a.gdone, a.gdone_stride,
-            a.act_blocks, a.n_act, a.x};
+            a.inv, a.invf, a.i_cur, a.done, a.row_graph, a.inv_stride, a.act_blocks, a.n_act, a.x};
   const bool prescaled = g->plan.prescale && a.lap == SPHYNX_NORMALIZED && a.tin != DT::BF16 && g->n > 0;
 
   // schedule: forced, or the one the autotuner chose for this graph at create

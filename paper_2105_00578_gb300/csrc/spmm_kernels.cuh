@@ -161,19 +161,12 @@ struct SpmmDev {              // kernel-side view of SpmmArgs
   const int *done;
   const int32_t *row_graph;  // batches: graph of every row, whose roots start at
   int inv_stride;            // inv[row_graph[row] * inv_stride] (NULL: one graph)
-  const int *gdone;          // batches: a row of graph q is skipped when gdone[q * gdone_stride]
-  int gdone_stride;          // is nonzero (its graph has finished); NULL: no row is skipped
   const int32_t *act_blocks; // batches: the 1024-row blocks (row >> 10) that hold a row of a graph
   const int *n_act;          // still iterating, and their count; a fixed grid walks the list
   const void *xe;            // the epilogue's own rows X_i (x itself, or X when x holds D^{-1/2} X)
 };
 
 constexpr int kListGrid = kSmCount * 16;   // CTAs of a launch that walks an active-block list
-
-// a row whose graph has finished iterating (batches): no gathers, no output
-__device__ __forceinline__ bool row_idle(const SpmmDev &a, int64_t row) {
-  return a.gdone && a.gdone[static_cast<int64_t>(__ldg(a.row_graph + row)) * a.gdone_stride] != 0;
-}
 
 // acc = sum_j w_ij (s_j) X_j of row `row`; epilogue applies the diagonal part.
 template <int LAP, typename TI, typename TT, int BP, int MODE>
@@ -714,8 +707,6 @@ __device__ __forceinline__ void short_rows(const LapView &L, const SpmmDev &a, i
   if (row0 >= L.n) return;  // uniform per warp
   const int64_t row = row0 + lane;
   const bool valid = row < L.n;
-  const bool idle = valid && row_idle(a, row);
-  if (__all_sync(kFull, !valid || idle)) return;   // every row's graph has finished
   int64_t rb = 0, re = 0;
   if (valid) {
     rb = __ldcs(L.rowptr + row);
@@ -741,7 +732,7 @@ __device__ __forceinline__ void short_rows(const LapView &L, const SpmmDev &a, i
     }
   }
   __syncwarp();
-  if (!valid || idle || re - rb > kShortDeg) return;
+  if (!valid || re - rb > kShortDeg) return;
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> acc;
   acc.zero();
@@ -817,8 +808,6 @@ __device__ __forceinline__ void sell_slice(const LapView &L, const SpmmDev &a, c
   using TA = typename AccOf<TI>::T;
   if (slice * 32 >= L.n) return;  // uniform per warp
   const int64_t row = slice * 32 + lane;
-  const bool idle = row < L.n && row_idle(a, row);
-  if (a.gdone && __all_sync(kFull, row >= L.n || idle)) return;   // every row's graph has finished
   const int64_t cbase = __ldg(cptr + slice);
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> acc;
@@ -828,7 +817,7 @@ __device__ __forceinline__ void sell_slice(const LapView &L, const SpmmDev &a, c
       // one 64-byte offset list and one mask per lane: no per-entry index stream
       const int16_t *pb = pcol + (cbase - kPatternTag);
       const int myoff = __ldg(pb + lane);
-      const unsigned mk = idle ? 0x80000000u : __ldg(reinterpret_cast<const unsigned *>(pb + 32) + lane);
+      const unsigned mk = __ldg(reinterpret_cast<const unsigned *>(pb + 32) + lane);
       const unsigned any = __reduce_or_sync(kFull, mk & 0x7fffffffu);
       const int nu = 32 - __clz(any);
       spmm_pattern_row<LAP, TI, BP>(L, x, static_cast<int>(row), myoff, mk, nu, acc);
@@ -840,7 +829,7 @@ __device__ __forceinline__ void sell_slice(const LapView &L, const SpmmDev &a, c
     }
   }
   if constexpr (KIND != 3) {
-    const bool valid = row < L.n && !idle;
+    const bool valid = row < L.n;
     const int sd = valid ? sdeg[row] : 0xFF;
     const int d = sd == 0xFF ? 0 : sd;
     const float *wp = W ? sw + __ldg(sptr + slice) + lane : nullptr;
@@ -924,12 +913,8 @@ k_spmm_group(const LapView L, const SpmmDev a, const int32_t *__restrict__ grow,
   int d = 0;
   if (r < rows) {
     row = __ldg(grow + u.x + r);
-    if (row_idle(a, row)) {
-      row = -1;
-    } else {
-      beg = __ldg(L.rowptr + row);
-      d = static_cast<int>(__ldg(L.rowptr + row + 1) - beg);
-    }
+    beg = __ldg(L.rowptr + row);
+    d = static_cast<int>(__ldg(L.rowptr + row + 1) - beg);
   }
   const int nl = d > gl ? ((d - gl - 1) >> lg) + 1 : 0;   // this lane's entries
   const int32_t *cp = L.col + beg + gl;
@@ -960,7 +945,6 @@ k_spmm_long(const LapView L, const SpmmDev a, const int64_t *__restrict__ items,
   const int lane = threadIdx.x & 31;
   const int64_t item = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (item >= n_items) return;
-  if (row_idle(a, items[item * 4])) return;   // uniform per warp
   const int64_t b = items[item * 4 + 1], e = items[item * 4 + 2];
   const TI *__restrict__ x = static_cast<const TI *>(a.x);
   RowAcc<TI, BP> racc;
@@ -998,7 +982,6 @@ k_spmm_finalize(const LapView L, const SpmmDev a, const int64_t *__restrict__ sp
   const int64_t t = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (t >= n_long) return;   // uniform per warp
   const int64_t row = split[t * 3], first = split[t * 3 + 1], cnt = split[t * 3 + 2];
-  if (row_idle(a, row)) return;
   TA acc[BP];
 #pragma unroll
   for (int c = 0; c < BP; ++c) acc[c] = TA(0);
