@@ -156,6 +156,12 @@ struct SpmmPlan {
   // gather costs a 32-byte sector per entry.  Set at create for irregular
   // graphs (maximum degree above 10 x the mean).
   bool prescale = false;
+  // Normalized products with bfloat16 input on irregular graphs read a
+  // per-entry coefficient c_ij = (w_ij or 1) D^{-1/2}_j, rounded in float as
+  // the kernels round it, from a stream (CSR order and SELL slot order)
+  // instead of gathering D^{-1/2}_j; built at the first such product.
+  DevBuf ncoef_csr;                  // float [nnz]
+  DevBuf ncoef_sell;                 // float [sell_entries]
   double pat_bytes = 0;              // bytes a product reads from this layout
   DevBuf pat_cptr;                   // int64 [n_slices]
   DevBuf pat_col;                    // 16-bit units, 96 per shared-pattern slice

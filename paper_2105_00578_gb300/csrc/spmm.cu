@@ -32,6 +32,45 @@ __global__ void k_prescale(const T *__restrict__ x, const T *__restrict__ dinv, 
   }
 }
 
+// c_k = (w_k or 1) * dinv[col_k] in float, the kernels' own rounding of the
+// normalized coefficient
+__global__ void k_ncoef_csr(const int32_t *__restrict__ col, const float *__restrict__ w,
+                            const float *__restrict__ dinvf, int64_t nnz, float *__restrict__ c) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nnz;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float wk = w ? w[k] : 1.f;
+    c[k] = wk * dinvf[col[k]];
+  }
+}
+
+// the short rows' coefficients into SELL slot order (the layout of sell_w)
+__global__ void k_ncoef_sell(const int64_t *__restrict__ rp, const float *__restrict__ c, int64_t n,
+                             const uint8_t *__restrict__ sdeg, const int64_t *__restrict__ sptr, float *__restrict__ cs) {
+  const int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (row >= n) return;
+  const int d = sdeg[row];
+  if (d == 0xFF) return;
+  const int64_t b = sptr[row >> 5] + (row & 31), src = rp[row];
+  for (int t = 0; t < d; ++t) cs[b + 32 * t] = c[src + t];
+}
+
+void ensure_ncoef(sphynx_graph *g) {
+  SpmmPlan &p = g->plan;
+  if (p.ncoef_csr.p) return;
+  p.ncoef_csr.alloc(static_cast<size_t>(g->nnz > 0 ? g->nnz : 1) * sizeof(float));
+  p.ncoef_sell.alloc(static_cast<size_t>(p.sell_entries > 0 ? p.sell_entries : 1) * sizeof(float));
+  const unsigned gc = static_cast<unsigned>(std::min<int64_t>((g->nnz + 255) / 256, 16 * kSmCount));
+  if (g->nnz > 0) {
+    k_ncoef_csr<<<gc, 256, 0, g->stream>>>(g->col, g->w, g->dinvf.as<float>(), g->nnz, p.ncoef_csr.as<float>());
+    SPX_LAUNCHED();
+  }
+  k_ncoef_sell<<<static_cast<unsigned>((g->n + 255) / 256), 256, 0, g->stream>>>(
+      g->rowptr, p.ncoef_csr.as<float>(), g->n, p.sell_deg.as<uint8_t>(), p.sell_ptr.as<int64_t>(),
+      p.ncoef_sell.as<float>());
+  SPX_LAUNCHED();
+  g->ctr.launches += 2;
+}
+
 void dispatch(sphynx_graph *g, const SpmmArgs &a, const SpmmDev &d) {
   switch (a.tin) {
     case DT::F64: spmm_dispatch_f64(g, a, d); break;
@@ -56,7 +95,7 @@ SpmmDev tune_args(sphynx_graph *g, const SpmmArgs &a) {
     s.t_out = base + out_bytes;
   }
   return SpmmDev{s.x,      s.ld_x, s.ld_y, s.y,     s.t_out,      s.yacc,       s.first,   s.yterms,
-                 s.inv,    s.invf, s.i_cur, nullptr, s.row_graph, s.inv_stride, nullptr, nullptr, s.x};
+                 s.inv,    s.invf, s.i_cur, nullptr, s.row_graph, s.inv_stride, nullptr, nullptr, s.x, nullptr, nullptr};
 }
 
 }  // namespace
@@ -165,8 +204,14 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
   if (a.mode == 1 && (a.yterms < 0 || a.yterms > 2 || (a.first && a.yterms != 2)))
     fail(SPHYNX_ERR_INVALID_ARG, "spmm: polynomial step adds 0, 1 or 2 terms (2 on the first step)");
   SpmmDev d{a.x,   a.ld_x, a.ld_y, a.y,      a.t_out,    a.yacc,        a.first,  a.yterms,
-            a.inv, a.invf, a.i_cur, a.done, a.row_graph, a.inv_stride, a.act_blocks, a.n_act, a.x};
+            a.inv, a.invf, a.i_cur, a.done, a.row_graph, a.inv_stride, a.act_blocks, a.n_act, a.x, nullptr, nullptr};
   const bool prescaled = g->plan.prescale && a.lap == SPHYNX_NORMALIZED && a.tin != DT::BF16 && g->n > 0;
+  const bool coefs = g->plan.prescale && a.lap == SPHYNX_NORMALIZED && a.tin == DT::BF16 && g->n > 0;
+  if (coefs) {
+    ensure_ncoef(g);
+    d.coef_csr = g->plan.ncoef_csr.as<float>();
+    d.coef_sell = g->plan.ncoef_sell.as<float>();
+  }
 
   // schedule: forced, or the one the autotuner chose for this graph at create
   g->plan.variant = g->plan.forced >= 0 ? g->plan.forced : g->plan.tuned_variant;
@@ -187,6 +232,7 @@ void spmm(sphynx_graph *g, const SpmmArgs &a) {
       g->plan.med_bytes + g->plan.long_bytes;
   double bytes = graph_bytes + n * b * si + n * sa;
   if (prescaled) bytes += 3.0 * n * b * si;   // the pass reads X and writes Z; the epilogue reads X again
+  if (coefs && !g->weighted) bytes += 4.0 * nnz;   // the coefficient stream (weighted graphs: in place of the weights)
   if (a.mode == 0) {
     bytes += n * b * sa;
   } else {

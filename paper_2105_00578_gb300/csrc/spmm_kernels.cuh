@@ -164,6 +164,8 @@ struct SpmmDev {              // kernel-side view of SpmmArgs
   const int32_t *act_blocks; // batches: the 1024-row blocks (row >> 10) that hold a row of a graph
   const int *n_act;          // still iterating, and their count; a fixed grid walks the list
   const void *xe;            // the epilogue's own rows X_i (x itself, or X when x holds D^{-1/2} X)
+  const float *coef_csr;     // normalized: per-entry (w_ij or 1) D^{-1/2}_j in CSR order (NULL: gather D^{-1/2}_j)
+  const float *coef_sell;    // the same in SELL slot order
 };
 
 constexpr int kListGrid = kSmCount * 16;   // CTAs of a launch that walks an active-block list
@@ -1002,6 +1004,10 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
   using TA = typename AccOf<TI>::T;
   LapView L = g->view();
   if (a.xe != a.x) L.gather_scale = 0;   // x holds D^{-1/2} X
+  if (a.coef_csr) {                      // the coefficients already hold D^{-1/2}_j
+    L.w = a.coef_csr;
+    L.gather_scale = 0;
+  }
   cudaStream_t st = g->stream;
   const int64_t warps = (g->n + 31) / 32;
   const int64_t grid = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
@@ -1013,7 +1019,7 @@ void spmm_launch_t(sphynx_graph *g, const SpmmDev &a) {
       const unsigned gs = a.act_blocks ? static_cast<unsigned>(kListGrid)
                                        : static_cast<unsigned>(((warps + (int64_t{4} << ls) - 1) >> (ls + 2)) << ls);
       const int16_t *sc = p.sell_col.as<int16_t>();
-      const float *swp = p.sell_w.as<float>();
+      const float *swp = a.coef_sell ? a.coef_sell : p.sell_w.as<float>();
       const int64_t *sp = p.sell_ptr.as<int64_t>();
       const uint8_t *sd = p.sell_deg.as<uint8_t>();
       bool launched = false;
@@ -1077,7 +1083,7 @@ void spmm_bp(sphynx_graph *g, const SpmmDev &a, int bp) {
 
 template <typename TI, typename TT, int MODE>
 void spmm_lapw(sphynx_graph *g, const SpmmDev &a, int lap, int bp) {
-  const bool w = g->weighted;
+  const bool w = g->weighted || a.coef_csr != nullptr;
   if (bp == 1) {
     if constexpr (MODE == 0 && !std::is_same<TI, __nv_bfloat16>::value) {
       if (lap == SPHYNX_NORMALIZED) {
