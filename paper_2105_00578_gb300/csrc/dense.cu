@@ -157,10 +157,10 @@ k_update(int64_t n, const T *s0, const T *s1, const T *s2, const T *l1, const T 
 // ---------------------------------------------------------------------------
 // R = L X - B X Theta (Algorithm 1: the residual), ||r_c||^2_{B^-1} partials, and
 // the Jacobi scaling H = diag(L)^{-1} R (Sec. 5.1) when jinv is given.
-template <typename T, int LD>
+template <typename T, int LD, typename TO = T>
 __global__ void __launch_bounds__(256)
 k_residual(int64_t n, const T *x, const T *lx, const double *theta, const T *bdiag, const T *jinv,
-           T *out, double *partials, const int *done) {
+           TO *out, double *partials, const int *done) {
   __shared__ double red[256 / 32][LD];
   if (done && *done) return;
   T th[LD];
@@ -183,7 +183,14 @@ k_residual(int64_t n, const T *x, const T *lx, const double *theta, const T *bdi
       acc[c] += r[c] * r[c] * ib;
       r[c] *= sc;
     }
-    row_store<T, LD>(out + row * LD, r);
+    if constexpr (std::is_same<TO, __nv_bfloat16>::value) {
+      // the norms above use the float residual; only the stored copy is rounded
+#pragma unroll
+      for (int c = 0; c < LD; c += 2)
+        *reinterpret_cast<__nv_bfloat162 *>(out + row * LD + c) = __floats2bfloat162_rn(r[c], r[c + 1]);
+    } else {
+      row_store<T, LD>(out + row * LD, r);
+    }
   }
   // block reduction in double, fixed order
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -684,6 +691,15 @@ static void residual_ld(cudaStream_t st, const ResidualArgs &a, int grid) {
   } else {
     bd = a.bdiagf;
     jv = a.jinvf;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (a.out_bf16) {
+      k_residual<float, LD, __nv_bfloat16><<<grid, 256, 0, st>>>(
+          a.n, static_cast<const float *>(a.x), static_cast<const float *>(a.lx), a.theta, bd, jv,
+          static_cast<__nv_bfloat16 *>(a.out), a.norm_partials, a.done);
+      SPX_LAUNCHED();
+      return;
+    }
   }
   k_residual<T, LD><<<grid, 256, 0, st>>>(a.n, static_cast<const T *>(a.x), static_cast<const T *>(a.lx),
                                           a.theta, bd, jv, static_cast<T *>(a.out), a.norm_partials, a.done);

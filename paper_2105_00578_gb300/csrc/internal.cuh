@@ -375,6 +375,7 @@ struct ResidualArgs {
   void *out;                 // R or H = Jacobi(R)
   double *norm_partials;     // [grid][ld]
   const int *done;
+  int out_bf16 = 0;          // float blocks: out stored in bfloat16 (the mixed chain's first input)
 };
 int residual_grid(int64_t n);
 void launch_residual(cudaStream_t st, const ResidualArgs &a, int grid);

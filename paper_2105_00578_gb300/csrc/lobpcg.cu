@@ -136,7 +136,8 @@ void poly_setup(sphynx_graph *g, const sphynx_options *o) {
 }
 
 // H = p(L) R in product form; R and H are n x ld blocks of the block type
-void poly_apply(sphynx_graph *g, int precision, const void *r, void *h, int ld, int b, const int *done) {
+void poly_apply(sphynx_graph *g, int precision, const void *r, void *h, int ld, int b, const int *done,
+                bool r_bf16 = false) {
   const int k = g->poly_k;
   const DT dt = block_dt(precision), ct = chain_dt(precision);
   if (k == 1) {
@@ -151,7 +152,7 @@ void poly_apply(sphynx_graph *g, int precision, const void *r, void *h, int ld, 
   for (int i = 0; i + 1 < k; ++i) {
     SpmmArgs a{};
     a.lap = g->poly_laplacian;
-    a.tin = i == 0 ? dt : ct;
+    a.tin = i == 0 ? (r_bf16 ? DT::BF16 : dt) : ct;
     a.ld_x = ld;
     a.ld_y = ld;
     a.bp = ld;
@@ -284,6 +285,11 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   // the residual kernel writes H directly unless the polynomial or the multigrid cycle needs R
   const bool pre_r = o->precond == SPHYNX_PRECOND_POLY || o->precond == SPHYNX_PRECOND_AMG;
   void *res_out = pre_r ? R : H;
+  // mixed precision with the polynomial: R is only the chain's input, whose
+  // later vectors are stored in bfloat16 anyway, so the residual kernel
+  // stores it in bfloat16 (its norms come from the float values) and the
+  // first chain step gathers half the bytes
+  const bool r_bf16 = o->precond == SPHYNX_PRECOND_POLY && o->precision == SPHYNX_MIXED_BF16 && g->poly_k >= 2;
 
   // initial block
   if (x0_host) {
@@ -309,6 +315,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   plain_spmm(g, lap, dt, X[1], LX[1], ld, b, done);
   ResidualArgs ra{dt, ld, n, X[1], LX[1], state->theta, bd, bdf, jac ? g->jinv.as<double>() : nullptr,
                   jac ? g->jinvf.as<float>() : nullptr, res_out, npart, done};
+  ra.out_bf16 = r_bf16 ? 1 : 0;
   launch_residual(st, ra, rgrid);
   const int abs_test = o->conv == SPHYNX_CONV_ABS ? 1 : 0;
   launch_converge(st, state, npart, rgrid, b, ld, o->tol, floor_th, floor_res, 0, o->max_iter, 0, abs_test);
@@ -320,7 +327,7 @@ EigenResult lobpcg(sphynx_graph *g, const sphynx_options *o, int b, const double
   int *hflag = static_cast<int *>(g->host_flag);
   for (int it = 0; it < o->max_iter; ++it) {
     const int nx = cur ^ 1;
-    if (o->precond == SPHYNX_PRECOND_POLY) poly_apply(g, o->precision, R, H, ld, b, done);   // precondition
+    if (o->precond == SPHYNX_PRECOND_POLY) poly_apply(g, o->precision, R, H, ld, b, done, r_bf16);   // precondition
     if (o->precond == SPHYNX_PRECOND_AMG) amg_apply(g, dt, R, H, ld, done);
     plain_spmm(g, lap, dt, H, LH, ld, b, done);
     GramArgs g3{dt, 3, ld, n, {X[cur], H, P[cur]}, {LX[cur], LH, LP[cur]}, bd, bdf, gpart, ga, gb, done};
