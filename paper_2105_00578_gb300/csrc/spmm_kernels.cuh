@@ -792,10 +792,13 @@ k_spmm_short(const LapView L, const SpmmDev a) {
 // 16 (32 registers a thread, every warp slot of the SM) for rows of at most
 // 16 bytes, 8 (64 registers) for 32-byte float rows.
 template <typename TI, int BP> struct SellOccupancy {
+  static constexpr bool f32 = std::is_same<TI, float>::value;
+  // float rows of 12 and 16 values: without a bound the explicit-slice path
+  // took 134-180 registers, three resident blocks, and its gathers waited
   static constexpr int blocks =
-      ((std::is_same<TI, __nv_bfloat16>::value && BP <= 8) || (std::is_same<TI, float>::value && BP <= 4))
+      ((std::is_same<TI, __nv_bfloat16>::value && BP <= 8) || (f32 && BP <= 4))
           ? 16
-          : (std::is_same<TI, float>::value && BP == 8 ? 8 : 1);
+          : (f32 && BP == 8 ? 8 : (f32 && BP == 12 ? 6 : (f32 && BP == 16 ? 4 : 1)));
 };
 
 // Slice kinds a launch may meet.  KIND 0: explicit slices of 16- or 32-bit
