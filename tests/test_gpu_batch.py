@@ -225,3 +225,49 @@ def test_largest_graphs_of_the_2000_graph_batch_match_the_oracle():
             assert abs(cuts[q] - e["cut"]) <= 0.02 * e["cut"], (q, cuts[q], e["cut"])
     finally:
         spx.sphynx_destroy(h)
+
+
+def test_reordered_batch_agrees_with_the_callers_order():
+    """A batch created from host arrays is stored with each graph in reverse
+    Cuthill-McKee order; one created from device arrays keeps the caller's
+    order.  Both draw the same random numbers per vertex and report parts in
+    the caller's numbering, so in FP64 they reach the same Ritz values and,
+    up to the order of floating-point sums, the same partitions: every cut is
+    the oracle's cut of the returned parts, and the two runs' cuts agree
+    within 3 % (or two edges).  Vertices of each graph are first shuffled so that the
+    caller's order carries no locality at all."""
+    import paper_2105_00578_gb300 as spx
+    torch = torch_mod()
+    rng = np.random.default_rng(5)
+    graphs = []
+    for i, n in enumerate([900, 2500, 1600]):
+        g = W.rgg(n, seed=70 + i)
+        perm = rng.permutation(g.n)
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(g.n)
+        rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+        newr, newc = inv[rows], inv[g.col]
+        order = np.lexsort((newc, newr))
+        rp = np.zeros(g.n + 1, dtype=np.int64)
+        np.add.at(rp, newr + 1, 1)
+        graphs.append(W.graphs.CSRGraph(g.n, np.cumsum(rp), newc[order].astype(np.int32)))
+    big, gptr = W.concat_graphs(graphs)
+    opt = spx.options(laplacian="combinatorial", precond="jacobi", precision="fp64", tol=1e-3, seed=3)
+    rp_d = torch.from_numpy(big.row_ptr).cuda()
+    col_d = torch.from_numpy(big.col).cuda()
+    results = []
+    for flags, rp_, col_ in ((spx.HOST_PTRS, big.row_ptr, big.col), (spx.DEVICE_PTRS, rp_d, col_d)):
+        h = spx.sphynx_create_batch(rp_, col_, gptr, flags=flags, nnz=big.nnz)
+        try:
+            parts = np.full(big.n, -1, dtype=np.int32)
+            code, cuts, imbs, eigs, iters, status, _ = spx.sphynx_partition_batch(h, 4, opt, parts, len(graphs))
+            assert code == 0 and np.all(status == 0)
+            for q, gq in enumerate(graphs):
+                pq = parts[gptr[q]:gptr[q + 1]]
+                assert O.cutsize(gq, pq)[0] == cuts[q]
+            results.append((cuts, eigs))
+        finally:
+            spx.sphynx_destroy(h)
+    (c_host, e_host), (c_dev, e_dev) = results
+    assert np.allclose(e_host[:, 1:], e_dev[:, 1:], rtol=1e-5)
+    assert np.all(np.abs(c_host - c_dev) <= np.maximum(2.0, 0.03 * c_dev))
